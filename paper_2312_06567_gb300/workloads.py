@@ -1,0 +1,251 @@
+"""Seeded synthetic workloads: problem definitions and input generators.
+
+This module holds problem data only -- sizes, gas parameters, the analytic
+macroscopic initial fields and seeded random test states -- and none of the
+solver's arithmetic.  It is the one module that both the CUDA path's callers
+and the CPU oracle's tests draw inputs from.
+
+No public dataset, mesh or checkpoint stands behind these problems; they are
+analytic stand-ins with the structure of the paper's workloads (hex elements,
+uniform Cartesian velocity grids, Maxwellian initial data, a normal shock for
+the hypersonic physics).
+
+Layout conventions (shared by every caller):
+  element  e = e1 + n1 (e2 + n2 e3)
+  node     s = i1 + (p+1) (i2 + (p+1) i3)   (Gauss--Legendre nodes per axis)
+  velocity k = k1 + n1 (k2 + n2 k3)         (uniform nodes per axis)
+  state    f[c][k][e][s], c = 0 for F, 1 for G (delta > 0 only)
+"""
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+from numpy.polynomial.legendre import leggauss
+
+
+def mu_from_knudsen(kn, theta_ref=1.0, rho_ref=1.0, length=1.0):
+    """mu_ref from a Knudsen number via the hard-sphere-like mean free path
+    lambda = (mu/rho) sqrt(pi/(2 theta)) used by the paper's Kn_GLL."""
+    return kn * rho_ref * length * math.sqrt(2.0 * theta_ref / math.pi)
+
+
+def normal_shock_states(mach, gamma, rho1=1.0, theta1=1.0):
+    """Upstream and downstream (rho, u, theta) of a stationary normal shock
+    (Rankine--Hugoniot relations; sound speed sqrt(gamma theta))."""
+    u1 = mach * math.sqrt(gamma * theta1)
+    m2 = mach * mach
+    rho2 = rho1 * (gamma + 1.0) * m2 / ((gamma - 1.0) * m2 + 2.0)
+    p1 = rho1 * theta1
+    p2 = p1 * (1.0 + 2.0 * gamma / (gamma + 1.0) * (m2 - 1.0))
+    u2 = u1 * rho1 / rho2
+    return (rho1, u1, theta1), (rho2, u2, p2 / rho2)
+
+
+@dataclass
+class Workload:
+    name: str
+    mesh_n: tuple
+    mesh_lo: tuple
+    mesh_hi: tuple
+    periodic: tuple
+    p: int
+    vel_n: tuple
+    vel_lo: tuple
+    vel_hi: tuple
+    delta: float
+    Pr: float
+    mu_ref: float
+    theta_ref: float
+    theta_S: float
+    cfl: float
+    steps: int
+    init: object = None                     # x[..., 3] -> (rho, U[..., 3], theta)
+    dirichlet: dict = field(default_factory=dict)   # {(d, side): (rho, U(3), theta)}
+
+    @property
+    def n_elem(self):
+        return self.mesh_n[0] * self.mesh_n[1] * self.mesh_n[2]
+
+    @property
+    def n_sol(self):
+        return (self.p + 1) ** 3
+
+    @property
+    def n_vel(self):
+        return self.vel_n[0] * self.vel_n[1] * self.vel_n[2]
+
+    @property
+    def n_comp(self):
+        return 2 if self.delta > 0 else 1
+
+    @property
+    def dof(self):
+        return self.n_elem * self.n_sol * self.n_vel
+
+    def h_min(self):
+        return min((self.mesh_hi[d] - self.mesh_lo[d]) / self.mesh_n[d] for d in range(3))
+
+    def u_max(self):
+        return max(max(abs(self.vel_lo[d]), abs(self.vel_hi[d])) for d in range(3))
+
+    def dt(self):
+        """dt = CFL h_min / (u_max (2p+1))."""
+        return self.cfl * self.h_min() / (self.u_max() * (2 * self.p + 1))
+
+    def replace(self, **kw):
+        d = dict(self.__dict__)
+        d.update(kw)
+        return Workload(**d)
+
+
+# ---- analytic initial fields ---------------------------------------------
+def _init_sine_density(x):
+    rho = 1.0 + 0.1 * np.sin(2.0 * np.pi * x[..., 0])
+    return rho, np.zeros(x.shape), np.ones(x.shape[:-1])
+
+
+def _init_taylor_green(x, mach=0.1):
+    X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+    U = np.stack([mach * np.sin(X) * np.cos(Y) * np.cos(Z),
+                  -mach * np.cos(X) * np.sin(Y) * np.cos(Z),
+                  np.zeros_like(X)], axis=-1)
+    P = 1.0 + mach * mach / 16.0 * (np.cos(2 * X) + np.cos(2 * Y)) * (np.cos(2 * Z) + 2.0)
+    theta = np.ones_like(X)
+    return P / theta, U, theta
+
+
+def _shock_init(width, s1, s2):
+    def init(x):
+        blend = 0.5 * (1.0 + np.tanh(x[..., 0] / width))
+        rho = s1[0] + (s2[0] - s1[0]) * blend
+        ux = s1[1] + (s2[1] - s1[1]) * blend
+        theta = s1[2] + (s2[2] - s1[2]) * blend
+        U = np.zeros(x.shape)
+        U[..., 0] = ux
+        return rho, U, theta
+    return init
+
+
+THETA_S_RATIO = 110.4 / 203.0      # Sutherland 110.4 K over a 203 K freestream
+
+
+def periodic_sine_box():
+    """Small plain-method case: [0,1]^3, 4^3 hex, p=1, 8^3 velocities on [-6,6]^3,
+    BGK (Pr=1), monatomic, Kn=0.1, rho = 1 + 0.1 sin(2 pi x), U = 0, theta = 1."""
+    return Workload("periodic_sine_box_4x4x4_p1_u8", (4, 4, 4), (0, 0, 0), (1, 1, 1),
+                    (True, True, True), 1, (8, 8, 8), (-6, -6, -6), (6, 6, 6),
+                    0.0, 1.0, mu_from_knudsen(0.1), 1.0, THETA_S_RATIO, 0.1, 10,
+                    init=_init_sine_density)
+
+
+def taylor_green_box():
+    """Throughput case: [0,2pi]^3, 16^3 hex, p=3, 24^3 velocities on [-5,5]^3,
+    ES-BGK Pr=2/3, monatomic, Kn=0.01, Taylor--Green field at M=0.1, theta=1."""
+    two_pi = 2.0 * math.pi
+    return Workload("taylor_green_16x16x16_p3_u24", (16, 16, 16), (0, 0, 0),
+                    (two_pi, two_pi, two_pi), (True, True, True), 3, (24, 24, 24),
+                    (-5, -5, -5), (5, 5, 5), 0.0, 2.0 / 3.0, mu_from_knudsen(0.01), 1.0,
+                    THETA_S_RATIO, 0.1, 100, init=_init_taylor_green)
+
+
+def normal_shock_tube(mach=8.0, width=2.0):
+    """Hypersonic normal shock: [-20,40]x[0,1]^2 mean free paths, 64x4x4 hex, p=2,
+    32^3 velocities on [-30,30]x[-15,15]^2, diatomic delta=2 (F and G), ES-BGK
+    Pr=0.72, Sutherland with mu_ref from lambda_1 = 1; M=8 upstream at theta=1,
+    Rankine--Hugoniot downstream (gamma=1.4), tanh blend of width 2 at x=0;
+    Dirichlet x-ends, periodic y and z."""
+    s1, s2 = normal_shock_states(mach, 1.4)
+    dirichlet = {(0, -1): (s1[0], (s1[1], 0.0, 0.0), s1[2]),
+                 (0, 1): (s2[0], (s2[1], 0.0, 0.0), s2[2])}
+    return Workload("normal_shock_64x4x4_p2_u32_d2", (64, 4, 4), (-20, 0, 0), (40, 1, 1),
+                    (False, True, True), 2, (32, 32, 32), (-30, -15, -15), (30, 15, 15),
+                    2.0, 0.72, mu_from_knudsen(1.0), 1.0, THETA_S_RATIO, 0.1, 2000,
+                    init=_shock_init(width, s1, s2), dirichlet=dirichlet)
+
+
+# ---- sampled inputs --------------------------------------------------------
+def node_positions(wl):
+    """Solution node coordinates x[Ne, Ns, 3] (numpy's Gauss--Legendre nodes)."""
+    q = wl.p + 1
+    xi = leggauss(q)[0]
+    i3, i2, i1 = np.meshgrid(np.arange(q), np.arange(q), np.arange(q), indexing="ij")
+    loc = [xi[i1.ravel()], xi[i2.ravel()], xi[i3.ravel()]]
+    n1, n2, n3 = wl.mesh_n
+    e = np.arange(wl.n_elem)
+    c = [e % n1, (e // n1) % n2, e // (n1 * n2)]
+    x = np.empty((wl.n_elem, q ** 3, 3))
+    for d in range(3):
+        h = (wl.mesh_hi[d] - wl.mesh_lo[d]) / wl.mesh_n[d]
+        x[:, :, d] = wl.mesh_lo[d] + (c[d][:, None] + 0.5 * (loc[d][None, :] + 1.0)) * h
+    return x
+
+
+def velocity_nodes(wl):
+    """u[Nu, 3] in the k = k1 + n1 (k2 + n2 k3) order."""
+    ax = [np.linspace(wl.vel_lo[d], wl.vel_hi[d], wl.vel_n[d]) for d in range(3)]
+    k3, k2, k1 = np.meshgrid(*(np.arange(wl.vel_n[d]) for d in (2, 1, 0)), indexing="ij")
+    return np.stack([ax[0][k1.ravel()], ax[1][k2.ravel()], ax[2][k3.ravel()]], axis=1)
+
+
+def gaussian_samples(u, rho, U, cov):
+    """rho / sqrt(det(2 pi cov)) exp(-(u-U)^T cov^-1 (u-U)/2) for every (velocity,
+    point): u[Nu,3], rho[P], U[P,3], cov[P,3,3] -> [Nu, P].  Initial-data sampler."""
+    inv = np.linalg.inv(cov)
+    c = u[:, None, :] - U[None, :, :]
+    quad = np.einsum("kpi,pij,kpj->kp", c, inv, c)
+    return (rho / np.sqrt(np.linalg.det(2.0 * np.pi * cov)))[None, :] * np.exp(-0.5 * quad)
+
+
+def maxwellian_state(wl, x=None, fields=None):
+    """f[C, Nu, Ne, Ns] = the isotropic Maxwellian of the initial field at each node
+    (G = delta theta / 2 F)."""
+    if x is None:
+        x = node_positions(wl)
+    rho, U, theta = fields if fields is not None else wl.init(x)
+    P = wl.n_elem * wl.n_sol
+    rho, U, theta = (np.broadcast_to(rho, x.shape[:-1]).reshape(P),
+                     np.broadcast_to(U, x.shape).reshape(P, 3),
+                     np.broadcast_to(theta, x.shape[:-1]).reshape(P))
+    cov = theta[:, None, None] * np.eye(3)[None]
+    F = gaussian_samples(velocity_nodes(wl), rho, U, cov)
+    f = np.empty((wl.n_comp, wl.n_vel, wl.n_elem, wl.n_sol))
+    f[0] = F.reshape(wl.n_vel, wl.n_elem, wl.n_sol)
+    if wl.n_comp == 2:
+        f[1] = (0.5 * wl.delta * theta)[None, :].reshape(1, wl.n_elem, wl.n_sol) * f[0]
+    return f
+
+
+def random_anisotropic_state(wl, seed, spread=0.3, bimodal=0.3):
+    """Seeded non-equilibrium state: at every node a mixture of two Gaussians with
+    random means and random SPD covariances around the initial field, so that
+    Pi/rho is anisotropic and the element data are discontinuous."""
+    rng = np.random.default_rng(seed)
+    x = node_positions(wl)
+    rho, U, theta = wl.init(x)
+    P = wl.n_elem * wl.n_sol
+    rho = np.broadcast_to(rho, x.shape[:-1]).reshape(P) * (1 + 0.2 * rng.uniform(-1, 1, P))
+    U = np.broadcast_to(U, x.shape).reshape(P, 3) + 0.3 * rng.standard_normal((P, 3))
+    theta = np.broadcast_to(theta, x.shape[:-1]).reshape(P) * (1 + 0.3 * rng.uniform(-1, 1, P))
+    u = velocity_nodes(wl)
+    total = np.zeros((wl.n_vel, P))
+    for part, frac in ((0, 1.0 - bimodal), (1, bimodal)):
+        a = rng.standard_normal((P, 3, 3)) * spread
+        cov = theta[:, None, None] * (np.eye(3)[None] + np.einsum("pij,pkj->pik", a, a))
+        shift = 0.0 if part == 0 else 0.8 * np.sqrt(theta)[:, None] * rng.standard_normal((P, 3))
+        total += frac * gaussian_samples(u, rho, U + shift, cov)
+    f = np.empty((wl.n_comp, wl.n_vel, wl.n_elem, wl.n_sol))
+    f[0] = total.reshape(wl.n_vel, wl.n_elem, wl.n_sol)
+    if wl.n_comp == 2:
+        z = 0.5 * wl.delta * theta * (1 + 0.2 * rng.uniform(-1, 1, P))
+        f[1] = z.reshape(1, wl.n_elem, wl.n_sol) * f[0]
+    return f
+
+
+def reduced(wl, mesh_n=None, vel_n=None):
+    """Same physics and domain with fewer elements and/or velocity nodes."""
+    kw = {}
+    if mesh_n is not None:
+        kw["mesh_n"] = tuple(mesh_n)
+    if vel_n is not None:
+        kw["vel_n"] = tuple(vel_n)
+    return wl.replace(name=wl.name + "_reduced", **kw)

@@ -1,0 +1,237 @@
+"""Pins of the oracle's BGK source: the conservative Q' solve, the ES tensor,
+fixed points, the discrete relaxation law of SSP-RK3, the discrete H-theorem
+and exact conservation."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import bgk, dual, stage
+from oracle.mesh import BoxMesh
+from oracle.velocity import VelocityGrid
+from paper_2312_06567_gb300 import workloads as W
+
+
+def _random_points(P, seed, anis=0.25, bimodal=0.3, U_scale=0.4):
+    rng = np.random.default_rng(seed)
+    rho = rng.uniform(0.6, 1.6, P)
+    U = U_scale * rng.standard_normal((P, 3))
+    theta = rng.uniform(0.7, 1.3, P)
+    return rng, rho, U, theta
+
+
+def _bimodal(vg, seed, P=12, anis=0.25, bimodal=0.3):
+    rng, rho, U, theta = _random_points(P, seed)
+    f = np.zeros((vg.size, P))
+    for part, frac in ((0, 1 - bimodal), (1, bimodal)):
+        a = anis * rng.standard_normal((P, 3, 3))
+        cov = theta[:, None, None] * (np.eye(3) + np.einsum("pij,pkj->pik", a, a))
+        shift = 0 if part == 0 else 0.7 * rng.standard_normal((P, 3))
+        f += frac * W.gaussian_samples(vg.u, rho, U + shift, cov)
+    return f, theta
+
+
+def _fsum_moments(vg, F, G=None):
+    """Q = (rho, rho U, E) by exactly rounded sums (math.fsum), plain loops."""
+    out = []
+    for p in range(F.shape[1]):
+        rho = math.fsum(vg.w[k] * F[k, p] for k in range(vg.size))
+        mom = [math.fsum(vg.w[k] * vg.u[k, d] * F[k, p] for k in range(vg.size)) for d in range(3)]
+        E = math.fsum(vg.w[k] * 0.5 * (vg.u[k] @ vg.u[k]) * F[k, p] for k in range(vg.size))
+        if G is not None:
+            E = math.fsum([E] + [vg.w[k] * G[k, p] for k in range(vg.size)])
+        out.append([rho] + mom + [E])
+    return np.array(out)
+
+
+def test_gamma_and_internal_energy():
+    assert bgk.Gas(delta=0).gamma == pytest.approx(5 / 3, abs=1e-15)
+    assert bgk.Gas(delta=2).gamma == pytest.approx(7 / 5, abs=1e-15)
+    # A sampled Maxwellian with G = delta theta/2 F on a fine grid returns its own
+    # theta: E = rho|U|^2/2 + (3+delta)/2 rho theta.
+    vg = VelocityGrid((28, 28, 28), (-8, -8, -8), (8, 8, 8))
+    _, rho, U, theta = _random_points(5, 11)
+    for delta in (0.0, 2.0, 3.5):
+        gas = bgk.Gas(delta=delta)
+        F = bgk.maxwellian(vg, rho, U, theta)
+        G = 0.5 * delta * theta[None, :] * F if delta > 0 else None
+        r, Um, E, th, P, Pi = bgk.macroscopic(bgk.raw_moments(F, G, vg), gas)
+        assert np.allclose(th, theta, rtol=1e-11)
+        assert np.allclose(Um, U, atol=1e-11)
+        assert np.allclose(Pi / r[:, None, None], theta[:, None, None] * np.eye(3), atol=1e-10)
+
+
+def test_collision_time_special_cases():
+    gas = bgk.Gas(Pr=0.72, mu_ref=0.3, theta_ref=2.0, theta_S=0.5)
+    assert gas.viscosity(np.array([2.0]))[0] == pytest.approx(0.3, rel=1e-15)
+    # theta_S = 0: mu = mu_ref sqrt(theta/theta_ref)
+    g0 = bgk.Gas(mu_ref=0.3, theta_ref=2.0, theta_S=0.0)
+    assert g0.viscosity(np.array([8.0]))[0] == pytest.approx(0.6, rel=1e-15)
+    # tau = mu / (Pr P)
+    assert bgk.collision_time(np.array([2.0]), np.array([4.0]), gas)[0] == pytest.approx(
+        0.3 / (0.72 * 4.0), rel=1e-15)
+    # constant-viscosity switch
+    assert bgk.Gas(mu_ref=0.2, theta_S=-1).viscosity(np.array([5.0]))[0] == 0.2
+
+
+@pytest.mark.parametrize("delta", [0.0, 2.0])
+def test_sampled_maxwellian_is_a_fixed_point(delta):
+    """Pr=1: the discrete moments of a sampled Maxwellian g(q) are matched by
+    g(q) itself, so Newton must return q' = q and the source must vanish."""
+    vg = VelocityGrid((14, 14, 14), (-6, -6, -6), (6, 6, 6))
+    gas = bgk.Gas(delta=delta, Pr=1.0, mu_ref=0.05)
+    _, rho, U, theta = _random_points(16, 21)
+    F = bgk.maxwellian(vg, rho, U, theta)
+    G = 0.5 * delta * theta[None, :] * F if delta > 0 else None
+    S_F, S_G, info = bgk.bgk_source(F, G, gas, vg)
+    assert np.all(info["converged"])
+    assert np.allclose(info["qp"][:, 0], rho, rtol=1e-12)
+    assert np.allclose(info["qp"][:, 1:4], U, atol=1e-12)
+    assert np.allclose(info["qp"][:, 4], theta, rtol=1e-12)
+    tau = info["tau"]
+    assert np.max(np.abs(S_F) * tau) <= 1e-12 * np.max(F)
+    if G is not None:
+        assert np.max(np.abs(S_G) * tau) <= 1e-12 * np.max(G)
+
+
+def test_newton_matches_independent_dual_route():
+    """Pr=1, delta=0: the primitive-variable Newton and the convex-dual Newton
+    in the exponential parametrisation find the same discrete Maxwellian."""
+    vg = VelocityGrid((12, 12, 12), (-6, -6, -6), (6, 6, 6))
+    gas = bgk.Gas(delta=0.0, Pr=1.0)
+    F, _ = _bimodal(vg, 5)
+    m = bgk.raw_moments(F, None, vg)
+    qp, it, conv, res = bgk.solve_qprime(m, gas, vg)
+    assert np.all(conv)
+    g, _ = bgk.equilibrium(qp, m, gas, vg)
+    Q = _fsum_moments(vg, F)
+    for p in range(F.shape[1]):
+        gd, alpha, _ = dual.discrete_maxwellian_dual(Q[p], vg)
+        assert np.max(np.abs(g[:, p] - gd)) <= 1e-12 * np.max(gd)
+
+
+@pytest.mark.parametrize("delta,Pr", [(0.0, 2 / 3), (2.0, 0.72), (0.0, 1.0)])
+def test_es_equilibrium_conserves_and_has_prescribed_tensor(delta, Pr):
+    """The solved g' reproduces Q exactly (brute-force fsum check of the discrete
+    compatibility condition) and is the Gaussian whose covariance is
+    T'(theta') = theta'/Pr I + (1 - 1/Pr) Pi/rho with Pi, rho those of f."""
+    vg = VelocityGrid((26, 26, 26), (-8.5, -8.5, -8.5), (8.5, 8.5, 8.5))
+    gas = bgk.Gas(delta=delta, Pr=Pr)
+    F, theta = _bimodal(vg, 9, P=6)
+    G = 0.5 * delta * theta[None, :] * F * 1.1 if delta > 0 else None
+    m = bgk.raw_moments(F, G, vg)
+    qp, it, conv, res = bgk.solve_qprime(m, gas, vg)
+    assert np.all(conv) and np.all(res <= 1e-13)
+    g, Gg = bgk.equilibrium(qp, m, gas, vg)
+    Qf = _fsum_moments(vg, F, G)
+    Qg = _fsum_moments(vg, g, Gg)
+    rho, E = Qf[:, 0], Qf[:, 4]
+    th = (2 / (3 + delta)) * (E - 0.5 * np.sum(Qf[:, 1:4] ** 2, axis=1) / rho) / rho
+    assert np.all(np.abs(Qg[:, 0] - rho) <= 1e-13 * rho)
+    assert np.all(np.abs(Qg[:, 1:4] - Qf[:, 1:4]).max(axis=1) <= 1e-13 * rho * np.sqrt(th))
+    assert np.all(np.abs(Qg[:, 4] - E) <= 1e-13 * E)
+    for p in range(F.shape[1]):
+        U = Qf[p, 1:4] / rho[p]
+        c = vg.u - U
+        Pi = np.einsum("k,ki,kj->ij", vg.w * F[:, p], c, c)
+        Tp = qp[p, 4] / Pr * np.eye(3) + (1 - 1 / Pr) * Pi / rho[p]
+        Up = qp[p, 1:4]
+        cg = vg.u - Up
+        cov = np.einsum("k,ki,kj->ij", vg.w * g[:, p], cg, cg) / np.sum(vg.w * g[:, p])
+        assert np.allclose(cov, Tp, atol=1e-9)
+        assert np.allclose(np.sum(vg.w * vg.u.T * g[:, p], axis=1) / np.sum(vg.w * g[:, p]), Up,
+                           atol=1e-10)
+        if delta > 0:
+            assert np.allclose(Gg[:, p], 0.5 * delta * qp[p, 4] * g[:, p], rtol=1e-15)
+
+
+def test_analytic_jacobian_matches_finite_differences():
+    vg = VelocityGrid((10, 10, 10), (-6, -6, -6), (6, 6, 6))
+    gas = bgk.Gas(delta=2.0, Pr=0.72)
+    F, theta = _bimodal(vg, 4, P=4)
+    G = theta[None, :] * F
+    m = bgk.raw_moments(F, G, vg)
+    rho, U, E, th, P, Pi = bgk.macroscopic(m, gas)
+    Q = np.concatenate([rho[:, None], m[:, 1:4], E[:, None]], axis=1)
+    B = (1 - 1 / gas.Pr) * Pi / rho[:, None, None]
+    x = np.concatenate([rho[:, None] * 1.03, U + 0.05, th[:, None] * 0.97], axis=1)
+    R, J = bgk.compatibility_residual(x, Q, B, gas, vg)
+    for j in range(5):
+        hstep = 1e-6 * max(1.0, abs(x[0, j]))
+        xp, xm = x.copy(), x.copy()
+        xp[:, j] += hstep
+        xm[:, j] -= hstep
+        fd = (bgk.compatibility_residual(xp, Q, B, gas, vg)[0]
+              - bgk.compatibility_residual(xm, Q, B, gas, vg)[0]) / (2 * hstep)
+        assert np.allclose(J[:, :, j], fd, rtol=1e-6, atol=1e-8 * np.max(np.abs(J)))
+
+
+def _homogeneous_problem(delta, Pr, vel_n=12):
+    mesh = BoxMesh((1, 1, 1), (0, 0, 0), (1, 1, 1), (True, True, True))
+    vg = VelocityGrid((vel_n,) * 3, (-6, -6, -6), (6, 6, 6))
+    gas = bgk.Gas(delta=delta, Pr=Pr, mu_ref=0.05, theta_S=110.4 / 203)
+    return stage.Problem(mesh, 1, vg, gas)
+
+
+def test_homogeneous_relaxation_follows_rk3_stability_polynomial():
+    """Uniform-in-space data, Pr=1: Q, g' and tau are invariants, so each SSP-RK3
+    step maps f - g to P(-dt/tau)(f - g), P(z) = 1 + z + z^2/2 + z^3/6 exactly;
+    g is taken from the independent dual route.  The discrete entropy decreases."""
+    pb = _homogeneous_problem(0.0, 1.0)
+    F, _ = _bimodal(pb.vg, 13, P=1)
+    f0 = np.repeat(F[:, :1], pb.Ns, axis=1)[None, :, None, :]          # [1, Nu, 1, Ns]
+    Q = _fsum_moments(pb.vg, F[:, :1])[0]
+    g, _, _ = dual.discrete_maxwellian_dual(Q, pb.vg)
+    dt = 0.02
+    f = f0.copy()
+    H = pb.entropy(f)
+    tau = None
+    for n in range(1, 6):
+        f, infos = pb.step(f, dt)
+        tau = infos[0]["tau"][0]
+        z = -dt / tau
+        P = 1 + z + z * z / 2 + z ** 3 / 6
+        law = g[None, :, None, None] + (f0 - g[None, :, None, None]) * P ** n
+        assert np.max(np.abs(f - law)) <= 1e-12 * np.max(f0)
+        Hn = pb.entropy(f)
+        assert Hn < H
+        H = Hn
+    # continuous limit g + (f0 - g) exp(-t/tau) within the scheme's O(dt^3) error
+    t = 5 * dt
+    cont = g[None, :, None, None] + (f0 - g[None, :, None, None]) * np.exp(-t / tau)
+    assert np.max(np.abs(f - cont)) <= 5 * (dt / tau) ** 4 * t / dt * np.max(np.abs(f0 - g[None, :, None, None]))
+
+
+def test_homogeneous_relaxation_polyatomic_g_factor():
+    """delta=2, Pr=1: G relaxes to (delta theta'/2) g' at the same discrete rate."""
+    pb = _homogeneous_problem(2.0, 1.0, vel_n=10)
+    F, theta = _bimodal(pb.vg, 17, P=1)
+    G = 1.3 * theta[None, :1] * F[:, :1]
+    f0 = np.stack([np.repeat(F[:, :1], pb.Ns, axis=1), np.repeat(G, pb.Ns, axis=1)])[:, :, None, :]
+    f1, infos = pb.step(f0, 0.01)
+    qp = infos[0]["qp"][0]
+    m = infos[0]["m"][:1]
+    g, Gg = bgk.equilibrium(infos[0]["qp"][:1], m, pb.gas, pb.vg)
+    z = -0.01 / infos[0]["tau"][0]
+    P = 1 + z + z * z / 2 + z ** 3 / 6
+    assert np.allclose(Gg[:, 0], qp[4] * g[:, 0], rtol=1e-15)
+    lawG = Gg[:, 0][:, None] + (f0[1, :, 0] - Gg[:, 0][:, None]) * P
+    assert np.max(np.abs(f1[1, :, 0] - lawG)) <= 1e-12 * np.max(G)
+
+
+@pytest.mark.parametrize("delta,Pr,p", [(0.0, 2 / 3, 1), (2.0, 0.72, 2)])
+def test_full_step_conserves_totals(delta, Pr, p):
+    """Periodic mesh, random non-equilibrium data: one SSP-RK3 step of advection
+    plus source keeps total mass, momentum and energy to round-off."""
+    wl = W.Workload("t", (2, 2, 1), (0, 0, 0), (1, 1, 0.5), (True, True, True), p, (8, 8, 8),
+                    (-6, -6, -6), (6, 6, 6), delta, Pr, 0.05, 1.0, 110.4 / 203, 0.1, 1,
+                    init=lambda x: (1 + 0.1 * np.sin(2 * np.pi * x[..., 0]), np.zeros(x.shape),
+                                    np.ones(x.shape[:-1])))
+    pb = stage.problem_from_workload(wl)
+    f = W.random_anisotropic_state(wl, seed=1)
+    t0 = pb.totals(f)
+    f1, infos = pb.step(f, wl.dt())
+    t1 = pb.totals(f1)
+    scale = np.array([t0[0], t0[0], t0[0], t0[0], t0[4]])
+    assert np.all(np.abs(t1 - t0) <= 1e-13 * scale)
+    assert all(np.all(i["converged"]) for i in infos)
