@@ -1,0 +1,308 @@
+#!/usr/bin/env python
+"""Throughput of the Boltzmann--ES-BGK FR stage: DOF-updates/s per RK stage.
+
+Workload: the Taylor--Green periodic box (16^3 hex, p=3, 24^3 velocities on
+[-5,5]^3, ES-BGK Pr=2/3, Kn=0.01, M=0.1), N_e N_s N_u = 3.62e9 DOF, f
+initialised on the device to the Maxwellian of the Taylor--Green field.  A
+step is one SSP-RK3 step = 3 stages; value = DOF x 3 K / (timed seconds),
+summed over ranks (independent replicas, weak scaling).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--forms fp64,mixed] [--no-cpu-baseline]
+
+--impl reference times the FP64 CPU oracle (the method written out plainly,
+test infrastructure) on the host cores on a bounded sample of the same
+workload (one element, all 13,824 velocities per stage).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2312_06567_gb300 import workloads as W  # noqa: E402
+
+METRIC = "DOF-updates/s per RK stage (Ne*Ns*Nu)"
+UNIT = "DOF-updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--forms", default="fp64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+def oracle_stage_sample(wl, mesh_n=(1, 1, 1)):
+    """One oracle stage on a reduced-N_e copy of the workload (same p, N_u and
+    physics; per-DOF work does not depend on N_e).  Returns (DOF, wall s, cpu s)."""
+    from oracle import stage as ostage
+    sw = W.reduced(wl, mesh_n=mesh_n)
+    pb = ostage.problem_from_workload(sw)
+    f = W.maxwellian_state(sw)
+    t0, c0 = time.perf_counter(), time.process_time()
+    pb.stage(f, f, 0.0, 1.0, sw.dt())
+    return sw.dof, time.perf_counter() - t0, time.process_time() - c0
+
+
+def cpu_baseline(wl, target_s=12.0):
+    dof, wall, cpu = oracle_stage_sample(wl)
+    n = max(1, int(target_s / max(wall, 1e-3)))
+    tot_dof, tot_wall, tot_cpu = dof, wall, cpu
+    for _ in range(n - 1):
+        d, w_, c = oracle_stage_sample(wl)
+        tot_dof += d
+        tot_wall += w_
+        tot_cpu += c
+    return {"value": tot_dof / tot_wall, "unit": UNIT, "cores": round(tot_cpu / tot_wall, 2),
+            "kind": "oracle",
+            "sample": "%d oracle stage(s) of the workload reduced to 1 element (64 nodes x 13824 "
+                      "velocities = %d DOF each), %.1f s wall" % (n, dof, tot_wall)}
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms in the background."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.out.flush()
+        rows = []
+        for line in open(self.out.name):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.out.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# Algorithmic work per DOF ("Roofline accounting").
+def stage_flops_per_dof(p, C):
+    """FP64 flops of the fused stage per DOF: FR (sum-factorised derivative,
+    inflow traces, lift, metric scaling), source + RK, moment epilogue."""
+    q = p + 1
+    fr = 6 * q + 5 + 12 + 9.0 / q + 6
+    return C * fr + 26 + 4 * (C - 1) + 22 + 2 * (C - 1)
+
+
+def qprime_flops_per_dof_iter():
+    """Residual + analytic Jacobian sums of one Newton iteration per velocity."""
+    return 60.0
+
+
+def run_ours(args, rank, world, dev):
+    import torch
+    from paper_2312_06567_gb300 import bgk
+
+    wl = W.taylor_green_box()
+    dt = wl.dt()
+    stream = torch.cuda.current_stream()
+    results = {}
+    peaks = {}
+    if rank == 0:
+        for k in ("fp64_fma", "fp64_exp", "fp32_fma", "fp32_exp2"):
+            peaks[k] = bgk.probe_peak(k)
+    forms = [f for f in args.forms.split(",") if f]
+    for form in forms:
+        prec = bgk.BGK_FP64 if form == "fp64" else bgk.BGK_MIXED
+        s = bgk.Solver(wl, prec, stream=stream)
+        x = s.node_coords()
+        rho, U, theta = wl.init(x)
+        q = np.concatenate([rho.reshape(-1, 1), U.reshape(-1, 3), theta.reshape(-1, 1)], axis=1)
+        s.set_maxwellian(q)
+        for _ in range(args.warmup):
+            s.step(dt, 1)
+        torch.cuda.synchronize()
+        s.stats()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(dev.index if dev.index is not None else 0)
+        clocks.start()
+        s.profile(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = s.step(dt, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        ck = clocks.stop()
+        ms = e0.elapsed_time(e1)
+        prof = s.profile_read()
+        mean_it, max_it, res = s.stats()
+        s.profile(False)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        # e2e: host pinned state in, one step, state out, through the C-ABI
+        e2e = None
+        if args.e2e_steps > 0:
+            host = torch.empty(s.shape, dtype=torch.float64 if prec == bgk.BGK_FP64 else torch.float32,
+                               pin_memory=True)
+            s.get_state(host)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.e2e_steps):
+                s.set_state(host)
+                s.step(dt, 1)
+                s.get_state(host)
+            torch.cuda.synchronize()
+            e2e_s = time.perf_counter() - t0
+            nbytes = host.numel() * host.element_size()
+            e2e = {"value": world * wl.dof * 3 * args.e2e_steps / e2e_s, "unit": UNIT,
+                   "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+            del host
+        results[form] = dict(ms=ms, status=bgk.STATUS_NAMES[st], prof=prof, clocks=ck,
+                             newton=dict(mean_iters=mean_it, max_iters=max_it, max_residual=res),
+                             e2e=e2e)
+        s.destroy()
+        torch.cuda.empty_cache()
+    return wl, results, peaks
+
+
+def roofline_fp64(wl, r, peaks, steps):
+    """Dominant kernel of the FP64 form against the measured FP64 pipe."""
+    p64 = peaks["fp64_fma"]
+    exp_cost = p64 / peaks["fp64_exp"]                     # flops-equivalent of one exp
+    prof = r["prof"]
+    k_stage_ms, n_stage = prof["stage"]
+    k_q_ms, n_q = prof["qprime"]
+    dof = wl.dof
+    stage_fl = dof * (stage_flops_per_dof(wl.p, wl.n_comp) + exp_cost)
+    q_fl = dof * r["newton"]["mean_iters"] * (qprime_flops_per_dof_iter() + exp_cost)
+    cand = {"stage": (stage_fl, k_stage_ms / max(n_stage, 1)),
+            "qprime": (q_fl, k_q_ms / max(n_q, 1))}
+    name = max(cand, key=lambda k: cand[k][1])
+    fl, ms = cand[name]
+    achieved = fl / (ms * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": p64 / 1e12,
+            "unit": "TFLOP/s", "frac": achieved / (p64 / 1e12), "traffic": None,
+            "peak_source": "measured FP64 FMA probe (bgk_probe_peak), exp counted at "
+                           "%.1f flop-equivalents" % exp_cost}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    wl = W.taylor_green_box()
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        times, dofs, cpus = [], [], []
+        for i in range(args.warmup + args.steps):
+            d, w_, c = oracle_stage_sample(wl)
+            if i >= args.warmup:
+                times.append(w_)
+                dofs.append(d)
+                cpus.append(c)
+        v = sum(dofs) / sum(times)
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": wl.name, "sample": "1 element x 64 nodes x 13824 velocities "
+                           "per step (one oracle stage)"},
+                "cpu_baseline": {"kind": "oracle", "cores": round(sum(cpus) / sum(times), 2),
+                                 "sample": "one oracle stage on 1 element per step", "value": v,
+                                 "unit": UNIT},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl, results, peaks = run_ours(args, rank, world, dev)
+    if rank != 0:
+        return
+    main_form = "fp64" if "fp64" in results else list(results)[0]
+    r = results[main_form]
+    ms_per_step = r["ms"] / args.steps
+    value = world * wl.dof * 3 * args.steps / (r["ms"] * 1e-3)
+    launches = sum(v[1] for v in r["prof"].values())
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if main_form == "fp64" else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "dof": wl.dof, "elements": wl.n_elem, "order": wl.p,
+                   "velocities": wl.n_vel, "form": main_form, "parallelism": "replicas",
+                   "l2": "inputs larger than L2 (state %.1f GB per copy)" %
+                         (wl.dof * (8 if main_form == "fp64" else 4) / 1e9)},
+        "clocks": r["clocks"],
+        "e2e": r["e2e"],
+        "gpu_launches": launches,
+        "kernels_ms": {k: v[0] for k, v in r["prof"].items()},
+        "newton": r["newton"],
+        "status": r["status"],
+        "peaks_measured": peaks,
+    }
+    if main_form == "fp64":
+        line["roofline"] = roofline_fp64(wl, r, peaks, args.steps)
+    for form, rr in results.items():
+        if form != main_form:
+            line[form] = {"value": world * wl.dof * 3 * args.steps / (rr["ms"] * 1e-3),
+                          "ms_per_step": rr["ms"] / args.steps,
+                          "kernels_ms": {k: v[0] for k, v in rr["prof"].items()},
+                          "newton": rr["newton"], "e2e": rr["e2e"]}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl)
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,185 @@
+/*
+ * bgk.h -- C-ABI of libbgk: one explicit Runge--Kutta stage of the
+ * six-dimensional Boltzmann--(ES-)BGK residual on hexahedral elements,
+ * GB300 (sm_103a) native.
+ *
+ * Method: Dzanic & Martinelli, "Direct molecular gas dynamics simulations of
+ * re-entry vehicles via the Boltzmann equation" (arXiv 2312.06567),
+ * section "Methodology": flux-reconstruction (FR) advection u.grad f per
+ * discrete velocity with the upwind interface flux and the DG-recovering
+ * correction function, fused with the conservative BGK source (moments
+ * Q = (rho, rho U, E), the modified state Q' of the discrete compatibility
+ * condition, the ES-BGK equilibrium with the reduced F/G distributions).
+ *
+ * Conventions (every call):
+ *  - Layouts.  Element e = e1 + n1 (e2 + n2 e3) of a uniform box mesh.
+ *    Solution node s = i1 + (p+1)(i2 + (p+1) i3) at tensor Gauss--Legendre
+ *    points.  Velocity node k = k1 + n1 (k2 + n2 k3) of a uniform grid.
+ *    Point index P = e * Ns + s.  State f[c][k][e][s] (c = 0: F, c = 1: G,
+ *    present only when delta > 0), contiguous, s fastest.
+ *  - Precision.  BGK_FP64: state arrays are double.  BGK_MIXED: state arrays
+ *    are float (the moment reduction and the Q' solve stay FP64-accurate).
+ *    Moment / macroscopic arrays are always double.
+ *  - Ownership.  The context owns every buffer it allocates.  Caller
+ *    pointers are borrowed for the duration of the call, never retained.
+ *  - on_device = 1: the pointer is device memory of the context's device
+ *    (e.g. a torch tensor's data_ptr()); 0: host memory.
+ *  - Streams.  All work is ordered on the stream given to bgk_create.  Calls
+ *    that return host data synchronise that stream.
+ *  - Errors are returned as bgk_status codes, never by trap or abort; the
+ *    text of the last error is available from bgk_last_error.  A device-side
+ *    failure (Newton non-convergence, non-finite state) is recorded in a
+ *    device status word and reported by the next call that synchronises.
+ */
+#ifndef BGK_H
+#define BGK_H
+
+#if defined(__GNUC__)
+#define BGK_API __attribute__((visibility("default")))
+#else
+#define BGK_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bgk_ctx bgk_ctx;
+
+typedef enum {
+    BGK_OK = 0,
+    BGK_EINVAL = 1,    /* invalid argument or descriptor                       */
+    BGK_ENOMEM = 2,    /* device allocation failed                             */
+    BGK_ECUDA = 3,     /* a CUDA runtime call failed                           */
+    BGK_ENOCONV = 4,   /* the Q' Newton iteration did not converge somewhere   */
+    BGK_ETIMEOUT = 5,  /* reserved: a bounded device wait gave up              */
+    BGK_ENOTSUP = 6    /* valid but unsupported configuration                  */
+} bgk_status;
+
+typedef enum { BGK_FP64 = 0, BGK_MIXED = 1 } bgk_precision;
+
+/* Uniform hexahedral box mesh and FR order (section "Numerical method":
+ * N_e elements, N_s = (p+1)^3 solution nodes each).  Axes with periodic[d]=0
+ * are closed at both ends by weak Dirichlet faces (section "Implementation &
+ * problem setup": farfield states enforced through the Riemann flux) whose
+ * exterior state is the Maxwellian of bc_state[2d + (side>0)] =
+ * (rho, U1, U2, U3, theta); G's exterior state is delta theta / 2 times it.
+ * Requirements: n[d] >= 1, hi[d] > lo[d], 1 <= order <= 4. */
+typedef struct {
+    int n[3];
+    double lo[3], hi[3];
+    int periodic[3];
+    int order;
+    double bc_state[6][5];
+} bgk_mesh_desc;
+
+/* Uniform Cartesian velocity grid with trapezoid weights (section
+ * "Numerical method": discrete integration operator with strictly positive
+ * entries, the trapezoidal rule on a uniform grid).  n[d] >= 2, hi > lo. */
+typedef struct {
+    int n[3];
+    double lo[3], hi[3];
+} bgk_vgrid_desc;
+
+/* Gas (section "Governing equations"): delta internal degrees of freedom
+ * (>= 0; delta > 0 carries the reduced pair F, G), Prandtl number Pr of the
+ * ES-BGK temperature tensor (Pr >= 2/3 keeps it positive definite), and the
+ * Sutherland law mu = mu_ref (theta/theta_ref)^(3/2) (theta_ref + theta_S) /
+ * (theta + theta_S); theta_S < 0 selects mu = mu_ref.  tau = mu / (Pr P). */
+typedef struct {
+    double delta, Pr, mu_ref, theta_ref, theta_S;
+} bgk_gas_desc;
+
+/* Create a solver context on the current CUDA device.  stream: a
+ * cudaStream_t (NULL = legacy default stream).  Allocates three state
+ * copies (f^n and two stage buffers) plus per-point work arrays.
+ * Errors: BGK_EINVAL (descriptor), BGK_ENOMEM, BGK_ECUDA. */
+BGK_API bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_desc *vgrid,
+                      const bgk_gas_desc *gas, int precision, void *stream);
+BGK_API bgk_status bgk_destroy(bgk_ctx *ctx);
+
+/* N_e, N_s, N_u and the number of components (1 or 2). */
+BGK_API bgk_status bgk_sizes(const bgk_ctx *ctx, int *n_elem, int *n_sol, int *n_vel, int *n_comp);
+
+/* Solution-node coordinates x[P][3], P = N_e N_s, in the context's own
+ * Gauss--Legendre node placement. */
+BGK_API bgk_status bgk_node_coords(const bgk_ctx *ctx, double *x, int on_device);
+
+/* Copy the state in / out (f[c][k][e][s], element type by precision). */
+BGK_API bgk_status bgk_set_state(bgk_ctx *ctx, const void *f, int on_device);
+BGK_API bgk_status bgk_get_state(bgk_ctx *ctx, void *f, int on_device);
+
+/* Set f to the isotropic Maxwellian of q[P][5] = (rho, U1, U2, U3, theta) at
+ * every node (G = delta theta / 2 F).  Section "Governing equations", g_u
+ * with T = theta I. */
+BGK_API bgk_status bgk_set_maxwellian(bgk_ctx *ctx, const double *q, int on_device);
+
+/* Newton controls of the Q' solve: stop when the scaled residual
+ * max(|R_rho|/rho, |R_rhoU|_inf/(rho sqrt(theta)), |R_E|/E) <= tol, at most
+ * max_iter updates (defaults 1e-13, 50). */
+BGK_API bgk_status bgk_set_newton(bgk_ctx *ctx, double tol, int max_iter);
+
+/* One residual R(f) = -div(u f) + (g(Q') - f)/tau of f_in into r_out (both
+ * with the state's layout and element type).  Test and debug entry; it
+ * leaves the state unchanged. */
+BGK_API bgk_status bgk_rhs(bgk_ctx *ctx, const void *f_in, void *r_out, int on_device);
+
+/* n_steps steps of SSP-RK3 (Shu--Osher) with step dt on the stored state.
+ * Each stage is two kernels: the Q' solve from the moments of the stage
+ * input, and the fused FR + source + RK update that also reduces the
+ * moments of its output.  Returns BGK_ENOCONV if a Newton solve did not
+ * converge (the step is still completed with the last iterate). */
+BGK_API bgk_status bgk_step(bgk_ctx *ctx, double dt, int n_steps);
+
+/* One stage f_out = a f^n + b f_s + c R(f_s) with f^n the stored state and
+ * f_s = f_in (device arrays, state layout); f_out must not alias f_in. */
+BGK_API bgk_status bgk_stage(bgk_ctx *ctx, const void *f_n, const void *f_in, void *f_out,
+                     double a, double b, double c);
+
+/* Raw velocity moments of the stored state, m[P][11]: sum w F, sum w u_d F
+ * (3), sum w u_d^2 F (3), sum w u1u2 F, sum w u1u3 F, sum w u2u3 F, sum w G. */
+BGK_API bgk_status bgk_moments(bgk_ctx *ctx, double *m, int on_device);
+
+/* The Q' solve alone (section "Numerical method", discrete compatibility):
+ * from raw moments m[n_points][11] (layout of bgk_moments) to
+ * qp[n_points][5] = (rho', U'_1..3, theta') and Newton update counts
+ * iters[n_points] (may be NULL).  Returns BGK_ENOCONV if any point failed. */
+BGK_API bgk_status bgk_qprime(bgk_ctx *ctx, const double *m, int n_points, double *qp, int *iters,
+                      int on_device);
+
+/* Domain totals (rho, rho U, E) = sum_e sum_s W_s |J_e| sum_k w_k psi_k f of
+ * the stored state (W_s tensor Gauss weights, |J_e| the affine Jacobian). */
+BGK_API bgk_status bgk_totals(bgk_ctx *ctx, double totals[5]);
+
+/* Newton statistics accumulated since the last call (then reset):
+ * mean and max update count per point solve, and the worst final scaled
+ * residual. */
+BGK_API bgk_status bgk_stats(bgk_ctx *ctx, double *mean_iters, int *max_iters, double *max_residual);
+
+/* Per-kernel timing on the context's stream.  enable = 1 starts recording a
+ * CUDA event pair around every kernel the context launches (and clears the
+ * accumulators); 0 stops.  bgk_profile_read synchronises and returns, per
+ * kernel kind (BGK_K_*), the summed device milliseconds and launch counts
+ * since the last enable; either array may be NULL.  Launch counts are kept
+ * even when timing is off. */
+#define BGK_K_MOMENTS 0    /* raw moment partials of a state            */
+#define BGK_K_QPRIME 1     /* moment reduction + Q' Newton solve        */
+#define BGK_K_STAGE 2      /* fused FR + source + RK + moment epilogue  */
+#define BGK_K_OTHER 3      /* initialisation and reductions             */
+#define BGK_NKINDS 4
+BGK_API bgk_status bgk_profile(bgk_ctx *ctx, int enable);
+BGK_API bgk_status bgk_profile_read(bgk_ctx *ctx, double ms[BGK_NKINDS], long long launches[BGK_NKINDS]);
+
+/* Roofline probes of the current device (no context): kind 0 = FP64 FMA
+ * throughput, 1 = FP32 FMA throughput (both in flop/s, an FMA = 2 flops),
+ * 2 = FP64 exp() throughput (calls/s), 3 = FP32 exp2f throughput (calls/s).
+ * Each runs a register-resident kernel over every SM for ~50 ms. */
+BGK_API bgk_status bgk_probe_peak(int kind, double *value);
+
+/* Text of the last error on this context (never NULL). */
+BGK_API const char *bgk_last_error(const bgk_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BGK_H */

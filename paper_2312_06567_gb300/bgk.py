@@ -1,0 +1,280 @@
+"""Thin ctypes binding of libbgk (include/bgk.h): argument marshalling only.
+
+Every step of the stage runs in the library's CUDA kernels; this module only
+packs descriptors, passes pointers (numpy arrays as host memory, torch CUDA
+tensors as device memory) and turns status codes into exceptions.  There is no
+CPU fallback: if libbgk.so is missing the first call raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbgk.so")
+
+BGK_OK, BGK_EINVAL, BGK_ENOMEM, BGK_ECUDA, BGK_ENOCONV, BGK_ETIMEOUT, BGK_ENOTSUP = range(7)
+BGK_FP64, BGK_MIXED = 0, 1
+STATUS_NAMES = {0: "BGK_OK", 1: "BGK_EINVAL", 2: "BGK_ENOMEM", 3: "BGK_ECUDA",
+                4: "BGK_ENOCONV", 5: "BGK_ETIMEOUT", 6: "BGK_ENOTSUP"}
+
+c_int, c_double, c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("n", c_int * 3), ("lo", c_double * 3), ("hi", c_double * 3),
+                ("periodic", c_int * 3), ("order", c_int), ("bc_state", (c_double * 5) * 6)]
+
+
+class VGridDesc(ctypes.Structure):
+    _fields_ = [("n", c_int * 3), ("lo", c_double * 3), ("hi", c_double * 3)]
+
+
+class GasDesc(ctypes.Structure):
+    _fields_ = [("delta", c_double), ("Pr", c_double), ("mu_ref", c_double),
+                ("theta_ref", c_double), ("theta_S", c_double)]
+
+
+# name -> (restype, argtypes) for every entry point of include/bgk.h
+SIGNATURES = {
+    "bgk_create": (c_int, [ctypes.POINTER(c_void_p), ctypes.POINTER(MeshDesc),
+                           ctypes.POINTER(VGridDesc), ctypes.POINTER(GasDesc), c_int, c_void_p]),
+    "bgk_destroy": (c_int, [c_void_p]),
+    "bgk_sizes": (c_int, [c_void_p] + [ctypes.POINTER(c_int)] * 4),
+    "bgk_node_coords": (c_int, [c_void_p, c_void_p, c_int]),
+    "bgk_set_state": (c_int, [c_void_p, c_void_p, c_int]),
+    "bgk_get_state": (c_int, [c_void_p, c_void_p, c_int]),
+    "bgk_set_maxwellian": (c_int, [c_void_p, c_void_p, c_int]),
+    "bgk_set_newton": (c_int, [c_void_p, c_double, c_int]),
+    "bgk_rhs": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
+    "bgk_step": (c_int, [c_void_p, c_double, c_int]),
+    "bgk_stage": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_double, c_double]),
+    "bgk_moments": (c_int, [c_void_p, c_void_p, c_int]),
+    "bgk_qprime": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_int]),
+    "bgk_totals": (c_int, [c_void_p, ctypes.POINTER(c_double)]),
+    "bgk_stats": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int),
+                          ctypes.POINTER(c_double)]),
+    "bgk_profile": (c_int, [c_void_p, c_int]),
+    "bgk_profile_read": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(ctypes.c_longlong)]),
+    "bgk_probe_peak": (c_int, [c_int, ctypes.POINTER(c_double)]),
+    "bgk_last_error": (ctypes.c_char_p, [c_void_p]),
+}
+
+KERNEL_KINDS = ("moments", "qprime", "stage", "other")
+PROBE_KINDS = {"fp64_fma": 0, "fp32_fma": 1, "fp64_exp": 2, "fp32_exp2": 3}
+
+
+def probe_peak(kind):
+    """Measured device throughput: flop/s for *_fma, calls/s for *_exp*."""
+    lib = load()
+    v = c_double()
+    st = lib.bgk_probe_peak(PROBE_KINDS[kind], ctypes.byref(v))
+    if st != BGK_OK:
+        raise BGKError(st, "probe %s failed" % kind)
+    return v.value
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load libbgk.so (raises if it is not built) and declare every signature."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError("libbgk.so is not built (run __graft_entry__.build()); "
+                               "there is no CPU fallback")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype, fn.argtypes = res, args
+        _lib = lib
+    return _lib
+
+
+class BGKError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+def _ptr(x):
+    """(pointer, on_device) of a numpy array (host) or torch tensor (device if CUDA)."""
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return c_void_p(x.ctypes.data), 0
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return c_void_p(x.data_ptr()), 1 if x.is_cuda else 0
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    return c_void_p(getattr(stream, "cuda_stream", stream))
+
+
+def descriptors(wl):
+    """(MeshDesc, VGridDesc, GasDesc) of a workload definition."""
+    m = MeshDesc()
+    for d in range(3):
+        m.n[d], m.lo[d], m.hi[d] = wl.mesh_n[d], wl.mesh_lo[d], wl.mesh_hi[d]
+        m.periodic[d] = 1 if wl.periodic[d] else 0
+    m.order = wl.p
+    for (d, side), (rho, U, theta) in wl.dirichlet.items():
+        row = m.bc_state[2 * d + (1 if side > 0 else 0)]
+        row[0], row[1], row[2], row[3], row[4] = rho, U[0], U[1], U[2], theta
+    v = VGridDesc()
+    for d in range(3):
+        v.n[d], v.lo[d], v.hi[d] = wl.vel_n[d], wl.vel_lo[d], wl.vel_hi[d]
+    g = GasDesc(wl.delta, wl.Pr, wl.mu_ref, wl.theta_ref, wl.theta_S)
+    return m, v, g
+
+
+class Solver:
+    """One libbgk context.  Methods carry the C entry points' names."""
+
+    def __init__(self, wl, precision=BGK_FP64, stream=None):
+        self.lib = load()
+        self.wl = wl
+        self.precision = precision
+        self._h = c_void_p()
+        m, v, g = descriptors(wl)
+        st = self.lib.bgk_create(ctypes.byref(self._h), ctypes.byref(m), ctypes.byref(v),
+                                 ctypes.byref(g), precision, _stream_handle(stream))
+        if st != BGK_OK:
+            msg = self.lib.bgk_last_error(self._h).decode() if self._h else ""
+            if self._h:
+                self.lib.bgk_destroy(self._h)
+                self._h = c_void_p()
+            raise BGKError(st, msg)
+        ne, ns, nu, nc = c_int(), c_int(), c_int(), c_int()
+        self._check(self.lib.bgk_sizes(self._h, ctypes.byref(ne), ctypes.byref(ns),
+                                       ctypes.byref(nu), ctypes.byref(nc)))
+        self.n_elem, self.n_sol, self.n_vel, self.n_comp = ne.value, ns.value, nu.value, nc.value
+        self.dtype = np.float64 if precision == BGK_FP64 else np.float32
+
+    @property
+    def shape(self):
+        return (self.n_comp, self.n_vel, self.n_elem, self.n_sol)
+
+    @property
+    def n_points(self):
+        return self.n_elem * self.n_sol
+
+    def _check(self, st):
+        if st != BGK_OK:
+            raise BGKError(st, self.lib.bgk_last_error(self._h).decode())
+
+    def destroy(self):
+        if self._h:
+            self.lib.bgk_destroy(self._h)
+            self._h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+    # -- entry points ------------------------------------------------------
+    def node_coords(self):
+        x = np.empty((self.n_elem, self.n_sol, 3))
+        p, dev = _ptr(x)
+        self._check(self.lib.bgk_node_coords(self._h, p, dev))
+        return x
+
+    def set_state(self, f):
+        if isinstance(f, np.ndarray):
+            f = np.ascontiguousarray(f, dtype=self.dtype)
+        if tuple(f.shape) != self.shape:
+            raise ValueError("state shape %s, expected %s" % (tuple(f.shape), self.shape))
+        p, dev = _ptr(f)
+        self._check(self.lib.bgk_set_state(self._h, p, dev))
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.empty(self.shape, dtype=self.dtype)
+        p, dev = _ptr(out)
+        self._check(self.lib.bgk_get_state(self._h, p, dev))
+        return out
+
+    def set_maxwellian(self, q):
+        if isinstance(q, np.ndarray):
+            q = np.ascontiguousarray(q, dtype=np.float64).reshape(self.n_points, 5)
+        p, dev = _ptr(q)
+        self._check(self.lib.bgk_set_maxwellian(self._h, p, dev))
+
+    def set_newton(self, tol=1e-13, max_iter=50):
+        self._check(self.lib.bgk_set_newton(self._h, tol, max_iter))
+
+    def rhs(self, f, out=None):
+        if isinstance(f, np.ndarray):
+            f = np.ascontiguousarray(f, dtype=self.dtype)
+            out = np.empty(self.shape, dtype=self.dtype) if out is None else out
+        pf, dev = _ptr(f)
+        po, dev2 = _ptr(out)
+        if dev != dev2:
+            raise ValueError("input and output must both be host or both be device")
+        self._check(self.lib.bgk_rhs(self._h, pf, po, dev))
+        return out
+
+    def step(self, dt, n_steps=1):
+        """Returns the status code (BGK_OK, or BGK_ENOCONV if a solve did not
+        converge); other failures raise."""
+        st = self.lib.bgk_step(self._h, dt, n_steps)
+        if st not in (BGK_OK, BGK_ENOCONV):
+            self._check(st)
+        return st
+
+    def stage(self, f_n, f_in, f_out, a, b, c):
+        pn = _ptr(f_n)[0] if f_n is not None else None
+        self._check(self.lib.bgk_stage(self._h, pn, _ptr(f_in)[0], _ptr(f_out)[0], a, b, c))
+
+    def moments(self, out=None):
+        out = np.empty((self.n_points, 11)) if out is None else out
+        p, dev = _ptr(out)
+        self._check(self.lib.bgk_moments(self._h, p, dev))
+        return out
+
+    def qprime(self, m):
+        m = np.ascontiguousarray(m, dtype=np.float64)
+        n = m.shape[0]
+        qp = np.empty((n, 5))
+        it = np.empty(n, dtype=np.int32)
+        st = self.lib.bgk_qprime(self._h, _ptr(m)[0], n, _ptr(qp)[0], _ptr(it)[0], 0)
+        if st not in (BGK_OK, BGK_ENOCONV):
+            self._check(st)
+        return qp, it, st
+
+    def totals(self):
+        t = (c_double * 5)()
+        self._check(self.lib.bgk_totals(self._h, t))
+        return np.array(list(t))
+
+    def stats(self):
+        mean, mx, res = c_double(), c_int(), c_double()
+        self._check(self.lib.bgk_stats(self._h, ctypes.byref(mean), ctypes.byref(mx),
+                                       ctypes.byref(res)))
+        return mean.value, mx.value, res.value
+
+    def profile(self, enable=True):
+        self._check(self.lib.bgk_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{kind: (ms, launches)} since the last profile(True)."""
+        ms = (c_double * 4)()
+        n = (ctypes.c_longlong * 4)()
+        self._check(self.lib.bgk_profile_read(self._h, ms, n))
+        return {k: (ms[i], n[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+    def last_error(self):
+        return self.lib.bgk_last_error(self._h).decode()

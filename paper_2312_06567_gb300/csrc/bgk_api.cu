@@ -1,0 +1,620 @@
+// libbgk C-ABI: context, host-side operator construction, stage sequencing.
+// See include/bgk.h for the contract of every entry point.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/bgk.h"
+#include "bgk_internal.cuh"
+
+struct bgk_ctx {
+    // problem
+    int p, q, Ns, Ne, Nu, C, P;
+    int vn[3];
+    int precision;
+    MeshInfo mesh;
+    FROps fr;
+    GasInfo gas;
+    double jac;                       // |J_e|
+    double lo[3];                     // mesh box corner
+    double bc[6][5];
+    std::vector<double> vtab_h;       // [Nu][BGK_VTAB]
+    // device
+    cudaStream_t stream;
+    int device;
+    size_t elem;                      // bytes per state element
+    void *f[3];                       // state (f^n) and two stage buffers
+    double *part;                     // [n_vblk][NMOM][P]
+    double *mom;                      // [P][NMOM]
+    double *eq;                       // [P][NEQ]
+    double *qp;                       // [P][5]
+    double *vtab;                     // [Nu][VTAB]
+    double *bcval;                    // [6][C][Nu]
+    unsigned int *status;
+    NewtonStats *stats;
+    int *iters;
+    int Kblk, n_vblk;
+    bool part_valid;
+    double tol;
+    int max_iter;
+    std::string err;
+    // profiling: event pairs around launches, accumulated per kernel kind
+    bool prof_on;
+    struct Rec { int kind; cudaEvent_t a, b; };
+    std::vector<Rec> prof_pending;
+    std::vector<cudaEvent_t> ev_pool;
+    double prof_ms[BGK_NKINDS];
+    long long launches[BGK_NKINDS];
+};
+
+namespace {
+
+bgk_status fail(bgk_ctx *ctx, bgk_status st, const char *fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return st;
+}
+
+#define CU(call)                                                                       \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? BGK_ENOMEM : BGK_ECUDA,  \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,     \
+                        __LINE__);                                                     \
+    } while (0)
+
+// ---- host-side FR operators (section "Numerical method") -------------------
+// Legendre P_n and P_n' by the three-term recurrence.
+void legendre(int n, double x, double &pn, double &dpn) {
+    double p0 = 1.0, p1 = x, d0 = 0.0, d1 = 1.0;
+    if (n == 0) { pn = 1.0; dpn = 0.0; return; }
+    for (int k = 1; k < n; ++k) {
+        const double p2 = ((2 * k + 1) * x * p1 - k * p0) / (k + 1);
+        const double d2 = d0 + (2 * k + 1) * p1;
+        p0 = p1; p1 = p2; d0 = d1; d1 = d2;
+    }
+    pn = p1; dpn = d1;
+}
+
+void build_fr(int p, FROps &fr) {
+    const int q = p + 1;
+    fr.q = q;
+    std::vector<double> x(q), lam(q);
+    for (int i = 0; i < q; ++i) {        // Newton on P_q from cosine estimates
+        double t = -std::cos(M_PI * (i + 0.75) / (q + 0.5));
+        for (int it = 0; it < 100; ++it) {
+            double pn, dpn;
+            legendre(q, t, pn, dpn);
+            const double dt = pn / dpn;
+            t -= dt;
+            if (std::fabs(dt) < 1e-16) break;
+        }
+        double pn, dpn;
+        legendre(q, t, pn, dpn);
+        x[i] = t;
+        fr.wq[i] = 2.0 / ((1.0 - t * t) * dpn * dpn);
+        fr.xi[i] = t;
+    }
+    // barycentric weights lambda_j = 1 / prod_{m != j}(x_j - x_m)
+    for (int j = 0; j < q; ++j) {
+        double pr = 1.0;
+        for (int m = 0; m < q; ++m)
+            if (m != j) pr *= (x[j] - x[m]);
+        lam[j] = 1.0 / pr;
+    }
+    // D_ij = (lambda_j / lambda_i) / (x_i - x_j), D_ii = -sum_{j != i} D_ij
+    for (int i = 0; i < q; ++i) {
+        double diag = 0.0;
+        for (int j = 0; j < q; ++j) {
+            if (j == i) continue;
+            fr.D[i][j] = (lam[j] / lam[i]) / (x[i] - x[j]);
+            diag -= fr.D[i][j];
+        }
+        fr.D[i][i] = diag;
+    }
+    // l_j(t) at t = -1, +1 by the barycentric formula of the second kind
+    for (int side = 0; side < 2; ++side) {
+        const double t = side ? 1.0 : -1.0;
+        double den = 0.0;
+        for (int j = 0; j < q; ++j) den += lam[j] / (t - x[j]);
+        for (int j = 0; j < q; ++j) {
+            const double v = (lam[j] / (t - x[j])) / den;
+            if (side) fr.lp[j] = v; else fr.lm[j] = v;
+        }
+    }
+    // DG-recovering correction: g_L = (-1)^(p+1)/2 (P_{p+1} - P_p), g_R = (P_{p+1} + P_p)/2
+    const double sL = (p % 2 == 0) ? -0.5 : 0.5;
+    for (int i = 0; i < q; ++i) {
+        double a, da, b, db;
+        legendre(p + 1, x[i], a, da);
+        legendre(p, x[i], b, db);
+        fr.dgL[i] = sL * (da - db);
+        fr.dgR[i] = 0.5 * (da + db);
+    }
+}
+
+double maxwellian_value(double u1, double u2, double u3, const double *st) {
+    const double rho = st[0], th = st[4];
+    const double c1 = u1 - st[1], c2 = u2 - st[2], c3 = u3 - st[3];
+    return rho / std::pow(2.0 * M_PI * th, 1.5) * std::exp(-(c1 * c1 + c2 * c2 + c3 * c3) / (2.0 * th));
+}
+
+cudaEvent_t pool_event(bgk_ctx *ctx) {
+    if (!ctx->ev_pool.empty()) {
+        cudaEvent_t e = ctx->ev_pool.back();
+        ctx->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Bracket one kernel launch: counts it and, when profiling, records events.
+struct LaunchScope {
+    bgk_ctx *ctx;
+    int kind;
+    cudaEvent_t b = nullptr;
+    LaunchScope(bgk_ctx *c, int k) : ctx(c), kind(k) {
+        ctx->launches[kind]++;
+        if (ctx->prof_on) {
+            cudaEvent_t a = pool_event(ctx);
+            b = pool_event(ctx);
+            cudaEventRecord(a, ctx->stream);
+            ctx->prof_pending.push_back({kind, a, b});
+        }
+    }
+    ~LaunchScope() {
+        if (b) cudaEventRecord(b, ctx->stream);
+    }
+};
+
+bgk_status check_device_status(bgk_ctx *ctx) {
+    unsigned int st = 0;
+    CU(cudaMemcpyAsync(&st, ctx->status, sizeof st, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (st) {
+        CU(cudaMemsetAsync(ctx->status, 0, sizeof(unsigned int), ctx->stream));
+        if (st & BGK_DEV_NOCONV)
+            return fail(ctx, BGK_ENOCONV, "Q' Newton iteration did not converge at some point");
+        return fail(ctx, BGK_ENOCONV, "device status 0x%x", st);
+    }
+    return BGK_OK;
+}
+
+bgk_status run_moments(bgk_ctx *ctx, const void *f) {
+    if (ctx->precision != BGK_FP64) return fail(ctx, BGK_ENOTSUP, "mixed precision not built");
+    MomentArgs64 a{(const double *)f, ctx->part, ctx->vtab, ctx->Nu, ctx->P, ctx->Kblk, ctx->C};
+    LaunchScope ls(ctx, BGK_K_MOMENTS);
+    CU(launch_moments_f64(a, ctx->n_vblk, ctx->stream));
+    return BGK_OK;
+}
+
+bgk_status run_qprime(bgk_ctx *ctx, const double *part, int n_vblk, int P, double *eq, double *qp,
+                      int *iters, const double *guess) {
+    QPrimeArgs a{};
+    a.part = part; a.n_vblk = n_vblk; a.vtab = ctx->vtab; a.guess = guess; a.eq = eq; a.qp = qp;
+    a.iters = iters; a.status = ctx->status; a.stats = ctx->stats; a.P = P; a.Nu = ctx->Nu;
+    a.tol = ctx->tol; a.max_iter = ctx->max_iter; a.gas = ctx->gas;
+    LaunchScope ls(ctx, BGK_K_QPRIME);
+    CU(launch_qprime_f64(a, ctx->stream));
+    return BGK_OK;
+}
+
+bgk_status run_stage(bgk_ctx *ctx, const void *fn, const void *fs, void *fo, double a, double b,
+                     double c, bool moments) {
+    if (ctx->precision != BGK_FP64) return fail(ctx, BGK_ENOTSUP, "mixed precision not built");
+    StageArgs<double> s{};
+    s.f_n = (const double *)fn; s.f_s = (const double *)fs; s.f_out = (double *)fo;
+    s.eq = ctx->eq; s.vtab = ctx->vtab; s.bcval = ctx->bcval; s.part = moments ? ctx->part : nullptr;
+    s.a = a; s.b = b; s.c = c; s.Nu = ctx->Nu; s.P = ctx->P; s.Kblk = ctx->Kblk;
+    s.vel_n1 = ctx->vn[0]; s.vel_n2 = ctx->vn[1]; s.fr = ctx->fr; s.mesh = ctx->mesh;
+    LaunchScope ls(ctx, BGK_K_STAGE);
+    CU(launch_stage_f64(s, ctx->C, ctx->n_vblk, ctx->stream));
+    return BGK_OK;
+}
+
+// One full stage on device arrays: moments of fs must be in ctx->part.
+bgk_status stage_from_partials(bgk_ctx *ctx, const void *fn, const void *fs, void *fo, double a,
+                               double b, double c, bool moments_out) {
+    bgk_status st = run_qprime(ctx, ctx->part, ctx->n_vblk, ctx->P, ctx->eq, ctx->qp, nullptr, nullptr);
+    if (st) return st;
+    return run_stage(ctx, fn, fs, fo, a, b, c, moments_out);
+}
+
+}  // namespace
+
+extern "C" {
+
+bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_desc *vg,
+                      const bgk_gas_desc *gas, int precision, void *stream) {
+    if (!out || !mesh || !vg || !gas) return BGK_EINVAL;
+    *out = nullptr;
+    bgk_ctx *ctx = new bgk_ctx();
+    auto bad = [&](const char *msg) {
+        ctx->err = msg;
+        *out = ctx;   // keep the context so the caller can read the message
+        return BGK_EINVAL;
+    };
+    if (mesh->order < 1 || mesh->order > 4) return bad("order must be in 1..4");
+    for (int d = 0; d < 3; ++d) {
+        if (mesh->n[d] < 1) return bad("mesh n[d] must be >= 1");
+        if (!(mesh->hi[d] > mesh->lo[d])) return bad("mesh hi must exceed lo");
+        if (vg->n[d] < 2) return bad("velocity grid needs >= 2 nodes per axis");
+        if (!(vg->hi[d] > vg->lo[d])) return bad("velocity hi must exceed lo");
+    }
+    if (!(gas->delta >= 0.0)) return bad("delta must be >= 0");
+    if (!(gas->Pr >= 2.0 / 3.0 - 1e-12)) return bad("Pr must be >= 2/3");
+    if (!(gas->mu_ref > 0.0) || !(gas->theta_ref > 0.0)) return bad("mu_ref, theta_ref must be > 0");
+    if (precision != BGK_FP64 && precision != BGK_MIXED) return bad("unknown precision");
+    for (int d = 0; d < 3; ++d)
+        if (!mesh->periodic[d])
+            for (int s = 0; s < 2; ++s) {
+                const double *b = mesh->bc_state[2 * d + s];
+                if (!(b[0] > 0.0) || !(b[4] > 0.0)) return bad("Dirichlet state needs rho, theta > 0");
+            }
+    const long long Ne = (long long)mesh->n[0] * mesh->n[1] * mesh->n[2];
+    const long long Nu = (long long)vg->n[0] * vg->n[1] * vg->n[2];
+    const long long Ns = (long long)(mesh->order + 1) * (mesh->order + 1) * (mesh->order + 1);
+    if (Ne * Ns > (1ll << 30) || Nu > (1ll << 30)) return bad("problem too large");
+
+    ctx->p = mesh->order; ctx->q = mesh->order + 1; ctx->Ns = (int)Ns; ctx->Ne = (int)Ne;
+    ctx->Nu = (int)Nu; ctx->C = gas->delta > 0.0 ? 2 : 1; ctx->P = (int)(Ne * Ns);
+    ctx->precision = precision;
+    ctx->stream = (cudaStream_t)stream;
+    ctx->tol = 1e-13;
+    ctx->max_iter = 50;
+    for (int d = 0; d < 3; ++d) {
+        ctx->vn[d] = vg->n[d];
+        ctx->mesh.n[d] = mesh->n[d];
+        ctx->mesh.periodic[d] = mesh->periodic[d] ? 1 : 0;
+        ctx->mesh.two_over_h[d] = 2.0 * mesh->n[d] / (mesh->hi[d] - mesh->lo[d]);
+    }
+    ctx->mesh.Ne = ctx->Ne; ctx->mesh.Ns = ctx->Ns;
+    ctx->jac = 1.0;
+    for (int d = 0; d < 3; ++d) {
+        ctx->jac *= 0.5 * (mesh->hi[d] - mesh->lo[d]) / mesh->n[d];
+        ctx->lo[d] = mesh->lo[d];
+    }
+    std::memcpy(ctx->bc, mesh->bc_state, sizeof ctx->bc);
+    build_fr(ctx->p, ctx->fr);
+    ctx->gas.delta = gas->delta; ctx->gas.Pr = gas->Pr; ctx->gas.mu_ref = gas->mu_ref;
+    ctx->gas.theta_ref = gas->theta_ref; ctx->gas.theta_S = gas->theta_S;
+    ctx->gas.gamma = (5.0 + gas->delta) / (3.0 + gas->delta);
+
+    // velocity table: nodes, trapezoid weights, |u|^2/2
+    std::vector<double> ax[3], wt[3];
+    for (int d = 0; d < 3; ++d) {
+        const double h = (vg->hi[d] - vg->lo[d]) / (vg->n[d] - 1);
+        for (int j = 0; j < vg->n[d]; ++j) {
+            ax[d].push_back(vg->lo[d] + j * h);
+            wt[d].push_back((j == 0 || j == vg->n[d] - 1) ? 0.5 * h : h);
+        }
+    }
+    ctx->vtab_h.assign((size_t)Nu * BGK_VTAB, 0.0);
+    for (int k = 0; k < Nu; ++k) {
+        const int k1 = k % vg->n[0], k2 = (k / vg->n[0]) % vg->n[1], k3 = k / (vg->n[0] * vg->n[1]);
+        double *v = &ctx->vtab_h[(size_t)k * BGK_VTAB];
+        v[0] = ax[0][k1]; v[1] = ax[1][k2]; v[2] = ax[2][k3];
+        v[3] = wt[0][k1] * wt[1][k2] * wt[2][k3];
+        v[4] = 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    }
+    // Dirichlet exterior states per face and velocity
+    std::vector<double> bcv((size_t)6 * ctx->C * Nu, 0.0);
+    for (int face = 0; face < 6; ++face) {
+        if (mesh->periodic[face / 2]) continue;
+        const double *st = mesh->bc_state[face];
+        for (int k = 0; k < Nu; ++k) {
+            const double *v = &ctx->vtab_h[(size_t)k * BGK_VTAB];
+            const double F = maxwellian_value(v[0], v[1], v[2], st);
+            bcv[((size_t)face * ctx->C + 0) * Nu + k] = F;
+            if (ctx->C == 2) bcv[((size_t)face * ctx->C + 1) * Nu + k] = 0.5 * gas->delta * st[4] * F;
+        }
+    }
+    // velocity blocking: enough CTAs to fill the GPU, bounded partial buffer
+    {
+        const int n_pb = (ctx->P + 255) / 256;
+        const int lines = (int)(Nu / vg->n[0]);
+        int want = (2432 + n_pb - 1) / n_pb;
+        if (want > 64) want = 64;
+        if (want > lines) want = lines;
+        if (want < 1) want = 1;
+        const int lines_per_blk = (lines + want - 1) / want;
+        ctx->Kblk = lines_per_blk * vg->n[0];
+        ctx->n_vblk = (int)((Nu + ctx->Kblk - 1) / ctx->Kblk);
+    }
+
+    bgk_status st = BGK_OK;
+    auto cu = [&](cudaError_t e, const char *what) {
+        if (e != cudaSuccess && st == BGK_OK) {
+            st = e == cudaErrorMemoryAllocation ? BGK_ENOMEM : BGK_ECUDA;
+            ctx->err = std::string(what) + ": " + cudaGetErrorString(e);
+        }
+    };
+    cu(cudaGetDevice(&ctx->device), "cudaGetDevice");
+    ctx->elem = precision == BGK_FP64 ? sizeof(double) : sizeof(float);
+    const size_t fbytes = (size_t)ctx->C * Nu * ctx->P * ctx->elem;
+    for (int i = 0; i < 3; ++i) {
+        ctx->f[i] = nullptr;
+        if (st == BGK_OK) cu(cudaMalloc(&ctx->f[i], fbytes), "cudaMalloc(state)");
+    }
+    const size_t P = ctx->P;
+    if (st == BGK_OK) cu(cudaMalloc(&ctx->part, (size_t)ctx->n_vblk * BGK_NMOM * P * sizeof(double)), "cudaMalloc(part)");
+    if (st == BGK_OK) cu(cudaMalloc(&ctx->mom, P * BGK_NMOM * sizeof(double)), "cudaMalloc(mom)");
+    if (st == BGK_OK) cu(cudaMalloc(&ctx->eq, P * BGK_NEQ * sizeof(double)), "cudaMalloc(eq)");
+    if (st == BGK_OK) cu(cudaMalloc(&ctx->qp, P * 5 * sizeof(double)), "cudaMalloc(qp)");
+    if (st == BGK_OK) cu(cudaMalloc(&ctx->iters, P * sizeof(int)), "cudaMalloc(iters)");
+    if (st == BGK_OK) cu(cudaMalloc(&ctx->vtab, ctx->vtab_h.size() * sizeof(double)), "cudaMalloc(vtab)");
+    if (st == BGK_OK) cu(cudaMalloc(&ctx->bcval, bcv.size() * sizeof(double)), "cudaMalloc(bcval)");
+    if (st == BGK_OK) cu(cudaMalloc(&ctx->status, sizeof(unsigned int)), "cudaMalloc(status)");
+    if (st == BGK_OK) cu(cudaMalloc(&ctx->stats, sizeof(NewtonStats)), "cudaMalloc(stats)");
+    if (st == BGK_OK) cu(cudaMemcpyAsync(ctx->vtab, ctx->vtab_h.data(), ctx->vtab_h.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload vtab");
+    if (st == BGK_OK) cu(cudaMemcpyAsync(ctx->bcval, bcv.data(), bcv.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload bc");
+    if (st == BGK_OK) cu(cudaMemsetAsync(ctx->status, 0, sizeof(unsigned int), ctx->stream), "memset status");
+    if (st == BGK_OK) cu(cudaMemsetAsync(ctx->stats, 0, sizeof(NewtonStats), ctx->stream), "memset stats");
+    if (st == BGK_OK) cu(cudaMemsetAsync(ctx->f[0], 0, fbytes, ctx->stream), "memset state");
+    if (st == BGK_OK) cu(cudaStreamSynchronize(ctx->stream), "sync");
+    ctx->part_valid = false;
+    *out = ctx;
+    return st;
+}
+
+bgk_status bgk_destroy(bgk_ctx *ctx) {
+    if (!ctx) return BGK_EINVAL;
+    cudaStreamSynchronize(ctx->stream);
+    for (auto &r : ctx->prof_pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+    for (int i = 0; i < 3; ++i) cudaFree(ctx->f[i]);
+    cudaFree(ctx->part); cudaFree(ctx->mom); cudaFree(ctx->eq); cudaFree(ctx->qp);
+    cudaFree(ctx->iters); cudaFree(ctx->vtab); cudaFree(ctx->bcval); cudaFree(ctx->status);
+    cudaFree(ctx->stats);
+    delete ctx;
+    return BGK_OK;
+}
+
+bgk_status bgk_sizes(const bgk_ctx *ctx, int *n_elem, int *n_sol, int *n_vel, int *n_comp) {
+    if (!ctx) return BGK_EINVAL;
+    if (n_elem) *n_elem = ctx->Ne;
+    if (n_sol) *n_sol = ctx->Ns;
+    if (n_vel) *n_vel = ctx->Nu;
+    if (n_comp) *n_comp = ctx->C;
+    return BGK_OK;
+}
+
+const char *bgk_last_error(const bgk_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+bgk_status bgk_node_coords(const bgk_ctx *ctx_c, double *x, int on_device) {
+    bgk_ctx *ctx = const_cast<bgk_ctx *>(ctx_c);
+    if (!ctx || !x) return BGK_EINVAL;
+    const int q = ctx->q, n1 = ctx->mesh.n[0], n2 = ctx->mesh.n[1];
+    std::vector<double> h((size_t)ctx->P * 3);
+    for (int e = 0; e < ctx->Ne; ++e) {
+        const int c[3] = {e % n1, (e / n1) % n2, e / (n1 * n2)};
+        for (int s = 0; s < ctx->Ns; ++s) {
+            const int id[3] = {s % q, (s / q) % q, s / (q * q)};
+            for (int d = 0; d < 3; ++d) {
+                const double hd = 2.0 / ctx->mesh.two_over_h[d];
+                h[((size_t)e * ctx->Ns + s) * 3 + d] =
+                    ctx->lo[d] + (c[d] + 0.5 * (ctx->fr.xi[id[d]] + 1.0)) * hd;
+            }
+        }
+    }
+    CU(cudaMemcpyAsync(x, h.data(), h.size() * sizeof(double),
+                       on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return BGK_OK;
+}
+
+bgk_status bgk_set_state(bgk_ctx *ctx, const void *f, int on_device) {
+    if (!ctx || !f) return BGK_EINVAL;
+    const size_t bytes = (size_t)ctx->C * ctx->Nu * ctx->P * ctx->elem;
+    CU(cudaMemcpyAsync(ctx->f[0], f, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       ctx->stream));
+    ctx->part_valid = false;
+    if (!on_device) CU(cudaStreamSynchronize(ctx->stream));
+    return BGK_OK;
+}
+
+bgk_status bgk_get_state(bgk_ctx *ctx, void *f, int on_device) {
+    if (!ctx || !f) return BGK_EINVAL;
+    const size_t bytes = (size_t)ctx->C * ctx->Nu * ctx->P * ctx->elem;
+    CU(cudaMemcpyAsync(f, ctx->f[0], bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    if (!on_device) CU(cudaStreamSynchronize(ctx->stream));
+    return BGK_OK;
+}
+
+bgk_status bgk_set_maxwellian(bgk_ctx *ctx, const double *q, int on_device) {
+    if (!ctx || !q) return BGK_EINVAL;
+    if (ctx->precision != BGK_FP64) return fail(ctx, BGK_ENOTSUP, "mixed precision not built");
+    const double *dq = q;
+    double *tmp = nullptr;
+    if (!on_device) {
+        CU(cudaMallocAsync((void **)&tmp, (size_t)ctx->P * 5 * sizeof(double), ctx->stream));
+        CU(cudaMemcpyAsync(tmp, q, (size_t)ctx->P * 5 * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        dq = tmp;
+    }
+    {
+        LaunchScope ls(ctx, BGK_K_OTHER);
+        CU(launch_maxwellian_f64((double *)ctx->f[0], dq, ctx->vtab, ctx->Nu, ctx->P, ctx->C,
+                                 ctx->gas.delta, ctx->stream));
+    }
+    if (tmp) CU(cudaFreeAsync(tmp, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->part_valid = false;
+    return BGK_OK;
+}
+
+bgk_status bgk_set_newton(bgk_ctx *ctx, double tol, int max_iter) {
+    if (!ctx || !(tol > 0.0) || max_iter < 0) return BGK_EINVAL;
+    ctx->tol = tol;
+    ctx->max_iter = max_iter;
+    return BGK_OK;
+}
+
+bgk_status bgk_step(bgk_ctx *ctx, double dt, int n_steps) {
+    if (!ctx || !(dt > 0.0) || n_steps < 0) return BGK_EINVAL;
+    bgk_status st;
+    if (!ctx->part_valid) {
+        if ((st = run_moments(ctx, ctx->f[0]))) return st;
+        ctx->part_valid = true;
+    }
+    for (int n = 0; n < n_steps; ++n) {
+        void *f0 = ctx->f[0], *f1 = ctx->f[1], *f2 = ctx->f[2];
+        if ((st = stage_from_partials(ctx, nullptr, f0, f1, 0.0, 1.0, dt, true))) return st;
+        if ((st = stage_from_partials(ctx, f0, f1, f2, 0.75, 0.25, 0.25 * dt, true))) return st;
+        if ((st = stage_from_partials(ctx, f0, f2, f1, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0 * dt, true))) return st;
+        ctx->f[0] = f1;
+        ctx->f[1] = f0;
+    }
+    return check_device_status(ctx);
+}
+
+bgk_status bgk_stage(bgk_ctx *ctx, const void *f_n, const void *f_in, void *f_out, double a,
+                     double b, double c) {
+    if (!ctx || !f_in || !f_out || f_in == f_out) return BGK_EINVAL;
+    if (a != 0.0 && !f_n) return BGK_EINVAL;
+    bgk_status st;
+    if ((st = run_moments(ctx, f_in))) return st;
+    if ((st = stage_from_partials(ctx, f_n, f_in, f_out, a, b, c, false))) return st;
+    ctx->part_valid = false;
+    return check_device_status(ctx);
+}
+
+bgk_status bgk_rhs(bgk_ctx *ctx, const void *f_in, void *r_out, int on_device) {
+    if (!ctx || !f_in || !r_out) return BGK_EINVAL;
+    const size_t bytes = (size_t)ctx->C * ctx->Nu * ctx->P * ctx->elem;
+    CU(cudaMemcpyAsync(ctx->f[1], f_in, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       ctx->stream));
+    bgk_status st;
+    if ((st = run_moments(ctx, ctx->f[1]))) return st;
+    if ((st = stage_from_partials(ctx, nullptr, ctx->f[1], ctx->f[2], 0.0, 0.0, 1.0, false))) return st;
+    ctx->part_valid = false;
+    CU(cudaMemcpyAsync(r_out, ctx->f[2], bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return check_device_status(ctx);
+}
+
+bgk_status bgk_moments(bgk_ctx *ctx, double *m, int on_device) {
+    if (!ctx || !m) return BGK_EINVAL;
+    bgk_status st;
+    if (!ctx->part_valid) {
+        if ((st = run_moments(ctx, ctx->f[0]))) return st;
+        ctx->part_valid = true;
+    }
+    {
+        LaunchScope ls(ctx, BGK_K_OTHER);
+        CU(launch_reduce_moments(ctx->part, ctx->n_vblk, ctx->P, ctx->mom, ctx->stream));
+    }
+    CU(cudaMemcpyAsync(m, ctx->mom, (size_t)ctx->P * BGK_NMOM * sizeof(double),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return BGK_OK;
+}
+
+bgk_status bgk_qprime(bgk_ctx *ctx, const double *m, int n_points, double *qp, int *iters,
+                      int on_device) {
+    if (!ctx || !m || !qp || n_points <= 0) return BGK_EINVAL;
+    // moments laid out [P][NMOM] by the caller; the kernel reads [vb][NMOM][P]
+    double *dm = nullptr, *dq = nullptr;
+    int *di = nullptr;
+    const size_t n = (size_t)n_points;
+    CU(cudaMallocAsync((void **)&dm, n * BGK_NMOM * sizeof(double), ctx->stream));
+    CU(cudaMallocAsync((void **)&dq, n * 5 * sizeof(double), ctx->stream));
+    CU(cudaMallocAsync((void **)&di, n * sizeof(int), ctx->stream));
+    std::vector<double> hm(n * BGK_NMOM), ht(n * BGK_NMOM);
+    CU(cudaMemcpyAsync(hm.data(), m, hm.size() * sizeof(double),
+                       on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    for (size_t p = 0; p < n; ++p)
+        for (int j = 0; j < BGK_NMOM; ++j) ht[(size_t)j * n + p] = hm[p * BGK_NMOM + j];
+    CU(cudaMemcpyAsync(dm, ht.data(), ht.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    bgk_status st = run_qprime(ctx, dm, 1, n_points, nullptr, dq, di, nullptr);
+    if (st) return st;
+    CU(cudaMemcpyAsync(qp, dq, n * 5 * sizeof(double),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    if (iters)
+        CU(cudaMemcpyAsync(iters, di, n * sizeof(int),
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaFreeAsync(dm, ctx->stream));
+    CU(cudaFreeAsync(dq, ctx->stream));
+    CU(cudaFreeAsync(di, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return check_device_status(ctx);
+}
+
+bgk_status bgk_totals(bgk_ctx *ctx, double totals[5]) {
+    if (!ctx || !totals) return BGK_EINVAL;
+    std::vector<double> m((size_t)ctx->P * BGK_NMOM);
+    bgk_status st = bgk_moments(ctx, m.data(), 0);
+    if (st) return st;
+    const int q = ctx->q;
+    double t[5] = {0, 0, 0, 0, 0};
+    for (int p = 0; p < ctx->P; ++p) {
+        const int s = p % ctx->Ns;
+        const double W = ctx->fr.wq[s % q] * ctx->fr.wq[(s / q) % q] * ctx->fr.wq[s / (q * q)] * ctx->jac;
+        const double *mm = &m[(size_t)p * BGK_NMOM];
+        t[0] += W * mm[0]; t[1] += W * mm[1]; t[2] += W * mm[2]; t[3] += W * mm[3];
+        t[4] += W * (0.5 * (mm[4] + mm[5] + mm[6]) + mm[10]);
+    }
+    for (int j = 0; j < 5; ++j) totals[j] = t[j];
+    return BGK_OK;
+}
+
+bgk_status bgk_profile(bgk_ctx *ctx, int enable) {
+    if (!ctx) return BGK_EINVAL;
+    CU(cudaStreamSynchronize(ctx->stream));
+    for (auto &r : ctx->prof_pending) { ctx->ev_pool.push_back(r.a); ctx->ev_pool.push_back(r.b); }
+    ctx->prof_pending.clear();
+    for (int k = 0; k < BGK_NKINDS; ++k) { ctx->prof_ms[k] = 0.0; ctx->launches[k] = 0; }
+    ctx->prof_on = enable != 0;
+    return BGK_OK;
+}
+
+bgk_status bgk_profile_read(bgk_ctx *ctx, double ms[BGK_NKINDS], long long launches[BGK_NKINDS]) {
+    if (!ctx) return BGK_EINVAL;
+    CU(cudaStreamSynchronize(ctx->stream));
+    for (auto &r : ctx->prof_pending) {
+        float t = 0.f;
+        CU(cudaEventElapsedTime(&t, r.a, r.b));
+        ctx->prof_ms[r.kind] += t;
+        ctx->ev_pool.push_back(r.a);
+        ctx->ev_pool.push_back(r.b);
+    }
+    ctx->prof_pending.clear();
+    for (int k = 0; k < BGK_NKINDS; ++k) {
+        if (ms) ms[k] = ctx->prof_ms[k];
+        if (launches) launches[k] = ctx->launches[k];
+    }
+    return BGK_OK;
+}
+
+bgk_status bgk_stats(bgk_ctx *ctx, double *mean_iters, int *max_iters, double *max_residual) {
+    if (!ctx) return BGK_EINVAL;
+    NewtonStats s;
+    CU(cudaMemcpyAsync(&s, ctx->stats, sizeof s, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemsetAsync(ctx->stats, 0, sizeof(NewtonStats), ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (mean_iters) *mean_iters = s.solves ? (double)s.iter_sum / (double)s.solves : 0.0;
+    if (max_iters) *max_iters = s.iter_max;
+    if (max_residual) {
+        double r;
+        long long bits = (long long)s.res_max_bits;
+        std::memcpy(&r, &bits, sizeof r);
+        *max_residual = r;
+    }
+    return BGK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,95 @@
+// Internal declarations shared by the libbgk translation units.
+// Kernel argument structs are passed by value (constant bank), so every
+// operator table a kernel needs travels with its launch.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#define BGK_MAXQ 5          // FR order p <= 4
+#define BGK_NMOM 11         // raw moment slots per point
+#define BGK_NEQ 12          // equilibrium record per point
+#define BGK_VTAB 8          // velocity table record: u1 u2 u3 w e=|u|^2/2 (3 pad)
+
+// Device status bits (OR-ed by kernels, read by the host after a stage).
+#define BGK_DEV_NOCONV 1u
+#define BGK_DEV_NONFINITE 2u
+
+// 1-D FR operators on Gauss--Legendre nodes (section "Numerical method").
+struct FROps {
+    int q;                              // p + 1
+    double D[BGK_MAXQ][BGK_MAXQ];       // D[i][j] = l_j'(xi_i)
+    double lm[BGK_MAXQ], lp[BGK_MAXQ];  // l_j(-1), l_j(+1)
+    double dgL[BGK_MAXQ], dgR[BGK_MAXQ];// correction-function derivatives at the nodes
+    double wq[BGK_MAXQ];                // Gauss weights
+    double xi[BGK_MAXQ];                // nodes
+};
+
+struct MeshInfo {
+    int n[3];
+    int periodic[3];
+    double two_over_h[3];
+    int Ne, Ns;
+};
+
+struct GasInfo {
+    double delta, Pr, mu_ref, theta_ref, theta_S, gamma;
+};
+
+// Newton statistics accumulated on the device.
+struct NewtonStats {
+    unsigned long long iter_sum;
+    unsigned long long solves;
+    int iter_max;
+    int pad;
+    unsigned long long res_max_bits;    // bit pattern of a non-negative double
+};
+
+// Arguments of the fused stage kernel:  f_out = a f_n + b f_s + c R(f_s).
+template <typename T>
+struct StageArgs {
+    const T *f_n;            // may be null when a == 0
+    const T *f_s;
+    T *f_out;
+    const double *eq;        // [P][BGK_NEQ]
+    const double *vtab;      // [Nu][BGK_VTAB]
+    const double *bcval;     // [6][C][Nu] exterior Maxwellian values of Dirichlet faces
+    double *part;            // [n_vblk][BGK_NMOM][P] moment partials of f_out (or null)
+    double a, b, c;
+    int Nu, P, Kblk, vel_n1, vel_n2;
+    FROps fr;
+    MeshInfo mesh;
+};
+
+struct QPrimeArgs {
+    const double *part;      // [n_vblk][BGK_NMOM][P]
+    int n_vblk;
+    const double *vtab;
+    const double *guess;     // [P][5] or null
+    double *eq;              // [P][BGK_NEQ] or null
+    double *qp;              // [P][5] or null
+    int *iters;              // [P] or null
+    unsigned int *status;
+    NewtonStats *stats;
+    int P, Nu;
+    double tol;
+    int max_iter;
+    GasInfo gas;
+};
+
+struct MomentArgs64 {
+    const double *f;
+    double *part;
+    const double *vtab;
+    int Nu, P, Kblk, C;
+};
+
+// Launchers (kernels_f64.cu).
+cudaError_t launch_moments_f64(const MomentArgs64 &a, int n_vblk, cudaStream_t s);
+cudaError_t launch_qprime_f64(const QPrimeArgs &a, cudaStream_t s);
+cudaError_t launch_stage_f64(const StageArgs<double> &a, int C, int n_vblk, cudaStream_t s);
+cudaError_t launch_maxwellian_f64(double *f, const double *q, const double *vtab, int Nu, int P,
+                                  int C, double delta, cudaStream_t s);
+cudaError_t launch_reduce_moments(const double *part, int n_vblk, int P, double *m_out,
+                                  cudaStream_t s);

@@ -1,0 +1,80 @@
+"""The C-ABI library loads and exports every entry point include/bgk.h declares
+(no compute calls: this runs without a GPU)."""
+import ctypes
+import os
+import re
+
+from paper_2312_06567_gb300 import bgk
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            names += re.findall(r"BGK_API\s+[\w\s\*]+?\b(bgk_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("bgk_create", "bgk_destroy", "bgk_step", "bgk_rhs", "bgk_qprime",
+                     "bgk_moments", "bgk_set_state", "bgk_get_state", "bgk_totals"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libbgk):
+    for name in _declared():
+        assert hasattr(libbgk, name), name
+        assert isinstance(getattr(libbgk, name), ctypes._CFuncPtr)
+
+
+def test_binding_covers_every_declared_symbol():
+    assert set(_declared()) == set(bgk.SIGNATURES)
+
+
+def test_descriptor_layout_matches_header(tmp_path):
+    """ctypes structures agree with the C compiler's layout of include/bgk.h."""
+    import subprocess
+    src = tmp_path / "layout.c"
+    src.write_text("""#include <stdio.h>
+#include <stddef.h>
+#include "bgk.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(bgk_mesh_desc), offsetof(bgk_mesh_desc, lo),
+         offsetof(bgk_mesh_desc, hi), offsetof(bgk_mesh_desc, periodic),
+         offsetof(bgk_mesh_desc, order), offsetof(bgk_mesh_desc, bc_state));
+  printf("%zu %zu %zu\\n", sizeof(bgk_vgrid_desc), offsetof(bgk_vgrid_desc, lo),
+         offsetof(bgk_vgrid_desc, hi));
+  printf("%zu %zu\\n", sizeof(bgk_gas_desc), offsetof(bgk_gas_desc, theta_S));
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = [list(map(int, l.split())) for l in subprocess.check_output([str(exe)]).decode().splitlines()]
+    M = bgk.MeshDesc
+    assert out[0] == [ctypes.sizeof(M), M.lo.offset, M.hi.offset, M.periodic.offset,
+                      M.order.offset, M.bc_state.offset]
+    V = bgk.VGridDesc
+    assert out[1] == [ctypes.sizeof(V), V.lo.offset, V.hi.offset]
+    assert out[2] == [ctypes.sizeof(bgk.GasDesc), bgk.GasDesc.theta_S.offset]
+
+
+def test_invalid_descriptors_rejected_on_the_host(libbgk):
+    """Descriptor validation happens before any CUDA call: BGK_EINVAL + message."""
+    import pytest
+    from paper_2312_06567_gb300 import workloads as W
+    base = W.periodic_sine_box()
+    bad = [base.replace(p=0), base.replace(p=5), base.replace(vel_n=(1, 8, 8)),
+           base.replace(delta=-1.0), base.replace(Pr=0.5), base.replace(mesh_n=(0, 4, 4)),
+           base.replace(mesh_hi=(0.0, 1, 1)),
+           W.normal_shock_tube().replace(dirichlet={(0, -1): (0.0, (1, 0, 0), 1.0),
+                                                    (0, 1): (1.0, (1, 0, 0), 1.0)})]
+    for wl in bad:
+        with pytest.raises(bgk.BGKError) as ei:
+            bgk.Solver(wl)
+        assert ei.value.status == bgk.BGK_EINVAL
+        assert str(ei.value)
