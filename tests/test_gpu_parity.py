@@ -57,17 +57,20 @@ def _mild_es_box(mesh_n=(3, 2, 2), p=3, vel_n=(10, 9, 8)):
     return W.reduced(W.taylor_green_box(), mesh_n=mesh_n, vel_n=vel_n).replace(p=p)
 
 
-def _mild_shock(mesh_n=(6, 1, 1), vel_n=(12, 7, 6), mach=3.0):
-    return W.reduced(W.normal_shock_tube(mach=mach), mesh_n=mesh_n, vel_n=vel_n)
+def _mild_shock(mesh_n=(6, 1, 1), vel_n=(16, 10, 9), mach=3.0):
+    """Polyatomic (F, G) normal shock with Dirichlet x-ends at M=3, on a velocity
+    box narrowed to the M=3 states so a small grid still resolves them."""
+    wl = W.reduced(W.normal_shock_tube(mach=mach), mesh_n=mesh_n, vel_n=vel_n)
+    return wl.replace(vel_lo=(-9.0, -8.0, -8.0), vel_hi=(11.0, 8.0, 8.0))
 
 
 CASES = {
     "sine_box_p1": lambda: W.periodic_sine_box(),
     "tgv_es_p3_ragged": lambda: _mild_es_box(),
     "shock_fg_p2_dirichlet": lambda: _mild_shock(),
-    "tiny_p4_single_element": lambda: _mild_es_box(mesh_n=(1, 1, 1), p=4, vel_n=(4, 3, 5)),
-    "ragged_p1_dirichlet_x": lambda: _mild_shock(mesh_n=(3, 1, 2), vel_n=(5, 3, 7)).replace(
-        p=1, periodic=(False, True, True)),
+    "tiny_p4_single_element": lambda: _mild_es_box(mesh_n=(1, 1, 1), p=4, vel_n=(9, 8, 10)),
+    "ragged_p1_dirichlet_x": lambda: _mild_shock(mesh_n=(3, 1, 2), vel_n=(13, 9, 11)).replace(
+        p=1),
 }
 
 
@@ -84,6 +87,7 @@ def test_moments_and_rhs_match_oracle(lib, name):
                              if wl.n_comp == 2 else None, pb.vg)
     assert moment_err(m_gpu, m_ora, wl.delta) <= 1e-13
     r_ora, info = pb.rhs(f)
+    assert np.all(info["converged"])
     assert rhs_err(r_gpu, r_ora, f, wl, info["tau"].min()) <= TOL
 
 
@@ -157,7 +161,7 @@ def test_set_maxwellian_matches_generator(lib):
         assert np.allclose(s.node_coords(), x, rtol=0, atol=1e-13)
         s.set_maxwellian(q)
         f_gpu = s.get_state()
-    assert slab_err(f_gpu, W.maxwellian_state(wl)) <= 1e-14
+    assert slab_err(f_gpu, W.maxwellian_state(wl)) <= TOL
 
 
 def test_newton_nonconvergence_is_reported_not_trapped(lib):
