@@ -140,6 +140,26 @@ BGK_API bgk_status bgk_stage(bgk_ctx *ctx, const void *f_n, const void *f_in, vo
  * (3), sum w u_d^2 F (3), sum w u1u2 F, sum w u1u3 F, sum w u2u3 F, sum w G. */
 BGK_API bgk_status bgk_moments(bgk_ctx *ctx, double *m, int on_device);
 
+/* Raw moments of a caller-owned state without allocating any device memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc (a framework that has claimed the whole memory
+ * pool, a real-time loop that must not allocate, a plugin host that forbids
+ * allocation) and therefore cannot create a context.
+ *   vgrid   velocity grid (as for bgk_create); N_u = n[0] n[1] n[2]
+ *   f       device array f[n_comp][N_u][n_points], double (BGK_FP64 layout)
+ *   m       device output m[n_points][11], slots as in bgk_moments
+ *   stream  cudaStream_t (NULL = legacy default stream); the call is
+ *           asynchronous on it and returns after the launches.
+ * Scratch: a fixed 16 MiB device array inside libbgk (2^21 doubles), held by
+ * every GPU that loads the library until the process exits;
+ * n_points * 11 must not exceed 2^21 (n_points <= 190650), else BGK_EINVAL.
+ * All calls share that array, so calls that overlap on the GPU race; each
+ * call overwrites every partial sum it reads, so nothing needs clearing.
+ * The first call on each device looks up the array's device address; make
+ * it before starting any stream capture.  Errors: BGK_EINVAL, BGK_ECUDA. */
+BGK_API bgk_status bgk_moments_noalloc(const bgk_vgrid_desc *vgrid, const double *f, int n_comp,
+                                       int n_points, double *m, void *stream);
+
 /* The Q' solve alone (section "Numerical method", discrete compatibility):
  * from raw moments m[n_points][11] (layout of bgk_moments) to
  * qp[n_points][5] = (rho', U'_1..3, theta') and Newton update counts

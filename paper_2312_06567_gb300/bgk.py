@@ -50,6 +50,8 @@ SIGNATURES = {
     "bgk_step": (c_int, [c_void_p, c_double, c_int]),
     "bgk_stage": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_double, c_double]),
     "bgk_moments": (c_int, [c_void_p, c_void_p, c_int]),
+    "bgk_moments_noalloc": (c_int, [ctypes.POINTER(VGridDesc), c_void_p, c_int, c_int, c_void_p,
+                                    c_void_p]),
     "bgk_qprime": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_int]),
     "bgk_totals": (c_int, [c_void_p, ctypes.POINTER(c_double)]),
     "bgk_stats": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int),
@@ -131,6 +133,18 @@ def descriptors(wl):
         v.n[d], v.lo[d], v.hi[d] = wl.vel_n[d], wl.vel_lo[d], wl.vel_hi[d]
     g = GasDesc(wl.delta, wl.Pr, wl.mu_ref, wl.theta_ref, wl.theta_S)
     return m, v, g
+
+
+def moments_noalloc(vgrid, f, n_comp, n_points, m, stream=None):
+    """bgk_moments_noalloc: raw moments of a device state into a device output
+    without any device allocation by the library (see include/bgk.h).
+    vgrid: VGridDesc; f: CUDA tensor [n_comp, N_u, n_points] float64;
+    m: CUDA tensor [n_points, 11] float64."""
+    lib = load()
+    st = lib.bgk_moments_noalloc(ctypes.byref(vgrid), _ptr(f)[0], n_comp, n_points, _ptr(m)[0],
+                                 _stream_handle(stream))
+    if st != BGK_OK:
+        raise BGKError(st, "bgk_moments_noalloc failed")
 
 
 class Solver:
