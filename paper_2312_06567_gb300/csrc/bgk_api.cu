@@ -18,6 +18,7 @@ struct bgk_ctx {
     MeshInfo mesh;
     FROps fr;
     GasInfo gas;
+    VelGrid vg;
     double jac;                       // |J_e|
     double lo[3];                     // mesh box corner
     double bc[6][5];
@@ -205,7 +206,7 @@ bgk_status run_qprime(bgk_ctx *ctx, const double *part, int n_vblk, int P, doubl
     QPrimeArgs a{};
     a.part = part; a.n_vblk = n_vblk; a.vtab = ctx->vtab; a.guess = guess; a.eq = eq; a.qp = qp;
     a.iters = iters; a.status = ctx->status; a.stats = ctx->stats; a.P = P; a.Nu = ctx->Nu;
-    a.tol = ctx->tol; a.max_iter = ctx->max_iter; a.gas = ctx->gas;
+    a.tol = ctx->tol; a.max_iter = ctx->max_iter; a.gas = ctx->gas; a.vg = ctx->vg;
     LaunchScope ls(ctx, BGK_K_QPRIME);
     CU(launch_qprime_f64(a, ctx->stream));
     return BGK_OK;
@@ -218,7 +219,7 @@ bgk_status run_stage(bgk_ctx *ctx, const void *fn, const void *fs, void *fo, dou
     s.f_n = (const double *)fn; s.f_s = (const double *)fs; s.f_out = (double *)fo;
     s.eq = ctx->eq; s.vtab = ctx->vtab; s.bcval = ctx->bcval; s.part = moments ? ctx->part : nullptr;
     s.a = a; s.b = b; s.c = c; s.Nu = ctx->Nu; s.P = ctx->P; s.Kblk = ctx->Kblk;
-    s.vel_n1 = ctx->vn[0]; s.vel_n2 = ctx->vn[1]; s.fr = ctx->fr; s.mesh = ctx->mesh;
+    s.vg = ctx->vg; s.fr = ctx->fr; s.mesh = ctx->mesh;
     LaunchScope ls(ctx, BGK_K_STAGE);
     CU(launch_stage_f64(s, ctx->C, ctx->n_vblk, ctx->stream));
     return BGK_OK;
@@ -250,7 +251,7 @@ bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
     for (int d = 0; d < 3; ++d) {
         if (mesh->n[d] < 1) return bad("mesh n[d] must be >= 1");
         if (!(mesh->hi[d] > mesh->lo[d])) return bad("mesh hi must exceed lo");
-        if (vg->n[d] < 2) return bad("velocity grid needs >= 2 nodes per axis");
+        if (vg->n[d] < 2 || vg->n[d] > BGK_MAXV) return bad("velocity grid needs 2..128 nodes per axis");
         if (!(vg->hi[d] > vg->lo[d])) return bad("velocity hi must exceed lo");
     }
     if (!(gas->delta >= 0.0)) return bad("delta must be >= 0");
@@ -276,6 +277,9 @@ bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
     ctx->max_iter = 50;
     for (int d = 0; d < 3; ++d) {
         ctx->vn[d] = vg->n[d];
+        ctx->vg.n[d] = vg->n[d];
+        ctx->vg.lo[d] = vg->lo[d];
+        ctx->vg.h[d] = (vg->hi[d] - vg->lo[d]) / (vg->n[d] - 1);
         ctx->mesh.n[d] = mesh->n[d];
         ctx->mesh.periodic[d] = mesh->periodic[d] ? 1 : 0;
         ctx->mesh.two_over_h[d] = 2.0 * mesh->n[d] / (mesh->hi[d] - mesh->lo[d]);
@@ -297,7 +301,7 @@ bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
     for (int d = 0; d < 3; ++d) {
         const double h = (vg->hi[d] - vg->lo[d]) / (vg->n[d] - 1);
         for (int j = 0; j < vg->n[d]; ++j) {
-            ax[d].push_back(vg->lo[d] + j * h);
+            ax[d].push_back(std::fma((double)j, h, vg->lo[d]));
             wt[d].push_back((j == 0 || j == vg->n[d] - 1) ? 0.5 * h : h);
         }
     }
@@ -308,6 +312,8 @@ bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
         v[0] = ax[0][k1]; v[1] = ax[1][k2]; v[2] = ax[2][k3];
         v[3] = wt[0][k1] * wt[1][k2] * wt[2][k3];
         v[4] = 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        v[5] = v[3] * v[0];
+        v[6] = v[3] * v[0] * v[0];
     }
     // Dirichlet exterior states per face and velocity
     std::vector<double> bcv((size_t)6 * ctx->C * Nu, 0.0);

@@ -10,7 +10,8 @@
 #define BGK_MAXQ 5          // FR order p <= 4
 #define BGK_NMOM 11         // raw moment slots per point
 #define BGK_NEQ 12          // equilibrium record per point
-#define BGK_VTAB 8          // velocity table record: u1 u2 u3 w e=|u|^2/2 (3 pad)
+#define BGK_VTAB 8          // velocity table record: u1 u2 u3 w e=|u|^2/2 w*u1 w*u1^2 (1 pad)
+#define BGK_MAXV 128        // nodes per velocity axis at most
 
 // Device status bits (OR-ed by kernels, read by the host after a stage).
 #define BGK_DEV_NOCONV 1u
@@ -31,6 +32,12 @@ struct MeshInfo {
     int periodic[3];
     double two_over_h[3];
     int Ne, Ns;
+};
+
+// Uniform velocity grid: node j on axis d is lo[d] + j h[d].
+struct VelGrid {
+    int n[3];
+    double lo[3], h[3];
 };
 
 struct GasInfo {
@@ -57,7 +64,8 @@ struct StageArgs {
     const double *bcval;     // [6][C][Nu] exterior Maxwellian values of Dirichlet faces
     double *part;            // [n_vblk][BGK_NMOM][P] moment partials of f_out (or null)
     double a, b, c;
-    int Nu, P, Kblk, vel_n1, vel_n2;
+    int Nu, P, Kblk;
+    VelGrid vg;
     FROps fr;
     MeshInfo mesh;
 };
@@ -76,6 +84,7 @@ struct QPrimeArgs {
     double tol;
     int max_iter;
     GasInfo gas;
+    VelGrid vg;
 };
 
 struct MomentArgs64 {

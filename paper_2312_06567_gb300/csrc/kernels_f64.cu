@@ -4,12 +4,12 @@
 //   moments   raw velocity moments of f, partial over velocity blocks
 //   qprime    reduce the partials to Q, build the ES tensor and tau, and solve
 //             the discrete compatibility condition for Q' by Newton's method
-//             (one warp per point, lanes split the velocity sums)
+//             (one warp per point, lanes split the velocity lines)
 //   stage     FR divergence (nodal derivative + upwind interface jump lifted
 //             with the DG correction function) + BGK source + Shu--Osher
 //             combination, with the moment partials of the output in the
 //             epilogue (one thread per solution point, looping over a block
-//             of velocities so the point's equilibrium record stays in
+//             of velocity lines so the point's equilibrium record stays in
 //             registers)
 #include "bgk_internal.cuh"
 
@@ -138,11 +138,44 @@ __device__ __forceinline__ bool solve5(double J[5][5], double r[5]) {
     return true;
 }
 
+// Index of the centred raw moment sum w g ut1^p1 ut2^p2 ut3^p3 (p1+p2+p3 <= 4)
+// in the 35-slot accumulator; the slots run over (p2, p3, p1) in that order.
+__host__ __device__ constexpr int midx(int p1, int p2, int p3) {
+    int idx = 0;
+    for (int a = 0; a <= 4; ++a)
+        for (int b = 0; b <= 4 - a; ++b)
+            for (int m = 0; m <= 4 - a - b; ++m) {
+                if (a == p2 && b == p3 && m == p1) return idx;
+                ++idx;
+            }
+    return -1;
+}
+
+template <int N>
+__device__ __forceinline__ void warp_sum_n(double (&v)[N]) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = warp_sum(v[i]);
+}
+
+// Q' solve, one warp per point.  Velocity sums are organised by lines along
+// the first velocity axis: lane-strided over the n2*n3 lines, each line walked
+// outward from the node nearest its own peak with the Gaussian ratio
+// recurrence g_{j+1} = g_j r_j, r_{j+1} = r_j exp(-A11 h1^2) (one exp for the
+// peak value and one for the first ratio per line; the walk only ever
+// decreases g, so tails underflow harmlessly).  Each line yields the five sums
+// T_m = sum_j w1 g ut1^m, folded into the 35 raw moments of order <= 4 in
+// coordinates ut = u - U centred on the point's macroscopic velocity; the
+// residual and the analytic Jacobian are linear combinations of those.
 __global__ void __launch_bounds__(256) k_qprime_f64(QPrimeArgs a) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    __shared__ double tab[8][BGK_MAXV][5];
+    const int wib = threadIdx.x >> 5;
+    const int warp = blockIdx.x * 8 + wib;
     const int lane = threadIdx.x & 31;
     if (warp >= a.P) return;                 // whole warps exit together
     const int p = warp;
+    const VelGrid &vg = a.vg;
+    const int n1 = vg.n[0], n2 = vg.n[1], n3 = vg.n[2];
+    const double h1 = vg.h[0], h2 = vg.h[1], h3 = vg.h[2];
 
     // 1. reduce the moment partials of this point
     double m[BGK_NMOM];
@@ -152,24 +185,25 @@ __global__ void __launch_bounds__(256) k_qprime_f64(QPrimeArgs a) {
 #pragma unroll
         for (int j = 0; j < BGK_NMOM; ++j) m[j] += a.part[((size_t)vb * BGK_NMOM + j) * a.P + p];
     }
-#pragma unroll
-    for (int j = 0; j < BGK_NMOM; ++j) m[j] = warp_sum(m[j]);
+    warp_sum_n(m);
 
     // 2. macroscopic state, ES tensor, collision time
     const GasInfo &gs = a.gas;
     const double rho = m[0];
-    const double U1 = m[1] / rho, U2 = m[2] / rho, U3 = m[3] / rho;
+    const double U0[3] = {m[1] / rho, m[2] / rho, m[3] / rho};
     const double E = 0.5 * (m[4] + m[5] + m[6]) + m[10];
-    const double pres = (gs.gamma - 1.0) * (E - 0.5 * rho * (U1 * U1 + U2 * U2 + U3 * U3));
+    const double kin = 0.5 * rho * (U0[0] * U0[0] + U0[1] * U0[1] + U0[2] * U0[2]);
+    const double Eth = E - kin;
+    const double pres = (gs.gamma - 1.0) * Eth;
     const double theta = pres / rho;
     const double es = (1.0 - 1.0 / gs.Pr) / rho;
     Sym3 B;
-    B.t11 = es * (m[4] - rho * U1 * U1);
-    B.t22 = es * (m[5] - rho * U2 * U2);
-    B.t33 = es * (m[6] - rho * U3 * U3);
-    B.t12 = es * (m[7] - rho * U1 * U2);
-    B.t13 = es * (m[8] - rho * U1 * U3);
-    B.t23 = es * (m[9] - rho * U2 * U3);
+    B.t11 = es * (m[4] - rho * U0[0] * U0[0]);
+    B.t22 = es * (m[5] - rho * U0[1] * U0[1]);
+    B.t33 = es * (m[6] - rho * U0[2] * U0[2]);
+    B.t12 = es * (m[7] - rho * U0[0] * U0[1]);
+    B.t13 = es * (m[8] - rho * U0[0] * U0[2]);
+    B.t23 = es * (m[9] - rho * U0[1] * U0[2]);
     double mu = gs.mu_ref;
     if (gs.theta_S >= 0.0) {
         const double r = theta / gs.theta_ref;
@@ -177,7 +211,20 @@ __global__ void __launch_bounds__(256) k_qprime_f64(QPrimeArgs a) {
     }
     const double tau = mu / (gs.Pr * pres);
     const double sc_rho = 1.0 / rho, sc_mom = 1.0 / (rho * sqrt(theta)), sc_E = 1.0 / fabs(E);
-    const double Q[5] = {rho, m[1], m[2], m[3], E};
+    const double hU2 = 0.5 * (U0[0] * U0[0] + U0[1] * U0[1] + U0[2] * U0[2]);
+
+    // centred first-axis table: w1(j) ut1(j)^m
+    const double s1 = vg.lo[0] - U0[0];
+    for (int j = lane; j < n1; j += 32) {
+        const double ut = fma((double)j, h1, s1);
+        const double w = (j == 0 || j == n1 - 1) ? 0.5 * h1 : h1;
+        tab[wib][j][0] = w;
+        tab[wib][j][1] = w * ut;
+        tab[wib][j][2] = w * ut * ut;
+        tab[wib][j][3] = w * ut * ut * ut;
+        tab[wib][j][4] = w * ut * ut * ut * ut;
+    }
+    __syncwarp();
 
     // 3. Newton
     double x[5];
@@ -185,7 +232,7 @@ __global__ void __launch_bounds__(256) k_qprime_f64(QPrimeArgs a) {
 #pragma unroll
         for (int j = 0; j < 5; ++j) x[j] = a.guess[(size_t)p * 5 + j];
     } else {
-        x[0] = rho; x[1] = U1; x[2] = U2; x[3] = U3; x[4] = theta;
+        x[0] = rho; x[1] = U0[0]; x[2] = U0[1]; x[3] = U0[2]; x[4] = theta;
     }
     const double hd = 0.5 * gs.delta;
     int it = 0;
@@ -199,71 +246,191 @@ __global__ void __launch_bounds__(256) k_qprime_f64(QPrimeArgs a) {
         double det;
         sym3_inverse(T, A, det);
         c0 = log(x[0]) - 0.5 * log(kTwoPi * kTwoPi * kTwoPi * det);
-        // lane-strided velocity sums: g, g u, g e | g v, g u v, g e v | g vv, g u vv, g e vv
-        double s_g = 0, s_gu[3] = {0, 0, 0}, s_ge = 0;
-        double s_gv[3] = {0, 0, 0}, s_guv[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, s_gev[3] = {0, 0, 0};
-        double s_gvv = 0, s_guvv[3] = {0, 0, 0}, s_gevv = 0;
-        for (int k = lane; k < a.Nu; k += 32) {
-            const double *vt = a.vtab + (size_t)k * BGK_VTAB;
-            const double u[3] = {__ldg(vt + 0), __ldg(vt + 1), __ldg(vt + 2)};
-            const double w = __ldg(vt + 3), e = __ldg(vt + 4);
-            const double c1 = u[0] - x[1], c2 = u[1] - x[2], c3 = u[2] - x[3];
-            const double v[3] = {A.t11 * c1 + A.t12 * c2 + A.t13 * c3,
-                                 A.t12 * c1 + A.t22 * c2 + A.t23 * c3,
-                                 A.t13 * c1 + A.t23 * c2 + A.t33 * c3};
-            const double qf = c1 * v[0] + c2 * v[1] + c3 * v[2];
-            const double g = w * exp(c0 - 0.5 * qf);
-            const double vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-            const double ge = g * e, gvv = g * vv;
-            s_g += g;
-            s_ge += ge;
-            s_gvv += gvv;
-            s_gevv = fma(ge, vv, s_gevv);
+        const double dl[3] = {x[1] - U0[0], x[2] - U0[1], x[3] - U0[2]};
+        const double rho1 = exp(-A.t11 * h1 * h1);
+        const double ia11 = 1.0 / A.t11, ih1 = 1.0 / h1;
+        double M[35];
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const double gu = g * u[d];
-                s_gu[d] += gu;
-                s_gv[d] = fma(g, v[d], s_gv[d]);
-                s_gev[d] = fma(ge, v[d], s_gev[d]);
-                s_guvv[d] = fma(gu, vv, s_guvv[d]);
+        for (int i = 0; i < 35; ++i) M[i] = 0.0;
+        for (int line = lane; line < n2 * n3; line += 32) {
+            const int j2 = line % n2, j3 = line / n2;
+            const double ut2 = fma((double)j2, h2, vg.lo[1] - U0[1]);
+            const double ut3 = fma((double)j3, h3, vg.lo[2] - U0[2]);
+            const double w23 = ((j2 == 0 || j2 == n2 - 1) ? 0.5 * h2 : h2) *
+                               ((j3 == 0 || j3 == n3 - 1) ? 0.5 * h3 : h3);
+            const double c2 = ut2 - dl[1], c3 = ut3 - dl[2];
+            const double lin = A.t12 * c2 + A.t13 * c3;
+            const double cst = A.t22 * c2 * c2 + 2.0 * A.t23 * c2 * c3 + A.t33 * c3 * c3;
+            const double jf = (-lin * ia11 + dl[0] - s1) * ih1;
+            const int js = (int)rint(fmin(fmax(jf, 0.0), (double)(n1 - 1)));
+            const double c1s = fma((double)js, h1, s1) - dl[0];
+            const double G = exp(c0 - 0.5 * (A.t11 * c1s * c1s + 2.0 * c1s * lin + cst));
+            const double D = fmin(fmax(-h1 * (A.t11 * (c1s + 0.5 * h1) + lin), -700.0), 700.0);
+            const double rup = exp(D);
+            const double rdn = rho1 / rup;
+            double Tm[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+            int j = js, dir = 1;
+            double g = G, r = rup;
+            const int nup = n1 - js;
+            for (int t = 0; t < n1; ++t) {
+                if (t == nup) { j = js - 1; dir = -1; g = G * rdn; r = rdn * rho1; }
+                const double *tb = tab[wib][j];
 #pragma unroll
-                for (int f = 0; f < 3; ++f) s_guv[d][f] = fma(gu, v[f], s_guv[d][f]);
+                for (int q = 0; q < 5; ++q) Tm[q] = fma(g, tb[q], Tm[q]);
+                g *= r;
+                r *= rho1;
+                j += dir;
             }
-        }
-        s_g = warp_sum(s_g); s_ge = warp_sum(s_ge); s_gvv = warp_sum(s_gvv); s_gevv = warp_sum(s_gevv);
+            double pu2[5], pu3[5];
+            pu2[0] = w23; pu3[0] = 1.0;
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            s_gu[d] = warp_sum(s_gu[d]); s_gv[d] = warp_sum(s_gv[d]);
-            s_gev[d] = warp_sum(s_gev[d]); s_guvv[d] = warp_sum(s_guvv[d]);
+            for (int q = 1; q < 5; ++q) { pu2[q] = pu2[q - 1] * ut2; pu3[q] = pu3[q - 1] * ut3; }
 #pragma unroll
-            for (int f = 0; f < 3; ++f) s_guv[d][f] = warp_sum(s_guv[d][f]);
+            for (int aa = 0; aa <= 4; ++aa)
+#pragma unroll
+                for (int bb = 0; bb <= 4 - aa; ++bb) {
+                    const double P = pu2[aa] * pu3[bb];
+#pragma unroll
+                    for (int mm = 0; mm <= 4 - aa - bb; ++mm)
+                        M[midx(mm, aa, bb)] = fma(P, Tm[mm], M[midx(mm, aa, bb)]);
+                }
         }
-        const double eint = hd * x[4];                       // delta theta' / 2
-        double R[5] = {s_g - Q[0], s_gu[0] - Q[1], s_gu[1] - Q[2], s_gu[2] - Q[3],
-                       s_ge + eint * s_g - Q[4]};
+        warp_sum_n(M);
+
+        // residual in absolute coordinates from the centred moments
+#define MM(p1, p2, p3) M[midx(p1, p2, p3)]
+        const double M0 = MM(0, 0, 0);
+        const double Me[3] = {MM(1, 0, 0), MM(0, 1, 0), MM(0, 0, 1)};
+        const double Se = 0.5 * (MM(2, 0, 0) + MM(0, 2, 0) + MM(0, 0, 2));
+        const double eint = hd * x[4];
+        const double dM0 = M0 - rho;
+        const double UMe = U0[0] * Me[0] + U0[1] * Me[1] + U0[2] * Me[2];
+        double R[5];
+        R[0] = dM0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) R[1 + d] = fma(U0[d], dM0, Me[d]);
+        R[4] = Se + UMe + hU2 * dM0 + eint * M0 - Eth;
         res = fmax(fabs(R[0]) * sc_rho,
                    fmax(fmax(fabs(R[1]), fmax(fabs(R[2]), fabs(R[3]))) * sc_mom, fabs(R[4]) * sc_E));
         if (res <= a.tol) { conv = true; break; }
         if (it >= a.max_iter || !(res == res)) break;
-        const double trA = A.t11 + A.t22 + A.t33;
-        const double k2 = 0.5 / gs.Pr;
-        double J[5][5];
-        const double ir = 1.0 / x[0];
-        J[0][0] = s_g * ir;
-        J[4][0] = (s_ge + eint * s_g) * ir;
+
+        // Jacobian: moment combinations of v = A c = A ut - A dl
+        const double Am[3][3] = {{A.t11, A.t12, A.t13}, {A.t12, A.t22, A.t23}, {A.t13, A.t23, A.t33}};
+        double bt[3];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) J[1 + d][0] = s_gu[d] * ir;
+        for (int f = 0; f < 3; ++f) bt[f] = Am[f][0] * dl[0] + Am[f][1] * dl[1] + Am[f][2] * dl[2];
+        double A2[3][3], bb2[3];
+#pragma unroll
+        for (int e1 = 0; e1 < 3; ++e1) {
+#pragma unroll
+            for (int e2 = 0; e2 < 3; ++e2)
+                A2[e1][e2] = Am[e1][0] * Am[0][e2] + Am[e1][1] * Am[1][e2] + Am[e1][2] * Am[2][e2];
+            bb2[e1] = Am[e1][0] * bt[0] + Am[e1][1] * bt[1] + Am[e1][2] * bt[2];
+        }
+        const double s0 = bt[0] * bt[0] + bt[1] * bt[1] + bt[2] * bt[2];
+        double V[3], Vd[3][3], VE[3], W0, Wd[3], WE;
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
-            J[0][1 + f] = s_gv[f];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) J[1 + d][1 + f] = s_guv[d][f];
-            J[4][1 + f] = s_gev[f] + eint * s_gv[f];
+            V[f] = Am[f][0] * Me[0] + Am[f][1] * Me[1] + Am[f][2] * Me[2] - bt[f] * M0;
         }
-        J[0][4] = k2 * (s_gvv - trA * s_g);
+        // second/third/fourth order moments by explicit exponent triples
+        double Mij[3][3];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) J[1 + d][4] = k2 * (s_guvv[d] - trA * s_gu[d]);
-        J[4][4] = k2 * ((s_gevv - trA * s_ge) + eint * (s_gvv - trA * s_g)) + hd * s_g;
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int e = 0; e < 3; ++e)
+                Mij[d][e] = M[midx((d == 0) + (e == 0), (d == 1) + (e == 1), (d == 2) + (e == 2))];
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int f = 0; f < 3; ++f)
+                Vd[d][f] = Am[f][0] * Mij[d][0] + Am[f][1] * Mij[d][1] + Am[f][2] * Mij[d][2] -
+                           bt[f] * Me[d];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            double acc = 0.0;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+#pragma unroll
+                for (int e = 0; e < 3; ++e)
+                    acc += Am[f][e] * M[midx(2 * (d == 0) + (e == 0), 2 * (d == 1) + (e == 1),
+                                             2 * (d == 2) + (e == 2))];
+                acc -= bt[f] * Mij[d][d];
+            }
+            VE[f] = 0.5 * acc;
+        }
+        W0 = s0 * M0;
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            W0 -= 2.0 * bb2[e] * Me[e];
+#pragma unroll
+            for (int e2 = 0; e2 < 3; ++e2) W0 += A2[e][e2] * Mij[e][e2];
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            double acc = s0 * Me[d];
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                acc -= 2.0 * bb2[e] * Mij[d][e];
+#pragma unroll
+                for (int e2 = 0; e2 < 3; ++e2)
+                    acc += A2[e][e2] * M[midx((d == 0) + (e == 0) + (e2 == 0), (d == 1) + (e == 1) + (e2 == 1),
+                                              (d == 2) + (e == 2) + (e2 == 2))];
+            }
+            Wd[d] = acc;
+        }
+        {
+            double acc = 0.0;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                acc += s0 * Mij[d][d];
+#pragma unroll
+                for (int e = 0; e < 3; ++e) {
+                    acc -= 2.0 * bb2[e] * M[midx(2 * (d == 0) + (e == 0), 2 * (d == 1) + (e == 1),
+                                                 2 * (d == 2) + (e == 2))];
+#pragma unroll
+                    for (int e2 = 0; e2 < 3; ++e2)
+                        acc += A2[e][e2] * M[midx(2 * (d == 0) + (e == 0) + (e2 == 0),
+                                                  2 * (d == 1) + (e == 1) + (e2 == 1),
+                                                  2 * (d == 2) + (e == 2) + (e2 == 2))];
+                }
+            }
+            WE = 0.5 * acc;
+        }
+        const double trA = A.t11 + A.t22 + A.t33;
+        const double k2 = 0.5 / gs.Pr;
+        const double ir = 1.0 / x[0];
+        const double cE = hU2 + eint;
+        double J[5][5];
+        // column rho'
+        J[0][0] = M0 * ir;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) J[1 + d][0] = fma(U0[d], M0, Me[d]) * ir;
+        J[4][0] = (Se + UMe + cE * M0) * ir;
+        // columns U'_f
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            J[0][1 + f] = V[f];
+            double UV = 0.0;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                J[1 + d][1 + f] = fma(U0[d], V[f], Vd[d][f]);
+                UV = fma(U0[d], Vd[d][f], UV);
+            }
+            J[4][1 + f] = VE[f] + UV + cE * V[f];
+        }
+        // column theta'
+        const double Z0 = W0 - trA * M0;
+        double Zd[3], UZ = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) { Zd[d] = Wd[d] - trA * Me[d]; UZ = fma(U0[d], Zd[d], UZ); }
+        const double ZE = WE - trA * Se;
+        J[0][4] = k2 * Z0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) J[1 + d][4] = k2 * fma(U0[d], Z0, Zd[d]);
+        J[4][4] = k2 * (ZE + UZ + cE * Z0) + hd * M0;
+#undef MM
         double dx[5] = {-R[0], -R[1], -R[2], -R[3], -R[4]};
         if (!solve5(J, dx)) break;
         bool finite = true;
@@ -309,112 +476,168 @@ __global__ void __launch_bounds__(256) k_qprime_f64(QPrimeArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Fused stage.  Per point (e, s) and velocity k, along each reference
-// direction d the 1-D FR derivative of the line through s is
-//   u_d sum_j D[i][j] f_j + u_d (f^+ - f^-) dg(xi_i)
-// where the jump is taken only at the inflow face (the upwind flux makes the
-// outflow jump zero): for u_d > 0 the left face (f^- = sum lm f, f^+ the
-// left neighbour's right trace, dg = g_L'), for u_d < 0 the right face
-// (f^- = sum lp f, f^+ the right neighbour's left trace, dg = g_R').
-// div = sum_d (2/h_d) (...).  R = -div + (g' - f)/tau.
+// Fused stage.  Along each reference direction d the 1-D FR derivative at
+// node i of the line through the thread's node is
+//   u_d [ sum_j D_ij f_j + (f^+ - f^-) dg(xi_i) ]
+// with the jump only at the inflow face (upwind: the outflow jump is zero).
+// With f^- = sum_j l_j f_j this is u_d [ sum_j Dt_ij f_j + dg_i f^+ ] where
+// Dt = D - dg (x) l is the derivative with the inflow trace folded in:
+// Dt_L = D - g_L' (x) l(-1) when u_d > 0, Dt_R = D - g_R' (x) l(+1) when
+// u_d < 0 (either when u_d = 0, whose contribution vanishes).  f^+ is the
+// neighbour's trace at the shared face (l(+1) of the left neighbour, l(-1)
+// of the right one) or the Dirichlet exterior value.
+// div = sum_d (2/h_d) u_d [...],  R = -div + (g' - f)/tau.
+// g' = exp(c0 - c^T A c / 2) is advanced along each first-axis velocity line
+// by the ratio recurrence (exact exp at the line start and wherever the
+// exponent is below -650, where the recurrence would underflow).
+// The block holds EB whole elements; their values for the current velocity
+// are staged in shared memory (double buffered, one barrier per velocity).
 template <int Q, int C>
 __global__ void __launch_bounds__(256) k_stage_f64(StageArgs<double> a) {
     constexpr int NS = Q * Q * Q;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= a.P) return;
+    constexpr int EB = 256 / NS;
+    constexpr int NT = EB * NS;
+    __shared__ double sf[2][C][NT];
+    __shared__ double sD[2][Q][Q];        // Dt_L, Dt_R
+    __shared__ double sdg[2][Q];          // g_L', g_R'
+    __shared__ double sl[2][Q];           // neighbour trace weights: l(+1) for left inflow, l(-1) for right
+    const int tid = threadIdx.x;
+    if (tid < Q * Q) {
+        const int i = tid / Q, j = tid % Q;
+        sD[0][i][j] = a.fr.D[i][j] - a.fr.dgL[i] * a.fr.lm[j];
+        sD[1][i][j] = a.fr.D[i][j] - a.fr.dgR[i] * a.fr.lp[j];
+    }
+    if (tid < Q) {
+        sdg[0][tid] = a.fr.dgL[tid]; sdg[1][tid] = a.fr.dgR[tid];
+        sl[0][tid] = a.fr.lp[tid];   sl[1][tid] = a.fr.lm[tid];
+    }
+    const int e0 = blockIdx.x * EB;
+    const int le = tid / NS, s = tid - le * NS;
+    const int e = e0 + le;
+    const bool active = tid < NT && e < a.mesh.Ne;
+    const int p = e * NS + s;
     const int vb = blockIdx.y;
     const int k0 = vb * a.Kblk;
     const int k1 = min(a.Nu, k0 + a.Kblk);
-    const int e = p / NS, s = p - e * NS;
     const int id[3] = {s % Q, (s / Q) % Q, s / (Q * Q)};
     const int stride[3] = {1, Q, Q * Q};
     const int n1 = a.mesh.n[0], n2 = a.mesh.n[1], n3 = a.mesh.n[2];
     const int ec[3] = {e % n1, (e / n1) % n2, e / (n1 * n2)};
     const int estr[3] = {1, n1, n1 * n2};
     const int nn[3] = {n1, n2, n3};
-    int eL[3], eR[3], base[3];
+    int en_[3][2], base[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        eL[d] = ec[d] > 0 ? e - estr[d] : (a.mesh.periodic[d] ? e + (nn[d] - 1) * estr[d] : -1);
-        eR[d] = ec[d] < nn[d] - 1 ? e + estr[d] : (a.mesh.periodic[d] ? e - (nn[d] - 1) * estr[d] : -1);
+        en_[d][0] = ec[d] > 0 ? e - estr[d] : (a.mesh.periodic[d] ? e + (nn[d] - 1) * estr[d] : -1);
+        en_[d][1] = ec[d] < nn[d] - 1 ? e + estr[d] : (a.mesh.periodic[d] ? e - (nn[d] - 1) * estr[d] : -1);
         base[d] = s - id[d] * stride[d];
     }
-    const double *q = a.eq + (size_t)p * BGK_NEQ;
-    const double c0 = q[0], V1 = q[1], V2 = q[2], V3 = q[3];
-    const double A11 = q[4], A22 = q[5], A33 = q[6], A12 = q[7], A13 = q[8], A23 = q[9];
-    const double itau = q[10], gfac = q[11];
+    double c0 = 0, V1 = 0, V2 = 0, V3 = 0, A11 = 1, A22 = 1, A33 = 1, A12 = 0, A13 = 0, A23 = 0;
+    double itau = 0, gfac = 0;
+    if (active) {
+        const double *q = a.eq + (size_t)p * BGK_NEQ;
+        c0 = q[0]; V1 = q[1]; V2 = q[2]; V3 = q[3];
+        A11 = q[4]; A22 = q[5]; A33 = q[6]; A12 = q[7]; A13 = q[8]; A23 = q[9];
+        itau = q[10]; gfac = q[11];
+    }
+    const double h1 = a.vg.h[0];
+    const double ah = -0.5 * A11 * h1 * h1;              // q(j) = q0 + j D0 + ah j (j - 1)
+    const double rho1 = exp(2.0 * ah);
+    const int vn1 = a.vg.n[0];
     double m[BGK_NMOM];
 #pragma unroll
     for (int j = 0; j < BGK_NMOM; ++j) m[j] = 0.0;
     const size_t slab = (size_t)a.P;
+    __syncthreads();
 
-    for (int k = k0; k < k1; ++k) {
-        const double *vt = a.vtab + (size_t)k * BGK_VTAB;
-        const double u[3] = {__ldg(vt + 0), __ldg(vt + 1), __ldg(vt + 2)};
-        const double w = __ldg(vt + 3);
-        const double c1 = u[0] - V1, c2 = u[1] - V2, c3 = u[2] - V3;
-        const double qf = 0.5 * (A11 * c1 * c1 + A22 * c2 * c2 + A33 * c3 * c3) +
-                          (A12 * c1 * c2 + A13 * c1 * c3 + A23 * c2 * c3);
-        const double g = exp(c0 - qf);
-        double outv[C];
+    int buf = 0;
+    for (int kl = k0; kl < k1; kl += vn1) {           // one first-axis velocity line
+        const double *vl = a.vtab + (size_t)kl * BGK_VTAB;
+        const double u2 = __ldg(vl + 1), u3 = __ldg(vl + 2);
+        const double c1_0 = __ldg(vl + 0) - V1, c2 = u2 - V2, c3 = u3 - V3;
+        const double lin = A12 * c2 + A13 * c3;
+        const double cst = A22 * c2 * c2 + 2.0 * A23 * c2 * c3 + A33 * c3 * c3;
+        const double q0 = c0 - 0.5 * (A11 * c1_0 * c1_0 + 2.0 * c1_0 * lin + cst);
+        const double D0 = -h1 * (A11 * (c1_0 + 0.5 * h1) + lin);
+        const float q0f = (float)q0, D0f = (float)D0, ahf = (float)ah;
+        double g = 0.0, r = 0.0;
+        bool rec = false;
+        double T0 = 0, T1 = 0, T2 = 0, TG = 0;
+        for (int j1 = 0; j1 < vn1; ++j1) {
+            const int k = kl + j1;
+            const double *vt = a.vtab + (size_t)k * BGK_VTAB;
+            double fself[C];
+            if (active) {
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-            const double *fs = a.f_s + ((size_t)c * a.Nu + k) * slab;
-            const double fself = __ldg(fs + p);
-            double div = 0.0;
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const double ud = u[d];
-                const double *own = fs + (size_t)e * NS + base[d];
-                double line[Q];
-#pragma unroll
-                for (int j = 0; j < Q; ++j) line[j] = __ldg(own + j * stride[d]);
-                double dfd = 0.0;
-#pragma unroll
-                for (int j = 0; j < Q; ++j) dfd = fma(a.fr.D[id[d]][j], line[j], dfd);
-                double corr = 0.0;
-                if (ud != 0.0) {
-                    const bool left = ud > 0.0;
-                    const int en = left ? eL[d] : eR[d];
-                    double fm = 0.0, fp = 0.0;
-#pragma unroll
-                    for (int j = 0; j < Q; ++j) fm = fma(left ? a.fr.lm[j] : a.fr.lp[j], line[j], fm);
-                    if (en >= 0) {
-                        const double *nb = fs + (size_t)en * NS + base[d];
-#pragma unroll
-                        for (int j = 0; j < Q; ++j)
-                            fp = fma(left ? a.fr.lp[j] : a.fr.lm[j], __ldg(nb + j * stride[d]), fp);
-                    } else {
-                        const int face = 2 * d + (left ? 0 : 1);
-                        fp = __ldg(a.bcval + ((size_t)face * C + c) * a.Nu + k);
-                    }
-                    corr = (fp - fm) * (left ? a.fr.dgL[id[d]] : a.fr.dgR[id[d]]);
+                for (int c = 0; c < C; ++c) {
+                    fself[c] = __ldg(a.f_s + ((size_t)c * a.Nu + k) * slab + p);
+                    sf[buf][c][tid] = fself[c];
                 }
-                div = fma(a.mesh.two_over_h[d] * ud, dfd + corr, div);
             }
-            const double eqv = (c == 0) ? g : gfac * g;
-            const double R = fma(eqv - fself, itau, -div);
-            double out = fma(a.c, R, a.b * fself);
-            if (a.a != 0.0) out = fma(a.a, __ldg(a.f_n + ((size_t)c * a.Nu + k) * slab + p), out);
-            a.f_out[((size_t)c * a.Nu + k) * slab + p] = out;
-            outv[c] = out;
+            // equilibrium value at this velocity
+            const float qf = q0f + (float)j1 * (D0f + ahf * (float)(j1 - 1));
+            if (qf < -650.0f) {
+                g = exp(q0 + j1 * (D0 + ah * (j1 - 1)));
+                rec = false;
+            } else if (!rec) {
+                g = exp(q0 + j1 * (D0 + ah * (j1 - 1)));
+                r = exp(fmin(D0 + 2.0 * ah * j1, 700.0));
+                rec = true;
+            }
+            __syncthreads();
+            if (active) {
+                const double u[3] = {__ldg(vt + 0), u2, u3};
+                double outv[C];
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const double *fs = a.f_s + ((size_t)c * a.Nu + k) * slab;
+                    const double *sfc = sf[buf][c];
+                    double div = 0.0;
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        const int side = u[d] > 0.0 ? 0 : 1;
+                        const double *own = sfc + le * NS + base[d];
+                        double t = 0.0;
+#pragma unroll
+                        for (int j = 0; j < Q; ++j) t = fma(sD[side][id[d]][j], own[j * stride[d]], t);
+                        const int en = en_[d][side];
+                        double fp = 0.0;
+                        if (en >= e0 && en < e0 + EB) {
+                            const double *nb = sfc + (en - e0) * NS + base[d];
+#pragma unroll
+                            for (int j = 0; j < Q; ++j) fp = fma(sl[side][j], nb[j * stride[d]], fp);
+                        } else if (en >= 0) {
+                            const double *nb = fs + (size_t)en * NS + base[d];
+#pragma unroll
+                            for (int j = 0; j < Q; ++j) fp = fma(sl[side][j], __ldg(nb + j * stride[d]), fp);
+                        } else {
+                            fp = __ldg(a.bcval + ((size_t)(2 * d + side) * C + c) * a.Nu + k);
+                        }
+                        t = fma(sdg[side][id[d]], fp, t);
+                        div = fma(a.mesh.two_over_h[d] * u[d], t, div);
+                    }
+                    const double eqv = (c == 0) ? g : gfac * g;
+                    const double R = fma(eqv - fself[c], itau, -div);
+                    double out = fma(a.c, R, a.b * fself[c]);
+                    if (a.a != 0.0) out = fma(a.a, __ldg(a.f_n + ((size_t)c * a.Nu + k) * slab + p), out);
+                    a.f_out[((size_t)c * a.Nu + k) * slab + p] = out;
+                    outv[c] = out;
+                }
+                T0 = fma(__ldg(vt + 3), outv[0], T0);
+                T1 = fma(__ldg(vt + 5), outv[0], T1);
+                T2 = fma(__ldg(vt + 6), outv[0], T2);
+                if (C == 2) TG = fma(__ldg(vt + 3), outv[C - 1], TG);
+            }
+            if (rec) { g *= r; r *= rho1; }
+            buf ^= 1;
         }
-        if (a.part) {
-            const double wF = w * outv[0];
-            m[0] += wF;
-            m[1] = fma(wF, u[0], m[1]);
-            m[2] = fma(wF, u[1], m[2]);
-            m[3] = fma(wF, u[2], m[3]);
-            m[4] = fma(wF * u[0], u[0], m[4]);
-            m[5] = fma(wF * u[1], u[1], m[5]);
-            m[6] = fma(wF * u[2], u[2], m[6]);
-            m[7] = fma(wF * u[0], u[1], m[7]);
-            m[8] = fma(wF * u[0], u[2], m[8]);
-            m[9] = fma(wF * u[1], u[2], m[9]);
-            if (C == 2) m[10] = fma(w, outv[C - 1], m[10]);
-        }
+        // fold the line sums: T_m = sum_j w u1^m F over the line
+        m[0] += T0; m[1] += T1; m[2] = fma(u2, T0, m[2]); m[3] = fma(u3, T0, m[3]);
+        m[4] += T2; m[5] = fma(u2 * u2, T0, m[5]); m[6] = fma(u3 * u3, T0, m[6]);
+        m[7] = fma(u2, T1, m[7]); m[8] = fma(u3, T1, m[8]); m[9] = fma(u2 * u3, T0, m[9]);
+        m[10] += TG;
     }
-    if (a.part) {
+    if (a.part && active) {
 #pragma unroll
         for (int j = 0; j < BGK_NMOM; ++j) a.part[((size_t)vb * BGK_NMOM + j) * a.P + p] = m[j];
     }
@@ -450,25 +673,25 @@ cudaError_t launch_reduce_moments(const double *part, int n_vblk, int P, double 
 }
 
 cudaError_t launch_qprime_f64(const QPrimeArgs &a, cudaStream_t s) {
-    const long long threads = (long long)a.P * 32;
-    k_qprime_f64<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a);
+    k_qprime_f64<<<(unsigned)((a.P + 7) / 8), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int Q>
-static cudaError_t stage_q(const StageArgs<double> &a, int C, dim3 grid, cudaStream_t s) {
-    if (C == 1) k_stage_f64<Q, 1><<<grid, 256, 0, s>>>(a);
-    else k_stage_f64<Q, 2><<<grid, 256, 0, s>>>(a);
+static cudaError_t stage_q(const StageArgs<double> &a, int C, int n_vblk, cudaStream_t s) {
+    constexpr int NS = Q * Q * Q, EB = 256 / NS;
+    dim3 grid((a.mesh.Ne + EB - 1) / EB, n_vblk);
+    if (C == 1) k_stage_f64<Q, 1><<<grid, EB * NS, 0, s>>>(a);
+    else k_stage_f64<Q, 2><<<grid, EB * NS, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_stage_f64(const StageArgs<double> &a, int C, int n_vblk, cudaStream_t s) {
-    dim3 grid((a.P + 255) / 256, n_vblk);
     switch (a.fr.q) {
-        case 2: return stage_q<2>(a, C, grid, s);
-        case 3: return stage_q<3>(a, C, grid, s);
-        case 4: return stage_q<4>(a, C, grid, s);
-        case 5: return stage_q<5>(a, C, grid, s);
+        case 2: return stage_q<2>(a, C, n_vblk, s);
+        case 3: return stage_q<3>(a, C, n_vblk, s);
+        case 4: return stage_q<4>(a, C, n_vblk, s);
+        case 5: return stage_q<5>(a, C, n_vblk, s);
         default: return cudaErrorInvalidValue;
     }
 }
