@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--forms", default="fp64")
+    ap.add_argument("--forms", default="fp64,mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--workload", default="taylor_green", choices=sorted(WORKLOADS))
@@ -180,6 +180,7 @@ def run_ours(args, rank, world, dev):
             s.step(dt, 1)
         torch.cuda.synchronize()
         s.stats()
+        tot0 = s.totals()
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
@@ -200,6 +201,9 @@ def run_ours(args, rank, world, dev):
         prof = s.profile_read()
         mean_it, max_it, res = s.stats()
         s.profile(False)
+        tot1 = s.totals()
+        scale = np.array([tot0[0]] * 4 + [tot0[4]])
+        drift = float(np.max(np.abs(tot1 - tot0) / scale)) / args.steps
         if world > 1:
             t = torch.tensor([ms], device=dev)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -224,10 +228,25 @@ def run_ours(args, rank, world, dev):
             del host
         results[form] = dict(ms=ms, status=bgk.STATUS_NAMES[st], prof=prof, clocks=ck,
                              newton=dict(mean_iters=mean_it, max_iters=max_it, max_residual=res),
-                             e2e=e2e)
+                             e2e=e2e, drift=drift)
         s.destroy()
         torch.cuda.empty_cache()
     return wl, results, peaks
+
+
+def stage_bytes_per_dof(C, elem):
+    """Algorithmic HBM bytes per DOF of one stage, averaged over the three
+    SSP-RK3 stages: read f_s and write f_out (stage 1), plus read f^n (2, 3)."""
+    return C * elem * (2 + 3 + 3) / 3.0
+
+
+def roofline_stage_hbm(wl, r, peaks, elem):
+    ms, n = r["prof"]["stage"]
+    per = ms / max(n, 1)
+    bytes_ = wl.dof * stage_bytes_per_dof(wl.n_comp, elem)
+    achieved = bytes_ / (per * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": "stage", "achieved": achieved, "peak": peaks["hbm_gbs"],
+            "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None, "ms": per}
 
 
 def roofline_fp64(wl, r, peaks, steps):
@@ -250,6 +269,15 @@ def roofline_fp64(wl, r, peaks, steps):
             "peak_source": "measured FP64 FMA throughput (bgk_probe_peak) on this GPU",
             "other": {k: {"tflops": cand[k][0] / (cand[k][1] * 1e-3) / 1e12, "ms": cand[k][1]}
                       for k in cand}}
+
+
+def _measured_hbm():
+    """HBM copy bandwidth of this GPU pool (MEASURED_PEAKS.json, driver-written),
+    else the profiling recipe's fallback figure."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
 
 
 def main():
@@ -292,7 +320,8 @@ def main():
     wl, results, peaks = run_ours(args, rank, world, dev)
     if rank != 0:
         return
-    main_form = "fp64" if "fp64" in results else list(results)[0]
+    main_form = "mixed" if "mixed" in results else list(results)[0]
+    peaks["hbm_gbs"] = _measured_hbm()
     r = results[main_form]
     ms_per_step = r["ms"] / args.steps
     value = world * wl.dof * 3 * args.steps / (r["ms"] * 1e-3)
@@ -308,20 +337,25 @@ def main():
                          (wl.dof * (8 if main_form == "fp64" else 4) / 1e9)},
         "clocks": r["clocks"],
         "e2e": r["e2e"],
+        "conservation_drift_per_step": r["drift"],
         "gpu_launches": launches,
         "kernels_ms": {k: v[0] for k, v in r["prof"].items()},
         "newton": r["newton"],
         "status": r["status"],
         "peaks_measured": peaks,
     }
-    if main_form == "fp64":
-        line["roofline"] = roofline_fp64(wl, r, peaks, args.steps)
+    line["roofline"] = roofline_fp64(wl, r, peaks, args.steps)
+    if main_form == "mixed":
+        line["roofline_stage_kernel"] = roofline_stage_hbm(wl, r, peaks, 4)
     for form, rr in results.items():
         if form != main_form:
             line[form] = {"value": world * wl.dof * 3 * args.steps / (rr["ms"] * 1e-3),
                           "ms_per_step": rr["ms"] / args.steps,
                           "kernels_ms": {k: v[0] for k, v in rr["prof"].items()},
-                          "newton": rr["newton"], "e2e": rr["e2e"]}
+                          "newton": rr["newton"], "e2e": rr["e2e"],
+                          "conservation_drift_per_step": rr["drift"],
+                          "roofline": roofline_fp64(wl, rr, peaks, args.steps),
+                          "clocks": rr["clocks"]}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line))

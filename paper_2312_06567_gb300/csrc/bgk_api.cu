@@ -194,10 +194,14 @@ bgk_status check_device_status(bgk_ctx *ctx) {
 }
 
 bgk_status run_moments(bgk_ctx *ctx, const void *f) {
-    if (ctx->precision != BGK_FP64) return fail(ctx, BGK_ENOTSUP, "mixed precision not built");
-    MomentArgs64 a{(const double *)f, ctx->part, ctx->vtab, ctx->Nu, ctx->P, ctx->Kblk, ctx->C};
     LaunchScope ls(ctx, BGK_K_MOMENTS);
-    CU(launch_moments_f64(a, ctx->n_vblk, ctx->stream));
+    if (ctx->precision == BGK_FP64) {
+        MomentArgs64 a{(const double *)f, ctx->part, ctx->vtab, ctx->Nu, ctx->P, ctx->Kblk, ctx->C};
+        CU(launch_moments_f64(a, ctx->n_vblk, ctx->stream));
+    } else {
+        CU(launch_moments_f32((const float *)f, ctx->part, ctx->vtab, ctx->Nu, ctx->P, ctx->Kblk,
+                              ctx->C, ctx->n_vblk, ctx->stream));
+    }
     return BGK_OK;
 }
 
@@ -207,21 +211,32 @@ bgk_status run_qprime(bgk_ctx *ctx, const double *part, int n_vblk, int P, doubl
     a.part = part; a.n_vblk = n_vblk; a.vtab = ctx->vtab; a.guess = guess; a.eq = eq; a.qp = qp;
     a.iters = iters; a.status = ctx->status; a.stats = ctx->stats; a.P = P; a.Nu = ctx->Nu;
     a.tol = ctx->tol; a.max_iter = ctx->max_iter; a.gas = ctx->gas; a.vg = ctx->vg;
+    a.mixed = ctx->precision == BGK_MIXED ? 1 : 0;
     LaunchScope ls(ctx, BGK_K_QPRIME);
     CU(launch_qprime_f64(a, ctx->stream));
     return BGK_OK;
 }
 
-bgk_status run_stage(bgk_ctx *ctx, const void *fn, const void *fs, void *fo, double a, double b,
-                     double c, bool moments) {
-    if (ctx->precision != BGK_FP64) return fail(ctx, BGK_ENOTSUP, "mixed precision not built");
-    StageArgs<double> s{};
-    s.f_n = (const double *)fn; s.f_s = (const double *)fs; s.f_out = (double *)fo;
+template <typename T>
+StageArgs<T> stage_args(bgk_ctx *ctx, const void *fn, const void *fs, void *fo, double a, double b,
+                        double c, bool moments) {
+    StageArgs<T> s{};
+    s.f_n = (const T *)fn; s.f_s = (const T *)fs; s.f_out = (T *)fo;
     s.eq = ctx->eq; s.vtab = ctx->vtab; s.bcval = ctx->bcval; s.part = moments ? ctx->part : nullptr;
     s.a = a; s.b = b; s.c = c; s.Nu = ctx->Nu; s.P = ctx->P; s.Kblk = ctx->Kblk;
     s.vg = ctx->vg; s.fr = ctx->fr; s.mesh = ctx->mesh;
+    return s;
+}
+
+bgk_status run_stage(bgk_ctx *ctx, const void *fn, const void *fs, void *fo, double a, double b,
+                     double c, bool moments) {
     LaunchScope ls(ctx, BGK_K_STAGE);
-    CU(launch_stage_f64(s, ctx->C, ctx->n_vblk, ctx->stream));
+    if (ctx->precision == BGK_FP64)
+        CU(launch_stage_f64(stage_args<double>(ctx, fn, fs, fo, a, b, c, moments), ctx->C, ctx->n_vblk,
+                            ctx->stream));
+    else
+        CU(launch_stage_f32(stage_args<float>(ctx, fn, fs, fo, a, b, c, moments), ctx->C, ctx->n_vblk,
+                            ctx->stream));
     return BGK_OK;
 }
 
@@ -442,7 +457,6 @@ bgk_status bgk_get_state(bgk_ctx *ctx, void *f, int on_device) {
 
 bgk_status bgk_set_maxwellian(bgk_ctx *ctx, const double *q, int on_device) {
     if (!ctx || !q) return BGK_EINVAL;
-    if (ctx->precision != BGK_FP64) return fail(ctx, BGK_ENOTSUP, "mixed precision not built");
     const double *dq = q;
     double *tmp = nullptr;
     if (!on_device) {
@@ -452,8 +466,12 @@ bgk_status bgk_set_maxwellian(bgk_ctx *ctx, const double *q, int on_device) {
     }
     {
         LaunchScope ls(ctx, BGK_K_OTHER);
-        CU(launch_maxwellian_f64((double *)ctx->f[0], dq, ctx->vtab, ctx->Nu, ctx->P, ctx->C,
-                                 ctx->gas.delta, ctx->stream));
+        if (ctx->precision == BGK_FP64)
+            CU(launch_maxwellian_f64((double *)ctx->f[0], dq, ctx->vtab, ctx->Nu, ctx->P, ctx->C,
+                                     ctx->gas.delta, ctx->stream));
+        else
+            CU(launch_maxwellian_f32((float *)ctx->f[0], dq, ctx->vtab, ctx->Nu, ctx->P, ctx->C,
+                                     ctx->gas.delta, ctx->stream));
     }
     if (tmp) CU(cudaFreeAsync(tmp, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));

@@ -9,7 +9,7 @@
 
 #define BGK_MAXQ 5          // FR order p <= 4
 #define BGK_NMOM 11         // raw moment slots per point
-#define BGK_NEQ 12          // equilibrium record per point
+#define BGK_NEQ 20          // equilibrium record per point (12 used by the FP64 form)
 #define BGK_VTAB 8          // velocity table record: u1 u2 u3 w e=|u|^2/2 w*u1 w*u1^2 (1 pad)
 #define BGK_MAXV 128        // nodes per velocity axis at most
 
@@ -42,6 +42,33 @@ struct VelGrid {
 
 struct GasInfo {
     double delta, Pr, mu_ref, theta_ref, theta_S, gamma;
+};
+
+// FP32 equilibrium exactly as the mixed-form stage evaluates it:
+// g32(u) = E0 * exp2(L), L = -log2(e)/2 c^T A c, c = u - V, all in FP32 with
+// every product rounded explicitly (no contraction), so the Q' kernel can
+// reproduce the stage's values bit for bit when it measures their moments.
+struct Eq32 {
+    float E0, V1, V2, V3, A11, A22, A33, A12, A13, A23;   // A pre-scaled by -log2(e)/2 (x2 off-diagonal)
+    __device__ __forceinline__ void load(const double *q) {
+        const float s2 = -0.72134752044448170f;            // -log2(e)/2
+        E0 = (float)exp(q[0]);
+        V1 = (float)q[1]; V2 = (float)q[2]; V3 = (float)q[3];
+        A11 = __fmul_rn((float)q[4], s2); A22 = __fmul_rn((float)q[5], s2);
+        A33 = __fmul_rn((float)q[6], s2);
+        A12 = __fmul_rn((float)q[7], 2.f * s2); A13 = __fmul_rn((float)q[8], 2.f * s2);
+        A23 = __fmul_rn((float)q[9], 2.f * s2);
+    }
+    // per first-axis line: the coefficient of c1 and the constant part
+    __device__ __forceinline__ void line(float u2, float u3, float &lin, float &cst) const {
+        const float c2 = __fsub_rn(u2, V2), c3 = __fsub_rn(u3, V3);
+        lin = fmaf(A12, c2, __fmul_rn(A13, c3));
+        cst = fmaf(__fmul_rn(A22, c2), c2, fmaf(__fmul_rn(A23, c2), c3, __fmul_rn(__fmul_rn(A33, c3), c3)));
+    }
+    __device__ __forceinline__ float g(float u1, float lin, float cst) const {
+        const float c1 = __fsub_rn(u1, V1);
+        return __fmul_rn(E0, exp2f(fmaf(c1, fmaf(A11, c1, lin), cst)));
+    }
 };
 
 // Newton statistics accumulated on the device.
@@ -85,6 +112,7 @@ struct QPrimeArgs {
     int max_iter;
     GasInfo gas;
     VelGrid vg;
+    int mixed;               // also fit the FP32-equilibrium moment correction
 };
 
 struct MomentArgs64 {
@@ -100,5 +128,10 @@ cudaError_t launch_qprime_f64(const QPrimeArgs &a, cudaStream_t s);
 cudaError_t launch_stage_f64(const StageArgs<double> &a, int C, int n_vblk, cudaStream_t s);
 cudaError_t launch_maxwellian_f64(double *f, const double *q, const double *vtab, int Nu, int P,
                                   int C, double delta, cudaStream_t s);
+cudaError_t launch_moments_f32(const float *f, double *part, const double *vtab, int Nu, int P,
+                               int Kblk, int C, int n_vblk, cudaStream_t s);
+cudaError_t launch_stage_f32(const StageArgs<float> &a, int C, int n_vblk, cudaStream_t s);
+cudaError_t launch_maxwellian_f32(float *f, const double *q, const double *vtab, int Nu, int P, int C,
+                                  double delta, cudaStream_t s);
 cudaError_t launch_reduce_moments(const double *part, int n_vblk, int P, double *m_out,
                                   cudaStream_t s);

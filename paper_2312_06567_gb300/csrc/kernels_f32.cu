@@ -1,0 +1,408 @@
+// Mixed-precision (BGK_MIXED) kernels: the state f is FP32 and the FR
+// advection, equilibrium evaluation, source and Runge--Kutta update run in
+// FP32; the moments that feed the Q' solve are accumulated so that their
+// error stays random (unbiased) and far below FP32 resolution, and the Q'
+// solve itself runs in FP64 (the k_qprime_f64 kernel, shared with the FP64
+// form).  Dzanic & Martinelli, arXiv 2312.06567, section "Methodology".
+//
+// Moment accumulation without systematic error: with centred velocity
+// indices jt = j - jc on each axis (u = uc + jt h) and trapezoid factors
+// c in {1/2, 1}, every coefficient c jt^a (|jt| < 64, a <= 2) is exact in
+// FP32.  Along each first-axis line the sums L_a = sum c1 jt1^a F are FP32
+// (a few tens of terms), the lines of one (j3 = const) plane are combined
+// with exact coefficients c2 jt2^b in Kahan-compensated FP32, and the planes
+// in FP64; the index moments J_abc = sum c F jt1^a jt2^b jt3^c are turned
+// into the raw moments sum w u^alpha F in FP64 at the end.
+#include "bgk_internal.cuh"
+
+namespace {
+
+// Kahan step; the represented sum is s - comp.
+__device__ __forceinline__ void kahan_add(float &s, float &comp, float v) {
+    const float y = __fsub_rn(v, comp);
+    const float t = __fadd_rn(s, y);
+    comp = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
+// Index moments (J000, J100, J200, J010, J110, J020, J001, J101, J011, J002, JG)
+// of one thread -> the 11 raw moment slots, W = h1 h2 h3.
+__device__ __forceinline__ void index_to_raw(const double J[11], const VelGrid &vg, const double uc[3],
+                                             double m[BGK_NMOM]) {
+    const double W = vg.h[0] * vg.h[1] * vg.h[2];
+    const double h1 = vg.h[0], h2 = vg.h[1], h3 = vg.h[2];
+    const double J000 = J[0], J100 = J[1], J200 = J[2], J010 = J[3], J110 = J[4], J020 = J[5];
+    const double J001 = J[6], J101 = J[7], J011 = J[8], J002 = J[9];
+    m[0] = W * J000;
+    m[1] = W * (uc[0] * J000 + h1 * J100);
+    m[2] = W * (uc[1] * J000 + h2 * J010);
+    m[3] = W * (uc[2] * J000 + h3 * J001);
+    m[4] = W * (uc[0] * uc[0] * J000 + 2.0 * uc[0] * h1 * J100 + h1 * h1 * J200);
+    m[5] = W * (uc[1] * uc[1] * J000 + 2.0 * uc[1] * h2 * J010 + h2 * h2 * J020);
+    m[6] = W * (uc[2] * uc[2] * J000 + 2.0 * uc[2] * h3 * J001 + h3 * h3 * J002);
+    m[7] = W * (uc[0] * uc[1] * J000 + uc[0] * h2 * J010 + h1 * uc[1] * J100 + h1 * h2 * J110);
+    m[8] = W * (uc[0] * uc[2] * J000 + uc[0] * h3 * J001 + h1 * uc[2] * J100 + h1 * h3 * J101);
+    m[9] = W * (uc[1] * uc[2] * J000 + uc[1] * h3 * J001 + h2 * uc[2] * J010 + h2 * h3 * J011);
+    m[10] = W * J[10];
+}
+
+// Dt[side] = D - dg (x) l rounded to FP32 with explicit roundings, so every
+// use (the operator itself and the conservation weights built from it) sees
+// the same FP32 entries.
+__device__ __forceinline__ float folded_dt(const FROps &fr, int side, int i, int j) {
+    const double dg = side == 0 ? fr.dgL[i] : fr.dgR[i];
+    const double l = side == 0 ? fr.lm[j] : fr.lp[j];
+    return __double2float_rn(__dsub_rn(fr.D[i][j], __dmul_rn(dg, l)));
+}
+
+__device__ __forceinline__ float trap(int j, int n) { return (j == 0 || j == n - 1) ? 0.5f : 1.0f; }
+
+// Per-thread accumulator of index moments over a run of whole first-axis lines.
+// Line sums are Kahan sums of exact products (c F exact; c F jt and c F jt^2
+// split into product + FMA-exact error), their compensations kept; plane
+// sums are Kahan sums of the lines' (sum, compensation) pairs; planes fold in
+// FP64.  So the index moments carry FP32 rounding noise only far below
+// 2^-24 of the sums, and no bias.
+struct IndexMoments {
+    float L[4], Lc[4];                    // current line: 0, jt, jt^2, G (Kahan pairs)
+    float P[7], Pc[7];                    // current plane (Kahan): 00 10 20 01 11 02 G
+    double J[11];
+    int j3cur;
+    __device__ void init() {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) L[i] = Lc[i] = 0.f;
+#pragma unroll
+        for (int i = 0; i < 7; ++i) P[i] = Pc[i] = 0.f;
+#pragma unroll
+        for (int i = 0; i < 11; ++i) J[i] = 0.0;
+        j3cur = -1;
+    }
+    __device__ __forceinline__ void add(float cj1, float jt1, float F, float G) {
+        const float cF = __fmul_rn(cj1, F);                 // exact: cj1 in {1/2, 1}
+        kahan_add(L[0], Lc[0], cF);
+        const float p1 = __fmul_rn(cF, jt1);
+        kahan_add(L[1], Lc[1], p1);
+        Lc[1] = __fsub_rn(Lc[1], fmaf(cF, jt1, -p1));       // exact product error joins the compensation
+        const float jj = __fmul_rn(jt1, jt1);               // exact: |jt1| < 128
+        const float p2 = __fmul_rn(cF, jj);
+        kahan_add(L[2], Lc[2], p2);
+        Lc[2] = __fsub_rn(Lc[2], fmaf(cF, jj, -p2));
+        kahan_add(L[3], Lc[3], __fmul_rn(cj1, G));
+    }
+    __device__ __forceinline__ void flush_plane(float c3, float jt3) {
+        const double c = c3, t = jt3;
+        // Kahan: the compensated plane sum is P - Pc
+        const double P00 = (double)P[0] - (double)Pc[0], P10 = (double)P[1] - (double)Pc[1];
+        const double P20 = (double)P[2] - (double)Pc[2], P01 = (double)P[3] - (double)Pc[3];
+        const double P11 = (double)P[4] - (double)Pc[4], P02 = (double)P[5] - (double)Pc[5];
+        const double PG = (double)P[6] - (double)Pc[6];
+        // J_abc += c3 jt3^c P_ab
+        J[0] = fma(c, P00, J[0]);
+        J[1] = fma(c, P10, J[1]);
+        J[2] = fma(c, P20, J[2]);
+        J[3] = fma(c, P01, J[3]);
+        J[4] = fma(c, P11, J[4]);
+        J[5] = fma(c, P02, J[5]);
+        J[6] = fma(c * t, P00, J[6]);
+        J[7] = fma(c * t, P10, J[7]);
+        J[8] = fma(c * t, P01, J[8]);
+        J[9] = fma(c * t * t, P00, J[9]);
+        J[10] = fma(c, PG, J[10]);
+#pragma unroll
+        for (int i = 0; i < 7; ++i) P[i] = Pc[i] = 0.f;
+    }
+    // add c * (s - comp) of a line pair into a plane Kahan pair, exactly up to
+    // the plane sum's own rounding (c is a small integer or half-integer)
+    __device__ __forceinline__ void plane_add(int i, float c, float sum, float comp) {
+        const float ps = __fmul_rn(c, sum);
+        kahan_add(P[i], Pc[i], ps);
+        Pc[i] = __fsub_rn(Pc[i], fmaf(c, sum, -ps));
+        const float pc = __fmul_rn(c, comp);
+        kahan_add(P[i], Pc[i], -pc);
+    }
+    __device__ __forceinline__ void end_line(float c2, float jt2) {
+        const float a = c2, b = __fmul_rn(c2, jt2), bb = __fmul_rn(__fmul_rn(c2, jt2), jt2);   // exact
+        plane_add(0, a, L[0], Lc[0]);
+        plane_add(1, a, L[1], Lc[1]);
+        plane_add(2, a, L[2], Lc[2]);
+        plane_add(3, b, L[0], Lc[0]);
+        plane_add(4, b, L[1], Lc[1]);
+        plane_add(5, bb, L[0], Lc[0]);
+        plane_add(6, a, L[3], Lc[3]);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) L[i] = Lc[i] = 0.f;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Fused stage, FP32 state.  Same discretisation as the FP64 stage kernel:
+// per direction t_d = sum_j Dt[side][i][j] f_j + dg[side][i] f^+ with the
+// inflow trace folded into Dt; div = sum_d (2/h_d) u_d t_d;
+// R = -div + (g' - f)/tau.  g' = exp(c0) * exp2(-log2(e)/2 c^T A c) with the
+// per-point factor exp(c0) from FP64 and the exponent in FP32.
+template <int Q, int C>
+__global__ void __launch_bounds__(256) k_stage_f32(StageArgs<float> a) {
+    constexpr int NS = Q * Q * Q;
+    constexpr int EB = 256 / NS;
+    constexpr int NT = EB * NS;
+    __shared__ float sf[2][C][NT];
+    __shared__ float sD[2][Q][Q];         // Dt = D - dg (x) l, FP32
+    __shared__ float sdg[2][Q];           // dg (FP32)
+    __shared__ float seps[2][Q];          // eps_i = sum_j Dt_ij + dg_i  (exact defect, tiny)
+    __shared__ float slam[2][Q];          // neighbour-trace weights lambda_j
+    __shared__ float sdlam[2];            // sum_j lambda_j - 1 (exact defect, tiny)
+    const int tid = threadIdx.x;
+    // Operators and the deviation form.  With f_i the thread's own value,
+    //   t_i = sum_j Dt_ij (f_j - f_i) + dg_i dn + eps_i f_i,
+    //   dn  = sum_j lambda_j (nb_j - f_i) + dlam f_i   (= f^+ - f_i),
+    // equals sum_j Dt_ij f_j + dg_i f^+ in exact arithmetic.  Every product
+    // with an O(1) coefficient acts on a deviation, so FP32 cancellation error
+    // no longer repeats coherently across velocities and elements; lambda_j
+    // = +-sum_i W_i Dt_ij (side L: the left neighbour's right trace, side R:
+    // the right neighbour's left trace) makes sum_i W_i t_i telescope between
+    // neighbours, which keeps the advection discretely conservative up to
+    // second-order rounding terms.
+    if (tid < Q * Q) {
+        const int i = tid / Q, j = tid % Q;
+        sD[0][i][j] = folded_dt(a.fr, 0, i, j);
+        sD[1][i][j] = folded_dt(a.fr, 1, i, j);
+    }
+    if (tid < 2 * Q) {
+        const int side = tid / Q, j = tid % Q;
+        double lam = 0.0, eps = side == 0 ? a.fr.dgL[j] : a.fr.dgR[j];
+        for (int i = 0; i < Q; ++i) {
+            lam = fma(a.fr.wq[i], (double)folded_dt(a.fr, side, i, j), lam);
+            eps += (double)folded_dt(a.fr, side, j, i);
+        }
+        slam[side][j] = (float)(side == 0 ? lam : -lam);
+        seps[side][j] = (float)eps;
+        sdg[side][j] = (float)(side == 0 ? a.fr.dgL[j] : a.fr.dgR[j]);
+        if (j == 0) {
+            double tot = 0.0;
+            for (int jj = 0; jj < Q; ++jj)
+                for (int i = 0; i < Q; ++i) tot = fma(a.fr.wq[i], (double)folded_dt(a.fr, side, i, jj), tot);
+            sdlam[side] = (float)((side == 0 ? tot : -tot) - 1.0);
+        }
+    }
+    const int e0 = blockIdx.x * EB;
+    const int le = tid / NS, s = tid - le * NS;
+    const int e = e0 + le;
+    const bool active = tid < NT && e < a.mesh.Ne;
+    const int p = e * NS + s;
+    const int vb = blockIdx.y;
+    const int k0 = vb * a.Kblk;
+    const int k1 = min(a.Nu, k0 + a.Kblk);
+    const int id[3] = {s % Q, (s / Q) % Q, s / (Q * Q)};
+    const int stride[3] = {1, Q, Q * Q};
+    const int n1 = a.mesh.n[0], n2 = a.mesh.n[1], n3 = a.mesh.n[2];
+    const int ec[3] = {e % n1, (e / n1) % n2, e / (n1 * n2)};
+    const int estr[3] = {1, n1, n1 * n2};
+    const int nn[3] = {n1, n2, n3};
+    int en_[3][2], base[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        en_[d][0] = ec[d] > 0 ? e - estr[d] : (a.mesh.periodic[d] ? e + (nn[d] - 1) * estr[d] : -1);
+        en_[d][1] = ec[d] < nn[d] - 1 ? e + estr[d] : (a.mesh.periodic[d] ? e - (nn[d] - 1) * estr[d] : -1);
+        base[d] = s - id[d] * stride[d];
+    }
+    Eq32 e32;
+    float itau = 0.f, gfac = 0.f;
+    float gm[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, U0f[3] = {0.f, 0.f, 0.f};
+    {
+        const double qz[10] = {0.0, 0.0, 0.0, 0.0, 1.0, 1.0, 1.0, 0.0, 0.0, 0.0};
+        const double *q = active ? a.eq + (size_t)p * BGK_NEQ : qz;
+        e32.load(q);
+        if (active) {
+            itau = (float)q[10]; gfac = (float)q[11];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) gm[i] = (float)q[12 + i];
+            U0f[0] = (float)q[17]; U0f[1] = (float)q[18]; U0f[2] = (float)q[19];
+        }
+    }
+    const VelGrid &vg = a.vg;
+    const int vn1 = vg.n[0], vn2 = vg.n[1], vn3 = vg.n[2];
+    const int jc[3] = {(vn1 - 1) / 2, (vn2 - 1) / 2, (vn3 - 1) / 2};
+    const double uc[3] = {vg.lo[0] + jc[0] * vg.h[0], vg.lo[1] + jc[1] * vg.h[1], vg.lo[2] + jc[2] * vg.h[2]};
+    const float toh[3] = {(float)a.mesh.two_over_h[0], (float)a.mesh.two_over_h[1], (float)a.mesh.two_over_h[2]};
+    // f_out = a f^n + b f + c R written as (a + b) f + a (f^n - f) + c R: for
+    // SSP-RK3 a + b = 1 exactly, which FP32 roundings of a and b would not keep
+    // (1/3 and 2/3 both round up in FP32, a 3e-8 mass gain per step).
+    const float fa = (float)a.a, fab = (float)(a.a + a.b), fc = (float)a.c;
+    IndexMoments acc;
+    acc.init();
+    const size_t slab = (size_t)a.P;
+    __syncthreads();
+
+    int buf = 0;
+    for (int kl = k0; kl < k1; kl += vn1) {
+        const int line = kl / vn1;
+        const int j2 = line % vn2, j3 = line / vn2;
+        if (j3 != acc.j3cur) {
+            if (acc.j3cur >= 0) acc.flush_plane(trap(acc.j3cur, vn3), (float)(acc.j3cur - jc[2]));
+            acc.j3cur = j3;
+        }
+        const double *vl = a.vtab + (size_t)kl * BGK_VTAB;
+        const float u2 = (float)__ldg(vl + 1), u3 = (float)__ldg(vl + 2);
+        float lin, cst;
+        e32.line(u2, u3, lin, cst);
+        // moment correction gamma . phi(ut): the part that is constant on the line
+        const float t2 = u2 - U0f[1], t3 = u3 - U0f[2];
+        const float corr_line = fmaf(gm[2], t2, fmaf(gm[3], t3, fmaf(0.5f * gm[4], fmaf(t2, t2, t3 * t3), gm[0])));
+        for (int j1 = 0; j1 < vn1; ++j1) {
+            const int k = kl + j1;
+            float fself[C];
+            if (active) {
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    fself[c] = __ldg(a.f_s + ((size_t)c * a.Nu + k) * slab + p);
+                    sf[buf][c][tid] = fself[c];
+                }
+            }
+            __syncthreads();
+            if (active) {
+                const float u1 = (float)__ldg(a.vtab + (size_t)k * BGK_VTAB);
+                const float u[3] = {u1, u2, u3};
+                const float g32 = e32.g(u1, lin, cst);
+                const float t1 = u1 - U0f[0];
+                const float corr = fmaf(t1, fmaf(0.5f * gm[4], t1, gm[1]), corr_line);
+                // The correction g32 * corr is a fraction of an ulp of g32; it is
+                // added to the residual (whose exact value has random low bits,
+                // so the rounding stays unbiased), never rounded into g itself.
+                const float gc = __fmul_rn(g32, corr);
+                float outv[C];
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const float *fs = a.f_s + ((size_t)c * a.Nu + k) * slab;
+                    const float *sfc = sf[buf][c];
+                    const float fi = fself[c];
+                    float div = 0.f;
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        const int side = u[d] > 0.f ? 0 : 1;
+                        const float *own = sfc + le * NS + base[d];
+                        float t = 0.f;
+#pragma unroll
+                        for (int j = 0; j < Q; ++j) t = fmaf(sD[side][id[d]][j], own[j * stride[d]] - fi, t);
+                        const int en = en_[d][side];
+                        float dn;
+                        if (en >= e0 && en < e0 + EB) {
+                            const float *nb = sfc + (en - e0) * NS + base[d];
+                            dn = sdlam[side] * fi;
+#pragma unroll
+                            for (int j = 0; j < Q; ++j) dn = fmaf(slam[side][j], nb[j * stride[d]] - fi, dn);
+                        } else if (en >= 0) {
+                            const float *nb = fs + (size_t)en * NS + base[d];
+                            dn = sdlam[side] * fi;
+#pragma unroll
+                            for (int j = 0; j < Q; ++j) dn = fmaf(slam[side][j], __ldg(nb + j * stride[d]) - fi, dn);
+                        } else {
+                            dn = (float)__ldg(a.bcval + ((size_t)(2 * d + side) * C + c) * a.Nu + k) - fi;
+                        }
+                        t = fmaf(sdg[side][id[d]], dn, fmaf(seps[side][id[d]], fi, t));
+                        div = fmaf(toh[d] * u[d], t, div);
+                    }
+                    const float eqv = (c == 0) ? g32 : gfac * g32;
+                    const float eqc = (c == 0) ? gc : gfac * gc;
+                    const float R = fmaf(eqv - fself[c], itau, fmaf(eqc, itau, -div));
+                    float out = fab == 1.f ? fself[c] : fab * fself[c];
+                    if (fa != 0.f)
+                        out = fmaf(fa, __ldg(a.f_n + ((size_t)c * a.Nu + k) * slab + p) - fself[c], out);
+                    out = fmaf(fc, R, out);
+                    a.f_out[((size_t)c * a.Nu + k) * slab + p] = out;
+                    outv[c] = out;
+                }
+                acc.add(trap(j1, vn1), (float)(j1 - jc[0]), outv[0], C == 2 ? outv[C - 1] : 0.f);
+            }
+            buf ^= 1;
+        }
+        acc.end_line(trap(j2, vn2), (float)(j2 - jc[1]));
+    }
+    if (acc.j3cur >= 0) acc.flush_plane(trap(acc.j3cur, vn3), (float)(acc.j3cur - jc[2]));
+    if (a.part && active) {
+        double m[BGK_NMOM];
+        index_to_raw(acc.J, vg, uc, m);
+#pragma unroll
+        for (int j = 0; j < BGK_NMOM; ++j) a.part[((size_t)vb * BGK_NMOM + j) * a.P + p] = m[j];
+    }
+}
+
+// Raw moments of an FP32 state with FP64 accumulation (initialisation and
+// test entry points; the stepping loop takes its moments from the stage).
+__global__ void __launch_bounds__(256) k_moments_f32(const float *f, double *part, const double *vtab,
+                                                     int Nu, int P, int Kblk, int C) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const int vb = blockIdx.y;
+    const int k0 = vb * Kblk, k1 = min(Nu, k0 + Kblk);
+    double m[BGK_NMOM];
+#pragma unroll
+    for (int j = 0; j < BGK_NMOM; ++j) m[j] = 0.0;
+    for (int k = k0; k < k1; ++k) {
+        const double *v = vtab + (size_t)k * BGK_VTAB;
+        const double u1 = __ldg(v + 0), u2 = __ldg(v + 1), u3 = __ldg(v + 2), w = __ldg(v + 3);
+        const double wF = w * (double)__ldg(f + (size_t)k * P + p);
+        m[0] += wF;
+        m[1] = fma(wF, u1, m[1]);
+        m[2] = fma(wF, u2, m[2]);
+        m[3] = fma(wF, u3, m[3]);
+        m[4] = fma(wF * u1, u1, m[4]);
+        m[5] = fma(wF * u2, u2, m[5]);
+        m[6] = fma(wF * u3, u3, m[6]);
+        m[7] = fma(wF * u1, u2, m[7]);
+        m[8] = fma(wF * u1, u3, m[8]);
+        m[9] = fma(wF * u2, u3, m[9]);
+        if (C == 2) m[10] = fma(w, (double)__ldg(f + ((size_t)Nu + k) * P + p), m[10]);
+    }
+#pragma unroll
+    for (int j = 0; j < BGK_NMOM; ++j) part[((size_t)vb * BGK_NMOM + j) * P + p] = m[j];
+}
+
+__global__ void k_maxwellian_f32(float *f, const double *qin, const double *vtab, int Nu, int P,
+                                 int C, double delta) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)Nu * P) return;
+    const int k = (int)(i / P), p = (int)(i - (size_t)k * P);
+    const double *q = qin + (size_t)p * 5;
+    const double rho = q[0], th = q[4];
+    const double *vt = vtab + (size_t)k * BGK_VTAB;
+    const double c1 = vt[0] - q[1], c2 = vt[1] - q[2], c3 = vt[2] - q[3];
+    const double twopi_th = 6.283185307179586476925286766559 * th;
+    const double F = rho / (twopi_th * sqrt(twopi_th)) * exp(-(c1 * c1 + c2 * c2 + c3 * c3) / (2.0 * th));
+    f[(size_t)k * P + p] = (float)F;
+    if (C == 2) f[((size_t)Nu + k) * P + p] = (float)(0.5 * delta * th * F);
+}
+
+}  // namespace
+
+cudaError_t launch_moments_f32(const float *f, double *part, const double *vtab, int Nu, int P,
+                               int Kblk, int C, int n_vblk, cudaStream_t s) {
+    dim3 grid((P + 255) / 256, n_vblk);
+    k_moments_f32<<<grid, 256, 0, s>>>(f, part, vtab, Nu, P, Kblk, C);
+    return cudaGetLastError();
+}
+
+template <int Q>
+static cudaError_t stage32_q(const StageArgs<float> &a, int C, int n_vblk, cudaStream_t s) {
+    constexpr int NS = Q * Q * Q, EB = 256 / NS;
+    dim3 grid((a.mesh.Ne + EB - 1) / EB, n_vblk);
+    if (C == 1) k_stage_f32<Q, 1><<<grid, EB * NS, 0, s>>>(a);
+    else k_stage_f32<Q, 2><<<grid, EB * NS, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stage_f32(const StageArgs<float> &a, int C, int n_vblk, cudaStream_t s) {
+    switch (a.fr.q) {
+        case 2: return stage32_q<2>(a, C, n_vblk, s);
+        case 3: return stage32_q<3>(a, C, n_vblk, s);
+        case 4: return stage32_q<4>(a, C, n_vblk, s);
+        case 5: return stage32_q<5>(a, C, n_vblk, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_maxwellian_f32(float *f, const double *q, const double *vtab, int Nu, int P, int C,
+                                  double delta, cudaStream_t s) {
+    const size_t n = (size_t)Nu * P;
+    k_maxwellian_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(f, q, vtab, Nu, P, C, delta);
+    return cudaGetLastError();
+}

@@ -240,6 +240,7 @@ __global__ void __launch_bounds__(256) k_qprime_f64(QPrimeArgs a) {
     double res = 1.0e300;
     Sym3 A;
     double c0 = 0.0;
+    double M[35];
     for (;;) {
         Sym3 T = B;
         T.t11 += x[4] / gs.Pr; T.t22 += x[4] / gs.Pr; T.t33 += x[4] / gs.Pr;
@@ -249,7 +250,6 @@ __global__ void __launch_bounds__(256) k_qprime_f64(QPrimeArgs a) {
         const double dl[3] = {x[1] - U0[0], x[2] - U0[1], x[3] - U0[2]};
         const double rho1 = exp(-A.t11 * h1 * h1);
         const double ia11 = 1.0 / A.t11, ih1 = 1.0 / h1;
-        double M[35];
 #pragma unroll
         for (int i = 0; i < 35; ++i) M[i] = 0.0;
         for (int line = lane; line < n2 * n3; line += 32) {
@@ -452,6 +452,81 @@ __global__ void __launch_bounds__(256) k_qprime_f64(QPrimeArgs a) {
         ++it;
     }
 
+    // Mixed form: the stage evaluates the equilibrium in FP32 (Eq32), whose
+    // discrete moments miss Q by ~1e-7 with a bias shared by neighbouring
+    // points.  Measure that defect here, on the exact FP32 values the stage
+    // will produce, and fit gamma so that g32 (1 + gamma . phi(ut)),
+    // phi = (1, ut, |ut|^2/2), has the discrete moments of g(Q') again:
+    // G gamma = -(S - T), G_ij = sum w phi_i phi_j g, T_i = sum w phi_i g.
+    double gam[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (a.mixed && a.eq) {
+        const double qd[10] = {c0, x[1], x[2], x[3], A.t11, A.t22, A.t33, A.t12, A.t13, A.t23};
+        Eq32 e32;
+        e32.load(qd);
+        double S[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int line = lane; line < n2 * n3; line += 32) {
+            const int j2 = line % n2, j3 = line / n2;
+            const double *vl = a.vtab + (size_t)line * n1 * BGK_VTAB;
+            const double ut2 = vl[1] - U0[1], ut3 = vl[2] - U0[2];
+            const double w23 = ((j2 == 0 || j2 == n2 - 1) ? 0.5 * h2 : h2) *
+                               ((j3 == 0 || j3 == n3 - 1) ? 0.5 * h3 : h3);
+            float lin, cst;
+            e32.line((float)vl[1], (float)vl[2], lin, cst);
+            double L0 = 0.0, L1 = 0.0, L2 = 0.0;
+            for (int j1 = 0; j1 < n1; ++j1) {
+                const double g = (double)e32.g((float)vl[(size_t)j1 * BGK_VTAB], lin, cst);
+                L0 = fma(g, tab[wib][j1][0], L0);
+                L1 = fma(g, tab[wib][j1][1], L1);
+                L2 = fma(g, tab[wib][j1][2], L2);
+            }
+            S[0] = fma(w23, L0, S[0]);
+            S[1] = fma(w23, L1, S[1]);
+            S[2] = fma(w23 * ut2, L0, S[2]);
+            S[3] = fma(w23 * ut3, L0, S[3]);
+            S[4] = fma(0.5 * w23, fma(ut2 * ut2 + ut3 * ut3, L0, L2), S[4]);
+        }
+        warp_sum_n(S);
+#define MM(p1, p2, p3) M[midx(p1, p2, p3)]
+        double Gm[5][5];
+        Gm[0][0] = MM(0, 0, 0);
+        Gm[0][1] = MM(1, 0, 0); Gm[0][2] = MM(0, 1, 0); Gm[0][3] = MM(0, 0, 1);
+        Gm[0][4] = 0.5 * (MM(2, 0, 0) + MM(0, 2, 0) + MM(0, 0, 2));
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+#pragma unroll
+            for (int e = 0; e < 3; ++e)
+                Gm[1 + d][1 + e] = M[midx((d == 0) + (e == 0), (d == 1) + (e == 1), (d == 2) + (e == 2))];
+            double acc = 0.0;
+#pragma unroll
+            for (int e = 0; e < 3; ++e)
+                acc += M[midx((d == 0) + 2 * (e == 0), (d == 1) + 2 * (e == 1), (d == 2) + 2 * (e == 2))];
+            Gm[1 + d][4] = 0.5 * acc;
+        }
+        {
+            double acc = 0.0;
+#pragma unroll
+            for (int e = 0; e < 3; ++e)
+#pragma unroll
+                for (int f = 0; f < 3; ++f)
+                    acc += M[midx(2 * (e == 0) + 2 * (f == 0), 2 * (e == 1) + 2 * (f == 1),
+                                  2 * (e == 2) + 2 * (f == 2))];
+            Gm[4][4] = 0.25 * acc;
+        }
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+#pragma unroll
+            for (int j = 0; j < i; ++j) Gm[i][j] = Gm[j][i];
+        const double Tt[5] = {Gm[0][0], Gm[0][1], Gm[0][2], Gm[0][3], Gm[0][4]};
+#undef MM
+        double rhs[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) rhs[i] = Tt[i] - S[i];
+        if (solve5(Gm, rhs)) {
+#pragma unroll
+            for (int i = 0; i < 5; ++i) gam[i] = isfinite(rhs[i]) ? rhs[i] : 0.0;
+        }
+    }
+
     if (lane == 0) {
         if (a.qp) {
 #pragma unroll
@@ -464,6 +539,9 @@ __global__ void __launch_bounds__(256) k_qprime_f64(QPrimeArgs a) {
             q[4] = A.t11; q[5] = A.t22; q[6] = A.t33; q[7] = A.t12; q[8] = A.t13; q[9] = A.t23;
             q[10] = 1.0 / tau;
             q[11] = hd * x[4];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) q[12 + i] = gam[i];
+            q[17] = U0[0]; q[18] = U0[1]; q[19] = U0[2];
         }
         if (!conv) atomicOr(a.status, BGK_DEV_NOCONV);
         if (a.stats) {
@@ -544,6 +622,7 @@ __global__ void __launch_bounds__(256) k_stage_f64(StageArgs<double> a) {
     const double ah = -0.5 * A11 * h1 * h1;              // q(j) = q0 + j D0 + ah j (j - 1)
     const double rho1 = exp(2.0 * ah);
     const int vn1 = a.vg.n[0];
+    const double ab = a.a + a.b;
     double m[BGK_NMOM];
 #pragma unroll
     for (int j = 0; j < BGK_NMOM; ++j) m[j] = 0.0;
@@ -618,8 +697,11 @@ __global__ void __launch_bounds__(256) k_stage_f64(StageArgs<double> a) {
                     }
                     const double eqv = (c == 0) ? g : gfac * g;
                     const double R = fma(eqv - fself[c], itau, -div);
-                    double out = fma(a.c, R, a.b * fself[c]);
-                    if (a.a != 0.0) out = fma(a.a, __ldg(a.f_n + ((size_t)c * a.Nu + k) * slab + p), out);
+                    // (a + b) f + a (f^n - f) + c R keeps a + b = 1 exact for SSP-RK3
+                    double out = ab == 1.0 ? fself[c] : ab * fself[c];
+                    if (a.a != 0.0)
+                        out = fma(a.a, __ldg(a.f_n + ((size_t)c * a.Nu + k) * slab + p) - fself[c], out);
+                    out = fma(a.c, R, out);
                     a.f_out[((size_t)c * a.Nu + k) * slab + p] = out;
                     outv[c] = out;
                 }
