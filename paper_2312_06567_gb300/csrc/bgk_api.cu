@@ -33,6 +33,7 @@ struct bgk_ctx {
     double *eq;                       // [P][NEQ]
     double *qp;                       // [P][5]
     double *vtab;                     // [Nu][VTAB]
+    float4 *vtab32;                   // [Nu] FP32 velocity nodes
     double *bcval;                    // [6][C][Nu]
     unsigned int *status;
     NewtonStats *stats;
@@ -208,7 +209,7 @@ bgk_status run_moments(bgk_ctx *ctx, const void *f) {
 bgk_status run_qprime(bgk_ctx *ctx, const double *part, int n_vblk, int P, double *eq, double *qp,
                       int *iters, const double *guess) {
     QPrimeArgs a{};
-    a.part = part; a.n_vblk = n_vblk; a.vtab = ctx->vtab; a.guess = guess; a.eq = eq; a.qp = qp;
+    a.part = part; a.n_vblk = n_vblk; a.vtab = ctx->vtab; a.vtab32 = ctx->vtab32; a.guess = guess; a.eq = eq; a.qp = qp;
     a.iters = iters; a.status = ctx->status; a.stats = ctx->stats; a.P = P; a.Nu = ctx->Nu;
     a.tol = ctx->tol; a.max_iter = ctx->max_iter; a.gas = ctx->gas; a.vg = ctx->vg;
     a.mixed = ctx->precision == BGK_MIXED ? 1 : 0;
@@ -222,9 +223,12 @@ StageArgs<T> stage_args(bgk_ctx *ctx, const void *fn, const void *fs, void *fo, 
                         double c, bool moments) {
     StageArgs<T> s{};
     s.f_n = (const T *)fn; s.f_s = (const T *)fs; s.f_out = (T *)fo;
-    s.eq = ctx->eq; s.vtab = ctx->vtab; s.bcval = ctx->bcval; s.part = moments ? ctx->part : nullptr;
+    s.eq = ctx->eq; s.vtab = ctx->vtab; s.vtab32 = ctx->vtab32; s.bcval = ctx->bcval;
+    s.part = moments ? ctx->part : nullptr;
     s.a = a; s.b = b; s.c = c; s.Nu = ctx->Nu; s.P = ctx->P; s.Kblk = ctx->Kblk;
     s.vg = ctx->vg; s.fr = ctx->fr; s.mesh = ctx->mesh;
+    s.a32 = (float)a; s.ab32 = (float)(a + b); s.c32 = (float)c;
+    for (int d = 0; d < 3; ++d) s.toh32[d] = (float)ctx->mesh.two_over_h[d];
     return s;
 }
 
@@ -329,6 +333,7 @@ bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
         v[4] = 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
         v[5] = v[3] * v[0];
         v[6] = v[3] * v[0] * v[0];
+        v[7] = 2.0 * mesh->n[0] / (mesh->hi[0] - mesh->lo[0]) * v[0];   // (2/h_1) u_1
     }
     // Dirichlet exterior states per face and velocity
     std::vector<double> bcv((size_t)6 * ctx->C * Nu, 0.0);
@@ -377,6 +382,13 @@ bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
     if (st == BGK_OK) cu(cudaMalloc(&ctx->iters, P * sizeof(int)), "cudaMalloc(iters)");
     if (st == BGK_OK) cu(cudaMalloc(&ctx->vtab, ctx->vtab_h.size() * sizeof(double)), "cudaMalloc(vtab)");
     if (st == BGK_OK) cu(cudaMalloc(&ctx->bcval, bcv.size() * sizeof(double)), "cudaMalloc(bcval)");
+    std::vector<float4> v32(Nu);
+    for (int k = 0; k < Nu; ++k) {
+        const double *v = &ctx->vtab_h[(size_t)k * BGK_VTAB];
+        v32[k] = make_float4((float)v[0], (float)v[1], (float)v[2], 0.f);
+    }
+    if (st == BGK_OK) cu(cudaMalloc(&ctx->vtab32, v32.size() * sizeof(float4)), "cudaMalloc(vtab32)");
+    if (st == BGK_OK) cu(cudaMemcpyAsync(ctx->vtab32, v32.data(), v32.size() * sizeof(float4), cudaMemcpyHostToDevice, ctx->stream), "upload vtab32");
     if (st == BGK_OK) cu(cudaMalloc(&ctx->status, sizeof(unsigned int)), "cudaMalloc(status)");
     if (st == BGK_OK) cu(cudaMalloc(&ctx->stats, sizeof(NewtonStats)), "cudaMalloc(stats)");
     if (st == BGK_OK) cu(cudaMemcpyAsync(ctx->vtab, ctx->vtab_h.data(), ctx->vtab_h.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload vtab");
@@ -397,7 +409,7 @@ bgk_status bgk_destroy(bgk_ctx *ctx) {
     for (auto e : ctx->ev_pool) cudaEventDestroy(e);
     for (int i = 0; i < 3; ++i) cudaFree(ctx->f[i]);
     cudaFree(ctx->part); cudaFree(ctx->mom); cudaFree(ctx->eq); cudaFree(ctx->qp);
-    cudaFree(ctx->iters); cudaFree(ctx->vtab); cudaFree(ctx->bcval); cudaFree(ctx->status);
+    cudaFree(ctx->iters); cudaFree(ctx->vtab); cudaFree(ctx->vtab32); cudaFree(ctx->bcval); cudaFree(ctx->status);
     cudaFree(ctx->stats);
     delete ctx;
     return BGK_OK;

@@ -10,7 +10,7 @@
 #define BGK_MAXQ 5          // FR order p <= 4
 #define BGK_NMOM 11         // raw moment slots per point
 #define BGK_NEQ 20          // equilibrium record per point (12 used by the FP64 form)
-#define BGK_VTAB 8          // velocity table record: u1 u2 u3 w e=|u|^2/2 w*u1 w*u1^2 (1 pad)
+#define BGK_VTAB 8          // velocity table record: u1 u2 u3 w e=|u|^2/2 w*u1 w*u1^2 (2/h1)*u1
 #define BGK_MAXV 128        // nodes per velocity axis at most
 
 // Device status bits (OR-ed by kernels, read by the host after a stage).
@@ -67,7 +67,14 @@ struct Eq32 {
     }
     __device__ __forceinline__ float g(float u1, float lin, float cst) const {
         const float c1 = __fsub_rn(u1, V1);
-        return __fmul_rn(E0, exp2f(fmaf(c1, fmaf(A11, c1, lin), cst)));
+        return __fmul_rn(E0, ex2(fmaf(c1, fmaf(A11, c1, lin), cst)));
+    }
+    // 2^x on the special-function unit (a few ulp; the moment correction
+    // absorbs the bias, and both kernels that use Eq32 see the same values)
+    static __device__ __forceinline__ float ex2(float x) {
+        float y;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
     }
 };
 
@@ -88,9 +95,14 @@ struct StageArgs {
     T *f_out;
     const double *eq;        // [P][BGK_NEQ]
     const double *vtab;      // [Nu][BGK_VTAB]
+    const float4 *vtab32;    // [Nu] (u1, u2, u3, 0) rounded to FP32
     const double *bcval;     // [6][C][Nu] exterior Maxwellian values of Dirichlet faces
     double *part;            // [n_vblk][BGK_NMOM][P] moment partials of f_out (or null)
     double a, b, c;
+    // FP32 copies made on the host: a, a + b, c, and the metric terms 2/h_d
+    // (converting them in the kernel costs an FP64-pipe instruction each time
+    // the compiler rematerialises them inside the velocity loop)
+    float a32, ab32, c32, toh32[3];
     int Nu, P, Kblk;
     VelGrid vg;
     FROps fr;
@@ -101,6 +113,7 @@ struct QPrimeArgs {
     const double *part;      // [n_vblk][BGK_NMOM][P]
     int n_vblk;
     const double *vtab;
+    const float4 *vtab32;
     const double *guess;     // [P][5] or null
     double *eq;              // [P][BGK_NEQ] or null
     double *qp;              // [P][5] or null

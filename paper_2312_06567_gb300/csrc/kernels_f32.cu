@@ -223,11 +223,11 @@ __global__ void __launch_bounds__(256) k_stage_f32(StageArgs<float> a) {
     const int vn1 = vg.n[0], vn2 = vg.n[1], vn3 = vg.n[2];
     const int jc[3] = {(vn1 - 1) / 2, (vn2 - 1) / 2, (vn3 - 1) / 2};
     const double uc[3] = {vg.lo[0] + jc[0] * vg.h[0], vg.lo[1] + jc[1] * vg.h[1], vg.lo[2] + jc[2] * vg.h[2]};
-    const float toh[3] = {(float)a.mesh.two_over_h[0], (float)a.mesh.two_over_h[1], (float)a.mesh.two_over_h[2]};
+    const float toh[3] = {a.toh32[0], a.toh32[1], a.toh32[2]};
     // f_out = a f^n + b f + c R written as (a + b) f + a (f^n - f) + c R: for
     // SSP-RK3 a + b = 1 exactly, which FP32 roundings of a and b would not keep
     // (1/3 and 2/3 both round up in FP32, a 3e-8 mass gain per step).
-    const float fa = (float)a.a, fab = (float)(a.a + a.b), fc = (float)a.c;
+    const float fa = a.a32, fab = a.ab32, fc = a.c32;
     IndexMoments acc;
     acc.init();
     const size_t slab = (size_t)a.P;
@@ -241,14 +241,15 @@ __global__ void __launch_bounds__(256) k_stage_f32(StageArgs<float> a) {
             if (acc.j3cur >= 0) acc.flush_plane(trap(acc.j3cur, vn3), (float)(acc.j3cur - jc[2]));
             acc.j3cur = j3;
         }
-        const double *vl = a.vtab + (size_t)kl * BGK_VTAB;
-        const float u2 = (float)__ldg(vl + 1), u3 = (float)__ldg(vl + 2);
+        const float4 vl = __ldg(a.vtab32 + kl);
+        const float u2 = vl.y, u3 = vl.z;
         float lin, cst;
         e32.line(u2, u3, lin, cst);
         // moment correction gamma . phi(ut): the part that is constant on the line
         const float t2 = u2 - U0f[1], t3 = u3 - U0f[2];
         const float corr_line = fmaf(gm[2], t2, fmaf(gm[3], t3, fmaf(0.5f * gm[4], fmaf(t2, t2, t3 * t3), gm[0])));
-        for (int j1 = 0; j1 < vn1; ++j1) {
+        float jt1 = (float)(-jc[0]);                  // centred index as a float counter
+        for (int j1 = 0; j1 < vn1; ++j1, jt1 += 1.f) {
             const int k = kl + j1;
             float fself[C];
             if (active) {
@@ -260,7 +261,7 @@ __global__ void __launch_bounds__(256) k_stage_f32(StageArgs<float> a) {
             }
             __syncthreads();
             if (active) {
-                const float u1 = (float)__ldg(a.vtab + (size_t)k * BGK_VTAB);
+                const float u1 = __ldg(a.vtab32 + k).x;
                 const float u[3] = {u1, u2, u3};
                 const float g32 = e32.g(u1, lin, cst);
                 const float t1 = u1 - U0f[0];
@@ -283,7 +284,7 @@ __global__ void __launch_bounds__(256) k_stage_f32(StageArgs<float> a) {
                         float t = 0.f;
 #pragma unroll
                         for (int j = 0; j < Q; ++j) t = fmaf(sD[side][id[d]][j], own[j * stride[d]] - fi, t);
-                        const int en = en_[d][side];
+                        const int en = side ? en_[d][1] : en_[d][0];
                         float dn;
                         if (en >= e0 && en < e0 + EB) {
                             const float *nb = sfc + (en - e0) * NS + base[d];
@@ -311,7 +312,7 @@ __global__ void __launch_bounds__(256) k_stage_f32(StageArgs<float> a) {
                     a.f_out[((size_t)c * a.Nu + k) * slab + p] = out;
                     outv[c] = out;
                 }
-                acc.add(trap(j1, vn1), (float)(j1 - jc[0]), outv[0], C == 2 ? outv[C - 1] : 0.f);
+                acc.add(trap(j1, vn1), jt1, outv[0], C == 2 ? outv[C - 1] : 0.f);
             }
             buf ^= 1;
         }

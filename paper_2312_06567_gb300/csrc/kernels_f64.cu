@@ -470,11 +470,12 @@ __global__ void __launch_bounds__(256) k_qprime_f64(QPrimeArgs a) {
             const double ut2 = vl[1] - U0[1], ut3 = vl[2] - U0[2];
             const double w23 = ((j2 == 0 || j2 == n2 - 1) ? 0.5 * h2 : h2) *
                                ((j3 == 0 || j3 == n3 - 1) ? 0.5 * h3 : h3);
+            const float4 *vl32 = a.vtab32 + (size_t)line * n1;
             float lin, cst;
-            e32.line((float)vl[1], (float)vl[2], lin, cst);
+            e32.line(vl32[0].y, vl32[0].z, lin, cst);
             double L0 = 0.0, L1 = 0.0, L2 = 0.0;
             for (int j1 = 0; j1 < n1; ++j1) {
-                const double g = (double)e32.g((float)vl[(size_t)j1 * BGK_VTAB], lin, cst);
+                const double g = (double)e32.g(vl32[j1].x, lin, cst);
                 L0 = fma(g, tab[wib][j1][0], L0);
                 L1 = fma(g, tab[wib][j1][1], L1);
                 L2 = fma(g, tab[wib][j1][2], L2);
@@ -633,6 +634,7 @@ __global__ void __launch_bounds__(256) k_stage_f64(StageArgs<double> a) {
     for (int kl = k0; kl < k1; kl += vn1) {           // one first-axis velocity line
         const double *vl = a.vtab + (size_t)kl * BGK_VTAB;
         const double u2 = __ldg(vl + 1), u3 = __ldg(vl + 2);
+        const double sc2 = a.mesh.two_over_h[1] * u2, sc3 = a.mesh.two_over_h[2] * u3;
         const double c1_0 = __ldg(vl + 0) - V1, c2 = u2 - V2, c3 = u3 - V3;
         const double lin = A12 * c2 + A13 * c3;
         const double cst = A22 * c2 * c2 + 2.0 * A23 * c2 * c3 + A33 * c3 * c3;
@@ -666,6 +668,7 @@ __global__ void __launch_bounds__(256) k_stage_f64(StageArgs<double> a) {
             __syncthreads();
             if (active) {
                 const double u[3] = {__ldg(vt + 0), u2, u3};
+                const double sc[3] = {__ldg(vt + 7), sc2, sc3};       // (2/h_d) u_d
                 double outv[C];
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
@@ -679,7 +682,7 @@ __global__ void __launch_bounds__(256) k_stage_f64(StageArgs<double> a) {
                         double t = 0.0;
 #pragma unroll
                         for (int j = 0; j < Q; ++j) t = fma(sD[side][id[d]][j], own[j * stride[d]], t);
-                        const int en = en_[d][side];
+                        const int en = side ? en_[d][1] : en_[d][0];
                         double fp = 0.0;
                         if (en >= e0 && en < e0 + EB) {
                             const double *nb = sfc + (en - e0) * NS + base[d];
@@ -693,7 +696,7 @@ __global__ void __launch_bounds__(256) k_stage_f64(StageArgs<double> a) {
                             fp = __ldg(a.bcval + ((size_t)(2 * d + side) * C + c) * a.Nu + k);
                         }
                         t = fma(sdg[side][id[d]], fp, t);
-                        div = fma(a.mesh.two_over_h[d] * u[d], t, div);
+                        div = fma(sc[d], t, div);
                     }
                     const double eqv = (c == 0) ? g : gfac * g;
                     const double R = fma(eqv - fself[c], itau, -div);
