@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--forms", default="fp64,mixed")
+    ap.add_argument("--forms", default="fp64,mixed,mixed_learned")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--workload", default="taylor_green", choices=sorted(WORKLOADS))
@@ -167,8 +167,10 @@ def run_ours(args, rank, world, dev):
         for k in ("fp64_fma", "fp64_exp", "fp32_fma", "fp32_exp2"):
             peaks[k] = bgk.probe_peak(k)
     forms = [f for f in args.forms.split(",") if f]
+    headline = next((f for f in ("mixed_learned", "mixed", "fp64") if f in forms), forms[0])
     for form in forms:
         prec = bgk.BGK_FP64 if form == "fp64" else bgk.BGK_MIXED
+        learned = form.endswith("_learned")
         s = bgk.Solver(wl, prec, stream=stream)
         x = s.node_coords()
         rho, U, theta = wl.init(x)
@@ -176,9 +178,26 @@ def run_ours(args, rank, world, dev):
                          np.broadcast_to(theta, x.shape[:-1]))
         q = np.concatenate([rho.reshape(-1, 1), U.reshape(-1, 3), theta.reshape(-1, 1)], axis=1)
         s.set_maxwellian(q)
+        train = None
+        if learned:
+            # warm-up steps log the solver's own (features, Delta) pairs; the
+            # network is trained on them (outside the timed region) and the
+            # timed steps start Newton from its guess
+            s.mlp_log(True, 3 * wl.n_elem * wl.n_sol * args.warmup + 1)
         for _ in range(args.warmup):
             s.step(dt, 1)
         torch.cuda.synchronize()
+        if learned:
+            s.mlp_log(False)
+            s.stats()
+            t0 = time.perf_counter()
+            loss = s.mlp_train(epochs=8, batch=4096, lr=2e-3, seed=0, bf16=True)
+            torch.cuda.synchronize()
+            train = {"seconds": time.perf_counter() - t0, "final_loss": loss, "epochs": 8,
+                     "batch": 4096, "pairs": 3 * wl.n_elem * wl.n_sol * args.warmup,
+                     "precision": "bf16 operands, fp32 accumulate, fp32 master weights"}
+            s.set_guess(1, bf16=True)
+            s.mlp_stats()
         s.stats()
         tot0 = s.totals()
         if world > 1:
@@ -210,7 +229,7 @@ def run_ours(args, rank, world, dev):
             ms = float(t.item())
         # e2e: host pinned state in, one step, state out, through the C-ABI
         e2e = None
-        if args.e2e_steps > 0:
+        if args.e2e_steps > 0 and form == headline:
             host = torch.empty(s.shape, dtype=torch.float64 if prec == bgk.BGK_FP64 else torch.float32,
                                pin_memory=True)
             s.get_state(host)
@@ -226,9 +245,12 @@ def run_ours(args, rank, world, dev):
             e2e = {"value": world * wl.dof * 3 * args.e2e_steps / e2e_s, "unit": UNIT,
                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
             del host
+        newton = dict(mean_iters=mean_it, max_iters=max_it, max_residual=res)
+        if learned:
+            newton["guess_fallbacks"] = s.mlp_stats()
+            newton["training"] = train
         results[form] = dict(ms=ms, status=bgk.STATUS_NAMES[st], prof=prof, clocks=ck,
-                             newton=dict(mean_iters=mean_it, max_iters=max_it, max_residual=res),
-                             e2e=e2e, drift=drift)
+                             newton=newton, e2e=e2e, drift=drift)
         s.destroy()
         torch.cuda.empty_cache()
     return wl, results, peaks
@@ -320,7 +342,7 @@ def main():
     wl, results, peaks = run_ours(args, rank, world, dev)
     if rank != 0:
         return
-    main_form = "mixed" if "mixed" in results else list(results)[0]
+    main_form = next((f for f in ("mixed_learned", "mixed", "fp64") if f in results), list(results)[0])
     peaks["hbm_gbs"] = _measured_hbm()
     r = results[main_form]
     ms_per_step = r["ms"] / args.steps
@@ -329,7 +351,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if main_form == "fp64" else "f32+f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if main_form == "fp64" else "f32+f64" + ("+bf16" if "learned" in main_form else ""),
         "data": "synthetic",
         "config": {"workload": wl.name, "dof": wl.dof, "elements": wl.n_elem, "order": wl.p,
                    "velocities": wl.n_vel, "form": main_form, "parallelism": "replicas",
@@ -345,7 +367,7 @@ def main():
         "peaks_measured": peaks,
     }
     line["roofline"] = roofline_fp64(wl, r, peaks, args.steps)
-    if main_form == "mixed":
+    if main_form.startswith("mixed"):
         line["roofline_stage_kernel"] = roofline_stage_hbm(wl, r, peaks, 4)
     for form, rr in results.items():
         if form != main_form:

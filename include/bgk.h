@@ -196,6 +196,47 @@ BGK_API bgk_status bgk_profile_read(bgk_ctx *ctx, double ms[BGK_NKINDS], long lo
  * Each runs a register-resident kernel over every SM for ~50 ms. */
 BGK_API bgk_status bgk_probe_peak(int kind, double *value);
 
+/* ---- Learned initial guess of the Q' solve -------------------------------
+ * Not in the paper (which starts Newton from the macroscopic state): a
+ * 9 -> 64 -> 64 -> 5 SiLU network maps the point's state to a correction
+ * Delta whose application gives Newton's starting point, trained on the GPU
+ * on pairs logged by the solver's own converged solves.  Features: rho,
+ * U1..3, theta, the invariants tr A, (tr(A)^2 - tr(A^2))/2, det A of
+ * A = Pi/(rho theta), and the mean free path lambda = mu/rho sqrt(pi/(2 theta)).
+ * Target: rho'/rho - 1, (U' - U)/sqrt(theta), theta'/theta - 1.  Weights and
+ * layer inputs are rounded to BF16 (bf16 = 1), sums accumulate in FP32, the
+ * optimiser (Adam) keeps FP32 master weights.  A guess whose first scaled
+ * residual exceeds 1e-3, or from which Newton does not converge, is
+ * discarded and the solve restarts from the macroscopic state. */
+#define BGK_MLP_NPARAM 5125   /* W1[9][64] b1[64] W2[64][64] b2[64] W3[64][5] b3[5] */
+#define BGK_MLP_NNORM 28      /* x_mean[9] x_std[9] t_mean[5] t_std[5] */
+#define BGK_MLP_LOG_STRIDE 14 /* 9 features then 5 targets per logged pair */
+
+/* mode 0: start Newton from the macroscopic state; 1: from the network
+ * (requires weights from bgk_mlp_train or bgk_mlp_weights). */
+BGK_API bgk_status bgk_set_guess(bgk_ctx *ctx, int mode, int bf16);
+/* Start (enable = 1, clearing earlier pairs) or stop logging the (features,
+ * Delta) pair of every converged point solve, at most max_pairs of them. */
+BGK_API bgk_status bgk_mlp_log(bgk_ctx *ctx, int enable, long long max_pairs);
+/* Copy up to max_pairs logged pairs (host out[n][14]); *n_out = pairs copied. */
+BGK_API bgk_status bgk_mlp_log_read(bgk_ctx *ctx, float *out, long long max_pairs, long long *n_out);
+/* Train from scratch on the logged pairs: normalisation from their mean and
+ * standard deviation, He-normal initialisation from seed, Adam with a cosine
+ * learning-rate decay from lr to lr/10, MSE loss on normalised targets.
+ * *final_loss = mean batch loss of the last epoch. */
+BGK_API bgk_status bgk_mlp_train(bgk_ctx *ctx, int epochs, int batch, float lr, unsigned long long seed,
+                                 int bf16, double *final_loss);
+/* Save (load = 0) or load (load = 1) the weights and normalisation:
+ * host buf[BGK_MLP_NPARAM + BGK_MLP_NNORM]. */
+BGK_API bgk_status bgk_mlp_weights(bgk_ctx *ctx, float *buf, int load);
+/* Loss and gradient of the current weights on one batch (host arrays:
+ * x[n][9] raw features, t[n][5] raw targets, grad[BGK_MLP_NPARAM]); the
+ * training kernel's forward and backward pass without the update. */
+BGK_API bgk_status bgk_mlp_grad(bgk_ctx *ctx, const float *x, const float *t, int n, int bf16, double *loss,
+                                float *grad);
+/* Number of learned guesses discarded since the last call (then reset). */
+BGK_API bgk_status bgk_mlp_stats(bgk_ctx *ctx, unsigned long long *fallbacks);
+
 /* Text of the last error on this context (never NULL). */
 BGK_API const char *bgk_last_error(const bgk_ctx *ctx);
 

@@ -56,6 +56,15 @@ SIGNATURES = {
     "bgk_totals": (c_int, [c_void_p, ctypes.POINTER(c_double)]),
     "bgk_stats": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int),
                           ctypes.POINTER(c_double)]),
+    "bgk_set_guess": (c_int, [c_void_p, c_int, c_int]),
+    "bgk_mlp_log": (c_int, [c_void_p, c_int, ctypes.c_longlong]),
+    "bgk_mlp_log_read": (c_int, [c_void_p, c_void_p, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]),
+    "bgk_mlp_train": (c_int, [c_void_p, c_int, c_int, ctypes.c_float, ctypes.c_ulonglong, c_int,
+                              ctypes.POINTER(c_double)]),
+    "bgk_mlp_weights": (c_int, [c_void_p, c_void_p, c_int]),
+    "bgk_mlp_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, ctypes.POINTER(c_double),
+                             c_void_p]),
+    "bgk_mlp_stats": (c_int, [c_void_p, ctypes.POINTER(ctypes.c_ulonglong)]),
     "bgk_profile": (c_int, [c_void_p, c_int]),
     "bgk_profile_read": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(ctypes.c_longlong)]),
     "bgk_probe_peak": (c_int, [c_int, ctypes.POINTER(c_double)]),
@@ -63,6 +72,8 @@ SIGNATURES = {
 }
 
 KERNEL_KINDS = ("moments", "qprime", "stage", "other")
+MLP_NPARAM, MLP_NNORM, MLP_LOG_STRIDE = 5125, 28, 14
+MLP_SHAPES = ((9, 64), (64,), (64, 64), (64,), (64, 5), (5,))
 PROBE_KINDS = {"fp64_fma": 0, "fp32_fma": 1, "fp64_exp": 2, "fp32_exp2": 3}
 
 
@@ -279,6 +290,60 @@ class Solver:
         self._check(self.lib.bgk_stats(self._h, ctypes.byref(mean), ctypes.byref(mx),
                                        ctypes.byref(res)))
         return mean.value, mx.value, res.value
+
+    # -- learned Q' guess ----------------------------------------------------
+    def set_guess(self, mode, bf16=True):
+        self._check(self.lib.bgk_set_guess(self._h, int(mode), 1 if bf16 else 0))
+
+    def mlp_log(self, enable=True, max_pairs=1 << 20):
+        self._check(self.lib.bgk_mlp_log(self._h, 1 if enable else 0, int(max_pairs)))
+
+    def mlp_log_read(self, max_pairs=1 << 20):
+        out = np.empty((max_pairs, MLP_LOG_STRIDE), dtype=np.float32)
+        n = ctypes.c_longlong()
+        self._check(self.lib.bgk_mlp_log_read(self._h, _ptr(out)[0], max_pairs, ctypes.byref(n)))
+        return out[:n.value]
+
+    def mlp_train(self, epochs=20, batch=4096, lr=1e-3, seed=0, bf16=True):
+        loss = c_double()
+        self._check(self.lib.bgk_mlp_train(self._h, epochs, batch, lr, seed, 1 if bf16 else 0,
+                                           ctypes.byref(loss)))
+        return loss.value
+
+    def mlp_weights(self, load=None):
+        """Return (params list, norm) or load them (params list of arrays, norm[28])."""
+        buf = np.empty(MLP_NPARAM + MLP_NNORM, dtype=np.float32)
+        if load is None:
+            self._check(self.lib.bgk_mlp_weights(self._h, _ptr(buf)[0], 0))
+            params, off = [], 0
+            for shp in MLP_SHAPES:
+                n = int(np.prod(shp))
+                params.append(buf[off:off + n].reshape(shp).copy())
+                off += n
+            return params, buf[MLP_NPARAM:].copy()
+        params, norm = load
+        buf[:MLP_NPARAM] = np.concatenate([np.asarray(p, dtype=np.float32).ravel() for p in params])
+        buf[MLP_NPARAM:] = np.asarray(norm, dtype=np.float32)
+        self._check(self.lib.bgk_mlp_weights(self._h, _ptr(buf)[0], 1))
+
+    def mlp_grad(self, x, t, bf16=True):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        g = np.empty(MLP_NPARAM, dtype=np.float32)
+        loss = c_double()
+        self._check(self.lib.bgk_mlp_grad(self._h, _ptr(x)[0], _ptr(t)[0], x.shape[0],
+                                          1 if bf16 else 0, ctypes.byref(loss), _ptr(g)[0]))
+        grads, off = [], 0
+        for shp in MLP_SHAPES:
+            n = int(np.prod(shp))
+            grads.append(g[off:off + n].reshape(shp).astype(np.float64))
+            off += n
+        return loss.value, grads
+
+    def mlp_stats(self):
+        n = ctypes.c_ulonglong()
+        self._check(self.lib.bgk_mlp_stats(self._h, ctypes.byref(n)))
+        return n.value
 
     def profile(self, enable=True):
         self._check(self.lib.bgk_profile(self._h, 1 if enable else 0))

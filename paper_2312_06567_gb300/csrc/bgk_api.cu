@@ -1,7 +1,9 @@
 // libbgk C-ABI: context, host-side operator construction, stage sequencing.
 // See include/bgk.h for the contract of every entry point.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <random>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -50,6 +52,15 @@ struct bgk_ctx {
     std::vector<cudaEvent_t> ev_pool;
     double prof_ms[BGK_NKINDS];
     long long launches[BGK_NKINDS];
+    // learned guess
+    float *mlp_w, *mlp_norm, *mlp_m, *mlp_v, *mlp_grad;
+    double *mlp_loss;
+    bool mlp_ready;
+    int guess_mode, mlp_bf16;
+    float *log;
+    unsigned long long *log_count, *fallbacks;
+    long long log_max;
+    bool log_on;
 };
 
 namespace {
@@ -213,6 +224,11 @@ bgk_status run_qprime(bgk_ctx *ctx, const double *part, int n_vblk, int P, doubl
     a.iters = iters; a.status = ctx->status; a.stats = ctx->stats; a.P = P; a.Nu = ctx->Nu;
     a.tol = ctx->tol; a.max_iter = ctx->max_iter; a.gas = ctx->gas; a.vg = ctx->vg;
     a.mixed = ctx->precision == BGK_MIXED ? 1 : 0;
+    a.mlp.w = ctx->mlp_w; a.mlp.norm = ctx->mlp_norm;
+    a.guess_mode = (ctx->guess_mode == 1 && ctx->mlp_ready) ? 1 : 0;
+    a.mlp_bf16 = ctx->mlp_bf16;
+    a.log = ctx->log_on ? ctx->log : nullptr;
+    a.log_count = ctx->log_count; a.log_max = ctx->log_max; a.fallbacks = ctx->fallbacks;
     LaunchScope ls(ctx, BGK_K_QPRIME);
     CU(launch_qprime_f64(a, ctx->stream));
     return BGK_OK;
@@ -391,6 +407,17 @@ bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
     if (st == BGK_OK) cu(cudaMemcpyAsync(ctx->vtab32, v32.data(), v32.size() * sizeof(float4), cudaMemcpyHostToDevice, ctx->stream), "upload vtab32");
     if (st == BGK_OK) cu(cudaMalloc(&ctx->status, sizeof(unsigned int)), "cudaMalloc(status)");
     if (st == BGK_OK) cu(cudaMalloc(&ctx->stats, sizeof(NewtonStats)), "cudaMalloc(stats)");
+    if (st == BGK_OK) cu(cudaMalloc(&ctx->mlp_w, MLP_NPARAM * sizeof(float)), "cudaMalloc(mlp)");
+    if (st == BGK_OK) cu(cudaMalloc(&ctx->mlp_norm, MLP_NNORM * sizeof(float)), "cudaMalloc(mlp)");
+    if (st == BGK_OK) cu(cudaMalloc(&ctx->mlp_m, MLP_NPARAM * sizeof(float)), "cudaMalloc(mlp)");
+    if (st == BGK_OK) cu(cudaMalloc(&ctx->mlp_v, MLP_NPARAM * sizeof(float)), "cudaMalloc(mlp)");
+    if (st == BGK_OK) cu(cudaMalloc(&ctx->mlp_grad, MLP_NPARAM * sizeof(float)), "cudaMalloc(mlp)");
+    if (st == BGK_OK) cu(cudaMalloc(&ctx->mlp_loss, sizeof(double)), "cudaMalloc(mlp)");
+    if (st == BGK_OK) cu(cudaMalloc(&ctx->log_count, 2 * sizeof(unsigned long long)), "cudaMalloc(log)");
+    if (st == BGK_OK) {
+        ctx->fallbacks = ctx->log_count + 1;
+        cu(cudaMemsetAsync(ctx->log_count, 0, 2 * sizeof(unsigned long long), ctx->stream), "memset log");
+    }
     if (st == BGK_OK) cu(cudaMemcpyAsync(ctx->vtab, ctx->vtab_h.data(), ctx->vtab_h.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload vtab");
     if (st == BGK_OK) cu(cudaMemcpyAsync(ctx->bcval, bcv.data(), bcv.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload bc");
     if (st == BGK_OK) cu(cudaMemsetAsync(ctx->status, 0, sizeof(unsigned int), ctx->stream), "memset status");
@@ -411,6 +438,8 @@ bgk_status bgk_destroy(bgk_ctx *ctx) {
     cudaFree(ctx->part); cudaFree(ctx->mom); cudaFree(ctx->eq); cudaFree(ctx->qp);
     cudaFree(ctx->iters); cudaFree(ctx->vtab); cudaFree(ctx->vtab32); cudaFree(ctx->bcval); cudaFree(ctx->status);
     cudaFree(ctx->stats);
+    cudaFree(ctx->mlp_w); cudaFree(ctx->mlp_norm); cudaFree(ctx->mlp_m); cudaFree(ctx->mlp_v);
+    cudaFree(ctx->mlp_grad); cudaFree(ctx->mlp_loss); cudaFree(ctx->log); cudaFree(ctx->log_count);
     delete ctx;
     return BGK_OK;
 }
@@ -605,6 +634,211 @@ bgk_status bgk_totals(bgk_ctx *ctx, double totals[5]) {
         t[4] += W * (0.5 * (mm[4] + mm[5] + mm[6]) + mm[10]);
     }
     for (int j = 0; j < 5; ++j) totals[j] = t[j];
+    return BGK_OK;
+}
+
+// ---- learned guess ---------------------------------------------------------
+bgk_status bgk_set_guess(bgk_ctx *ctx, int mode, int bf16) {
+    if (!ctx || mode < 0 || mode > 1) return BGK_EINVAL;
+    if (mode == 1 && !ctx->mlp_ready) return fail(ctx, BGK_EINVAL, "no trained or loaded network");
+    ctx->guess_mode = mode;
+    ctx->mlp_bf16 = bf16 ? 1 : 0;
+    return BGK_OK;
+}
+
+bgk_status bgk_mlp_log(bgk_ctx *ctx, int enable, long long max_pairs) {
+    if (!ctx || (enable && max_pairs <= 0)) return BGK_EINVAL;
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (enable) {
+        if (max_pairs > ctx->log_max) {
+            CU(cudaFree(ctx->log));
+            ctx->log = nullptr;
+            CU(cudaMalloc(&ctx->log, (size_t)max_pairs * MLP_LOG_STRIDE * sizeof(float)));
+            ctx->log_max = max_pairs;
+        }
+        CU(cudaMemsetAsync(ctx->log_count, 0, sizeof(unsigned long long), ctx->stream));
+    }
+    ctx->log_on = enable != 0;
+    return BGK_OK;
+}
+
+static bgk_status log_count(bgk_ctx *ctx, long long *n) {
+    unsigned long long c = 0;
+    CU(cudaMemcpyAsync(&c, ctx->log_count, sizeof c, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    *n = std::min((long long)c, ctx->log_max);
+    return BGK_OK;
+}
+
+bgk_status bgk_mlp_log_read(bgk_ctx *ctx, float *out, long long max_pairs, long long *n_out) {
+    if (!ctx || !out || !n_out || max_pairs < 0) return BGK_EINVAL;
+    long long n;
+    bgk_status st = log_count(ctx, &n);
+    if (st) return st;
+    n = std::min(n, max_pairs);
+    if (n > 0)
+        CU(cudaMemcpyAsync(out, ctx->log, (size_t)n * MLP_LOG_STRIDE * sizeof(float), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    *n_out = n;
+    return BGK_OK;
+}
+
+bgk_status bgk_mlp_weights(bgk_ctx *ctx, float *buf, int load) {
+    if (!ctx || !buf) return BGK_EINVAL;
+    if (load) {
+        CU(cudaMemcpyAsync(ctx->mlp_w, buf, MLP_NPARAM * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaMemcpyAsync(ctx->mlp_norm, buf + MLP_NPARAM, MLP_NNORM * sizeof(float), cudaMemcpyHostToDevice,
+                           ctx->stream));
+        ctx->mlp_ready = true;
+    } else {
+        if (!ctx->mlp_ready) return fail(ctx, BGK_EINVAL, "no trained or loaded network");
+        CU(cudaMemcpyAsync(buf, ctx->mlp_w, MLP_NPARAM * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaMemcpyAsync(buf + MLP_NPARAM, ctx->mlp_norm, MLP_NNORM * sizeof(float), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+    return BGK_OK;
+}
+
+// Upload x[n][9], t[n][5] (host) and run the training kernel over all n samples.
+static bgk_status mlp_batch_pass(bgk_ctx *ctx, const float *dx, const float *dt, const int *didx, int n,
+                                 int bf16) {
+    MlpParams p{ctx->mlp_w, ctx->mlp_norm};
+    LaunchScope ls(ctx, BGK_K_OTHER);
+    CU(launch_mlp_train(p, dx, dt, didx, n, ctx->mlp_grad, ctx->mlp_loss, bf16, ctx->stream));
+    return BGK_OK;
+}
+
+bgk_status bgk_mlp_grad(bgk_ctx *ctx, const float *x, const float *t, int n, int bf16, double *loss, float *grad) {
+    if (!ctx || !x || !t || n <= 0 || !loss || !grad) return BGK_EINVAL;
+    if (!ctx->mlp_ready) return fail(ctx, BGK_EINVAL, "no trained or loaded network");
+    float *dx = nullptr, *dt = nullptr;
+    int *didx = nullptr;
+    std::vector<int> idx(n);
+    for (int i = 0; i < n; ++i) idx[i] = i;
+    CU(cudaMallocAsync((void **)&dx, (size_t)n * MLP_IN * sizeof(float), ctx->stream));
+    CU(cudaMallocAsync((void **)&dt, (size_t)n * MLP_OUT * sizeof(float), ctx->stream));
+    CU(cudaMallocAsync((void **)&didx, (size_t)n * sizeof(int), ctx->stream));
+    CU(cudaMemcpyAsync(dx, x, (size_t)n * MLP_IN * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(dt, t, (size_t)n * MLP_OUT * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(didx, idx.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemsetAsync(ctx->mlp_grad, 0, MLP_NPARAM * sizeof(float), ctx->stream));
+    CU(cudaMemsetAsync(ctx->mlp_loss, 0, sizeof(double), ctx->stream));
+    bgk_status st = mlp_batch_pass(ctx, dx, dt, didx, n, bf16);
+    if (st) return st;
+    CU(cudaMemcpyAsync(grad, ctx->mlp_grad, MLP_NPARAM * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(loss, ctx->mlp_loss, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaFreeAsync(dx, ctx->stream));
+    CU(cudaFreeAsync(dt, ctx->stream));
+    CU(cudaFreeAsync(didx, ctx->stream));
+    CU(cudaMemsetAsync(ctx->mlp_grad, 0, MLP_NPARAM * sizeof(float), ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return BGK_OK;
+}
+
+bgk_status bgk_mlp_train(bgk_ctx *ctx, int epochs, int batch, float lr, unsigned long long seed, int bf16,
+                         double *final_loss) {
+    if (!ctx || epochs <= 0 || batch <= 0 || !(lr > 0.f)) return BGK_EINVAL;
+    long long n;
+    bgk_status st = log_count(ctx, &n);
+    if (st) return st;
+    if (n < batch) return fail(ctx, BGK_EINVAL, "only %lld logged pairs for batch %d", n, batch);
+    if (n > (1ll << 30)) n = 1ll << 30;
+    // pairs to host: normalisation statistics and the split into x and t
+    std::vector<float> pairs((size_t)n * MLP_LOG_STRIDE);
+    CU(cudaMemcpyAsync(pairs.data(), ctx->log, pairs.size() * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    std::vector<double> mean(MLP_LOG_STRIDE, 0.0), var(MLP_LOG_STRIDE, 0.0);
+    for (long long i = 0; i < n; ++i)
+        for (int j = 0; j < MLP_LOG_STRIDE; ++j) mean[j] += pairs[(size_t)i * MLP_LOG_STRIDE + j];
+    for (int j = 0; j < MLP_LOG_STRIDE; ++j) mean[j] /= (double)n;
+    for (long long i = 0; i < n; ++i)
+        for (int j = 0; j < MLP_LOG_STRIDE; ++j) {
+            const double d = pairs[(size_t)i * MLP_LOG_STRIDE + j] - mean[j];
+            var[j] += d * d;
+        }
+    std::vector<float> norm(MLP_NNORM), hx((size_t)n * MLP_IN), ht((size_t)n * MLP_OUT);
+    // Standard deviations get floors so that components that are constant up
+    // to round-off (e.g. a velocity component that is zero in the whole flow)
+    // are not blown up into unit-variance noise: 1e-6 of the feature's scale,
+    // 1e-7 absolute for the (dimensionless) targets.
+    for (int j = 0; j < MLP_LOG_STRIDE; ++j) {
+        double sd = std::sqrt(var[j] / (double)n);
+        const double floor = j < MLP_IN ? 1e-6 * std::max(std::fabs(mean[j]), 1.0) : 1e-7;
+        if (!(sd > floor)) sd = floor;
+        if (j < MLP_IN) { norm[j] = (float)mean[j]; norm[MLP_IN + j] = (float)sd; }
+        else { norm[2 * MLP_IN + (j - MLP_IN)] = (float)mean[j]; norm[2 * MLP_IN + MLP_OUT + (j - MLP_IN)] = (float)sd; }
+    }
+    for (long long i = 0; i < n; ++i) {
+        for (int j = 0; j < MLP_IN; ++j) hx[(size_t)i * MLP_IN + j] = pairs[(size_t)i * MLP_LOG_STRIDE + j];
+        for (int j = 0; j < MLP_OUT; ++j) ht[(size_t)i * MLP_OUT + j] = pairs[(size_t)i * MLP_LOG_STRIDE + MLP_IN + j];
+    }
+    // He-normal initialisation, zero biases
+    std::mt19937_64 rng(seed);
+    std::normal_distribution<double> nd(0.0, 1.0);
+    std::vector<float> w(MLP_NPARAM, 0.f);
+    const int fan[3][2] = {{MLP_IN, MLP_H}, {MLP_H, MLP_H}, {MLP_H, MLP_OUT}};
+    size_t off = 0;
+    for (int l = 0; l < 3; ++l) {
+        const double sc = std::sqrt(2.0 / fan[l][0]);
+        for (int i = 0; i < fan[l][0] * fan[l][1]; ++i) w[off + i] = (float)(nd(rng) * sc);
+        off += (size_t)fan[l][0] * fan[l][1] + fan[l][1];
+    }
+    float *dx = nullptr, *dt = nullptr;
+    int *didx = nullptr;
+    CU(cudaMalloc(&dx, hx.size() * sizeof(float)));
+    CU(cudaMalloc(&dt, ht.size() * sizeof(float)));
+    CU(cudaMalloc(&didx, (size_t)n * sizeof(int)));
+    CU(cudaMemcpyAsync(dx, hx.data(), hx.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(dt, ht.data(), ht.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->mlp_w, w.data(), MLP_NPARAM * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->mlp_norm, norm.data(), MLP_NNORM * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemsetAsync(ctx->mlp_m, 0, MLP_NPARAM * sizeof(float), ctx->stream));
+    CU(cudaMemsetAsync(ctx->mlp_v, 0, MLP_NPARAM * sizeof(float), ctx->stream));
+    CU(cudaMemsetAsync(ctx->mlp_grad, 0, MLP_NPARAM * sizeof(float), ctx->stream));
+    ctx->mlp_ready = true;
+    std::vector<int> perm((size_t)n);
+    for (long long i = 0; i < n; ++i) perm[i] = (int)i;
+    const long long nbatch = n / batch;
+    const long long total = (long long)epochs * nbatch;
+    long long step = 0;
+    double last = 0.0;
+    for (int ep = 0; ep < epochs; ++ep) {
+        std::shuffle(perm.begin(), perm.end(), rng);
+        CU(cudaMemcpyAsync(didx, perm.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaMemsetAsync(ctx->mlp_loss, 0, sizeof(double), ctx->stream));
+        for (long long b = 0; b < nbatch; ++b) {
+            st = mlp_batch_pass(ctx, dx, dt, didx + b * batch, batch, bf16);
+            if (st) break;
+            ++step;
+            const double frac = (double)(step - 1) / (double)std::max(1ll, total - 1);
+            const float lr_t = (float)(lr * (0.1 + 0.45 * (1.0 + std::cos(M_PI * frac))));
+            LaunchScope ls(ctx, BGK_K_OTHER);
+            cudaError_t e = launch_mlp_adam(ctx->mlp_w, ctx->mlp_m, ctx->mlp_v, ctx->mlp_grad, MLP_NPARAM, lr_t,
+                                            0.9f, 0.999f, 1e-8f, (int)step, ctx->stream);
+            if (e != cudaSuccess) { st = fail(ctx, BGK_ECUDA, "adam: %s", cudaGetErrorString(e)); break; }
+        }
+        if (st) break;
+        double ls_sum = 0.0;
+        cudaMemcpyAsync(&ls_sum, ctx->mlp_loss, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+        cudaStreamSynchronize(ctx->stream);
+        last = ls_sum / (double)nbatch;
+    }
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(dx);
+    cudaFree(dt);
+    cudaFree(didx);
+    if (st) return st;
+    if (final_loss) *final_loss = last;
+    return BGK_OK;
+}
+
+bgk_status bgk_mlp_stats(bgk_ctx *ctx, unsigned long long *fallbacks) {
+    if (!ctx || !fallbacks) return BGK_EINVAL;
+    CU(cudaMemcpyAsync(fallbacks, ctx->fallbacks, sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemsetAsync(ctx->fallbacks, 0, sizeof(unsigned long long), ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
     return BGK_OK;
 }
 

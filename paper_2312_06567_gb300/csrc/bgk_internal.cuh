@@ -7,6 +7,8 @@
 #include <cstddef>
 #include <cstdint>
 
+#include "bgk_mlp.cuh"
+
 #define BGK_MAXQ 5          // FR order p <= 4
 #define BGK_NMOM 11         // raw moment slots per point
 #define BGK_NEQ 20          // equilibrium record per point (12 used by the FP64 form)
@@ -126,6 +128,14 @@ struct QPrimeArgs {
     GasInfo gas;
     VelGrid vg;
     int mixed;               // also fit the FP32-equilibrium moment correction
+    // learned initial guess and the training log
+    MlpParams mlp;
+    int guess_mode;          // 0: start from q, 1: start from the network's guess
+    int mlp_bf16;
+    float *log;              // [log_max][MLP_LOG_STRIDE] (features, Delta) of converged solves
+    unsigned long long *log_count;
+    long long log_max;
+    unsigned long long *fallbacks;   // guesses rejected (restart from q)
 };
 
 struct MomentArgs64 {

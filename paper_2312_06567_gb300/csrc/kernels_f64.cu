@@ -226,16 +226,51 @@ __global__ void __launch_bounds__(256) k_qprime_f64(QPrimeArgs a) {
     }
     __syncwarp();
 
+    // features of the learned guess: rho, U, theta, invariants of A = Pi/(rho theta), lambda
+    float feat[MLP_IN];
+    {
+        const double ia = 1.0 / (rho * theta);
+        const double a11 = (m[4] - rho * U0[0] * U0[0]) * ia, a22 = (m[5] - rho * U0[1] * U0[1]) * ia;
+        const double a33 = (m[6] - rho * U0[2] * U0[2]) * ia, a12 = (m[7] - rho * U0[0] * U0[1]) * ia;
+        const double a13 = (m[8] - rho * U0[0] * U0[2]) * ia, a23 = (m[9] - rho * U0[1] * U0[2]) * ia;
+        const double tr = a11 + a22 + a33;
+        const double tr2 = a11 * a11 + a22 * a22 + a33 * a33 + 2.0 * (a12 * a12 + a13 * a13 + a23 * a23);
+        const double det = a11 * (a22 * a33 - a23 * a23) - a12 * (a12 * a33 - a23 * a13) +
+                           a13 * (a12 * a23 - a22 * a13);
+        feat[0] = (float)rho; feat[1] = (float)U0[0]; feat[2] = (float)U0[1]; feat[3] = (float)U0[2];
+        feat[4] = (float)theta; feat[5] = (float)tr; feat[6] = (float)(0.5 * (tr * tr - tr2));
+        feat[7] = (float)det;
+        feat[8] = (float)(mu / rho * sqrt(0.5 * kTwoPi * 0.5 / theta));   // sqrt(pi / (2 theta))
+    }
+
     // 3. Newton
     double x[5];
+    const double xq[5] = {rho, U0[0], U0[1], U0[2], theta};
+    bool from_guess = false;
     if (a.guess) {
 #pragma unroll
         for (int j = 0; j < 5; ++j) x[j] = a.guess[(size_t)p * 5 + j];
+    } else if (a.guess_mode == 1) {
+        float dg[MLP_OUT];
+        mlp_infer_warp(a.mlp, feat, dg, a.mlp_bf16, lane);
+        const double st = sqrt(theta);
+        x[0] = rho * (1.0 + dg[0]);
+        x[1] = U0[0] + st * dg[1]; x[2] = U0[1] + st * dg[2]; x[3] = U0[2] + st * dg[3];
+        x[4] = theta * (1.0 + dg[4]);
+        from_guess = true;
+        // a guess that leaves the admissible set falls back to q at once
+        if (!(x[0] > 0.0) || !(x[4] > 0.0)) {
+#pragma unroll
+            for (int j = 0; j < 5; ++j) x[j] = xq[j];
+            from_guess = false;
+            if (lane == 0 && a.fallbacks) atomicAdd(a.fallbacks, 1ull);
+        }
     } else {
-        x[0] = rho; x[1] = U0[0]; x[2] = U0[1]; x[3] = U0[2]; x[4] = theta;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) x[j] = xq[j];
     }
     const double hd = 0.5 * gs.delta;
-    int it = 0;
+    int it = 0, tot = 0;         // updates of the current solve / of all attempts
     bool conv = false;
     double res = 1.0e300;
     Sym3 A;
@@ -313,6 +348,16 @@ __global__ void __launch_bounds__(256) k_qprime_f64(QPrimeArgs a) {
         res = fmax(fabs(R[0]) * sc_rho,
                    fmax(fmax(fabs(R[1]), fmax(fabs(R[2]), fabs(R[3]))) * sc_mom, fabs(R[4]) * sc_E));
         if (res <= a.tol) { conv = true; break; }
+        // The learned guess is judged by its own residual: one that is not
+        // small (or a solve that runs out of updates from it) restarts from q.
+        if (from_guess && ((it == 0 && !(res <= 1e-3)) || it >= a.max_iter || !(res == res))) {
+#pragma unroll
+            for (int j = 0; j < 5; ++j) x[j] = xq[j];
+            from_guess = false;
+            it = 0;
+            if (lane == 0 && a.fallbacks) atomicAdd(a.fallbacks, 1ull);
+            continue;
+        }
         if (it >= a.max_iter || !(res == res)) break;
 
         // Jacobian: moment combinations of v = A c = A ut - A dl
@@ -450,6 +495,7 @@ __global__ void __launch_bounds__(256) k_qprime_f64(QPrimeArgs a) {
 #pragma unroll
         for (int j = 0; j < 5; ++j) x[j] = fma(lam, dx[j], x[j]);
         ++it;
+        ++tot;
     }
 
     // Mixed form: the stage evaluates the equilibrium in FP32 (Eq32), whose
@@ -533,7 +579,7 @@ __global__ void __launch_bounds__(256) k_qprime_f64(QPrimeArgs a) {
 #pragma unroll
             for (int j = 0; j < 5; ++j) a.qp[(size_t)p * 5 + j] = x[j];
         }
-        if (a.iters) a.iters[p] = it;
+        if (a.iters) a.iters[p] = tot;
         if (a.eq) {
             double *q = a.eq + (size_t)p * BGK_NEQ;
             q[0] = c0; q[1] = x[1]; q[2] = x[2]; q[3] = x[3];
@@ -545,10 +591,24 @@ __global__ void __launch_bounds__(256) k_qprime_f64(QPrimeArgs a) {
             q[17] = U0[0]; q[18] = U0[1]; q[19] = U0[2];
         }
         if (!conv) atomicOr(a.status, BGK_DEV_NOCONV);
+        if (a.log && conv) {
+            const unsigned long long slot = atomicAdd(a.log_count, 1ull);
+            if ((long long)slot < a.log_max) {
+                float *r = a.log + (size_t)slot * MLP_LOG_STRIDE;
+#pragma unroll
+                for (int f = 0; f < MLP_IN; ++f) r[f] = feat[f];
+                const double st = sqrt(theta);
+                r[MLP_IN + 0] = (float)(x[0] / rho - 1.0);
+                r[MLP_IN + 1] = (float)((x[1] - U0[0]) / st);
+                r[MLP_IN + 2] = (float)((x[2] - U0[1]) / st);
+                r[MLP_IN + 3] = (float)((x[3] - U0[2]) / st);
+                r[MLP_IN + 4] = (float)(x[4] / theta - 1.0);
+            }
+        }
         if (a.stats) {
-            atomicAdd(&a.stats->iter_sum, (unsigned long long)it);
+            atomicAdd(&a.stats->iter_sum, (unsigned long long)tot);
             atomicAdd(&a.stats->solves, 1ull);
-            atomicMax(&a.stats->iter_max, it);
+            atomicMax(&a.stats->iter_max, tot);
             atomic_max_nonneg_double(&a.stats->res_max_bits, res);
         }
     }

@@ -1,0 +1,71 @@
+"""Pins of the FP64 reference MLP: analytic backprop vs central differences,
+SiLU closed forms, feature/target definitions against their special cases."""
+import numpy as np
+import pytest
+
+from oracle import bgk, mlp
+from oracle.velocity import VelocityGrid
+
+
+def test_silu_closed_forms():
+    z = np.array([-3.0, -0.5, 0.0, 0.7, 4.0])
+    assert np.allclose(mlp.silu(z), z / (1 + np.exp(-z)), rtol=0, atol=0)
+    assert mlp.silu(np.array([0.0]))[0] == 0.0
+    assert mlp.silu_grad(np.array([0.0]))[0] == pytest.approx(0.5, abs=1e-16)
+    h = 1e-6
+    assert np.allclose(mlp.silu_grad(z), (mlp.silu(z + h) - mlp.silu(z - h)) / (2 * h), atol=1e-9)
+
+
+def test_backprop_matches_central_differences():
+    rng = np.random.default_rng(0)
+    params = mlp.init_params(3)
+    xn = rng.standard_normal((7, 9))
+    tn = rng.standard_normal((7, 5))
+    loss, grads = mlp.loss_and_grads(params, xn, tn)
+    for pi, (p, g) in enumerate(zip(params, grads)):
+        flat = p.reshape(-1)
+        idx = rng.choice(flat.size, size=min(12, flat.size), replace=False)
+        for i in idx:
+            old = flat[i]
+            h = 1e-6 * max(1.0, abs(old))
+            flat[i] = old + h
+            lp, _ = mlp.loss_and_grads(params, xn, tn)
+            flat[i] = old - h
+            lm, _ = mlp.loss_and_grads(params, xn, tn)
+            flat[i] = old
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - g.reshape(-1)[i]) <= 1e-7 * max(1.0, abs(fd)), (pi, i)
+
+
+def test_linear_special_case():
+    """With W1 = W2 = 0 the network is the constant b3 + silu(b2) W3."""
+    params = mlp.init_params(1)
+    params[0][:] = 0
+    params[2][:] = 0
+    params[3][:] = 0.3
+    y, _ = mlp.forward(params, np.random.default_rng(2).standard_normal((4, 9)))
+    expect = mlp.silu(np.full(64, 0.3)) @ params[4] + params[5]
+    assert np.allclose(y, expect[None, :], atol=1e-14)
+
+
+def test_features_and_target_special_cases():
+    """Isotropic sampled Maxwellian: A = I (I1 = 3, I2 = 3, I3 = 1) on a fine grid,
+    and the target of q' = q is zero; guess() inverts target()."""
+    vg = VelocityGrid((26, 26, 26), (-8, -8, -8), (8, 8, 8))
+    gas = bgk.Gas(delta=0.0, Pr=1.0, mu_ref=0.1, theta_ref=1.0, theta_S=0.5)
+    rho = np.array([1.2, 0.8])
+    U = np.array([[0.1, -0.2, 0.3], [0.0, 0.4, 0.0]])
+    th = np.array([1.1, 0.9])
+    m = bgk.raw_moments(bgk.maxwellian(vg, rho, U, th), None, vg)
+    x = mlp.features(m, gas)
+    assert np.allclose(x[:, 0], rho, rtol=1e-12) and np.allclose(x[:, 1:4], U, atol=1e-12)
+    assert np.allclose(x[:, 4], th, rtol=1e-11)
+    assert np.allclose(x[:, 5], 3.0, atol=1e-10) and np.allclose(x[:, 6], 3.0, atol=1e-10)
+    assert np.allclose(x[:, 7], 1.0, atol=1e-10)
+    lam = gas.viscosity(th) / rho * np.sqrt(np.pi / (2 * th))
+    assert np.allclose(x[:, 8], lam, rtol=1e-11)
+    r, Um, E, theta, P, Pi = bgk.macroscopic(m, gas)
+    qp = np.concatenate([r[:, None], Um, theta[:, None]], axis=1)
+    assert np.allclose(mlp.target(m, qp, gas), 0.0, atol=1e-15)
+    d = np.random.default_rng(5).standard_normal((2, 5)) * 1e-3
+    assert np.allclose(mlp.target(m, mlp.guess(m, d, gas), gas), d, atol=1e-14)
