@@ -262,35 +262,48 @@ def stage_bytes_per_dof(C, elem):
     return C * elem * (2 + 3 + 3) / 3.0
 
 
-def roofline_stage_hbm(wl, r, peaks, elem):
-    ms, n = r["prof"]["stage"]
-    per = ms / max(n, 1)
-    bytes_ = wl.dof * stage_bytes_per_dof(wl.n_comp, elem)
-    achieved = bytes_ / (per * 1e-3) / 1e9
-    return {"bound": "hbm", "kernel": "stage", "achieved": achieved, "peak": peaks["hbm_gbs"],
-            "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None, "ms": per}
+def qprime_ops_per_dof_eval_fp32(n1):
+    """FP32 operations of one evaluation per velocity in the FP32-sum engine:
+    ratio recurrence 2, on-the-fly monomials 3, five line sums 5, weight
+    select 1; per line (n1 velocities) the fold into 35 moments (35 FMA = 70
+    flops + 30 for prefactors) and the anchors."""
+    return 2 * (2 + 3 + 5 + 1) + (70.0 + 30.0 + 9.0) / n1
 
 
-def roofline_fp64(wl, r, peaks, steps):
-    """Dominant kernel of the FP64 form against the measured FP64 pipe."""
-    p64 = peaks["fp64_fma"]
+def kernel_rooflines(wl, r, peaks, form):
+    """Per-kernel roofline of one form: algorithmic work / event-timed launch
+    duration against the pipe or memory that bounds it."""
     prof = r["prof"]
-    k_stage_ms, n_stage = prof["stage"]
-    k_q_ms, n_q = prof["qprime"]
-    dof = wl.dof
-    stage_fl = dof * stage_flops_per_dof(wl.p, wl.n_comp)
-    evals = r["newton"]["mean_iters"] + 1.0                 # updates + the final check
-    q_fl = dof * evals * qprime_flops_per_dof_eval(wl.vel_n[0])
-    cand = {"stage": (stage_fl, k_stage_ms / max(n_stage, 1)),
-            "qprime": (q_fl, k_q_ms / max(n_q, 1))}
-    name = max(cand, key=lambda k: cand[k][1])
-    fl, ms = cand[name]
-    achieved = fl / (ms * 1e-3) / 1e12
-    return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": p64 / 1e12,
-            "unit": "TFLOP/s", "frac": achieved / (p64 / 1e12), "traffic": None,
-            "peak_source": "measured FP64 FMA throughput (bgk_probe_peak) on this GPU",
-            "other": {k: {"tflops": cand[k][0] / (cand[k][1] * 1e-3) / 1e12, "ms": cand[k][1]}
-                      for k in cand}}
+    out = {}
+    evals = r["newton"]["mean_iters"] + 1.0           # updates + the converged check
+    ms_s = prof["stage"][0] / max(prof["stage"][1], 1)
+    ms_q = prof["qprime"][0] / max(prof["qprime"][1], 1)
+    if form == "fp64":
+        fl = wl.dof * stage_flops_per_dof(wl.p, wl.n_comp)
+        out["stage"] = {"bound": "alu", "kernel": "stage", "pipe": "fp64", "achieved": fl / (ms_s * 1e-3) / 1e12,
+                        "peak": peaks["fp64_fma"] / 1e12, "unit": "TFLOP/s", "ms": ms_s}
+        fl = wl.dof * evals * qprime_flops_per_dof_eval(wl.vel_n[0])
+        out["qprime"] = {"bound": "alu", "kernel": "qprime", "pipe": "fp64", "achieved": fl / (ms_q * 1e-3) / 1e12,
+                         "peak": peaks["fp64_fma"] / 1e12, "unit": "TFLOP/s", "ms": ms_q}
+    else:
+        by = wl.dof * stage_bytes_per_dof(wl.n_comp, 4)
+        out["stage"] = {"bound": "hbm", "kernel": "stage", "achieved": by / (ms_s * 1e-3) / 1e9,
+                        "peak": peaks["hbm_gbs"], "unit": "GB/s", "ms": ms_s}
+        fl = wl.dof * evals * qprime_ops_per_dof_eval_fp32(wl.vel_n[0])
+        out["qprime"] = {"bound": "alu", "kernel": "qprime", "pipe": "fp32", "achieved": fl / (ms_q * 1e-3) / 1e12,
+                         "peak": peaks["fp32_fma"] / 1e12, "unit": "TFLOP/s", "ms": ms_q}
+    for v in out.values():
+        v["frac"] = v["achieved"] / v["peak"]
+        v["traffic"] = None
+    return out
+
+
+def dominant_roofline(rl):
+    k = max(rl, key=lambda n: rl[n]["ms"])
+    d = dict(rl[k])
+    d["peak_source"] = ("MEASURED_PEAKS.json hbm_gbs" if d["bound"] == "hbm"
+                        else "measured %s FMA throughput (bgk_probe_peak) on this GPU" % d.get("pipe", ""))
+    return d
 
 
 def _measured_hbm():
@@ -366,9 +379,9 @@ def main():
         "status": r["status"],
         "peaks_measured": peaks,
     }
-    line["roofline"] = roofline_fp64(wl, r, peaks, args.steps)
-    if main_form.startswith("mixed"):
-        line["roofline_stage_kernel"] = roofline_stage_hbm(wl, r, peaks, 4)
+    rl = kernel_rooflines(wl, r, peaks, main_form)
+    line["roofline"] = dominant_roofline(rl)
+    line["roofline_kernels"] = rl
     for form, rr in results.items():
         if form != main_form:
             line[form] = {"value": world * wl.dof * 3 * args.steps / (rr["ms"] * 1e-3),
@@ -376,7 +389,7 @@ def main():
                           "kernels_ms": {k: v[0] for k, v in rr["prof"].items()},
                           "newton": rr["newton"], "e2e": rr["e2e"],
                           "conservation_drift_per_step": rr["drift"],
-                          "roofline": roofline_fp64(wl, rr, peaks, args.steps),
+                          "roofline_kernels": kernel_rooflines(wl, rr, peaks, form),
                           "clocks": rr["clocks"]}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)

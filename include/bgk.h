@@ -119,6 +119,16 @@ BGK_API bgk_status bgk_set_maxwellian(bgk_ctx *ctx, const double *q, int on_devi
  * max_iter updates (defaults 1e-13, 50). */
 BGK_API bgk_status bgk_set_newton(bgk_ctx *ctx, double tol, int max_iter);
 
+/* Engine of the Q' velocity sums.  fp32_sums = 0: FP64 throughout (the FP64
+ * form, and optionally the mixed form).  fp32_sums = 1 (mixed form only, its
+ * default): the velocity sums of the Newton iteration run on the FP32 pipe
+ * (GB300 issues FP64 at 1/64 of the FP32 rate), the per-point Newton algebra
+ * in FP64, stopping at a scaled residual of 1e-6; the discrete compatibility
+ * of the equilibrium actually used is then restored by the FP32-equilibrium
+ * moment correction, which measures its moments with exact compensated sums
+ * against the moments of f.  Errors: BGK_EINVAL for fp32_sums on the FP64 form. */
+BGK_API bgk_status bgk_set_qprime_engine(bgk_ctx *ctx, int fp32_sums);
+
 /* One residual R(f) = -div(u f) + (g(Q') - f)/tau of f_in into r_out (both
  * with the state's layout and element type).  Test and debug entry; it
  * leaves the state unchanged. */

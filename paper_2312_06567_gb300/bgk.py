@@ -46,6 +46,7 @@ SIGNATURES = {
     "bgk_get_state": (c_int, [c_void_p, c_void_p, c_int]),
     "bgk_set_maxwellian": (c_int, [c_void_p, c_void_p, c_int]),
     "bgk_set_newton": (c_int, [c_void_p, c_double, c_int]),
+    "bgk_set_qprime_engine": (c_int, [c_void_p, c_int]),
     "bgk_rhs": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
     "bgk_step": (c_int, [c_void_p, c_double, c_int]),
     "bgk_stage": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_double, c_double]),
@@ -240,6 +241,9 @@ class Solver:
 
     def set_newton(self, tol=1e-13, max_iter=50):
         self._check(self.lib.bgk_set_newton(self._h, tol, max_iter))
+
+    def set_qprime_engine(self, fp32_sums):
+        self._check(self.lib.bgk_set_qprime_engine(self._h, 1 if fp32_sums else 0))
 
     def rhs(self, f, out=None):
         if isinstance(f, np.ndarray):

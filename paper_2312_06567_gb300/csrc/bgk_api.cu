@@ -44,6 +44,7 @@ struct bgk_ctx {
     bool part_valid;
     double tol;
     int max_iter;
+    int qp_fp32;                      // Q' velocity sums on the FP32 pipe (mixed form default)
     std::string err;
     // profiling: event pairs around launches, accumulated per kernel kind
     bool prof_on;
@@ -222,7 +223,7 @@ bgk_status run_qprime(bgk_ctx *ctx, const double *part, int n_vblk, int P, doubl
     QPrimeArgs a{};
     a.part = part; a.n_vblk = n_vblk; a.vtab = ctx->vtab; a.vtab32 = ctx->vtab32; a.guess = guess; a.eq = eq; a.qp = qp;
     a.iters = iters; a.status = ctx->status; a.stats = ctx->stats; a.P = P; a.Nu = ctx->Nu;
-    a.tol = ctx->tol; a.max_iter = ctx->max_iter; a.gas = ctx->gas; a.vg = ctx->vg;
+    a.tol = ctx->tol; a.tol32 = 1e-6; a.max_iter = ctx->max_iter; a.gas = ctx->gas; a.vg = ctx->vg;
     a.mixed = ctx->precision == BGK_MIXED ? 1 : 0;
     a.mlp.w = ctx->mlp_w; a.mlp.norm = ctx->mlp_norm;
     a.guess_mode = (ctx->guess_mode == 1 && ctx->mlp_ready) ? 1 : 0;
@@ -230,7 +231,7 @@ bgk_status run_qprime(bgk_ctx *ctx, const double *part, int n_vblk, int P, doubl
     a.log = ctx->log_on ? ctx->log : nullptr;
     a.log_count = ctx->log_count; a.log_max = ctx->log_max; a.fallbacks = ctx->fallbacks;
     LaunchScope ls(ctx, BGK_K_QPRIME);
-    CU(launch_qprime_f64(a, ctx->stream));
+    CU(launch_qprime(a, ctx->qp_fp32 != 0, ctx->stream));
     return BGK_OK;
 }
 
@@ -310,6 +311,7 @@ bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
     ctx->stream = (cudaStream_t)stream;
     ctx->tol = 1e-13;
     ctx->max_iter = 50;
+    ctx->qp_fp32 = precision == BGK_MIXED ? 1 : 0;
     for (int d = 0; d < 3; ++d) {
         ctx->vn[d] = vg->n[d];
         ctx->vg.n[d] = vg->n[d];
@@ -517,6 +519,14 @@ bgk_status bgk_set_maxwellian(bgk_ctx *ctx, const double *q, int on_device) {
     if (tmp) CU(cudaFreeAsync(tmp, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     ctx->part_valid = false;
+    return BGK_OK;
+}
+
+bgk_status bgk_set_qprime_engine(bgk_ctx *ctx, int fp32_sums) {
+    if (!ctx) return BGK_EINVAL;
+    if (fp32_sums && ctx->precision != BGK_MIXED)
+        return fail(ctx, BGK_EINVAL, "FP32 Q' sums are for the mixed form only");
+    ctx->qp_fp32 = fp32_sums ? 1 : 0;
     return BGK_OK;
 }
 

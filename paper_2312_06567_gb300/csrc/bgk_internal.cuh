@@ -123,7 +123,8 @@ struct QPrimeArgs {
     unsigned int *status;
     NewtonStats *stats;
     int P, Nu;
-    double tol;
+    double tol;              // stopping tolerance of the FP64 engine
+    double tol32;            // stopping tolerance of the FP32-sum engine
     int max_iter;
     GasInfo gas;
     VelGrid vg;
@@ -147,7 +148,7 @@ struct MomentArgs64 {
 
 // Launchers (kernels_f64.cu).
 cudaError_t launch_moments_f64(const MomentArgs64 &a, int n_vblk, cudaStream_t s);
-cudaError_t launch_qprime_f64(const QPrimeArgs &a, cudaStream_t s);
+cudaError_t launch_qprime(const QPrimeArgs &a, bool fp32_sums, cudaStream_t s);
 cudaError_t launch_stage_f64(const StageArgs<double> &a, int C, int n_vblk, cudaStream_t s);
 cudaError_t launch_maxwellian_f64(double *f, const double *q, const double *vtab, int Nu, int P,
                                   int C, double delta, cudaStream_t s);

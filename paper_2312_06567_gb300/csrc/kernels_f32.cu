@@ -17,12 +17,15 @@
 
 namespace {
 
-// Kahan step; the represented sum is s - comp.
-__device__ __forceinline__ void kahan_add(float &s, float &comp, float v) {
-    const float y = __fsub_rn(v, comp);
-    const float t = __fadd_rn(s, y);
-    comp = __fsub_rn(__fsub_rn(t, s), y);
+// Error-free accumulation (Ogita, Rump & Oishi 2005, "Sum2"): TwoSum keeps
+// the exact rounding error of each addition in comp; the represented sum is
+// s + comp, accurate to O(eps^2) of the sum of magnitudes.
+__device__ __forceinline__ void sum2(float &s, float &comp, float v) {
+    const float t = __fadd_rn(s, v);
+    const float bp = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp));
     s = t;
+    comp = __fadd_rn(comp, e);
 }
 
 // Index moments (J000, J100, J200, J010, J110, J020, J001, J101, J011, J002, JG)
@@ -58,14 +61,13 @@ __device__ __forceinline__ float folded_dt(const FROps &fr, int side, int i, int
 __device__ __forceinline__ float trap(int j, int n) { return (j == 0 || j == n - 1) ? 0.5f : 1.0f; }
 
 // Per-thread accumulator of index moments over a run of whole first-axis lines.
-// Line sums are Kahan sums of exact products (c F exact; c F jt and c F jt^2
-// split into product + FMA-exact error), their compensations kept; plane
-// sums are Kahan sums of the lines' (sum, compensation) pairs; planes fold in
-// FP64.  So the index moments carry FP32 rounding noise only far below
-// 2^-24 of the sums, and no bias.
+// Line sums are error-free (Sum2) sums of exact products (c F exact; c F jt
+// and c F jt^2 split into product + FMA-exact error); plane sums accumulate
+// the lines' (sum, error) pairs the same way; planes fold in FP64.  So the
+// index moments are accurate to O(2^-48) of the sums, with no bias.
 struct IndexMoments {
-    float L[4], Lc[4];                    // current line: 0, jt, jt^2, G (Kahan pairs)
-    float P[7], Pc[7];                    // current plane (Kahan): 00 10 20 01 11 02 G
+    float L[4], Lc[4];                    // current line: 0, jt, jt^2, G (sum, error) pairs
+    float P[7], Pc[7];                    // current plane: 00 10 20 01 11 02 G
     double J[11];
     int j3cur;
     __device__ void init() {
@@ -79,23 +81,23 @@ struct IndexMoments {
     }
     __device__ __forceinline__ void add(float cj1, float jt1, float F, float G) {
         const float cF = __fmul_rn(cj1, F);                 // exact: cj1 in {1/2, 1}
-        kahan_add(L[0], Lc[0], cF);
+        sum2(L[0], Lc[0], cF);
         const float p1 = __fmul_rn(cF, jt1);
-        kahan_add(L[1], Lc[1], p1);
-        Lc[1] = __fsub_rn(Lc[1], fmaf(cF, jt1, -p1));       // exact product error joins the compensation
+        sum2(L[1], Lc[1], p1);
+        Lc[1] = __fadd_rn(Lc[1], fmaf(cF, jt1, -p1));       // exact product error joins the error term
         const float jj = __fmul_rn(jt1, jt1);               // exact: |jt1| < 128
         const float p2 = __fmul_rn(cF, jj);
-        kahan_add(L[2], Lc[2], p2);
-        Lc[2] = __fsub_rn(Lc[2], fmaf(cF, jj, -p2));
-        kahan_add(L[3], Lc[3], __fmul_rn(cj1, G));
+        sum2(L[2], Lc[2], p2);
+        Lc[2] = __fadd_rn(Lc[2], fmaf(cF, jj, -p2));
+        sum2(L[3], Lc[3], __fmul_rn(cj1, G));
     }
     __device__ __forceinline__ void flush_plane(float c3, float jt3) {
         const double c = c3, t = jt3;
-        // Kahan: the compensated plane sum is P - Pc
-        const double P00 = (double)P[0] - (double)Pc[0], P10 = (double)P[1] - (double)Pc[1];
-        const double P20 = (double)P[2] - (double)Pc[2], P01 = (double)P[3] - (double)Pc[3];
-        const double P11 = (double)P[4] - (double)Pc[4], P02 = (double)P[5] - (double)Pc[5];
-        const double PG = (double)P[6] - (double)Pc[6];
+        // the plane sums are P + Pc
+        const double P00 = (double)P[0] + (double)Pc[0], P10 = (double)P[1] + (double)Pc[1];
+        const double P20 = (double)P[2] + (double)Pc[2], P01 = (double)P[3] + (double)Pc[3];
+        const double P11 = (double)P[4] + (double)Pc[4], P02 = (double)P[5] + (double)Pc[5];
+        const double PG = (double)P[6] + (double)Pc[6];
         // J_abc += c3 jt3^c P_ab
         J[0] = fma(c, P00, J[0]);
         J[1] = fma(c, P10, J[1]);
@@ -111,14 +113,13 @@ struct IndexMoments {
 #pragma unroll
         for (int i = 0; i < 7; ++i) P[i] = Pc[i] = 0.f;
     }
-    // add c * (s - comp) of a line pair into a plane Kahan pair, exactly up to
-    // the plane sum's own rounding (c is a small integer or half-integer)
-    __device__ __forceinline__ void plane_add(int i, float c, float sum, float comp) {
+    // add c * (sum + err) of a line pair into a plane pair, error-free up to
+    // O(eps^2) (c is a small integer or half-integer)
+    __device__ __forceinline__ void plane_add(int i, float c, float sum, float err) {
         const float ps = __fmul_rn(c, sum);
-        kahan_add(P[i], Pc[i], ps);
-        Pc[i] = __fsub_rn(Pc[i], fmaf(c, sum, -ps));
-        const float pc = __fmul_rn(c, comp);
-        kahan_add(P[i], Pc[i], -pc);
+        sum2(P[i], Pc[i], ps);
+        Pc[i] = __fadd_rn(Pc[i], fmaf(c, sum, -ps));
+        Pc[i] = fmaf(c, err, Pc[i]);
     }
     __device__ __forceinline__ void end_line(float c2, float jt2) {
         const float a = c2, b = __fmul_rn(c2, jt2), bb = __fmul_rn(__fmul_rn(c2, jt2), jt2);   // exact

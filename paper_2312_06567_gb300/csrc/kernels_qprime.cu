@@ -1,0 +1,733 @@
+// The Q' solve (Dzanic & Martinelli, arXiv 2312.06567, section "Numerical
+// method": the modified equilibrium whose discrete moments equal those of f,
+// found by Newton's method), one warp per solution point.
+//
+// Unknowns x = (rho', U', theta'); T'(theta') = theta'/Pr I + B with
+// B = (1 - 1/Pr) Pi/rho of f; g = rho'/sqrt(det(2 pi T')) exp(-c^T T'^-1 c/2),
+// c = u - U'.  Residual R = sum_k w_k psi~_k g_k - Q with
+// psi~ = (1, u, |u|^2/2 + delta theta'/2); analytic Jacobian
+//   dg/drho' = g/rho',  dg/dU' = g A c,  dg/dtheta' = g (|A c|^2 - tr A)/(2 Pr).
+// Velocity sums are organised by lines along the first velocity axis: lanes
+// take the n2*n3 lines, each line is walked outward from the node nearest
+// its own peak with the Gaussian ratio recurrence g_{j+1} = g_j r_j,
+// r_{j+1} = r_j exp(-A11 h1^2) (two exps per line; the walk only ever
+// decreases g, so tails underflow harmlessly), giving five line sums
+// T_m = sum_j w1 g ut1^m that fold into the 35 raw moments of order <= 4 in
+// coordinates ut = u - U centred on the point's macroscopic velocity; R and
+// J are linear combinations of those.
+//
+// Two engines for the velocity sums (k_qprime<F32>):
+//   Engine64  FP64 throughout (the FP64 form; parity with the oracle);
+//   Engine32  FP32 walk and fold (GB300's FP64 pipe issues 1/64 of the FP32
+//             rate), Newton algebra in FP64, converged to FP32 resolution.
+//             Used by the mixed form, whose conservation does not rest on
+//             this solve: see the correction pass below.
+// The mixed form's correction pass evaluates the exact FP32 equilibrium the
+// stage will use (Eq32), measures its moments with exact-product compensated
+// sums, and fits gamma so that g32 (1 + gamma . phi(ut)), phi = (1, ut,
+// |ut|^2/2), has exactly the moments of f: the discrete compatibility
+// condition then holds for the equilibrium actually used.
+#include "bgk_internal.cuh"
+
+namespace {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <int N>
+__device__ __forceinline__ void warp_sum_n(double (&v)[N]) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = warp_sum(v[i]);
+}
+
+__device__ __forceinline__ void atomic_max_nonneg_double(unsigned long long *addr, double v) {
+    if (!(v >= 0.0)) v = 1.0e300;      // NaN / negative: record as "huge"
+    atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+struct Sym3 {
+    double t11, t22, t33, t12, t13, t23;
+};
+
+__device__ __forceinline__ bool sym3_inverse(const Sym3 &t, Sym3 &inv, double &det) {
+    const double c11 = t.t22 * t.t33 - t.t23 * t.t23;
+    const double c12 = t.t13 * t.t23 - t.t12 * t.t33;
+    const double c13 = t.t12 * t.t23 - t.t13 * t.t22;
+    const double c22 = t.t11 * t.t33 - t.t13 * t.t13;
+    const double c23 = t.t12 * t.t13 - t.t11 * t.t23;
+    const double c33 = t.t11 * t.t22 - t.t12 * t.t12;
+    det = t.t11 * c11 + t.t12 * c12 + t.t13 * c13;
+    const bool spd = (t.t11 > 0.0) && (c33 > 0.0) && (det > 0.0);
+    const double r = 1.0 / det;
+    inv.t11 = c11 * r; inv.t22 = c22 * r; inv.t33 = c33 * r;
+    inv.t12 = c12 * r; inv.t13 = c13 * r; inv.t23 = c23 * r;
+    return spd;
+}
+
+// Gaussian elimination with partial pivoting on a 5x5 system; compile-time
+// indices only so everything stays in registers.  Returns false if singular.
+__device__ __forceinline__ bool solve5(double J[5][5], double r[5]) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+        int piv = c;
+        double best = fabs(J[c][c]);
+#pragma unroll
+        for (int i = c + 1; i < 5; ++i) {
+            const double v = fabs(J[i][c]);
+            if (v > best) { best = v; piv = i; }
+        }
+        if (!(best > 0.0)) return false;
+#pragma unroll
+        for (int i = c + 1; i < 5; ++i) {
+            if (i == piv) {
+#pragma unroll
+                for (int j = 0; j < 5; ++j) {
+                    const double t = J[c][j]; J[c][j] = J[i][j]; J[i][j] = t;
+                }
+                const double t = r[c]; r[c] = r[i]; r[i] = t;
+            }
+        }
+        const double inv = 1.0 / J[c][c];
+#pragma unroll
+        for (int i = c + 1; i < 5; ++i) {
+            const double l = J[i][c] * inv;
+#pragma unroll
+            for (int j = c + 1; j < 5; ++j) J[i][j] = fma(-l, J[c][j], J[i][j]);
+            r[i] = fma(-l, r[c], r[i]);
+        }
+    }
+#pragma unroll
+    for (int c = 4; c >= 0; --c) {
+        double s = r[c];
+#pragma unroll
+        for (int j = c + 1; j < 5; ++j) s = fma(-J[c][j], r[j], s);
+        r[c] = s / J[c][c];
+    }
+    return true;
+}
+
+// Index of the centred raw moment sum w g ut1^p1 ut2^p2 ut3^p3 (p1+p2+p3 <= 4)
+// in the 35-slot accumulator; the slots run over (p2, p3, p1) in that order.
+__host__ __device__ constexpr int midx(int p1, int p2, int p3) {
+    int idx = 0;
+    for (int a = 0; a <= 4; ++a)
+        for (int b = 0; b <= 4 - a; ++b)
+            for (int m = 0; m <= 4 - a - b; ++m) {
+                if (a == p2 && b == p3 && m == p1) return idx;
+                ++idx;
+            }
+    return -1;
+}
+
+// ---- per-point state shared by both engines ---------------------------------
+struct PointState {
+    double m[BGK_NMOM];
+    double rho, U0[3], E, Eth, theta, mu, tau, hU2;
+    double sc_rho, sc_mom, sc_E;
+    Sym3 B;
+    float feat[MLP_IN];
+};
+
+__device__ __forceinline__ void point_prologue(const QPrimeArgs &a, int p, int lane, PointState &ps) {
+#pragma unroll
+    for (int j = 0; j < BGK_NMOM; ++j) ps.m[j] = 0.0;
+    for (int vb = lane; vb < a.n_vblk; vb += 32) {
+#pragma unroll
+        for (int j = 0; j < BGK_NMOM; ++j) ps.m[j] += a.part[((size_t)vb * BGK_NMOM + j) * a.P + p];
+    }
+    warp_sum_n(ps.m);
+    const double *m = ps.m;
+    const GasInfo &gs = a.gas;
+    const double rho = m[0];
+    ps.rho = rho;
+    ps.U0[0] = m[1] / rho; ps.U0[1] = m[2] / rho; ps.U0[2] = m[3] / rho;
+    const double *U0 = ps.U0;
+    ps.E = 0.5 * (m[4] + m[5] + m[6]) + m[10];
+    ps.hU2 = 0.5 * (U0[0] * U0[0] + U0[1] * U0[1] + U0[2] * U0[2]);
+    ps.Eth = ps.E - rho * ps.hU2;
+    const double pres = (gs.gamma - 1.0) * ps.Eth;
+    ps.theta = pres / rho;
+    const double es = (1.0 - 1.0 / gs.Pr) / rho;
+    ps.B.t11 = es * (m[4] - rho * U0[0] * U0[0]);
+    ps.B.t22 = es * (m[5] - rho * U0[1] * U0[1]);
+    ps.B.t33 = es * (m[6] - rho * U0[2] * U0[2]);
+    ps.B.t12 = es * (m[7] - rho * U0[0] * U0[1]);
+    ps.B.t13 = es * (m[8] - rho * U0[0] * U0[2]);
+    ps.B.t23 = es * (m[9] - rho * U0[1] * U0[2]);
+    ps.mu = gs.mu_ref;
+    if (gs.theta_S >= 0.0) {
+        const double r = ps.theta / gs.theta_ref;
+        ps.mu = gs.mu_ref * r * sqrt(r) * (gs.theta_ref + gs.theta_S) / (ps.theta + gs.theta_S);
+    }
+    ps.tau = ps.mu / (gs.Pr * pres);
+    ps.sc_rho = 1.0 / rho;
+    ps.sc_mom = 1.0 / (rho * sqrt(ps.theta));
+    ps.sc_E = 1.0 / fabs(ps.E);
+    // features of the learned guess: rho, U, theta, invariants of A = Pi/(rho theta), lambda
+    const double ia = 1.0 / (rho * ps.theta);
+    const double a11 = (m[4] - rho * U0[0] * U0[0]) * ia, a22 = (m[5] - rho * U0[1] * U0[1]) * ia;
+    const double a33 = (m[6] - rho * U0[2] * U0[2]) * ia, a12 = (m[7] - rho * U0[0] * U0[1]) * ia;
+    const double a13 = (m[8] - rho * U0[0] * U0[2]) * ia, a23 = (m[9] - rho * U0[1] * U0[2]) * ia;
+    const double tr = a11 + a22 + a33;
+    const double tr2 = a11 * a11 + a22 * a22 + a33 * a33 + 2.0 * (a12 * a12 + a13 * a13 + a23 * a23);
+    const double det = a11 * (a22 * a33 - a23 * a23) - a12 * (a12 * a33 - a23 * a13) + a13 * (a12 * a23 - a22 * a13);
+    ps.feat[0] = (float)rho; ps.feat[1] = (float)U0[0]; ps.feat[2] = (float)U0[1]; ps.feat[3] = (float)U0[2];
+    ps.feat[4] = (float)ps.theta; ps.feat[5] = (float)tr; ps.feat[6] = (float)(0.5 * (tr * tr - tr2));
+    ps.feat[7] = (float)det;
+    ps.feat[8] = (float)(ps.mu / rho * sqrt(0.5 * kTwoPi * 0.5 / ps.theta));   // sqrt(pi / (2 theta))
+}
+
+// Newton's starting point: a supplied guess, the network's, or q.
+__device__ __forceinline__ bool initial_guess(const QPrimeArgs &a, int p, int lane, const PointState &ps, double x[5]) {
+    const double xq[5] = {ps.rho, ps.U0[0], ps.U0[1], ps.U0[2], ps.theta};
+    if (a.guess) {
+#pragma unroll
+        for (int j = 0; j < 5; ++j) x[j] = a.guess[(size_t)p * 5 + j];
+        return false;
+    }
+    if (a.guess_mode == 1) {
+        float dg[MLP_OUT];
+        mlp_infer_warp(a.mlp, ps.feat, dg, a.mlp_bf16, lane);
+        const double st = sqrt(ps.theta);
+        x[0] = ps.rho * (1.0 + dg[0]);
+        x[1] = ps.U0[0] + st * dg[1]; x[2] = ps.U0[1] + st * dg[2]; x[3] = ps.U0[2] + st * dg[3];
+        x[4] = ps.theta * (1.0 + dg[4]);
+        if (x[0] > 0.0 && x[4] > 0.0) return true;
+        if (lane == 0 && a.fallbacks) atomicAdd(a.fallbacks, 1ull);   // left the admissible set
+    }
+#pragma unroll
+    for (int j = 0; j < 5; ++j) x[j] = xq[j];
+    return false;
+}
+
+// A = T'^-1, c0 = ln rho' - ln sqrt(det(2 pi T')) at x.
+__device__ __forceinline__ void equilibrium_params(const PointState &ps, double Pr, const double x[5], Sym3 &A,
+                                                   double &c0) {
+    Sym3 T = ps.B;
+    T.t11 += x[4] / Pr; T.t22 += x[4] / Pr; T.t33 += x[4] / Pr;
+    double det;
+    sym3_inverse(T, A, det);
+    c0 = log(x[0]) - 0.5 * log(kTwoPi * kTwoPi * kTwoPi * det);
+}
+
+// Residual (returns the scaled norm) and, if J != nullptr, the Jacobian, from
+// the 35 centred moments M of g(x).
+__device__ __forceinline__ double assemble(const double M[35], const PointState &ps, const GasInfo &gs,
+                                           const double x[5], const Sym3 &A, double R[5], double (*J)[5]) {
+#define MM(p1, p2, p3) M[midx(p1, p2, p3)]
+    const double *U0 = ps.U0;
+    const double hd = 0.5 * gs.delta;
+    const double dl[3] = {x[1] - U0[0], x[2] - U0[1], x[3] - U0[2]};
+    const double M0 = MM(0, 0, 0);
+    const double Me[3] = {MM(1, 0, 0), MM(0, 1, 0), MM(0, 0, 1)};
+    const double Se = 0.5 * (MM(2, 0, 0) + MM(0, 2, 0) + MM(0, 0, 2));
+    const double eint = hd * x[4];
+    const double dM0 = M0 - ps.rho;
+    const double UMe = U0[0] * Me[0] + U0[1] * Me[1] + U0[2] * Me[2];
+    R[0] = dM0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) R[1 + d] = fma(U0[d], dM0, Me[d]);
+    R[4] = Se + UMe + ps.hU2 * dM0 + eint * M0 - ps.Eth;
+    const double res = fmax(fabs(R[0]) * ps.sc_rho,
+                            fmax(fmax(fabs(R[1]), fmax(fabs(R[2]), fabs(R[3]))) * ps.sc_mom, fabs(R[4]) * ps.sc_E));
+    if (!J) return res;
+    // Jacobian: moment combinations of v = A c = A ut - A dl
+    const double Am[3][3] = {{A.t11, A.t12, A.t13}, {A.t12, A.t22, A.t23}, {A.t13, A.t23, A.t33}};
+    double bt[3];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) bt[f] = Am[f][0] * dl[0] + Am[f][1] * dl[1] + Am[f][2] * dl[2];
+    double A2[3][3], bb2[3];
+#pragma unroll
+    for (int e1 = 0; e1 < 3; ++e1) {
+#pragma unroll
+        for (int e2 = 0; e2 < 3; ++e2)
+            A2[e1][e2] = Am[e1][0] * Am[0][e2] + Am[e1][1] * Am[1][e2] + Am[e1][2] * Am[2][e2];
+        bb2[e1] = Am[e1][0] * bt[0] + Am[e1][1] * bt[1] + Am[e1][2] * bt[2];
+    }
+    const double s0 = bt[0] * bt[0] + bt[1] * bt[1] + bt[2] * bt[2];
+    double V[3], Vd[3][3], VE[3], W0, Wd[3], WE;
+#pragma unroll
+    for (int f = 0; f < 3; ++f) V[f] = Am[f][0] * Me[0] + Am[f][1] * Me[1] + Am[f][2] * Me[2] - bt[f] * M0;
+    double Mij[3][3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int e = 0; e < 3; ++e) Mij[d][e] = M[midx((d == 0) + (e == 0), (d == 1) + (e == 1), (d == 2) + (e == 2))];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int f = 0; f < 3; ++f)
+            Vd[d][f] = Am[f][0] * Mij[d][0] + Am[f][1] * Mij[d][1] + Am[f][2] * Mij[d][2] - bt[f] * Me[d];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+        double acc = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+#pragma unroll
+            for (int e = 0; e < 3; ++e)
+                acc += Am[f][e] * M[midx(2 * (d == 0) + (e == 0), 2 * (d == 1) + (e == 1), 2 * (d == 2) + (e == 2))];
+            acc -= bt[f] * Mij[d][d];
+        }
+        VE[f] = 0.5 * acc;
+    }
+    W0 = s0 * M0;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        W0 -= 2.0 * bb2[e] * Me[e];
+#pragma unroll
+        for (int e2 = 0; e2 < 3; ++e2) W0 += A2[e][e2] * Mij[e][e2];
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        double acc = s0 * Me[d];
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            acc -= 2.0 * bb2[e] * Mij[d][e];
+#pragma unroll
+            for (int e2 = 0; e2 < 3; ++e2)
+                acc += A2[e][e2] * M[midx((d == 0) + (e == 0) + (e2 == 0), (d == 1) + (e == 1) + (e2 == 1),
+                                          (d == 2) + (e == 2) + (e2 == 2))];
+        }
+        Wd[d] = acc;
+    }
+    {
+        double acc = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            acc += s0 * Mij[d][d];
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                acc -= 2.0 * bb2[e] * M[midx(2 * (d == 0) + (e == 0), 2 * (d == 1) + (e == 1), 2 * (d == 2) + (e == 2))];
+#pragma unroll
+                for (int e2 = 0; e2 < 3; ++e2)
+                    acc += A2[e][e2] * M[midx(2 * (d == 0) + (e == 0) + (e2 == 0), 2 * (d == 1) + (e == 1) + (e2 == 1),
+                                              2 * (d == 2) + (e == 2) + (e2 == 2))];
+            }
+        }
+        WE = 0.5 * acc;
+    }
+    const double trA = A.t11 + A.t22 + A.t33;
+    const double k2 = 0.5 / gs.Pr;
+    const double ir = 1.0 / x[0];
+    const double cE = ps.hU2 + eint;
+    J[0][0] = M0 * ir;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) J[1 + d][0] = fma(U0[d], M0, Me[d]) * ir;
+    J[4][0] = (Se + UMe + cE * M0) * ir;
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+        J[0][1 + f] = V[f];
+        double UV = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            J[1 + d][1 + f] = fma(U0[d], V[f], Vd[d][f]);
+            UV = fma(U0[d], Vd[d][f], UV);
+        }
+        J[4][1 + f] = VE[f] + UV + cE * V[f];
+    }
+    const double Z0 = W0 - trA * M0;
+    double Zd[3], UZ = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) { Zd[d] = Wd[d] - trA * Me[d]; UZ = fma(U0[d], Zd[d], UZ); }
+    const double ZE = WE - trA * Se;
+    J[0][4] = k2 * Z0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) J[1 + d][4] = k2 * fma(U0[d], Z0, Zd[d]);
+    J[4][4] = k2 * (ZE + UZ + cE * Z0) + hd * M0;
+#undef MM
+    return res;
+}
+
+// Newton update with step halving while rho', theta' <= 0 or T' is not SPD.
+__device__ __forceinline__ bool newton_update(double J[5][5], const double R[5], double x[5], const Sym3 &B,
+                                              double Pr) {
+    double dx[5] = {-R[0], -R[1], -R[2], -R[3], -R[4]};
+    if (!solve5(J, dx)) return false;
+#pragma unroll
+    for (int j = 0; j < 5; ++j)
+        if (!isfinite(dx[j])) return false;
+    double lam = 1.0;
+    for (int h = 0; h < 60; ++h) {
+        const double r0 = x[0] + lam * dx[0], t0 = x[4] + lam * dx[4];
+        Sym3 Tt = B;
+        Tt.t11 += t0 / Pr; Tt.t22 += t0 / Pr; Tt.t33 += t0 / Pr;
+        Sym3 dummy;
+        double dd;
+        if (r0 > 0.0 && t0 > 0.0 && sym3_inverse(Tt, dummy, dd)) break;
+        lam *= 0.5;
+    }
+#pragma unroll
+    for (int j = 0; j < 5; ++j) x[j] = fma(lam, dx[j], x[j]);
+    return true;
+}
+
+// ---- FP32-equilibrium moment correction (mixed form) ------------------------
+// Error-free accumulation (Ogita, Rump & Oishi 2005, "Sum2"): TwoSum keeps
+// the exact rounding error of each addition in c; the sum is s + c.
+__device__ __forceinline__ void sum2(float &s, float &c, float v) {
+    const float t = __fadd_rn(s, v);
+    const float bp = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp));
+    s = t;
+    c = __fadd_rn(c, e);
+}
+
+// Exact index moments J_abc = sum c g32 jt1^a jt2^b jt3^c of the stage's FP32
+// equilibrium (jt = j - jc centred indices, c the trapezoid factors), then
+// gamma from G gamma = T - S with T the centred moments of f itself.
+__device__ __forceinline__ void correction(const QPrimeArgs &a, int lane, const PointState &ps, double c0,
+                                           const double x[5], const Sym3 &A, const double Gsrc[35], double gam[5]) {
+    const VelGrid &vg = a.vg;
+    const int n1 = vg.n[0], n2 = vg.n[1], n3 = vg.n[2];
+    const int jc[3] = {(n1 - 1) / 2, (n2 - 1) / 2, (n3 - 1) / 2};
+    const double qd[10] = {c0, x[1], x[2], x[3], A.t11, A.t22, A.t33, A.t12, A.t13, A.t23};
+    Eq32 e32;
+    e32.load(qd);
+    // index moments J000 J100 J200 J010 J020 J001 J002 of this lane's lines (FP64)
+    double Jm[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int line = lane; line < n2 * n3; line += 32) {
+        const int j2 = line % n2, j3 = line / n2;
+        const float4 *vl32 = a.vtab32 + (size_t)line * n1;
+        float lin, cst;
+        e32.line(vl32[0].y, vl32[0].z, lin, cst);
+        float L0 = 0.f, C0 = 0.f, L1 = 0.f, C1 = 0.f, L2 = 0.f, C2 = 0.f;
+        float jt = (float)(-jc[0]);
+        for (int j1 = 0; j1 < n1; ++j1, jt += 1.f) {
+            const float g = e32.g(vl32[j1].x, lin, cst);
+            const float cg = (j1 == 0 || j1 == n1 - 1) ? __fmul_rn(0.5f, g) : g;     // exact
+            sum2(L0, C0, cg);
+            const float p1 = __fmul_rn(cg, jt);
+            sum2(L1, C1, p1);
+            C1 = __fadd_rn(C1, fmaf(cg, jt, -p1));                          // exact product error
+            const float jj = __fmul_rn(jt, jt);                             // exact
+            const float p2 = __fmul_rn(cg, jj);
+            sum2(L2, C2, p2);
+            C2 = __fadd_rn(C2, fmaf(cg, jj, -p2));
+        }
+        const double l0 = (double)L0 + (double)C0, l1 = (double)L1 + (double)C1, l2 = (double)L2 + (double)C2;
+        const double c23 = ((j2 == 0 || j2 == n2 - 1) ? 0.5 : 1.0) * ((j3 == 0 || j3 == n3 - 1) ? 0.5 : 1.0);
+        const double t2 = (double)(j2 - jc[1]), t3 = (double)(j3 - jc[2]);
+        Jm[0] = fma(c23, l0, Jm[0]);
+        Jm[1] = fma(c23, l1, Jm[1]);
+        Jm[2] = fma(c23, l2, Jm[2]);
+        Jm[3] = fma(c23 * t2, l0, Jm[3]);
+        Jm[4] = fma(c23 * t2 * t2, l0, Jm[4]);
+        Jm[5] = fma(c23 * t3, l0, Jm[5]);
+        Jm[6] = fma(c23 * t3 * t3, l0, Jm[6]);
+    }
+    warp_sum_n(Jm);
+    // S_i = sum w phi_i g32 in ut = u - U0 coordinates: u_d = uc_d + jt_d h_d
+    const double W = vg.h[0] * vg.h[1] * vg.h[2];
+    const double o[3] = {vg.lo[0] + jc[0] * vg.h[0] - ps.U0[0], vg.lo[1] + jc[1] * vg.h[1] - ps.U0[1],
+                         vg.lo[2] + jc[2] * vg.h[2] - ps.U0[2]};
+    const double J1[3] = {Jm[1], Jm[3], Jm[5]}, J2[3] = {Jm[2], Jm[4], Jm[6]};
+    double S[5];
+    S[0] = W * Jm[0];
+    double s4 = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        S[1 + d] = W * (o[d] * Jm[0] + vg.h[d] * J1[d]);
+        s4 += o[d] * o[d] * Jm[0] + 2.0 * o[d] * vg.h[d] * J1[d] + vg.h[d] * vg.h[d] * J2[d];
+    }
+    S[4] = 0.5 * W * s4;
+    // targets: the centred moments of f, with the G equilibrium's share of
+    // the energy (delta theta'/2 per unit mass) taken out of phi_4
+    const double *m = ps.m;
+    const double gfac = 0.5 * a.gas.delta * x[4];
+    double T[5];
+    T[0] = m[0];
+    T[1] = m[1] - ps.U0[0] * m[0];
+    T[2] = m[2] - ps.U0[1] * m[0];
+    T[3] = m[3] - ps.U0[2] * m[0];
+    T[4] = ps.Eth - gfac * m[0];
+    // G_ij = sum w phi_i phi_j g from the solve's moments (accuracy not critical)
+#define MM(p1, p2, p3) Gsrc[midx(p1, p2, p3)]
+    double Gm[5][5];
+    Gm[0][0] = MM(0, 0, 0);
+    Gm[0][1] = MM(1, 0, 0); Gm[0][2] = MM(0, 1, 0); Gm[0][3] = MM(0, 0, 1);
+    Gm[0][4] = 0.5 * (MM(2, 0, 0) + MM(0, 2, 0) + MM(0, 0, 2));
+#undef MM
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+#pragma unroll
+        for (int e = 0; e < 3; ++e)
+            Gm[1 + d][1 + e] = Gsrc[midx((d == 0) + (e == 0), (d == 1) + (e == 1), (d == 2) + (e == 2))];
+        double acc = 0.0;
+#pragma unroll
+        for (int e = 0; e < 3; ++e) acc += Gsrc[midx((d == 0) + 2 * (e == 0), (d == 1) + 2 * (e == 1), (d == 2) + 2 * (e == 2))];
+        Gm[1 + d][4] = 0.5 * acc;
+    }
+    {
+        double acc = 0.0;
+#pragma unroll
+        for (int e = 0; e < 3; ++e)
+#pragma unroll
+            for (int f = 0; f < 3; ++f)
+                acc += Gsrc[midx(2 * (e == 0) + 2 * (f == 0), 2 * (e == 1) + 2 * (f == 1), 2 * (e == 2) + 2 * (f == 2))];
+        Gm[4][4] = 0.25 * acc;
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+        for (int j = 0; j < i; ++j) Gm[i][j] = Gm[j][i];
+    double rhs[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) rhs[i] = T[i] - S[i];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) gam[i] = 0.0;
+    if (solve5(Gm, rhs)) {
+#pragma unroll
+        for (int i = 0; i < 5; ++i) gam[i] = isfinite(rhs[i]) ? rhs[i] : 0.0;
+    }
+}
+
+__device__ __forceinline__ void point_epilogue(const QPrimeArgs &a, int p, int lane, const PointState &ps,
+                                               const double x[5], const Sym3 &A, double c0, const double gam[5],
+                                               int tot, bool conv, double res) {
+    if (lane != 0) return;
+    const double hd = 0.5 * a.gas.delta;
+    if (a.qp) {
+#pragma unroll
+        for (int j = 0; j < 5; ++j) a.qp[(size_t)p * 5 + j] = x[j];
+    }
+    if (a.iters) a.iters[p] = tot;
+    if (a.eq) {
+        double *q = a.eq + (size_t)p * BGK_NEQ;
+        q[0] = c0; q[1] = x[1]; q[2] = x[2]; q[3] = x[3];
+        q[4] = A.t11; q[5] = A.t22; q[6] = A.t33; q[7] = A.t12; q[8] = A.t13; q[9] = A.t23;
+        q[10] = 1.0 / ps.tau;
+        q[11] = hd * x[4];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) q[12 + i] = gam[i];
+        q[17] = ps.U0[0]; q[18] = ps.U0[1]; q[19] = ps.U0[2];
+    }
+    if (!conv) atomicOr(a.status, BGK_DEV_NOCONV);
+    if (a.log && conv) {
+        const unsigned long long slot = atomicAdd(a.log_count, 1ull);
+        if ((long long)slot < a.log_max) {
+            float *r = a.log + (size_t)slot * MLP_LOG_STRIDE;
+#pragma unroll
+            for (int f = 0; f < MLP_IN; ++f) r[f] = ps.feat[f];
+            const double st = sqrt(ps.theta);
+            r[MLP_IN + 0] = (float)(x[0] / ps.rho - 1.0);
+            r[MLP_IN + 1] = (float)((x[1] - ps.U0[0]) / st);
+            r[MLP_IN + 2] = (float)((x[2] - ps.U0[1]) / st);
+            r[MLP_IN + 3] = (float)((x[3] - ps.U0[2]) / st);
+            r[MLP_IN + 4] = (float)(x[4] / ps.theta - 1.0);
+        }
+    }
+    if (a.stats) {
+        atomicAdd(&a.stats->iter_sum, (unsigned long long)tot);
+        atomicAdd(&a.stats->solves, 1ull);
+        atomicMax(&a.stats->iter_max, tot);
+        atomic_max_nonneg_double(&a.stats->res_max_bits, res);
+    }
+}
+
+// ---- velocity-sum engines ------------------------------------------------------
+// FP64: table w1 ut1^m in shared memory, FP64 walk and fold.
+struct Engine64 {
+    double (*tab)[5];
+    __device__ void init(double (*t)[5], const VelGrid &vg, const PointState &ps, int lane) {
+        tab = t;
+        const double s1 = vg.lo[0] - ps.U0[0], h1 = vg.h[0];
+        for (int j = lane; j < vg.n[0]; j += 32) {
+            const double ut = fma((double)j, h1, s1);
+            const double w = (j == 0 || j == vg.n[0] - 1) ? 0.5 * h1 : h1;
+            tab[j][0] = w; tab[j][1] = w * ut; tab[j][2] = w * ut * ut;
+            tab[j][3] = w * ut * ut * ut; tab[j][4] = w * ut * ut * ut * ut;
+        }
+        __syncwarp();
+    }
+    __device__ void moments(const VelGrid &vg, const PointState &ps, const double x[5], const Sym3 &A, double c0,
+                            int lane, double M[35]) const {
+        const int n1 = vg.n[0], n2 = vg.n[1], n3 = vg.n[2];
+        const double h1 = vg.h[0], h2 = vg.h[1], h3 = vg.h[2];
+        const double s1 = vg.lo[0] - ps.U0[0];
+        const double dl[3] = {x[1] - ps.U0[0], x[2] - ps.U0[1], x[3] - ps.U0[2]};
+        const double rho1 = exp(-A.t11 * h1 * h1);
+        const double ia11 = 1.0 / A.t11, ih1 = 1.0 / h1;
+#pragma unroll
+        for (int i = 0; i < 35; ++i) M[i] = 0.0;
+        for (int line = lane; line < n2 * n3; line += 32) {
+            const int j2 = line % n2, j3 = line / n2;
+            const double ut2 = fma((double)j2, h2, vg.lo[1] - ps.U0[1]);
+            const double ut3 = fma((double)j3, h3, vg.lo[2] - ps.U0[2]);
+            const double w23 = ((j2 == 0 || j2 == n2 - 1) ? 0.5 * h2 : h2) * ((j3 == 0 || j3 == n3 - 1) ? 0.5 * h3 : h3);
+            const double c2 = ut2 - dl[1], c3 = ut3 - dl[2];
+            const double lin = A.t12 * c2 + A.t13 * c3;
+            const double cst = A.t22 * c2 * c2 + 2.0 * A.t23 * c2 * c3 + A.t33 * c3 * c3;
+            const double jf = (-lin * ia11 + dl[0] - s1) * ih1;
+            const int js = (int)rint(fmin(fmax(jf, 0.0), (double)(n1 - 1)));
+            const double c1s = fma((double)js, h1, s1) - dl[0];
+            const double G = exp(c0 - 0.5 * (A.t11 * c1s * c1s + 2.0 * c1s * lin + cst));
+            const double D = fmin(fmax(-h1 * (A.t11 * (c1s + 0.5 * h1) + lin), -700.0), 700.0);
+            const double rup = exp(D);
+            const double rdn = rho1 / rup;
+            double Tm[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+            int j = js, dir = 1;
+            double g = G, r = rup;
+            const int nup = n1 - js;
+            for (int t = 0; t < n1; ++t) {
+                if (t == nup) { j = js - 1; dir = -1; g = G * rdn; r = rdn * rho1; }
+                const double *tb = tab[j];
+#pragma unroll
+                for (int q = 0; q < 5; ++q) Tm[q] = fma(g, tb[q], Tm[q]);
+                g *= r;
+                r *= rho1;
+                j += dir;
+            }
+            double pu2[5], pu3[5];
+            pu2[0] = w23; pu3[0] = 1.0;
+#pragma unroll
+            for (int q = 1; q < 5; ++q) { pu2[q] = pu2[q - 1] * ut2; pu3[q] = pu3[q - 1] * ut3; }
+#pragma unroll
+            for (int aa = 0; aa <= 4; ++aa)
+#pragma unroll
+                for (int bb = 0; bb <= 4 - aa; ++bb) {
+                    const double P = pu2[aa] * pu3[bb];
+#pragma unroll
+                    for (int mm = 0; mm <= 4 - aa - bb; ++mm) M[midx(mm, aa, bb)] = fma(P, Tm[mm], M[midx(mm, aa, bb)]);
+                }
+        }
+#pragma unroll
+        for (int i = 0; i < 35; ++i) M[i] = warp_sum(M[i]);
+    }
+};
+
+// FP32: same walk in FP32, monomials formed on the fly (no table), anchors
+// from the FP32 exp2 unit; the 35 moments accumulate in FP32 per lane and
+// are reduced across the warp in FP64.
+struct Engine32 {
+    __device__ void moments(const VelGrid &vg, const PointState &ps, const double x[5], const Sym3 &Ad, double c0d,
+                            int lane, double Md[35]) const {
+        const int n1 = vg.n[0], n2 = vg.n[1], n3 = vg.n[2];
+        const float h1 = (float)vg.h[0];
+        const float s1 = (float)(vg.lo[0] - ps.U0[0]);
+        const float o2 = (float)(vg.lo[1] - ps.U0[1]), o3 = (float)(vg.lo[2] - ps.U0[2]);
+        const float h2 = (float)vg.h[1], h3 = (float)vg.h[2];
+        const float dl0 = (float)(x[1] - ps.U0[0]), dl1 = (float)(x[2] - ps.U0[1]), dl2 = (float)(x[3] - ps.U0[2]);
+        const float A11 = (float)Ad.t11, A22 = (float)Ad.t22, A33 = (float)Ad.t33;
+        const float A12 = (float)Ad.t12, A13 = (float)Ad.t13, A23 = (float)Ad.t23;
+        const float c0 = (float)c0d;
+        const float L2E = 1.4426950408889634f;
+        const float rho1 = Eq32::ex2(-A11 * h1 * h1 * L2E);
+        const float ia11 = 1.f / A11, ih1 = 1.f / h1;
+        float M[35];
+#pragma unroll
+        for (int i = 0; i < 35; ++i) M[i] = 0.f;
+        for (int line = lane; line < n2 * n3; line += 32) {
+            const int j2 = line % n2, j3 = line / n2;
+            const float ut2 = fmaf((float)j2, h2, o2), ut3 = fmaf((float)j3, h3, o3);
+            const float w23 = ((j2 == 0 || j2 == n2 - 1) ? 0.5f * h2 : h2) * ((j3 == 0 || j3 == n3 - 1) ? 0.5f * h3 : h3) * h1;
+            const float c2 = ut2 - dl1, c3 = ut3 - dl2;
+            const float lin = A12 * c2 + A13 * c3;
+            const float cst = A22 * c2 * c2 + 2.f * A23 * c2 * c3 + A33 * c3 * c3;
+            const float jf = (-lin * ia11 + dl0 - s1) * ih1;
+            const int js = (int)rintf(fminf(fmaxf(jf, 0.f), (float)(n1 - 1)));
+            const float c1s = fmaf((float)js, h1, s1) - dl0;
+            const float G = Eq32::ex2((c0 - 0.5f * (A11 * c1s * c1s + 2.f * c1s * lin + cst)) * L2E);
+            const float D = fminf(fmaxf(-h1 * (A11 * (c1s + 0.5f * h1) + lin), -80.f), 80.f);
+            const float rup = Eq32::ex2(D * L2E);
+            const float rdn = rho1 / rup;
+            float Tm[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+            // walk up from js, then down from js-1; ut1 advances with j
+            float g = G, r = rup, ut = fmaf((float)js, h1, s1), step = h1;
+            int j = js;
+            const int nup = n1 - js;
+            for (int t = 0; t < n1; ++t) {
+                if (t == nup) { j = js - 1; step = -h1; g = G * rdn; r = rdn * rho1; ut = fmaf((float)j, h1, s1); }
+                const float gw = (j == 0 || j == n1 - 1) ? 0.5f * g : g;
+                const float t1 = gw * ut, t2 = t1 * ut, t3 = t2 * ut;
+                Tm[0] += gw; Tm[1] += t1; Tm[2] += t2; Tm[3] += t3; Tm[4] = fmaf(t3, ut, Tm[4]);
+                g *= r;
+                r *= rho1;
+                ut += step;
+                j += (step > 0.f) ? 1 : -1;
+            }
+            float pu2[5], pu3[5];
+            pu2[0] = w23; pu3[0] = 1.f;
+#pragma unroll
+            for (int q = 1; q < 5; ++q) { pu2[q] = pu2[q - 1] * ut2; pu3[q] = pu3[q - 1] * ut3; }
+#pragma unroll
+            for (int aa = 0; aa <= 4; ++aa)
+#pragma unroll
+                for (int bb = 0; bb <= 4 - aa; ++bb) {
+                    const float P = pu2[aa] * pu3[bb];
+#pragma unroll
+                    for (int mm = 0; mm <= 4 - aa - bb; ++mm) M[midx(mm, aa, bb)] = fmaf(P, Tm[mm], M[midx(mm, aa, bb)]);
+                }
+        }
+#pragma unroll
+        for (int i = 0; i < 35; ++i) Md[i] = warp_sum((double)M[i]);
+    }
+};
+
+template <bool F32>
+__global__ void __launch_bounds__(256) k_qprime(QPrimeArgs a) {
+    __shared__ double tab[F32 ? 1 : 8][F32 ? 1 : BGK_MAXV][5];
+    const int wib = threadIdx.x >> 5;
+    const int warp = blockIdx.x * 8 + wib;
+    const int lane = threadIdx.x & 31;
+    if (warp >= a.P) return;                 // whole warps exit together
+    const int p = warp;
+    PointState ps;
+    point_prologue(a, p, lane, ps);
+    Engine64 e64;
+    Engine32 e32;
+    if (!F32) e64.init(tab[F32 ? 0 : wib], a.vg, ps, lane);
+
+    double x[5];
+    bool from_guess = initial_guess(a, p, lane, ps, x);
+    const double xq[5] = {ps.rho, ps.U0[0], ps.U0[1], ps.U0[2], ps.theta};
+    const double tol = F32 ? a.tol32 : a.tol;
+    int it = 0, tot = 0;         // updates of the current solve / of all attempts
+    bool conv = false;
+    double res = 1.0e300;
+    Sym3 A;
+    double c0 = 0.0;
+    double M[35];
+    for (;;) {
+        equilibrium_params(ps, a.gas.Pr, x, A, c0);
+        if (F32) e32.moments(a.vg, ps, x, A, c0, lane, M);
+        else e64.moments(a.vg, ps, x, A, c0, lane, M);
+        double R[5], J[5][5];
+        res = assemble(M, ps, a.gas, x, A, R, J);
+        if (res <= tol) { conv = true; break; }
+        // The learned guess is judged by its own residual: one that is not
+        // small (or a solve that runs out of updates from it) restarts from q.
+        if (from_guess && ((it == 0 && !(res <= 1e-3)) || it >= a.max_iter || !(res == res))) {
+#pragma unroll
+            for (int j = 0; j < 5; ++j) x[j] = xq[j];
+            from_guess = false;
+            it = 0;
+            if (lane == 0 && a.fallbacks) atomicAdd(a.fallbacks, 1ull);
+            continue;
+        }
+        if (it >= a.max_iter || !(res == res)) break;
+        if (!newton_update(J, R, x, ps.B, a.gas.Pr)) break;
+        ++it;
+        ++tot;
+    }
+    double gam[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (a.mixed && a.eq) correction(a, lane, ps, c0, x, A, M, gam);
+    point_epilogue(a, p, lane, ps, x, A, c0, gam, tot, conv, res);
+}
+
+}  // namespace
+
+cudaError_t launch_qprime(const QPrimeArgs &a, bool fp32_sums, cudaStream_t s) {
+    const unsigned grid = (unsigned)((a.P + 7) / 8);
+    if (fp32_sums) k_qprime<true><<<grid, 256, 0, s>>>(a);
+    else k_qprime<false><<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}

@@ -151,3 +151,30 @@ def test_mixed_set_maxwellian(lib):
         f_gpu = s.get_state()
     assert f_gpu.dtype == np.float32
     assert slab_err(f_gpu.astype(np.float64), W.maxwellian_state(wl)) <= 1e-6
+
+
+def test_mixed_fp32_and_fp64_newton_sums_agree(lib):
+    """The mixed form with the Q' velocity sums on the FP32 pipe (default) and
+    with FP64 sums: moments within 1e-5 after 3 steps, both conservative."""
+    wl = CASES["tgv_es_p3_ragged"]()
+    f = W.random_anisotropic_state(wl, seed=6).astype(np.float32)
+    out = {}
+    for fp32 in (True, False):
+        with lib.Solver(wl, lib.BGK_MIXED) as s:
+            s.set_qprime_engine(fp32)
+            s.set_state(f)
+            t0 = s.totals()
+            assert s.step(wl.dt(), 3) == lib.BGK_OK
+            out[fp32] = s.moments()
+            t1 = _true_totals(s)
+            scale = np.array([t0[0]] * 4 + [t0[4]])
+            assert np.all(np.abs(t1 - t0) / scale / 3 <= 1e-8)
+    assert moment_err(out[True], out[False]) <= TOL_MIXED
+
+
+def test_fp32_newton_sums_rejected_for_fp64_form(lib):
+    wl = CASES["sine_box_p1"]()
+    with lib.Solver(wl, lib.BGK_FP64) as s:
+        with pytest.raises(lib.BGKError) as ei:
+            s.set_qprime_engine(True)
+        assert ei.value.status == lib.BGK_EINVAL
