@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--workload", default="taylor_green", choices=sorted(WORKLOADS))
+    ap.add_argument("--stage-kernel", default="tune", choices=["tune", "auto", "plain", "async"],
+                    help="mixed-form stage kernel; 'tune' times the candidates on the workload (untimed)")
+    ap.add_argument("--depth", type=int, default=6, help="copy-ring depth of the async stage kernel")
     return ap.parse_args()
 
 
@@ -178,6 +181,14 @@ def run_ours(args, rank, world, dev):
                          np.broadcast_to(theta, x.shape[:-1]))
         q = np.concatenate([rho.reshape(-1, 1), U.reshape(-1, 3), theta.reshape(-1, 1)], axis=1)
         s.set_maxwellian(q)
+        tuned = None
+        if prec == bgk.BGK_MIXED:
+            if args.stage_kernel == "tune":
+                v, d, tms = s.tune_stage(dt)
+                tuned = {"variant": v, "depth": d, "ms_per_stage": tms}
+            else:
+                s.set_stage_kernel(args.stage_kernel, args.depth)
+                tuned = {"variant": args.stage_kernel, "depth": args.depth}
         train = None
         if learned:
             # warm-up steps log the solver's own (features, Delta) pairs; the
@@ -250,7 +261,7 @@ def run_ours(args, rank, world, dev):
             newton["guess_fallbacks"] = s.mlp_stats()
             newton["training"] = train
         results[form] = dict(ms=ms, status=bgk.STATUS_NAMES[st], prof=prof, clocks=ck,
-                             newton=newton, e2e=e2e, drift=drift)
+                             newton=newton, e2e=e2e, drift=drift, stage_kernel=tuned)
         s.destroy()
         torch.cuda.empty_cache()
     return wl, results, peaks
@@ -376,6 +387,7 @@ def main():
         "gpu_launches": launches,
         "kernels_ms": {k: v[0] for k, v in r["prof"].items()},
         "newton": r["newton"],
+        "stage_kernel": r["stage_kernel"],
         "status": r["status"],
         "peaks_measured": peaks,
     }
@@ -390,7 +402,7 @@ def main():
                           "newton": rr["newton"], "e2e": rr["e2e"],
                           "conservation_drift_per_step": rr["drift"],
                           "roofline_kernels": kernel_rooflines(wl, rr, peaks, form),
-                          "clocks": rr["clocks"]}
+                          "stage_kernel": rr["stage_kernel"], "clocks": rr["clocks"]}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line))

@@ -52,7 +52,7 @@ typedef enum {
     BGK_ENOMEM = 2,    /* device allocation failed                             */
     BGK_ECUDA = 3,     /* a CUDA runtime call failed                           */
     BGK_ENOCONV = 4,   /* the Q' Newton iteration did not converge somewhere   */
-    BGK_ETIMEOUT = 5,  /* reserved: a bounded device wait gave up              */
+    BGK_ETIMEOUT = 5,  /* a bounded wait inside a kernel gave up               */
     BGK_ENOTSUP = 6    /* valid but unsupported configuration                  */
 } bgk_status;
 
@@ -128,6 +128,34 @@ BGK_API bgk_status bgk_set_newton(bgk_ctx *ctx, double tol, int max_iter);
  * moment correction, which measures its moments with exact compensated sums
  * against the moments of f.  Errors: BGK_EINVAL for fp32_sums on the FP64 form. */
 BGK_API bgk_status bgk_set_qprime_engine(bgk_ctx *ctx, int fp32_sums);
+
+/* Kernel of the mixed-form stage (the fused step of section "Methodology":
+ * FR advection, BGK source, Runge--Kutta update and the moments of the
+ * result).  variant 0 (default): the asynchronous-copy kernel where it
+ * applies, else the plain one; 1: the plain kernel (each thread loads its
+ * operands itself, one block-wide barrier per velocity); 2: the
+ * asynchronous-copy kernel (a producer warp stages the element run, its
+ * upwind neighbours and f^n for up to `depth` velocities ahead with bulk
+ * copies completing on mbarriers).  Both compute the same values bit for
+ * bit.  depth: 2..16 copy-ring stages (default 6).  The asynchronous kernel
+ * needs p = 1 or 3 (element slabs of whole 16-byte units) and 16-byte
+ * aligned state buffers; every wait in it is bounded and a wait that gives
+ * up makes the next status check return BGK_ETIMEOUT.  Errors: BGK_EINVAL
+ * (range), BGK_ENOTSUP (variant 2 on the FP64 form or an unsupported order). */
+BGK_API bgk_status bgk_set_stage_kernel(bgk_ctx *ctx, int variant, int depth);
+
+/* Autotune the mixed-form stage kernel on this context's own problem: time
+ * the plain kernel and the asynchronous one at every supported ring depth
+ * (2, 3, 4, 6, 8, 12, 16), each over `reps` stages with f^n and the moment
+ * epilogue (time step dt), from the current state into a scratch buffer, and
+ * keep the fastest (as bgk_set_stage_kernel would).  The state is not
+ * changed; the cached moments are recomputed by the next step.  Outputs (each
+ * may be NULL): the chosen variant and depth and its mean time per stage in
+ * ms.  The FP64 form has one kernel: returns variant 1 and 0 ms.  Errors:
+ * BGK_EINVAL, BGK_ECUDA, BGK_ETIMEOUT, BGK_ENOCONV (the Q' solve of the
+ * current state). */
+BGK_API bgk_status bgk_tune_stage(bgk_ctx *ctx, double dt, int reps, int *variant_out, int *depth_out,
+                                  double *ms_out);
 
 /* One residual R(f) = -div(u f) + (g(Q') - f)/tau of f_in into r_out (both
  * with the state's layout and element type).  Test and debug entry; it

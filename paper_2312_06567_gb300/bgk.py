@@ -47,6 +47,9 @@ SIGNATURES = {
     "bgk_set_maxwellian": (c_int, [c_void_p, c_void_p, c_int]),
     "bgk_set_newton": (c_int, [c_void_p, c_double, c_int]),
     "bgk_set_qprime_engine": (c_int, [c_void_p, c_int]),
+    "bgk_set_stage_kernel": (c_int, [c_void_p, c_int, c_int]),
+    "bgk_tune_stage": (c_int, [c_void_p, c_double, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                               ctypes.POINTER(c_double)]),
     "bgk_rhs": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
     "bgk_step": (c_int, [c_void_p, c_double, c_int]),
     "bgk_stage": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_double, c_double]),
@@ -244,6 +247,21 @@ class Solver:
 
     def set_qprime_engine(self, fp32_sums):
         self._check(self.lib.bgk_set_qprime_engine(self._h, 1 if fp32_sums else 0))
+
+    STAGE_KERNELS = {"auto": 0, "plain": 1, "async": 2}
+
+    def set_stage_kernel(self, variant="auto", depth=6):
+        """Mixed-form stage kernel: "auto", "plain" or "async" (bulk-copy ring of `depth` stages)."""
+        self._check(self.lib.bgk_set_stage_kernel(self._h, self.STAGE_KERNELS[variant], int(depth)))
+
+    def tune_stage(self, dt, reps=3):
+        """Time the stage kernel candidates on this problem, keep the fastest;
+        returns (variant name, depth, ms per stage)."""
+        v, d, ms = c_int(), c_int(), c_double()
+        self._check(self.lib.bgk_tune_stage(self._h, dt, int(reps), ctypes.byref(v), ctypes.byref(d),
+                                            ctypes.byref(ms)))
+        names = {b: a for a, b in self.STAGE_KERNELS.items()}
+        return names[v.value], d.value, ms.value
 
     def rhs(self, f, out=None):
         if isinstance(f, np.ndarray):

@@ -45,6 +45,7 @@ struct bgk_ctx {
     double tol;
     int max_iter;
     int qp_fp32;                      // Q' velocity sums on the FP32 pipe (mixed form default)
+    int stage_variant, stage_depth;   // FP32 stage kernel choice and copy-ring depth
     std::string err;
     // profiling: event pairs around launches, accumulated per kernel kind
     bool prof_on;
@@ -199,6 +200,8 @@ bgk_status check_device_status(bgk_ctx *ctx) {
     CU(cudaStreamSynchronize(ctx->stream));
     if (st) {
         CU(cudaMemsetAsync(ctx->status, 0, sizeof(unsigned int), ctx->stream));
+        if (st & BGK_DEV_TIMEOUT)
+            return fail(ctx, BGK_ETIMEOUT, "a bounded wait in the stage kernel gave up (device status 0x%x)", st);
         if (st & BGK_DEV_NOCONV)
             return fail(ctx, BGK_ENOCONV, "Q' Newton iteration did not converge at some point");
         return fail(ctx, BGK_ENOCONV, "device status 0x%x", st);
@@ -242,6 +245,7 @@ StageArgs<T> stage_args(bgk_ctx *ctx, const void *fn, const void *fs, void *fo, 
     s.f_n = (const T *)fn; s.f_s = (const T *)fs; s.f_out = (T *)fo;
     s.eq = ctx->eq; s.vtab = ctx->vtab; s.vtab32 = ctx->vtab32; s.bcval = ctx->bcval;
     s.part = moments ? ctx->part : nullptr;
+    s.status = ctx->status;
     s.a = a; s.b = b; s.c = c; s.Nu = ctx->Nu; s.P = ctx->P; s.Kblk = ctx->Kblk;
     s.vg = ctx->vg; s.fr = ctx->fr; s.mesh = ctx->mesh;
     s.a32 = (float)a; s.ab32 = (float)(a + b); s.c32 = (float)c;
@@ -257,7 +261,7 @@ bgk_status run_stage(bgk_ctx *ctx, const void *fn, const void *fs, void *fo, dou
                             ctx->stream));
     else
         CU(launch_stage_f32(stage_args<float>(ctx, fn, fs, fo, a, b, c, moments), ctx->C, ctx->n_vblk,
-                            ctx->stream));
+                            ctx->stage_variant, ctx->stage_depth, ctx->stream));
     return BGK_OK;
 }
 
@@ -312,6 +316,8 @@ bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
     ctx->tol = 1e-13;
     ctx->max_iter = 50;
     ctx->qp_fp32 = precision == BGK_MIXED ? 1 : 0;
+    ctx->stage_variant = BGK_STAGE_AUTO;
+    ctx->stage_depth = 6;
     for (int d = 0; d < 3; ++d) {
         ctx->vn[d] = vg->n[d];
         ctx->vg.n[d] = vg->n[d];
@@ -527,6 +533,74 @@ bgk_status bgk_set_qprime_engine(bgk_ctx *ctx, int fp32_sums) {
     if (fp32_sums && ctx->precision != BGK_MIXED)
         return fail(ctx, BGK_EINVAL, "FP32 Q' sums are for the mixed form only");
     ctx->qp_fp32 = fp32_sums ? 1 : 0;
+    return BGK_OK;
+}
+
+bgk_status bgk_set_stage_kernel(bgk_ctx *ctx, int variant, int depth) {
+    if (!ctx || variant < BGK_STAGE_AUTO || variant > BGK_STAGE_ASYNC || depth < 2 || depth > BGK_MAX_DEPTH)
+        return BGK_EINVAL;
+    if (variant == BGK_STAGE_ASYNC) {
+        if (ctx->precision != BGK_MIXED)
+            return fail(ctx, BGK_ENOTSUP, "the asynchronous-copy stage kernel is for the mixed form only");
+        const StageArgs<float> a = stage_args<float>(ctx, ctx->f[0], ctx->f[1], ctx->f[2], 0.5, 0.5, 1.0, true);
+        if (!stage_f32_tma_supported(a, ctx->C, depth))
+            return fail(ctx, BGK_ENOTSUP, "asynchronous-copy stage kernel needs p = 1 or 3 and fitting shared memory");
+    }
+    ctx->stage_variant = variant;
+    ctx->stage_depth = depth;
+    return BGK_OK;
+}
+
+bgk_status bgk_tune_stage(bgk_ctx *ctx, double dt, int reps, int *variant_out, int *depth_out, double *ms_out) {
+    if (!ctx || !(dt > 0.0) || reps < 1) return BGK_EINVAL;
+    if (ctx->precision != BGK_MIXED) {
+        if (variant_out) *variant_out = BGK_STAGE_PLAIN;
+        if (depth_out) *depth_out = ctx->stage_depth;
+        if (ms_out) *ms_out = 0.0;
+        return BGK_OK;
+    }
+    bgk_status st;
+    if (!ctx->part_valid) {
+        if ((st = run_moments(ctx, ctx->f[0]))) return st;
+        ctx->part_valid = true;
+    }
+    if ((st = run_qprime(ctx, ctx->part, ctx->n_vblk, ctx->P, ctx->eq, ctx->qp, nullptr, nullptr))) return st;
+    // candidates: the plain kernel and every ring depth of the asynchronous one;
+    // each runs a full stage (with f^n and the moment epilogue) from the
+    // current state into the scratch buffer, so the state itself is untouched
+    const StageArgs<float> sa = stage_args<float>(ctx, ctx->f[0], ctx->f[0], ctx->f[2], 0.75, 0.25, 0.25 * dt, true);
+    struct Cand { int v, d; };
+    std::vector<Cand> cands{{BGK_STAGE_PLAIN, ctx->stage_depth}};
+    for (int d : {2, 3, 4, 6, 8, 12, 16})
+        if (stage_f32_tma_supported(sa, ctx->C, d)) cands.push_back({BGK_STAGE_ASYNC, d});
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    CU(cudaEventCreate(&ea));
+    CU(cudaEventCreate(&eb));
+    double best = 1e300;
+    Cand pick = cands[0];
+    cudaError_t err = cudaSuccess;
+    for (const Cand &c : cands) {
+        err = launch_stage_f32(sa, ctx->C, ctx->n_vblk, c.v, c.d, ctx->stream);      // warm-up
+        if (err == cudaSuccess) err = cudaEventRecord(ea, ctx->stream);
+        for (int r = 0; r < reps && err == cudaSuccess; ++r)
+            err = launch_stage_f32(sa, ctx->C, ctx->n_vblk, c.v, c.d, ctx->stream);
+        if (err == cudaSuccess) err = cudaEventRecord(eb, ctx->stream);
+        if (err == cudaSuccess) err = cudaEventSynchronize(eb);
+        float ms = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, ea, eb);
+        if (err != cudaSuccess) break;
+        if (ms / reps < best) { best = ms / reps; pick = c; }
+    }
+    cudaEventDestroy(ea);
+    cudaEventDestroy(eb);
+    CU(err);
+    ctx->part_valid = false;              // the partials now describe the scratch output
+    if ((st = check_device_status(ctx))) return st;
+    ctx->stage_variant = pick.v;
+    ctx->stage_depth = pick.d;
+    if (variant_out) *variant_out = pick.v;
+    if (depth_out) *depth_out = pick.d;
+    if (ms_out) *ms_out = best;
     return BGK_OK;
 }
 

@@ -18,6 +18,13 @@
 // Device status bits (OR-ed by kernels, read by the host after a stage).
 #define BGK_DEV_NOCONV 1u
 #define BGK_DEV_NONFINITE 2u
+#define BGK_DEV_TIMEOUT 4u     // a bounded wait inside a kernel gave up
+
+// FP32 stage kernel variants (bgk_set_stage_kernel) and the deepest copy ring.
+#define BGK_STAGE_AUTO 0
+#define BGK_STAGE_PLAIN 1
+#define BGK_STAGE_ASYNC 2
+#define BGK_MAX_DEPTH 16
 
 // 1-D FR operators on Gauss--Legendre nodes (section "Numerical method").
 struct FROps {
@@ -100,6 +107,7 @@ struct StageArgs {
     const float4 *vtab32;    // [Nu] (u1, u2, u3, 0) rounded to FP32
     const double *bcval;     // [6][C][Nu] exterior Maxwellian values of Dirichlet faces
     double *part;            // [n_vblk][BGK_NMOM][P] moment partials of f_out (or null)
+    unsigned int *status;    // device status word (BGK_DEV_* bits)
     double a, b, c;
     // FP32 copies made on the host: a, a + b, c, and the metric terms 2/h_d
     // (converting them in the kernel costs an FP64-pipe instruction each time
@@ -154,7 +162,9 @@ cudaError_t launch_maxwellian_f64(double *f, const double *q, const double *vtab
                                   int C, double delta, cudaStream_t s);
 cudaError_t launch_moments_f32(const float *f, double *part, const double *vtab, int Nu, int P,
                                int Kblk, int C, int n_vblk, cudaStream_t s);
-cudaError_t launch_stage_f32(const StageArgs<float> &a, int C, int n_vblk, cudaStream_t s);
+cudaError_t launch_stage_f32(const StageArgs<float> &a, int C, int n_vblk, int variant, int depth,
+                             cudaStream_t s);
+bool stage_f32_tma_supported(const StageArgs<float> &a, int C, int depth);
 cudaError_t launch_maxwellian_f32(float *f, const double *q, const double *vtab, int Nu, int P, int C,
                                   double delta, cudaStream_t s);
 cudaError_t launch_reduce_moments(const double *part, int n_vblk, int P, double *m_out,

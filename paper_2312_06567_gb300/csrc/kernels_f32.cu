@@ -49,6 +49,89 @@ __device__ __forceinline__ void index_to_raw(const double J[11], const VelGrid &
     m[10] = W * J[10];
 }
 
+// The same accumulation with the plane pairs and the FP64 index moments kept
+// in shared memory (column `t` of [field][n] arrays, so a warp's accesses hit
+// distinct banks): they change once per line and once per plane, and holding
+// them in registers would cost the pipelined stage kernel a third of its
+// occupancy.
+struct IndexMomentsS {
+    float L[4], Lc[4];
+    float *P;                 // [14][n]: P[0..6] then Pc[0..6]
+    double *J;                // [11][n]
+    int n;
+    int j3cur;
+    __device__ void init(float *Ps, double *Js, int ncol, int t) {
+        P = Ps + t;
+        J = Js + t;
+        n = ncol;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) L[i] = Lc[i] = 0.f;
+#pragma unroll
+        for (int i = 0; i < 14; ++i) P[i * n] = 0.f;
+#pragma unroll
+        for (int i = 0; i < 11; ++i) J[i * n] = 0.0;
+        j3cur = -1;
+    }
+    __device__ __forceinline__ void add(float cj1, float jt1, float F, float G) {
+        const float cF = __fmul_rn(cj1, F);
+        sum2(L[0], Lc[0], cF);
+        const float p1 = __fmul_rn(cF, jt1);
+        sum2(L[1], Lc[1], p1);
+        Lc[1] = __fadd_rn(Lc[1], fmaf(cF, jt1, -p1));
+        const float jj = __fmul_rn(jt1, jt1);
+        const float p2 = __fmul_rn(cF, jj);
+        sum2(L[2], Lc[2], p2);
+        Lc[2] = __fadd_rn(Lc[2], fmaf(cF, jj, -p2));
+        sum2(L[3], Lc[3], __fmul_rn(cj1, G));
+    }
+    __device__ __forceinline__ void plane_add(int i, float c, float sum, float err) {
+        float ps = P[i * n], pc = P[(7 + i) * n];
+        const float pr = __fmul_rn(c, sum);
+        sum2(ps, pc, pr);
+        pc = __fadd_rn(pc, fmaf(c, sum, -pr));
+        pc = fmaf(c, err, pc);
+        P[i * n] = ps;
+        P[(7 + i) * n] = pc;
+    }
+    __device__ __forceinline__ void end_line(float c2, float jt2) {
+        const float a = c2, b = __fmul_rn(c2, jt2), bb = __fmul_rn(__fmul_rn(c2, jt2), jt2);
+        plane_add(0, a, L[0], Lc[0]);
+        plane_add(1, a, L[1], Lc[1]);
+        plane_add(2, a, L[2], Lc[2]);
+        plane_add(3, b, L[0], Lc[0]);
+        plane_add(4, b, L[1], Lc[1]);
+        plane_add(5, bb, L[0], Lc[0]);
+        plane_add(6, a, L[3], Lc[3]);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) L[i] = Lc[i] = 0.f;
+    }
+    __device__ __forceinline__ void flush_plane(float c3, float jt3) {
+        const double c = c3, t = jt3;
+        double Pd[7];
+#pragma unroll
+        for (int i = 0; i < 7; ++i) {
+            Pd[i] = (double)P[i * n] + (double)P[(7 + i) * n];
+            P[i * n] = 0.f;
+            P[(7 + i) * n] = 0.f;
+        }
+        J[0] = fma(c, Pd[0], J[0]);
+        J[n] = fma(c, Pd[1], J[n]);
+        J[2 * n] = fma(c, Pd[2], J[2 * n]);
+        J[3 * n] = fma(c, Pd[3], J[3 * n]);
+        J[4 * n] = fma(c, Pd[4], J[4 * n]);
+        J[5 * n] = fma(c, Pd[5], J[5 * n]);
+        J[6 * n] = fma(c * t, Pd[0], J[6 * n]);
+        J[7 * n] = fma(c * t, Pd[1], J[7 * n]);
+        J[8 * n] = fma(c * t, Pd[3], J[8 * n]);
+        J[9 * n] = fma(c * t * t, Pd[0], J[9 * n]);
+        J[10 * n] = fma(c, Pd[6], J[10 * n]);
+    }
+    __device__ __forceinline__ void get(double out[11]) const {
+#pragma unroll
+        for (int i = 0; i < 11; ++i) out[i] = J[i * n];
+    }
+};
+
 // Dt[side] = D - dg (x) l rounded to FP32 with explicit roundings, so every
 // use (the operator itself and the conservation weights built from it) sees
 // the same FP32 entries.
@@ -135,6 +218,37 @@ struct IndexMoments {
     }
 };
 
+// Shared-memory FP32 operator tables of the deviation-form advection (used by
+// both FP32 stage kernels): Dt[side] (inflow trace folded in), dg[side], the
+// exact defects eps_i = sum_j Dt_ij + dg_i, the telescoping neighbour-trace
+// weights lambda_j = +-sum_i W_i Dt_ij and dlam = sum_j lambda_j - 1.
+template <int Q>
+__device__ __forceinline__ void load_ops_f32(const FROps &fr, int tid, float (*sD)[Q][Q], float (*sdg)[Q],
+                                             float (*seps)[Q], float (*slam)[Q], float *sdlam) {
+    if (tid < Q * Q) {
+        const int i = tid / Q, j = tid % Q;
+        sD[0][i][j] = folded_dt(fr, 0, i, j);
+        sD[1][i][j] = folded_dt(fr, 1, i, j);
+    }
+    if (tid < 2 * Q) {
+        const int side = tid / Q, j = tid % Q;
+        double lam = 0.0, eps = side == 0 ? fr.dgL[j] : fr.dgR[j];
+        for (int i = 0; i < Q; ++i) {
+            lam = fma(fr.wq[i], (double)folded_dt(fr, side, i, j), lam);
+            eps += (double)folded_dt(fr, side, j, i);
+        }
+        slam[side][j] = (float)(side == 0 ? lam : -lam);
+        seps[side][j] = (float)eps;
+        sdg[side][j] = (float)(side == 0 ? fr.dgL[j] : fr.dgR[j]);
+        if (j == 0) {
+            double tot = 0.0;
+            for (int jj = 0; jj < Q; ++jj)
+                for (int i = 0; i < Q; ++i) tot = fma(fr.wq[i], (double)folded_dt(fr, side, i, jj), tot);
+            sdlam[side] = (float)((side == 0 ? tot : -tot) - 1.0);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Fused stage, FP32 state.  Same discretisation as the FP64 stage kernel:
 // per direction t_d = sum_j Dt[side][i][j] f_j + dg[side][i] f^+ with the
@@ -163,28 +277,7 @@ __global__ void __launch_bounds__(256) k_stage_f32(StageArgs<float> a) {
     // the right neighbour's left trace) makes sum_i W_i t_i telescope between
     // neighbours, which keeps the advection discretely conservative up to
     // second-order rounding terms.
-    if (tid < Q * Q) {
-        const int i = tid / Q, j = tid % Q;
-        sD[0][i][j] = folded_dt(a.fr, 0, i, j);
-        sD[1][i][j] = folded_dt(a.fr, 1, i, j);
-    }
-    if (tid < 2 * Q) {
-        const int side = tid / Q, j = tid % Q;
-        double lam = 0.0, eps = side == 0 ? a.fr.dgL[j] : a.fr.dgR[j];
-        for (int i = 0; i < Q; ++i) {
-            lam = fma(a.fr.wq[i], (double)folded_dt(a.fr, side, i, j), lam);
-            eps += (double)folded_dt(a.fr, side, j, i);
-        }
-        slam[side][j] = (float)(side == 0 ? lam : -lam);
-        seps[side][j] = (float)eps;
-        sdg[side][j] = (float)(side == 0 ? a.fr.dgL[j] : a.fr.dgR[j]);
-        if (j == 0) {
-            double tot = 0.0;
-            for (int jj = 0; jj < Q; ++jj)
-                for (int i = 0; i < Q; ++i) tot = fma(a.fr.wq[i], (double)folded_dt(a.fr, side, i, jj), tot);
-            sdlam[side] = (float)((side == 0 ? tot : -tot) - 1.0);
-        }
-    }
+    load_ops_f32<Q>(a.fr, tid, sD, sdg, seps, slam, sdlam);
     const int e0 = blockIdx.x * EB;
     const int le = tid / NS, s = tid - le * NS;
     const int e = e0 + le;
@@ -328,6 +421,284 @@ __global__ void __launch_bounds__(256) k_stage_f32(StageArgs<float> a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Fused FP32 stage with asynchronous staging.  The arithmetic is that of
+// k_stage_f32, term for term; only the source of the operands differs.  A
+// block owns a run of EB consecutive elements of one mesh row (first axis).
+// For each velocity it needs its own values, the upwind neighbour element
+// along the first axis (outside the run only at its two ends), the upwind
+// neighbour runs along the second and third axes (each contiguous in the
+// [k][e][s] layout) and f^n.  One producer thread copies these with bulk
+// asynchronous copies (cp.async.bulk, completion counted in bytes on an
+// mbarrier) into a ring of S stage buffers, up to S velocities ahead of the
+// consumer warps, which wait on the stage's "full" barrier, compute from
+// shared memory and release the stage on its "empty" barrier.  Every wait
+// is bounded (about 2 s): a wait that gives up sets BGK_DEV_TIMEOUT, and the
+// producer then waits, again bounded, for its copies still in flight before
+// the block exits.
+template <int Q, int C>
+struct TmaGeom {
+    static constexpr int NS = Q * Q * Q;
+    static constexpr int EB = 256 / NS;                  // elements per block
+    static constexpr int NCT = (EB * NS + 31) / 32 * 32;  // consumer threads
+    static constexpr int NTHR = NCT + 32;                 // + one producer warp
+    static constexpr int SLOTS = EB + 2;                  // x-halo, EB own elements, x-halo
+    static constexpr int PER_C = (SLOTS + 3 * EB) * NS;   // own + halos, y run, z run, f^n run
+    static constexpr int STAGE = C * PER_C;               // floats per stage buffer
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the completion of the barrier phase of the given parity; false
+// after about 2 s without it.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try(bar, parity))
+        if (global_ns() - t0 > 2000000000ull) return false;
+    return true;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const float *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+template <int Q, int C>
+__global__ void __launch_bounds__(TmaGeom<Q, C>::NTHR, 2) k_stage_f32_tma(StageArgs<float> a, int S) {
+    using G = TmaGeom<Q, C>;
+    constexpr int NS = G::NS, EB = G::EB, NCT = G::NCT, SLOTS = G::SLOTS, PER_C = G::PER_C, STAGE = G::STAGE;
+    extern __shared__ __align__(128) float sbuf[];
+    // [S][STAGE] copy ring | [11][NCT] FP64 index moments | [14][NCT] plane pairs | 2S mbarriers
+    double *Jsm = reinterpret_cast<double *>(sbuf + (size_t)S * STAGE);
+    float *Psm = reinterpret_cast<float *>(Jsm + 11 * NCT);
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(Psm + 14 * NCT);
+    __shared__ float sD[2][Q][Q];
+    __shared__ float sdg[2][Q], seps[2][Q], slam[2][Q], sdlam[2];
+    __shared__ int s_abort;
+    const int tid = threadIdx.x;
+    const int n1 = a.mesh.n[0], n2 = a.mesh.n[1], n3 = a.mesh.n[2];
+    const int cpr = (n1 + EB - 1) / EB;
+    const int row = blockIdx.x / cpr, x0 = (blockIdx.x - row * cpr) * EB;
+    const int nel = min(EB, n1 - x0);
+    const int e0 = row * n1 + x0;
+    const int ey = row % n2, ez = row / n2, pl = n1 * n2;
+    // first element of the upwind neighbour run on side 0 (left) / 1 (right); -1: Dirichlet face
+    const int xn0 = x0 > 0 ? e0 - 1 : (a.mesh.periodic[0] ? row * n1 + n1 - 1 : -1);
+    const int xn1 = x0 + nel < n1 ? e0 + nel : (a.mesh.periodic[0] ? row * n1 : -1);
+    const int yn0 = ey > 0 ? e0 - n1 : (a.mesh.periodic[1] ? e0 + (n2 - 1) * n1 : -1);
+    const int yn1 = ey < n2 - 1 ? e0 + n1 : (a.mesh.periodic[1] ? e0 - (n2 - 1) * n1 : -1);
+    const int zn0 = ez > 0 ? e0 - pl : (a.mesh.periodic[2] ? e0 + (n3 - 1) * pl : -1);
+    const int zn1 = ez < n3 - 1 ? e0 + pl : (a.mesh.periodic[2] ? e0 - (n3 - 1) * pl : -1);
+    const int vb = blockIdx.y;
+    const int k0 = vb * a.Kblk, k1 = min(a.Nu, k0 + a.Kblk);
+    const size_t slab = (size_t)a.P;
+    if (tid == 0) {
+        for (int i = 0; i < S; ++i) {
+            mbar_init(smem_u32(bars + i), 1);              // full: the producer's arrive + bytes
+            mbar_init(smem_u32(bars + S + i), NCT / 32);    // empty: one arrival per consumer warp
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
+    }
+    load_ops_f32<Q>(a.fr, tid, sD, sdg, seps, slam, sdlam);
+    __syncthreads();
+
+    if (tid >= NCT) {
+        // ---- producer: one thread issues every copy ----
+        if (tid != NCT) return;
+        const uint32_t runb = (uint32_t)(nel * NS * 4), elb = NS * 4;
+        const bool with_fn = a.a32 != 0.f;
+        int i = 0;
+        bool ok = true;
+        for (; i < k1 - k0; ++i) {
+            const int slot = i % S;
+            if (i >= S && !mbar_wait(smem_u32(bars + S + slot), ((i / S) & 1) ^ 1)) { ok = false; break; }
+            if (*(volatile int *)&s_abort) { ok = false; break; }
+            const int k = k0 + i;
+            const float4 u = __ldg(a.vtab32 + k);
+            const int xe = u.x > 0.f ? xn0 : xn1, ye = u.y > 0.f ? yn0 : yn1, ze = u.z > 0.f ? zn0 : zn1;
+            const uint32_t bytes = C * (runb + (xe >= 0 ? elb : 0u) + (ye >= 0 ? runb : 0u) + (ze >= 0 ? runb : 0u) +
+                                        (with_fn ? runb : 0u));
+            const uint32_t full = smem_u32(bars + slot);
+            mbar_expect_tx(full, bytes);
+            float *st = sbuf + (size_t)slot * STAGE;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const float *src = a.f_s + ((size_t)c * a.Nu + k) * slab;
+                float *own = st + c * PER_C;
+                bulk_g2s(smem_u32(own + NS), src + (size_t)e0 * NS, runb, full);
+                if (xe >= 0) bulk_g2s(smem_u32(own + (u.x > 0.f ? 0 : (nel + 1) * NS)), src + (size_t)xe * NS, elb, full);
+                if (ye >= 0) bulk_g2s(smem_u32(own + SLOTS * NS), src + (size_t)ye * NS, runb, full);
+                if (ze >= 0) bulk_g2s(smem_u32(own + (SLOTS + EB) * NS), src + (size_t)ze * NS, runb, full);
+                if (with_fn)
+                    bulk_g2s(smem_u32(own + (SLOTS + 2 * EB) * NS), a.f_n + ((size_t)c * a.Nu + k) * slab + (size_t)e0 * NS,
+                             runb, full);
+            }
+        }
+        if (!ok) {
+            // no copy may still be in flight when the block exits
+            for (int j = max(0, i - S); j < i; ++j) mbar_wait(smem_u32(bars + j % S), (j / S) & 1);
+            atomicOr(a.status, BGK_DEV_TIMEOUT);
+        }
+        return;
+    }
+
+    // ---- consumers ----
+    const int lane = tid & 31;
+    const int l = tid / NS, s = tid - l * NS;
+    const bool active = l < nel;
+    const int p = (e0 + l) * NS + s;
+    const int id[3] = {s % Q, (s / Q) % Q, s / (Q * Q)};
+    const int stride[3] = {1, Q, Q * Q};
+    int base[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) base[d] = s - id[d] * stride[d];
+    // Dirichlet faces of this element: bit 2d + side
+    const int bcm = (l == 0 && xn0 < 0 ? 1 : 0) | (l == nel - 1 && xn1 < 0 ? 2 : 0) | (yn0 < 0 ? 4 : 0) |
+                    (yn1 < 0 ? 8 : 0) | (zn0 < 0 ? 16 : 0) | (zn1 < 0 ? 32 : 0);
+    // offsets (floats, within a component's stage region) of the own line and
+    // of the upwind neighbour line; along x the neighbour sits one slot left
+    // (side 0) or right (side 1) of the own element
+    const int own_off = (l + 1) * NS;
+    const int nby_off = (SLOTS + l) * NS + base[1], nbz_off = (SLOTS + EB + l) * NS + base[2];
+    const int fn_off = (SLOTS + 2 * EB + l) * NS + s;
+    Eq32 e32;
+    float itau = 0.f, gfac = 0.f;
+    float gm[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, U0f[3] = {0.f, 0.f, 0.f};
+    {
+        const double qz[10] = {0.0, 0.0, 0.0, 0.0, 1.0, 1.0, 1.0, 0.0, 0.0, 0.0};
+        const double *q = active ? a.eq + (size_t)p * BGK_NEQ : qz;
+        e32.load(q);
+        if (active) {
+            itau = (float)q[10]; gfac = (float)q[11];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) gm[i] = (float)q[12 + i];
+            U0f[0] = (float)q[17]; U0f[1] = (float)q[18]; U0f[2] = (float)q[19];
+        }
+    }
+    const VelGrid &vg = a.vg;
+    const int vn1 = vg.n[0], vn2 = vg.n[1], vn3 = vg.n[2];
+    const int jc[3] = {(vn1 - 1) / 2, (vn2 - 1) / 2, (vn3 - 1) / 2};
+    const double uc[3] = {vg.lo[0] + jc[0] * vg.h[0], vg.lo[1] + jc[1] * vg.h[1], vg.lo[2] + jc[2] * vg.h[2]};
+    const float toh[3] = {a.toh32[0], a.toh32[1], a.toh32[2]};
+    const float fa = a.a32, fab = a.ab32, fc = a.c32;
+    IndexMomentsS acc;
+    acc.init(Psm, Jsm, NCT, tid);
+    int slot = 0;
+    uint32_t par = 0;
+    bool ok = true;
+    for (int kl = k0; kl < k1; kl += vn1) {
+        const int line = kl / vn1;
+        const int j2 = line % vn2, j3 = line / vn2;
+        if (j3 != acc.j3cur) {
+            if (acc.j3cur >= 0) acc.flush_plane(trap(acc.j3cur, vn3), (float)(acc.j3cur - jc[2]));
+            acc.j3cur = j3;
+        }
+        const float4 vl = __ldg(a.vtab32 + kl);
+        const float u2 = vl.y, u3 = vl.z;
+        float lin, cst;
+        e32.line(u2, u3, lin, cst);
+        const float t2 = u2 - U0f[1], t3 = u3 - U0f[2];
+        const float corr_line = fmaf(gm[2], t2, fmaf(gm[3], t3, fmaf(0.5f * gm[4], fmaf(t2, t2, t3 * t3), gm[0])));
+        float jt1 = (float)(-jc[0]);
+        for (int j1 = 0; j1 < vn1; ++j1, jt1 += 1.f) {
+            const int k = kl + j1;
+            ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(bars + slot), par));
+            if (!ok) break;
+            if (active) {
+                const float *st = sbuf + (size_t)slot * STAGE;
+                const float u1 = __ldg(a.vtab32 + k).x;
+                const float u[3] = {u1, u2, u3};
+                const float g32 = e32.g(u1, lin, cst);
+                const float t1 = u1 - U0f[0];
+                const float corr = fmaf(t1, fmaf(0.5f * gm[4], t1, gm[1]), corr_line);
+                const float gc = __fmul_rn(g32, corr);
+                float outv[C];
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const float *sc = st + c * PER_C;
+                    const float fi = sc[own_off + s];
+                    float div = 0.f;
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        const int side = u[d] > 0.f ? 0 : 1;
+                        const float *own = sc + own_off + base[d];
+                        float t = 0.f;
+#pragma unroll
+                        for (int j = 0; j < Q; ++j) t = fmaf(sD[side][id[d]][j], own[j * stride[d]] - fi, t);
+                        float dn;
+                        if (!((bcm >> (2 * d + side)) & 1)) {
+                            const float *nb = sc + (d == 0 ? own_off + base[0] + (side ? NS : -NS)
+                                                           : (d == 1 ? nby_off : nbz_off));
+                            dn = sdlam[side] * fi;
+#pragma unroll
+                            for (int j = 0; j < Q; ++j) dn = fmaf(slam[side][j], nb[j * stride[d]] - fi, dn);
+                        } else {
+                            dn = (float)__ldg(a.bcval + ((size_t)(2 * d + side) * C + c) * a.Nu + k) - fi;
+                        }
+                        t = fmaf(sdg[side][id[d]], dn, fmaf(seps[side][id[d]], fi, t));
+                        div = fmaf(toh[d] * u[d], t, div);
+                    }
+                    const float eqv = (c == 0) ? g32 : gfac * g32;
+                    const float eqc = (c == 0) ? gc : gfac * gc;
+                    const float R = fmaf(eqv - fi, itau, fmaf(eqc, itau, -div));
+                    float out = fab == 1.f ? fi : fab * fi;
+                    if (fa != 0.f) out = fmaf(fa, sc[fn_off] - fi, out);
+                    out = fmaf(fc, R, out);
+                    a.f_out[((size_t)c * a.Nu + k) * slab + p] = out;
+                    outv[c] = out;
+                }
+                acc.add(trap(j1, vn1), jt1, outv[0], C == 2 ? outv[C - 1] : 0.f);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(bars + S + slot));
+            if (++slot == S) { slot = 0; par ^= 1u; }
+        }
+        if (!ok) break;
+        acc.end_line(trap(j2, vn2), (float)(j2 - jc[1]));
+    }
+    if (!ok) {
+        *(volatile int *)&s_abort = 1;
+        if (lane == 0) atomicOr(a.status, BGK_DEV_TIMEOUT);
+        return;
+    }
+    if (acc.j3cur >= 0) acc.flush_plane(trap(acc.j3cur, vn3), (float)(acc.j3cur - jc[2]));
+    if (a.part && active) {
+        double J[11], m[BGK_NMOM];
+        acc.get(J);
+        index_to_raw(J, vg, uc, m);
+#pragma unroll
+        for (int j = 0; j < BGK_NMOM; ++j) a.part[((size_t)vb * BGK_NMOM + j) * a.P + p] = m[j];
+    }
+}
+
 // Raw moments of an FP32 state with FP64 accumulation (initialisation and
 // test entry points; the stepping loop takes its moments from the stage).
 __global__ void __launch_bounds__(256) k_moments_f32(const float *f, double *part, const double *vtab,
@@ -392,7 +763,46 @@ static cudaError_t stage32_q(const StageArgs<float> &a, int C, int n_vblk, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t launch_stage_f32(const StageArgs<float> &a, int C, int n_vblk, cudaStream_t s) {
+template <int Q, int C>
+static size_t tma_smem(int depth) {
+    using G = TmaGeom<Q, C>;
+    return (size_t)depth * G::STAGE * sizeof(float) + (11 * sizeof(double) + 14 * sizeof(float)) * G::NCT +
+           2 * (size_t)depth * sizeof(unsigned long long);
+}
+
+template <int Q, int C>
+static cudaError_t stage32_tma(const StageArgs<float> &a, int n_vblk, int depth, cudaStream_t s) {
+    using G = TmaGeom<Q, C>;
+    const size_t smem = tma_smem<Q, C>(depth);
+    static size_t attr = 0;               // dynamic shared memory limit set so far
+    if (smem > attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_stage_f32_tma<Q, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = smem;
+    }
+    const int cpr = (a.mesh.n[0] + G::EB - 1) / G::EB;
+    dim3 grid(cpr * a.mesh.n[1] * a.mesh.n[2], n_vblk);
+    k_stage_f32_tma<Q, C><<<grid, G::NTHR, smem, s>>>(a, depth);
+    return cudaGetLastError();
+}
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+bool stage_f32_tma_supported(const StageArgs<float> &a, int C, int depth) {
+    if (a.fr.q != 2 && a.fr.q != 4) return false;          // element slabs of whole 16-byte units
+    if (depth < 2 || depth > BGK_MAX_DEPTH) return false;
+    if (!aligned16(a.f_s) || (a.a32 != 0.f && !aligned16(a.f_n))) return false;
+    const size_t smem = a.fr.q == 2 ? (C == 1 ? tma_smem<2, 1>(depth) : tma_smem<2, 2>(depth))
+                                    : (C == 1 ? tma_smem<4, 1>(depth) : tma_smem<4, 2>(depth));
+    return smem <= 200 * 1024;
+}
+
+cudaError_t launch_stage_f32(const StageArgs<float> &a, int C, int n_vblk, int variant, int depth, cudaStream_t s) {
+    if (variant != BGK_STAGE_PLAIN && stage_f32_tma_supported(a, C, depth)) {
+        if (a.fr.q == 2) return C == 1 ? stage32_tma<2, 1>(a, n_vblk, depth, s) : stage32_tma<2, 2>(a, n_vblk, depth, s);
+        return C == 1 ? stage32_tma<4, 1>(a, n_vblk, depth, s) : stage32_tma<4, 2>(a, n_vblk, depth, s);
+    }
+    if (variant == BGK_STAGE_ASYNC) return cudaErrorInvalidValue;
     switch (a.fr.q) {
         case 2: return stage32_q<2>(a, C, n_vblk, s);
         case 3: return stage32_q<3>(a, C, n_vblk, s);
