@@ -219,9 +219,11 @@ def run_ours(args, rank, world, dev):
         s.profile(True)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("timed")        # lets a profiler select the timed region
         e0.record(stream)
         st = s.step(dt, args.steps)
         e1.record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()

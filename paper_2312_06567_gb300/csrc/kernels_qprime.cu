@@ -137,14 +137,15 @@ struct PointState {
     float feat[MLP_IN];
 };
 
-__device__ __forceinline__ void point_prologue(const QPrimeArgs &a, int p, int lane, PointState &ps) {
+// One thread: the point's moments (sum of the velocity-block partials) and
+// everything derived from them.
+__device__ __forceinline__ void point_prologue(const QPrimeArgs &a, int p, PointState &ps) {
 #pragma unroll
     for (int j = 0; j < BGK_NMOM; ++j) ps.m[j] = 0.0;
-    for (int vb = lane; vb < a.n_vblk; vb += 32) {
+    for (int vb = 0; vb < a.n_vblk; ++vb) {
 #pragma unroll
         for (int j = 0; j < BGK_NMOM; ++j) ps.m[j] += a.part[((size_t)vb * BGK_NMOM + j) * a.P + p];
     }
-    warp_sum_n(ps.m);
     const double *m = ps.m;
     const GasInfo &gs = a.gas;
     const double rho = m[0];
@@ -186,9 +187,13 @@ __device__ __forceinline__ void point_prologue(const QPrimeArgs &a, int p, int l
     ps.feat[8] = (float)(ps.mu / rho * sqrt(0.5 * kTwoPi * 0.5 / ps.theta));   // sqrt(pi / (2 theta))
 }
 
-// Newton's starting point: a supplied guess, the network's, or q.
-__device__ __forceinline__ bool initial_guess(const QPrimeArgs &a, int p, int lane, const PointState &ps, double x[5]) {
+// Newton's starting point: a supplied guess, the network's, or q.  The
+// network runs on the whole warp; every lane returns the same x.  `left` is
+// set when the network's guess left the admissible set (rho', theta' > 0).
+__device__ __forceinline__ bool initial_guess(const QPrimeArgs &a, int p, int lane, const PointState &ps, double x[5],
+                                              bool &left) {
     const double xq[5] = {ps.rho, ps.U0[0], ps.U0[1], ps.U0[2], ps.theta};
+    left = false;
     if (a.guess) {
 #pragma unroll
         for (int j = 0; j < 5; ++j) x[j] = a.guess[(size_t)p * 5 + j];
@@ -202,7 +207,7 @@ __device__ __forceinline__ bool initial_guess(const QPrimeArgs &a, int p, int la
         x[1] = ps.U0[0] + st * dg[1]; x[2] = ps.U0[1] + st * dg[2]; x[3] = ps.U0[2] + st * dg[3];
         x[4] = ps.theta * (1.0 + dg[4]);
         if (x[0] > 0.0 && x[4] > 0.0) return true;
-        if (lane == 0 && a.fallbacks) atomicAdd(a.fallbacks, 1ull);   // left the admissible set
+        left = true;
     }
 #pragma unroll
     for (int j = 0; j < 5; ++j) x[j] = xq[j];
@@ -381,28 +386,60 @@ __device__ __forceinline__ void sum2(float &s, float &c, float v) {
     c = __fadd_rn(c, e);
 }
 
+__device__ __forceinline__ float trapf(int j, int n) { return (j == 0 || j == n - 1) ? 0.5f : 1.0f; }
+
+// add c * (sum + err) of a line pair into a plane pair, error-free up to O(eps^2)
+__device__ __forceinline__ void plane_add(float &P, float &Pc, float c, float sum, float err) {
+    const float ps = __fmul_rn(c, sum);
+    sum2(P, Pc, ps);
+    Pc = __fadd_rn(Pc, fmaf(c, sum, -ps));
+    Pc = fmaf(c, err, Pc);
+}
+
 // Exact index moments J_abc = sum c g32 jt1^a jt2^b jt3^c of the stage's FP32
-// equilibrium (jt = j - jc centred indices, c the trapezoid factors), then
-// gamma from G gamma = T - S with T the centred moments of f itself.
-__device__ __forceinline__ void correction(const QPrimeArgs &a, int lane, const PointState &ps, double c0,
-                                           const double x[5], const Sym3 &A, const double Gsrc[35], double gam[5]) {
+// equilibrium (jt = j - jc centred indices, c the trapezoid factors):
+// J000 J100 J200 J010 J020 J001 J002, reduced over the warp (every lane
+// returns them).  Lane l takes a contiguous run of lines; the line sums are
+// error-free (Sum2) sums of exact products, the lines of one plane
+// (j3 = const) accumulate as (sum, error) pairs with exact coefficients, and
+// the planes in FP64, so the result is accurate to O(2^-48) of the sums.
+__device__ __forceinline__ void correction_sums(const QPrimeArgs &a, int lane, double c0, const double x[5],
+                                                const Sym3 &A, double Jm[7]) {
     const VelGrid &vg = a.vg;
     const int n1 = vg.n[0], n2 = vg.n[1], n3 = vg.n[2];
     const int jc[3] = {(n1 - 1) / 2, (n2 - 1) / 2, (n3 - 1) / 2};
     const double qd[10] = {c0, x[1], x[2], x[3], A.t11, A.t22, A.t33, A.t12, A.t13, A.t23};
     Eq32 e32;
     e32.load(qd);
-    // index moments J000 J100 J200 J010 J020 J001 J002 of this lane's lines (FP64)
-    double Jm[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int line = lane; line < n2 * n3; line += 32) {
+#pragma unroll
+    for (int i = 0; i < 7; ++i) Jm[i] = 0.0;
+    float P[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, Pc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    const int nl = n2 * n3, chunk = (nl + 31) / 32;
+    const int l0 = min(nl, lane * chunk), l1 = min(nl, l0 + chunk);
+    int j3cur = l0 < l1 ? l0 / n2 : -1;
+    auto flush = [&](int j3) {
+        const double c3 = (j3 == 0 || j3 == n3 - 1) ? 0.5 : 1.0, t3 = (double)(j3 - jc[2]);
+        double Pd[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) { Pd[i] = (double)P[i] + (double)Pc[i]; P[i] = Pc[i] = 0.f; }
+        Jm[0] = fma(c3, Pd[0], Jm[0]);
+        Jm[1] = fma(c3, Pd[1], Jm[1]);
+        Jm[2] = fma(c3, Pd[2], Jm[2]);
+        Jm[3] = fma(c3, Pd[3], Jm[3]);
+        Jm[4] = fma(c3, Pd[4], Jm[4]);
+        Jm[5] = fma(c3 * t3, Pd[0], Jm[5]);
+        Jm[6] = fma(c3 * t3 * t3, Pd[0], Jm[6]);
+    };
+    for (int line = l0; line < l1; ++line) {
         const int j2 = line % n2, j3 = line / n2;
+        if (j3 != j3cur) { flush(j3cur); j3cur = j3; }
         const float4 *vl32 = a.vtab32 + (size_t)line * n1;
         float lin, cst;
         e32.line(vl32[0].y, vl32[0].z, lin, cst);
         float L0 = 0.f, C0 = 0.f, L1 = 0.f, C1 = 0.f, L2 = 0.f, C2 = 0.f;
         float jt = (float)(-jc[0]);
         for (int j1 = 0; j1 < n1; ++j1, jt += 1.f) {
-            const float g = e32.g(vl32[j1].x, lin, cst);
+            const float g = e32.g(__ldg(&vl32[j1].x), lin, cst);
             const float cg = (j1 == 0 || j1 == n1 - 1) ? __fmul_rn(0.5f, g) : g;     // exact
             sum2(L0, C0, cg);
             const float p1 = __fmul_rn(cg, jt);
@@ -413,18 +450,26 @@ __device__ __forceinline__ void correction(const QPrimeArgs &a, int lane, const 
             sum2(L2, C2, p2);
             C2 = __fadd_rn(C2, fmaf(cg, jj, -p2));
         }
-        const double l0 = (double)L0 + (double)C0, l1 = (double)L1 + (double)C1, l2 = (double)L2 + (double)C2;
-        const double c23 = ((j2 == 0 || j2 == n2 - 1) ? 0.5 : 1.0) * ((j3 == 0 || j3 == n3 - 1) ? 0.5 : 1.0);
-        const double t2 = (double)(j2 - jc[1]), t3 = (double)(j3 - jc[2]);
-        Jm[0] = fma(c23, l0, Jm[0]);
-        Jm[1] = fma(c23, l1, Jm[1]);
-        Jm[2] = fma(c23, l2, Jm[2]);
-        Jm[3] = fma(c23 * t2, l0, Jm[3]);
-        Jm[4] = fma(c23 * t2 * t2, l0, Jm[4]);
-        Jm[5] = fma(c23 * t3, l0, Jm[5]);
-        Jm[6] = fma(c23 * t3 * t3, l0, Jm[6]);
+        const float c2 = trapf(j2, n2), t2 = (float)(j2 - jc[1]);
+        const float b = __fmul_rn(c2, t2), bb = __fmul_rn(b, t2);                  // exact
+        plane_add(P[0], Pc[0], c2, L0, C0);
+        plane_add(P[1], Pc[1], c2, L1, C1);
+        plane_add(P[2], Pc[2], c2, L2, C2);
+        plane_add(P[3], Pc[3], b, L0, C0);
+        plane_add(P[4], Pc[4], bb, L0, C0);
     }
-    warp_sum_n(Jm);
+    if (j3cur >= 0) flush(j3cur);
+#pragma unroll
+    for (int i = 0; i < 7; ++i) Jm[i] = warp_sum(Jm[i]);
+}
+
+// gamma from G gamma = T - S (one thread), with S the moments of g32 from the
+// index moments Jm, T the centred moments of f itself and G from the
+// solve's moments.
+__device__ __forceinline__ void correction_fit(const QPrimeArgs &a, const PointState &ps, const double x[5],
+                                               const double Jm[7], const double Gsrc[35], double gam[5]) {
+    const VelGrid &vg = a.vg;
+    const int jc[3] = {(vg.n[0] - 1) / 2, (vg.n[1] - 1) / 2, (vg.n[2] - 1) / 2};
     // S_i = sum w phi_i g32 in ut = u - U0 coordinates: u_d = uc_d + jt_d h_d
     const double W = vg.h[0] * vg.h[1] * vg.h[2];
     const double o[3] = {vg.lo[0] + jc[0] * vg.h[0] - ps.U0[0], vg.lo[1] + jc[1] * vg.h[1] - ps.U0[1],
@@ -490,10 +535,35 @@ __device__ __forceinline__ void correction(const QPrimeArgs &a, int lane, const 
     }
 }
 
-__device__ __forceinline__ void point_epilogue(const QPrimeArgs &a, int p, int lane, const PointState &ps,
+// One thread per point: the solution, the equilibrium record, the training
+// log; statistics and log slots are aggregated over the warp (call from all
+// 32 lanes; `valid` marks the lanes that hold a point).
+__device__ __forceinline__ void point_epilogue(const QPrimeArgs &a, int p, bool valid, const PointState &ps,
                                                const double x[5], const Sym3 &A, double c0, const double gam[5],
                                                int tot, bool conv, double res) {
-    if (lane != 0) return;
+    const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+    const unsigned lmask = __ballot_sync(0xffffffffu, valid && conv && a.log != nullptr);
+    const int lane = threadIdx.x & 31;
+    if (a.stats) {
+        const unsigned isum = __reduce_add_sync(0xffffffffu, valid ? (unsigned)tot : 0u);
+        const unsigned imax = __reduce_max_sync(0xffffffffu, valid ? (unsigned)tot : 0u);
+        double r = valid ? (res >= 0.0 ? res : 1.0e300) : 0.0;
+        if (!(r == r)) r = 1.0e300;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+        if (lane == 0 && vmask) {
+            atomicAdd(&a.stats->iter_sum, (unsigned long long)isum);
+            atomicAdd(&a.stats->solves, (unsigned long long)__popc(vmask));
+            atomicMax(&a.stats->iter_max, (int)imax);
+            atomic_max_nonneg_double(&a.stats->res_max_bits, r);
+        }
+    }
+    unsigned long long lbase = 0;
+    if (lmask) {
+        if (lane == 0) lbase = atomicAdd(a.log_count, (unsigned long long)__popc(lmask));
+        lbase = __shfl_sync(0xffffffffu, lbase, 0);
+    }
+    if (!valid) return;
     const double hd = 0.5 * a.gas.delta;
     if (a.qp) {
 #pragma unroll
@@ -512,7 +582,7 @@ __device__ __forceinline__ void point_epilogue(const QPrimeArgs &a, int p, int l
     }
     if (!conv) atomicOr(a.status, BGK_DEV_NOCONV);
     if (a.log && conv) {
-        const unsigned long long slot = atomicAdd(a.log_count, 1ull);
+        const unsigned long long slot = lbase + __popc(lmask & ((1u << lane) - 1u));
         if ((long long)slot < a.log_max) {
             float *r = a.log + (size_t)slot * MLP_LOG_STRIDE;
 #pragma unroll
@@ -524,12 +594,6 @@ __device__ __forceinline__ void point_epilogue(const QPrimeArgs &a, int p, int l
             r[MLP_IN + 3] = (float)((x[3] - ps.U0[2]) / st);
             r[MLP_IN + 4] = (float)(x[4] / ps.theta - 1.0);
         }
-    }
-    if (a.stats) {
-        atomicAdd(&a.stats->iter_sum, (unsigned long long)tot);
-        atomicAdd(&a.stats->solves, 1ull);
-        atomicMax(&a.stats->iter_max, tot);
-        atomic_max_nonneg_double(&a.stats->res_max_bits, res);
     }
 }
 
@@ -667,67 +731,173 @@ struct Engine32 {
                     for (int mm = 0; mm <= 4 - aa - bb; ++mm) M[midx(mm, aa, bb)] = fmaf(P, Tm[mm], M[midx(mm, aa, bb)]);
                 }
         }
+        // the lane partials carry FP32 rounding already; the tree sum in FP32
+        // keeps the reduction off the FP64 pipe
 #pragma unroll
-        for (int i = 0; i < 35; ++i) Md[i] = warp_sum((double)M[i]);
+        for (int i = 0; i < 35; ++i) Md[i] = (double)warp_sumf(M[i]);
     }
 };
 
-template <bool F32>
-__global__ void __launch_bounds__(256) k_qprime(QPrimeArgs a) {
-    __shared__ double tab[F32 ? 1 : 8][F32 ? 1 : BGK_MAXV][5];
-    const int wib = threadIdx.x >> 5;
-    const int warp = blockIdx.x * 8 + wib;
-    const int lane = threadIdx.x & 31;
-    if (warp >= a.P) return;                 // whole warps exit together
-    const int p = warp;
-    PointState ps;
-    point_prologue(a, p, lane, ps);
-    Engine64 e64;
-    Engine32 e32;
-    if (!F32) e64.init(tab[F32 ? 0 : wib], a.vg, ps, lane);
+// One block solves a batch of QB points.  The velocity sums run one warp per
+// point (QW warps take the batch's points in turn); the per-point algebra
+// (prologue, Newton step, correction fit, epilogue) runs one lane of warp 0
+// per point, so the FP64 work of a point issues once rather than on 32 lanes.
+constexpr int QB = 32;
+constexpr int QW = 8;
 
-    double x[5];
-    bool from_guess = initial_guess(a, p, lane, ps, x);
-    const double xq[5] = {ps.rho, ps.U0[0], ps.U0[1], ps.U0[2], ps.theta};
+struct QPShared {
+    PointState ps[QB];
+    double x[QB][5];
+    double A[QB][6];
+    double c0[QB];
+    double res[QB];
+    double M[QB][35];
+    double Jm[QB][7];
+    int it[QB], tot[QB];
+    int conv[QB], from_guess[QB], active[QB];
+    int any_active;
+};
+
+__device__ __forceinline__ Sym3 load_sym3(const double *t) { return Sym3{t[0], t[1], t[2], t[3], t[4], t[5]}; }
+
+template <bool F32>
+__global__ void __launch_bounds__(QB * QW, 2) k_qprime(QPrimeArgs a) {
+    __shared__ QPShared S;
+    extern __shared__ double dyn_tab[];      // FP64 engine: [QW][n1][5] tables w1 ut1^m
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int p0 = blockIdx.x * QB;
+    const int nb = min(QB, a.P - p0);
     const double tol = F32 ? a.tol32 : a.tol;
-    int it = 0, tot = 0;         // updates of the current solve / of all attempts
-    bool conv = false;
-    double res = 1.0e300;
-    Sym3 A;
-    double c0 = 0.0;
-    double M[35];
-    for (;;) {
-        equilibrium_params(ps, a.gas.Pr, x, A, c0);
-        if (F32) e32.moments(a.vg, ps, x, A, c0, lane, M);
-        else e64.moments(a.vg, ps, x, A, c0, lane, M);
-        double R[5], J[5][5];
-        res = assemble(M, ps, a.gas, x, A, R, J);
-        if (res <= tol) { conv = true; break; }
-        // The learned guess is judged by its own residual: one that is not
-        // small (or a solve that runs out of updates from it) restarts from q.
-        if (from_guess && ((it == 0 && !(res <= 1e-3)) || it >= a.max_iter || !(res == res))) {
+    const double Pr = a.gas.Pr;
+    // -- prologue: one lane per point
+    if (wib == 0 && lane < nb) point_prologue(a, p0 + lane, S.ps[lane]);
+    __syncthreads();
+    // -- starting points: one warp per point (the network runs on the warp)
+    for (int i = wib; i < nb; i += QW) {
+        double x[5];
+        bool left;
+        const bool fg = initial_guess(a, p0 + i, lane, S.ps[i], x, left);
+        if (lane == 0) {
 #pragma unroll
-            for (int j = 0; j < 5; ++j) x[j] = xq[j];
-            from_guess = false;
-            it = 0;
-            if (lane == 0 && a.fallbacks) atomicAdd(a.fallbacks, 1ull);
-            continue;
+            for (int j = 0; j < 5; ++j) S.x[i][j] = x[j];
+            S.from_guess[i] = fg;
+            S.it[i] = 0; S.tot[i] = 0; S.conv[i] = 0; S.active[i] = 1;
+            S.res[i] = 1.0e300;
+            if (left && a.fallbacks) atomicAdd(a.fallbacks, 1ull);
         }
-        if (it >= a.max_iter || !(res == res)) break;
-        if (!newton_update(J, R, x, ps.B, a.gas.Pr)) break;
-        ++it;
-        ++tot;
     }
-    double gam[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    if (a.mixed && a.eq) correction(a, lane, ps, c0, x, A, M, gam);
-    point_epilogue(a, p, lane, ps, x, A, c0, gam, tot, conv, res);
+    __syncthreads();
+    // -- Newton iterations over the batch until every point has stopped
+    for (;;) {
+        if (wib == 0 && lane < nb && S.active[lane]) {
+            Sym3 A;
+            double c0;
+            equilibrium_params(S.ps[lane], Pr, S.x[lane], A, c0);
+            S.A[lane][0] = A.t11; S.A[lane][1] = A.t22; S.A[lane][2] = A.t33;
+            S.A[lane][3] = A.t12; S.A[lane][4] = A.t13; S.A[lane][5] = A.t23;
+            S.c0[lane] = c0;
+        }
+        __syncthreads();
+        for (int i = wib; i < nb; i += QW) {
+            if (!S.active[i]) continue;
+            const Sym3 A = load_sym3(S.A[i]);
+            double x[5];
+#pragma unroll
+            for (int j = 0; j < 5; ++j) x[j] = S.x[i][j];
+            double M[35];
+            if (F32) {
+                Engine32 e32;
+                e32.moments(a.vg, S.ps[i], x, A, S.c0[i], lane, M);
+            } else {
+                Engine64 e64;
+                e64.init(reinterpret_cast<double (*)[5]>(dyn_tab + (size_t)wib * a.vg.n[0] * 5), a.vg, S.ps[i], lane);
+                e64.moments(a.vg, S.ps[i], x, A, S.c0[i], lane, M);
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int j = 0; j < 35; ++j) S.M[i][j] = M[j];
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        if (wib == 0) {
+            bool act = false;
+            if (lane < nb && S.active[lane]) {
+                const PointState &ps = S.ps[lane];
+                double x[5];
+#pragma unroll
+                for (int j = 0; j < 5; ++j) x[j] = S.x[lane][j];
+                const Sym3 A = load_sym3(S.A[lane]);
+                double R[5], J[5][5];
+                const double res = assemble(S.M[lane], ps, a.gas, x, A, R, J);
+                S.res[lane] = res;
+                int it = S.it[lane];
+                act = true;
+                if (res <= tol) {
+                    S.conv[lane] = 1;
+                    act = false;
+                } else if (S.from_guess[lane] && ((it == 0 && !(res <= 1e-3)) || it >= a.max_iter || !(res == res))) {
+                    // the learned guess is judged by its own residual: one that is
+                    // not small (or a solve that runs out of updates from it)
+                    // restarts from q
+                    x[0] = ps.rho; x[1] = ps.U0[0]; x[2] = ps.U0[1]; x[3] = ps.U0[2]; x[4] = ps.theta;
+                    S.from_guess[lane] = 0;
+                    it = 0;
+                    if (a.fallbacks) atomicAdd(a.fallbacks, 1ull);
+                } else if (it >= a.max_iter || !(res == res) || !newton_update(J, R, x, ps.B, Pr)) {
+                    act = false;
+                } else {
+                    ++it;
+                    ++S.tot[lane];
+                }
+                S.it[lane] = it;
+#pragma unroll
+                for (int j = 0; j < 5; ++j) S.x[lane][j] = x[j];
+                S.active[lane] = act;
+            }
+            const bool any = __any_sync(0xffffffffu, act);
+            if (lane == 0) S.any_active = any;
+        }
+        __syncthreads();
+        if (!S.any_active) break;
+    }
+    // -- mixed form: exact moments of the stage's FP32 equilibrium, one warp per point
+    const bool fit = a.mixed && a.eq;
+    if (fit) {
+        for (int i = wib; i < nb; i += QW) {
+            double x[5], Jm[7];
+#pragma unroll
+            for (int j = 0; j < 5; ++j) x[j] = S.x[i][j];
+            correction_sums(a, lane, S.c0[i], x, load_sym3(S.A[i]), Jm);
+            if (lane == 0) {
+#pragma unroll
+                for (int j = 0; j < 7; ++j) S.Jm[i][j] = Jm[j];
+            }
+        }
+        __syncthreads();
+    }
+    // -- correction fit and epilogue: one lane per point
+    if (wib == 0) {
+        const bool valid = lane < nb;
+        const int i = valid ? lane : 0;
+        double x[5], gam[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+        for (int j = 0; j < 5; ++j) x[j] = S.x[i][j];
+        if (fit && valid) correction_fit(a, S.ps[i], x, S.Jm[i], S.M[i], gam);
+        point_epilogue(a, p0 + i, valid, S.ps[i], x, load_sym3(S.A[i]), S.c0[i], gam, S.tot[i], S.conv[i] != 0,
+                       S.res[i]);
+    }
 }
 
 }  // namespace
 
 cudaError_t launch_qprime(const QPrimeArgs &a, bool fp32_sums, cudaStream_t s) {
-    const unsigned grid = (unsigned)((a.P + 7) / 8);
-    if (fp32_sums) k_qprime<true><<<grid, 256, 0, s>>>(a);
-    else k_qprime<false><<<grid, 256, 0, s>>>(a);
+    const unsigned grid = (unsigned)((a.P + QB - 1) / QB);
+    if (fp32_sums) {
+        k_qprime<true><<<grid, QB * QW, 0, s>>>(a);
+    } else {
+        const size_t dyn = (size_t)QW * a.vg.n[0] * 5 * sizeof(double);
+        k_qprime<false><<<grid, QB * QW, dyn, s>>>(a);
+    }
     return cudaGetLastError();
 }
