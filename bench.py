@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--workload", default="taylor_green", choices=sorted(WORKLOADS))
-    ap.add_argument("--stage-kernel", default="tune", choices=["tune", "auto", "plain", "async"],
+    ap.add_argument("--stage-kernel", default="tune", choices=["tune", "auto", "plain", "async", "line", "line_wide", "half", "half_wide"],
                     help="mixed-form stage kernel; 'tune' times the candidates on the workload (untimed)")
     ap.add_argument("--depth", type=int, default=6, help="copy-ring depth of the async stage kernel")
     return ap.parse_args()

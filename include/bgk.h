@@ -131,22 +131,29 @@ BGK_API bgk_status bgk_set_qprime_engine(bgk_ctx *ctx, int fp32_sums);
 
 /* Kernel of the mixed-form stage (the fused step of section "Methodology":
  * FR advection, BGK source, Runge--Kutta update and the moments of the
- * result).  variant 0 (default): the asynchronous-copy kernel where it
- * applies, else the plain one; 1: the plain kernel (each thread loads its
- * operands itself, one block-wide barrier per velocity); 2: the
- * asynchronous-copy kernel (a producer warp stages the element run, its
- * upwind neighbours and f^n for up to `depth` velocities ahead with bulk
- * copies completing on mbarriers).  Both compute the same values bit for
- * bit.  depth: 2..16 copy-ring stages (default 6).  The asynchronous kernel
- * needs p = 1 or 3 (element slabs of whole 16-byte units) and 16-byte
- * aligned state buffers; every wait in it is bounded and a wait that gives
- * up makes the next status check return BGK_ETIMEOUT.  Errors: BGK_EINVAL
- * (range), BGK_ENOTSUP (variant 2 on the FP64 form or an unsupported order). */
+ * result).  All variants compute the same values bit for bit.
+ *   0 (default) the asynchronous-copy kernel where it applies, else the plain one;
+ *   1 plain: each thread loads its operands itself, one block-wide barrier
+ *     per velocity;
+ *   2 async: a producer warp stages the element run, its upwind neighbours
+ *     and f^n for up to `depth` velocities ahead with bulk copies completing
+ *     on mbarriers; one thread per solution node;
+ *   3 line: the same copy ring, one thread per first-axis node line (p + 1
+ *     points), short element runs;
+ *   4 line, runs twice as long;
+ *   5 half: the same copy ring, one thread per half first-axis node line;
+ *   6 half, runs twice as long.
+ * depth: 2..16 copy-ring stages (default 6).  Variants 2-6 need p = 1 or 3
+ * (element slabs of whole 16-byte units) and 16-byte aligned state buffers
+ * (bgk_stage runs caller buffers that are not on the plain kernel); every
+ * wait in them is bounded and a wait that gives up makes the next status
+ * check return BGK_ETIMEOUT.  Errors: BGK_EINVAL (range), BGK_ENOTSUP
+ * (variants 2-6 on the FP64 form or an unsupported order). */
 BGK_API bgk_status bgk_set_stage_kernel(bgk_ctx *ctx, int variant, int depth);
 
 /* Autotune the mixed-form stage kernel on this context's own problem: time
- * the plain kernel and the asynchronous one at every supported ring depth
- * (2, 3, 4, 6, 8, 12, 16), each over `reps` stages with f^n and the moment
+ * the plain kernel and every supported asynchronous variant at every ring
+ * depth (2, 3, 4, 6, 8, 12, 16), each over `reps` stages with f^n and the moment
  * epilogue (time step dt), from the current state into a scratch buffer, and
  * keep the fastest (as bgk_set_stage_kernel would).  The state is not
  * changed; the cached moments are recomputed by the next step.  Outputs (each

@@ -248,10 +248,11 @@ class Solver:
     def set_qprime_engine(self, fp32_sums):
         self._check(self.lib.bgk_set_qprime_engine(self._h, 1 if fp32_sums else 0))
 
-    STAGE_KERNELS = {"auto": 0, "plain": 1, "async": 2}
+    STAGE_KERNELS = {"auto": 0, "plain": 1, "async": 2, "line": 3, "line_wide": 4, "half": 5, "half_wide": 6}
 
     def set_stage_kernel(self, variant="auto", depth=6):
-        """Mixed-form stage kernel: "auto", "plain" or "async" (bulk-copy ring of `depth` stages)."""
+        """Mixed-form stage kernel: "auto", "plain", "async", "line", "line_wide", "half" or
+        "half_wide" (all but the first two on a bulk-copy ring of `depth` stages)."""
         self._check(self.lib.bgk_set_stage_kernel(self._h, self.STAGE_KERNELS[variant], int(depth)))
 
     def tune_stage(self, dt, reps=3):

@@ -33,6 +33,7 @@ struct bgk_ctx {
     double *part;                     // [n_vblk][NMOM][P]
     double *mom;                      // [P][NMOM]
     double *eq;                       // [P][NEQ]
+    float *eq32;                      // [P][NEQ32] (mixed form)
     double *qp;                       // [P][5]
     double *vtab;                     // [Nu][VTAB]
     float4 *vtab32;                   // [Nu] FP32 velocity nodes
@@ -225,6 +226,7 @@ bgk_status run_qprime(bgk_ctx *ctx, const double *part, int n_vblk, int P, doubl
                       int *iters, const double *guess) {
     QPrimeArgs a{};
     a.part = part; a.n_vblk = n_vblk; a.vtab = ctx->vtab; a.vtab32 = ctx->vtab32; a.guess = guess; a.eq = eq; a.qp = qp;
+    a.eq32 = (eq && eq == ctx->eq) ? ctx->eq32 : nullptr;
     a.iters = iters; a.status = ctx->status; a.stats = ctx->stats; a.P = P; a.Nu = ctx->Nu;
     a.tol = ctx->tol; a.tol32 = 1e-6; a.max_iter = ctx->max_iter; a.gas = ctx->gas; a.vg = ctx->vg;
     a.mixed = ctx->precision == BGK_MIXED ? 1 : 0;
@@ -245,6 +247,7 @@ StageArgs<T> stage_args(bgk_ctx *ctx, const void *fn, const void *fs, void *fo, 
     s.f_n = (const T *)fn; s.f_s = (const T *)fs; s.f_out = (T *)fo;
     s.eq = ctx->eq; s.vtab = ctx->vtab; s.vtab32 = ctx->vtab32; s.bcval = ctx->bcval;
     s.part = moments ? ctx->part : nullptr;
+    s.eq32 = ctx->eq32;
     s.status = ctx->status;
     s.a = a; s.b = b; s.c = c; s.Nu = ctx->Nu; s.P = ctx->P; s.Kblk = ctx->Kblk;
     s.vg = ctx->vg; s.fr = ctx->fr; s.mesh = ctx->mesh;
@@ -259,9 +262,13 @@ bgk_status run_stage(bgk_ctx *ctx, const void *fn, const void *fs, void *fo, dou
     if (ctx->precision == BGK_FP64)
         CU(launch_stage_f64(stage_args<double>(ctx, fn, fs, fo, a, b, c, moments), ctx->C, ctx->n_vblk,
                             ctx->stream));
-    else
-        CU(launch_stage_f32(stage_args<float>(ctx, fn, fs, fo, a, b, c, moments), ctx->C, ctx->n_vblk,
-                            ctx->stage_variant, ctx->stage_depth, ctx->stream));
+    else {
+        const StageArgs<float> sa = stage_args<float>(ctx, fn, fs, fo, a, b, c, moments);
+        // caller buffers that a chosen variant cannot take (alignment) run on the plain kernel
+        const int v = stage_f32_variant_supported(sa, ctx->C, ctx->stage_variant, ctx->stage_depth) ? ctx->stage_variant
+                                                                                                   : BGK_STAGE_AUTO;
+        CU(launch_stage_f32(sa, ctx->C, ctx->n_vblk, v, ctx->stage_depth, ctx->stream));
+    }
     return BGK_OK;
 }
 
@@ -402,6 +409,9 @@ bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
     if (st == BGK_OK) cu(cudaMalloc(&ctx->part, (size_t)ctx->n_vblk * BGK_NMOM * P * sizeof(double)), "cudaMalloc(part)");
     if (st == BGK_OK) cu(cudaMalloc(&ctx->mom, P * BGK_NMOM * sizeof(double)), "cudaMalloc(mom)");
     if (st == BGK_OK) cu(cudaMalloc(&ctx->eq, P * BGK_NEQ * sizeof(double)), "cudaMalloc(eq)");
+    ctx->eq32 = nullptr;
+    if (st == BGK_OK && precision == BGK_MIXED)
+        cu(cudaMalloc(&ctx->eq32, P * BGK_NEQ32 * sizeof(float)), "cudaMalloc(eq32)");
     if (st == BGK_OK) cu(cudaMalloc(&ctx->qp, P * 5 * sizeof(double)), "cudaMalloc(qp)");
     if (st == BGK_OK) cu(cudaMalloc(&ctx->iters, P * sizeof(int)), "cudaMalloc(iters)");
     if (st == BGK_OK) cu(cudaMalloc(&ctx->vtab, ctx->vtab_h.size() * sizeof(double)), "cudaMalloc(vtab)");
@@ -444,7 +454,7 @@ bgk_status bgk_destroy(bgk_ctx *ctx) {
     for (auto e : ctx->ev_pool) cudaEventDestroy(e);
     for (int i = 0; i < 3; ++i) cudaFree(ctx->f[i]);
     cudaFree(ctx->part); cudaFree(ctx->mom); cudaFree(ctx->eq); cudaFree(ctx->qp);
-    cudaFree(ctx->iters); cudaFree(ctx->vtab); cudaFree(ctx->vtab32); cudaFree(ctx->bcval); cudaFree(ctx->status);
+    cudaFree(ctx->iters); cudaFree(ctx->eq32); cudaFree(ctx->vtab); cudaFree(ctx->vtab32); cudaFree(ctx->bcval); cudaFree(ctx->status);
     cudaFree(ctx->stats);
     cudaFree(ctx->mlp_w); cudaFree(ctx->mlp_norm); cudaFree(ctx->mlp_m); cudaFree(ctx->mlp_v);
     cudaFree(ctx->mlp_grad); cudaFree(ctx->mlp_loss); cudaFree(ctx->log); cudaFree(ctx->log_count);
@@ -537,14 +547,14 @@ bgk_status bgk_set_qprime_engine(bgk_ctx *ctx, int fp32_sums) {
 }
 
 bgk_status bgk_set_stage_kernel(bgk_ctx *ctx, int variant, int depth) {
-    if (!ctx || variant < BGK_STAGE_AUTO || variant > BGK_STAGE_ASYNC || depth < 2 || depth > BGK_MAX_DEPTH)
+    if (!ctx || variant < BGK_STAGE_AUTO || variant > BGK_STAGE_HALF_WIDE || depth < 2 || depth > BGK_MAX_DEPTH)
         return BGK_EINVAL;
-    if (variant == BGK_STAGE_ASYNC) {
+    if (variant >= BGK_STAGE_ASYNC) {
         if (ctx->precision != BGK_MIXED)
-            return fail(ctx, BGK_ENOTSUP, "the asynchronous-copy stage kernel is for the mixed form only");
+            return fail(ctx, BGK_ENOTSUP, "the asynchronous-copy stage kernels are for the mixed form only");
         const StageArgs<float> a = stage_args<float>(ctx, ctx->f[0], ctx->f[1], ctx->f[2], 0.5, 0.5, 1.0, true);
-        if (!stage_f32_tma_supported(a, ctx->C, depth))
-            return fail(ctx, BGK_ENOTSUP, "asynchronous-copy stage kernel needs p = 1 or 3 and fitting shared memory");
+        if (!stage_f32_variant_supported(a, ctx->C, variant, depth))
+            return fail(ctx, BGK_ENOTSUP, "asynchronous-copy stage kernels need p = 1 or 3 and fitting shared memory");
     }
     ctx->stage_variant = variant;
     ctx->stage_depth = depth;
@@ -571,8 +581,9 @@ bgk_status bgk_tune_stage(bgk_ctx *ctx, double dt, int reps, int *variant_out, i
     const StageArgs<float> sa = stage_args<float>(ctx, ctx->f[0], ctx->f[0], ctx->f[2], 0.75, 0.25, 0.25 * dt, true);
     struct Cand { int v, d; };
     std::vector<Cand> cands{{BGK_STAGE_PLAIN, ctx->stage_depth}};
-    for (int d : {2, 3, 4, 6, 8, 12, 16})
-        if (stage_f32_tma_supported(sa, ctx->C, d)) cands.push_back({BGK_STAGE_ASYNC, d});
+    for (int v : {BGK_STAGE_ASYNC, BGK_STAGE_LINE, BGK_STAGE_LINE_WIDE, BGK_STAGE_HALF, BGK_STAGE_HALF_WIDE})
+        for (int d : {2, 3, 4, 6, 8, 12, 16})
+            if (stage_f32_variant_supported(sa, ctx->C, v, d)) cands.push_back({v, d});
     cudaEvent_t ea = nullptr, eb = nullptr;
     CU(cudaEventCreate(&ea));
     CU(cudaEventCreate(&eb));

@@ -12,6 +12,12 @@
 #define BGK_MAXQ 5          // FR order p <= 4
 #define BGK_NMOM 11         // raw moment slots per point
 #define BGK_NEQ 20          // equilibrium record per point (12 used by the FP64 form)
+// FP32 equilibrium record per point (mixed form), the FP32 values the stage
+// kernels derive from the FP64 record, in the order they are used:
+//   0 E0  1 V1  2 A11  3 1/tau  4 gamma1  5 gamma4/2  6 U0_1  7 gfac
+//   8 V2  9 V3  10 A12  11 A13  12 A22  13 A23  14 A33  15 gamma0
+//   16 gamma2  17 gamma3  18 U0_2  19 U0_3  20 gamma4  21..23 unused
+#define BGK_NEQ32 24
 #define BGK_VTAB 8          // velocity table record: u1 u2 u3 w e=|u|^2/2 w*u1 w*u1^2 (2/h1)*u1
 #define BGK_MAXV 128        // nodes per velocity axis at most
 
@@ -24,6 +30,10 @@
 #define BGK_STAGE_AUTO 0
 #define BGK_STAGE_PLAIN 1
 #define BGK_STAGE_ASYNC 2
+#define BGK_STAGE_LINE 3        // asynchronous copies, one thread per node line, short runs
+#define BGK_STAGE_LINE_WIDE 4   // the same with runs twice as long
+#define BGK_STAGE_HALF 5        // asynchronous copies, one thread per half node line, short runs
+#define BGK_STAGE_HALF_WIDE 6   // the same with runs twice as long
 #define BGK_MAX_DEPTH 16
 
 // 1-D FR operators on Gauss--Legendre nodes (section "Numerical method").
@@ -107,6 +117,7 @@ struct StageArgs {
     const float4 *vtab32;    // [Nu] (u1, u2, u3, 0) rounded to FP32
     const double *bcval;     // [6][C][Nu] exterior Maxwellian values of Dirichlet faces
     double *part;            // [n_vblk][BGK_NMOM][P] moment partials of f_out (or null)
+    const float *eq32;       // [P][BGK_NEQ32] (mixed form)
     unsigned int *status;    // device status word (BGK_DEV_* bits)
     double a, b, c;
     // FP32 copies made on the host: a, a + b, c, and the metric terms 2/h_d
@@ -126,6 +137,7 @@ struct QPrimeArgs {
     const float4 *vtab32;
     const double *guess;     // [P][5] or null
     double *eq;              // [P][BGK_NEQ] or null
+    float *eq32;             // [P][BGK_NEQ32] or null (written with eq)
     double *qp;              // [P][5] or null
     int *iters;              // [P] or null
     unsigned int *status;
@@ -165,6 +177,11 @@ cudaError_t launch_moments_f32(const float *f, double *part, const double *vtab,
 cudaError_t launch_stage_f32(const StageArgs<float> &a, int C, int n_vblk, int variant, int depth,
                              cudaStream_t s);
 bool stage_f32_tma_supported(const StageArgs<float> &a, int C, int depth);
+// line kernels: kind 0 line, 1 line_wide, 2 half, 3 half_wide
+bool stage_f32_line_supported(const StageArgs<float> &a, int C, int kind, int depth);
+cudaError_t launch_stage_f32_line(const StageArgs<float> &a, int C, int n_vblk, int kind, int depth, cudaStream_t s);
+// any FP32 stage variant: is it available for these arguments
+bool stage_f32_variant_supported(const StageArgs<float> &a, int C, int variant, int depth);
 cudaError_t launch_maxwellian_f32(float *f, const double *q, const double *vtab, int Nu, int P, int C,
                                   double delta, cudaStream_t s);
 cudaError_t launch_reduce_moments(const double *part, int n_vblk, int P, double *m_out,

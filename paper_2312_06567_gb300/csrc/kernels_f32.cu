@@ -13,241 +13,9 @@
 // with exact coefficients c2 jt2^b in Kahan-compensated FP32, and the planes
 // in FP64; the index moments J_abc = sum c F jt1^a jt2^b jt3^c are turned
 // into the raw moments sum w u^alpha F in FP64 at the end.
-#include "bgk_internal.cuh"
+#include "stage_f32_common.cuh"
 
 namespace {
-
-// Error-free accumulation (Ogita, Rump & Oishi 2005, "Sum2"): TwoSum keeps
-// the exact rounding error of each addition in comp; the represented sum is
-// s + comp, accurate to O(eps^2) of the sum of magnitudes.
-__device__ __forceinline__ void sum2(float &s, float &comp, float v) {
-    const float t = __fadd_rn(s, v);
-    const float bp = __fsub_rn(t, s);
-    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp));
-    s = t;
-    comp = __fadd_rn(comp, e);
-}
-
-// Index moments (J000, J100, J200, J010, J110, J020, J001, J101, J011, J002, JG)
-// of one thread -> the 11 raw moment slots, W = h1 h2 h3.
-__device__ __forceinline__ void index_to_raw(const double J[11], const VelGrid &vg, const double uc[3],
-                                             double m[BGK_NMOM]) {
-    const double W = vg.h[0] * vg.h[1] * vg.h[2];
-    const double h1 = vg.h[0], h2 = vg.h[1], h3 = vg.h[2];
-    const double J000 = J[0], J100 = J[1], J200 = J[2], J010 = J[3], J110 = J[4], J020 = J[5];
-    const double J001 = J[6], J101 = J[7], J011 = J[8], J002 = J[9];
-    m[0] = W * J000;
-    m[1] = W * (uc[0] * J000 + h1 * J100);
-    m[2] = W * (uc[1] * J000 + h2 * J010);
-    m[3] = W * (uc[2] * J000 + h3 * J001);
-    m[4] = W * (uc[0] * uc[0] * J000 + 2.0 * uc[0] * h1 * J100 + h1 * h1 * J200);
-    m[5] = W * (uc[1] * uc[1] * J000 + 2.0 * uc[1] * h2 * J010 + h2 * h2 * J020);
-    m[6] = W * (uc[2] * uc[2] * J000 + 2.0 * uc[2] * h3 * J001 + h3 * h3 * J002);
-    m[7] = W * (uc[0] * uc[1] * J000 + uc[0] * h2 * J010 + h1 * uc[1] * J100 + h1 * h2 * J110);
-    m[8] = W * (uc[0] * uc[2] * J000 + uc[0] * h3 * J001 + h1 * uc[2] * J100 + h1 * h3 * J101);
-    m[9] = W * (uc[1] * uc[2] * J000 + uc[1] * h3 * J001 + h2 * uc[2] * J010 + h2 * h3 * J011);
-    m[10] = W * J[10];
-}
-
-// The same accumulation with the plane pairs and the FP64 index moments kept
-// in shared memory (column `t` of [field][n] arrays, so a warp's accesses hit
-// distinct banks): they change once per line and once per plane, and holding
-// them in registers would cost the pipelined stage kernel a third of its
-// occupancy.
-struct IndexMomentsS {
-    float L[4], Lc[4];
-    float *P;                 // [14][n]: P[0..6] then Pc[0..6]
-    double *J;                // [11][n]
-    int n;
-    int j3cur;
-    __device__ void init(float *Ps, double *Js, int ncol, int t) {
-        P = Ps + t;
-        J = Js + t;
-        n = ncol;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) L[i] = Lc[i] = 0.f;
-#pragma unroll
-        for (int i = 0; i < 14; ++i) P[i * n] = 0.f;
-#pragma unroll
-        for (int i = 0; i < 11; ++i) J[i * n] = 0.0;
-        j3cur = -1;
-    }
-    __device__ __forceinline__ void add(float cj1, float jt1, float F, float G) {
-        const float cF = __fmul_rn(cj1, F);
-        sum2(L[0], Lc[0], cF);
-        const float p1 = __fmul_rn(cF, jt1);
-        sum2(L[1], Lc[1], p1);
-        Lc[1] = __fadd_rn(Lc[1], fmaf(cF, jt1, -p1));
-        const float jj = __fmul_rn(jt1, jt1);
-        const float p2 = __fmul_rn(cF, jj);
-        sum2(L[2], Lc[2], p2);
-        Lc[2] = __fadd_rn(Lc[2], fmaf(cF, jj, -p2));
-        sum2(L[3], Lc[3], __fmul_rn(cj1, G));
-    }
-    __device__ __forceinline__ void plane_add(int i, float c, float sum, float err) {
-        float ps = P[i * n], pc = P[(7 + i) * n];
-        const float pr = __fmul_rn(c, sum);
-        sum2(ps, pc, pr);
-        pc = __fadd_rn(pc, fmaf(c, sum, -pr));
-        pc = fmaf(c, err, pc);
-        P[i * n] = ps;
-        P[(7 + i) * n] = pc;
-    }
-    __device__ __forceinline__ void end_line(float c2, float jt2) {
-        const float a = c2, b = __fmul_rn(c2, jt2), bb = __fmul_rn(__fmul_rn(c2, jt2), jt2);
-        plane_add(0, a, L[0], Lc[0]);
-        plane_add(1, a, L[1], Lc[1]);
-        plane_add(2, a, L[2], Lc[2]);
-        plane_add(3, b, L[0], Lc[0]);
-        plane_add(4, b, L[1], Lc[1]);
-        plane_add(5, bb, L[0], Lc[0]);
-        plane_add(6, a, L[3], Lc[3]);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) L[i] = Lc[i] = 0.f;
-    }
-    __device__ __forceinline__ void flush_plane(float c3, float jt3) {
-        const double c = c3, t = jt3;
-        double Pd[7];
-#pragma unroll
-        for (int i = 0; i < 7; ++i) {
-            Pd[i] = (double)P[i * n] + (double)P[(7 + i) * n];
-            P[i * n] = 0.f;
-            P[(7 + i) * n] = 0.f;
-        }
-        J[0] = fma(c, Pd[0], J[0]);
-        J[n] = fma(c, Pd[1], J[n]);
-        J[2 * n] = fma(c, Pd[2], J[2 * n]);
-        J[3 * n] = fma(c, Pd[3], J[3 * n]);
-        J[4 * n] = fma(c, Pd[4], J[4 * n]);
-        J[5 * n] = fma(c, Pd[5], J[5 * n]);
-        J[6 * n] = fma(c * t, Pd[0], J[6 * n]);
-        J[7 * n] = fma(c * t, Pd[1], J[7 * n]);
-        J[8 * n] = fma(c * t, Pd[3], J[8 * n]);
-        J[9 * n] = fma(c * t * t, Pd[0], J[9 * n]);
-        J[10 * n] = fma(c, Pd[6], J[10 * n]);
-    }
-    __device__ __forceinline__ void get(double out[11]) const {
-#pragma unroll
-        for (int i = 0; i < 11; ++i) out[i] = J[i * n];
-    }
-};
-
-// Dt[side] = D - dg (x) l rounded to FP32 with explicit roundings, so every
-// use (the operator itself and the conservation weights built from it) sees
-// the same FP32 entries.
-__device__ __forceinline__ float folded_dt(const FROps &fr, int side, int i, int j) {
-    const double dg = side == 0 ? fr.dgL[i] : fr.dgR[i];
-    const double l = side == 0 ? fr.lm[j] : fr.lp[j];
-    return __double2float_rn(__dsub_rn(fr.D[i][j], __dmul_rn(dg, l)));
-}
-
-__device__ __forceinline__ float trap(int j, int n) { return (j == 0 || j == n - 1) ? 0.5f : 1.0f; }
-
-// Per-thread accumulator of index moments over a run of whole first-axis lines.
-// Line sums are error-free (Sum2) sums of exact products (c F exact; c F jt
-// and c F jt^2 split into product + FMA-exact error); plane sums accumulate
-// the lines' (sum, error) pairs the same way; planes fold in FP64.  So the
-// index moments are accurate to O(2^-48) of the sums, with no bias.
-struct IndexMoments {
-    float L[4], Lc[4];                    // current line: 0, jt, jt^2, G (sum, error) pairs
-    float P[7], Pc[7];                    // current plane: 00 10 20 01 11 02 G
-    double J[11];
-    int j3cur;
-    __device__ void init() {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) L[i] = Lc[i] = 0.f;
-#pragma unroll
-        for (int i = 0; i < 7; ++i) P[i] = Pc[i] = 0.f;
-#pragma unroll
-        for (int i = 0; i < 11; ++i) J[i] = 0.0;
-        j3cur = -1;
-    }
-    __device__ __forceinline__ void add(float cj1, float jt1, float F, float G) {
-        const float cF = __fmul_rn(cj1, F);                 // exact: cj1 in {1/2, 1}
-        sum2(L[0], Lc[0], cF);
-        const float p1 = __fmul_rn(cF, jt1);
-        sum2(L[1], Lc[1], p1);
-        Lc[1] = __fadd_rn(Lc[1], fmaf(cF, jt1, -p1));       // exact product error joins the error term
-        const float jj = __fmul_rn(jt1, jt1);               // exact: |jt1| < 128
-        const float p2 = __fmul_rn(cF, jj);
-        sum2(L[2], Lc[2], p2);
-        Lc[2] = __fadd_rn(Lc[2], fmaf(cF, jj, -p2));
-        sum2(L[3], Lc[3], __fmul_rn(cj1, G));
-    }
-    __device__ __forceinline__ void flush_plane(float c3, float jt3) {
-        const double c = c3, t = jt3;
-        // the plane sums are P + Pc
-        const double P00 = (double)P[0] + (double)Pc[0], P10 = (double)P[1] + (double)Pc[1];
-        const double P20 = (double)P[2] + (double)Pc[2], P01 = (double)P[3] + (double)Pc[3];
-        const double P11 = (double)P[4] + (double)Pc[4], P02 = (double)P[5] + (double)Pc[5];
-        const double PG = (double)P[6] + (double)Pc[6];
-        // J_abc += c3 jt3^c P_ab
-        J[0] = fma(c, P00, J[0]);
-        J[1] = fma(c, P10, J[1]);
-        J[2] = fma(c, P20, J[2]);
-        J[3] = fma(c, P01, J[3]);
-        J[4] = fma(c, P11, J[4]);
-        J[5] = fma(c, P02, J[5]);
-        J[6] = fma(c * t, P00, J[6]);
-        J[7] = fma(c * t, P10, J[7]);
-        J[8] = fma(c * t, P01, J[8]);
-        J[9] = fma(c * t * t, P00, J[9]);
-        J[10] = fma(c, PG, J[10]);
-#pragma unroll
-        for (int i = 0; i < 7; ++i) P[i] = Pc[i] = 0.f;
-    }
-    // add c * (sum + err) of a line pair into a plane pair, error-free up to
-    // O(eps^2) (c is a small integer or half-integer)
-    __device__ __forceinline__ void plane_add(int i, float c, float sum, float err) {
-        const float ps = __fmul_rn(c, sum);
-        sum2(P[i], Pc[i], ps);
-        Pc[i] = __fadd_rn(Pc[i], fmaf(c, sum, -ps));
-        Pc[i] = fmaf(c, err, Pc[i]);
-    }
-    __device__ __forceinline__ void end_line(float c2, float jt2) {
-        const float a = c2, b = __fmul_rn(c2, jt2), bb = __fmul_rn(__fmul_rn(c2, jt2), jt2);   // exact
-        plane_add(0, a, L[0], Lc[0]);
-        plane_add(1, a, L[1], Lc[1]);
-        plane_add(2, a, L[2], Lc[2]);
-        plane_add(3, b, L[0], Lc[0]);
-        plane_add(4, b, L[1], Lc[1]);
-        plane_add(5, bb, L[0], Lc[0]);
-        plane_add(6, a, L[3], Lc[3]);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) L[i] = Lc[i] = 0.f;
-    }
-};
-
-// Shared-memory FP32 operator tables of the deviation-form advection (used by
-// both FP32 stage kernels): Dt[side] (inflow trace folded in), dg[side], the
-// exact defects eps_i = sum_j Dt_ij + dg_i, the telescoping neighbour-trace
-// weights lambda_j = +-sum_i W_i Dt_ij and dlam = sum_j lambda_j - 1.
-template <int Q>
-__device__ __forceinline__ void load_ops_f32(const FROps &fr, int tid, float (*sD)[Q][Q], float (*sdg)[Q],
-                                             float (*seps)[Q], float (*slam)[Q], float *sdlam) {
-    if (tid < Q * Q) {
-        const int i = tid / Q, j = tid % Q;
-        sD[0][i][j] = folded_dt(fr, 0, i, j);
-        sD[1][i][j] = folded_dt(fr, 1, i, j);
-    }
-    if (tid < 2 * Q) {
-        const int side = tid / Q, j = tid % Q;
-        double lam = 0.0, eps = side == 0 ? fr.dgL[j] : fr.dgR[j];
-        for (int i = 0; i < Q; ++i) {
-            lam = fma(fr.wq[i], (double)folded_dt(fr, side, i, j), lam);
-            eps += (double)folded_dt(fr, side, j, i);
-        }
-        slam[side][j] = (float)(side == 0 ? lam : -lam);
-        seps[side][j] = (float)eps;
-        sdg[side][j] = (float)(side == 0 ? fr.dgL[j] : fr.dgR[j]);
-        if (j == 0) {
-            double tot = 0.0;
-            for (int jj = 0; jj < Q; ++jj)
-                for (int i = 0; i < Q; ++i) tot = fma(fr.wq[i], (double)folded_dt(fr, side, i, jj), tot);
-            sdlam[side] = (float)((side == 0 ? tot : -tot) - 1.0);
-        }
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Fused stage, FP32 state.  Same discretisation as the FP64 stage kernel:
@@ -442,53 +210,11 @@ struct TmaGeom {
     static constexpr int EB = 256 / NS;                  // elements per block
     static constexpr int NCT = (EB * NS + 31) / 32 * 32;  // consumer threads
     static constexpr int NTHR = NCT + 32;                 // + one producer warp
-    static constexpr int SLOTS = EB + 2;                  // x-halo, EB own elements, x-halo
-    static constexpr int PER_C = (SLOTS + 3 * EB) * NS;   // own + halos, y run, z run, f^n run
-    static constexpr int STAGE = C * PER_C;               // floats per stage buffer
+    static constexpr int SLOTS = StageGeom<Q, C, EB>::SLOTS;
+    static constexpr int PER_C = StageGeom<Q, C, EB>::PER_C;
+    static constexpr int STAGE = StageGeom<Q, C, EB>::STAGE;
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-// Wait for the completion of the barrier phase of the given parity; false
-// after about 2 s without it.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    if (mbar_try(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    while (!mbar_try(bar, parity))
-        if (global_ns() - t0 > 2000000000ull) return false;
-    return true;
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const float *src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
 
 template <int Q, int C>
 __global__ void __launch_bounds__(TmaGeom<Q, C>::NTHR, 2) k_stage_f32_tma(StageArgs<float> a, int S) {
@@ -503,70 +229,22 @@ __global__ void __launch_bounds__(TmaGeom<Q, C>::NTHR, 2) k_stage_f32_tma(StageA
     __shared__ float sdg[2][Q], seps[2][Q], slam[2][Q], sdlam[2];
     __shared__ int s_abort;
     const int tid = threadIdx.x;
-    const int n1 = a.mesh.n[0], n2 = a.mesh.n[1], n3 = a.mesh.n[2];
-    const int cpr = (n1 + EB - 1) / EB;
-    const int row = blockIdx.x / cpr, x0 = (blockIdx.x - row * cpr) * EB;
-    const int nel = min(EB, n1 - x0);
-    const int e0 = row * n1 + x0;
-    const int ey = row % n2, ez = row / n2, pl = n1 * n2;
-    // first element of the upwind neighbour run on side 0 (left) / 1 (right); -1: Dirichlet face
-    const int xn0 = x0 > 0 ? e0 - 1 : (a.mesh.periodic[0] ? row * n1 + n1 - 1 : -1);
-    const int xn1 = x0 + nel < n1 ? e0 + nel : (a.mesh.periodic[0] ? row * n1 : -1);
-    const int yn0 = ey > 0 ? e0 - n1 : (a.mesh.periodic[1] ? e0 + (n2 - 1) * n1 : -1);
-    const int yn1 = ey < n2 - 1 ? e0 + n1 : (a.mesh.periodic[1] ? e0 - (n2 - 1) * n1 : -1);
-    const int zn0 = ez > 0 ? e0 - pl : (a.mesh.periodic[2] ? e0 + (n3 - 1) * pl : -1);
-    const int zn1 = ez < n3 - 1 ? e0 + pl : (a.mesh.periodic[2] ? e0 - (n3 - 1) * pl : -1);
+    RunGeom g;
+    g.init(a.mesh, EB, blockIdx.x);
+    const int nel = g.nel, e0 = g.e0;
+    const int xn0 = g.xn0, xn1 = g.xn1, yn0 = g.yn0, yn1 = g.yn1, zn0 = g.zn0, zn1 = g.zn1;
     const int vb = blockIdx.y;
     const int k0 = vb * a.Kblk, k1 = min(a.Nu, k0 + a.Kblk);
     const size_t slab = (size_t)a.P;
     if (tid == 0) {
-        for (int i = 0; i < S; ++i) {
-            mbar_init(smem_u32(bars + i), 1);              // full: the producer's arrive + bytes
-            mbar_init(smem_u32(bars + S + i), NCT / 32);    // empty: one arrival per consumer warp
-        }
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        ring_init(bars, S, NCT / 32);
         s_abort = 0;
     }
     load_ops_f32<Q>(a.fr, tid, sD, sdg, seps, slam, sdlam);
     __syncthreads();
 
     if (tid >= NCT) {
-        // ---- producer: one thread issues every copy ----
-        if (tid != NCT) return;
-        const uint32_t runb = (uint32_t)(nel * NS * 4), elb = NS * 4;
-        const bool with_fn = a.a32 != 0.f;
-        int i = 0;
-        bool ok = true;
-        for (; i < k1 - k0; ++i) {
-            const int slot = i % S;
-            if (i >= S && !mbar_wait(smem_u32(bars + S + slot), ((i / S) & 1) ^ 1)) { ok = false; break; }
-            if (*(volatile int *)&s_abort) { ok = false; break; }
-            const int k = k0 + i;
-            const float4 u = __ldg(a.vtab32 + k);
-            const int xe = u.x > 0.f ? xn0 : xn1, ye = u.y > 0.f ? yn0 : yn1, ze = u.z > 0.f ? zn0 : zn1;
-            const uint32_t bytes = C * (runb + (xe >= 0 ? elb : 0u) + (ye >= 0 ? runb : 0u) + (ze >= 0 ? runb : 0u) +
-                                        (with_fn ? runb : 0u));
-            const uint32_t full = smem_u32(bars + slot);
-            mbar_expect_tx(full, bytes);
-            float *st = sbuf + (size_t)slot * STAGE;
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-                const float *src = a.f_s + ((size_t)c * a.Nu + k) * slab;
-                float *own = st + c * PER_C;
-                bulk_g2s(smem_u32(own + NS), src + (size_t)e0 * NS, runb, full);
-                if (xe >= 0) bulk_g2s(smem_u32(own + (u.x > 0.f ? 0 : (nel + 1) * NS)), src + (size_t)xe * NS, elb, full);
-                if (ye >= 0) bulk_g2s(smem_u32(own + SLOTS * NS), src + (size_t)ye * NS, runb, full);
-                if (ze >= 0) bulk_g2s(smem_u32(own + (SLOTS + EB) * NS), src + (size_t)ze * NS, runb, full);
-                if (with_fn)
-                    bulk_g2s(smem_u32(own + (SLOTS + 2 * EB) * NS), a.f_n + ((size_t)c * a.Nu + k) * slab + (size_t)e0 * NS,
-                             runb, full);
-            }
-        }
-        if (!ok) {
-            // no copy may still be in flight when the block exits
-            for (int j = max(0, i - S); j < i; ++j) mbar_wait(smem_u32(bars + j % S), (j / S) & 1);
-            atomicOr(a.status, BGK_DEV_TIMEOUT);
-        }
+        if (tid == NCT) ring_producer<Q, C, EB>(a, g, sbuf, bars, S, k0, k1, &s_abort);
         return;
     }
 
@@ -797,8 +475,23 @@ bool stage_f32_tma_supported(const StageArgs<float> &a, int C, int depth) {
     return smem <= 200 * 1024;
 }
 
+bool stage_f32_variant_supported(const StageArgs<float> &a, int C, int variant, int depth) {
+    switch (variant) {
+        case BGK_STAGE_AUTO:
+        case BGK_STAGE_PLAIN: return a.fr.q >= 2 && a.fr.q <= BGK_MAXQ;
+        case BGK_STAGE_ASYNC: return stage_f32_tma_supported(a, C, depth);
+        case BGK_STAGE_LINE:
+        case BGK_STAGE_LINE_WIDE:
+        case BGK_STAGE_HALF:
+        case BGK_STAGE_HALF_WIDE: return stage_f32_line_supported(a, C, variant - BGK_STAGE_LINE, depth);
+        default: return false;
+    }
+}
+
 cudaError_t launch_stage_f32(const StageArgs<float> &a, int C, int n_vblk, int variant, int depth, cudaStream_t s) {
-    if (variant != BGK_STAGE_PLAIN && stage_f32_tma_supported(a, C, depth)) {
+    if (variant >= BGK_STAGE_LINE && variant <= BGK_STAGE_HALF_WIDE)
+        return launch_stage_f32_line(a, C, n_vblk, variant - BGK_STAGE_LINE, depth, s);
+    if ((variant == BGK_STAGE_AUTO || variant == BGK_STAGE_ASYNC) && stage_f32_tma_supported(a, C, depth)) {
         if (a.fr.q == 2) return C == 1 ? stage32_tma<2, 1>(a, n_vblk, depth, s) : stage32_tma<2, 2>(a, n_vblk, depth, s);
         return C == 1 ? stage32_tma<4, 1>(a, n_vblk, depth, s) : stage32_tma<4, 2>(a, n_vblk, depth, s);
     }

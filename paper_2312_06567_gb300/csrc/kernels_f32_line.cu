@@ -1,0 +1,527 @@
+// Mixed-form fused stage, one thread per first-axis node line.
+//
+// Same FR advection (deviation form with telescoping trace weights), FP32
+// equilibrium with its moment correction, Runge--Kutta update and
+// error-free moment epilogue as k_stage_f32, evaluated term for term in the
+// same order for every point, so the results are bit-identical; what
+// changes is the work mapping.  Each consumer thread owns the Q nodes
+// (i, j, k), i = 0..Q-1, of one line along the first element axis, i.e. Q
+// points:
+//   - its own line and every line it needs (the other lines of its element
+//     in the second and third directions, the upwind neighbours' lines)
+//     arrive as one vector load each from the shared-memory stage;
+//   - the coefficients of the second- and third-direction sums are the same
+//     for the thread's Q points (one load serves Q products), and the
+//     first-direction deviations f_j - f_i are formed once per pair (the
+//     negated difference is exact);
+//   - the barrier wait, the velocity bookkeeping and the loop control are
+//     paid once per Q points.
+// The operands arrive through the same asynchronous copy ring as in the
+// node-per-thread pipelined kernel (ring_producer).  The FP32 equilibrium
+// parameters come from the record the Q' solve writes beside its FP64 one
+// (BGK_NEQ32), the plane-level moment pairs live in shared memory and the
+// FP64 index moments accumulate in the moment-partials buffer, which this
+// block owns for its points and velocity block, converted to raw moments at
+// the end.  Dzanic & Martinelli, arXiv 2312.06567, section "Methodology".
+#include "stage_f32_common.cuh"
+
+namespace {
+
+template <int Q, int C, int EB, int NPT>
+struct LineGeom {
+    static constexpr int NH = Q / NPT;                  // threads per node line
+    static constexpr int NCT = EB * Q * Q * NH;         // consumer threads
+    static constexpr int NTHR = NCT + 32;               // + one producer warp
+    static constexpr int NQ = C == 2 ? 7 : 6;           // plane quantities per point
+    // resident blocks asked of the register allocator: a budget of about 96
+    // registers per thread (128 with a whole line per thread)
+    static constexpr int MINB = 65536 / (NTHR * (NPT == Q ? 128 : 96)) > 0 ? 65536 / (NTHR * (NPT == Q ? 128 : 96)) : 1;
+    static_assert(NCT % 32 == 0, "consumer threads must fill whole warps");
+    static_assert(Q % NPT == 0, "a thread takes a whole fraction of a line");
+};
+
+template <int N>
+__device__ __forceinline__ void ld_vec(const float *p, float (&v)[N]);
+template <>
+__device__ __forceinline__ void ld_vec<4>(const float *p, float (&v)[4]) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+template <>
+__device__ __forceinline__ void ld_vec<2>(const float *p, float (&v)[2]) {
+    const float2 t = *reinterpret_cast<const float2 *>(p);
+    v[0] = t.x; v[1] = t.y;
+}
+template <>
+__device__ __forceinline__ void ld_vec<1>(const float *p, float (&v)[1]) {
+    v[0] = *p;
+}
+template <int N>
+__device__ __forceinline__ void st_vec(float *p, const float (&v)[N]);
+template <>
+__device__ __forceinline__ void st_vec<4>(float *p, const float (&v)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ void st_vec<2>(float *p, const float (&v)[2]) {
+    *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+}
+template <>
+__device__ __forceinline__ void st_vec<1>(float *p, const float (&v)[1]) {
+    *p = v[0];
+}
+
+// Line sums of one point (the first level of IndexMoments): F, F jt, F jt^2
+// and, with two components, G; error-free pairs.
+template <int C>
+struct LineAcc {
+    float L[C == 2 ? 4 : 3], Lc[C == 2 ? 4 : 3];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int q = 0; q < (C == 2 ? 4 : 3); ++q) L[q] = Lc[q] = 0.f;
+    }
+    __device__ __forceinline__ void add(float cj1, float jt1, float F, float G) {
+        const float cF = __fmul_rn(cj1, F);
+        sum2(L[0], Lc[0], cF);
+        const float p1 = __fmul_rn(cF, jt1);
+        sum2(L[1], Lc[1], p1);
+        Lc[1] = __fadd_rn(Lc[1], fmaf(cF, jt1, -p1));
+        const float jj = __fmul_rn(jt1, jt1);
+        const float p2 = __fmul_rn(cF, jj);
+        sum2(L[2], Lc[2], p2);
+        Lc[2] = __fadd_rn(Lc[2], fmaf(cF, jj, -p2));
+        if (C == 2) sum2(L[C == 2 ? 3 : 0], Lc[C == 2 ? 3 : 0], __fmul_rn(cj1, G));
+    }
+};
+
+// Plane pairs of one point in shared memory: P[q] at P[q * n], errors at
+// P[(NQ + q) * n]; the same operations as IndexMoments::plane_add/end_line.
+template <int NQ>
+__device__ __forceinline__ void plane_add_s(float *P, int n, int q, float c, float sum, float err) {
+    float ps = P[q * n], pc = P[(NQ + q) * n];
+    const float pr = __fmul_rn(c, sum);
+    sum2(ps, pc, pr);
+    pc = __fadd_rn(pc, fmaf(c, sum, -pr));
+    pc = fmaf(c, err, pc);
+    P[q * n] = ps;
+    P[(NQ + q) * n] = pc;
+}
+
+template <int Q, int C, int EB, int NPT>
+__global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, EB, NPT>::MINB) k_stage_f32_line(StageArgs<float> a, int S) {
+    using SG = StageGeom<Q, C, EB>;
+    using LG = LineGeom<Q, C, EB, NPT>;
+    constexpr int NS = SG::NS, SLOTS = SG::SLOTS, PER_C = SG::PER_C, STAGE = SG::STAGE;
+    constexpr int NCT = LG::NCT, NQ = LG::NQ, NH = LG::NH, NTT = Q * Q * NH;
+    extern __shared__ __align__(128) float sbuf[];
+    // [S][STAGE] copy ring | [NPT][2 NQ][NCT] plane pairs | 2S mbarriers
+    float *Psm = sbuf + (size_t)S * STAGE;
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(Psm + NPT * 2 * NQ * NCT);
+    __shared__ float sD[2][Q][Q];
+    __shared__ float sdg[2][Q], seps[2][Q], slam[2][Q], sdlam[2];
+    __shared__ float su1[BGK_MAXV];                      // u1 of the first-axis nodes (the same on every line)
+    __shared__ int s_abort;
+    const int tid = threadIdx.x;
+    RunGeom g;
+    g.init(a.mesh, EB, blockIdx.x);
+    const int vb = blockIdx.y;
+    const int k0 = vb * a.Kblk, k1 = min(a.Nu, k0 + a.Kblk);
+    const size_t slab = (size_t)a.P;
+    const VelGrid &vg = a.vg;
+    const int vn1 = vg.n[0], vn2 = vg.n[1], vn3 = vg.n[2];
+    if (tid == 0) {
+        ring_init(bars, S, NCT / 32);
+        s_abort = 0;
+    }
+    for (int j = tid; j < vn1; j += blockDim.x) su1[j] = __ldg(a.vtab32 + j).x;
+    load_ops_f32<Q>(a.fr, tid, sD, sdg, seps, slam, sdlam);
+    __syncthreads();
+    if (tid >= NCT) {
+        if (tid == NCT) ring_producer<Q, C, EB>(a, g, sbuf, bars, S, k0, k1, &s_abort);
+        return;
+    }
+
+    // ---- consumers: thread = (element l of the run, node line r = jy + Q kz, part h of the line) ----
+    const int lane = tid & 31;
+    const int l = tid / NTT, rem = tid - l * NTT;
+    const int r = rem / NH, h = rem - r * NH;
+    const int jy = r % Q, kz = r / Q;
+    const int i0 = NPT * h;                              // first node of this thread on its line
+    const bool active = l < g.nel;
+    const int pb = (g.e0 + l) * NS + Q * r + i0;         // point of local node i: pb + i
+    const int bcm = (l == 0 && g.xn0 < 0 ? 1 : 0) | (l == g.nel - 1 && g.xn1 < 0 ? 2 : 0) | (g.yn0 < 0 ? 4 : 0) |
+                    (g.yn1 < 0 ? 8 : 0) | (g.zn0 < 0 ? 16 : 0) | (g.zn1 < 0 ? 32 : 0);
+    const int own_off = (l + 1) * NS;                    // own element within a component's stage region
+    const int ln = Q * r;                                // own line within an element
+    const bool mom = a.part != nullptr;
+    // per-point FP32 parameters used every velocity
+    float E0[NPT], V1[NPT], A11[NPT], itau[NPT], gm1[NPT], gm4h[NPT], U0x[NPT], gfac[NPT];
+#pragma unroll
+    for (int i = 0; i < NPT; ++i) {
+        E0[i] = V1[i] = A11[i] = itau[i] = gm1[i] = gm4h[i] = U0x[i] = gfac[i] = 0.f;
+        if (active) {
+            const float4 *rec = reinterpret_cast<const float4 *>(a.eq32 + (size_t)(pb + i) * BGK_NEQ32);
+            const float4 r0 = __ldg(rec), r1 = __ldg(rec + 1);
+            E0[i] = r0.x; V1[i] = r0.y; A11[i] = r0.z; itau[i] = r0.w;
+            gm1[i] = r1.x; gm4h[i] = r1.y; U0x[i] = r1.z; gfac[i] = r1.w;
+        }
+    }
+    const int jc[3] = {(vn1 - 1) / 2, (vn2 - 1) / 2, (vn3 - 1) / 2};
+    const float toh0 = a.toh32[0], toh1 = a.toh32[1], toh2 = a.toh32[2];
+    const float fa = a.a32, fab = a.ab32, fc = a.c32;
+    float *Pme = Psm + tid;                              // this thread's plane pairs: point i at Pme + i 2NQ NCT
+    if (mom) {
+#pragma unroll
+        for (int i = 0; i < NPT; ++i)
+#pragma unroll
+            for (int q = 0; q < 2 * NQ; ++q) Pme[(i * 2 * NQ + q) * NCT] = 0.f;
+    }
+    // FP64 index moments of the finished planes, kept in the partials buffer
+    int j3cur = -1;
+    bool first_plane = true;
+    auto flush_plane = [&](int j3) {
+        const double c = trap(j3, vn3), t = (float)(j3 - jc[2]);
+#pragma unroll
+        for (int i = 0; i < NPT; ++i) {
+            float *P = Pme + i * 2 * NQ * NCT;
+            double Pd[7];
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                Pd[q] = 0.0;
+                if (q < NQ) {
+                    Pd[q] = (double)P[q * NCT] + (double)P[(NQ + q) * NCT];
+                    P[q * NCT] = 0.f;
+                    P[(NQ + q) * NCT] = 0.f;
+                }
+            }
+            double *J = a.part + (size_t)vb * BGK_NMOM * a.P + pb + i;
+            double Jo[11];
+#pragma unroll
+            for (int q = 0; q < 11; ++q) Jo[q] = first_plane ? 0.0 : J[(size_t)q * a.P];
+            Jo[0] = fma(c, Pd[0], Jo[0]);
+            Jo[1] = fma(c, Pd[1], Jo[1]);
+            Jo[2] = fma(c, Pd[2], Jo[2]);
+            Jo[3] = fma(c, Pd[3], Jo[3]);
+            Jo[4] = fma(c, Pd[4], Jo[4]);
+            Jo[5] = fma(c, Pd[5], Jo[5]);
+            Jo[6] = fma(c * t, Pd[0], Jo[6]);
+            Jo[7] = fma(c * t, Pd[1], Jo[7]);
+            Jo[8] = fma(c * t, Pd[3], Jo[8]);
+            Jo[9] = fma(c * t * t, Pd[0], Jo[9]);
+            Jo[10] = fma(c, Pd[6], Jo[10]);
+#pragma unroll
+            for (int q = 0; q < 11; ++q) J[(size_t)q * a.P] = Jo[q];
+        }
+        first_plane = false;
+    };
+
+    int slot = 0;
+    uint32_t par = 0;
+    bool ok = true;
+    for (int kl = k0; kl < k1; kl += vn1) {
+        const int line = kl / vn1;
+        const int j2 = line % vn2, j3 = line / vn2;
+        if (mom && active && j3 != j3cur) {
+            if (j3cur >= 0) flush_plane(j3cur);
+            j3cur = j3;
+        }
+        const float4 vl = __ldg(a.vtab32 + kl);
+        const float u2 = vl.y, u3 = vl.z;
+        const int sy = u2 > 0.f ? 0 : 1, sz = u3 > 0.f ? 0 : 1;
+        // per-point line constants of the equilibrium exponent and the correction
+        float lin[NPT], cst[NPT], cl[NPT];
+#pragma unroll
+        for (int i = 0; i < NPT; ++i) {
+            lin[i] = cst[i] = cl[i] = 0.f;
+            if (active) {
+                const float4 *rec = reinterpret_cast<const float4 *>(a.eq32 + (size_t)(pb + i) * BGK_NEQ32);
+                const float4 r2 = __ldg(rec + 2), r3 = __ldg(rec + 3), r4 = __ldg(rec + 4), r5 = __ldg(rec + 5);
+                Eq32 e;
+                e.V2 = r2.x; e.V3 = r2.y; e.A12 = r2.z; e.A13 = r2.w;
+                e.A22 = r3.x; e.A23 = r3.y; e.A33 = r3.z;
+                e.line(u2, u3, lin[i], cst[i]);
+                const float t2 = u2 - r4.z, t3 = u3 - r4.w;
+                cl[i] = fmaf(r4.x, t2, fmaf(r4.y, t3, fmaf(0.5f * r5.x, fmaf(t2, t2, t3 * t3), r3.w)));
+            }
+        }
+        LineAcc<C> acc[NPT];
+#pragma unroll
+        for (int i = 0; i < NPT; ++i) acc[i].zero();
+        float jt1 = (float)(-jc[0]);
+        for (int j1 = 0; j1 < vn1; ++j1, jt1 += 1.f) {
+            const int k = kl + j1;
+            ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(bars + slot), par));
+            if (!ok) break;
+            if (active) {
+                const float *st = sbuf + (size_t)slot * STAGE;
+                const float u1 = su1[j1];
+                const int sx = u1 > 0.f ? 0 : 1;
+                float outv[C][NPT];
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const float *sc = st + c * PER_C;
+                    float Fi[NPT];                       // this thread's nodes
+                    ld_vec<NPT>(sc + own_off + ln + i0, Fi);
+                    float div[NPT];
+                    // ---- first direction: the line itself and the upwind neighbour's line
+                    {
+                        float F[Q];
+                        ld_vec<Q>(sc + own_off + ln, F);
+                        float t[NPT];
+                        if (NPT == Q) {
+                            // deviations formed once per pair: f_i - f_j = -(f_j - f_i) exactly
+                            float dv[Q][Q];
+#pragma unroll
+                            for (int i = 0; i < Q; ++i)
+#pragma unroll
+                                for (int j = i + 1; j < Q; ++j) dv[i][j] = F[j] - F[i];
+#pragma unroll
+                            for (int i = 0; i < NPT; ++i) {
+                                t[i] = 0.f;
+#pragma unroll
+                                for (int j = 0; j < Q; ++j)
+                                    if (j != i) t[i] = fmaf(sD[sx][i][j], j > i ? dv[i][j] : -dv[j][i], t[i]);
+                            }
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < NPT; ++i) {
+                                t[i] = 0.f;
+#pragma unroll
+                                for (int j = 0; j < Q; ++j)
+                                    if (j != i0 + i) t[i] = fmaf(sD[sx][i0 + i][j], F[j] - Fi[i], t[i]);
+                            }
+                        }
+                        float dn[NPT];
+                        if (!((bcm >> sx) & 1)) {
+                            float NB[Q];
+                            ld_vec<Q>(sc + own_off + (sx ? NS : -NS) + ln, NB);
+#pragma unroll
+                            for (int i = 0; i < NPT; ++i) {
+                                dn[i] = sdlam[sx] * Fi[i];
+#pragma unroll
+                                for (int j = 0; j < Q; ++j) dn[i] = fmaf(slam[sx][j], NB[j] - Fi[i], dn[i]);
+                            }
+                        } else {
+                            const float bv = (float)__ldg(a.bcval + ((size_t)(0 + sx) * C + c) * a.Nu + k);
+#pragma unroll
+                            for (int i = 0; i < NPT; ++i) dn[i] = bv - Fi[i];
+                        }
+                        const float cu = toh0 * u1;
+#pragma unroll
+                        for (int i = 0; i < NPT; ++i) {
+                            t[i] = fmaf(sdg[sx][i0 + i], dn[i], fmaf(seps[sx][i0 + i], Fi[i], t[i]));
+                            div[i] = fmaf(cu, t[i], 0.f);
+                        }
+                    }
+                    // ---- second direction: lines (j', kz) of the element and of the upwind y element
+                    {
+                        float t[NPT], dn[NPT];
+#pragma unroll
+                        for (int i = 0; i < NPT; ++i) t[i] = 0.f;
+#pragma unroll
+                        for (int jp = 0; jp < Q; ++jp) {
+                            if (jp == jy) continue;
+                            float Gv[NPT];
+                            ld_vec<NPT>(sc + own_off + Q * (jp + Q * kz) + i0, Gv);
+                            const float D = sD[sy][jy][jp];
+#pragma unroll
+                            for (int i = 0; i < NPT; ++i) t[i] = fmaf(D, Gv[i] - Fi[i], t[i]);
+                        }
+                        if (!((bcm >> (2 + sy)) & 1)) {
+#pragma unroll
+                            for (int i = 0; i < NPT; ++i) dn[i] = sdlam[sy] * Fi[i];
+#pragma unroll
+                            for (int jp = 0; jp < Q; ++jp) {
+                                float H[NPT];
+                                ld_vec<NPT>(sc + (SLOTS + l) * NS + Q * (jp + Q * kz) + i0, H);
+                                const float lam = slam[sy][jp];
+#pragma unroll
+                                for (int i = 0; i < NPT; ++i) dn[i] = fmaf(lam, H[i] - Fi[i], dn[i]);
+                            }
+                        } else {
+                            const float bv = (float)__ldg(a.bcval + ((size_t)(2 + sy) * C + c) * a.Nu + k);
+#pragma unroll
+                            for (int i = 0; i < NPT; ++i) dn[i] = bv - Fi[i];
+                        }
+                        const float cu = toh1 * u2, dgv = sdg[sy][jy], epv = seps[sy][jy];
+#pragma unroll
+                        for (int i = 0; i < NPT; ++i) {
+                            t[i] = fmaf(dgv, dn[i], fmaf(epv, Fi[i], t[i]));
+                            div[i] = fmaf(cu, t[i], div[i]);
+                        }
+                    }
+                    // ---- third direction: lines (jy, k') of the element and of the upwind z element
+                    {
+                        float t[NPT], dn[NPT];
+#pragma unroll
+                        for (int i = 0; i < NPT; ++i) t[i] = 0.f;
+#pragma unroll
+                        for (int kp = 0; kp < Q; ++kp) {
+                            if (kp == kz) continue;
+                            float Gv[NPT];
+                            ld_vec<NPT>(sc + own_off + Q * (jy + Q * kp) + i0, Gv);
+                            const float D = sD[sz][kz][kp];
+#pragma unroll
+                            for (int i = 0; i < NPT; ++i) t[i] = fmaf(D, Gv[i] - Fi[i], t[i]);
+                        }
+                        if (!((bcm >> (4 + sz)) & 1)) {
+#pragma unroll
+                            for (int i = 0; i < NPT; ++i) dn[i] = sdlam[sz] * Fi[i];
+#pragma unroll
+                            for (int kp = 0; kp < Q; ++kp) {
+                                float H[NPT];
+                                ld_vec<NPT>(sc + (SLOTS + EB + l) * NS + Q * (jy + Q * kp) + i0, H);
+                                const float lam = slam[sz][kp];
+#pragma unroll
+                                for (int i = 0; i < NPT; ++i) dn[i] = fmaf(lam, H[i] - Fi[i], dn[i]);
+                            }
+                        } else {
+                            const float bv = (float)__ldg(a.bcval + ((size_t)(4 + sz) * C + c) * a.Nu + k);
+#pragma unroll
+                            for (int i = 0; i < NPT; ++i) dn[i] = bv - Fi[i];
+                        }
+                        const float cu = toh2 * u3, dgv = sdg[sz][kz], epv = seps[sz][kz];
+#pragma unroll
+                        for (int i = 0; i < NPT; ++i) {
+                            t[i] = fmaf(dgv, dn[i], fmaf(epv, Fi[i], t[i]));
+                            div[i] = fmaf(cu, t[i], div[i]);
+                        }
+                    }
+                    // ---- equilibrium, source and Runge--Kutta update
+                    float FN[NPT];
+                    if (fa != 0.f) ld_vec<NPT>(sc + (SLOTS + 2 * EB + l) * NS + ln + i0, FN);
+#pragma unroll
+                    for (int i = 0; i < NPT; ++i) {
+                        const float c1 = __fsub_rn(u1, V1[i]);
+                        const float g32 = __fmul_rn(E0[i], Eq32::ex2(fmaf(c1, fmaf(A11[i], c1, lin[i]), cst[i])));
+                        const float t1 = u1 - U0x[i];
+                        const float corr = fmaf(t1, fmaf(gm4h[i], t1, gm1[i]), cl[i]);
+                        const float gc = __fmul_rn(g32, corr);
+                        const float eqv = (c == 0) ? g32 : gfac[i] * g32;
+                        const float eqc = (c == 0) ? gc : gfac[i] * gc;
+                        const float R = fmaf(eqv - Fi[i], itau[i], fmaf(eqc, itau[i], -div[i]));
+                        float out = fab == 1.f ? Fi[i] : fab * Fi[i];
+                        if (fa != 0.f) out = fmaf(fa, FN[i] - Fi[i], out);
+                        outv[c][i] = fmaf(fc, R, out);
+                    }
+                    st_vec<NPT>(a.f_out + ((size_t)c * a.Nu + k) * slab + pb, outv[c]);
+                }
+                if (mom) {
+                    const float cj = trap(j1, vn1);
+#pragma unroll
+                    for (int i = 0; i < NPT; ++i) acc[i].add(cj, jt1, outv[0][i], C == 2 ? outv[C - 1][i] : 0.f);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(bars + S + slot));
+            if (++slot == S) { slot = 0; par ^= 1u; }
+        }
+        if (!ok) break;
+        if (mom && active) {
+            // end of the line: c2 jt2^b (line pair) into the plane pairs
+            const float c2 = trap(j2, vn2), jt2 = (float)(j2 - jc[1]);
+            const float bq = __fmul_rn(c2, jt2), bbq = __fmul_rn(__fmul_rn(c2, jt2), jt2);
+#pragma unroll
+            for (int i = 0; i < NPT; ++i) {
+                float *P = Pme + i * 2 * NQ * NCT;
+                plane_add_s<NQ>(P, NCT, 0, c2, acc[i].L[0], acc[i].Lc[0]);
+                plane_add_s<NQ>(P, NCT, 1, c2, acc[i].L[1], acc[i].Lc[1]);
+                plane_add_s<NQ>(P, NCT, 2, c2, acc[i].L[2], acc[i].Lc[2]);
+                plane_add_s<NQ>(P, NCT, 3, bq, acc[i].L[0], acc[i].Lc[0]);
+                plane_add_s<NQ>(P, NCT, 4, bq, acc[i].L[1], acc[i].Lc[1]);
+                plane_add_s<NQ>(P, NCT, 5, bbq, acc[i].L[0], acc[i].Lc[0]);
+                if (C == 2) plane_add_s<NQ>(P, NCT, NQ - 1, c2, acc[i].L[C == 2 ? 3 : 0], acc[i].Lc[C == 2 ? 3 : 0]);
+            }
+        }
+    }
+    if (!ok) {
+        *(volatile int *)&s_abort = 1;
+        if (lane == 0) atomicOr(a.status, BGK_DEV_TIMEOUT);
+        return;
+    }
+    if (mom && active) {
+        if (j3cur >= 0) flush_plane(j3cur);
+        const double uc[3] = {vg.lo[0] + jc[0] * vg.h[0], vg.lo[1] + jc[1] * vg.h[1], vg.lo[2] + jc[2] * vg.h[2]};
+#pragma unroll
+        for (int i = 0; i < NPT; ++i) {
+            double *J = a.part + (size_t)vb * BGK_NMOM * a.P + pb + i;
+            double Jv[11], m[BGK_NMOM];
+#pragma unroll
+            for (int q = 0; q < 11; ++q) Jv[q] = first_plane ? 0.0 : J[(size_t)q * a.P];
+            index_to_raw(Jv, vg, uc, m);
+#pragma unroll
+            for (int q = 0; q < BGK_NMOM; ++q) J[(size_t)q * a.P] = m[q];
+        }
+    }
+}
+
+// Launch configurations: (nodes per thread, run length) per variant and order.
+//   line:      NPT = Q,   runs of 4 (Q = 4) / 16 (Q = 2) elements
+//   line_wide: NPT = Q,   runs of 8 / 32
+//   half:      NPT = Q/2, runs of 4 / 16
+//   half_wide: NPT = Q/2, runs of 8 / 32
+template <int Q, int C, int EB, int NPT>
+size_t line_smem(int depth) {
+    using LG = LineGeom<Q, C, EB, NPT>;
+    return (size_t)depth * StageGeom<Q, C, EB>::STAGE * sizeof(float) +
+           (size_t)NPT * 2 * LG::NQ * LG::NCT * sizeof(float) + 2 * (size_t)depth * sizeof(unsigned long long);
+}
+
+template <int Q, int C, int EB, int NPT>
+cudaError_t line_launch(const StageArgs<float> &a, int n_vblk, int depth, cudaStream_t s) {
+    const size_t smem = line_smem<Q, C, EB, NPT>(depth);
+    static size_t attr = 0;
+    if (smem > attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_stage_f32_line<Q, C, EB, NPT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = smem;
+    }
+    const int cpr = (a.mesh.n[0] + EB - 1) / EB;
+    dim3 grid(cpr * a.mesh.n[1] * a.mesh.n[2], n_vblk);
+    k_stage_f32_line<Q, C, EB, NPT><<<grid, LineGeom<Q, C, EB, NPT>::NTHR, smem, s>>>(a, depth);
+    return cudaGetLastError();
+}
+
+// kind: 0 line, 1 line_wide, 2 half, 3 half_wide.  With launch == false only
+// the shared-memory size is returned (through *smem).
+template <int Q, int C>
+cudaError_t line_dispatch(int kind, bool launch, const StageArgs<float> &a, int n_vblk, int depth, cudaStream_t s,
+                          size_t *smem) {
+    constexpr int EBS = Q == 4 ? 4 : 16, EBW = 2 * EBS, NH = Q / 2;
+    switch (kind) {
+        case 0: *smem = line_smem<Q, C, EBS, Q>(depth); return launch ? line_launch<Q, C, EBS, Q>(a, n_vblk, depth, s) : cudaSuccess;
+        case 1: *smem = line_smem<Q, C, EBW, Q>(depth); return launch ? line_launch<Q, C, EBW, Q>(a, n_vblk, depth, s) : cudaSuccess;
+        case 2: *smem = line_smem<Q, C, EBS, NH>(depth); return launch ? line_launch<Q, C, EBS, NH>(a, n_vblk, depth, s) : cudaSuccess;
+        case 3: *smem = line_smem<Q, C, EBW, NH>(depth); return launch ? line_launch<Q, C, EBW, NH>(a, n_vblk, depth, s) : cudaSuccess;
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t line_any(int kind, bool launch, const StageArgs<float> &a, int C, int n_vblk, int depth, cudaStream_t s,
+                     size_t *smem) {
+    if (a.fr.q == 4) return C == 1 ? line_dispatch<4, 1>(kind, launch, a, n_vblk, depth, s, smem)
+                                   : line_dispatch<4, 2>(kind, launch, a, n_vblk, depth, s, smem);
+    return C == 1 ? line_dispatch<2, 1>(kind, launch, a, n_vblk, depth, s, smem)
+                  : line_dispatch<2, 2>(kind, launch, a, n_vblk, depth, s, smem);
+}
+
+bool aligned_to(const void *p, uintptr_t n) { return ((uintptr_t)p & (n - 1)) == 0; }
+
+}  // namespace
+
+bool stage_f32_line_supported(const StageArgs<float> &a, int C, int kind, int depth) {
+    const int Q = a.fr.q;
+    if (Q != 2 && Q != 4) return false;
+    if (kind < 0 || kind > 3 || depth < 2 || depth > BGK_MAX_DEPTH || !a.eq32) return false;
+    if (!aligned_to(a.f_s, 16) || (a.a32 != 0.f && !aligned_to(a.f_n, 16)) || !aligned_to(a.f_out, 16)) return false;
+    size_t smem = 0;
+    line_any(kind, false, a, C, 0, depth, nullptr, &smem);
+    return smem <= 200 * 1024;
+}
+
+cudaError_t launch_stage_f32_line(const StageArgs<float> &a, int C, int n_vblk, int kind, int depth, cudaStream_t s) {
+    if (!stage_f32_line_supported(a, C, kind, depth)) return cudaErrorInvalidValue;
+    size_t smem = 0;
+    return line_any(kind, true, a, C, n_vblk, depth, s, &smem);
+}

@@ -404,7 +404,7 @@ __device__ __forceinline__ void plane_add(float &P, float &Pc, float c, float su
 // (j3 = const) accumulate as (sum, error) pairs with exact coefficients, and
 // the planes in FP64, so the result is accurate to O(2^-48) of the sums.
 __device__ __forceinline__ void correction_sums(const QPrimeArgs &a, int lane, double c0, const double x[5],
-                                                const Sym3 &A, double Jm[7]) {
+                                                const Sym3 &A, const float *su1, double Jm[7]) {
     const VelGrid &vg = a.vg;
     const int n1 = vg.n[0], n2 = vg.n[1], n3 = vg.n[2];
     const int jc[3] = {(n1 - 1) / 2, (n2 - 1) / 2, (n3 - 1) / 2};
@@ -417,29 +417,34 @@ __device__ __forceinline__ void correction_sums(const QPrimeArgs &a, int lane, d
     const int nl = n2 * n3, chunk = (nl + 31) / 32;
     const int l0 = min(nl, lane * chunk), l1 = min(nl, l0 + chunk);
     int j3cur = l0 < l1 ? l0 / n2 : -1;
-    auto flush = [&](int j3) {
-        const double c3 = (j3 == 0 || j3 == n3 - 1) ? 0.5 : 1.0, t3 = (double)(j3 - jc[2]);
-        double Pd[5];
-#pragma unroll
-        for (int i = 0; i < 5; ++i) { Pd[i] = (double)P[i] + (double)Pc[i]; P[i] = Pc[i] = 0.f; }
-        Jm[0] = fma(c3, Pd[0], Jm[0]);
-        Jm[1] = fma(c3, Pd[1], Jm[1]);
-        Jm[2] = fma(c3, Pd[2], Jm[2]);
-        Jm[3] = fma(c3, Pd[3], Jm[3]);
-        Jm[4] = fma(c3, Pd[4], Jm[4]);
-        Jm[5] = fma(c3 * t3, Pd[0], Jm[5]);
-        Jm[6] = fma(c3 * t3 * t3, Pd[0], Jm[6]);
-    };
+    // plane (j3) sums into the FP64 index moments (written out twice below,
+    // not as a lambda, so the pairs stay in registers)
+#define BGK_FLUSH_PLANE(J3)                                                                     \
+    do {                                                                                        \
+        const double c3 = ((J3) == 0 || (J3) == n3 - 1) ? 0.5 : 1.0, t3 = (double)((J3) - jc[2]); \
+        double Pd[5];                                                                           \
+        _Pragma("unroll") for (int i = 0; i < 5; ++i) {                                         \
+            Pd[i] = (double)P[i] + (double)Pc[i];                                               \
+            P[i] = Pc[i] = 0.f;                                                                 \
+        }                                                                                       \
+        Jm[0] = fma(c3, Pd[0], Jm[0]);                                                          \
+        Jm[1] = fma(c3, Pd[1], Jm[1]);                                                          \
+        Jm[2] = fma(c3, Pd[2], Jm[2]);                                                          \
+        Jm[3] = fma(c3, Pd[3], Jm[3]);                                                          \
+        Jm[4] = fma(c3, Pd[4], Jm[4]);                                                          \
+        Jm[5] = fma(c3 * t3, Pd[0], Jm[5]);                                                     \
+        Jm[6] = fma(c3 * t3 * t3, Pd[0], Jm[6]);                                                \
+    } while (0)
     for (int line = l0; line < l1; ++line) {
         const int j2 = line % n2, j3 = line / n2;
-        if (j3 != j3cur) { flush(j3cur); j3cur = j3; }
+        if (j3 != j3cur) { BGK_FLUSH_PLANE(j3cur); j3cur = j3; }
         const float4 *vl32 = a.vtab32 + (size_t)line * n1;
         float lin, cst;
         e32.line(vl32[0].y, vl32[0].z, lin, cst);
         float L0 = 0.f, C0 = 0.f, L1 = 0.f, C1 = 0.f, L2 = 0.f, C2 = 0.f;
         float jt = (float)(-jc[0]);
         for (int j1 = 0; j1 < n1; ++j1, jt += 1.f) {
-            const float g = e32.g(__ldg(&vl32[j1].x), lin, cst);
+            const float g = e32.g(su1[j1], lin, cst);
             const float cg = (j1 == 0 || j1 == n1 - 1) ? __fmul_rn(0.5f, g) : g;     // exact
             sum2(L0, C0, cg);
             const float p1 = __fmul_rn(cg, jt);
@@ -458,7 +463,8 @@ __device__ __forceinline__ void correction_sums(const QPrimeArgs &a, int lane, d
         plane_add(P[3], Pc[3], b, L0, C0);
         plane_add(P[4], Pc[4], bb, L0, C0);
     }
-    if (j3cur >= 0) flush(j3cur);
+    if (j3cur >= 0) BGK_FLUSH_PLANE(j3cur);
+#undef BGK_FLUSH_PLANE
 #pragma unroll
     for (int i = 0; i < 7; ++i) Jm[i] = warp_sum(Jm[i]);
 }
@@ -579,6 +585,25 @@ __device__ __forceinline__ void point_epilogue(const QPrimeArgs &a, int p, bool 
 #pragma unroll
         for (int i = 0; i < 5; ++i) q[12 + i] = gam[i];
         q[17] = ps.U0[0]; q[18] = ps.U0[1]; q[19] = ps.U0[2];
+        if (a.eq32) {
+            // the FP32 values the stage kernels derive from this record, with
+            // the same conversions (Eq32::load and plain roundings)
+            double qr[BGK_NEQ];
+#pragma unroll
+            for (int i = 0; i < BGK_NEQ; ++i) qr[i] = q[i];
+            Eq32 e;
+            e.load(qr);
+            float g[5];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) g[i] = (float)qr[12 + i];
+            float4 *r = reinterpret_cast<float4 *>(a.eq32 + (size_t)p * BGK_NEQ32);
+            r[0] = make_float4(e.E0, e.V1, e.A11, (float)qr[10]);
+            r[1] = make_float4(g[1], 0.5f * g[4], (float)qr[17], (float)qr[11]);
+            r[2] = make_float4(e.V2, e.V3, e.A12, e.A13);
+            r[3] = make_float4(e.A22, e.A23, e.A33, g[0]);
+            r[4] = make_float4(g[2], g[3], (float)qr[18], (float)qr[19]);
+            r[5] = make_float4(g[4], 0.f, 0.f, 0.f);
+        }
     }
     if (!conv) atomicOr(a.status, BGK_DEV_NOCONV);
     if (a.log && conv) {
@@ -654,13 +679,15 @@ struct Engine64 {
             pu2[0] = w23; pu3[0] = 1.0;
 #pragma unroll
             for (int q = 1; q < 5; ++q) { pu2[q] = pu2[q - 1] * ut2; pu3[q] = pu3[q - 1] * ut3; }
+            // slots in midx order: (p2, p3) outer, p1 inner (a running index keeps them compile-time)
+            int idx = 0;
 #pragma unroll
             for (int aa = 0; aa <= 4; ++aa)
 #pragma unroll
                 for (int bb = 0; bb <= 4 - aa; ++bb) {
                     const double P = pu2[aa] * pu3[bb];
 #pragma unroll
-                    for (int mm = 0; mm <= 4 - aa - bb; ++mm) M[midx(mm, aa, bb)] = fma(P, Tm[mm], M[midx(mm, aa, bb)]);
+                    for (int mm = 0; mm <= 4 - aa - bb; ++mm, ++idx) M[idx] = fma(P, Tm[mm], M[idx]);
                 }
         }
 #pragma unroll
@@ -722,13 +749,14 @@ struct Engine32 {
             pu2[0] = w23; pu3[0] = 1.f;
 #pragma unroll
             for (int q = 1; q < 5; ++q) { pu2[q] = pu2[q - 1] * ut2; pu3[q] = pu3[q - 1] * ut3; }
+            int idx = 0;
 #pragma unroll
             for (int aa = 0; aa <= 4; ++aa)
 #pragma unroll
                 for (int bb = 0; bb <= 4 - aa; ++bb) {
                     const float P = pu2[aa] * pu3[bb];
 #pragma unroll
-                    for (int mm = 0; mm <= 4 - aa - bb; ++mm) M[midx(mm, aa, bb)] = fmaf(P, Tm[mm], M[midx(mm, aa, bb)]);
+                    for (int mm = 0; mm <= 4 - aa - bb; ++mm, ++idx) M[idx] = fmaf(P, Tm[mm], M[idx]);
                 }
         }
         // the lane partials carry FP32 rounding already; the tree sum in FP32
@@ -763,12 +791,14 @@ __device__ __forceinline__ Sym3 load_sym3(const double *t) { return Sym3{t[0], t
 template <bool F32>
 __global__ void __launch_bounds__(QB * QW, 2) k_qprime(QPrimeArgs a) {
     __shared__ QPShared S;
+    __shared__ float su1[BGK_MAXV];          // u1 of the first-axis velocity nodes (the same on every line)
     extern __shared__ double dyn_tab[];      // FP64 engine: [QW][n1][5] tables w1 ut1^m
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int p0 = blockIdx.x * QB;
     const int nb = min(QB, a.P - p0);
     const double tol = F32 ? a.tol32 : a.tol;
     const double Pr = a.gas.Pr;
+    for (int j = threadIdx.x; j < a.vg.n[0]; j += blockDim.x) su1[j] = __ldg(a.vtab32 + j).x;
     // -- prologue: one lane per point
     if (wib == 0 && lane < nb) point_prologue(a, p0 + lane, S.ps[lane]);
     __syncthreads();
@@ -868,7 +898,7 @@ __global__ void __launch_bounds__(QB * QW, 2) k_qprime(QPrimeArgs a) {
             double x[5], Jm[7];
 #pragma unroll
             for (int j = 0; j < 5; ++j) x[j] = S.x[i][j];
-            correction_sums(a, lane, S.c0[i], x, load_sym3(S.A[i]), Jm);
+            correction_sums(a, lane, S.c0[i], x, load_sym3(S.A[i]), su1, Jm);
             if (lane == 0) {
 #pragma unroll
                 for (int j = 0; j < 7; ++j) S.Jm[i][j] = Jm[j];

@@ -1,10 +1,11 @@
-"""The asynchronous-copy mixed-form stage kernel against the plain one.
+"""The asynchronous-copy mixed-form stage kernels against the plain one.
 
-Both kernels evaluate the same FP32 expressions in the same order (the
-deviation-form FR advection, the corrected FP32 equilibrium, the Runge--Kutta
-update and the error-free moment epilogue); only the way the operands reach
-the threads differs (bulk copies into a shared-memory ring instead of
-per-thread loads).  So their states and moments must agree bit for bit, for
+All variants evaluate the same FP32 expressions in the same order for every
+point (the deviation-form FR advection, the corrected FP32 equilibrium, the
+Runge--Kutta update and the error-free moment epilogue); only the way the
+operands reach the threads (bulk copies into a shared-memory ring instead of
+per-thread loads) and the work mapping (one node or one first-axis node line
+per thread) differ.  So their states and moments must agree bit for bit, for
 every copy-ring depth, on ragged element runs (first mesh axis not a multiple
 of the run length), Dirichlet faces, two-component (F, G) states and the
 Runge--Kutta stages with and without f^n.  The plain kernel is itself checked
@@ -26,6 +27,8 @@ def lib(libbgk, cuda_device):
     return bgk
 
 
+VARIANTS = ("async", "line", "line_wide", "half", "half_wide")
+
 ASYNC_CASES = {
     # Q = 2: 32-element runs, all rows shorter than a run
     "sine_box_p1": lambda: W.periodic_sine_box(),
@@ -36,6 +39,22 @@ ASYNC_CASES = {
     "shock_fg_p3_dirichlet": lambda: _mild_shock(mesh_n=(6, 1, 1), vel_n=(16, 10, 9)).replace(p=3),
     "shock_fg_p3_dirichlet_3d": lambda: _mild_shock(mesh_n=(5, 2, 3), vel_n=(12, 9, 8)).replace(p=3),
 }
+
+
+def _smem_bytes(variant, q, C, depth):
+    """Shared memory of an asynchronous stage kernel (the launcher's formula);
+    a configuration above 200 KB is refused by design."""
+    ns = q ** 3
+    if variant == "async":
+        eb = 256 // ns
+        nct = eb * ns
+        return depth * C * (4 * eb + 2) * ns * 4 + (11 * 8 + 14 * 4) * nct + 16 * depth
+    wide = variant.endswith("_wide")
+    eb = (4 if q == 4 else 16) * (2 if wide else 1)
+    npt = q if variant.startswith("line") else q // 2
+    nct = eb * q * q * (q // npt)
+    nq = 7 if C == 2 else 6
+    return depth * C * (4 * eb + 2) * ns * 4 + npt * 2 * nq * nct * 4 + 16 * depth
 
 
 def _run(lib, wl, f0, variant, depth, steps):
@@ -52,11 +71,17 @@ def test_async_stage_is_bitwise_plain_stage(lib, name):
     wl = ASYNC_CASES[name]()
     f0 = W.random_anisotropic_state(wl, seed=5).astype(np.float32)
     r_p, f_p, m_p = _run(lib, wl, f0, "plain", 6, 2)
-    for depth in (2, 3, 6, 16):
-        r_a, f_a, m_a = _run(lib, wl, f0, "async", depth, 2)
-        assert np.array_equal(r_a, r_p), (name, depth, float(np.max(np.abs(r_a - r_p))))
-        assert np.array_equal(f_a, f_p), (name, depth, float(np.max(np.abs(f_a - f_p))))
-        assert np.array_equal(m_a, m_p), (name, depth, float(np.max(np.abs(m_a - m_p))))
+    for variant in VARIANTS:
+        for depth in (2, 3, 6, 16):
+            if _smem_bytes(variant, wl.p + 1, wl.n_comp, depth) > 200 * 1024:
+                with pytest.raises(RuntimeError):
+                    _run(lib, wl, f0, variant, depth, 2)
+                continue
+            r_a, f_a, m_a = _run(lib, wl, f0, variant, depth, 2)
+            tag = (name, variant, depth)
+            assert np.array_equal(r_a, r_p), (tag, float(np.max(np.abs(r_a - r_p))))
+            assert np.array_equal(f_a, f_p), (tag, float(np.max(np.abs(f_a - f_p))))
+            assert np.array_equal(m_a, m_p), (tag, float(np.max(np.abs(m_a - m_p))))
 
 
 def test_async_stage_entry_point_with_fn(lib):
@@ -65,7 +90,7 @@ def test_async_stage_entry_point_with_fn(lib):
     fn = W.random_anisotropic_state(wl, seed=6).astype(np.float32)
     fs = W.random_anisotropic_state(wl, seed=7).astype(np.float32)
     outs = []
-    for variant in ("plain", "async"):
+    for variant in ("plain",) + VARIANTS:
         with lib.Solver(wl, lib.BGK_MIXED) as s:
             s.set_stage_kernel(variant, 4)
             s.set_state(fs)          # the Q' solve reads the moments of f_in itself
@@ -75,23 +100,26 @@ def test_async_stage_entry_point_with_fn(lib):
             do = torch.empty_like(ds)
             s.stage(dn, ds, do, 0.75, 0.25, 0.25 * wl.dt())
             outs.append(do.cpu().numpy())
-    assert np.array_equal(outs[0], outs[1])
+    for o in outs[1:]:
+        assert np.array_equal(outs[0], o)
 
 
 def test_async_stage_unsupported_configurations(lib):
     # p = 2: element slabs of 27 floats are not whole 16-byte units
     wl = _mild_shock()
     with lib.Solver(wl, lib.BGK_MIXED) as s:
-        with pytest.raises(RuntimeError):
-            s.set_stage_kernel("async", 6)
+        for variant in VARIANTS:
+            with pytest.raises(RuntimeError):
+                s.set_stage_kernel(variant, 6)
         s.set_stage_kernel("auto", 6)           # falls back to the plain kernel
         with pytest.raises(RuntimeError):
             s.set_stage_kernel("auto", 1)       # depth out of range
         with pytest.raises(RuntimeError):
             s.set_stage_kernel("auto", 17)
     with lib.Solver(ASYNC_CASES["sine_box_p1"](), lib.BGK_FP64) as s:
-        with pytest.raises(RuntimeError):
-            s.set_stage_kernel("async", 6)
+        for variant in VARIANTS:
+            with pytest.raises(RuntimeError):
+                s.set_stage_kernel(variant, 6)
 
 
 def test_async_stage_bitwise_at_scale(lib):
@@ -101,7 +129,7 @@ def test_async_stage_bitwise_at_scale(lib):
     import torch
     wl = W.reduced(W.taylor_green_box(), mesh_n=(8, 8, 4))
     res = []
-    for variant in ("plain", "async"):
+    for variant in ("plain",) + VARIANTS:
         with lib.Solver(wl, lib.BGK_MIXED) as s:
             s.set_stage_kernel(variant, 6)
             x = s.node_coords()
@@ -112,5 +140,20 @@ def test_async_stage_bitwise_at_scale(lib):
             f = torch.empty(s.shape, dtype=torch.float32, device="cuda")
             s.get_state(f)
             res.append((f, s.moments()))
-    assert torch.equal(res[0][0], res[1][0])
-    assert np.array_equal(res[0][1], res[1][1])
+    for f, m in res[1:]:
+        assert torch.equal(res[0][0], f)
+        assert np.array_equal(res[0][1], m)
+
+
+def test_tuner_keeps_state_and_picks_a_supported_kernel(lib):
+    wl = ASYNC_CASES["tgv_es_p3_two_runs"]()
+    f0 = W.random_anisotropic_state(wl, seed=8).astype(np.float32)
+    with lib.Solver(wl, lib.BGK_MIXED) as s:
+        s.set_state(f0)
+        v, d, ms = s.tune_stage(wl.dt(), reps=1)
+        assert v in ("plain",) + VARIANTS and 2 <= d <= 16 and ms > 0.0
+        assert np.array_equal(s.get_state(), f0)
+        assert s.step(wl.dt(), 1) == lib.BGK_OK
+        f1 = s.get_state()
+    _, f_p, _ = _run(lib, wl, f0, "plain", 6, 1)
+    assert np.array_equal(f1, f_p)
