@@ -16,8 +16,11 @@
 //     negated difference is exact);
 //   - the barrier wait, the velocity bookkeeping and the loop control are
 //     paid once per Q points.
-// The operands arrive through the same asynchronous copy ring as in the
-// node-per-thread pipelined kernel (ring_producer).  The FP32 equilibrium
+// The operands arrive through the copy ring of the node-per-thread pipelined
+// kernel, fed here without a producer warp: the consumer warp that releases
+// a slot last (a shared-memory count, ordered by block-scope fences before
+// and after it) refills the slot for the velocity S ahead (ring_issue), so
+// every register of the block works on the stage.  The FP32 equilibrium
 // parameters come from the record the Q' solve writes beside its FP64 one
 // (BGK_NEQ32), the plane-level moment pairs live in shared memory and the
 // FP64 index moments accumulate in the moment-partials buffer, which this
@@ -31,7 +34,8 @@ template <int Q, int C, int EB, int NPT>
 struct LineGeom {
     static constexpr int NH = Q / NPT;                  // threads per node line
     static constexpr int NCT = EB * Q * Q * NH;         // consumer threads
-    static constexpr int NTHR = NCT + 32;               // + one producer warp
+    static constexpr int NTHR = NCT;                    // no producer warp: the ring feeds itself
+    static constexpr int NW = NCT / 32;
     static constexpr int NQ = C == 2 ? 7 : 6;           // plane quantities per point
     // resident blocks asked of the register allocator: a budget of about 96
     // registers per thread (128 with a whole line per thread)
@@ -114,32 +118,41 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
     constexpr int NS = SG::NS, SLOTS = SG::SLOTS, PER_C = SG::PER_C, STAGE = SG::STAGE;
     constexpr int NCT = LG::NCT, NQ = LG::NQ, NH = LG::NH, NTT = Q * Q * NH;
     extern __shared__ __align__(128) float sbuf[];
-    // [S][STAGE] copy ring | [NPT][2 NQ][NCT] plane pairs | 2S mbarriers
+    // [S][STAGE] copy ring | [NPT][2 NQ][NCT] plane pairs | 2S mbarriers | [S] release counts | [S] fills
     float *Psm = sbuf + (size_t)S * STAGE;
     unsigned long long *bars = reinterpret_cast<unsigned long long *>(Psm + NPT * 2 * NQ * NCT);
+    unsigned int *rel = reinterpret_cast<unsigned int *>(bars + 2 * S);
+    unsigned int *fills = rel + S;
     __shared__ float sD[2][Q][Q];
     __shared__ float sdg[2][Q], seps[2][Q], slam[2][Q], sdlam[2];
     __shared__ float su1[BGK_MAXV];                      // u1 of the first-axis nodes (the same on every line)
-    __shared__ int s_abort;
+    __shared__ unsigned int s_exited;
+    constexpr int NW = LG::NW;
     const int tid = threadIdx.x;
     RunGeom g;
     g.init(a.mesh, EB, blockIdx.x);
     const int vb = blockIdx.y;
     const int k0 = vb * a.Kblk, k1 = min(a.Nu, k0 + a.Kblk);
+    const int nk = k1 - k0;
     const size_t slab = (size_t)a.P;
     const VelGrid &vg = a.vg;
     const int vn1 = vg.n[0], vn2 = vg.n[1], vn3 = vg.n[2];
     if (tid == 0) {
-        ring_init(bars, S, NCT / 32);
-        s_abort = 0;
+        ring_init(bars, S, NW);
+        s_exited = 0;
+        for (int i = 0; i < S; ++i) {
+            rel[i] = 0;
+            fills[i] = 0;
+        }
+        // the first S velocities
+        for (int i = 0; i < S && i < nk; ++i) {
+            ring_issue<Q, C, EB>(a, g, sbuf, bars, i, k0 + i);
+            fills[i] = 1;
+        }
     }
     for (int j = tid; j < vn1; j += blockDim.x) su1[j] = __ldg(a.vtab32 + j).x;
     load_ops_f32<Q>(a.fr, tid, sD, sdg, seps, slam, sdlam);
     __syncthreads();
-    if (tid >= NCT) {
-        if (tid == NCT) ring_producer<Q, C, EB>(a, g, sbuf, bars, S, k0, k1, &s_abort);
-        return;
-    }
 
     // ---- consumers: thread = (element l of the run, node line r = jy + Q kz, part h of the line) ----
     const int lane = tid & 31;
@@ -412,8 +425,21 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                     for (int i = 0; i < NPT; ++i) acc[i].add(cj, jt1, outv[0][i], C == 2 ? outv[C - 1][i] : 0.f);
                 }
             }
+            // release the slot; the warp that releases it last refills it with
+            // the velocity S ahead
             __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(bars + S + slot));
+            if (lane == 0) {
+                __threadfence_block();
+                if (atomicAdd(&rel[slot], 1u) == NW - 1) {
+                    rel[slot] = 0;
+                    __threadfence_block();
+                    const int inext = (k - k0) + S;
+                    if (inext < nk) {
+                        ring_issue<Q, C, EB>(a, g, sbuf, bars, slot, k0 + inext);
+                        fills[slot] += 1;
+                    }
+                }
+            }
             if (++slot == S) { slot = 0; par ^= 1u; }
         }
         if (!ok) break;
@@ -435,8 +461,17 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
         }
     }
     if (!ok) {
-        *(volatile int *)&s_abort = 1;
-        if (lane == 0) atomicOr(a.status, BGK_DEV_TIMEOUT);
+        // a wait gave up: report it; the last warp to leave waits (bounded)
+        // for the latest fill of every slot, so no copy is in flight at exit
+        if (lane == 0) {
+            atomicOr(a.status, BGK_DEV_TIMEOUT);
+            __threadfence_block();
+            if (atomicAdd(&s_exited, 1u) == NW - 1) {
+                __threadfence_block();
+                for (int i = 0; i < S; ++i)
+                    if (fills[i] > 0) mbar_wait(smem_u32(bars + i), (fills[i] - 1) & 1);
+            }
+        }
         return;
     }
     if (mom && active) {
@@ -464,7 +499,8 @@ template <int Q, int C, int EB, int NPT>
 size_t line_smem(int depth) {
     using LG = LineGeom<Q, C, EB, NPT>;
     return (size_t)depth * StageGeom<Q, C, EB>::STAGE * sizeof(float) +
-           (size_t)NPT * 2 * LG::NQ * LG::NCT * sizeof(float) + 2 * (size_t)depth * sizeof(unsigned long long);
+           (size_t)NPT * 2 * LG::NQ * LG::NCT * sizeof(float) + 2 * (size_t)depth * sizeof(unsigned long long) +
+           2 * (size_t)depth * sizeof(unsigned int);
 }
 
 template <int Q, int C, int EB, int NPT>

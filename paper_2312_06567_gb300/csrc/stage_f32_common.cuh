@@ -328,47 +328,52 @@ __device__ __forceinline__ void ring_init(unsigned long long *bars, int S, int c
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// The producer (one thread): for every velocity of [k0, k1) wait until the
-// ring slot is free, then copy the run, the upwind x element (if outside the
-// run), the upwind y and z runs and f^n into it with bulk copies that
-// complete on the slot's full barrier.  On a timeout (its own, or a
-// consumer's through *abort) it stops, waits (bounded) for its copies still
-// in flight and sets BGK_DEV_TIMEOUT.
+// Copy everything velocity k needs into ring slot `slot`: the run, the upwind
+// x element (if outside the run), the upwind y and z runs and f^n, with bulk
+// copies that complete on the slot's full barrier (one thread).
 template <int Q, int C, int EB>
-__device__ void ring_producer(const StageArgs<float> &a, const RunGeom &g, float *sbuf, unsigned long long *bars,
-                              int S, int k0, int k1, volatile int *abort) {
+__device__ __forceinline__ void ring_issue(const StageArgs<float> &a, const RunGeom &g, float *sbuf,
+                                           unsigned long long *bars, int slot, int k) {
     using SG = StageGeom<Q, C, EB>;
     constexpr int NS = SG::NS, SLOTS = SG::SLOTS, PER_C = SG::PER_C, STAGE = SG::STAGE;
     const size_t slab = (size_t)a.P;
     const uint32_t runb = (uint32_t)(g.nel * NS * 4), elb = NS * 4;
     const bool with_fn = a.a32 != 0.f;
+    const float4 u = __ldg(a.vtab32 + k);
+    const int xe = u.x > 0.f ? g.xn0 : g.xn1, ye = u.y > 0.f ? g.yn0 : g.yn1, ze = u.z > 0.f ? g.zn0 : g.zn1;
+    const uint32_t bytes =
+        C * (runb + (xe >= 0 ? elb : 0u) + (ye >= 0 ? runb : 0u) + (ze >= 0 ? runb : 0u) + (with_fn ? runb : 0u));
+    const uint32_t full = smem_u32(bars + slot);
+    mbar_expect_tx(full, bytes);
+    float *st = sbuf + (size_t)slot * STAGE;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const float *src = a.f_s + ((size_t)c * a.Nu + k) * slab;
+        float *own = st + c * PER_C;
+        bulk_g2s(smem_u32(own + NS), src + (size_t)g.e0 * NS, runb, full);
+        if (xe >= 0) bulk_g2s(smem_u32(own + (u.x > 0.f ? 0 : (g.nel + 1) * NS)), src + (size_t)xe * NS, elb, full);
+        if (ye >= 0) bulk_g2s(smem_u32(own + SLOTS * NS), src + (size_t)ye * NS, runb, full);
+        if (ze >= 0) bulk_g2s(smem_u32(own + (SLOTS + EB) * NS), src + (size_t)ze * NS, runb, full);
+        if (with_fn)
+            bulk_g2s(smem_u32(own + (SLOTS + 2 * EB) * NS), a.f_n + ((size_t)c * a.Nu + k) * slab + (size_t)g.e0 * NS,
+                     runb, full);
+    }
+}
+
+// The producer (one thread): for every velocity of [k0, k1) wait until the
+// ring slot is free, then fill it (ring_issue).  On a timeout (its own, or a
+// consumer's through *abort) it stops, waits (bounded) for its copies still
+// in flight and sets BGK_DEV_TIMEOUT.
+template <int Q, int C, int EB>
+__device__ void ring_producer(const StageArgs<float> &a, const RunGeom &g, float *sbuf, unsigned long long *bars,
+                              int S, int k0, int k1, volatile int *abort) {
     int i = 0;
     bool ok = true;
     for (; i < k1 - k0; ++i) {
         const int slot = i % S;
         if (i >= S && !mbar_wait(smem_u32(bars + S + slot), ((i / S) & 1) ^ 1)) { ok = false; break; }
         if (*abort) { ok = false; break; }
-        const int k = k0 + i;
-        const float4 u = __ldg(a.vtab32 + k);
-        const int xe = u.x > 0.f ? g.xn0 : g.xn1, ye = u.y > 0.f ? g.yn0 : g.yn1, ze = u.z > 0.f ? g.zn0 : g.zn1;
-        const uint32_t bytes = C * (runb + (xe >= 0 ? elb : 0u) + (ye >= 0 ? runb : 0u) + (ze >= 0 ? runb : 0u) +
-                                    (with_fn ? runb : 0u));
-        const uint32_t full = smem_u32(bars + slot);
-        mbar_expect_tx(full, bytes);
-        float *st = sbuf + (size_t)slot * STAGE;
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-            const float *src = a.f_s + ((size_t)c * a.Nu + k) * slab;
-            float *own = st + c * PER_C;
-            bulk_g2s(smem_u32(own + NS), src + (size_t)g.e0 * NS, runb, full);
-            if (xe >= 0)
-                bulk_g2s(smem_u32(own + (u.x > 0.f ? 0 : (g.nel + 1) * NS)), src + (size_t)xe * NS, elb, full);
-            if (ye >= 0) bulk_g2s(smem_u32(own + SLOTS * NS), src + (size_t)ye * NS, runb, full);
-            if (ze >= 0) bulk_g2s(smem_u32(own + (SLOTS + EB) * NS), src + (size_t)ze * NS, runb, full);
-            if (with_fn)
-                bulk_g2s(smem_u32(own + (SLOTS + 2 * EB) * NS), a.f_n + ((size_t)c * a.Nu + k) * slab + (size_t)g.e0 * NS,
-                         runb, full);
-        }
+        ring_issue<Q, C, EB>(a, g, sbuf, bars, slot, k0 + i);
     }
     if (!ok) {
         // no copy may still be in flight when the block exits
