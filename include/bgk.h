@@ -114,6 +114,18 @@ BGK_API bgk_status bgk_get_state(bgk_ctx *ctx, void *f, int on_device);
  * with T = theta I. */
 BGK_API bgk_status bgk_set_maxwellian(bgk_ctx *ctx, const double *q, int on_device);
 
+/* Run bgk_step as CUDA-graph replays (enable = 1) or as direct launches
+ * (0, the default).  With graphs on, the first step captures the six
+ * launches of one SSP-RK3 step (Q' solve and fused stage, three times) into a
+ * graph per buffer parity and later steps replay it; a graph is captured
+ * again whenever something baked into its kernel arguments changes (dt, the
+ * Newton settings, the learned-guess mode, the training log, the stage
+ * kernel).  Results are bit-identical to direct launches.  While profiling
+ * (bgk_profile) is on, steps run as direct launches so each kernel can be
+ * timed.  Errors: BGK_EINVAL, BGK_ECUDA.  The paper's method has no notion
+ * of graphs; this is the launch mechanism only. */
+BGK_API bgk_status bgk_set_graphs(bgk_ctx *ctx, int enable);
+
 /* Newton controls of the Q' solve: stop when the scaled residual
  * max(|R_rho|/rho, |R_rhoU|_inf/(rho sqrt(theta)), |R_E|/E) <= tol, at most
  * max_iter updates (defaults 1e-13, 50). */

@@ -48,6 +48,7 @@ SIGNATURES = {
     "bgk_set_newton": (c_int, [c_void_p, c_double, c_int]),
     "bgk_set_qprime_engine": (c_int, [c_void_p, c_int]),
     "bgk_set_stage_kernel": (c_int, [c_void_p, c_int, c_int]),
+    "bgk_set_graphs": (c_int, [c_void_p, c_int]),
     "bgk_tune_stage": (c_int, [c_void_p, c_double, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
                                ctypes.POINTER(c_double)]),
     "bgk_rhs": (c_int, [c_void_p, c_void_p, c_void_p, c_int]),
@@ -254,6 +255,10 @@ class Solver:
         """Mixed-form stage kernel: "auto", "plain", "async", "line", "line_wide", "half" or
         "half_wide" (all but the first two on a bulk-copy ring of `depth` stages)."""
         self._check(self.lib.bgk_set_stage_kernel(self._h, self.STAGE_KERNELS[variant], int(depth)))
+
+    def set_graphs(self, enable=True):
+        """bgk_step as CUDA-graph replays (captured per buffer parity)."""
+        self._check(self.lib.bgk_set_graphs(self._h, 1 if enable else 0))
 
     def tune_stage(self, dt, reps=3):
         """Time the stage kernel candidates on this problem, keep the fastest;

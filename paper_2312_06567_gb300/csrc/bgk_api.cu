@@ -47,6 +47,15 @@ struct bgk_ctx {
     int max_iter;
     int qp_fp32;                      // Q' velocity sums on the FP32 pipe (mixed form default)
     int stage_variant, stage_depth;   // FP32 stage kernel choice and copy-ring depth
+    // CUDA graphs of one SSP-RK3 step, one per buffer parity (f[0] alternates
+    // between two buffers); recaptured when a launch parameter changes
+    bool graphs_on;
+    cudaStream_t cap_stream;          // private stream the graphs are captured on
+    struct StepGraph {
+        cudaGraphExec_t exec = nullptr;
+        void *f[3] = {nullptr, nullptr, nullptr};
+        std::vector<double> sig;
+    } graph[2];
     std::string err;
     // profiling: event pairs around launches, accumulated per kernel kind
     bool prof_on;
@@ -280,6 +289,72 @@ bgk_status stage_from_partials(bgk_ctx *ctx, const void *fn, const void *fs, voi
     return run_stage(ctx, fn, fs, fo, a, b, c, moments_out);
 }
 
+// The three stages of one SSP-RK3 step (Shu--Osher form) on the context's
+// buffers: f[0] = f^n, f[1], f[2] stage buffers; the result lands in f[1].
+bgk_status enqueue_step(bgk_ctx *ctx, double dt) {
+    void *f0 = ctx->f[0], *f1 = ctx->f[1], *f2 = ctx->f[2];
+    bgk_status st;
+    if ((st = stage_from_partials(ctx, nullptr, f0, f1, 0.0, 1.0, dt, true))) return st;
+    if ((st = stage_from_partials(ctx, f0, f1, f2, 0.75, 0.25, 0.25 * dt, true))) return st;
+    return stage_from_partials(ctx, f0, f2, f1, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0 * dt, true);
+}
+
+// Everything a captured step bakes into its kernel arguments.
+std::vector<double> step_signature(const bgk_ctx *ctx, double dt) {
+    return {dt,
+            ctx->tol,
+            (double)ctx->max_iter,
+            (double)((ctx->guess_mode == 1 && ctx->mlp_ready) ? 1 : 0),
+            (double)ctx->mlp_bf16,
+            (double)(ctx->log_on ? 1 : 0),
+            (double)(uintptr_t)ctx->log,
+            (double)ctx->log_max,
+            (double)ctx->stage_variant,
+            (double)ctx->stage_depth,
+            (double)ctx->qp_fp32};
+}
+
+void drop_graphs(bgk_ctx *ctx) {
+    for (auto &g : ctx->graph) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g = bgk_ctx::StepGraph{};
+    }
+}
+
+// Launch one step as a CUDA graph, capturing it first if there is no graph
+// for these buffers and parameters.
+bgk_status replay_step(bgk_ctx *ctx, double dt) {
+    const int slot = ctx->graph[0].f[0] == nullptr || ctx->graph[0].f[0] == ctx->f[0] ? 0 : 1;
+    bgk_ctx::StepGraph &g = ctx->graph[slot];
+    const std::vector<double> sig = step_signature(ctx, dt);
+    if (!g.exec || g.sig != sig || g.f[0] != ctx->f[0] || g.f[1] != ctx->f[1] || g.f[2] != ctx->f[2]) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g = bgk_ctx::StepGraph{};
+        // capture on a private stream (the context's stream may be the legacy
+        // default stream, which cannot be captured); replay on the context's
+        if (!ctx->cap_stream) CU(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+        const cudaStream_t user = ctx->stream;
+        CU(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed));
+        ctx->stream = ctx->cap_stream;
+        const bgk_status st = enqueue_step(ctx, dt);
+        ctx->stream = user;
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+        if (st) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        CU(e);
+        const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CU(ei);
+        g.f[0] = ctx->f[0]; g.f[1] = ctx->f[1]; g.f[2] = ctx->f[2];
+        g.sig = sig;
+    }
+    CU(cudaGraphLaunch(g.exec, ctx->stream));
+    return BGK_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -325,6 +400,8 @@ bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
     ctx->qp_fp32 = precision == BGK_MIXED ? 1 : 0;
     ctx->stage_variant = BGK_STAGE_AUTO;
     ctx->stage_depth = 6;
+    ctx->graphs_on = false;
+    ctx->cap_stream = nullptr;
     for (int d = 0; d < 3; ++d) {
         ctx->vn[d] = vg->n[d];
         ctx->vg.n[d] = vg->n[d];
@@ -450,6 +527,8 @@ bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
 bgk_status bgk_destroy(bgk_ctx *ctx) {
     if (!ctx) return BGK_EINVAL;
     cudaStreamSynchronize(ctx->stream);
+    drop_graphs(ctx);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (auto &r : ctx->prof_pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : ctx->ev_pool) cudaEventDestroy(e);
     for (int i = 0; i < 3; ++i) cudaFree(ctx->f[i]);
@@ -615,6 +694,14 @@ bgk_status bgk_tune_stage(bgk_ctx *ctx, double dt, int reps, int *variant_out, i
     return BGK_OK;
 }
 
+bgk_status bgk_set_graphs(bgk_ctx *ctx, int enable) {
+    if (!ctx) return BGK_EINVAL;
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (!enable) drop_graphs(ctx);
+    ctx->graphs_on = enable != 0;
+    return BGK_OK;
+}
+
 bgk_status bgk_set_newton(bgk_ctx *ctx, double tol, int max_iter) {
     if (!ctx || !(tol > 0.0) || max_iter < 0) return BGK_EINVAL;
     ctx->tol = tol;
@@ -629,11 +716,14 @@ bgk_status bgk_step(bgk_ctx *ctx, double dt, int n_steps) {
         if ((st = run_moments(ctx, ctx->f[0]))) return st;
         ctx->part_valid = true;
     }
+    const bool graphs = ctx->graphs_on && !ctx->prof_on;
     for (int n = 0; n < n_steps; ++n) {
-        void *f0 = ctx->f[0], *f1 = ctx->f[1], *f2 = ctx->f[2];
-        if ((st = stage_from_partials(ctx, nullptr, f0, f1, 0.0, 1.0, dt, true))) return st;
-        if ((st = stage_from_partials(ctx, f0, f1, f2, 0.75, 0.25, 0.25 * dt, true))) return st;
-        if ((st = stage_from_partials(ctx, f0, f2, f1, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0 * dt, true))) return st;
+        void *f0 = ctx->f[0], *f1 = ctx->f[1];
+        if (graphs) {
+            if ((st = replay_step(ctx, dt))) return st;
+        } else if ((st = enqueue_step(ctx, dt))) {
+            return st;
+        }
         ctx->f[0] = f1;
         ctx->f[1] = f0;
     }
