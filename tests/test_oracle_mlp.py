@@ -69,3 +69,23 @@ def test_features_and_target_special_cases():
     assert np.allclose(mlp.target(m, qp, gas), 0.0, atol=1e-15)
     d = np.random.default_rng(5).standard_normal((2, 5)) * 1e-3
     assert np.allclose(mlp.target(m, mlp.guess(m, d, gas), gas), d, atol=1e-14)
+
+
+def test_invariants_of_a_rotated_anisotropic_state():
+    """A sampled anisotropic Gaussian with covariance R diag(s) R^T (R a random
+    rotation): A = Pi/(rho theta) has the eigenvalues s/theta, so I1, I2, I3 are
+    the elementary symmetric functions of s/theta whatever R is."""
+    vg = VelocityGrid((40, 40, 40), (-9, -9, -9), (9, 9, 9))
+    gas = bgk.Gas(delta=0.0, Pr=2.0 / 3.0, mu_ref=0.05, theta_ref=1.0, theta_S=0.5)
+    q, _ = np.linalg.qr(np.random.default_rng(7).standard_normal((3, 3)))
+    s = np.array([0.7, 1.0, 1.45])
+    T = q @ np.diag(s) @ q.T
+    F = bgk.gaussian(vg.u, np.array([1.3]), np.array([[0.2, -0.1, 0.05]]), T[None])
+    m = bgk.raw_moments(F, None, vg)
+    x = mlp.features(m, gas)
+    theta = s.mean()
+    ev = s / theta
+    assert np.isclose(x[0, 4], theta, rtol=1e-9)
+    assert np.isclose(x[0, 5], ev.sum(), rtol=1e-9)
+    assert np.isclose(x[0, 6], ev[0] * ev[1] + ev[0] * ev[2] + ev[1] * ev[2], rtol=1e-9)
+    assert np.isclose(x[0, 7], ev.prod(), rtol=1e-9)
