@@ -171,6 +171,31 @@ class Problem:
         return float(np.sum(self.vg.w[None, :, None, None] * Wx * f * f))
 
 
+def element_residual(h, p, vg, gas, f27, guess=None, tol=1e-13, max_iter=50, with_source=False):
+    """R(f) = -div(u f) + S(f) of one element from its 3x3x3 block of elements.
+
+    f27[C, Nu, 27, Ns] holds the element (block index 13) and its neighbours in
+    the order e = i1 + 3 (i2 + 3 i3); only the six face neighbours enter the
+    element's residual (the upwind flux couples face neighbours only, and S is
+    local).  The block is evaluated as a 3x3x3 box of spacing h whose outer
+    faces see a zero exterior state, which affects the outer elements only.
+    Used to check single elements of states too large for the whole-mesh
+    routines.  Returns R[C, Nu, Ns] (and the source part S[C, Nu, Ns] with
+    with_source).
+    """
+    from .mesh import BoxMesh
+    mesh = BoxMesh((3, 3, 3), (0.0, 0.0, 0.0), tuple(3.0 * np.asarray(h, dtype=np.float64)), (False, False, False))
+    prob = Problem(mesh, p, vg, gas, exterior=lambda d, side, fm: np.zeros_like(fm))
+    div = prob.divergence(f27)[:, :, 13, :]
+    C, Nu = f27.shape[:2]
+    F = f27[0, :, 13, :]
+    G = f27[1, :, 13, :] if C == 2 else None
+    S_F, S_G, _ = bgk.bgk_source(F, G, gas, vg, guess=guess, tol=tol, max_iter=max_iter)
+    S = np.stack([S_F] + ([S_G] if C == 2 else []))
+    R = S - div
+    return (R, S) if with_source else R
+
+
 def cfl_dt(mesh, vg, p, cfl):
     """dt = CFL h_min / (u_max (2p + 1)) (the paper gives only the explicit scheme)."""
     umax = float(np.max(np.abs(vg.u)))

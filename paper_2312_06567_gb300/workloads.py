@@ -241,6 +241,46 @@ def random_anisotropic_state(wl, seed, spread=0.3, bimodal=0.3):
     return f
 
 
+def mixture_params(wl, x, elem):
+    """Per-point parameters of a deterministic non-equilibrium state for states
+    too large for the seeded generators: at every node a mixture
+    3/4 N(U, diag s) + 1/4 N(U + a, 0.6 theta I) around the initial field, with
+    smooth anisotropic s(x), a shifted second mean a(x), density and
+    temperature modulations and a per-element density jump (discontinuous
+    element data).  x[P, 3] node coordinates, elem[P] element indices."""
+    rho, U, theta = wl.init(x)
+    P = x.shape[0]
+    rho = np.broadcast_to(rho, (P,)).astype(np.float64)
+    U = np.broadcast_to(U, (P, 3)).astype(np.float64)
+    theta = np.broadcast_to(theta, (P,)).astype(np.float64)
+    s1, s2, s3 = x[:, 0], x[:, 1], x[:, 2]
+    n1, n2 = wl.mesh_n[0], wl.mesh_n[1]
+    e1, e2, e3 = elem % n1, (elem // n1) % n2, elem // (n1 * n2)
+    jump = 1.0 + 0.025 * (((e1 + 2 * e2 + 3 * e3) % 5) - 2)
+    rho = rho * (1.0 + 0.15 * np.sin(3.0 * s1 + 2.0 * s2 - s3)) * jump
+    theta = theta * (1.0 + 0.2 * np.cos(2.0 * s1 - s2 + 3.0 * s3))
+    var1 = theta[:, None] * (1.0 + 0.3 * np.sin(np.stack([s1, s2 + 1.0, s3 + 2.0], axis=1)))
+    mean2 = U + 0.25 * np.sqrt(theta)[:, None] * np.sin(np.stack([s2 + 2.0 * s3, s3 + 2.0 * s1, s1 + 2.0 * s2], axis=1))
+    var2 = np.repeat((0.6 * theta)[:, None], 3, axis=1)
+    norm1 = 0.75 * rho / np.sqrt((2.0 * np.pi) ** 3 * var1[:, 0] * var1[:, 1] * var1[:, 2])
+    norm2 = 0.25 * rho / np.sqrt((2.0 * np.pi) ** 3 * var2[:, 0] * var2[:, 1] * var2[:, 2])
+    gfac = 0.5 * wl.delta * theta
+    return dict(mean1=U, var1=var1, norm1=norm1, mean2=mean2, var2=var2, norm2=norm2, gfac=gfac)
+
+
+def mixture_values(par, u, exp):
+    """F[len(u), P] of the mixture_params state at velocities u[Nu, 3]; the
+    arrays may be numpy or torch (exp is the matching exponential)."""
+    out = 0.0
+    for mean, var, norm in ((par["mean1"], par["var1"], par["norm1"]), (par["mean2"], par["var2"], par["norm2"])):
+        q = 0.0
+        for d in range(3):
+            c = u[:, d:d + 1] - mean[None, :, d]
+            q = q + c * c / var[None, :, d]
+        out = out + norm[None, :] * exp(-0.5 * q)
+    return out
+
+
 def reduced(wl, mesh_n=None, vel_n=None):
     """Same physics and domain with fewer elements and/or velocity nodes."""
     kw = {}

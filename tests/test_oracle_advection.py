@@ -184,3 +184,24 @@ def test_advection_conserves_totals_periodic(p):
     tot = pb.totals(div)
     scale = np.max(np.abs(pb.totals(np.abs(div))))
     assert np.all(np.abs(tot) <= 1e-14 * scale)
+
+
+def test_element_residual_from_its_block_equals_the_whole_mesh():
+    """The single-element residual evaluated on a 3x3x3 block (the element and
+    its neighbours, periodic wrap taken by the caller) equals the whole-mesh
+    residual at that element: advection and BGK source, ES with G."""
+    from oracle import stage as ost
+    from paper_2312_06567_gb300 import workloads as W
+    wl = W.reduced(W.normal_shock_tube(mach=3.0), mesh_n=(4, 3, 5), vel_n=(13, 9, 11)).replace(
+        p=2, periodic=(True, True, True), dirichlet=None, vel_lo=(-9.0, -8.0, -8.0), vel_hi=(11.0, 8.0, 8.0))
+    pb = ost.problem_from_workload(wl)
+    f = W.random_anisotropic_state(wl, seed=21)
+    R, _ = pb.rhs(f)
+    n1, n2, n3 = wl.mesh_n
+    for e in (0, 17, wl.n_elem - 1):
+        c = (e % n1, (e // n1) % n2, e // (n1 * n2))
+        idx = [((c[0] + d1) % n1) + n1 * (((c[1] + d2) % n2) + n2 * ((c[2] + d3) % n3))
+               for d3 in (-1, 0, 1) for d2 in (-1, 0, 1) for d1 in (-1, 0, 1)]
+        Re = ost.element_residual(pb.mesh.h, wl.p, pb.vg, pb.gas, f[:, :, idx, :])
+        scale = np.abs(R[:, :, e, :]).max()
+        assert np.max(np.abs(Re - R[:, :, e, :])) <= 1e-13 * scale
