@@ -238,6 +238,9 @@ def run_ours(args, rank, world, dev):
         tot1 = s.totals()
         scale = np.array([tot0[0]] * 4 + [tot0[4]])
         drift = float(np.max(np.abs(tot1 - tot0) / scale)) / args.steps
+        mac = s.macro()                                 # Kn_GLL etc. of the final state (untimed)
+        diag = {"kn_gll_max": float(mac[:, 9].max()), "mach_max": float(mac[:, 6].max()),
+                "breakdown_fraction": float(np.mean(mac[:, 9] > 0.05))}
         # per-kernel times: one more step with direct launches and an event
         # pair around each kernel (outside the timed region)
         s.profile(True)
@@ -272,7 +275,7 @@ def run_ours(args, rank, world, dev):
             newton["guess_fallbacks"] = s.mlp_stats()
             newton["training"] = train
         results[form] = dict(ms=ms, status=bgk.STATUS_NAMES[st], prof=prof, clocks=ck,
-                             newton=newton, e2e=e2e, drift=drift, stage_kernel=tuned)
+                             newton=newton, e2e=e2e, drift=drift, stage_kernel=tuned, diagnostics=diag)
         s.destroy()
         torch.cuda.empty_cache()
     return wl, results, peaks
@@ -401,6 +404,7 @@ def main():
         "component_updates_per_s": value * wl.n_comp,
         "newton": r["newton"],
         "stage_kernel": r["stage_kernel"],
+        "diagnostics": r["diagnostics"],
         "status": r["status"],
         "peaks_measured": peaks,
     }

@@ -217,6 +217,20 @@ BGK_API bgk_status bgk_moments(bgk_ctx *ctx, double *m, int on_device);
 BGK_API bgk_status bgk_moments_noalloc(const bgk_vgrid_desc *vgrid, const double *f, int n_comp,
                                        int n_points, double *m, void *stream);
 
+/* Macroscopic fields of the current state per solution point (section
+ * "Results": the density gradient-length local Knudsen number
+ * Kn_GLL = lambda ||grad rho||_2 / rho with the local mean free path
+ * lambda = (mu(theta)/rho) sqrt(pi/(2 theta)); continuum breakdown is expected
+ * above 0.05), out[n_elem * n_sol][10] FP64, points e-major:
+ *   rho, U1, U2, U3, theta, p, Mach = |U|/sqrt(gamma theta), lambda,
+ *   ||grad rho||_2, Kn_GLL.
+ * grad rho is the gradient of the FR-corrected density polynomial (nodal
+ * derivative plus correction-function terms carrying the central common
+ * interface value; at a Dirichlet face the average with the face state's
+ * density).  out is host memory (on_device = 0) or device memory (1).
+ * Errors: BGK_EINVAL, BGK_ECUDA. */
+BGK_API bgk_status bgk_macro(bgk_ctx *ctx, double *out, int on_device);
+
 /* The Q' solve alone (section "Numerical method", discrete compatibility):
  * from raw moments m[n_points][11] (layout of bgk_moments) to
  * qp[n_points][5] = (rho', U'_1..3, theta') and Newton update counts

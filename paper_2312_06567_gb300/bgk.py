@@ -55,6 +55,7 @@ SIGNATURES = {
     "bgk_step": (c_int, [c_void_p, c_double, c_int]),
     "bgk_stage": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_double, c_double]),
     "bgk_moments": (c_int, [c_void_p, c_void_p, c_int]),
+    "bgk_macro": (c_int, [c_void_p, c_void_p, c_int]),
     "bgk_moments_noalloc": (c_int, [ctypes.POINTER(VGridDesc), c_void_p, c_int, c_int, c_void_p,
                                     c_void_p]),
     "bgk_qprime": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_int]),
@@ -296,6 +297,15 @@ class Solver:
         out = np.empty((self.n_points, 11)) if out is None else out
         p, dev = _ptr(out)
         self._check(self.lib.bgk_moments(self._h, p, dev))
+        return out
+
+    MACRO_FIELDS = ("rho", "U1", "U2", "U3", "theta", "p", "mach", "lambda", "grad_rho", "kn_gll")
+
+    def macro(self, out=None):
+        """[n_points, 10] macroscopic fields (MACRO_FIELDS), incl. Kn_GLL."""
+        out = np.empty((self.n_points, 10)) if out is None else out
+        p, dev = _ptr(out)
+        self._check(self.lib.bgk_macro(self._h, p, dev))
         return out
 
     def qprime(self, m):

@@ -773,6 +773,31 @@ bgk_status bgk_moments(bgk_ctx *ctx, double *m, int on_device) {
     return BGK_OK;
 }
 
+bgk_status bgk_macro(bgk_ctx *ctx, double *out, int on_device) {
+    if (!ctx || !out) return BGK_EINVAL;
+    bgk_status st;
+    if (!ctx->part_valid) {
+        if ((st = run_moments(ctx, ctx->f[0]))) return st;
+        ctx->part_valid = true;
+    }
+    const size_t bytes = (size_t)ctx->P * BGK_NMACRO * sizeof(double);
+    double *dst = out;
+    if (!on_device) CU(cudaMallocAsync((void **)&dst, bytes, ctx->stream));
+    double face_rho[6];
+    for (int f = 0; f < 6; ++f) face_rho[f] = ctx->bc[f][0];
+    {
+        LaunchScope ls(ctx, BGK_K_OTHER);
+        CU(launch_reduce_moments(ctx->part, ctx->n_vblk, ctx->P, ctx->mom, ctx->stream));
+        CU(launch_macro(ctx->mom, dst, ctx->P, ctx->mesh, ctx->fr, ctx->gas, face_rho, ctx->stream));
+    }
+    if (!on_device) {
+        CU(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaFreeAsync(dst, ctx->stream));
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+    return BGK_OK;
+}
+
 bgk_status bgk_qprime(bgk_ctx *ctx, const double *m, int n_points, double *qp, int *iters,
                       int on_device) {
     if (!ctx || !m || !qp || n_points <= 0) return BGK_EINVAL;

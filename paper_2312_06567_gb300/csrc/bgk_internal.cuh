@@ -11,6 +11,7 @@
 
 #define BGK_MAXQ 5          // FR order p <= 4
 #define BGK_NMOM 11         // raw moment slots per point
+#define BGK_NMACRO 10       // macroscopic fields per point (bgk_macro)
 #define BGK_NEQ 20          // equilibrium record per point (12 used by the FP64 form)
 // FP32 equilibrium record per point (mixed form), the FP32 values the stage
 // kernels derive from the FP64 record, in the order they are used:
@@ -184,5 +185,7 @@ cudaError_t launch_stage_f32_line(const StageArgs<float> &a, int C, int n_vblk, 
 bool stage_f32_variant_supported(const StageArgs<float> &a, int C, int variant, int depth);
 cudaError_t launch_maxwellian_f32(float *f, const double *q, const double *vtab, int Nu, int P, int C,
                                   double delta, cudaStream_t s);
+cudaError_t launch_macro(const double *mom, double *out, int P, const MeshInfo &mesh, const FROps &fr,
+                         const GasInfo &gas, const double face_rho[6], cudaStream_t s);
 cudaError_t launch_reduce_moments(const double *part, int n_vblk, int P, double *m_out,
                                   cudaStream_t s);

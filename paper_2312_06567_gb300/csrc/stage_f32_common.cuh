@@ -275,9 +275,12 @@ __device__ __forceinline__ unsigned long long global_ns() {
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
-    while (!mbar_try(bar, parity))
+    for (;;) {
+        // the timer is read once per 32 polls (each poll may suspend briefly)
+        for (int i = 0; i < 32; ++i)
+            if (mbar_try(bar, parity)) return true;
         if (global_ns() - t0 > 2000000000ull) return false;
-    return true;
+    }
 }
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const float *src, uint32_t bytes, uint32_t bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
@@ -289,11 +292,11 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const float *src, uint32_
 // elements of one mesh row (first axis); its stage buffer holds, per
 // component: [x-halo | the run's EB elements | x-halo] [upwind y run]
 // [upwind z run] [f^n run], each element NS floats.
-template <int Q, int C, int EB>
+template <int Q, int C, int EB, bool FN = true>
 struct StageGeom {
     static constexpr int NS = Q * Q * Q;
     static constexpr int SLOTS = EB + 2;
-    static constexpr int PER_C = (SLOTS + 3 * EB) * NS;
+    static constexpr int PER_C = (SLOTS + (FN ? 3 : 2) * EB) * NS;   // f^n run only with FN
     static constexpr int STAGE = C * PER_C;               // floats per stage buffer
 };
 
@@ -329,16 +332,16 @@ __device__ __forceinline__ void ring_init(unsigned long long *bars, int S, int c
 }
 
 // Copy everything velocity k needs into ring slot `slot`: the run, the upwind
-// x element (if outside the run), the upwind y and z runs and f^n, with bulk
-// copies that complete on the slot's full barrier (one thread).
-template <int Q, int C, int EB>
+// x element (if outside the run), the upwind y and z runs and (with FN) f^n,
+// with bulk copies that complete on the slot's full barrier (one thread).
+template <int Q, int C, int EB, bool FN = true>
 __device__ __forceinline__ void ring_issue(const StageArgs<float> &a, const RunGeom &g, float *sbuf,
                                            unsigned long long *bars, int slot, int k) {
-    using SG = StageGeom<Q, C, EB>;
+    using SG = StageGeom<Q, C, EB, FN>;
     constexpr int NS = SG::NS, SLOTS = SG::SLOTS, PER_C = SG::PER_C, STAGE = SG::STAGE;
     const size_t slab = (size_t)a.P;
     const uint32_t runb = (uint32_t)(g.nel * NS * 4), elb = NS * 4;
-    const bool with_fn = a.a32 != 0.f;
+    const bool with_fn = FN && a.a32 != 0.f;
     const float4 u = __ldg(a.vtab32 + k);
     const int xe = u.x > 0.f ? g.xn0 : g.xn1, ye = u.y > 0.f ? g.yn0 : g.yn1, ze = u.z > 0.f ? g.zn0 : g.zn1;
     const uint32_t bytes =
