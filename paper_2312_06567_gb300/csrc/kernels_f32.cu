@@ -18,7 +18,9 @@
 namespace {
 
 // ---------------------------------------------------------------------------
-// Fused stage, FP32 state.  Same discretisation as the FP64 stage kernel:
+// Fused stage, FP32 state.  Same discretisation as the FP64 stage kernel
+// (all FP32 stage kernels sum each node's own-line terms in the order
+// j = i+1, ..., i+Q-1 mod Q, so their results agree bit for bit):
 // per direction t_d = sum_j Dt[side][i][j] f_j + dg[side][i] f^+ with the
 // inflow trace folded into Dt; div = sum_d (2/h_d) u_d t_d;
 // R = -div + (g' - f)/tau.  g' = exp(c0) * exp2(-log2(e)/2 c^T A c) with the
@@ -145,7 +147,13 @@ __global__ void __launch_bounds__(256) k_stage_f32(StageArgs<float> a) {
                         const float *own = sfc + le * NS + base[d];
                         float t = 0.f;
 #pragma unroll
-                        for (int j = 0; j < Q; ++j) t = fmaf(sD[side][id[d]][j], own[j * stride[d]] - fi, t);
+                        // own-line sum in the canonical order j = i+1, ..., i+Q-1 (mod Q);
+                        // the j = i term is zero
+#pragma unroll
+                        for (int m = 1; m < Q; ++m) {
+                            const int j = (id[d] + m) % Q;
+                            t = fmaf(sD[side][id[d]][j], own[j * stride[d]] - fi, t);
+                        }
                         const int en = side ? en_[d][1] : en_[d][0];
                         float dn;
                         if (en >= e0 && en < e0 + EB) {
@@ -330,7 +338,13 @@ __global__ void __launch_bounds__(TmaGeom<Q, C>::NTHR, 2) k_stage_f32_tma(StageA
                         const float *own = sc + own_off + base[d];
                         float t = 0.f;
 #pragma unroll
-                        for (int j = 0; j < Q; ++j) t = fmaf(sD[side][id[d]][j], own[j * stride[d]] - fi, t);
+                        // own-line sum in the canonical order j = i+1, ..., i+Q-1 (mod Q);
+                        // the j = i term is zero
+#pragma unroll
+                        for (int m = 1; m < Q; ++m) {
+                            const int j = (id[d] + m) % Q;
+                            t = fmaf(sD[side][id[d]][j], own[j * stride[d]] - fi, t);
+                        }
                         float dn;
                         if (!((bcm >> (2 * d + side)) & 1)) {
                             const float *nb = sc + (d == 0 ? own_off + base[0] + (side ? NS : -NS)

@@ -10,6 +10,8 @@
 //   - its own line and every line it needs (the other lines of its element
 //     in the second and third directions, the upwind neighbours' lines)
 //     arrive as one vector load each from the shared-memory stage;
+//   - own-line sums run in the canonical order j = i+1, ..., i+Q-1 (mod Q)
+//     of all FP32 stage kernels, Q-1 terms with no masked iteration;
 //   - the coefficients of the second- and third-direction sums are the same
 //     for the thread's Q points (one load serves Q products), and the
 //     first-direction deviations f_j - f_i are formed once per pair (the
@@ -292,16 +294,25 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                             for (int i = 0; i < NPT; ++i) {
                                 t[i] = 0.f;
 #pragma unroll
-                                for (int j = 0; j < Q; ++j)
-                                    if (j != i) t[i] = fmaf(sD[sx][i][j], j > i ? dv[i][j] : -dv[j][i], t[i]);
+                                for (int m = 1; m < Q; ++m) {
+                                    const int j = (i + m) % Q;      // the canonical order
+                                    t[i] = fmaf(sD[sx][i][j], j > i ? dv[i][j] : -dv[j][i], t[i]);
+                                }
                             }
                         } else {
 #pragma unroll
                             for (int i = 0; i < NPT; ++i) {
                                 t[i] = 0.f;
 #pragma unroll
-                                for (int j = 0; j < Q; ++j)
-                                    if (j != i0 + i) t[i] = fmaf(sD[sx][i0 + i][j], F[j] - Fi[i], t[i]);
+                                for (int m = 1; m < Q; ++m) {
+                                    // node j = (i0 + i + m) mod Q of the line, picked from F
+                                    // without indexing a register array at run time
+                                    const int j = (i0 + i + m) & (Q - 1);
+                                    float Fj = F[0];
+#pragma unroll
+                                    for (int jj = 1; jj < Q; ++jj) Fj = j == jj ? F[jj] : Fj;
+                                    t[i] = fmaf(sD[sx][i0 + i][j], Fj - Fi[i], t[i]);
+                                }
                             }
                         }
                         float dn[NPT];
@@ -332,8 +343,8 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
 #pragma unroll
                         for (int i = 0; i < NPT; ++i) t[i] = 0.f;
 #pragma unroll
-                        for (int jp = 0; jp < Q; ++jp) {
-                            if (jp == jy) continue;
+                        for (int m = 1; m < Q; ++m) {
+                            const int jp = (jy + m) & (Q - 1);       // the canonical order
                             float Gv[NPT];
                             ld_vec<NPT>(sc + own_off + Q * (jp + Q * kz) + i0, Gv);
                             const float D = sD[sy][jy][jp];
@@ -369,8 +380,8 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
 #pragma unroll
                         for (int i = 0; i < NPT; ++i) t[i] = 0.f;
 #pragma unroll
-                        for (int kp = 0; kp < Q; ++kp) {
-                            if (kp == kz) continue;
+                        for (int m = 1; m < Q; ++m) {
+                            const int kp = (kz + m) & (Q - 1);       // the canonical order
                             float Gv[NPT];
                             ld_vec<NPT>(sc + own_off + Q * (jy + Q * kp) + i0, Gv);
                             const float D = sD[sz][kz][kp];
