@@ -113,7 +113,9 @@ __device__ __forceinline__ void plane_add_s(float *P, int n, int q, float c, flo
     P[(NQ + q) * n] = pc;
 }
 
-template <int Q, int C, int EB, int NPT>
+// BC = false: the mesh is periodic in every direction, so no face is a
+// Dirichlet face and the per-direction tests drop out.
+template <int Q, int C, int EB, int NPT, bool BC>
 __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, EB, NPT>::MINB) k_stage_f32_line(StageArgs<float> a, int S) {
     using SG = StageGeom<Q, C, EB>;
     using LG = LineGeom<Q, C, EB, NPT>;
@@ -164,8 +166,9 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
     const int i0 = NPT * h;                              // first node of this thread on its line
     const bool active = l < g.nel;
     const int pb = (g.e0 + l) * NS + Q * r + i0;         // point of local node i: pb + i
-    const int bcm = (l == 0 && g.xn0 < 0 ? 1 : 0) | (l == g.nel - 1 && g.xn1 < 0 ? 2 : 0) | (g.yn0 < 0 ? 4 : 0) |
-                    (g.yn1 < 0 ? 8 : 0) | (g.zn0 < 0 ? 16 : 0) | (g.zn1 < 0 ? 32 : 0);
+    const int bcm = !BC ? 0
+                        : (l == 0 && g.xn0 < 0 ? 1 : 0) | (l == g.nel - 1 && g.xn1 < 0 ? 2 : 0) | (g.yn0 < 0 ? 4 : 0) |
+                              (g.yn1 < 0 ? 8 : 0) | (g.zn0 < 0 ? 16 : 0) | (g.zn1 < 0 ? 32 : 0);
     const int own_off = (l + 1) * NS;                    // own element within a component's stage region
     const int ln = Q * r;                                // own line within an element
     const bool mom = a.part != nullptr;
@@ -316,7 +319,7 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                             }
                         }
                         float dn[NPT];
-                        if (!((bcm >> sx) & 1)) {
+                        if (!BC || !((bcm >> sx) & 1)) {
                             float NB[Q];
                             ld_vec<Q>(sc + own_off + (sx ? NS : -NS) + ln, NB);
 #pragma unroll
@@ -351,7 +354,7 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
 #pragma unroll
                             for (int i = 0; i < NPT; ++i) t[i] = fmaf(D, Gv[i] - Fi[i], t[i]);
                         }
-                        if (!((bcm >> (2 + sy)) & 1)) {
+                        if (!BC || !((bcm >> (2 + sy)) & 1)) {
 #pragma unroll
                             for (int i = 0; i < NPT; ++i) dn[i] = sdlam[sy] * Fi[i];
 #pragma unroll
@@ -388,7 +391,7 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
 #pragma unroll
                             for (int i = 0; i < NPT; ++i) t[i] = fmaf(D, Gv[i] - Fi[i], t[i]);
                         }
-                        if (!((bcm >> (4 + sz)) & 1)) {
+                        if (!BC || !((bcm >> (4 + sz)) & 1)) {
 #pragma unroll
                             for (int i = 0; i < NPT; ++i) dn[i] = sdlam[sz] * Fi[i];
 #pragma unroll
@@ -519,14 +522,20 @@ cudaError_t line_launch(const StageArgs<float> &a, int n_vblk, int depth, cudaSt
     const size_t smem = line_smem<Q, C, EB, NPT>(depth);
     static size_t attr = 0;
     if (smem > attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_stage_f32_line<Q, C, EB, NPT>,
+        cudaError_t e = cudaFuncSetAttribute(k_stage_f32_line<Q, C, EB, NPT, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_stage_f32_line<Q, C, EB, NPT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
         if (e != cudaSuccess) return e;
         attr = smem;
     }
     const int cpr = (a.mesh.n[0] + EB - 1) / EB;
     dim3 grid(cpr * a.mesh.n[1] * a.mesh.n[2], n_vblk);
-    k_stage_f32_line<Q, C, EB, NPT><<<grid, LineGeom<Q, C, EB, NPT>::NTHR, smem, s>>>(a, depth);
+    if (a.mesh.periodic[0] && a.mesh.periodic[1] && a.mesh.periodic[2])
+        k_stage_f32_line<Q, C, EB, NPT, false><<<grid, LineGeom<Q, C, EB, NPT>::NTHR, smem, s>>>(a, depth);
+    else
+        k_stage_f32_line<Q, C, EB, NPT, true><<<grid, LineGeom<Q, C, EB, NPT>::NTHR, smem, s>>>(a, depth);
     return cudaGetLastError();
 }
 
