@@ -16,12 +16,17 @@
 // coordinates ut = u - U centred on the point's macroscopic velocity; R and
 // J are linear combinations of those.
 //
-// Two engines for the velocity sums (k_qprime<F32>):
+// Velocity-sum engines (k_qprime<F32>):
 //   Engine64  FP64 throughout (the FP64 form; parity with the oracle);
 //   Engine32  FP32 walk and fold (GB300's FP64 pipe issues 1/64 of the FP32
 //             rate), Newton algebra in FP64, converged to FP32 resolution.
 //             Used by the mixed form, whose conservation does not rest on
-//             this solve: see the correction pass below.
+//             this solve: see the correction pass below;
+//   fused_pass  (mixed form) the exact FP32 equilibrium evaluated once per
+//             velocity for both the residual (from its exact moments) and
+//             the Jacobian moments: used where the evaluation is expected to
+//             be the last (from the learned guess, after an update), so the
+//             correction needs no pass of its own.
 // The mixed form's correction pass evaluates the exact FP32 equilibrium the
 // stage will use (Eq32), measures its moments with exact-product compensated
 // sums, and fits gamma so that g32 (1 + gamma . phi(ut)), phi = (1, ut,
@@ -226,15 +231,19 @@ __device__ __forceinline__ void equilibrium_params(const PointState &ps, double 
 
 // Residual (returns the scaled norm) and, if J != nullptr, the Jacobian, from
 // the 35 centred moments M of g(x).
+// low (optional): exact centred moments (sum w g, sum w g ut_d, sum w g |ut|^2/2)
+// of the equilibrium actually used, replacing the first three orders of M in
+// the residual and the Jacobian's leading terms.
 __device__ __forceinline__ double assemble(const double M[35], const PointState &ps, const GasInfo &gs,
-                                           const double x[5], const Sym3 &A, double R[5], double (*J)[5]) {
+                                           const double x[5], const Sym3 &A, double R[5], double (*J)[5],
+                                           const double *low = nullptr) {
 #define MM(p1, p2, p3) M[midx(p1, p2, p3)]
     const double *U0 = ps.U0;
     const double hd = 0.5 * gs.delta;
     const double dl[3] = {x[1] - U0[0], x[2] - U0[1], x[3] - U0[2]};
-    const double M0 = MM(0, 0, 0);
-    const double Me[3] = {MM(1, 0, 0), MM(0, 1, 0), MM(0, 0, 1)};
-    const double Se = 0.5 * (MM(2, 0, 0) + MM(0, 2, 0) + MM(0, 0, 2));
+    const double M0 = low ? low[0] : MM(0, 0, 0);
+    const double Me[3] = {low ? low[1] : MM(1, 0, 0), low ? low[2] : MM(0, 1, 0), low ? low[3] : MM(0, 0, 1)};
+    const double Se = low ? low[4] : 0.5 * (MM(2, 0, 0) + MM(0, 2, 0) + MM(0, 0, 2));
     const double eint = hd * x[4];
     const double dM0 = M0 - ps.rho;
     const double UMe = U0[0] * Me[0] + U0[1] * Me[1] + U0[2] * Me[2];
@@ -472,16 +481,15 @@ __device__ __forceinline__ void correction_sums(const QPrimeArgs &a, int lane, d
 // gamma from G gamma = T - S (one thread), with S the moments of g32 from the
 // index moments Jm, T the centred moments of f itself and G from the
 // solve's moments.
-__device__ __forceinline__ void correction_fit(const QPrimeArgs &a, const PointState &ps, const double x[5],
-                                               const double Jm[7], const double Gsrc[35], double gam[5]) {
-    const VelGrid &vg = a.vg;
+// S_i = sum w phi_i g32 in ut = u - U0 coordinates (u_d = uc_d + jt_d h_d) from
+// the index moments J000 J100 J200 J010 J020 J001 J002.
+__device__ __forceinline__ void exact_low_moments(const VelGrid &vg, const PointState &ps, const double Jm[7],
+                                                  double S[5]) {
     const int jc[3] = {(vg.n[0] - 1) / 2, (vg.n[1] - 1) / 2, (vg.n[2] - 1) / 2};
-    // S_i = sum w phi_i g32 in ut = u - U0 coordinates: u_d = uc_d + jt_d h_d
     const double W = vg.h[0] * vg.h[1] * vg.h[2];
     const double o[3] = {vg.lo[0] + jc[0] * vg.h[0] - ps.U0[0], vg.lo[1] + jc[1] * vg.h[1] - ps.U0[1],
                          vg.lo[2] + jc[2] * vg.h[2] - ps.U0[2]};
     const double J1[3] = {Jm[1], Jm[3], Jm[5]}, J2[3] = {Jm[2], Jm[4], Jm[6]};
-    double S[5];
     S[0] = W * Jm[0];
     double s4 = 0.0;
 #pragma unroll
@@ -490,6 +498,12 @@ __device__ __forceinline__ void correction_fit(const QPrimeArgs &a, const PointS
         s4 += o[d] * o[d] * Jm[0] + 2.0 * o[d] * vg.h[d] * J1[d] + vg.h[d] * vg.h[d] * J2[d];
     }
     S[4] = 0.5 * W * s4;
+}
+
+__device__ __forceinline__ void correction_fit(const QPrimeArgs &a, const PointState &ps, const double x[5],
+                                               const double Jm[7], const double Gsrc[35], double gam[5]) {
+    double S[5];
+    exact_low_moments(a.vg, ps, Jm, S);
     // targets: the centred moments of f, with the G equilibrium's share of
     // the energy (delta theta'/2 per unit mass) taken out of phi_4
     const double *m = ps.m;
@@ -766,6 +780,108 @@ struct Engine32 {
     }
 };
 
+// One pass that serves both the Newton residual and the correction: the
+// stage's exact FP32 equilibrium g32 (Eq32) is evaluated once per velocity
+// and accumulated (a) into the error-free index moments J000..J002 (as in
+// correction_sums), which give the exact discrete moments of g32 and so the
+// residual of the equilibrium actually used, and (b) into plain FP32 line
+// sums T_m = sum_j1 w1 g32 ut1^m, m <= 4, folded per line into the 35 centred
+// moments (as in Engine32) for the Jacobian and the correction's G.
+__device__ __forceinline__ void fused_pass(const QPrimeArgs &a, int lane, const PointState &ps, double c0,
+                                           const double x[5], const Sym3 &A, const float *su1, double Md[35],
+                                           double Jm[7]) {
+    const VelGrid &vg = a.vg;
+    const int n1 = vg.n[0], n2 = vg.n[1], n3 = vg.n[2];
+    const int jc[3] = {(n1 - 1) / 2, (n2 - 1) / 2, (n3 - 1) / 2};
+    const double qd[10] = {c0, x[1], x[2], x[3], A.t11, A.t22, A.t33, A.t12, A.t13, A.t23};
+    Eq32 e32;
+    e32.load(qd);
+    const float U0x = (float)ps.U0[0];
+    const float h1 = (float)vg.h[0], h2 = (float)vg.h[1], h3 = (float)vg.h[2];
+    const float o2 = (float)(vg.lo[1] - ps.U0[1]), o3 = (float)(vg.lo[2] - ps.U0[2]);
+    float M[35];
+#pragma unroll
+    for (int i = 0; i < 35; ++i) M[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < 7; ++i) Jm[i] = 0.0;
+    float P[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, Pc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    const int nl = n2 * n3, chunk = (nl + 31) / 32;
+    const int l0 = min(nl, lane * chunk), l1 = min(nl, l0 + chunk);
+    int j3cur = l0 < l1 ? l0 / n2 : -1;
+#define BGK_FLUSH_PLANE(J3)                                                                     \
+    do {                                                                                        \
+        const double c3 = ((J3) == 0 || (J3) == n3 - 1) ? 0.5 : 1.0, t3 = (double)((J3) - jc[2]); \
+        double Pd[5];                                                                           \
+        _Pragma("unroll") for (int i = 0; i < 5; ++i) {                                         \
+            Pd[i] = (double)P[i] + (double)Pc[i];                                               \
+            P[i] = Pc[i] = 0.f;                                                                 \
+        }                                                                                       \
+        Jm[0] = fma(c3, Pd[0], Jm[0]);                                                          \
+        Jm[1] = fma(c3, Pd[1], Jm[1]);                                                          \
+        Jm[2] = fma(c3, Pd[2], Jm[2]);                                                          \
+        Jm[3] = fma(c3, Pd[3], Jm[3]);                                                          \
+        Jm[4] = fma(c3, Pd[4], Jm[4]);                                                          \
+        Jm[5] = fma(c3 * t3, Pd[0], Jm[5]);                                                     \
+        Jm[6] = fma(c3 * t3 * t3, Pd[0], Jm[6]);                                                \
+    } while (0)
+    for (int line = l0; line < l1; ++line) {
+        const int j2 = line % n2, j3 = line / n2;
+        if (j3 != j3cur) { BGK_FLUSH_PLANE(j3cur); j3cur = j3; }
+        const float4 *vl32 = a.vtab32 + (size_t)line * n1;
+        float lin, cst;
+        e32.line(vl32[0].y, vl32[0].z, lin, cst);
+        float L0 = 0.f, C0 = 0.f, L1 = 0.f, C1 = 0.f, L2 = 0.f, C2 = 0.f;
+        float Tm[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        float jt = (float)(-jc[0]);
+        for (int j1 = 0; j1 < n1; ++j1, jt += 1.f) {
+            const float u1 = su1[j1];
+            const float g = e32.g(u1, lin, cst);
+            const float cg = (j1 == 0 || j1 == n1 - 1) ? __fmul_rn(0.5f, g) : g;     // exact
+            sum2(L0, C0, cg);
+            const float p1 = __fmul_rn(cg, jt);
+            sum2(L1, C1, p1);
+            C1 = __fadd_rn(C1, fmaf(cg, jt, -p1));
+            const float jj = __fmul_rn(jt, jt);
+            const float p2 = __fmul_rn(cg, jj);
+            sum2(L2, C2, p2);
+            C2 = __fadd_rn(C2, fmaf(cg, jj, -p2));
+            // Jacobian line sums (plain FP32)
+            const float ut = u1 - U0x;
+            const float t1 = cg * ut, t2 = t1 * ut, t3 = t2 * ut;
+            Tm[0] += cg; Tm[1] += t1; Tm[2] += t2; Tm[3] += t3; Tm[4] = fmaf(t3, ut, Tm[4]);
+        }
+        const float c2 = trapf(j2, n2), jt2 = (float)(j2 - jc[1]);
+        const float b = __fmul_rn(c2, jt2), bb = __fmul_rn(b, jt2);                  // exact
+        plane_add(P[0], Pc[0], c2, L0, C0);
+        plane_add(P[1], Pc[1], c2, L1, C1);
+        plane_add(P[2], Pc[2], c2, L2, C2);
+        plane_add(P[3], Pc[3], b, L0, C0);
+        plane_add(P[4], Pc[4], bb, L0, C0);
+        // fold the line sums into the 35 centred moments
+        const float ut2 = fmaf((float)j2, h2, o2), ut3 = fmaf((float)j3, h3, o3);
+        const float w23 = ((j2 == 0 || j2 == n2 - 1) ? 0.5f * h2 : h2) * ((j3 == 0 || j3 == n3 - 1) ? 0.5f * h3 : h3) * h1;
+        float pu2[5], pu3[5];
+        pu2[0] = w23; pu3[0] = 1.f;
+#pragma unroll
+        for (int q = 1; q < 5; ++q) { pu2[q] = pu2[q - 1] * ut2; pu3[q] = pu3[q - 1] * ut3; }
+        int idx = 0;
+#pragma unroll
+        for (int aa = 0; aa <= 4; ++aa)
+#pragma unroll
+            for (int bb2 = 0; bb2 <= 4 - aa; ++bb2) {
+                const float Pp = pu2[aa] * pu3[bb2];
+#pragma unroll
+                for (int mm = 0; mm <= 4 - aa - bb2; ++mm, ++idx) M[idx] = fmaf(Pp, Tm[mm], M[idx]);
+            }
+    }
+    if (j3cur >= 0) BGK_FLUSH_PLANE(j3cur);
+#undef BGK_FLUSH_PLANE
+#pragma unroll
+    for (int i = 0; i < 7; ++i) Jm[i] = warp_sum(Jm[i]);
+#pragma unroll
+    for (int i = 0; i < 35; ++i) Md[i] = (double)warp_sumf(M[i]);
+}
+
 // One block solves a batch of QB points.  The velocity sums run one warp per
 // point (QW warps take the batch's points in turn); the per-point algebra
 // (prologue, Newton step, correction fit, epilogue) runs one lane of warp 0
@@ -783,6 +899,8 @@ struct QPShared {
     double Jm[QB][7];
     int it[QB], tot[QB];
     int conv[QB], from_guess[QB], active[QB];
+    int fused[QB];           // next evaluation by the fused pass (FP32-sum engine)
+    int exact[QB];           // Jm holds the exact moments of the last evaluation
     int any_active;
 };
 
@@ -813,6 +931,10 @@ __global__ void __launch_bounds__(QB * QW, 2) k_qprime(QPrimeArgs a) {
             S.from_guess[i] = fg;
             S.it[i] = 0; S.tot[i] = 0; S.conv[i] = 0; S.active[i] = 1;
             S.res[i] = 1.0e300;
+            // from the learned guess the first evaluation is expected to be the
+            // last: the fused pass gives its residual and its correction at once
+            S.fused[i] = F32 && fg && a.mixed && a.eq;
+            S.exact[i] = 0;
             if (left && a.fallbacks) atomicAdd(a.fallbacks, 1ull);
         }
     }
@@ -835,7 +957,14 @@ __global__ void __launch_bounds__(QB * QW, 2) k_qprime(QPrimeArgs a) {
 #pragma unroll
             for (int j = 0; j < 5; ++j) x[j] = S.x[i][j];
             double M[35];
-            if (F32) {
+            if (F32 && S.fused[i]) {
+                double Jm[7];
+                fused_pass(a, lane, S.ps[i], S.c0[i], x, A, su1, M, Jm);
+                if (lane == 0) {
+#pragma unroll
+                    for (int j = 0; j < 7; ++j) S.Jm[i][j] = Jm[j];
+                }
+            } else if (F32) {
                 Engine32 e32;
                 e32.moments(a.vg, S.ps[i], x, A, S.c0[i], lane, M);
             } else {
@@ -846,6 +975,7 @@ __global__ void __launch_bounds__(QB * QW, 2) k_qprime(QPrimeArgs a) {
             if (lane == 0) {
 #pragma unroll
                 for (int j = 0; j < 35; ++j) S.M[i][j] = M[j];
+                S.exact[i] = F32 && S.fused[i];
             }
             __syncwarp();
         }
@@ -858,8 +988,10 @@ __global__ void __launch_bounds__(QB * QW, 2) k_qprime(QPrimeArgs a) {
 #pragma unroll
                 for (int j = 0; j < 5; ++j) x[j] = S.x[lane][j];
                 const Sym3 A = load_sym3(S.A[lane]);
-                double R[5], J[5][5];
-                const double res = assemble(S.M[lane], ps, a.gas, x, A, R, J);
+                double R[5], J[5][5], low[5];
+                const bool ex = S.exact[lane];
+                if (ex) exact_low_moments(a.vg, ps, S.Jm[lane], low);
+                const double res = assemble(S.M[lane], ps, a.gas, x, A, R, J, ex ? low : nullptr);
                 S.res[lane] = res;
                 int it = S.it[lane];
                 act = true;
@@ -872,6 +1004,7 @@ __global__ void __launch_bounds__(QB * QW, 2) k_qprime(QPrimeArgs a) {
                     // restarts from q
                     x[0] = ps.rho; x[1] = ps.U0[0]; x[2] = ps.U0[1]; x[3] = ps.U0[2]; x[4] = ps.theta;
                     S.from_guess[lane] = 0;
+                    S.fused[lane] = 0;                   // from q, an update is expected first
                     it = 0;
                     if (a.fallbacks) atomicAdd(a.fallbacks, 1ull);
                 } else if (it >= a.max_iter || !(res == res) || !newton_update(J, R, x, ps.B, Pr)) {
@@ -879,6 +1012,8 @@ __global__ void __launch_bounds__(QB * QW, 2) k_qprime(QPrimeArgs a) {
                 } else {
                     ++it;
                     ++S.tot[lane];
+                    // after an update the next evaluation is usually the last
+                    S.fused[lane] = F32 && a.mixed && a.eq;
                 }
                 S.it[lane] = it;
 #pragma unroll
@@ -895,6 +1030,7 @@ __global__ void __launch_bounds__(QB * QW, 2) k_qprime(QPrimeArgs a) {
     const bool fit = a.mixed && a.eq;
     if (fit) {
         for (int i = wib; i < nb; i += QW) {
+            if (S.exact[i]) continue;            // the fused pass measured them already
             double x[5], Jm[7];
 #pragma unroll
             for (int j = 0; j < 5; ++j) x[j] = S.x[i][j];
