@@ -219,14 +219,20 @@ bgk_status check_device_status(bgk_ctx *ctx) {
     return BGK_OK;
 }
 
-bgk_status run_moments(bgk_ctx *ctx, const void *f) {
+// Moment partials of a state.  The FP32 state's stepping path (resum =
+// false) uses the stage epilogue's error-free FP32 accumulation; the
+// diagnostic entry points (resum = true) re-sum in FP64, independently of it.
+bgk_status run_moments(bgk_ctx *ctx, const void *f, bool resum = false) {
     LaunchScope ls(ctx, BGK_K_MOMENTS);
     if (ctx->precision == BGK_FP64) {
         MomentArgs64 a{(const double *)f, ctx->part, ctx->vtab, ctx->Nu, ctx->P, ctx->Kblk, ctx->C};
         CU(launch_moments_f64(a, ctx->n_vblk, ctx->stream));
-    } else {
+    } else if (resum) {
         CU(launch_moments_f32((const float *)f, ctx->part, ctx->vtab, ctx->Nu, ctx->P, ctx->Kblk,
                               ctx->C, ctx->n_vblk, ctx->stream));
+    } else {
+        CU(launch_moments_f32_exact((const float *)f, ctx->part, ctx->vg, ctx->Nu, ctx->P, ctx->Kblk, ctx->C,
+                                    ctx->n_vblk, ctx->stream));
     }
     return BGK_OK;
 }
@@ -760,7 +766,7 @@ bgk_status bgk_moments(bgk_ctx *ctx, double *m, int on_device) {
     if (!ctx || !m) return BGK_EINVAL;
     bgk_status st;
     if (!ctx->part_valid) {
-        if ((st = run_moments(ctx, ctx->f[0]))) return st;
+        if ((st = run_moments(ctx, ctx->f[0], true))) return st;
         ctx->part_valid = true;
     }
     {
@@ -777,7 +783,7 @@ bgk_status bgk_macro(bgk_ctx *ctx, double *out, int on_device) {
     if (!ctx || !out) return BGK_EINVAL;
     bgk_status st;
     if (!ctx->part_valid) {
-        if ((st = run_moments(ctx, ctx->f[0]))) return st;
+        if ((st = run_moments(ctx, ctx->f[0], true))) return st;
         ctx->part_valid = true;
     }
     const size_t bytes = (size_t)ctx->P * BGK_NMACRO * sizeof(double);

@@ -175,6 +175,8 @@ cudaError_t launch_maxwellian_f64(double *f, const double *q, const double *vtab
                                   int C, double delta, cudaStream_t s);
 cudaError_t launch_moments_f32(const float *f, double *part, const double *vtab, int Nu, int P,
                                int Kblk, int C, int n_vblk, cudaStream_t s);
+cudaError_t launch_moments_f32_exact(const float *f, double *part, const VelGrid &vg, int Nu, int P, int Kblk,
+                                     int C, int n_vblk, cudaStream_t s);
 cudaError_t launch_stage_f32(const StageArgs<float> &a, int C, int n_vblk, int variant, int depth,
                              cudaStream_t s);
 bool stage_f32_tma_supported(const StageArgs<float> &a, int C, int depth);

@@ -391,6 +391,45 @@ __global__ void __launch_bounds__(TmaGeom<Q, C>::NTHR, 2) k_stage_f32_tma(StageA
     }
 }
 
+// Raw moments of an FP32 state with the stage epilogue's error-free
+// accumulation (IndexMoments, velocities in the same order), for the stepping
+// path when the state was set from outside: memory-bound, with no FP64 work
+// per DOF, and equal to what a stage's epilogue yields for the same values.
+__global__ void __launch_bounds__(256) k_moments_f32_exact(const float *f, double *part, VelGrid vg, int Nu, int P,
+                                                            int Kblk, int C) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const int vb = blockIdx.y;
+    const int k0 = vb * Kblk, k1 = min(Nu, k0 + Kblk);
+    const int vn1 = vg.n[0], vn2 = vg.n[1], vn3 = vg.n[2];
+    const int jc[3] = {(vn1 - 1) / 2, (vn2 - 1) / 2, (vn3 - 1) / 2};
+    IndexMoments acc;
+    acc.init();
+    for (int kl = k0; kl < k1; kl += vn1) {
+        const int line = kl / vn1;
+        const int j2 = line % vn2, j3 = line / vn2;
+        if (j3 != acc.j3cur) {
+            if (acc.j3cur >= 0) acc.flush_plane(trap(acc.j3cur, vn3), (float)(acc.j3cur - jc[2]));
+            acc.j3cur = j3;
+        }
+        float jt1 = (float)(-jc[0]);
+#pragma unroll 8
+        for (int j1 = 0; j1 < vn1; ++j1, jt1 += 1.f) {
+            const size_t k = (size_t)(kl + j1);
+            const float F = __ldcs(f + k * P + p);
+            const float G = C == 2 ? __ldcs(f + ((size_t)Nu + k) * P + p) : 0.f;
+            acc.add(trap(j1, vn1), jt1, F, G);
+        }
+        acc.end_line(trap(j2, vn2), (float)(j2 - jc[1]));
+    }
+    if (acc.j3cur >= 0) acc.flush_plane(trap(acc.j3cur, vn3), (float)(acc.j3cur - jc[2]));
+    const double uc[3] = {vg.lo[0] + jc[0] * vg.h[0], vg.lo[1] + jc[1] * vg.h[1], vg.lo[2] + jc[2] * vg.h[2]};
+    double m[BGK_NMOM];
+    index_to_raw(acc.J, vg, uc, m);
+#pragma unroll
+    for (int j = 0; j < BGK_NMOM; ++j) part[((size_t)vb * BGK_NMOM + j) * P + p] = m[j];
+}
+
 // Raw moments of an FP32 state with FP64 accumulation (initialisation and
 // test entry points; the stepping loop takes its moments from the stage).
 __global__ void __launch_bounds__(256) k_moments_f32(const float *f, double *part, const double *vtab,
@@ -438,6 +477,13 @@ __global__ void k_maxwellian_f32(float *f, const double *qin, const double *vtab
 }
 
 }  // namespace
+
+cudaError_t launch_moments_f32_exact(const float *f, double *part, const VelGrid &vg, int Nu, int P, int Kblk,
+                                     int C, int n_vblk, cudaStream_t s) {
+    dim3 grid((P + 255) / 256, n_vblk);
+    k_moments_f32_exact<<<grid, 256, 0, s>>>(f, part, vg, Nu, P, Kblk, C);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_moments_f32(const float *f, double *part, const double *vtab, int Nu, int P,
                                int Kblk, int C, int n_vblk, cudaStream_t s) {
