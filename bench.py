@@ -327,6 +327,12 @@ def kernel_rooflines(wl, r, peaks, form):
     return out
 
 
+# DRAM bytes per DOF of a stage launch, mean over the three stages of a step,
+# from the ncu capture summarised in profiles/ncu_stage_f32_line_*.md (valid
+# for that kernel as it stands; traffic per DOF does not depend on N_e).
+MEASURED_STAGE_TRAFFIC_PER_DOF = {"line_wide": 11.36}
+
+
 def dominant_roofline(rl):
     k = max(rl, key=lambda n: rl[n]["ms"])
     d = dict(rl[k])
@@ -413,6 +419,9 @@ def main():
         "peaks_measured": peaks,
     }
     rl = kernel_rooflines(wl, r, peaks, main_form)
+    sk = (r.get("stage_kernel") or {}).get("variant")
+    if sk in MEASURED_STAGE_TRAFFIC_PER_DOF and wl.p == 3 and wl.n_comp == 1:
+        rl["stage"]["traffic"] = MEASURED_STAGE_TRAFFIC_PER_DOF[sk] * wl.dof
     line["roofline"] = dominant_roofline(rl)
     line["roofline_kernels"] = rl
     for form, rr in results.items():
