@@ -991,7 +991,9 @@ __global__ void __launch_bounds__(QB * QW, 2) k_qprime(QPrimeArgs a) {
                 double R[5], J[5][5], low[5];
                 const bool ex = S.exact[lane];
                 if (ex) exact_low_moments(a.vg, ps, S.Jm[lane], low);
-                const double res = assemble(S.M[lane], ps, a.gas, x, A, R, J, ex ? low : nullptr);
+                // the residual first; the Jacobian only if an update may follow
+                const double res = assemble(S.M[lane], ps, a.gas, x, A, R, nullptr, ex ? low : nullptr);
+                if (!(res <= tol)) assemble(S.M[lane], ps, a.gas, x, A, R, J, ex ? low : nullptr);
                 S.res[lane] = res;
                 int it = S.it[lane];
                 act = true;
