@@ -158,6 +158,23 @@ def qprime_flops_per_dof_eval(n1):
     return 12.0 + (70.0 + 30.0 + 9.0) / n1
 
 
+def max_over_ranks(x, world, device=None):
+    """The largest x over the ranks (the slowest rank's time; x itself on one
+    rank).  Works with any torch.distributed backend (gloo needs device=None)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, dof, steps, ms):
+    """DOF-updates/s per RK stage of the whole job: every rank advances its own
+    replica (weak scaling), 3 stages per step, over the slowest rank's time."""
+    return world * dof * 3 * steps / (ms * 1e-3)
+
+
 def run_ours(args, rank, world, dev):
     import torch
     from paper_2312_06567_gb300 import bgk
@@ -248,10 +265,7 @@ def run_ours(args, rank, world, dev):
         prof = s.profile_read()
         s.profile(False)
         s.stats()
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, world, dev)
         # e2e: host pinned state in, one step, state out, through the C-ABI
         e2e = None
         if args.e2e_steps > 0 and form == headline:
@@ -269,9 +283,9 @@ def run_ours(args, rank, world, dev):
                 s.step(dt, 1)
                 s.get_state(host)
             torch.cuda.synchronize()
-            e2e_s = time.perf_counter() - t0
+            e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
             nbytes = host.numel() * host.element_size()
-            e2e = {"value": world * wl.dof * 3 * args.e2e_steps / e2e_s, "unit": UNIT,
+            e2e = {"value": job_throughput(world, wl.dof, args.e2e_steps, 1e3 * e2e_s), "unit": UNIT,
                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
             del host
         newton = dict(mean_iters=mean_it, max_iters=max_it, max_residual=res)
@@ -394,7 +408,7 @@ def main():
     peaks["hbm_gbs"] = _measured_hbm()
     r = results[main_form]
     ms_per_step = r["ms"] / args.steps
-    value = world * wl.dof * 3 * args.steps / (r["ms"] * 1e-3)
+    value = job_throughput(world, wl.dof, args.steps, r["ms"])
     launches = sum(v[1] for v in r["prof"].values()) * args.steps     # the profiled step x timed steps
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -426,7 +440,7 @@ def main():
     line["roofline_kernels"] = rl
     for form, rr in results.items():
         if form != main_form:
-            line[form] = {"value": world * wl.dof * 3 * args.steps / (rr["ms"] * 1e-3),
+            line[form] = {"value": job_throughput(world, wl.dof, args.steps, rr["ms"]),
                           "ms_per_step": rr["ms"] / args.steps,
                           "kernels_ms_per_step": {k: v[0] for k, v in rr["prof"].items()},
                           "newton": rr["newton"], "e2e": rr["e2e"],
