@@ -60,10 +60,11 @@ typedef enum { BGK_FP64 = 0, BGK_MIXED = 1 } bgk_precision;
 
 /* Uniform hexahedral box mesh and FR order (section "Numerical method":
  * N_e elements, N_s = (p+1)^3 solution nodes each).  Axes with periodic[d]=0
- * are closed at both ends by weak Dirichlet faces (section "Implementation &
- * problem setup": farfield states enforced through the Riemann flux) whose
- * exterior state is the Maxwellian of bc_state[2d + (side>0)] =
- * (rho, U1, U2, U3, theta); G's exterior state is delta theta / 2 times it.
+ * are closed at both ends by weak faces (section "Implementation & problem
+ * setup": exterior states enforced through the Riemann flux): a Dirichlet
+ * face's exterior state is the Maxwellian of bc_state[2d + (side>0)] =
+ * (rho, U1, U2, U3, theta), G's delta theta / 2 times it; a specular face
+ * (face_type) reflects the particles.
  * Requirements: n[d] >= 1, hi[d] > lo[d], 1 <= order <= 4. */
 typedef struct {
     int n[3];
@@ -71,7 +72,14 @@ typedef struct {
     int periodic[3];
     int order;
     double bc_state[6][5];
+    int face_type[6];    /* per non-periodic face 2d + (side > 0): BGK_FACE_DIRICHLET (0, bc_state)
+                          * or BGK_FACE_SPECULAR (1: a symmetry plane; the exterior state at
+                          * velocity u is the element's own trace at u with its d-component
+                          * negated, so the velocity grid must be symmetric in axis d) */
 } bgk_mesh_desc;
+
+#define BGK_FACE_DIRICHLET 0
+#define BGK_FACE_SPECULAR 1
 
 /* Uniform Cartesian velocity grid with trapezoid weights (section
  * "Numerical method": discrete integration operator with strictly positive

@@ -13,8 +13,10 @@ solves with FR; its gradient is not spelled out): along each reference
 direction and line of nodes the corrected polynomial
     rho~(xi) = rho(xi) + (rho^I_L - rho_L) g_L(xi) + (rho^I_R - rho_R) g_R(xi)
 matches the common interface values rho^I at both ends, with the central
-common value rho^I = (rho^- + rho^+)/2 at interior faces and, at a Dirichlet
-face, the average with the face state's density; d/dx_d = (2/h_d) d/dxi_d.
+common value rho^I = (rho^- + rho^+)/2 at interior faces, at a Dirichlet
+face the average with the face state's density, and at a specular face the
+element's own trace (its mirror image has the same density);
+d/dx_d = (2/h_d) d/dxi_d.
 """
 import numpy as np
 
@@ -42,7 +44,9 @@ def macro_fields(problem, m):
             inner = nb >= 0
             outer[inner] = tr_other[nb[inner]]
             if np.any(~inner):
-                outer[~inner] = problem.dirichlet[(d, side)][0]
+                # a specular face mirrors the element: its own trace is the exterior density
+                outer[~inner] = (tr_own[~inner] if (d, side) in problem.specular
+                                 else problem.dirichlet[(d, side)][0])
             common = 0.5 * (tr_own + outer)
             drl = drl + (common - tr_own)[..., None] * dg
         grad[..., d] = np.moveaxis((2.0 / mesh.h[d]) * drl, -1, ax)

@@ -21,7 +21,11 @@ scales d/dx_d = (2/h_d) d/dxi_d, and R(f) = -div F + S.
 Boundary conditions (section "Implementation & problem setup") are weak: a
 boundary face sees an exterior state f^+.  A Dirichlet face's exterior state
 is the Maxwellian of a prescribed (rho, U, theta) (for G: delta theta/2
-times it), the same at every flux node of the face.
+times it), the same at every flux node of the face.  A specular (symmetry)
+face reflects the particles: its exterior state at velocity u is the
+element's own trace at the mirrored velocity u - 2 (u.n) n, i.e. with the
+face's normal component negated (the velocity grid must be symmetric in that
+axis so the mirrored velocity is a node).
 
 Time integration: the paper only says "explicit"; the stage is the
 Shu--Osher three-stage SSP Runge--Kutta scheme,
@@ -42,20 +46,29 @@ class Problem:
     exterior: optional callable (d, side, fm) -> f^+ face traces replacing
     the Dirichlet state (used by the tests to prescribe exact data); fm is
     the interior trace array [C, Nu, Ne, q, q] of that side.
+    specular: the non-periodic faces (d, side) that reflect specularly.
     """
 
-    def __init__(self, mesh, p, vg, gas, dirichlet=None, exterior=None):
+    def __init__(self, mesh, p, vg, gas, dirichlet=None, exterior=None, specular=()):
         self.mesh, self.p, self.vg, self.gas = mesh, p, vg, gas
         self.fr = FR1D(p)
         self.q = p + 1
         self.Ns = self.q ** 3
         self.dirichlet = dict(dirichlet or {})
         self.exterior = exterior
+        self.specular = set(specular)
         for d in range(3):
             if not mesh.periodic[d] and exterior is None:
                 for side in (-1, 1):
-                    if (d, side) not in self.dirichlet:
-                        raise ValueError("missing Dirichlet state for face (%d, %d)" % (d, side))
+                    if (d, side) not in self.dirichlet and (d, side) not in self.specular:
+                        raise ValueError("missing boundary state for face (%d, %d)" % (d, side))
+        self.mirror = {}
+        for d, side in self.specular:
+            if not np.isclose(vg.lo[d], -vg.hi[d]):
+                raise ValueError("specular face needs a velocity grid symmetric in axis %d" % d)
+            j = vg.index3()
+            j[d] = vg.n[d] - 1 - j[d]
+            self.mirror[d] = j[0] + vg.n[0] * (j[1] + vg.n[1] * j[2])
         self.nbr = {(d, s): mesh.neighbours(d, s) for d in range(3) for s in (-1, 1)}
 
     @property
@@ -95,6 +108,9 @@ class Problem:
                     if self.exterior is not None:
                         ext = self.exterior(d, side, fm)
                         fp[:, :, ~inner] = ext[:, :, ~inner]
+                    elif (d, side) in self.specular:
+                        # the element's own trace on this face at the mirrored velocity
+                        fp[:, :, ~inner] = fm[:, self.mirror[d]][:, :, ~inner]
                     else:
                         st = self._dirichlet_state(d, side)        # [C, Nu]
                         fp[:, :, ~inner] = st[:, :, None, None, None]
@@ -210,4 +226,5 @@ def problem_from_workload(wl, exterior=None):
     vg = VelocityGrid(wl.vel_n, wl.vel_lo, wl.vel_hi)
     gas = bgk.Gas(delta=wl.delta, Pr=wl.Pr, mu_ref=wl.mu_ref, theta_ref=wl.theta_ref,
                   theta_S=wl.theta_S)
-    return Problem(mesh, wl.p, vg, gas, dirichlet=wl.dirichlet, exterior=exterior)
+    return Problem(mesh, wl.p, vg, gas, dirichlet=wl.dirichlet, exterior=exterior,
+                   specular=getattr(wl, "specular", ()))

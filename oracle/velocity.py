@@ -38,6 +38,11 @@ class VelocityGrid:
             if self.w.shape != (self.size,) or np.any(self.w <= 0):
                 raise ValueError("weights must be strictly positive, one per node")
 
+    def index3(self):
+        """[k1, k2, k3] index arrays of every node k = k1 + n1 (k2 + n2 k3)."""
+        k = np.arange(self.size)
+        return [k % self.n[0], (k // self.n[0]) % self.n[1], k // (self.n[0] * self.n[1])]
+
     @property
     def size(self):
         return self.n[0] * self.n[1] * self.n[2]

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "libbgk.so")
 
 BGK_OK, BGK_EINVAL, BGK_ENOMEM, BGK_ECUDA, BGK_ENOCONV, BGK_ETIMEOUT, BGK_ENOTSUP = range(7)
 BGK_FP64, BGK_MIXED = 0, 1
+BGK_FACE_DIRICHLET, BGK_FACE_SPECULAR = 0, 1
 STATUS_NAMES = {0: "BGK_OK", 1: "BGK_EINVAL", 2: "BGK_ENOMEM", 3: "BGK_ECUDA",
                 4: "BGK_ENOCONV", 5: "BGK_ETIMEOUT", 6: "BGK_ENOTSUP"}
 
@@ -23,7 +24,8 @@ c_int, c_double, c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
 
 class MeshDesc(ctypes.Structure):
     _fields_ = [("n", c_int * 3), ("lo", c_double * 3), ("hi", c_double * 3),
-                ("periodic", c_int * 3), ("order", c_int), ("bc_state", (c_double * 5) * 6)]
+                ("periodic", c_int * 3), ("order", c_int), ("bc_state", (c_double * 5) * 6),
+                ("face_type", c_int * 6)]
 
 
 class VGridDesc(ctypes.Structure):
@@ -145,6 +147,8 @@ def descriptors(wl):
     for (d, side), (rho, U, theta) in wl.dirichlet.items():
         row = m.bc_state[2 * d + (1 if side > 0 else 0)]
         row[0], row[1], row[2], row[3], row[4] = rho, U[0], U[1], U[2], theta
+    for d, side in getattr(wl, "specular", ()):
+        m.face_type[2 * d + (1 if side > 0 else 0)] = BGK_FACE_SPECULAR
     v = VGridDesc()
     for d in range(3):
         v.n[d], v.lo[d], v.hi[d] = wl.vel_n[d], wl.vel_lo[d], wl.vel_hi[d]

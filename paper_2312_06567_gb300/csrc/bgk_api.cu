@@ -389,6 +389,7 @@ bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
     for (int d = 0; d < 3; ++d)
         if (!mesh->periodic[d])
             for (int s = 0; s < 2; ++s) {
+                if (mesh->face_type[2 * d + s] == BGK_FACE_SPECULAR) continue;
                 const double *b = mesh->bc_state[2 * d + s];
                 if (!(b[0] > 0.0) || !(b[4] > 0.0)) return bad("Dirichlet state needs rho, theta > 0");
             }
@@ -396,6 +397,16 @@ bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
     const long long Nu = (long long)vg->n[0] * vg->n[1] * vg->n[2];
     const long long Ns = (long long)(mesh->order + 1) * (mesh->order + 1) * (mesh->order + 1);
     if (Ne * Ns > (1ll << 30) || Nu > (1ll << 30)) return bad("problem too large");
+    for (int f = 0; f < 6; ++f) {
+        const int d = f / 2;
+        if (mesh->face_type[f] != BGK_FACE_DIRICHLET && mesh->face_type[f] != BGK_FACE_SPECULAR)
+            return bad("face_type must be BGK_FACE_DIRICHLET or BGK_FACE_SPECULAR");
+        if (mesh->face_type[f] == BGK_FACE_SPECULAR) {
+            if (mesh->periodic[d]) return bad("a specular face must be non-periodic");
+            if (std::fabs(vg->lo[d] + vg->hi[d]) > 1e-12 * (std::fabs(vg->lo[d]) + std::fabs(vg->hi[d])))
+                return bad("a specular face needs a velocity grid symmetric in its axis");
+        }
+    }
 
     ctx->p = mesh->order; ctx->q = mesh->order + 1; ctx->Ns = (int)Ns; ctx->Ne = (int)Ne;
     ctx->Nu = (int)Nu; ctx->C = gas->delta > 0.0 ? 2 : 1; ctx->P = (int)(Ne * Ns);
@@ -418,6 +429,8 @@ bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
         ctx->mesh.two_over_h[d] = 2.0 * mesh->n[d] / (mesh->hi[d] - mesh->lo[d]);
     }
     ctx->mesh.Ne = ctx->Ne; ctx->mesh.Ns = ctx->Ns;
+    for (int f = 0; f < 6; ++f)
+        ctx->mesh.specular[f] = !mesh->periodic[f / 2] && mesh->face_type[f] == BGK_FACE_SPECULAR;
     ctx->jac = 1.0;
     for (int d = 0; d < 3; ++d) {
         ctx->jac *= 0.5 * (mesh->hi[d] - mesh->lo[d]) / mesh->n[d];
@@ -452,7 +465,7 @@ bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
     // Dirichlet exterior states per face and velocity
     std::vector<double> bcv((size_t)6 * ctx->C * Nu, 0.0);
     for (int face = 0; face < 6; ++face) {
-        if (mesh->periodic[face / 2]) continue;
+        if (mesh->periodic[face / 2] || ctx->mesh.specular[face]) continue;
         const double *st = mesh->bc_state[face];
         for (int k = 0; k < Nu; ++k) {
             const double *v = &ctx->vtab_h[(size_t)k * BGK_VTAB];

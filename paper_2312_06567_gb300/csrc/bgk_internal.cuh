@@ -50,6 +50,7 @@ struct FROps {
 struct MeshInfo {
     int n[3];
     int periodic[3];
+    int specular[6];                    // face 2d + side reflects specularly
     double two_over_h[3];
     int Ne, Ns;
 };
@@ -63,6 +64,14 @@ struct VelGrid {
 struct GasInfo {
     double delta, Pr, mu_ref, theta_ref, theta_S, gamma;
 };
+
+// Velocity node k with its index on axis d mirrored (j_d -> n_d - 1 - j_d):
+// the reflection u_d -> -u_d on a grid symmetric in axis d.
+__device__ __forceinline__ int mirror_velocity(int k, int d, const int n[3]) {
+    const int j1 = k % n[0], j2 = (k / n[0]) % n[1], j3 = k / (n[0] * n[1]);
+    const int m1 = d == 0 ? n[0] - 1 - j1 : j1, m2 = d == 1 ? n[1] - 1 - j2 : j2, m3 = d == 2 ? n[2] - 1 - j3 : j3;
+    return m1 + n[0] * (m2 + n[1] * m3);
+}
 
 // FP32 equilibrium exactly as the mixed-form stage evaluates it:
 // g32(u) = E0 * exp2(L), L = -log2(e)/2 c^T A c, c = u - V, all in FP32 with

@@ -166,6 +166,15 @@ __global__ void __launch_bounds__(256) k_stage_f32(StageArgs<float> a) {
                             dn = sdlam[side] * fi;
 #pragma unroll
                             for (int j = 0; j < Q; ++j) dn = fmaf(slam[side][j], __ldg(nb + j * stride[d]) - fi, dn);
+                        } else if (a.mesh.specular[2 * d + side]) {
+                            // the element's own outflow trace through this face at the
+                            // mirrored velocity, with the weights of that outflow, so the
+                            // reflected inflow telescopes against it exactly
+                            const float *mr = a.f_s + ((size_t)c * a.Nu + mirror_velocity(k, d, a.vg.n)) * slab +
+                                              (size_t)e * NS + base[d];
+                            dn = sdlam[1 - side] * fi;
+#pragma unroll
+                            for (int j = 0; j < Q; ++j) dn = fmaf(slam[1 - side][j], __ldg(mr + j * stride[d]) - fi, dn);
                         } else {
                             dn = (float)__ldg(a.bcval + ((size_t)(2 * d + side) * C + c) * a.Nu + k) - fi;
                         }
@@ -526,8 +535,15 @@ static cudaError_t stage32_tma(const StageArgs<float> &a, int n_vblk, int depth,
 
 static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
+static bool any_specular(const MeshInfo &m) {
+    for (int f = 0; f < 6; ++f)
+        if (m.specular[f]) return true;
+    return false;
+}
+
 bool stage_f32_tma_supported(const StageArgs<float> &a, int C, int depth) {
     if (a.fr.q != 2 && a.fr.q != 4) return false;          // element slabs of whole 16-byte units
+    if (any_specular(a.mesh)) return false;                 // reflected traces are not staged
     if (depth < 2 || depth > BGK_MAX_DEPTH) return false;
     if (!aligned16(a.f_s) || (a.a32 != 0.f && !aligned16(a.f_n))) return false;
     const size_t smem = a.fr.q == 2 ? (C == 1 ? tma_smem<2, 1>(depth) : tma_smem<2, 2>(depth))

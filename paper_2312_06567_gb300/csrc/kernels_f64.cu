@@ -196,6 +196,12 @@ __global__ void __launch_bounds__(256) k_stage_f64(StageArgs<double> a) {
                             const double *nb = fs + (size_t)en * NS + base[d];
 #pragma unroll
                             for (int j = 0; j < Q; ++j) fp = fma(sl[side][j], __ldg(nb + j * stride[d]), fp);
+                        } else if (a.mesh.specular[2 * d + side]) {
+                            // the element's own trace on this face at the mirrored velocity
+                            const double *mr = a.f_s + ((size_t)c * a.Nu + mirror_velocity(k, d, a.vg.n)) * slab +
+                                               (size_t)e * NS + base[d];
+#pragma unroll
+                            for (int j = 0; j < Q; ++j) fp = fma(sl[1 - side][j], __ldg(mr + j * stride[d]), fp);
                         } else {
                             fp = __ldg(a.bcval + ((size_t)(2 * d + side) * C + c) * a.Nu + k);
                         }

@@ -6,7 +6,8 @@
 // of the FR-corrected density polynomial along each reference direction:
 // the nodal derivative plus the correction-function derivatives times the
 // differences between the central common interface value (at a Dirichlet
-// face, the average with the face state's density) and the element's trace.
+// face, the average with the face state's density; at a specular face the
+// element's own trace) and the element's trace.
 // FP64; one thread per point.
 #include "bgk_internal.cuh"
 
@@ -59,13 +60,13 @@ __global__ void k_macro(const double *mom, double *out, int P, MeshInfo mesh, FR
             outL = 0.0;
             for (int j = 0; j < q; ++j) outL = fma(fr.lp[j], mom[((size_t)eL * NS + base + j * stride[d]) * BGK_NMOM], outL);
         } else {
-            outL = face_lo[d];
+            outL = mesh.specular[2 * d] ? trL : face_lo[d];        // a specular face mirrors the element
         }
         if (eR >= 0) {
             outR = 0.0;
             for (int j = 0; j < q; ++j) outR = fma(fr.lm[j], mom[((size_t)eR * NS + base + j * stride[d]) * BGK_NMOM], outR);
         } else {
-            outR = face_hi[d];
+            outR = mesh.specular[2 * d + 1] ? trR : face_hi[d];
         }
         const double cL = 0.5 * (trL + outL), cR = 0.5 * (trR + outR);
         der += (cL - trL) * fr.dgL[i] + (cR - trR) * fr.dgR[i];

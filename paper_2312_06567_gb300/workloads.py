@@ -61,6 +61,7 @@ class Workload:
     steps: int
     init: object = None                     # x[..., 3] -> (rho, U[..., 3], theta)
     dirichlet: dict = field(default_factory=dict)   # {(d, side): (rho, U(3), theta)}
+    specular: tuple = ()                    # ((d, side), ...) specular (symmetry) faces
 
     @property
     def n_elem(self):

@@ -43,9 +43,9 @@ def test_descriptor_layout_matches_header(tmp_path):
 #include <stddef.h>
 #include "bgk.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(bgk_mesh_desc), offsetof(bgk_mesh_desc, lo),
+  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(bgk_mesh_desc), offsetof(bgk_mesh_desc, lo),
          offsetof(bgk_mesh_desc, hi), offsetof(bgk_mesh_desc, periodic),
-         offsetof(bgk_mesh_desc, order), offsetof(bgk_mesh_desc, bc_state));
+         offsetof(bgk_mesh_desc, order), offsetof(bgk_mesh_desc, bc_state), offsetof(bgk_mesh_desc, face_type));
   printf("%zu %zu %zu\\n", sizeof(bgk_vgrid_desc), offsetof(bgk_vgrid_desc, lo),
          offsetof(bgk_vgrid_desc, hi));
   printf("%zu %zu\\n", sizeof(bgk_gas_desc), offsetof(bgk_gas_desc, theta_S));
@@ -57,7 +57,7 @@ int main(void) {
     out = [list(map(int, l.split())) for l in subprocess.check_output([str(exe)]).decode().splitlines()]
     M = bgk.MeshDesc
     assert out[0] == [ctypes.sizeof(M), M.lo.offset, M.hi.offset, M.periodic.offset,
-                      M.order.offset, M.bc_state.offset]
+                      M.order.offset, M.bc_state.offset, M.face_type.offset]
     V = bgk.VGridDesc
     assert out[1] == [ctypes.sizeof(V), V.lo.offset, V.hi.offset]
     assert out[2] == [ctypes.sizeof(bgk.GasDesc), bgk.GasDesc.theta_S.offset]
@@ -72,7 +72,11 @@ def test_invalid_descriptors_rejected_on_the_host(libbgk):
            base.replace(delta=-1.0), base.replace(Pr=0.5), base.replace(mesh_n=(0, 4, 4)),
            base.replace(mesh_hi=(0.0, 1, 1)),
            W.normal_shock_tube().replace(dirichlet={(0, -1): (0.0, (1, 0, 0), 1.0),
-                                                    (0, 1): (1.0, (1, 0, 0), 1.0)})]
+                                                    (0, 1): (1.0, (1, 0, 0), 1.0)}),
+           # specular faces: on a periodic axis, or with a velocity grid not symmetric in the axis
+           base.replace(specular=((0, -1),)),
+           W.normal_shock_tube().replace(dirichlet={}, specular=((0, -1), (0, 1)), vel_lo=(-9.0, -8.0, -8.0),
+                                         vel_hi=(11.0, 8.0, 8.0))]
     for wl in bad:
         with pytest.raises(bgk.BGKError) as ei:
             bgk.Solver(wl)

@@ -1,0 +1,128 @@
+"""Specular (symmetry) faces on the GPU against the oracle: residual and one
+SSP-RK3 step (FP64 within 1e-12, mixed within 1e-5), the mixed residual's
+totals of mass and energy (reflected inflow telescoping against the mirrored
+outflow), the diagnostics, and the pipelined stage kernels declining such
+meshes (their copy ring does not stage mirrored traces)."""
+import numpy as np
+import pytest
+
+from oracle import bgk as obgk
+from oracle import diagnostics as odiag
+from oracle import stage as ostage
+from paper_2312_06567_gb300 import workloads as W
+
+from test_gpu_parity import moment_err, rhs_err, slab_err
+
+
+def _rhs_err_src(r_gpu, r_ora, f, wl, S, mirror):
+    """Residual error over max(|f(u)|, |f(u mirrored)|) times the advection
+    rate plus max|S|: at a reflecting face the inflow at u is the outflow at
+    the mirrored velocity, which in the velocity tails can exceed f(u) by
+    orders of magnitude; and the FP32 equilibrium's few-ulp error scales with
+    g, which in the tails of an anisotropic state exceeds f likewise."""
+    C, Nu = f.shape[:2]
+    u = W.velocity_nodes(wl)
+    h = np.array([(wl.mesh_hi[d] - wl.mesh_lo[d]) / wl.mesh_n[d] for d in range(3)])
+    adv = np.sum(2 * np.abs(u) / h, axis=1)
+    fmax = np.abs(f).reshape(C, Nu, -1).max(axis=2)
+    fmax = np.maximum(fmax, fmax[:, mirror])
+    scale = fmax * adv[None, :] + np.abs(S).reshape(C, Nu, -1).max(axis=2)
+    d = np.abs(r_gpu - r_ora).reshape(C, Nu, -1).max(axis=2)
+    return float(np.max(d / np.maximum(scale, 1e-300)))
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib(libbgk, cuda_device):
+    from paper_2312_06567_gb300 import bgk
+    return bgk
+
+
+def _case(p=2, mesh_n=(3, 2, 1), delta=2.0):
+    base = W.reduced(W.normal_shock_tube(mach=3.0), mesh_n=mesh_n, vel_n=(12, 9, 8)).replace(
+        p=p, vel_lo=(-9.0, -8.0, -8.0), vel_hi=(9.0, 8.0, 8.0), mesh_lo=(0.0, 0.0, 0.0), mesh_hi=(3.0, 1.0, 1.0),
+        delta=delta)
+    return base.replace(periodic=(False, True, True), dirichlet={}, specular=((0, -1), (0, 1)))
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_specular_rhs_and_step_match_oracle(lib, p):
+    wl = _case(p=p)
+    pb = ostage.problem_from_workload(wl)
+    f = W.random_anisotropic_state(wl, seed=41)
+    r_ora, info = pb.rhs(f)
+    f1_ora, _ = pb.step(f, wl.dt())
+    with lib.Solver(wl, lib.BGK_FP64) as s:
+        s.set_state(f)
+        r = s.rhs(f)
+        assert s.step(wl.dt(), 1) == lib.BGK_OK
+        f1 = s.get_state()
+    assert rhs_err(r, r_ora, f, wl, info["tau"].min()) <= 1e-12
+    assert slab_err(f1, f1_ora) <= 1e-12
+    f32 = f.astype(np.float32)
+    fd = f32.astype(np.float64)
+    r_ora32, info32 = pb.rhs(fd)
+    f1_ora32, _ = pb.step(fd, wl.dt())
+    # element by element with the FP64 Newton engine (isolates the FP32 FR
+    # arithmetic at the reflecting faces from the FP32 engine's 1e-6 stopping
+    # tolerance, which moves g's tails by more than 1e-5); moments (the mixed
+    # form's contract) with the default FP32-sum engine
+    S32 = r_ora32 + pb.divergence(fd)
+    m1_ora = obgk.raw_moments(f1_ora32[0].reshape(wl.n_vel, -1), f1_ora32[1].reshape(wl.n_vel, -1), pb.vg)
+    for fp32_sums in (False, True):
+        with lib.Solver(wl, lib.BGK_MIXED) as s:
+            for v in ("async", "line", "line_wide", "half"):
+                with pytest.raises(RuntimeError):
+                    s.set_stage_kernel(v, 4)
+            s.set_qprime_engine(fp32_sums)
+            s.set_state(f32)
+            r = s.rhs(f32).astype(np.float64)
+            assert s.step(wl.dt(), 1) == lib.BGK_OK
+            f1 = s.get_state().astype(np.float64)
+            m1 = s.moments()
+        if not fp32_sums:
+            assert _rhs_err_src(r, r_ora32, fd, wl, S32, pb.mirror[0]) <= 1e-5
+            assert slab_err(f1, f1_ora32) <= 1e-5
+        assert moment_err(m1, m1_ora, wl.delta) <= 1e-5
+
+
+@pytest.mark.parametrize("form", ["fp64", "mixed"])
+def test_specular_residual_conserves_mass_and_energy(lib, form):
+    """Totals of mass sum w F and energy sum w (|u|^2/2 F + G) under the
+    residual with reflecting walls: 1e-12 of the totals per time step in the
+    FP64 form; 1e-9 in the mixed form, where the inflow through a reflecting
+    face at velocity u is the element's outflow at the mirrored velocity --
+    in the velocity tails orders of magnitude larger than f(u) -- so one FP32
+    rounding of that size per face point is not compensated (interior faces
+    exchange data of the same velocity and stay at ~1e-14)."""
+    wl = _case(p=3, mesh_n=(4, 2, 2))
+    pb = ostage.problem_from_workload(wl)
+    Wq = np.einsum("i,j,k->ijk", pb.fr.wq, pb.fr.wq, pb.fr.wq).reshape(-1)
+    f = W.random_anisotropic_state(wl, seed=42)
+    if form == "mixed":
+        f = f.astype(np.float32)
+    with lib.Solver(wl, lib.BGK_MIXED if form == "mixed" else lib.BGK_FP64) as s:
+        s.set_state(f)
+        r = s.rhs(f).astype(np.float64)
+    w, u = pb.vg.w, pb.vg.u
+    fd = f.astype(np.float64)
+    e_f = 0.5 * np.sum(u * u, axis=1)
+    bar = 1e-9 if form == "mixed" else 1e-12
+    for psis in ((np.ones(len(w)), None), (e_f, np.ones(len(w)))):
+        rate = sum(np.einsum("k,kes,s->", w * ps, r[c], Wq) for c, ps in enumerate(psis) if ps is not None)
+        tot = sum(np.einsum("k,kes,s->", w * np.abs(ps), fd[c], Wq) for c, ps in enumerate(psis) if ps is not None)
+        assert abs(rate) * wl.dt() <= bar * tot
+
+
+def test_specular_macro_diagnostics_match_oracle(lib):
+    wl = _case(p=2)
+    pb = ostage.problem_from_workload(wl)
+    f = W.random_anisotropic_state(wl, seed=43)
+    with lib.Solver(wl, lib.BGK_FP64) as s:
+        s.set_state(f)
+        out = s.macro()
+    m = obgk.raw_moments(f[0].reshape(wl.n_vel, -1), f[1].reshape(wl.n_vel, -1), pb.vg)
+    ora = odiag.macro_fields(pb, m)
+    sc = np.maximum(np.abs(ora).max(axis=0), 1e-300)
+    assert float(np.max(np.abs(out - ora) / sc[None, :])) <= 1e-12

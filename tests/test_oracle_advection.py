@@ -205,3 +205,55 @@ def test_element_residual_from_its_block_equals_the_whole_mesh():
         Re = ost.element_residual(pb.mesh.h, wl.p, pb.vg, pb.gas, f[:, :, idx, :])
         scale = np.abs(R[:, :, e, :]).max()
         assert np.max(np.abs(Re - R[:, :, e, :])) <= 1e-13 * scale
+
+
+def _mirror_case(p=2, with_g=True):
+    """A box [0, L] x [0,1]^2 with specular faces at x = 0 and x = L, and the
+    periodic doubled box [-L, L] holding the mirror image of the data."""
+    from oracle import stage as ost
+    from paper_2312_06567_gb300 import workloads as W
+    base = W.reduced(W.normal_shock_tube(mach=3.0), mesh_n=(3, 2, 1), vel_n=(8, 7, 6)).replace(
+        p=p, vel_lo=(-9.0, -8.0, -8.0), vel_hi=(9.0, 8.0, 8.0), mesh_lo=(0.0, 0.0, 0.0), mesh_hi=(3.0, 1.0, 1.0),
+        delta=2.0 if with_g else 0.0)
+    half = base.replace(periodic=(False, True, True), dirichlet={}, specular=((0, -1), (0, 1)))
+    full = base.replace(mesh_n=(6, 2, 1), mesh_lo=(-3.0, 0.0, 0.0), mesh_hi=(3.0, 1.0, 1.0),
+                        periodic=(True, True, True), dirichlet={}, specular=())
+    return ost.problem_from_workload(half), ost.problem_from_workload(full), half
+
+
+def test_specular_faces_equal_the_mirrored_periodic_domain():
+    """FR with specular walls at x = 0 and x = L on [0, L] gives exactly the
+    residual that the periodic domain [-L, L] gives on [0, L] when its data
+    are the mirror image f(-x, R u) of the half-domain data: the exterior
+    state of the reflecting face is what the mirrored neighbour presents."""
+    from paper_2312_06567_gb300 import workloads as W
+    ph, pf, half = _mirror_case()
+    f = W.random_anisotropic_state(half, seed=31)                       # [C, Nu, 6 elems, Ns]
+    C, Nu, Ne, Ns = f.shape
+    q = half.p + 1
+    mir = ph.mirror[0]
+    # element e = e1 + 3 e2 (n = (3, 2, 1)); the full box has e1' = e1 + 3 on [0, L] and the
+    # mirror image e1' = 2 - e1 on [-L, 0], nodes mirrored along x (i1 -> q - 1 - i1)
+    g = np.empty((C, Nu, 12, Ns))
+    f6 = f.reshape(C, Nu, 2, 3, q, q, q)                             # [c, k, e2, e1, i3, i2, i1]
+    full = np.empty((C, Nu, 2, 6, q, q, q))
+    full[:, :, :, 3:] = f6
+    full[:, :, :, :3] = f6[:, mir][:, :, :, ::-1, :, :, ::-1]
+    g = full.reshape(C, Nu, 12, Ns)
+    Rh, _ = ph.rhs(f)
+    Rf, _ = pf.rhs(g)
+    Rf6 = Rf.reshape(C, Nu, 2, 6, Ns)[:, :, :, 3:].reshape(C, Nu, 6, Ns)
+    assert np.max(np.abs(Rh - Rf6)) <= 1e-12 * np.max(np.abs(Rh))
+
+
+def test_specular_walls_conserve_mass_energy_and_tangential_momentum():
+    from paper_2312_06567_gb300 import workloads as W
+    ph, _, half = _mirror_case()
+    f = W.random_anisotropic_state(half, seed=32)
+    t0 = ph.totals(f)
+    f1, _ = ph.step(f, half.dt())
+    t1 = ph.totals(f1)
+    scale = np.abs(t0).max()
+    for i in (0, 2, 3, 4):                                   # mass, tangential momenta, energy
+        assert abs(t1[i] - t0[i]) <= 1e-13 * scale, i
+    assert abs(t1[1] - t0[1]) > 1e-10 * scale                # the walls push on the normal momentum
