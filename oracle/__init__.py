@@ -22,6 +22,8 @@ dual      A second, independent route to the Pr=1 discrete Maxwellian
           (convex dual in the exponential parametrisation) used only as a pin.
 stage     FR residual with upwind flux and correction lift, SSP-RK3,
           diagnostics (totals, entropy, L2).
+curved    FR on curvilinear hexahedra (GLL curl-form metric terms, transformed
+          flux), diffuse walls and collapsed faces.
 mlp       FP64 forward/backward of the small SiLU network used for the
           learned Q' initial guess.
 """

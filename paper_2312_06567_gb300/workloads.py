@@ -62,6 +62,13 @@ class Workload:
     init: object = None                     # x[..., 3] -> (rho, U[..., 3], theta)
     dirichlet: dict = field(default_factory=dict)   # {(d, side): (rho, U(3), theta)}
     specular: tuple = ()                    # ((d, side), ...) specular (symmetry) faces
+    # curvilinear meshes: mapping(t[..., 3]) -> x[..., 3] of the normalised lattice
+    # coordinates t in [0, 1]^3 (element e1 spans t1 in [e1/n1, (e1+1)/n1]); None = the
+    # uniform box mesh_lo..mesh_hi
+    mapping: object = None
+    diffuse: dict = field(default_factory=dict)     # {(d, side): (U_w(3), theta_w)} diffuse walls
+    closed: tuple = ()                      # ((d, side), ...) collapsed faces (no flux)
+    h_min_override: float = None            # smallest node spacing of a curvilinear mesh
 
     @property
     def n_elem(self):
@@ -84,6 +91,8 @@ class Workload:
         return self.n_elem * self.n_sol * self.n_vel
 
     def h_min(self):
+        if self.h_min_override is not None:
+            return self.h_min_override
         return min((self.mesh_hi[d] - self.mesh_lo[d]) / self.mesh_n[d] for d in range(3))
 
     def u_max(self):
@@ -164,11 +173,95 @@ def normal_shock_tube(mach=8.0, width=2.0):
                     init=_shock_init(width, s1, s2), dirichlet=dirichlet)
 
 
+def _wavy(amp):
+    """Periodic warp of the unit cube: x = t + amp sin(2 pi t1) sin(2 pi t2) sin(2 pi t3)
+    on every coordinate (a smooth curvilinear mesh of the periodic unit box)."""
+    def mapping(t):
+        w = amp * np.sin(2 * np.pi * t[..., 0]) * np.sin(2 * np.pi * t[..., 1]) * np.sin(2 * np.pi * t[..., 2])
+        return t + w[..., None]
+    return mapping
+
+
+def wavy_periodic_box(p=2, n=(3, 3, 3), vel_n=(8, 8, 8), amp=0.05, Pr=1.0):
+    """Curvilinear periodic case: the unit cube warped by _wavy, p, n hex, velocities
+    on [-6,6]^3, monatomic, Kn=0.1, rho = 1 + 0.1 sin(2 pi x), U = 0, theta = 1."""
+    return Workload("wavy_periodic_box_%dx%dx%d_p%d" % (n + (p,)), tuple(n), (0, 0, 0), (1, 1, 1),
+                    (True, True, True), p, tuple(vel_n), (-6, -6, -6), (6, 6, 6),
+                    0.0, Pr, mu_from_knudsen(0.1), 1.0, THETA_S_RATIO, 0.1, 10,
+                    init=_init_sine_density, mapping=_wavy(amp),
+                    h_min_override=(1.0 - 8.0 * amp) / max(n))
+
+
+def _sphere_shell(r_in, r_out, ratio, n_r):
+    """Latitude--longitude shell: t1 -> radius (geometric stretch `ratio` per radial
+    element), t2 -> polar angle in [0, pi] (poles on the z axis), t3 -> azimuth."""
+    def mapping(t):
+        tr = t[..., 0] * n_r
+        r = r_in + (r_out - r_in) * (ratio ** tr - 1.0) / (ratio ** n_r - 1.0)
+        th = np.pi * t[..., 1]
+        ph = 2.0 * np.pi * t[..., 2]
+        return np.stack([r * np.sin(th) * np.cos(ph), r * np.sin(th) * np.sin(ph), r * np.cos(th)], axis=-1)
+    return mapping
+
+
+def sphere_ogrid(n=(12, 24, 24), p=1, vel_n=(40, 40, 40), umax=35.0, mach=22.7, kn=8e-4,
+                 theta_w=0.1):
+    """Blunt-body case: latitude--longitude O-grid around a sphere of diameter 1
+    (r in [0.5, 4], radial stretch 1.15 per element), polar axis z perpendicular to
+    the freestream along +x.  Diatomic delta=2, ES-BGK Pr=0.72, Sutherland, mu_ref
+    from Kn_D; freestream Maxwellian at M (gamma=1.4, theta=1); diffuse wall at
+    theta_w on the sphere, Dirichlet freestream at r=4, collapsed (no-flux) faces at
+    the poles, periodic azimuth."""
+    u_inf = mach * math.sqrt(1.4)
+    free = (1.0, (u_inf, 0.0, 0.0), 1.0)
+    mapping = _sphere_shell(0.5, 4.0, 1.15, n[0])
+
+    def init(x):
+        U = np.zeros(x.shape)
+        U[..., 0] = u_inf
+        return np.ones(x.shape[:-1]), U, np.ones(x.shape[:-1])
+    # node spacing bound: the azimuthal extent at the first Gauss node off the pole
+    xi0 = leggauss(p + 1)[0][0]
+    th0 = np.pi / n[1] * 0.5 * (1.0 + xi0)
+    dr0 = (4.0 - 0.5) * (1.15 - 1.0) / (1.15 ** n[0] - 1.0)
+    h_min = min(0.5 * math.sin(th0) * 2.0 * math.pi / n[2], dr0) / (p + 1)
+    return Workload("sphere_ogrid_%dx%dx%d_p%d_u%d_d2" % (n + (p, vel_n[0])), tuple(n), (0, 0, 0), (1, 1, 1),
+                    (False, False, True), p, tuple(vel_n), (-umax,) * 3, (umax,) * 3,
+                    2.0, 0.72, mu_from_knudsen(kn), 1.0, THETA_S_RATIO, 0.1, 500, init=init,
+                    dirichlet={(0, 1): free}, diffuse={(0, -1): ((0.0, 0.0, 0.0), theta_w)},
+                    closed=((1, -1), (1, 1)), mapping=mapping, h_min_override=h_min)
+
+
 # ---- sampled inputs --------------------------------------------------------
+def gll_nodes(q):
+    """Gauss--Lobatto--Legendre nodes on [-1, 1] (the endpoints and the roots of
+    P'_{q-1}), used to sample a mapping on element boundaries."""
+    if q == 2:
+        return np.array([-1.0, 1.0])
+    inner = np.sort(np.polynomial.legendre.Legendre.basis(q - 1).deriv().roots().real)
+    return np.concatenate([[-1.0], inner, [1.0]])
+
+
+def _lagrange_matrix(src, dst):
+    """L[i, j] = l_j(dst_i) for the Lagrange basis on the nodes src."""
+    L = np.ones((len(dst), len(src)))
+    for j in range(len(src)):
+        for m in range(len(src)):
+            if m != j:
+                L[:, j] *= (dst - src[m]) / (src[j] - src[m])
+    return L
+
+
 def node_positions(wl):
-    """Solution node coordinates x[Ne, Ns, 3] (numpy's Gauss--Legendre nodes)."""
+    """Solution node coordinates x[Ne, Ns, 3] (numpy's Gauss--Legendre nodes).
+    Curvilinear meshes: each element's mapping is the tensor interpolant of degree
+    p of wl.mapping sampled at the element's Gauss--Lobatto points (shared by
+    neighbouring elements, so the geometry is continuous), evaluated at the
+    Gauss--Legendre nodes."""
     q = wl.p + 1
     xi = leggauss(q)[0]
+    if wl.mapping is not None:
+        return _mapped_node_positions(wl, xi)
     i3, i2, i1 = np.meshgrid(np.arange(q), np.arange(q), np.arange(q), indexing="ij")
     loc = [xi[i1.ravel()], xi[i2.ravel()], xi[i3.ravel()]]
     n1, n2, n3 = wl.mesh_n
@@ -179,6 +272,22 @@ def node_positions(wl):
         h = (wl.mesh_hi[d] - wl.mesh_lo[d]) / wl.mesh_n[d]
         x[:, :, d] = wl.mesh_lo[d] + (c[d][:, None] + 0.5 * (loc[d][None, :] + 1.0)) * h
     return x
+
+
+def _mapped_node_positions(wl, xi):
+    q = wl.p + 1
+    eta = gll_nodes(q)
+    L = _lagrange_matrix(eta, xi)                              # [gl, gll]
+    n1, n2, n3 = wl.mesh_n
+    e = np.arange(wl.n_elem)
+    c = np.stack([e % n1, (e // n1) % n2, e // (n1 * n2)], axis=1).astype(np.float64)
+    nn = np.asarray(wl.mesh_n, dtype=np.float64)
+    g3, g2, g1 = np.meshgrid(eta, eta, eta, indexing="ij")     # [i3, i2, i1]
+    loc = np.stack([g1, g2, g3], axis=-1)                      # GLL points, [q, q, q, 3]
+    t = (c[:, None, None, None, :] + 0.5 * (loc[None] + 1.0)) / nn
+    X = wl.mapping(t)                                          # [Ne, q, q, q, 3] at GLL points
+    X = np.einsum("ai,bj,ck,eijkn->eabcn", L, L, L, X)         # at GL nodes, [e, i3, i2, i1]
+    return X.reshape(wl.n_elem, q ** 3, 3)
 
 
 def velocity_nodes(wl):
