@@ -58,28 +58,51 @@ typedef enum {
 
 typedef enum { BGK_FP64 = 0, BGK_MIXED = 1 } bgk_precision;
 
-/* Uniform hexahedral box mesh and FR order (section "Numerical method":
- * N_e elements, N_s = (p+1)^3 solution nodes each).  Axes with periodic[d]=0
- * are closed at both ends by weak faces (section "Implementation & problem
- * setup": exterior states enforced through the Riemann flux): a Dirichlet
- * face's exterior state is the Maxwellian of bc_state[2d + (side>0)] =
- * (rho, U1, U2, U3, theta), G's delta theta / 2 times it; a specular face
- * (face_type) reflects the particles.
- * Requirements: n[d] >= 1, hi[d] > lo[d], 1 <= order <= 4. */
+/* Hexahedral mesh of structured topology and FR order (section "Numerical
+ * method": N_e elements, N_s = (p+1)^3 solution nodes each).  Element
+ * e = e1 + n1 (e2 + n2 e3) has the face neighbours e +- 1, e +- n1,
+ * e +- n1 n2 (wrapping on periodic axes).  Axes with periodic[d]=0 are
+ * closed at both ends by weak faces (section "Implementation & problem
+ * setup": exterior states enforced through the Riemann flux), chosen per
+ * face 2d + (side > 0) by face_type:
+ *   BGK_FACE_DIRICHLET: the exterior state is the Maxwellian of
+ *     bc_state = (rho, U1, U2, U3, theta), G's delta theta / 2 times it;
+ *   BGK_FACE_SPECULAR: a symmetry plane; the exterior state at velocity u
+ *     is the element's own trace at u with its d-component negated (the
+ *     velocity grid must be symmetric in axis d; uniform box only);
+ *   BGK_FACE_DIFFUSE: a diffuse wall at bc_state = (unused, U_w1..3,
+ *     theta_w): at each flux node the particles entering the gas come from
+ *     rho_w M(u; U_w, theta_w) (G: delta theta_w / 2 times it), rho_w set so
+ *     that no mass crosses the node (a reading: the paper names the
+ *     condition only);
+ *   BGK_FACE_CLOSED: a collapsed face of zero area (the pole of a
+ *     latitude--longitude grid); no flux crosses it.
+ * Geometry: node_xyz = NULL gives the uniform box lo..hi (hi[d] > lo[d]);
+ * otherwise node_xyz[P][3] (host memory, P = N_e N_s, node s = i1 + (p+1)
+ * (i2 + (p+1) i3) at the Gauss--Legendre points) are the coordinates of the
+ * solution nodes, and each element's geometry is their interpolant of
+ * degree p.  The library then forms the metric terms S^d = J grad xi_d in
+ * the conservative curl form on the element's Gauss--Lobatto points and
+ * runs FR on the equation mapped to the reference cube (transformed flux
+ * (u . S^d) f, face vectors = the traces of S^d averaged over both sides):
+ * conservative, and free-stream preserving when the geometry is continuous
+ * across faces.  Diffuse and closed faces use the same (curvilinear) path
+ * on the uniform box.  Specular faces are not available on it (BGK_ENOTSUP).
+ * Requirements: n[d] >= 1, 1 <= order <= 4, J > 0 at every node. */
 typedef struct {
     int n[3];
     double lo[3], hi[3];
     int periodic[3];
     int order;
     double bc_state[6][5];
-    int face_type[6];    /* per non-periodic face 2d + (side > 0): BGK_FACE_DIRICHLET (0, bc_state)
-                          * or BGK_FACE_SPECULAR (1: a symmetry plane; the exterior state at
-                          * velocity u is the element's own trace at u with its d-component
-                          * negated, so the velocity grid must be symmetric in axis d) */
+    int face_type[6];           /* BGK_FACE_* per non-periodic face 2d + (side > 0) */
+    const double *node_xyz;     /* NULL, or [P][3] solution-node coordinates (borrowed) */
 } bgk_mesh_desc;
 
 #define BGK_FACE_DIRICHLET 0
 #define BGK_FACE_SPECULAR 1
+#define BGK_FACE_DIFFUSE 2
+#define BGK_FACE_CLOSED 3
 
 /* Uniform Cartesian velocity grid with trapezoid weights (section
  * "Numerical method": discrete integration operator with strictly positive
@@ -265,7 +288,8 @@ BGK_API bgk_status bgk_stats(bgk_ctx *ctx, double *mean_iters, int *max_iters, d
 #define BGK_K_QPRIME 1     /* moment reduction + Q' Newton solve        */
 #define BGK_K_STAGE 2      /* fused FR + source + RK + moment epilogue  */
 #define BGK_K_OTHER 3      /* initialisation and reductions             */
-#define BGK_NKINDS 4
+#define BGK_K_WALL 4       /* diffuse-wall densities of a stage's input  */
+#define BGK_NKINDS 5
 BGK_API bgk_status bgk_profile(bgk_ctx *ctx, int enable);
 BGK_API bgk_status bgk_profile_read(bgk_ctx *ctx, double ms[BGK_NKINDS], long long launches[BGK_NKINDS]);
 

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "libbgk.so")
 
 BGK_OK, BGK_EINVAL, BGK_ENOMEM, BGK_ECUDA, BGK_ENOCONV, BGK_ETIMEOUT, BGK_ENOTSUP = range(7)
 BGK_FP64, BGK_MIXED = 0, 1
-BGK_FACE_DIRICHLET, BGK_FACE_SPECULAR = 0, 1
+BGK_FACE_DIRICHLET, BGK_FACE_SPECULAR, BGK_FACE_DIFFUSE, BGK_FACE_CLOSED = 0, 1, 2, 3
 STATUS_NAMES = {0: "BGK_OK", 1: "BGK_EINVAL", 2: "BGK_ENOMEM", 3: "BGK_ECUDA",
                 4: "BGK_ENOCONV", 5: "BGK_ETIMEOUT", 6: "BGK_ENOTSUP"}
 
@@ -25,7 +25,7 @@ c_int, c_double, c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
 class MeshDesc(ctypes.Structure):
     _fields_ = [("n", c_int * 3), ("lo", c_double * 3), ("hi", c_double * 3),
                 ("periodic", c_int * 3), ("order", c_int), ("bc_state", (c_double * 5) * 6),
-                ("face_type", c_int * 6)]
+                ("face_type", c_int * 6), ("node_xyz", c_void_p)]
 
 
 class VGridDesc(ctypes.Structure):
@@ -79,7 +79,7 @@ SIGNATURES = {
     "bgk_last_error": (ctypes.c_char_p, [c_void_p]),
 }
 
-KERNEL_KINDS = ("moments", "qprime", "stage", "other")
+KERNEL_KINDS = ("moments", "qprime", "stage", "other", "wall")
 MLP_NPARAM, MLP_NNORM, MLP_LOG_STRIDE = 5125, 28, 14
 MLP_SHAPES = ((9, 64), (64,), (64, 64), (64,), (64, 5), (5,))
 PROBE_KINDS = {"fp64_fma": 0, "fp32_fma": 1, "fp64_exp": 2, "fp32_exp2": 3}
@@ -137,8 +137,10 @@ def _stream_handle(stream):
     return c_void_p(getattr(stream, "cuda_stream", stream))
 
 
-def descriptors(wl):
-    """(MeshDesc, VGridDesc, GasDesc) of a workload definition."""
+def descriptors(wl, node_xyz=None):
+    """(MeshDesc, VGridDesc, GasDesc) of a workload definition.  node_xyz: the
+    solution-node coordinates [Ne, Ns, 3] of a curvilinear mesh (float64,
+    C-contiguous; the caller keeps it alive while the descriptor is used)."""
     m = MeshDesc()
     for d in range(3):
         m.n[d], m.lo[d], m.hi[d] = wl.mesh_n[d], wl.mesh_lo[d], wl.mesh_hi[d]
@@ -149,6 +151,15 @@ def descriptors(wl):
         row[0], row[1], row[2], row[3], row[4] = rho, U[0], U[1], U[2], theta
     for d, side in getattr(wl, "specular", ()):
         m.face_type[2 * d + (1 if side > 0 else 0)] = BGK_FACE_SPECULAR
+    for (d, side), (U_w, theta_w) in getattr(wl, "diffuse", {}).items():
+        f = 2 * d + (1 if side > 0 else 0)
+        m.face_type[f] = BGK_FACE_DIFFUSE
+        row = m.bc_state[f]
+        row[0], row[1], row[2], row[3], row[4] = 1.0, U_w[0], U_w[1], U_w[2], theta_w
+    for d, side in getattr(wl, "closed", ()):
+        m.face_type[2 * d + (1 if side > 0 else 0)] = BGK_FACE_CLOSED
+    if node_xyz is not None:
+        m.node_xyz = node_xyz.ctypes.data
     v = VGridDesc()
     for d in range(3):
         v.n[d], v.lo[d], v.hi[d] = wl.vel_n[d], wl.vel_lo[d], wl.vel_hi[d]
@@ -176,7 +187,11 @@ class Solver:
         self.wl = wl
         self.precision = precision
         self._h = c_void_p()
-        m, v, g = descriptors(wl)
+        self._xyz = None
+        if getattr(wl, "mapping", None) is not None:
+            from . import workloads
+            self._xyz = np.ascontiguousarray(workloads.node_positions(wl), dtype=np.float64)
+        m, v, g = descriptors(wl, self._xyz)
         st = self.lib.bgk_create(ctypes.byref(self._h), ctypes.byref(m), ctypes.byref(v),
                                  ctypes.byref(g), precision, _stream_handle(stream))
         if st != BGK_OK:
@@ -392,8 +407,8 @@ class Solver:
 
     def profile_read(self):
         """{kind: (ms, launches)} since the last profile(True)."""
-        ms = (c_double * 4)()
-        n = (ctypes.c_longlong * 4)()
+        ms = (c_double * len(KERNEL_KINDS))()
+        n = (ctypes.c_longlong * len(KERNEL_KINDS))()
         self._check(self.lib.bgk_profile_read(self._h, ms, n))
         return {k: (ms[i], n[i]) for i, k in enumerate(KERNEL_KINDS)}
 

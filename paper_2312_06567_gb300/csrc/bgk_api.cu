@@ -25,6 +25,16 @@ struct bgk_ctx {
     double lo[3];                     // mesh box corner
     double bc[6][5];
     std::vector<double> vtab_h;       // [Nu][BGK_VTAB]
+    // curvilinear path (node coordinates given, or diffuse / closed faces)
+    bool curved;
+    std::vector<double> xyz_h;        // [P][3] node coordinates
+    std::vector<double> geo_h;        // [P][BGK_NGEO]
+    double *geo, *fvec;               // FP64 metric terms and face vectors
+    float *geo32, *fvec32;            // their FP32 copies (mixed form)
+    double *rho_w;                    // [Ne][6][q*q] diffuse-wall densities
+    CurvOps32 cops;                   // FP32 tables of the mixed-form curvilinear stage
+    int *wall_ef;                     // [n_wall][2] (element, face) pairs on diffuse faces
+    int n_wall;
     // device
     cudaStream_t stream;
     int device;
@@ -256,6 +266,57 @@ bgk_status run_qprime(bgk_ctx *ctx, const double *part, int n_vblk, int P, doubl
 }
 
 template <typename T>
+void set_geometry(bgk_ctx *ctx, StageArgs<T> &s);
+template <>
+void set_geometry<double>(bgk_ctx *ctx, StageArgs<double> &s) {
+    s.geo = ctx->geo; s.fvec = ctx->fvec; s.rho_w = ctx->rho_w;
+}
+template <>
+void set_geometry<float>(bgk_ctx *ctx, StageArgs<float> &s) {
+    s.geo = ctx->geo32; s.fvec = ctx->fvec32; s.rho_w = ctx->rho_w;
+    s.cops = ctx->cops;
+}
+
+// The FP32 tables of the curvilinear mixed-form stage (see CurvOps32): the
+// rounded D, l(+1), g_R'; their mirror images for l(-1), g_L'; and the
+// column-sum defects of the rounded D measured in FP64.
+void build_curv_ops32(const FROps &fr, CurvOps32 &c) {
+    const int q = fr.q;
+    std::memset(&c, 0, sizeof c);
+    for (int i = 0; i < q; ++i) {
+        for (int j = 0; j < q; ++j) c.D[i][j] = (float)fr.D[i][j];
+        c.lp[i] = (float)fr.lp[i];
+        c.dgR[i] = (float)fr.dgR[i];
+    }
+    for (int i = 0; i < q; ++i) {
+        c.lm[i] = c.lp[q - 1 - i];
+        c.dgL[i] = -c.dgR[q - 1 - i];
+    }
+    // column sums of the deviation-form operator: off-diagonal D (c'_j), the
+    // own-value terms of each row (-W_j rho'_j), the lifted traces, and the
+    // implicit (1 - sum l) weight of the exact-for-constants traces
+    double sigR = 0.0, sigL = 0.0, wsum = 0.0, slp = 0.0, slm = 0.0;
+    for (int i = 0; i < q; ++i) {
+        sigR += fr.wq[i] * (double)c.dgR[i];
+        sigL += fr.wq[i] * (double)c.dgL[i];
+        wsum += fr.wq[i];
+        slp += (double)c.lp[i];
+        slm += (double)c.lm[i];
+    }
+    for (int j = 0; j < q; ++j) {
+        double col = 0.0, row = 0.0;
+        for (int i = 0; i < q; ++i)
+            if (i != j) {
+                col += fr.wq[i] * (double)c.D[i][j];
+                row += (double)c.D[j][i];
+            }
+        const double dj = col - fr.wq[j] * row - sigR * (double)c.lp[j] - sigL * (double)c.lm[j] -
+                          (1.0 - slp) * fr.wq[j] * (double)c.dgR[j] - (1.0 - slm) * fr.wq[j] * (double)c.dgL[j];
+        c.def[j] = (float)(dj / wsum);
+    }
+}
+
+template <typename T>
 StageArgs<T> stage_args(bgk_ctx *ctx, const void *fn, const void *fs, void *fo, double a, double b,
                         double c, bool moments) {
     StageArgs<T> s{};
@@ -268,11 +329,23 @@ StageArgs<T> stage_args(bgk_ctx *ctx, const void *fn, const void *fs, void *fo, 
     s.vg = ctx->vg; s.fr = ctx->fr; s.mesh = ctx->mesh;
     s.a32 = (float)a; s.ab32 = (float)(a + b); s.c32 = (float)c;
     for (int d = 0; d < 3; ++d) s.toh32[d] = (float)ctx->mesh.two_over_h[d];
+    if (ctx->curved) set_geometry<T>(ctx, s);
     return s;
 }
 
 bgk_status run_stage(bgk_ctx *ctx, const void *fn, const void *fs, void *fo, double a, double b,
                      double c, bool moments) {
+    if (ctx->n_wall > 0) {            // diffuse-wall densities of the stage's input
+        LaunchScope lw(ctx, BGK_K_WALL);
+        if (ctx->precision == BGK_FP64)
+            CU(launch_wall_density<double>((const double *)fs, ctx->fvec, ctx->bcval, ctx->vtab, ctx->wall_ef,
+                                           ctx->n_wall, ctx->q, ctx->Ne, ctx->Nu, ctx->C, ctx->fr, ctx->rho_w,
+                                           ctx->stream));
+        else
+            CU(launch_wall_density<float>((const float *)fs, ctx->fvec32, ctx->bcval, ctx->vtab, ctx->wall_ef,
+                                          ctx->n_wall, ctx->q, ctx->Ne, ctx->Nu, ctx->C, ctx->fr, ctx->rho_w,
+                                          ctx->stream));
+    }
     LaunchScope ls(ctx, BGK_K_STAGE);
     if (ctx->precision == BGK_FP64)
         CU(launch_stage_f64(stage_args<double>(ctx, fn, fs, fo, a, b, c, moments), ctx->C, ctx->n_vblk,
@@ -361,6 +434,21 @@ bgk_status replay_step(bgk_ctx *ctx, double dt) {
     return BGK_OK;
 }
 
+// Node coordinates of the uniform box mesh: x[P][3].
+void box_node_coords(const bgk_ctx *ctx, double *x) {
+    const int q = ctx->q, n1 = ctx->mesh.n[0], n2 = ctx->mesh.n[1];
+    for (int e = 0; e < ctx->Ne; ++e) {
+        const int c[3] = {e % n1, (e / n1) % n2, e / (n1 * n2)};
+        for (int s = 0; s < ctx->Ns; ++s) {
+            const int id[3] = {s % q, (s / q) % q, s / (q * q)};
+            for (int d = 0; d < 3; ++d) {
+                const double hd = 2.0 / ctx->mesh.two_over_h[d];
+                x[((size_t)e * ctx->Ns + s) * 3 + d] = ctx->lo[d] + (c[d] + 0.5 * (ctx->fr.xi[id[d]] + 1.0)) * hd;
+            }
+        }
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -378,7 +466,7 @@ bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
     if (mesh->order < 1 || mesh->order > 4) return bad("order must be in 1..4");
     for (int d = 0; d < 3; ++d) {
         if (mesh->n[d] < 1) return bad("mesh n[d] must be >= 1");
-        if (!(mesh->hi[d] > mesh->lo[d])) return bad("mesh hi must exceed lo");
+        if (!mesh->node_xyz && !(mesh->hi[d] > mesh->lo[d])) return bad("mesh hi must exceed lo");
         if (vg->n[d] < 2 || vg->n[d] > BGK_MAXV) return bad("velocity grid needs 2..128 nodes per axis");
         if (!(vg->hi[d] > vg->lo[d])) return bad("velocity hi must exceed lo");
     }
@@ -389,23 +477,35 @@ bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
     for (int d = 0; d < 3; ++d)
         if (!mesh->periodic[d])
             for (int s = 0; s < 2; ++s) {
-                if (mesh->face_type[2 * d + s] == BGK_FACE_SPECULAR) continue;
+                const int ft = mesh->face_type[2 * d + s];
                 const double *b = mesh->bc_state[2 * d + s];
-                if (!(b[0] > 0.0) || !(b[4] > 0.0)) return bad("Dirichlet state needs rho, theta > 0");
+                if (ft == BGK_FACE_DIRICHLET && (!(b[0] > 0.0) || !(b[4] > 0.0)))
+                    return bad("Dirichlet state needs rho, theta > 0");
+                if (ft == BGK_FACE_DIFFUSE && !(b[4] > 0.0)) return bad("a diffuse wall needs theta_w > 0");
             }
     const long long Ne = (long long)mesh->n[0] * mesh->n[1] * mesh->n[2];
     const long long Nu = (long long)vg->n[0] * vg->n[1] * vg->n[2];
     const long long Ns = (long long)(mesh->order + 1) * (mesh->order + 1) * (mesh->order + 1);
     if (Ne * Ns > (1ll << 30) || Nu > (1ll << 30)) return bad("problem too large");
+    bool curved = mesh->node_xyz != nullptr, any_specular = false;
     for (int f = 0; f < 6; ++f) {
         const int d = f / 2;
-        if (mesh->face_type[f] != BGK_FACE_DIRICHLET && mesh->face_type[f] != BGK_FACE_SPECULAR)
-            return bad("face_type must be BGK_FACE_DIRICHLET or BGK_FACE_SPECULAR");
+        if (mesh->face_type[f] < BGK_FACE_DIRICHLET || mesh->face_type[f] > BGK_FACE_CLOSED)
+            return bad("face_type must be one of BGK_FACE_DIRICHLET, _SPECULAR, _DIFFUSE, _CLOSED");
+        if (!mesh->periodic[d] && (mesh->face_type[f] == BGK_FACE_DIFFUSE || mesh->face_type[f] == BGK_FACE_CLOSED))
+            curved = true;
+        if (!mesh->periodic[d] && mesh->face_type[f] == BGK_FACE_SPECULAR) any_specular = true;
         if (mesh->face_type[f] == BGK_FACE_SPECULAR) {
             if (mesh->periodic[d]) return bad("a specular face must be non-periodic");
             if (std::fabs(vg->lo[d] + vg->hi[d]) > 1e-12 * (std::fabs(vg->lo[d]) + std::fabs(vg->hi[d])))
                 return bad("a specular face needs a velocity grid symmetric in its axis");
         }
+    }
+
+    if (curved && any_specular) {
+        ctx->err = "specular faces are supported on the uniform box mesh only (no node_xyz, no diffuse or closed faces)";
+        *out = ctx;
+        return BGK_ENOTSUP;
     }
 
     ctx->p = mesh->order; ctx->q = mesh->order + 1; ctx->Ns = (int)Ns; ctx->Ne = (int)Ne;
@@ -429,8 +529,10 @@ bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
         ctx->mesh.two_over_h[d] = 2.0 * mesh->n[d] / (mesh->hi[d] - mesh->lo[d]);
     }
     ctx->mesh.Ne = ctx->Ne; ctx->mesh.Ns = ctx->Ns;
-    for (int f = 0; f < 6; ++f)
+    for (int f = 0; f < 6; ++f) {
         ctx->mesh.specular[f] = !mesh->periodic[f / 2] && mesh->face_type[f] == BGK_FACE_SPECULAR;
+        ctx->mesh.face_kind[f] = mesh->periodic[f / 2] ? BGK_FK_DIRICHLET : mesh->face_type[f];
+    }
     ctx->jac = 1.0;
     for (int d = 0; d < 3; ++d) {
         ctx->jac *= 0.5 * (mesh->hi[d] - mesh->lo[d]) / mesh->n[d];
@@ -438,6 +540,46 @@ bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
     }
     std::memcpy(ctx->bc, mesh->bc_state, sizeof ctx->bc);
     build_fr(ctx->p, ctx->fr);
+    ctx->curved = curved;
+    ctx->geo = ctx->fvec = nullptr; ctx->geo32 = ctx->fvec32 = nullptr;
+    ctx->rho_w = nullptr; ctx->wall_ef = nullptr; ctx->n_wall = 0;
+    std::vector<double> fvec_h;
+    std::vector<int> wall_h;
+    if (curved) {
+        ctx->xyz_h.resize((size_t)ctx->P * 3);
+        if (mesh->node_xyz) {
+            std::memcpy(ctx->xyz_h.data(), mesh->node_xyz, ctx->xyz_h.size() * sizeof(double));
+        } else {
+            box_node_coords(ctx, ctx->xyz_h.data());
+        }
+        std::string gerr;
+        if (!build_curved_geometry(ctx->fr, mesh->n, ctx->mesh.periodic, ctx->xyz_h.data(), ctx->geo_h, fvec_h, gerr))
+            return bad(gerr.c_str());
+        build_curv_ops32(ctx->fr, ctx->cops);
+        if (precision == BGK_MIXED) {
+            // the mixed form divides by the FP32 1/J: its totals weigh the nodes
+            // with W_s / (1/J)_32, so the quadrature the stage conserves is the
+            // one the totals measure
+            for (int p = 0; p < ctx->P; ++p) {
+                double *g = &ctx->geo_h[(size_t)p * BGK_NGEO];
+                const int s = p % ctx->Ns, q = ctx->q;
+                const double W = ctx->fr.wq[s % q] * ctx->fr.wq[(s / q) % q] * ctx->fr.wq[s / (q * q)];
+                g[10] = W / (double)(float)g[9];
+            }
+        }
+        for (int e = 0; e < ctx->Ne; ++e) {
+            const int ec[3] = {e % mesh->n[0], (e / mesh->n[0]) % mesh->n[1], e / (mesh->n[0] * mesh->n[1])};
+            for (int f = 0; f < 6; ++f) {
+                const int d = f / 2;
+                const bool edge = (f % 2 == 0) ? ec[d] == 0 : ec[d] == mesh->n[d] - 1;
+                if (edge && !mesh->periodic[d] && mesh->face_type[f] == BGK_FACE_DIFFUSE) {
+                    wall_h.push_back(e);
+                    wall_h.push_back(f);
+                }
+            }
+        }
+        ctx->n_wall = (int)(wall_h.size() / 2);
+    }
     ctx->gas.delta = gas->delta; ctx->gas.Pr = gas->Pr; ctx->gas.mu_ref = gas->mu_ref;
     ctx->gas.theta_ref = gas->theta_ref; ctx->gas.theta_S = gas->theta_S;
     ctx->gas.gamma = (5.0 + gas->delta) / (3.0 + gas->delta);
@@ -465,8 +607,10 @@ bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
     // Dirichlet exterior states per face and velocity
     std::vector<double> bcv((size_t)6 * ctx->C * Nu, 0.0);
     for (int face = 0; face < 6; ++face) {
-        if (mesh->periodic[face / 2] || ctx->mesh.specular[face]) continue;
-        const double *st = mesh->bc_state[face];
+        if (mesh->periodic[face / 2] || ctx->mesh.specular[face] || mesh->face_type[face] == BGK_FACE_CLOSED) continue;
+        double st[5];
+        std::memcpy(st, mesh->bc_state[face], sizeof st);
+        if (mesh->face_type[face] == BGK_FACE_DIFFUSE) st[0] = 1.0;   // unit density; rho_w per flux node
         for (int k = 0; k < Nu; ++k) {
             const double *v = &ctx->vtab_h[(size_t)k * BGK_VTAB];
             const double F = maxwellian_value(v[0], v[1], v[2], st);
@@ -519,6 +663,63 @@ bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
     }
     if (st == BGK_OK) cu(cudaMalloc(&ctx->vtab32, v32.size() * sizeof(float4)), "cudaMalloc(vtab32)");
     if (st == BGK_OK) cu(cudaMemcpyAsync(ctx->vtab32, v32.data(), v32.size() * sizeof(float4), cudaMemcpyHostToDevice, ctx->stream), "upload vtab32");
+    if (st == BGK_OK && curved) {
+        const size_t ng = ctx->geo_h.size(), nf = fvec_h.size();
+        const int q = ctx->q, Ns = ctx->Ns;
+        // FP32 node records: S, 1/J, and S_face - S^d_node per face (in FP64)
+        std::vector<float> g32((size_t)ctx->P * BGK_NGEO32, 0.f), f32(nf);
+        for (int p = 0; p < ctx->P; ++p) {
+            const double *g = &ctx->geo_h[(size_t)p * BGK_NGEO];
+            float *o = &g32[(size_t)p * BGK_NGEO32];
+            for (int i = 0; i < 10; ++i) o[i] = (float)g[i];
+            const int e = p / Ns, s = p % Ns;
+            const int id[3] = {s % q, (s / q) % q, s / (q * q)};
+            const int fpi[3] = {id[1] + q * id[2], id[0] + q * id[2], id[0] + q * id[1]};
+            for (int fc = 0; fc < 6; ++fc) {
+                const int d = fc / 2;
+                const double *fv = &fvec_h[(((size_t)e * 6 + fc) * q * q + fpi[d]) * 3];
+                for (int c = 0; c < 3; ++c) o[10 + 3 * fc + c] = (float)(fv[c] - g[3 * d + c]);
+            }
+            // geometric remainder H (CurvOps32): the f_i-proportional terms of the
+            // three directions' operators, with the FP32 coefficients, in FP64
+            const CurvOps32 &co = ctx->cops;
+            const int stride[3] = {1, q, q * q};
+            double H[3] = {0.0, 0.0, 0.0};
+            for (int d = 0; d < 3; ++d) {
+                const int i = id[d];
+                const int base = s - i * stride[d];
+                const double *Si = &ctx->geo_h[((size_t)e * Ns + s) * BGK_NGEO + 3 * d];
+                const double *FL = &fvec_h[(((size_t)e * 6 + 2 * d) * q * q + fpi[d]) * 3];
+                const double *FR = &fvec_h[(((size_t)e * 6 + 2 * d + 1) * q * q + fpi[d]) * 3];
+                for (int c = 0; c < 3; ++c) {
+                    double vol = 0.0, trL = 0.0, trR = 0.0;
+                    for (int j = 0; j < q; ++j) {
+                        const double dS = ctx->geo_h[((size_t)e * Ns + base + j * stride[d]) * BGK_NGEO + 3 * d + c] - Si[c];
+                        if (j != i) vol += (double)co.D[i][j] * dS;
+                        vol -= (double)co.def[j] * dS;
+                        trL += (double)co.lm[j] * dS;
+                        trR += (double)co.lp[j] * dS;
+                    }
+                    H[c] += vol + (double)co.dgR[i] * (FR[c] - Si[c] - trR) + (double)co.dgL[i] * (FL[c] - Si[c] - trL);
+                }
+            }
+            for (int c = 0; c < 3; ++c) o[28 + c] = (float)H[c];
+        }
+        for (size_t i = 0; i < nf; ++i) f32[i] = (float)fvec_h[i];
+        cu(cudaMalloc(&ctx->geo, ng * sizeof(double)), "cudaMalloc(geo)");
+        if (st == BGK_OK) cu(cudaMalloc(&ctx->fvec, nf * sizeof(double)), "cudaMalloc(fvec)");
+        if (st == BGK_OK) cu(cudaMalloc(&ctx->geo32, g32.size() * sizeof(float)), "cudaMalloc(geo32)");
+        if (st == BGK_OK) cu(cudaMalloc(&ctx->fvec32, nf * sizeof(float)), "cudaMalloc(fvec32)");
+        if (st == BGK_OK) cu(cudaMalloc(&ctx->rho_w, (size_t)ctx->Ne * 6 * ctx->q * ctx->q * sizeof(double)), "cudaMalloc(rho_w)");
+        if (st == BGK_OK && ctx->n_wall) cu(cudaMalloc(&ctx->wall_ef, wall_h.size() * sizeof(int)), "cudaMalloc(wall)");
+        if (st == BGK_OK) cu(cudaMemcpy(ctx->geo, ctx->geo_h.data(), ng * sizeof(double), cudaMemcpyHostToDevice), "upload geo");
+        if (st == BGK_OK) cu(cudaMemcpy(ctx->fvec, fvec_h.data(), nf * sizeof(double), cudaMemcpyHostToDevice), "upload fvec");
+        if (st == BGK_OK) cu(cudaMemcpy(ctx->geo32, g32.data(), g32.size() * sizeof(float), cudaMemcpyHostToDevice), "upload geo32");
+        if (st == BGK_OK) cu(cudaMemcpy(ctx->fvec32, f32.data(), nf * sizeof(float), cudaMemcpyHostToDevice), "upload fvec32");
+        if (st == BGK_OK) cu(cudaMemset(ctx->rho_w, 0, (size_t)ctx->Ne * 6 * ctx->q * ctx->q * sizeof(double)), "memset rho_w");
+        if (st == BGK_OK && ctx->n_wall)
+            cu(cudaMemcpy(ctx->wall_ef, wall_h.data(), wall_h.size() * sizeof(int), cudaMemcpyHostToDevice), "upload wall");
+    }
     if (st == BGK_OK) cu(cudaMalloc(&ctx->status, sizeof(unsigned int)), "cudaMalloc(status)");
     if (st == BGK_OK) cu(cudaMalloc(&ctx->stats, sizeof(NewtonStats)), "cudaMalloc(stats)");
     if (st == BGK_OK) cu(cudaMalloc(&ctx->mlp_w, MLP_NPARAM * sizeof(float)), "cudaMalloc(mlp)");
@@ -554,6 +755,8 @@ bgk_status bgk_destroy(bgk_ctx *ctx) {
     cudaFree(ctx->part); cudaFree(ctx->mom); cudaFree(ctx->eq); cudaFree(ctx->qp);
     cudaFree(ctx->iters); cudaFree(ctx->eq32); cudaFree(ctx->vtab); cudaFree(ctx->vtab32); cudaFree(ctx->bcval); cudaFree(ctx->status);
     cudaFree(ctx->stats);
+    cudaFree(ctx->geo); cudaFree(ctx->fvec); cudaFree(ctx->geo32); cudaFree(ctx->fvec32);
+    cudaFree(ctx->rho_w); cudaFree(ctx->wall_ef);
     cudaFree(ctx->mlp_w); cudaFree(ctx->mlp_norm); cudaFree(ctx->mlp_m); cudaFree(ctx->mlp_v);
     cudaFree(ctx->mlp_grad); cudaFree(ctx->mlp_loss); cudaFree(ctx->log); cudaFree(ctx->log_count);
     delete ctx;
@@ -574,19 +777,9 @@ const char *bgk_last_error(const bgk_ctx *ctx) { return ctx ? ctx->err.c_str() :
 bgk_status bgk_node_coords(const bgk_ctx *ctx_c, double *x, int on_device) {
     bgk_ctx *ctx = const_cast<bgk_ctx *>(ctx_c);
     if (!ctx || !x) return BGK_EINVAL;
-    const int q = ctx->q, n1 = ctx->mesh.n[0], n2 = ctx->mesh.n[1];
     std::vector<double> h((size_t)ctx->P * 3);
-    for (int e = 0; e < ctx->Ne; ++e) {
-        const int c[3] = {e % n1, (e / n1) % n2, e / (n1 * n2)};
-        for (int s = 0; s < ctx->Ns; ++s) {
-            const int id[3] = {s % q, (s / q) % q, s / (q * q)};
-            for (int d = 0; d < 3; ++d) {
-                const double hd = 2.0 / ctx->mesh.two_over_h[d];
-                h[((size_t)e * ctx->Ns + s) * 3 + d] =
-                    ctx->lo[d] + (c[d] + 0.5 * (ctx->fr.xi[id[d]] + 1.0)) * hd;
-            }
-        }
-    }
+    if (ctx->curved) h = ctx->xyz_h;
+    else box_node_coords(ctx, h.data());
     CU(cudaMemcpyAsync(x, h.data(), h.size() * sizeof(double),
                        on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
@@ -652,7 +845,8 @@ bgk_status bgk_set_stage_kernel(bgk_ctx *ctx, int variant, int depth) {
             return fail(ctx, BGK_ENOTSUP, "the asynchronous-copy stage kernels are for the mixed form only");
         const StageArgs<float> a = stage_args<float>(ctx, ctx->f[0], ctx->f[1], ctx->f[2], 0.5, 0.5, 1.0, true);
         if (!stage_f32_variant_supported(a, ctx->C, variant, depth))
-            return fail(ctx, BGK_ENOTSUP, "asynchronous-copy stage kernels need p = 1 or 3 and fitting shared memory");
+            return fail(ctx, BGK_ENOTSUP, "asynchronous-copy stage kernels need the uniform box mesh (no specular, "
+                                          "diffuse or closed faces), p = 1 or 3 and fitting shared memory");
     }
     ctx->stage_variant = variant;
     ctx->stage_depth = depth;
@@ -794,6 +988,7 @@ bgk_status bgk_moments(bgk_ctx *ctx, double *m, int on_device) {
 
 bgk_status bgk_macro(bgk_ctx *ctx, double *out, int on_device) {
     if (!ctx || !out) return BGK_EINVAL;
+    if (ctx->curved) return fail(ctx, BGK_ENOTSUP, "macroscopic diagnostics are implemented for the uniform box mesh");
     bgk_status st;
     if (!ctx->part_valid) {
         if ((st = run_moments(ctx, ctx->f[0], true))) return st;
@@ -857,7 +1052,8 @@ bgk_status bgk_totals(bgk_ctx *ctx, double totals[5]) {
     double t[5] = {0, 0, 0, 0, 0};
     for (int p = 0; p < ctx->P; ++p) {
         const int s = p % ctx->Ns;
-        const double W = ctx->fr.wq[s % q] * ctx->fr.wq[(s / q) % q] * ctx->fr.wq[s / (q * q)] * ctx->jac;
+        const double W = ctx->curved ? ctx->geo_h[(size_t)p * BGK_NGEO + 10]
+                                     : ctx->fr.wq[s % q] * ctx->fr.wq[(s / q) % q] * ctx->fr.wq[s / (q * q)] * ctx->jac;
         const double *mm = &m[(size_t)p * BGK_NMOM];
         t[0] += W * mm[0]; t[1] += W * mm[1]; t[2] += W * mm[2]; t[3] += W * mm[3];
         t[4] += W * (0.5 * (mm[4] + mm[5] + mm[6]) + mm[10]);

@@ -19,6 +19,19 @@
 //   8 V2  9 V3  10 A12  11 A13  12 A22  13 A23  14 A33  15 gamma0
 //   16 gamma2  17 gamma3  18 U0_2  19 U0_3  20 gamma4  21..23 unused
 #define BGK_NEQ32 24
+// Curvilinear node record: S^1 (3), S^2 (3), S^3 (3) (S^d = J grad xi_d),
+// 1/J, the quadrature weight W_s J_s, unused.
+#define BGK_NGEO 12
+// FP32 node record of the mixed form: S^1..S^3 (9), 1/J, then for the six
+// faces 2d + side the difference S_face - S^d_node at the flux node on the
+// node's line (18; formed in FP64), the node's geometric remainder H (3, see
+// CurvOps32), unused.
+#define BGK_NGEO32 32
+// Non-periodic face kinds (face 2d + side).
+#define BGK_FK_DIRICHLET 0
+#define BGK_FK_SPECULAR 1
+#define BGK_FK_DIFFUSE 2
+#define BGK_FK_CLOSED 3
 #define BGK_VTAB 8          // velocity table record: u1 u2 u3 w e=|u|^2/2 w*u1 w*u1^2 (2/h1)*u1
 #define BGK_MAXV 128        // nodes per velocity axis at most
 
@@ -51,6 +64,7 @@ struct MeshInfo {
     int n[3];
     int periodic[3];
     int specular[6];                    // face 2d + side reflects specularly
+    int face_kind[6];                   // BGK_FK_* of each non-periodic face
     double two_over_h[3];
     int Ne, Ns;
 };
@@ -116,6 +130,29 @@ struct NewtonStats {
     unsigned long long res_max_bits;    // bit pattern of a non-negative double
 };
 
+// FP32 operator tables of the curvilinear mixed-form stage.  Per direction
+// and node i of a line, with Ft_j = a_j f_j (a_j = u . S^d_j), the operator is
+//   t_i = sum_{j != i} D_ij (Ft_j - Ft_i) - sum_j def_j (Ft_j - Ft_i)
+//       + g_R'_i (A_R f^up_R - Ft_i - sum_j l_j(+1) (Ft_j - Ft_i)) + (left face)
+// (the diagonal of D and the weight sums never enter, so the traces are exact
+// for constant data).  g_L' is the mirror image of g_R' and l(-1) that of
+// l(+1), so the two faces' lift weights sum_i W_i g'_i cancel exactly;
+// def[j] is the defect, divided by sum_i W_i, of the column sums
+// sum_i W_i (d t_i / d Ft_j) of the rounded operator (zero in exact
+// arithmetic; its entries sum to zero): the element quadrature of the
+// divergence then telescopes exactly for the stored coefficients.  The stage
+// evaluates it regrouped, Ft_j - Ft_i = a_j (f_j - f_i) + (a_j - a_i) f_i: the
+// sums act on deviations a_j (f_j - f_i), and every term proportional to f_i
+// is geometry times u, summed over the three directions into the node's
+// vector H (formed on the host in FP64 with these FP32 coefficients, about
+// zero for a continuous mesh) and added as f_i u . H.
+struct CurvOps32 {
+    float D[BGK_MAXQ][BGK_MAXQ];
+    float lp[BGK_MAXQ], lm[BGK_MAXQ];
+    float dgL[BGK_MAXQ], dgR[BGK_MAXQ];
+    float def[BGK_MAXQ];
+};
+
 // Arguments of the fused stage kernel:  f_out = a f_n + b f_s + c R(f_s).
 template <typename T>
 struct StageArgs {
@@ -128,6 +165,11 @@ struct StageArgs {
     const double *bcval;     // [6][C][Nu] exterior Maxwellian values of Dirichlet faces
     double *part;            // [n_vblk][BGK_NMOM][P] moment partials of f_out (or null)
     const float *eq32;       // [P][BGK_NEQ32] (mixed form)
+    // curvilinear meshes (all null on the uniform box)
+    const T *geo;            // [P][BGK_NGEO]
+    const T *fvec;           // [Ne][6][Q*Q][3] face vectors, oriented +xi_d
+    const double *rho_w;     // [Ne][6][Q*Q] diffuse-wall densities of this stage's input
+    CurvOps32 cops;          // FP32 operator tables (mixed form)
     unsigned int *status;    // device status word (BGK_DEV_* bits)
     double a, b, c;
     // FP32 copies made on the host: a, a + b, c, and the metric terms 2/h_d
@@ -175,6 +217,20 @@ struct MomentArgs64 {
     const double *vtab;
     int Nu, P, Kblk, C;
 };
+
+// Curvilinear metric terms (geometry.cu, host): geo[P][BGK_NGEO],
+// fvec[Ne][6][q*q][3]; false with err on a non-positive Jacobian.
+#include <string>
+#include <vector>
+bool build_curved_geometry(const FROps &fr, const int n[3], const int periodic[3], const double *x,
+                           std::vector<double> &geo, std::vector<double> &fvec, std::string &err);
+
+// Diffuse-wall densities of a state (wall.cu): rho_w[e][f][fp] for the n_wall
+// (element, face) pairs in wall_ef[2 * i], wall_ef[2 * i + 1].
+template <typename T>
+cudaError_t launch_wall_density(const T *f, const T *fvec, const double *bcval, const double *vtab,
+                                const int *wall_ef, int n_wall, int q, int Ne, int Nu, int C, FROps fr,
+                                double *rho_w, cudaStream_t s);
 
 // Launchers (kernels_f64.cu).
 cudaError_t launch_moments_f64(const MomentArgs64 &a, int n_vblk, cudaStream_t s);

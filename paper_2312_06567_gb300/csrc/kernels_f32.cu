@@ -25,12 +25,31 @@ namespace {
 // inflow trace folded into Dt; div = sum_d (2/h_d) u_d t_d;
 // R = -div + (g' - f)/tau.  g' = exp(c0) * exp2(-log2(e)/2 c^T A c) with the
 // per-point factor exp(c0) from FP64 and the exponent in FP32.
-template <int Q, int C>
+//
+// Curvilinear elements (CURV): the transformed-flux form of the FP64 stage
+// kernel (kernels_f64.cu) in FP32, regrouped so that every rounding acts on
+// deviations (see CurvOps32).  a_d = u . S^d per node is staged beside f; per
+// direction, with w_j = a_j (f_j - f_i),
+//   t_i = sum_{j != i} D_ij w_j - sum_j def_j w_j
+//       + g_R'_i (A_R dev_R - sum_j l_j(+1) w_j) + g_L'_i (A_L dev_L - sum_j l_j(-1) w_j),
+// A = a_i + u.(S_face - S_i) the face's normal velocity, dev = (upwind trace)
+// - f_i: the own trace sum_j l_j (f_j - f_i) on an outflow face, the
+// neighbour's sum_j l_j (nb_j - f_i) or the exterior value minus f_i on an
+// inflow face, -f_i on a closed face (F^I = 0); then
+// div = (1/J) (sum_d t_d + f_i u . H).  This is the FP64 kernel's F^I - trace
+// form term for term in exact arithmetic; constant data and the exact
+// telescoping of the element quadrature survive the FP32 arithmetic.
+template <int Q, int C, bool CURV>
 __global__ void __launch_bounds__(256) k_stage_f32(StageArgs<float> a) {
     constexpr int NS = Q * Q * Q;
     constexpr int EB = 256 / NS;
     constexpr int NT = EB * NS;
     __shared__ float sf[2][C][NT];
+    __shared__ float sA[CURV ? 2 : 1][CURV ? 3 : 1][CURV ? NT : 1];    // a_d = u . S^d (CURV)
+    __shared__ float cD[CURV ? Q : 1][CURV ? Q : 1];     // D (CURV)
+    __shared__ float cl[2][CURV ? Q : 1];                // l(+1), l(-1) (CURV)
+    __shared__ float cg[2][CURV ? Q : 1];                // g_L', g_R' (CURV)
+    __shared__ float cdef[CURV ? Q : 1];                 // column-sum defects of D (CURV)
     __shared__ float sD[2][Q][Q];         // Dt = D - dg (x) l, FP32
     __shared__ float sdg[2][Q];           // dg (FP32)
     __shared__ float seps[2][Q];          // eps_i = sum_j Dt_ij + dg_i  (exact defect, tiny)
@@ -48,6 +67,14 @@ __global__ void __launch_bounds__(256) k_stage_f32(StageArgs<float> a) {
     // neighbours, which keeps the advection discretely conservative up to
     // second-order rounding terms.
     load_ops_f32<Q>(a.fr, tid, sD, sdg, seps, slam, sdlam);
+    if constexpr (CURV) {
+        if (tid < Q * Q) cD[tid / Q][tid % Q] = a.cops.D[tid / Q][tid % Q];
+        if (tid < Q) {
+            cl[0][tid] = a.cops.lp[tid]; cl[1][tid] = a.cops.lm[tid];
+            cg[0][tid] = a.cops.dgL[tid]; cg[1][tid] = a.cops.dgR[tid];
+            cdef[tid] = a.cops.def[tid];
+        }
+    }
     const int e0 = blockIdx.x * EB;
     const int le = tid / NS, s = tid - le * NS;
     const int e = e0 + le;
@@ -68,6 +95,26 @@ __global__ void __launch_bounds__(256) k_stage_f32(StageArgs<float> a) {
         en_[d][0] = ec[d] > 0 ? e - estr[d] : (a.mesh.periodic[d] ? e + (nn[d] - 1) * estr[d] : -1);
         en_[d][1] = ec[d] < nn[d] - 1 ? e + estr[d] : (a.mesh.periodic[d] ? e - (nn[d] - 1) * estr[d] : -1);
         base[d] = s - id[d] * stride[d];
+    }
+    float Sm[CURV ? 3 : 1][3], invJ = 0.f, dFv[CURV ? 6 : 1][3], Hg[3] = {0.f, 0.f, 0.f};
+    if constexpr (CURV) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) Sm[d][0] = Sm[d][1] = Sm[d][2] = 0.f;
+#pragma unroll
+        for (int fc = 0; fc < 6; ++fc) dFv[fc][0] = dFv[fc][1] = dFv[fc][2] = 0.f;
+        if (active) {
+            const float *g = a.geo + (size_t)p * BGK_NGEO32;
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) Sm[d][c] = g[3 * d + c];
+            invJ = g[9];
+#pragma unroll
+            for (int fc = 0; fc < 6; ++fc)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) dFv[fc][c] = g[10 + 3 * fc + c];
+            Hg[0] = g[28]; Hg[1] = g[29]; Hg[2] = g[30];
+        }
     }
     Eq32 e32;
     float itau = 0.f, gfac = 0.f;
@@ -116,11 +163,21 @@ __global__ void __launch_bounds__(256) k_stage_f32(StageArgs<float> a) {
         for (int j1 = 0; j1 < vn1; ++j1, jt1 += 1.f) {
             const int k = kl + j1;
             float fself[C];
+            float ad[3] = {0.f, 0.f, 0.f};
             if (active) {
+                if constexpr (CURV) {
+                    const float uu[3] = {__ldg(a.vtab32 + k).x, u2, u3};
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) ad[d] = fmaf(uu[0], Sm[d][0], fmaf(uu[1], Sm[d][1], uu[2] * Sm[d][2]));
+                }
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
                     fself[c] = __ldg(a.f_s + ((size_t)c * a.Nu + k) * slab + p);
                     sf[buf][c][tid] = fself[c];
+                }
+                if constexpr (CURV) {
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) sA[buf][d][tid] = ad[d];
                 }
             }
             __syncthreads();
@@ -141,6 +198,62 @@ __global__ void __launch_bounds__(256) k_stage_f32(StageArgs<float> a) {
                     const float *sfc = sf[buf][c];
                     const float fi = fself[c];
                     float div = 0.f;
+                    if constexpr (CURV) {
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) {
+                            const float *own = sfc + le * NS + base[d];
+                            const float *ownA = sA[buf][d] + le * NS + base[d];
+                            float dF = 0.f, E = 0.f, trL = 0.f, trR = 0.f, fmL = 0.f, fmR = 0.f;
+#pragma unroll
+                            for (int m = 1; m < Q; ++m) {
+                                const int j = (id[d] + m) % Q;
+                                const float dfj = own[j * stride[d]] - fi;
+                                const float wj = ownA[j * stride[d]] * dfj;
+                                dF = fmaf(cD[id[d]][j], wj, dF);
+                                E = fmaf(cdef[j], wj, E);
+                                trL = fmaf(cl[1][j], wj, trL);
+                                trR = fmaf(cl[0][j], wj, trR);
+                                fmL = fmaf(cl[1][j], dfj, fmL);
+                                fmR = fmaf(cl[0][j], dfj, fmR);
+                            }
+                            float X[2];
+#pragma unroll
+                            for (int side = 0; side < 2; ++side) {
+                                const float *dv = dFv[2 * d + side];
+                                const float A = ad[d] + fmaf(u[0], dv[0], fmaf(u[1], dv[1], u[2] * dv[2]));
+                                const float un = side ? A : -A;           // outward
+                                const int en = en_[d][side];
+                                const int kind = a.mesh.face_kind[2 * d + side];
+                                float dev;
+                                if (en < 0 && kind == BGK_FK_CLOSED) {
+                                    dev = -fi;                            // F^I = 0
+                                } else if (un > 0.f) {
+                                    dev = side ? fmR : fmL;
+                                } else if (en >= e0 && en < e0 + EB) {
+                                    const float *nb = sfc + (en - e0) * NS + base[d];
+                                    dev = 0.f;
+#pragma unroll
+                                    for (int j = 0; j < Q; ++j) dev = fmaf(cl[side][j], nb[j * stride[d]] - fi, dev);
+                                } else if (en >= 0) {
+                                    const float *nb = fs + (size_t)en * NS + base[d];
+                                    dev = 0.f;
+#pragma unroll
+                                    for (int j = 0; j < Q; ++j) dev = fmaf(cl[side][j], __ldg(nb + j * stride[d]) - fi, dev);
+                                } else {
+                                    double fpd = __ldg(a.bcval + ((size_t)(2 * d + side) * C + c) * a.Nu + k);
+                                    if (kind == BGK_FK_DIFFUSE) {
+                                        const int fpi = d == 0 ? id[1] + Q * id[2] : (d == 1 ? id[0] + Q * id[2] : id[0] + Q * id[1]);
+                                        fpd *= __ldg(a.rho_w + ((size_t)e * 6 + 2 * d + side) * Q * Q + fpi);
+                                    }
+                                    dev = (float)fpd - fi;
+                                }
+                                X[side] = fmaf(A, dev, -(side ? trR : trL));
+                            }
+                            div += fmaf(X[1], cg[1][id[d]], fmaf(X[0], cg[0][id[d]], dF - E));
+                        }
+                        div = fmaf(fi, fmaf(u[0], Hg[0], fmaf(u[1], Hg[1], u[2] * Hg[2])), div);
+                        div *= invJ;
+                    } else {
 #pragma unroll
                     for (int d = 0; d < 3; ++d) {
                         const int side = u[d] > 0.f ? 0 : 1;
@@ -180,6 +293,7 @@ __global__ void __launch_bounds__(256) k_stage_f32(StageArgs<float> a) {
                         }
                         t = fmaf(sdg[side][id[d]], dn, fmaf(seps[side][id[d]], fi, t));
                         div = fmaf(toh[d] * u[d], t, div);
+                    }
                     }
                     const float eqv = (c == 0) ? g32 : gfac * g32;
                     const float eqc = (c == 0) ? gc : gfac * gc;
@@ -505,8 +619,13 @@ template <int Q>
 static cudaError_t stage32_q(const StageArgs<float> &a, int C, int n_vblk, cudaStream_t s) {
     constexpr int NS = Q * Q * Q, EB = 256 / NS;
     dim3 grid((a.mesh.Ne + EB - 1) / EB, n_vblk);
-    if (C == 1) k_stage_f32<Q, 1><<<grid, EB * NS, 0, s>>>(a);
-    else k_stage_f32<Q, 2><<<grid, EB * NS, 0, s>>>(a);
+    if (a.geo) {
+        if (C == 1) k_stage_f32<Q, 1, true><<<grid, EB * NS, 0, s>>>(a);
+        else k_stage_f32<Q, 2, true><<<grid, EB * NS, 0, s>>>(a);
+    } else {
+        if (C == 1) k_stage_f32<Q, 1, false><<<grid, EB * NS, 0, s>>>(a);
+        else k_stage_f32<Q, 2, false><<<grid, EB * NS, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -544,6 +663,7 @@ static bool any_specular(const MeshInfo &m) {
 bool stage_f32_tma_supported(const StageArgs<float> &a, int C, int depth) {
     if (a.fr.q != 2 && a.fr.q != 4) return false;          // element slabs of whole 16-byte units
     if (any_specular(a.mesh)) return false;                 // reflected traces are not staged
+    if (a.geo) return false;                                // curvilinear: the plain kernel only
     if (depth < 2 || depth > BGK_MAX_DEPTH) return false;
     if (!aligned16(a.f_s) || (a.a32 != 0.f && !aligned16(a.f_n))) return false;
     const size_t smem = a.fr.q == 2 ? (C == 1 ? tma_smem<2, 1>(depth) : tma_smem<2, 2>(depth))

@@ -572,6 +572,7 @@ bool stage_f32_line_supported(const StageArgs<float> &a, int C, int kind, int de
     if (kind < 0 || kind > 3 || depth < 2 || depth > BGK_MAX_DEPTH || !a.eq32) return false;
     for (int f = 0; f < 6; ++f)
         if (a.mesh.specular[f]) return false;               // reflected traces are not staged
+    if (a.geo) return false;                                // curvilinear: the plain kernel only
     if (!aligned_to(a.f_s, 16) || (a.a32 != 0.f && !aligned_to(a.f_n, 16)) || !aligned_to(a.f_out, 16)) return false;
     size_t smem = 0;
     line_any(kind, false, a, C, 0, depth, nullptr, &smem);

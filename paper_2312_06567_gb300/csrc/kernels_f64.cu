@@ -75,20 +75,37 @@ __global__ void k_reduce_moments(const double *part, int n_vblk, int P, double *
 // exponent is below -650, where the recurrence would underflow).
 // The block holds EB whole elements; their values for the current velocity
 // are staged in shared memory (double buffered, one barrier per velocity).
-template <int Q, int C>
+//
+// Curvilinear elements (CURV): the transformed flux Ft_d = a_d f with
+// a_d = u . S^d at each node (S^d = J grad xi_d), per direction and line
+//   dFt/dxi(xi_i) = sum_j D_ij Ft_j + J_R g_R'(xi_i) + J_L g_L'(xi_i),
+//   J_R = F^I_R - sum_j l_j(+1) Ft_j,   F^I_R = A_R (A_R > 0 ? f^-_R : f^+_R),
+//   J_L = -F^I_L,out - sum_j l_j(-1) Ft_j,  F^I_L,out = -A_L (-A_L > 0 ? f^-_L : f^+_L),
+// A = u . S_face at the line's flux nodes (face vectors oriented +xi_d), and
+// div = (1/J) sum_d dFt_d/dxi.  Both faces contribute (the trace of a f is
+// not A times the trace of f).  The element's own flux values are staged in
+// shared memory beside f.  Boundary faces: Dirichlet (prescribed exterior
+// Maxwellian), diffuse wall (rho_w times the wall Maxwellian), closed (no flux).
+template <int Q, int C, bool CURV>
 __global__ void __launch_bounds__(256) k_stage_f64(StageArgs<double> a) {
     constexpr int NS = Q * Q * Q;
     constexpr int EB = 256 / NS;
     constexpr int NT = EB * NS;
     __shared__ double sf[2][C][NT];
-    __shared__ double sD[2][Q][Q];        // Dt_L, Dt_R
+    __shared__ double sFt[CURV ? 2 : 1][CURV ? C : 1][CURV ? 3 : 1][CURV ? NT : 1];
+    __shared__ double sD[2][Q][Q];        // Dt_L, Dt_R (CURV: D, unused)
     __shared__ double sdg[2][Q];          // g_L', g_R'
     __shared__ double sl[2][Q];           // neighbour trace weights: l(+1) for left inflow, l(-1) for right
     const int tid = threadIdx.x;
     if (tid < Q * Q) {
         const int i = tid / Q, j = tid % Q;
-        sD[0][i][j] = a.fr.D[i][j] - a.fr.dgL[i] * a.fr.lm[j];
-        sD[1][i][j] = a.fr.D[i][j] - a.fr.dgR[i] * a.fr.lp[j];
+        if (CURV) {
+            sD[0][i][j] = a.fr.D[i][j];
+            sD[1][i][j] = a.fr.D[i][j];
+        } else {
+            sD[0][i][j] = a.fr.D[i][j] - a.fr.dgL[i] * a.fr.lm[j];
+            sD[1][i][j] = a.fr.D[i][j] - a.fr.dgR[i] * a.fr.lp[j];
+        }
     }
     if (tid < Q) {
         sdg[0][tid] = a.fr.dgL[tid]; sdg[1][tid] = a.fr.dgR[tid];
@@ -114,6 +131,31 @@ __global__ void __launch_bounds__(256) k_stage_f64(StageArgs<double> a) {
         en_[d][0] = ec[d] > 0 ? e - estr[d] : (a.mesh.periodic[d] ? e + (nn[d] - 1) * estr[d] : -1);
         en_[d][1] = ec[d] < nn[d] - 1 ? e + estr[d] : (a.mesh.periodic[d] ? e - (nn[d] - 1) * estr[d] : -1);
         base[d] = s - id[d] * stride[d];
+    }
+    // curvilinear: the node's metric vectors, 1/J and the face vectors of the
+    // flux nodes on its three lines (faces 2d and 2d + 1)
+    double Sm[CURV ? 3 : 1][3], invJ = 0.0, Fv[CURV ? 6 : 1][3];
+    if constexpr (CURV) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) Sm[d][c] = 0.0;
+#pragma unroll
+        for (int fc = 0; fc < 6; ++fc) Fv[fc][0] = Fv[fc][1] = Fv[fc][2] = 0.0;
+        if (active) {
+            const double *g = a.geo + (size_t)p * BGK_NGEO;
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) Sm[d][c] = g[3 * d + c];
+            invJ = g[9];
+            const int fpi[3] = {id[1] + Q * id[2], id[0] + Q * id[2], id[0] + Q * id[1]};
+#pragma unroll
+            for (int fc = 0; fc < 6; ++fc) {
+                const double *v = a.fvec + (((size_t)e * 6 + fc) * Q * Q + fpi[fc / 2]) * 3;
+                Fv[fc][0] = v[0]; Fv[fc][1] = v[1]; Fv[fc][2] = v[2];
+            }
+        }
     }
     double c0 = 0, V1 = 0, V2 = 0, V3 = 0, A11 = 1, A22 = 1, A33 = 1, A12 = 0, A13 = 0, A23 = 0;
     double itau = 0, gfac = 0;
@@ -152,11 +194,21 @@ __global__ void __launch_bounds__(256) k_stage_f64(StageArgs<double> a) {
             const int k = kl + j1;
             const double *vt = a.vtab + (size_t)k * BGK_VTAB;
             double fself[C];
+            double ad[3] = {0.0, 0.0, 0.0};
             if (active) {
+                if constexpr (CURV) {
+                    const double uu[3] = {__ldg(vt + 0), u2, u3};
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) ad[d] = fma(uu[0], Sm[d][0], fma(uu[1], Sm[d][1], uu[2] * Sm[d][2]));
+                }
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
                     fself[c] = __ldg(a.f_s + ((size_t)c * a.Nu + k) * slab + p);
                     sf[buf][c][tid] = fself[c];
+                    if constexpr (CURV) {
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) sFt[buf][c][d][tid] = ad[d] * fself[c];
+                    }
                 }
             }
             // equilibrium value at this velocity
@@ -179,6 +231,56 @@ __global__ void __launch_bounds__(256) k_stage_f64(StageArgs<double> a) {
                     const double *fs = a.f_s + ((size_t)c * a.Nu + k) * slab;
                     const double *sfc = sf[buf][c];
                     double div = 0.0;
+                    if constexpr (CURV) {
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) {
+                            const double *own = sfc + le * NS + base[d];
+                            const double *ownF = sFt[buf][c][d] + le * NS + base[d];
+                            double dF = 0.0, trL = 0.0, trR = 0.0, fmL = 0.0, fmR = 0.0;
+#pragma unroll
+                            for (int j = 0; j < Q; ++j) {
+                                const double Fj = ownF[j * stride[d]], fj = own[j * stride[d]];
+                                dF = fma(sD[0][id[d]][j], Fj, dF);
+                                trL = fma(sl[1][j], Fj, trL);        // sl[1] = l(-1)
+                                trR = fma(sl[0][j], Fj, trR);        // sl[0] = l(+1)
+                                fmL = fma(sl[1][j], fj, fmL);
+                                fmR = fma(sl[0][j], fj, fmR);
+                            }
+                            const double AL = fma(u[0], Fv[2 * d][0], fma(u[1], Fv[2 * d][1], u[2] * Fv[2 * d][2]));
+                            const double AR = fma(u[0], Fv[2 * d + 1][0], fma(u[1], Fv[2 * d + 1][1], u[2] * Fv[2 * d + 1][2]));
+                            double FI[2];                          // outward common flux, left and right
+#pragma unroll
+                            for (int side = 0; side < 2; ++side) {
+                                const double un = side ? AR : -AL;
+                                const double fm = side ? fmR : fmL;
+                                const int en = en_[d][side];
+                                const int kind = a.mesh.face_kind[2 * d + side];
+                                if (en < 0 && kind == BGK_FK_CLOSED) { FI[side] = 0.0; continue; }
+                                if (un > 0.0) { FI[side] = un * fm; continue; }
+                                double fp = 0.0;
+                                // the neighbour's trace on the shared face: l(+1) of the left one, l(-1) of the right
+                                if (en >= e0 && en < e0 + EB) {
+                                    const double *nb = sfc + (en - e0) * NS + base[d];
+#pragma unroll
+                                    for (int j = 0; j < Q; ++j) fp = fma(sl[side][j], nb[j * stride[d]], fp);
+                                } else if (en >= 0) {
+                                    const double *nb = fs + (size_t)en * NS + base[d];
+#pragma unroll
+                                    for (int j = 0; j < Q; ++j) fp = fma(sl[side][j], __ldg(nb + j * stride[d]), fp);
+                                } else {
+                                    fp = __ldg(a.bcval + ((size_t)(2 * d + side) * C + c) * a.Nu + k);
+                                    if (kind == BGK_FK_DIFFUSE) {
+                                        const int fpi = d == 0 ? id[1] + Q * id[2] : (d == 1 ? id[0] + Q * id[2] : id[0] + Q * id[1]);
+                                        fp *= __ldg(a.rho_w + ((size_t)e * 6 + 2 * d + side) * Q * Q + fpi);
+                                    }
+                                }
+                                FI[side] = un * fp;
+                            }
+                            const double JR = FI[1] - trR, JL = -FI[0] - trL;
+                            div += fma(JR, sdg[1][id[d]], fma(JL, sdg[0][id[d]], dF));
+                        }
+                        div *= invJ;
+                    } else {
 #pragma unroll
                     for (int d = 0; d < 3; ++d) {
                         const int side = u[d] > 0.0 ? 0 : 1;
@@ -207,6 +309,7 @@ __global__ void __launch_bounds__(256) k_stage_f64(StageArgs<double> a) {
                         }
                         t = fma(sdg[side][id[d]], fp, t);
                         div = fma(sc[d], t, div);
+                    }
                     }
                     const double eqv = (c == 0) ? g : gfac * g;
                     const double R = fma(eqv - fself[c], itau, -div);
@@ -271,8 +374,13 @@ template <int Q>
 static cudaError_t stage_q(const StageArgs<double> &a, int C, int n_vblk, cudaStream_t s) {
     constexpr int NS = Q * Q * Q, EB = 256 / NS;
     dim3 grid((a.mesh.Ne + EB - 1) / EB, n_vblk);
-    if (C == 1) k_stage_f64<Q, 1><<<grid, EB * NS, 0, s>>>(a);
-    else k_stage_f64<Q, 2><<<grid, EB * NS, 0, s>>>(a);
+    if (a.geo) {
+        if (C == 1) k_stage_f64<Q, 1, true><<<grid, EB * NS, 0, s>>>(a);
+        else k_stage_f64<Q, 2, true><<<grid, EB * NS, 0, s>>>(a);
+    } else {
+        if (C == 1) k_stage_f64<Q, 1, false><<<grid, EB * NS, 0, s>>>(a);
+        else k_stage_f64<Q, 2, false><<<grid, EB * NS, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -43,9 +43,10 @@ def test_descriptor_layout_matches_header(tmp_path):
 #include <stddef.h>
 #include "bgk.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(bgk_mesh_desc), offsetof(bgk_mesh_desc, lo),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(bgk_mesh_desc), offsetof(bgk_mesh_desc, lo),
          offsetof(bgk_mesh_desc, hi), offsetof(bgk_mesh_desc, periodic),
-         offsetof(bgk_mesh_desc, order), offsetof(bgk_mesh_desc, bc_state), offsetof(bgk_mesh_desc, face_type));
+         offsetof(bgk_mesh_desc, order), offsetof(bgk_mesh_desc, bc_state), offsetof(bgk_mesh_desc, face_type),
+         offsetof(bgk_mesh_desc, node_xyz));
   printf("%zu %zu %zu\\n", sizeof(bgk_vgrid_desc), offsetof(bgk_vgrid_desc, lo),
          offsetof(bgk_vgrid_desc, hi));
   printf("%zu %zu\\n", sizeof(bgk_gas_desc), offsetof(bgk_gas_desc, theta_S));
@@ -57,7 +58,7 @@ int main(void) {
     out = [list(map(int, l.split())) for l in subprocess.check_output([str(exe)]).decode().splitlines()]
     M = bgk.MeshDesc
     assert out[0] == [ctypes.sizeof(M), M.lo.offset, M.hi.offset, M.periodic.offset,
-                      M.order.offset, M.bc_state.offset, M.face_type.offset]
+                      M.order.offset, M.bc_state.offset, M.face_type.offset, M.node_xyz.offset]
     V = bgk.VGridDesc
     assert out[1] == [ctypes.sizeof(V), V.lo.offset, V.hi.offset]
     assert out[2] == [ctypes.sizeof(bgk.GasDesc), bgk.GasDesc.theta_S.offset]
@@ -82,3 +83,39 @@ def test_invalid_descriptors_rejected_on_the_host(libbgk):
             bgk.Solver(wl)
         assert ei.value.status == bgk.BGK_EINVAL
         assert str(ei.value)
+
+
+def test_curvilinear_descriptors_rejected_on_the_host(libbgk):
+    """Curvilinear and wall descriptors are validated before any CUDA call: a
+    mesh with a non-positive Jacobian (one element's node order mirrored), a
+    diffuse wall without a positive temperature, an unknown face type give
+    BGK_EINVAL; specular faces on the curvilinear path give BGK_ENOTSUP."""
+    import numpy as np
+    import pytest
+    from paper_2312_06567_gb300 import workloads as W
+    wl = W.wavy_periodic_box(p=2, n=(2, 2, 2), vel_n=(4, 4, 4))
+    x = np.ascontiguousarray(W.node_positions(wl))
+    x6 = x.reshape(wl.n_elem, 3, 3, 3, 3)
+    x6[1] = x6[1][:, :, ::-1].copy()                     # mirror element 1 along xi_1: J < 0
+    m, v, g = bgk.descriptors(wl, x)
+    lib = bgk.load()
+    h = ctypes.c_void_p()
+    st = lib.bgk_create(ctypes.byref(h), ctypes.byref(m), ctypes.byref(v), ctypes.byref(g), bgk.BGK_FP64, None)
+    msg = lib.bgk_last_error(h).decode()
+    lib.bgk_destroy(h)
+    assert st == bgk.BGK_EINVAL and "Jacobian" in msg
+    chan = wl.replace(periodic=(False, True, True), diffuse={(0, -1): ((0, 0, 0), 0.0), (0, 1): ((0, 0, 0), 1.0)})
+    with pytest.raises(bgk.BGKError) as ei:
+        bgk.Solver(chan)
+    assert ei.value.status == bgk.BGK_EINVAL
+    spec = W.normal_shock_tube().replace(dirichlet={(0, 1): (1.0, (1, 0, 0), 1.0)}, specular=((0, -1),),
+                                         diffuse={}, closed=(), vel_lo=(-9.0, -8.0, -8.0), vel_hi=(9.0, 8.0, 8.0))
+    for variant in (spec.replace(closed=((0, 1),), dirichlet={}), spec.replace(mapping=W._wavy(0.0))):
+        with pytest.raises(bgk.BGKError) as ei:
+            bgk.Solver(variant)
+        assert ei.value.status == bgk.BGK_ENOTSUP
+    m, v, g = bgk.descriptors(W.normal_shock_tube())
+    m.face_type[0] = 4
+    st = lib.bgk_create(ctypes.byref(h), ctypes.byref(m), ctypes.byref(v), ctypes.byref(g), bgk.BGK_FP64, None)
+    lib.bgk_destroy(h)
+    assert st == bgk.BGK_EINVAL
