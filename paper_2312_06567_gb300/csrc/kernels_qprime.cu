@@ -993,11 +993,22 @@ __global__ void __launch_bounds__(QB * QW, 2) k_qprime(QPrimeArgs a) {
                 if (ex) exact_low_moments(a.vg, ps, S.Jm[lane], low);
                 // the residual first; the Jacobian only if an update may follow
                 const double res = assemble(S.M[lane], ps, a.gas, x, A, R, nullptr, ex ? low : nullptr);
-                if (!(res <= tol)) assemble(S.M[lane], ps, a.gas, x, A, R, J, ex ? low : nullptr);
+                // the FP32-sum engine evaluates the equilibrium at U' rounded to
+                // FP32, whose spacing 2^-23 |U'| bounds the reachable momentum
+                // residual |R_rhoU| / (rho sqrt(theta')): at high speed (|U'| of
+                // tens of thermal speeds) that floor exceeds tol32, so the engine
+                // stops at a few spacings (the exact moment correction that
+                // follows closes the remaining residual)
+                double tol_pt = tol;
+                if (F32) {
+                    const double um = fmax(fabs(x[1]), fmax(fabs(x[2]), fabs(x[3])));
+                    tol_pt = fmax(tol, 8.0 * 0x1p-24 * um / sqrt(fmax(x[4], 1e-300)));
+                }
+                if (!(res <= tol_pt)) assemble(S.M[lane], ps, a.gas, x, A, R, J, ex ? low : nullptr);
                 S.res[lane] = res;
                 int it = S.it[lane];
                 act = true;
-                if (res <= tol) {
+                if (res <= tol_pt) {
                     S.conv[lane] = 1;
                     act = false;
                 } else if (S.from_guess[lane] && ((it == 0 && !(res <= 1e-3)) || it >= a.max_iter || !(res == res))) {
