@@ -68,9 +68,15 @@ def _ogrid_small():
     return W.sphere_ogrid(n=(6, 12, 12))
 
 
+def _ogrid_tiny():
+    """4x8x8 elements (1.3e8 DOF, 3 GB of state): a small case for full ncu captures."""
+    return W.sphere_ogrid(n=(4, 8, 8))
+
+
 WORKLOADS = {"taylor_green": W.taylor_green_box, "taylor_green_8x8x4": _tg_small,
              "normal_shock": _shock, "sine_box": W.periodic_sine_box,
-             "sphere_ogrid": W.sphere_ogrid, "sphere_ogrid_6x12x12": _ogrid_small}
+             "sphere_ogrid": W.sphere_ogrid, "sphere_ogrid_6x12x12": _ogrid_small,
+             "sphere_ogrid_4x8x8": _ogrid_tiny}
 
 
 def _sample_mesh(wl):
