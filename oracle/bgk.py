@@ -32,6 +32,19 @@ theta'); Pi/rho is that of f and held fixed; T'(theta') = theta'/Pr I +
 so mass, momentum and total energy of (F, G) are conserved exactly by the
 source.  tau is computed from the state of f (not of Q').
 
+Tensor variant (the paper's remark that ES-BGK may need a nonlinear solve of
+marginally higher dimension when the velocity grid lacks symmetry, section
+"Numerical method"; a reading, monatomic gas): the equilibrium is the
+discrete Gaussian g = exp(b0 + b.c + sum_{i<=j} b_ij c_i c_j), c = u - U, whose
+discrete moments against phi = (1, c, c_i c_j (i <= j)) equal (rho, 0, rho T)
+with T the ES target tensor above: 10 unknowns and 10 equations.  The trace
+of the second-moment rows is the energy, so mass, momentum and energy are
+conserved, and the discrete stress of g equals rho T exactly (the d+2 solve
+above matches only its trace).  Newton on the natural parameters b, whose
+Jacobian sum w phi phi^T g is symmetric positive definite (the equations are
+the gradient of the strictly convex sum w exp(b.phi) - b.(rho, 0, rho T)),
+so the solution is unique.
+
 Moment slots (11, shared with the C-ABI layout of raw moments):
     0: sum w F      1..3: sum w u_d F     4..6: sum w u_d^2 F
     7: sum w u1 u2 F  8: sum w u1 u3 F  9: sum w u2 u3 F   10: sum w G
@@ -47,9 +60,12 @@ class Gas:
     theta_S < 0 selects a constant viscosity mu = mu_ref.
     """
 
-    def __init__(self, delta=0.0, Pr=1.0, mu_ref=0.1, theta_ref=1.0, theta_S=-1.0):
+    def __init__(self, delta=0.0, Pr=1.0, mu_ref=0.1, theta_ref=1.0, theta_S=-1.0, es_tensor=False):
         if delta < 0:
             raise ValueError("delta must be >= 0")
+        if es_tensor and delta > 0:
+            raise ValueError("the tensor variant is for a monatomic gas (delta = 0)")
+        self.es_tensor = bool(es_tensor)
         self.delta = float(delta)
         self.Pr = float(Pr)
         self.mu_ref = float(mu_ref)
@@ -226,6 +242,102 @@ def solve_qprime(m, gas, vg, guess=None, tol=1e-13, max_iter=50):
     return x, iters, done, res
 
 
+# phi = (1, c1, c2, c3, c1^2, c2^2, c3^2, c1 c2, c1 c3, c2 c3) as exponents (p1, p2, p3)
+TENSOR_PHI = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 0, 0), (0, 2, 0), (0, 0, 2),
+              (1, 1, 0), (1, 0, 1), (0, 1, 1)]
+
+
+def _phi(c):
+    """phi[10, Nu, P] of c[Nu, P, 3]."""
+    return np.stack([c[..., 0] ** a * c[..., 1] ** b * c[..., 2] ** d for a, b, d in TENSOR_PHI])
+
+
+def tensor_targets(m, gas):
+    """(rho, 0, rho T_ij) per point [P, 10] in the frame c = u - U, the centre U."""
+    rho, U, E, theta, pres, Pi = macroscopic(m, gas)
+    T = temperature_tensor(theta, Pi / rho[:, None, None], gas.Pr)
+    t = np.zeros((len(rho), 10))
+    t[:, 0] = rho
+    for a, (i, j) in enumerate(PAIRS):
+        t[:, 4 + a] = rho * T[:, i, j]
+    return t, U, rho, theta
+
+
+def tensor_residual(b, t, U, vg):
+    """R = sum_k w phi g - t and J = sum_k w phi phi^T g for natural parameters b[P, 10]."""
+    c = vg.u[:, None, :] - U[None, :, :]                  # [Nu, P, 3]
+    ph = _phi(c)                                         # [10, Nu, P]
+    g = np.exp(np.einsum("pa,akp->kp", b, ph))
+    wg = vg.w[:, None] * g
+    R = np.einsum("akp,kp->pa", ph, wg) - t
+    J = np.einsum("akp,bkp,kp->pab", ph, ph, wg)
+    return R, J, g
+
+
+def _tensor_params(b):
+    """(A = T'^-1 [P,3,3], spd[P]) of the quadratic part of b."""
+    A = np.zeros((len(b), 3, 3))
+    for a, (i, j) in enumerate(PAIRS):
+        if i == j:
+            A[:, i, i] = -2.0 * b[:, 4 + a]
+        else:
+            A[:, i, j] = A[:, j, i] = -b[:, 4 + a]
+    return A, _spd(A)
+
+
+def solve_qprime_tensor(m, gas, vg, tol=1e-13, max_iter=50):
+    """Newton on the natural parameters of the tensor variant, from the
+    continuous Gaussian (rho, U, T) of f.  Returns (b[P,10], U[P,3], iters,
+    converged, final scaled residual); the scaled residual is
+    max(|R_0|/rho, |R_c|_inf/(rho sqrt(theta)), |R_cc|_inf/(rho theta)).  A
+    step is halved while the quadratic form would not be negative definite."""
+    t, U, rho, theta = tensor_targets(m, gas)
+    T = np.zeros((len(rho), 3, 3))
+    for a, (i, j) in enumerate(PAIRS):
+        T[:, i, j] = T[:, j, i] = t[:, 4 + a] / rho
+    A = np.linalg.inv(T)
+    b = np.zeros((len(rho), 10))
+    b[:, 0] = np.log(rho / np.sqrt(np.linalg.det(2.0 * np.pi * T)))
+    for a, (i, j) in enumerate(PAIRS):
+        b[:, 4 + a] = -0.5 * A[:, i, i] if i == j else -A[:, i, j]
+    P = len(rho)
+    iters = np.zeros(P, dtype=np.int64)
+    done = np.zeros(P, dtype=bool)
+    res = np.full(P, np.inf)
+    for it in range(max_iter + 1):
+        act = np.nonzero(~done)[0]
+        if len(act) == 0:
+            break
+        R, J, _ = tensor_residual(b[act], t[act], U[act], vg)
+        r = np.maximum.reduce([np.abs(R[:, 0]) / rho[act],
+                               np.max(np.abs(R[:, 1:4]), axis=1) / (rho[act] * np.sqrt(theta[act])),
+                               np.max(np.abs(R[:, 4:]), axis=1) / (rho[act] * theta[act])])
+        res[act] = r
+        conv = r <= tol
+        done[act[conv]] = True
+        if it == max_iter:
+            break
+        upd = act[~conv]
+        if len(upd) == 0:
+            break
+        db = np.linalg.solve(J[~conv], -R[~conv][:, :, None])[:, :, 0]
+        lam = np.ones(len(upd))
+        for _ in range(60):
+            _, ok = _tensor_params(b[upd] + lam[:, None] * db)
+            if np.all(ok):
+                break
+            lam = np.where(ok, lam, 0.5 * lam)
+        b[upd] = b[upd] + lam[:, None] * db
+        iters[upd] += 1
+    return b, U, iters, done, res
+
+
+def tensor_equilibrium(b, U, vg):
+    """g[Nu, P] = exp(b . phi(u - U))."""
+    c = vg.u[:, None, :] - U[None, :, :]
+    return np.exp(np.einsum("pa,akp->kp", b, _phi(c)))
+
+
 def equilibrium(qp, m, gas, vg):
     """F_eq = g_u(q'), G_eq = (delta theta'/2) g_u(q'), each [Nu, P]."""
     rho, U, E, theta, pres, Pi = macroscopic(m, gas)
@@ -246,6 +358,12 @@ def bgk_source(F, G, gas, vg, guess=None, tol=1e-13, max_iter=50):
     m = raw_moments(F, G, vg)
     rho, U, E, theta, pres, Pi = macroscopic(m, gas)
     tau = collision_time(theta, pres, gas)
+    if gas.es_tensor:
+        b, Uc, iters, conv, res = solve_qprime_tensor(m, gas, vg, tol=tol, max_iter=max_iter)
+        g = tensor_equilibrium(b, Uc, vg)
+        S_F = (g - F) / tau[None, :]
+        info = dict(b=b, iters=iters, converged=conv, residual=res, tau=tau, m=m)
+        return S_F, None, info
     qp, iters, conv, res = solve_qprime(m, gas, vg, guess=guess, tol=tol, max_iter=max_iter)
     g, Gg = equilibrium(qp, m, gas, vg)
     S_F = (g - F) / tau[None, :]

@@ -311,6 +311,7 @@ def problem_from_workload(wl, x, exterior=None):
     from .velocity import VelocityGrid
     mesh = CurvedMesh(wl.mesh_n, wl.periodic, x, wl.p)
     vg = VelocityGrid(wl.vel_n, wl.vel_lo, wl.vel_hi)
-    gas = bgk.Gas(delta=wl.delta, Pr=wl.Pr, mu_ref=wl.mu_ref, theta_ref=wl.theta_ref, theta_S=wl.theta_S)
+    gas = bgk.Gas(delta=wl.delta, Pr=wl.Pr, mu_ref=wl.mu_ref, theta_ref=wl.theta_ref, theta_S=wl.theta_S,
+                  es_tensor=getattr(wl, "es_tensor", False))
     return CurvedProblem(mesh, vg, gas, dirichlet=wl.dirichlet, diffuse=getattr(wl, "diffuse", {}),
                          closed=getattr(wl, "closed", ()), exterior=exterior)

@@ -225,6 +225,7 @@ def problem_from_workload(wl, exterior=None):
     mesh = BoxMesh(wl.mesh_n, wl.mesh_lo, wl.mesh_hi, wl.periodic)
     vg = VelocityGrid(wl.vel_n, wl.vel_lo, wl.vel_hi)
     gas = bgk.Gas(delta=wl.delta, Pr=wl.Pr, mu_ref=wl.mu_ref, theta_ref=wl.theta_ref,
-                  theta_S=wl.theta_S)
+                  theta_S=wl.theta_S,
+                  es_tensor=getattr(wl, "es_tensor", False))
     return Problem(mesh, wl.p, vg, gas, dirichlet=wl.dirichlet, exterior=exterior,
                    specular=getattr(wl, "specular", ()))

@@ -69,6 +69,7 @@ class Workload:
     diffuse: dict = field(default_factory=dict)     # {(d, side): (U_w(3), theta_w)} diffuse walls
     closed: tuple = ()                      # ((d, side), ...) collapsed faces (no flux)
     h_min_override: float = None            # smallest node spacing of a curvilinear mesh
+    es_tensor: bool = False                 # ES equilibrium matching the full target stress (delta = 0)
 
     @property
     def n_elem(self):
