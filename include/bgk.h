@@ -157,6 +157,22 @@ BGK_API bgk_status bgk_set_maxwellian(bgk_ctx *ctx, const double *q, int on_devi
  * of graphs; this is the launch mechanism only. */
 BGK_API bgk_status bgk_set_graphs(bgk_ctx *ctx, int enable);
 
+/* Tensor variant of the discrete ES equilibrium (section "Numerical method":
+ * ES-BGK may need a nonlinear solve of marginally higher dimension when the
+ * velocity grid lacks symmetry).  enable = 1: after the d+2 solve, each
+ * point's equilibrium is refined to the discrete Gaussian
+ * exp(b . phi(u - U)), phi = (1, u - U, (u_i - U_i)(u_j - U_j), i <= j), whose
+ * discrete moments are (rho, 0, rho T) with T = theta/Pr I + (1 - 1/Pr) Pi/rho
+ * the ES target: ten unknowns, Newton on b (symmetric positive definite
+ * Jacobian, unique solution).  Mass, momentum and energy stay conserved and
+ * the discrete stress of the equilibrium is rho T exactly (the d+2 solve
+ * matches only its trace).  The Newton statistics (bgk_stats) then count the
+ * refinement's updates; no training pairs are logged.  bgk_qprime keeps
+ * returning the d+2 solution.  Default 0.
+ * Errors: BGK_EINVAL; BGK_ENOTSUP for delta > 0 (a reading for the
+ * monatomic gas only). */
+BGK_API bgk_status bgk_set_es_tensor(bgk_ctx *ctx, int enable);
+
 /* Newton controls of the Q' solve: stop when the scaled residual
  * max(|R_rho|/rho, |R_rhoU|_inf/(rho sqrt(theta)), |R_E|/E) <= tol, at most
  * max_iter updates (defaults 1e-13, 50). */

@@ -44,6 +44,7 @@ SIGNATURES = {
     "bgk_destroy": (c_int, [c_void_p]),
     "bgk_sizes": (c_int, [c_void_p] + [ctypes.POINTER(c_int)] * 4),
     "bgk_node_coords": (c_int, [c_void_p, c_void_p, c_int]),
+    "bgk_set_es_tensor": (c_int, [c_void_p, c_int]),
     "bgk_set_state": (c_int, [c_void_p, c_void_p, c_int]),
     "bgk_get_state": (c_int, [c_void_p, c_void_p, c_int]),
     "bgk_set_maxwellian": (c_int, [c_void_p, c_void_p, c_int]),
@@ -205,6 +206,8 @@ class Solver:
                                        ctypes.byref(nu), ctypes.byref(nc)))
         self.n_elem, self.n_sol, self.n_vel, self.n_comp = ne.value, ns.value, nu.value, nc.value
         self.dtype = np.float64 if precision == BGK_FP64 else np.float32
+        if getattr(wl, "es_tensor", False):
+            self.set_es_tensor(True)
 
     @property
     def shape(self):
@@ -241,6 +244,9 @@ class Solver:
         p, dev = _ptr(x)
         self._check(self.lib.bgk_node_coords(self._h, p, dev))
         return x
+
+    def set_es_tensor(self, enable=True):
+        self._check(self.lib.bgk_set_es_tensor(self._h, 1 if enable else 0))
 
     def set_state(self, f):
         if isinstance(f, np.ndarray):

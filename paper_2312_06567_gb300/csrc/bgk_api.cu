@@ -56,6 +56,7 @@ struct bgk_ctx {
     double tol;
     int max_iter;
     int qp_fp32;                      // Q' velocity sums on the FP32 pipe (mixed form default)
+    int es_tensor;                    // tensor variant of the discrete ES equilibrium (delta = 0)
     int stage_variant, stage_depth;   // FP32 stage kernel choice and copy-ring depth
     // CUDA graphs of one SSP-RK3 step, one per buffer parity (f[0] alternates
     // between two buffers); recaptured when a launch parameter changes
@@ -261,6 +262,17 @@ bgk_status run_qprime(bgk_ctx *ctx, const double *part, int n_vblk, int P, doubl
     a.log = ctx->log_on ? ctx->log : nullptr;
     a.log_count = ctx->log_count; a.log_max = ctx->log_max; a.fallbacks = ctx->fallbacks;
     LaunchScope ls(ctx, BGK_K_QPRIME);
+    if (ctx->es_tensor && a.eq) {
+        // the d+2 solve gives the start; the refinement records the statistics
+        QPrimeArgs a5 = a;
+        a5.stats = nullptr;
+        a5.log = nullptr;
+        a5.eq32 = nullptr;
+        CU(launch_qprime(a5, ctx->qp_fp32 != 0, ctx->stream));
+        a.log = nullptr;
+        CU(launch_qprime_tensor(a, ctx->qp_fp32 != 0, ctx->stream));
+        return BGK_OK;
+    }
     CU(launch_qprime(a, ctx->qp_fp32 != 0, ctx->stream));
     return BGK_OK;
 }
@@ -390,7 +402,8 @@ std::vector<double> step_signature(const bgk_ctx *ctx, double dt) {
             (double)ctx->log_max,
             (double)ctx->stage_variant,
             (double)ctx->stage_depth,
-            (double)ctx->qp_fp32};
+            (double)ctx->qp_fp32,
+            (double)ctx->es_tensor};
 }
 
 void drop_graphs(bgk_ctx *ctx) {
@@ -515,6 +528,7 @@ bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
     ctx->tol = 1e-13;
     ctx->max_iter = 50;
     ctx->qp_fp32 = precision == BGK_MIXED ? 1 : 0;
+    ctx->es_tensor = 0;
     ctx->stage_variant = BGK_STAGE_AUTO;
     ctx->stage_depth = 6;
     ctx->graphs_on = false;
@@ -834,6 +848,14 @@ bgk_status bgk_set_qprime_engine(bgk_ctx *ctx, int fp32_sums) {
     if (fp32_sums && ctx->precision != BGK_MIXED)
         return fail(ctx, BGK_EINVAL, "FP32 Q' sums are for the mixed form only");
     ctx->qp_fp32 = fp32_sums ? 1 : 0;
+    return BGK_OK;
+}
+
+bgk_status bgk_set_es_tensor(bgk_ctx *ctx, int enable) {
+    if (!ctx) return BGK_EINVAL;
+    if (enable && ctx->C != 1)
+        return fail(ctx, BGK_ENOTSUP, "the tensor variant of the ES equilibrium is for a monatomic gas (delta = 0)");
+    ctx->es_tensor = enable ? 1 : 0;
     return BGK_OK;
 }
 

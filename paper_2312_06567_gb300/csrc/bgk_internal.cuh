@@ -235,6 +235,8 @@ cudaError_t launch_wall_density(const T *f, const T *fvec, const double *bcval, 
 // Launchers (kernels_f64.cu).
 cudaError_t launch_moments_f64(const MomentArgs64 &a, int n_vblk, cudaStream_t s);
 cudaError_t launch_qprime(const QPrimeArgs &a, bool fp32_sums, cudaStream_t s);
+// tensor variant of the ES equilibrium: refines the eq record k_qprime wrote
+cudaError_t launch_qprime_tensor(const QPrimeArgs &a, bool fp32_sums, cudaStream_t s);
 cudaError_t launch_stage_f64(const StageArgs<double> &a, int C, int n_vblk, cudaStream_t s);
 cudaError_t launch_maxwellian_f64(double *f, const double *q, const double *vtab, int Nu, int P,
                                   int C, double delta, cudaStream_t s);

@@ -1070,6 +1070,242 @@ __global__ void __launch_bounds__(QB * QW, 2) k_qprime(QPrimeArgs a) {
 
 }  // namespace
 
+// ---- tensor variant of the discrete ES equilibrium (monatomic) -------------
+// The discrete Gaussian g = exp(b . phi(ut)), ut = u - U (the point's
+// velocity), phi = (1, ut, ut_i ut_j (i <= j)), whose discrete moments are
+// (rho, 0, rho T) with T = theta/Pr I + (1 - 1/Pr) Pi/rho the ES target: the
+// paper's remark that ES-BGK may need a solve of marginally higher dimension
+// (section "Numerical method").  Newton on the ten natural parameters b from
+// the d+2 solution's record (written by k_qprime): R = sum w phi g - t and
+// J = sum w phi phi^T g are the centred moments of order <= 4 that the
+// velocity-sum engines already produce.  One warp per point; the 10x10
+// algebra on lane 0.  The mixed form then fits its FP32-equilibrium
+// correction as k_qprime does.
+
+// exponents (p1, p2, p3) of phi_a: 1, ut1, ut2, ut3, ut1^2, ut2^2, ut3^2, ut1 ut2, ut1 ut3, ut2 ut3
+__device__ __forceinline__ void tensor_phi(int a, int &p1, int &p2, int &p3) {
+    const int e1[10] = {0, 1, 0, 0, 2, 0, 0, 1, 1, 0};
+    const int e2[10] = {0, 0, 1, 0, 0, 2, 0, 1, 0, 1};
+    const int e3[10] = {0, 0, 0, 1, 0, 0, 2, 0, 1, 1};
+    p1 = e1[a]; p2 = e2[a]; p3 = e3[a];
+}
+
+// Gaussian elimination with partial pivoting, N x N, compile-time indices.
+template <int N>
+__device__ __forceinline__ bool solve_n(double (&J)[N][N], double (&r)[N]) {
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+        int piv = c;
+        double best = fabs(J[c][c]);
+#pragma unroll
+        for (int i = c + 1; i < N; ++i) {
+            const double v = fabs(J[i][c]);
+            if (v > best) { best = v; piv = i; }
+        }
+        if (!(best > 0.0)) return false;
+#pragma unroll
+        for (int i = c + 1; i < N; ++i) {
+            if (i == piv) {
+#pragma unroll
+                for (int j = 0; j < N; ++j) {
+                    const double t = J[c][j]; J[c][j] = J[i][j]; J[i][j] = t;
+                }
+                const double t = r[c]; r[c] = r[i]; r[i] = t;
+            }
+        }
+        const double inv = 1.0 / J[c][c];
+#pragma unroll
+        for (int i = c + 1; i < N; ++i) {
+            const double l = J[i][c] * inv;
+#pragma unroll
+            for (int j = c + 1; j < N; ++j) J[i][j] = fma(-l, J[c][j], J[i][j]);
+            r[i] = fma(-l, r[c], r[i]);
+        }
+    }
+#pragma unroll
+    for (int c = N - 1; c >= 0; --c) {
+        double sacc = r[c];
+#pragma unroll
+        for (int j = c + 1; j < N; ++j) sacc = fma(-J[c][j], r[j], sacc);
+        r[c] = sacc / J[c][c];
+    }
+    return true;
+}
+
+// (c0, U', A) <-> natural parameters b in the frame ut = u - U0
+__device__ __forceinline__ void tensor_to_b(const PointState &ps, double c0, const double U[3], const Sym3 &A,
+                                            double b[10]) {
+    const double ur[3] = {U[0] - ps.U0[0], U[1] - ps.U0[1], U[2] - ps.U0[2]};
+    const double au[3] = {A.t11 * ur[0] + A.t12 * ur[1] + A.t13 * ur[2], A.t12 * ur[0] + A.t22 * ur[1] + A.t23 * ur[2],
+                          A.t13 * ur[0] + A.t23 * ur[1] + A.t33 * ur[2]};
+    b[0] = c0 - 0.5 * (ur[0] * au[0] + ur[1] * au[1] + ur[2] * au[2]);
+    b[1] = au[0]; b[2] = au[1]; b[3] = au[2];
+    b[4] = -0.5 * A.t11; b[5] = -0.5 * A.t22; b[6] = -0.5 * A.t33;
+    b[7] = -A.t12; b[8] = -A.t13; b[9] = -A.t23;
+}
+
+__device__ __forceinline__ bool tensor_from_b(const PointState &ps, const double b[10], double &c0, double U[3],
+                                              Sym3 &A) {
+    A = Sym3{-2.0 * b[4], -2.0 * b[5], -2.0 * b[6], -b[7], -b[8], -b[9]};
+    Sym3 T;
+    double det;
+    if (!sym3_inverse(A, T, det)) return false;
+    const double ur[3] = {T.t11 * b[1] + T.t12 * b[2] + T.t13 * b[3], T.t12 * b[1] + T.t22 * b[2] + T.t23 * b[3],
+                          T.t13 * b[1] + T.t23 * b[2] + T.t33 * b[3]};
+    c0 = b[0] + 0.5 * (b[1] * ur[0] + b[2] * ur[1] + b[3] * ur[2]);
+    U[0] = ps.U0[0] + ur[0]; U[1] = ps.U0[1] + ur[1]; U[2] = ps.U0[2] + ur[2];
+    return true;
+}
+
+struct TensorShared {
+    PointState ps[QW];
+    double par[QW][10];       // c0, U'(3), A(6)
+    double M[QW][35];
+    int go[QW];
+};
+
+template <bool F32>
+__global__ void __launch_bounds__(QW * 32) k_qprime_tensor(QPrimeArgs a) {
+    __shared__ TensorShared S;
+    __shared__ float su1[BGK_MAXV];
+    extern __shared__ double dyn_tab[];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int j = threadIdx.x; j < a.vg.n[0]; j += blockDim.x) su1[j] = __ldg(a.vtab32 + j).x;
+    __syncthreads();
+    const int p = blockIdx.x * QW + wib;
+    if (p >= a.P) return;                       // whole warps; no block barrier follows
+    PointState &ps = S.ps[wib];
+    if (lane == 0) point_prologue(a, p, ps);
+    __syncwarp();
+    // targets in the frame ut = u - U0, and the start: the d+2 solution's record
+    double t[10], b[10];
+    double res = 1.0e300;
+    int it = 0;
+    bool conv = false;
+    if (lane == 0) {
+        const double ip = 1.0 / a.gas.Pr;
+        t[0] = ps.m[0];
+        t[1] = ps.m[1] - ps.U0[0] * ps.m[0];
+        t[2] = ps.m[2] - ps.U0[1] * ps.m[0];
+        t[3] = ps.m[3] - ps.U0[2] * ps.m[0];
+        const double rt = ps.rho * ps.theta * ip;
+        t[4] = fma(ps.rho, ps.B.t11, rt); t[5] = fma(ps.rho, ps.B.t22, rt); t[6] = fma(ps.rho, ps.B.t33, rt);
+        t[7] = ps.rho * ps.B.t12; t[8] = ps.rho * ps.B.t13; t[9] = ps.rho * ps.B.t23;
+        const double *q = a.eq + (size_t)p * BGK_NEQ;
+#pragma unroll
+        for (int j = 0; j < 10; ++j) S.par[wib][j] = q[j];
+        const Sym3 A0{q[4], q[5], q[6], q[7], q[8], q[9]};
+        const double U[3] = {q[1], q[2], q[3]};
+        tensor_to_b(ps, q[0], U, A0, b);
+    }
+    __syncwarp();
+    Engine64 e64;
+    if (!F32) e64.init(reinterpret_cast<double (*)[5]>(dyn_tab + (size_t)wib * a.vg.n[0] * 5), a.vg, ps, lane);
+    for (;;) {
+        const double *pr = S.par[wib];
+        const Sym3 A{pr[4], pr[5], pr[6], pr[7], pr[8], pr[9]};
+        const double x[5] = {0.0, pr[1], pr[2], pr[3], 0.0};
+        double M[35];
+        if (F32) {
+            Engine32 e32;
+            e32.moments(a.vg, ps, x, A, pr[0], lane, M);
+        } else {
+            e64.moments(a.vg, ps, x, A, pr[0], lane, M);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int j = 0; j < 35; ++j) S.M[wib][j] = M[j];
+            double R[10], J[10][10];
+#pragma unroll
+            for (int i = 0; i < 10; ++i) {
+                int a1, a2, a3;
+                tensor_phi(i, a1, a2, a3);
+                R[i] = M[midx(a1, a2, a3)] - t[i];
+#pragma unroll
+                for (int j = 0; j < 10; ++j) {
+                    int b1, b2, b3;
+                    tensor_phi(j, b1, b2, b3);
+                    J[i][j] = M[midx(a1 + b1, a2 + b2, a3 + b3)];
+                }
+            }
+            const double sq = 1.0 / (ps.rho * ps.theta);
+            res = fabs(R[0]) * ps.sc_rho;
+#pragma unroll
+            for (int i = 1; i < 4; ++i) res = fmax(res, fabs(R[i]) * ps.sc_mom);
+#pragma unroll
+            for (int i = 4; i < 10; ++i) res = fmax(res, fabs(R[i]) * sq);
+            double tol = F32 ? a.tol32 : a.tol;
+            if (F32) {
+                const double um = fmax(fabs(pr[1]), fmax(fabs(pr[2]), fabs(pr[3])));
+                tol = fmax(tol, 8.0 * 0x1p-24 * um * sqrt(fmax(A.t11 + A.t22 + A.t33, 0.0) / 3.0));
+            }
+            bool go = false;
+            if (res <= tol) {
+                conv = true;
+            } else if (it < a.max_iter && res == res) {
+                double db[10];
+#pragma unroll
+                for (int i = 0; i < 10; ++i) db[i] = -R[i];
+                if (solve_n<10>(J, db)) {
+                    double lam = 1.0, bt[10], c0n = 0.0, Un[3];
+                    Sym3 An;
+                    bool ok = false;
+                    for (int h = 0; h < 60 && !ok; ++h) {
+#pragma unroll
+                        for (int i = 0; i < 10; ++i) bt[i] = fma(lam, db[i], b[i]);
+                        ok = tensor_from_b(ps, bt, c0n, Un, An);
+                        if (!ok) lam *= 0.5;
+                    }
+                    if (ok) {
+#pragma unroll
+                        for (int i = 0; i < 10; ++i) b[i] = bt[i];
+                        S.par[wib][0] = c0n;
+                        S.par[wib][1] = Un[0]; S.par[wib][2] = Un[1]; S.par[wib][3] = Un[2];
+                        S.par[wib][4] = An.t11; S.par[wib][5] = An.t22; S.par[wib][6] = An.t33;
+                        S.par[wib][7] = An.t12; S.par[wib][8] = An.t13; S.par[wib][9] = An.t23;
+                        ++it;
+                        go = true;
+                    }
+                }
+            }
+            S.go[wib] = go;
+        }
+        __syncwarp();
+        if (!S.go[wib]) break;
+    }
+    // the converged Gaussian: x = (rho', U', theta' = tr T'/3) for the record and qp
+    const double *pr = S.par[wib];
+    const Sym3 A{pr[4], pr[5], pr[6], pr[7], pr[8], pr[9]};
+    Sym3 T;
+    double detA;
+    sym3_inverse(A, T, detA);
+    double x[5];
+    x[0] = exp(pr[0]) * sqrt(kTwoPi * kTwoPi * kTwoPi / detA);
+    x[1] = pr[1]; x[2] = pr[2]; x[3] = pr[3];
+    x[4] = (T.t11 + T.t22 + T.t33) / 3.0;
+    double gam[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (a.mixed && a.eq) {
+        double Jm[7];
+        correction_sums(a, lane, pr[0], x, A, su1, Jm);
+        if (lane == 0) correction_fit(a, ps, x, Jm, S.M[wib], gam);
+    }
+    const int tot = __shfl_sync(0xffffffffu, it, 0);
+    const bool cv = __shfl_sync(0xffffffffu, (int)conv, 0) != 0;
+    const double rs = __shfl_sync(0xffffffffu, res, 0);
+    point_epilogue(a, p, lane == 0, ps, x, A, pr[0], gam, tot, cv, rs);
+}
+
+cudaError_t launch_qprime_tensor(const QPrimeArgs &a, bool fp32_sums, cudaStream_t s) {
+    const unsigned grid = (unsigned)((a.P + QW - 1) / QW);
+    if (fp32_sums) {
+        k_qprime_tensor<true><<<grid, QW * 32, 0, s>>>(a);
+    } else {
+        const size_t dyn = (size_t)QW * a.vg.n[0] * 5 * sizeof(double);
+        k_qprime_tensor<false><<<grid, QW * 32, dyn, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_qprime(const QPrimeArgs &a, bool fp32_sums, cudaStream_t s) {
     const unsigned grid = (unsigned)((a.P + QB - 1) / QB);
     if (fp32_sums) {
