@@ -315,3 +315,25 @@ def problem_from_workload(wl, x, exterior=None):
                   es_tensor=getattr(wl, "es_tensor", False))
     return CurvedProblem(mesh, vg, gas, dirichlet=wl.dirichlet, diffuse=getattr(wl, "diffuse", {}),
                          closed=getattr(wl, "closed", ()), exterior=exterior)
+
+
+def element_residual(p, vg, gas, x27, f27, with_source=False, guess=None, tol=1e-13, max_iter=50):
+    """R(f) = -div(u f) + S(f) of one curvilinear element from its 3x3x3 block.
+
+    x27[27, Ns, 3] are the node coordinates and f27[C, Nu, 27, Ns] the state of
+    the element (block index 13) and its neighbours in the order
+    e = i1 + 3 (i2 + 3 i3); the face vectors of the element's faces are the
+    averages over both sides as in the whole mesh, and the block's outer faces
+    see a zero exterior state, which affects the outer elements only.  Used to
+    check single elements of states too large for the whole-mesh routines.
+    Returns R[C, Nu, Ns] (and the source part S[C, Nu, Ns] with with_source)."""
+    mesh = CurvedMesh((3, 3, 3), (False, False, False), x27, p)
+    prob = CurvedProblem(mesh, vg, gas, exterior=lambda d, side, fm: np.zeros_like(fm))
+    div = prob.divergence(f27)[:, :, 13, :]
+    C = f27.shape[0]
+    F = f27[0, :, 13, :]
+    G = f27[1, :, 13, :] if C == 2 else None
+    S_F, S_G, _ = bgk.bgk_source(F, G, gas, vg, guess=guess, tol=tol, max_iter=max_iter)
+    S = np.stack([S_F] + ([S_G] if C == 2 else []))
+    R = S - div
+    return (R, S) if with_source else R

@@ -993,22 +993,26 @@ __global__ void __launch_bounds__(QB * QW, 2) k_qprime(QPrimeArgs a) {
                 if (ex) exact_low_moments(a.vg, ps, S.Jm[lane], low);
                 // the residual first; the Jacobian only if an update may follow
                 const double res = assemble(S.M[lane], ps, a.gas, x, A, R, nullptr, ex ? low : nullptr);
-                // the FP32-sum engine evaluates the equilibrium at U' rounded to
-                // FP32, whose spacing 2^-23 |U'| bounds the reachable momentum
-                // residual |R_rhoU| / (rho sqrt(theta')): at high speed (|U'| of
-                // tens of thermal speeds) that floor exceeds tol32, so the engine
-                // stops at a few spacings (the exact moment correction that
-                // follows closes the remaining residual)
-                double tol_pt = tol;
-                if (F32) {
+                // The exact residual of the mixed form measures the stage's FP32
+                // equilibrium, whose mean is U' rounded to FP32: its spacing
+                // 2^-23 |U'| bounds the reachable momentum residual
+                // |R_rhoU| / (rho sqrt(theta')).  At high speed (|U'| of tens of
+                // thermal speeds) that floor exceeds tol32, so the momentum rows
+                // stop at a few spacings -- the linear term of the exact moment
+                // correction that follows absorbs such a mean shift to first
+                // order -- while density and energy converge to tol32.
+                bool done = res <= tol;
+                if (F32 && !done) {
                     const double um = fmax(fabs(x[1]), fmax(fabs(x[2]), fabs(x[3])));
-                    tol_pt = fmax(tol, 8.0 * 0x1p-24 * um / sqrt(fmax(x[4], 1e-300)));
+                    const double tol_mom = fmax(tol, 8.0 * 0x1p-24 * um / sqrt(fmax(x[4], 1e-300)));
+                    done = fabs(R[0]) * ps.sc_rho <= tol && fabs(R[4]) * ps.sc_E <= tol &&
+                           fmax(fabs(R[1]), fmax(fabs(R[2]), fabs(R[3]))) * ps.sc_mom <= tol_mom;
                 }
-                if (!(res <= tol_pt)) assemble(S.M[lane], ps, a.gas, x, A, R, J, ex ? low : nullptr);
+                if (!done) assemble(S.M[lane], ps, a.gas, x, A, R, J, ex ? low : nullptr);
                 S.res[lane] = res;
                 int it = S.it[lane];
                 act = true;
-                if (res <= tol_pt) {
+                if (done) {
                     S.conv[lane] = 1;
                     act = false;
                 } else if (S.from_guess[lane] && ((it == 0 && !(res <= 1e-3)) || it >= a.max_iter || !(res == res))) {
@@ -1229,18 +1233,20 @@ __global__ void __launch_bounds__(QW * 32) k_qprime_tensor(QPrimeArgs a) {
                 }
             }
             const double sq = 1.0 / (ps.rho * ps.theta);
-            res = fabs(R[0]) * ps.sc_rho;
+            double r_mom = 0.0, r_oth = fabs(R[0]) * ps.sc_rho;
 #pragma unroll
-            for (int i = 1; i < 4; ++i) res = fmax(res, fabs(R[i]) * ps.sc_mom);
+            for (int i = 1; i < 4; ++i) r_mom = fmax(r_mom, fabs(R[i]) * ps.sc_mom);
 #pragma unroll
-            for (int i = 4; i < 10; ++i) res = fmax(res, fabs(R[i]) * sq);
-            double tol = F32 ? a.tol32 : a.tol;
-            if (F32) {
+            for (int i = 4; i < 10; ++i) r_oth = fmax(r_oth, fabs(R[i]) * sq);
+            res = fmax(r_mom, r_oth);
+            const double tol = F32 ? a.tol32 : a.tol;
+            double tol_mom = tol;
+            if (F32) {        // the momentum rows' FP32 floor, as in k_qprime
                 const double um = fmax(fabs(pr[1]), fmax(fabs(pr[2]), fabs(pr[3])));
-                tol = fmax(tol, 8.0 * 0x1p-24 * um * sqrt(fmax(A.t11 + A.t22 + A.t33, 0.0) / 3.0));
+                tol_mom = fmax(tol, 8.0 * 0x1p-24 * um * sqrt(fmax(A.t11 + A.t22 + A.t33, 0.0) / 3.0));
             }
             bool go = false;
-            if (res <= tol) {
+            if (r_oth <= tol && r_mom <= tol_mom) {
                 conv = true;
             } else if (it < a.max_iter && res == res) {
                 double db[10];

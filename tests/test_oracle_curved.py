@@ -318,3 +318,22 @@ def test_ogrid_geometry_and_one_step():
     f1, infos = pb.step(f, wl.dt())
     assert np.all(np.isfinite(f1))
     assert pb.totals(f1)[0] > 0
+
+
+def test_curved_element_residual_from_its_block_equals_the_whole_mesh():
+    """The single-element residual of a curvilinear element on its 3x3x3 block
+    (node coordinates and state of the block) equals the whole-mesh residual
+    at that element: the sphere O-grid (periodic azimuth wrap included), F and G."""
+    wl = W.sphere_ogrid(n=(4, 5, 6), vel_n=(8, 7, 7), umax=6.0, mach=1.2, kn=0.05)
+    x = W.node_positions(wl)
+    pb = curved.problem_from_workload(wl, x)
+    f = W.random_anisotropic_state(wl, seed=90, spread=0.2)
+    R, _ = pb.rhs(f)
+    n1, n2, n3 = wl.mesh_n
+    for c in ((1, 2, 0), (2, 3, 5), (2, 1, 3)):
+        e = c[0] + n1 * (c[1] + n2 * c[2])
+        idx = [(c[0] + d1) + n1 * ((c[1] + d2) + n2 * ((c[2] + d3) % n3))
+               for d3 in (-1, 0, 1) for d2 in (-1, 0, 1) for d1 in (-1, 0, 1)]
+        Re = curved.element_residual(wl.p, pb.vg, pb.gas, x[idx], f[:, :, idx, :])
+        scale = np.abs(R[:, :, e, :]).max()
+        assert np.max(np.abs(Re - R[:, :, e, :])) <= 1e-13 * scale
