@@ -40,13 +40,13 @@ namespace {
 // form term for term in exact arithmetic; constant data and the exact
 // telescoping of the element quadrature survive the FP32 arithmetic.
 template <int Q, int C, bool CURV>
-// The curvilinear instantiation keeps its geometry in shared memory and is
-// held to 128 registers (two blocks, 16 warps per SM): 1.7x faster on the
+// Held to 128 registers (two blocks, 16 warps per SM; the curvilinear
+// instantiation keeps its geometry in shared memory): 1.7x faster on the
 // sphere O-grid at p = 1 than one block of 8 warps without the cap.
-#ifndef BGK_CURV_MINB
-#define BGK_CURV_MINB 2
+#ifndef BGK_PLAIN_MINB
+#define BGK_PLAIN_MINB 2
 #endif
-__global__ void __launch_bounds__(256, CURV ? BGK_CURV_MINB : 1) k_stage_f32(StageArgs<float> a) {
+__global__ void __launch_bounds__(256, BGK_PLAIN_MINB) k_stage_f32(StageArgs<float> a) {
     constexpr int NS = Q * Q * Q;
     constexpr int EB = 256 / NS;
     constexpr int NT = EB * NS;
