@@ -306,8 +306,8 @@ __global__ void __launch_bounds__(256, BGK_PLAIN_MINB) k_stage_f32(StageArgs<flo
                         div = fmaf(toh[d] * u[d], t, div);
                     }
                     }
-                    const float eqv = (c == 0) ? g32 : gfac * g32;
-                    const float eqc = (c == 0) ? gc : gfac * gc;
+                    const float eqv = (c == 0) ? g32 : __fmul_rn(gfac, g32);
+                    const float eqc = (c == 0) ? gc : __fmul_rn(gfac, gc);
                     const float R = fmaf(eqv - fself[c], itau, fmaf(eqc, itau, -div));
                     float out = fab == 1.f ? fself[c] : fab * fself[c];
                     if (fa != 0.f)
@@ -492,8 +492,8 @@ __global__ void __launch_bounds__(TmaGeom<Q, C>::NTHR, 2) k_stage_f32_tma(StageA
                         t = fmaf(sdg[side][id[d]], dn, fmaf(seps[side][id[d]], fi, t));
                         div = fmaf(toh[d] * u[d], t, div);
                     }
-                    const float eqv = (c == 0) ? g32 : gfac * g32;
-                    const float eqc = (c == 0) ? gc : gfac * gc;
+                    const float eqv = (c == 0) ? g32 : __fmul_rn(gfac, g32);
+                    const float eqc = (c == 0) ? gc : __fmul_rn(gfac, gc);
                     const float R = fmaf(eqv - fi, itau, fmaf(eqc, itau, -div));
                     float out = fab == 1.f ? fi : fab * fi;
                     if (fa != 0.f) out = fmaf(fa, sc[fn_off] - fi, out);

@@ -77,6 +77,84 @@ __device__ __forceinline__ void st_vec<1>(float *p, const float (&v)[1]) {
     *p = v[0];
 }
 
+// Element-wise FR updates over a thread's NPT points.  With NPT even they run
+// on pairs of points with the packed FP32 instructions (two IEEE operations
+// per issue, each rounded exactly as its scalar form), so the results are
+// bit-identical to the scalar sequence of the other FP32 stage kernels;
+// x - y is evaluated as x + (-y), the same IEEE operation.
+template <int N>
+__device__ __forceinline__ void negate(const float (&a)[N], float (&n)[N]) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) n[i] = -a[i];
+}
+// t[i] = fmaf(D, G[i] - F[i], t[i]), D common to the points
+template <int N>
+__device__ __forceinline__ void acc_dev(float (&t)[N], float D, const float (&G)[N], const float (&nF)[N]) {
+    if constexpr (N % 2 == 0) {
+        const float2 d2 = make_float2(D, D);
+#pragma unroll
+        for (int i = 0; i < N; i += 2) {
+            const float2 dv = __fadd2_rn(make_float2(G[i], G[i + 1]), make_float2(nF[i], nF[i + 1]));
+            const float2 r = __ffma2_rn(d2, dv, make_float2(t[i], t[i + 1]));
+            t[i] = r.x; t[i + 1] = r.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) t[i] = fmaf(D, __fadd_rn(G[i], nF[i]), t[i]);
+    }
+}
+// y[i] = c * F[i]
+template <int N>
+__device__ __forceinline__ void scale_vec(float (&y)[N], float c, const float (&F)[N]) {
+    if constexpr (N % 2 == 0) {
+        const float2 c2 = make_float2(c, c);
+#pragma unroll
+        for (int i = 0; i < N; i += 2) {
+            const float2 r = __fmul2_rn(c2, make_float2(F[i], F[i + 1]));
+            y[i] = r.x; y[i + 1] = r.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) y[i] = __fmul_rn(c, F[i]);
+    }
+}
+// t[i] = fmaf(a[i], dn[i], fmaf(b[i], F[i], t[i])); div[i] = fmaf(cu, t[i], div[i])
+template <int N>
+__device__ __forceinline__ void lift_vec(float (&t)[N], const float *a, const float *b, const float (&dn)[N],
+                                         const float (&F)[N], float cu, float (&div)[N], bool first) {
+    if constexpr (N % 2 == 0) {
+        const float2 cu2 = make_float2(cu, cu), z2 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < N; i += 2) {
+            const float2 a2 = make_float2(a[i], a[i + 1]), b2 = make_float2(b[i], b[i + 1]);
+            float2 tt = __ffma2_rn(b2, make_float2(F[i], F[i + 1]), make_float2(t[i], t[i + 1]));
+            tt = __ffma2_rn(a2, make_float2(dn[i], dn[i + 1]), tt);
+            const float2 dv = __ffma2_rn(cu2, tt, first ? z2 : make_float2(div[i], div[i + 1]));
+            t[i] = tt.x; t[i + 1] = tt.y;
+            div[i] = dv.x; div[i + 1] = dv.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            t[i] = fmaf(a[i], dn[i], fmaf(b[i], F[i], t[i]));
+            div[i] = fmaf(cu, t[i], first ? 0.f : div[i]);
+        }
+    }
+}
+
+// x - y as one rounding of the exact difference (y * -1 is exact), paired
+__device__ __forceinline__ float2 sub2(float2 x, float2 y) { return __ffma2_rn(y, make_float2(-1.f, -1.f), x); }
+__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
+// sum2 on two independent (sum, error) pairs at once
+__device__ __forceinline__ void sum2x2(float2 &s, float2 &c, float2 v) {
+    const float2 t = __fadd2_rn(s, v);
+    const float2 bp = sub2(t, s);
+    const float2 e = __fadd2_rn(sub2(s, sub2(t, bp)), sub2(v, bp));
+    s = t;
+    c = __fadd2_rn(c, e);
+}
+
 // Line sums of one point (the first level of IndexMoments): F, F jt, F jt^2
 // and, with two components, G; error-free pairs.
 template <int C>
@@ -99,6 +177,32 @@ struct LineAcc {
         if (C == 2) sum2(L[C == 2 ? 3 : 0], Lc[C == 2 ? 3 : 0], __fmul_rn(cj1, G));
     }
 };
+
+// LineAcc::add of two points at once, operation for operation
+template <int C>
+__device__ __forceinline__ void add_pair(LineAcc<C> &A, LineAcc<C> &B, float cj1, float jt1, float2 F, float2 G) {
+    const float2 cF = __fmul2_rn(dup2(cj1), F);
+    float2 s = make_float2(A.L[0], B.L[0]), e = make_float2(A.Lc[0], B.Lc[0]);
+    sum2x2(s, e, cF);
+    A.L[0] = s.x; B.L[0] = s.y; A.Lc[0] = e.x; B.Lc[0] = e.y;
+    const float2 jt = dup2(jt1);
+    const float2 p1 = __fmul2_rn(cF, jt);
+    s = make_float2(A.L[1], B.L[1]); e = make_float2(A.Lc[1], B.Lc[1]);
+    sum2x2(s, e, p1);
+    e = __fadd2_rn(e, __ffma2_rn(cF, jt, neg2(p1)));
+    A.L[1] = s.x; B.L[1] = s.y; A.Lc[1] = e.x; B.Lc[1] = e.y;
+    const float2 jj = dup2(__fmul_rn(jt1, jt1));
+    const float2 p2 = __fmul2_rn(cF, jj);
+    s = make_float2(A.L[2], B.L[2]); e = make_float2(A.Lc[2], B.Lc[2]);
+    sum2x2(s, e, p2);
+    e = __fadd2_rn(e, __ffma2_rn(cF, jj, neg2(p2)));
+    A.L[2] = s.x; B.L[2] = s.y; A.Lc[2] = e.x; B.Lc[2] = e.y;
+    if constexpr (C == 2) {
+        s = make_float2(A.L[3], B.L[3]); e = make_float2(A.Lc[3], B.Lc[3]);
+        sum2x2(s, e, __fmul2_rn(dup2(cj1), G));
+        A.L[3] = s.x; B.L[3] = s.y; A.Lc[3] = e.x; B.Lc[3] = e.y;
+    }
+}
 
 // Plane pairs of one point in shared memory: P[q] at P[q * n], errors at
 // P[(NQ + q) * n]; the same operations as IndexMoments::plane_add/end_line.
@@ -278,8 +382,9 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
                     const float *sc = st + c * PER_C;
-                    float Fi[NPT];                       // this thread's nodes
+                    float Fi[NPT], nFi[NPT];             // this thread's nodes (and their negatives)
                     ld_vec<NPT>(sc + own_off + ln + i0, Fi);
+                    negate<NPT>(Fi, nFi);
                     float div[NPT];
                     // ---- first direction: the line itself and the upwind neighbour's line
                     {
@@ -322,23 +427,20 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                         if (!BC || !((bcm >> sx) & 1)) {
                             float NB[Q];
                             ld_vec<Q>(sc + own_off + (sx ? NS : -NS) + ln, NB);
+                            scale_vec<NPT>(dn, sdlam[sx], Fi);
 #pragma unroll
-                            for (int i = 0; i < NPT; ++i) {
-                                dn[i] = sdlam[sx] * Fi[i];
+                            for (int j = 0; j < Q; ++j) {
+                                float NBj[NPT];
 #pragma unroll
-                                for (int j = 0; j < Q; ++j) dn[i] = fmaf(slam[sx][j], NB[j] - Fi[i], dn[i]);
+                                for (int i = 0; i < NPT; ++i) NBj[i] = NB[j];
+                                acc_dev<NPT>(dn, slam[sx][j], NBj, nFi);
                             }
                         } else {
                             const float bv = (float)__ldg(a.bcval + ((size_t)(0 + sx) * C + c) * a.Nu + k);
 #pragma unroll
                             for (int i = 0; i < NPT; ++i) dn[i] = bv - Fi[i];
                         }
-                        const float cu = toh0 * u1;
-#pragma unroll
-                        for (int i = 0; i < NPT; ++i) {
-                            t[i] = fmaf(sdg[sx][i0 + i], dn[i], fmaf(seps[sx][i0 + i], Fi[i], t[i]));
-                            div[i] = fmaf(cu, t[i], 0.f);
-                        }
+                        lift_vec<NPT>(t, &sdg[sx][i0], &seps[sx][i0], dn, Fi, toh0 * u1, div, true);
                     }
                     // ---- second direction: lines (j', kz) of the element and of the upwind y element
                     {
@@ -350,32 +452,25 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                             const int jp = (jy + m) & (Q - 1);       // the canonical order
                             float Gv[NPT];
                             ld_vec<NPT>(sc + own_off + Q * (jp + Q * kz) + i0, Gv);
-                            const float D = sD[sy][jy][jp];
-#pragma unroll
-                            for (int i = 0; i < NPT; ++i) t[i] = fmaf(D, Gv[i] - Fi[i], t[i]);
+                            acc_dev<NPT>(t, sD[sy][jy][jp], Gv, nFi);
                         }
                         if (!BC || !((bcm >> (2 + sy)) & 1)) {
-#pragma unroll
-                            for (int i = 0; i < NPT; ++i) dn[i] = sdlam[sy] * Fi[i];
+                            scale_vec<NPT>(dn, sdlam[sy], Fi);
 #pragma unroll
                             for (int jp = 0; jp < Q; ++jp) {
                                 float H[NPT];
                                 ld_vec<NPT>(sc + (SLOTS + l) * NS + Q * (jp + Q * kz) + i0, H);
-                                const float lam = slam[sy][jp];
-#pragma unroll
-                                for (int i = 0; i < NPT; ++i) dn[i] = fmaf(lam, H[i] - Fi[i], dn[i]);
+                                acc_dev<NPT>(dn, slam[sy][jp], H, nFi);
                             }
                         } else {
                             const float bv = (float)__ldg(a.bcval + ((size_t)(2 + sy) * C + c) * a.Nu + k);
 #pragma unroll
                             for (int i = 0; i < NPT; ++i) dn[i] = bv - Fi[i];
                         }
-                        const float cu = toh1 * u2, dgv = sdg[sy][jy], epv = seps[sy][jy];
+                        float dgv[NPT], epv[NPT];
 #pragma unroll
-                        for (int i = 0; i < NPT; ++i) {
-                            t[i] = fmaf(dgv, dn[i], fmaf(epv, Fi[i], t[i]));
-                            div[i] = fmaf(cu, t[i], div[i]);
-                        }
+                        for (int i = 0; i < NPT; ++i) { dgv[i] = sdg[sy][jy]; epv[i] = seps[sy][jy]; }
+                        lift_vec<NPT>(t, dgv, epv, dn, Fi, toh1 * u2, div, false);
                     }
                     // ---- third direction: lines (jy, k') of the element and of the upwind z element
                     {
@@ -387,36 +482,57 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                             const int kp = (kz + m) & (Q - 1);       // the canonical order
                             float Gv[NPT];
                             ld_vec<NPT>(sc + own_off + Q * (jy + Q * kp) + i0, Gv);
-                            const float D = sD[sz][kz][kp];
-#pragma unroll
-                            for (int i = 0; i < NPT; ++i) t[i] = fmaf(D, Gv[i] - Fi[i], t[i]);
+                            acc_dev<NPT>(t, sD[sz][kz][kp], Gv, nFi);
                         }
                         if (!BC || !((bcm >> (4 + sz)) & 1)) {
-#pragma unroll
-                            for (int i = 0; i < NPT; ++i) dn[i] = sdlam[sz] * Fi[i];
+                            scale_vec<NPT>(dn, sdlam[sz], Fi);
 #pragma unroll
                             for (int kp = 0; kp < Q; ++kp) {
                                 float H[NPT];
                                 ld_vec<NPT>(sc + (SLOTS + EB + l) * NS + Q * (jy + Q * kp) + i0, H);
-                                const float lam = slam[sz][kp];
-#pragma unroll
-                                for (int i = 0; i < NPT; ++i) dn[i] = fmaf(lam, H[i] - Fi[i], dn[i]);
+                                acc_dev<NPT>(dn, slam[sz][kp], H, nFi);
                             }
                         } else {
                             const float bv = (float)__ldg(a.bcval + ((size_t)(4 + sz) * C + c) * a.Nu + k);
 #pragma unroll
                             for (int i = 0; i < NPT; ++i) dn[i] = bv - Fi[i];
                         }
-                        const float cu = toh2 * u3, dgv = sdg[sz][kz], epv = seps[sz][kz];
+                        float dgv[NPT], epv[NPT];
 #pragma unroll
-                        for (int i = 0; i < NPT; ++i) {
-                            t[i] = fmaf(dgv, dn[i], fmaf(epv, Fi[i], t[i]));
-                            div[i] = fmaf(cu, t[i], div[i]);
-                        }
+                        for (int i = 0; i < NPT; ++i) { dgv[i] = sdg[sz][kz]; epv[i] = seps[sz][kz]; }
+                        lift_vec<NPT>(t, dgv, epv, dn, Fi, toh2 * u3, div, false);
                     }
                     // ---- equilibrium, source and Runge--Kutta update
                     float FN[NPT];
                     if (fa != 0.f) ld_vec<NPT>(sc + (SLOTS + 2 * EB + l) * NS + ln + i0, FN);
+                    if constexpr (NPT % 2 == 0) {
+                        // the same operations on pairs of points
+                        const float2 u12 = dup2(u1);
+#pragma unroll
+                        for (int i = 0; i < NPT; i += 2) {
+                            const float2 c1 = sub2(u12, make_float2(V1[i], V1[i + 1]));
+                            const float2 ex = __ffma2_rn(c1, __ffma2_rn(make_float2(A11[i], A11[i + 1]), c1,
+                                                                         make_float2(lin[i], lin[i + 1])),
+                                                         make_float2(cst[i], cst[i + 1]));
+                            const float2 g32 = __fmul2_rn(make_float2(E0[i], E0[i + 1]),
+                                                          make_float2(Eq32::ex2(ex.x), Eq32::ex2(ex.y)));
+                            const float2 t1 = sub2(u12, make_float2(U0x[i], U0x[i + 1]));
+                            const float2 corr = __ffma2_rn(t1, __ffma2_rn(make_float2(gm4h[i], gm4h[i + 1]), t1,
+                                                                           make_float2(gm1[i], gm1[i + 1])),
+                                                           make_float2(cl[i], cl[i + 1]));
+                            const float2 gc = __fmul2_rn(g32, corr);
+                            const float2 gf = make_float2(gfac[i], gfac[i + 1]);
+                            const float2 eqv = (c == 0) ? g32 : __fmul2_rn(gf, g32);
+                            const float2 eqc = (c == 0) ? gc : __fmul2_rn(gf, gc);
+                            const float2 F2 = make_float2(Fi[i], Fi[i + 1]), it2 = make_float2(itau[i], itau[i + 1]);
+                            const float2 R = __ffma2_rn(sub2(eqv, F2), it2,
+                                                        __ffma2_rn(eqc, it2, make_float2(-div[i], -div[i + 1])));
+                            float2 out = fab == 1.f ? F2 : __fmul2_rn(dup2(fab), F2);
+                            if (fa != 0.f) out = __ffma2_rn(dup2(fa), sub2(make_float2(FN[i], FN[i + 1]), F2), out);
+                            const float2 o = __ffma2_rn(dup2(fc), R, out);
+                            outv[c][i] = o.x; outv[c][i + 1] = o.y;
+                        }
+                    } else {
 #pragma unroll
                     for (int i = 0; i < NPT; ++i) {
                         const float c1 = __fsub_rn(u1, V1[i]);
@@ -424,19 +540,27 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                         const float t1 = u1 - U0x[i];
                         const float corr = fmaf(t1, fmaf(gm4h[i], t1, gm1[i]), cl[i]);
                         const float gc = __fmul_rn(g32, corr);
-                        const float eqv = (c == 0) ? g32 : gfac[i] * g32;
-                        const float eqc = (c == 0) ? gc : gfac[i] * gc;
+                        const float eqv = (c == 0) ? g32 : __fmul_rn(gfac[i], g32);
+                        const float eqc = (c == 0) ? gc : __fmul_rn(gfac[i], gc);
                         const float R = fmaf(eqv - Fi[i], itau[i], fmaf(eqc, itau[i], -div[i]));
                         float out = fab == 1.f ? Fi[i] : fab * Fi[i];
                         if (fa != 0.f) out = fmaf(fa, FN[i] - Fi[i], out);
                         outv[c][i] = fmaf(fc, R, out);
                     }
+                    }
                     st_vec<NPT>(a.f_out + ((size_t)c * a.Nu + k) * slab + pb, outv[c]);
                 }
                 if (mom) {
                     const float cj = trap(j1, vn1);
+                    if constexpr (NPT % 2 == 0) {
 #pragma unroll
-                    for (int i = 0; i < NPT; ++i) acc[i].add(cj, jt1, outv[0][i], C == 2 ? outv[C - 1][i] : 0.f);
+                        for (int i = 0; i < NPT; i += 2)
+                            add_pair<C>(acc[i], acc[i + 1], cj, jt1, make_float2(outv[0][i], outv[0][i + 1]),
+                                        C == 2 ? make_float2(outv[C - 1][i], outv[C - 1][i + 1]) : make_float2(0.f, 0.f));
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < NPT; ++i) acc[i].add(cj, jt1, outv[0][i], C == 2 ? outv[C - 1][i] : 0.f);
+                    }
                 }
             }
             // release the slot; the warp that releases it last refills it with
