@@ -397,6 +397,19 @@ __device__ __forceinline__ void sum2(float &s, float &c, float v) {
 
 __device__ __forceinline__ float trapf(int j, int n) { return (j == 0 || j == n - 1) ? 0.5f : 1.0f; }
 
+// packed FP32 (two IEEE operations per issue): x - y as one rounding of the
+// exact difference, and sum2 on two independent (sum, error) pairs
+__device__ __forceinline__ float2 qdup2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 qneg2(float2 v) { return make_float2(-v.x, -v.y); }
+__device__ __forceinline__ float2 qsub2(float2 x, float2 y) { return __ffma2_rn(y, make_float2(-1.f, -1.f), x); }
+__device__ __forceinline__ void qsum2x2(float2 &s, float2 &c, float2 v) {
+    const float2 t = __fadd2_rn(s, v);
+    const float2 bp = qsub2(t, s);
+    const float2 e = __fadd2_rn(qsub2(s, qsub2(t, bp)), qsub2(v, bp));
+    s = t;
+    c = __fadd2_rn(c, e);
+}
+
 // add c * (sum + err) of a line pair into a plane pair, error-free up to O(eps^2)
 __device__ __forceinline__ void plane_add(float &P, float &Pc, float c, float sum, float err) {
     const float ps = __fmul_rn(c, sum);
@@ -824,32 +837,11 @@ __device__ __forceinline__ void fused_pass(const QPrimeArgs &a, int lane, const 
         Jm[5] = fma(c3 * t3, Pd[0], Jm[5]);                                                     \
         Jm[6] = fma(c3 * t3 * t3, Pd[0], Jm[6]);                                                \
     } while (0)
-    for (int line = l0; line < l1; ++line) {
+    // the end of a line: its error-free sums into the plane pairs (in line
+    // order, flushing finished planes) and its Jacobian sums into the moments
+    auto end_line = [&](int line, float L0, float C0, float L1, float C1, float L2, float C2, const float (&Tm)[5]) {
         const int j2 = line % n2, j3 = line / n2;
         if (j3 != j3cur) { BGK_FLUSH_PLANE(j3cur); j3cur = j3; }
-        const float4 *vl32 = a.vtab32 + (size_t)line * n1;
-        float lin, cst;
-        e32.line(vl32[0].y, vl32[0].z, lin, cst);
-        float L0 = 0.f, C0 = 0.f, L1 = 0.f, C1 = 0.f, L2 = 0.f, C2 = 0.f;
-        float Tm[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-        float jt = (float)(-jc[0]);
-        for (int j1 = 0; j1 < n1; ++j1, jt += 1.f) {
-            const float u1 = su1[j1];
-            const float g = e32.g(u1, lin, cst);
-            const float cg = (j1 == 0 || j1 == n1 - 1) ? __fmul_rn(0.5f, g) : g;     // exact
-            sum2(L0, C0, cg);
-            const float p1 = __fmul_rn(cg, jt);
-            sum2(L1, C1, p1);
-            C1 = __fadd_rn(C1, fmaf(cg, jt, -p1));
-            const float jj = __fmul_rn(jt, jt);
-            const float p2 = __fmul_rn(cg, jj);
-            sum2(L2, C2, p2);
-            C2 = __fadd_rn(C2, fmaf(cg, jj, -p2));
-            // Jacobian line sums (plain FP32)
-            const float ut = u1 - U0x;
-            const float t1 = cg * ut, t2 = t1 * ut, t3 = t2 * ut;
-            Tm[0] += cg; Tm[1] += t1; Tm[2] += t2; Tm[3] += t3; Tm[4] = fmaf(t3, ut, Tm[4]);
-        }
         const float c2 = trapf(j2, n2), jt2 = (float)(j2 - jc[1]);
         const float b = __fmul_rn(c2, jt2), bb = __fmul_rn(b, jt2);                  // exact
         plane_add(P[0], Pc[0], c2, L0, C0);
@@ -873,6 +865,51 @@ __device__ __forceinline__ void fused_pass(const QPrimeArgs &a, int lane, const 
 #pragma unroll
                 for (int mm = 0; mm <= 4 - aa - bb2; ++mm, ++idx) M[idx] = fmaf(Pp, Tm[mm], M[idx]);
             }
+    };
+    // two lines of the lane's run at a time on packed FP32: they share u1,
+    // the equilibrium's point parameters and the weights, so every operation
+    // of a line's walk is the scalar one (the equilibrium values bit for bit
+    // those of the stage's Eq32), paired with the other line's
+    for (int line = l0; line < l1; line += 2) {
+        const bool two = line + 1 < l1;
+        const float4 *vl32 = a.vtab32 + (size_t)line * n1;
+        float linA, cstA, linB = 0.f, cstB = 0.f;
+        e32.line(vl32[0].y, vl32[0].z, linA, cstA);
+        if (two) e32.line(vl32[n1].y, vl32[n1].z, linB, cstB);
+        const float2 lin2 = make_float2(linA, linB), cst2 = make_float2(cstA, cstB);
+        const float2 A11 = qdup2(e32.A11), E0 = qdup2(e32.E0);
+        float2 L0 = qdup2(0.f), C0 = L0, L1 = L0, C1 = L0, L2 = L0, C2 = L0;
+        float2 T0 = L0, T1 = L0, T2 = L0, T3 = L0, T4 = L0;
+        float jt = (float)(-jc[0]);
+        for (int j1 = 0; j1 < n1; ++j1, jt += 1.f) {
+            const float u1 = su1[j1];
+            const float2 c1 = qdup2(__fsub_rn(u1, e32.V1));
+            const float2 ex = __ffma2_rn(c1, __ffma2_rn(A11, c1, lin2), cst2);
+            const float2 g = __fmul2_rn(E0, make_float2(Eq32::ex2(ex.x), Eq32::ex2(ex.y)));
+            const float2 cg = (j1 == 0 || j1 == n1 - 1) ? __fmul2_rn(qdup2(0.5f), g) : g;     // exact
+            qsum2x2(L0, C0, cg);
+            const float2 jtv = qdup2(jt);
+            const float2 p1 = __fmul2_rn(cg, jtv);
+            qsum2x2(L1, C1, p1);
+            C1 = __fadd2_rn(C1, __ffma2_rn(cg, jtv, qneg2(p1)));
+            const float2 jj = qdup2(__fmul_rn(jt, jt));
+            const float2 p2 = __fmul2_rn(cg, jj);
+            qsum2x2(L2, C2, p2);
+            C2 = __fadd2_rn(C2, __ffma2_rn(cg, jj, qneg2(p2)));
+            // Jacobian line sums (plain FP32)
+            const float2 ut = qdup2(u1 - U0x);
+            const float2 t1 = __fmul2_rn(cg, ut), t2 = __fmul2_rn(t1, ut), t3 = __fmul2_rn(t2, ut);
+            T0 = __fadd2_rn(T0, cg); T1 = __fadd2_rn(T1, t1); T2 = __fadd2_rn(T2, t2); T3 = __fadd2_rn(T3, t3);
+            T4 = __ffma2_rn(t3, ut, T4);
+        }
+        {
+            const float Tm[5] = {T0.x, T1.x, T2.x, T3.x, T4.x};
+            end_line(line, L0.x, C0.x, L1.x, C1.x, L2.x, C2.x, Tm);
+        }
+        if (two) {
+            const float Tm[5] = {T0.y, T1.y, T2.y, T3.y, T4.y};
+            end_line(line + 1, L0.y, C0.y, L1.y, C1.y, L2.y, C2.y, Tm);
+        }
     }
     if (j3cur >= 0) BGK_FLUSH_PLANE(j3cur);
 #undef BGK_FLUSH_PLANE
