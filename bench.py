@@ -371,8 +371,8 @@ def kernel_rooflines(wl, r, peaks, form):
 
 # DRAM bytes per DOF of a stage launch, mean over the three stages of a step,
 # from the ncu capture summarised in profiles/ncu_stage_f32_line_*.md (valid
-# for that kernel as it stands; traffic per DOF does not depend on N_e).
-MEASURED_STAGE_TRAFFIC_PER_DOF = {"line_wide": 11.36}
+# for that kernel variant as it stands; traffic per DOF does not depend on N_e).
+MEASURED_STAGE_TRAFFIC_PER_DOF = {"line": 11.25}
 
 
 def dominant_roofline(rl):

@@ -77,6 +77,7 @@ struct bgk_ctx {
     long long launches[BGK_NKINDS];
     // learned guess
     float *mlp_w, *mlp_norm, *mlp_m, *mlp_v, *mlp_grad;
+    float *mlp_w16;                   // BF16-rounded copy of mlp_w (refreshed when the weights change)
     double *mlp_loss;
     bool mlp_ready;
     int guess_mode, mlp_bf16;
@@ -256,7 +257,7 @@ bgk_status run_qprime(bgk_ctx *ctx, const double *part, int n_vblk, int P, doubl
     a.iters = iters; a.status = ctx->status; a.stats = ctx->stats; a.P = P; a.Nu = ctx->Nu;
     a.tol = ctx->tol; a.tol32 = 1e-6; a.max_iter = ctx->max_iter; a.gas = ctx->gas; a.vg = ctx->vg;
     a.mixed = ctx->precision == BGK_MIXED ? 1 : 0;
-    a.mlp.w = ctx->mlp_w; a.mlp.norm = ctx->mlp_norm;
+    a.mlp.w = ctx->mlp_w; a.mlp.norm = ctx->mlp_norm; a.mlp.w16 = ctx->mlp_w16;
     a.guess_mode = (ctx->guess_mode == 1 && ctx->mlp_ready) ? 1 : 0;
     a.mlp_bf16 = ctx->mlp_bf16;
     a.log = ctx->log_on ? ctx->log : nullptr;
@@ -738,6 +739,7 @@ bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
     if (st == BGK_OK) cu(cudaMalloc(&ctx->stats, sizeof(NewtonStats)), "cudaMalloc(stats)");
     if (st == BGK_OK) cu(cudaMalloc(&ctx->mlp_w, MLP_NPARAM * sizeof(float)), "cudaMalloc(mlp)");
     if (st == BGK_OK) cu(cudaMalloc(&ctx->mlp_norm, MLP_NNORM * sizeof(float)), "cudaMalloc(mlp)");
+    if (st == BGK_OK) cu(cudaMalloc(&ctx->mlp_w16, MLP_NPARAM * sizeof(float)), "cudaMalloc(mlp)");
     if (st == BGK_OK) cu(cudaMalloc(&ctx->mlp_m, MLP_NPARAM * sizeof(float)), "cudaMalloc(mlp)");
     if (st == BGK_OK) cu(cudaMalloc(&ctx->mlp_v, MLP_NPARAM * sizeof(float)), "cudaMalloc(mlp)");
     if (st == BGK_OK) cu(cudaMalloc(&ctx->mlp_grad, MLP_NPARAM * sizeof(float)), "cudaMalloc(mlp)");
@@ -771,7 +773,7 @@ bgk_status bgk_destroy(bgk_ctx *ctx) {
     cudaFree(ctx->stats);
     cudaFree(ctx->geo); cudaFree(ctx->fvec); cudaFree(ctx->geo32); cudaFree(ctx->fvec32);
     cudaFree(ctx->rho_w); cudaFree(ctx->wall_ef);
-    cudaFree(ctx->mlp_w); cudaFree(ctx->mlp_norm); cudaFree(ctx->mlp_m); cudaFree(ctx->mlp_v);
+    cudaFree(ctx->mlp_w); cudaFree(ctx->mlp_w16); cudaFree(ctx->mlp_norm); cudaFree(ctx->mlp_m); cudaFree(ctx->mlp_v);
     cudaFree(ctx->mlp_grad); cudaFree(ctx->mlp_loss); cudaFree(ctx->log); cudaFree(ctx->log_count);
     delete ctx;
     return BGK_OK;
@@ -1137,6 +1139,7 @@ bgk_status bgk_mlp_weights(bgk_ctx *ctx, float *buf, int load) {
         CU(cudaMemcpyAsync(ctx->mlp_w, buf, MLP_NPARAM * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
         CU(cudaMemcpyAsync(ctx->mlp_norm, buf + MLP_NPARAM, MLP_NNORM * sizeof(float), cudaMemcpyHostToDevice,
                            ctx->stream));
+        CU(launch_mlp_round(ctx->mlp_w, ctx->mlp_w16, MLP_NPARAM, ctx->stream));
         ctx->mlp_ready = true;
     } else {
         if (!ctx->mlp_ready) return fail(ctx, BGK_EINVAL, "no trained or loaded network");
@@ -1271,6 +1274,10 @@ bgk_status bgk_mlp_train(bgk_ctx *ctx, int epochs, int batch, float lr, unsigned
         cudaMemcpyAsync(&ls_sum, ctx->mlp_loss, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
         cudaStreamSynchronize(ctx->stream);
         last = ls_sum / (double)nbatch;
+    }
+    if (!st) {
+        const cudaError_t e = launch_mlp_round(ctx->mlp_w, ctx->mlp_w16, MLP_NPARAM, ctx->stream);
+        if (e != cudaSuccess) st = fail(ctx, BGK_ECUDA, "mlp round: %s", cudaGetErrorString(e));
     }
     cudaStreamSynchronize(ctx->stream);
     cudaFree(dx);

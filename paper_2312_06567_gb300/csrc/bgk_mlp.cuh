@@ -22,6 +22,7 @@
 struct MlpParams {
     const float *w;          // MLP_NPARAM FP32 master weights
     const float *norm;       // MLP_NNORM
+    const float *w16;        // the weights rounded to BF16 once (or null): BF16 inference reads them as they are
 };
 
 __device__ __forceinline__ float mlp_round(float x, int bf16) {
@@ -32,8 +33,12 @@ __device__ __forceinline__ float mlp_round(float x, int bf16) {
 // features and receives Delta.  Lane l owns hidden units l and l + 32.
 __device__ __forceinline__ void mlp_infer_warp(const MlpParams &p, const float x[MLP_IN], float delta[MLP_OUT],
                                                int bf16, int lane) {
-    const float *W1 = p.w, *b1 = W1 + MLP_IN * MLP_H, *W2 = b1 + MLP_H, *b2 = W2 + MLP_H * MLP_H;
+    // with the pre-rounded copy the weights need no rounding here (the same
+    // values: BF16 rounding of a value is a fixed function of it)
+    const bool pre = bf16 && p.w16 != nullptr;
+    const float *W1 = pre ? p.w16 : p.w, *b1 = W1 + MLP_IN * MLP_H, *W2 = b1 + MLP_H, *b2 = W2 + MLP_H * MLP_H;
     const float *W3 = b2 + MLP_H, *b3 = W3 + MLP_H * MLP_OUT;
+    const int wr = pre ? 0 : bf16;
     float xn[MLP_IN];
 #pragma unroll
     for (int f = 0; f < MLP_IN; ++f) xn[f] = mlp_round((x[f] - __ldg(p.norm + f)) / __ldg(p.norm + MLP_IN + f), bf16);
@@ -43,21 +48,21 @@ __device__ __forceinline__ void mlp_infer_warp(const MlpParams &p, const float x
         const int j = lane + 32 * r;
         float z = __ldg(b1 + j);
 #pragma unroll
-        for (int f = 0; f < MLP_IN; ++f) z = fmaf(xn[f], mlp_round(__ldg(W1 + f * MLP_H + j), bf16), z);
+        for (int f = 0; f < MLP_IN; ++f) z = fmaf(xn[f], mlp_round(__ldg(W1 + f * MLP_H + j), wr), z);
         h1[r] = mlp_round(z / (1.f + __expf(-z)), bf16);
     }
     float z2[2] = {__ldg(b2 + lane), __ldg(b2 + lane + 32)};
     for (int k = 0; k < MLP_H; ++k) {
         const float hk = __shfl_sync(0xffffffffu, h1[k >> 5], k & 31);
-        z2[0] = fmaf(hk, mlp_round(__ldg(W2 + k * MLP_H + lane), bf16), z2[0]);
-        z2[1] = fmaf(hk, mlp_round(__ldg(W2 + k * MLP_H + lane + 32), bf16), z2[1]);
+        z2[0] = fmaf(hk, mlp_round(__ldg(W2 + k * MLP_H + lane), wr), z2[0]);
+        z2[1] = fmaf(hk, mlp_round(__ldg(W2 + k * MLP_H + lane + 32), wr), z2[1]);
     }
 #pragma unroll
     for (int r = 0; r < 2; ++r) h2[r] = mlp_round(z2[r] / (1.f + __expf(-z2[r])), bf16);
 #pragma unroll
     for (int o = 0; o < MLP_OUT; ++o) {
-        float y = h2[0] * mlp_round(__ldg(W3 + lane * MLP_OUT + o), bf16) +
-                  h2[1] * mlp_round(__ldg(W3 + (lane + 32) * MLP_OUT + o), bf16);
+        float y = h2[0] * mlp_round(__ldg(W3 + lane * MLP_OUT + o), wr) +
+                  h2[1] * mlp_round(__ldg(W3 + (lane + 32) * MLP_OUT + o), wr);
 #pragma unroll
         for (int s = 16; s > 0; s >>= 1) y += __shfl_xor_sync(0xffffffffu, y, s);
         y += __ldg(b3 + o);
@@ -68,5 +73,7 @@ __device__ __forceinline__ void mlp_infer_warp(const MlpParams &p, const float x
 size_t mlp_train_smem();
 cudaError_t launch_mlp_train(const MlpParams &p, const float *x, const float *t, const int *idx, int nb,
                              float *grad, double *loss, int bf16, cudaStream_t s);
+// w16[i] = w[i] rounded to BF16 (held in FP32), the copy BF16 inference reads
+cudaError_t launch_mlp_round(const float *w, float *w16, int n, cudaStream_t s);
 cudaError_t launch_mlp_adam(float *w, float *m, float *v, float *grad, int n, float lr, float b1, float b2,
                             float eps, int step, cudaStream_t s);

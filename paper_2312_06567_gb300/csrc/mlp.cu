@@ -188,6 +188,16 @@ cudaError_t launch_mlp_train(const MlpParams &p, const float *x, const float *t,
     return cudaGetLastError();
 }
 
+__global__ void k_mlp_round(const float *w, float *w16, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) w16[i] = mlp_round(w[i], 1);
+}
+
+cudaError_t launch_mlp_round(const float *w, float *w16, int n, cudaStream_t s) {
+    k_mlp_round<<<(n + 255) / 256, 256, 0, s>>>(w, w16, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_mlp_adam(float *w, float *m, float *v, float *grad, int n, float lr, float b1, float b2,
                             float eps, int step, cudaStream_t s) {
     const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
