@@ -17,6 +17,11 @@
 
 namespace {
 
+// packed FP32 helpers (two IEEE operations per issue)
+__device__ __forceinline__ float2 pdup(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 pneg(float2 v) { return make_float2(-v.x, -v.y); }
+__device__ __forceinline__ float2 psub(float2 x, float2 y) { return __ffma2_rn(y, make_float2(-1.f, -1.f), x); }
+
 // ---------------------------------------------------------------------------
 // Fused stage, FP32 state.  Same discretisation as the FP64 stage kernel
 // (all FP32 stage kernels sum each node's own-line terms in the order
@@ -205,6 +210,90 @@ __global__ void __launch_bounds__(256, BGK_PLAIN_MINB) k_stage_f32(StageArgs<flo
                 // so the rounding stays unbiased), never rounded into g itself.
                 const float gc = __fmul_rn(g32, corr);
                 float outv[C];
+                if constexpr (CURV && C == 2) {
+                    // curvilinear, F and G: the per-component body below on the pair
+                    // (F, G) -- the two components share the geometry, the face
+                    // normal velocities, the upwind decisions and the equilibrium
+                    const float2 fi2 = make_float2(fself[0], fself[1]), nfi2 = pneg(fi2);
+                    const float *fs0 = a.f_s + (size_t)k * slab, *fs1 = a.f_s + ((size_t)a.Nu + k) * slab;
+                    float2 div = pdup(0.f);
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        const float *own0 = sf[buf][0] + le * NS + base[d], *own1 = sf[buf][1] + le * NS + base[d];
+                        const float *ownA = sA[buf][d] + le * NS + base[d];
+                        float2 dF = pdup(0.f), E = dF, trL = dF, trR = dF, fmL = dF, fmR = dF;
+#pragma unroll
+                        for (int m = 1; m < Q; ++m) {
+                            const int j = (id[d] + m) % Q;
+                            const float2 dfj = __fadd2_rn(make_float2(own0[j * stride[d]], own1[j * stride[d]]), nfi2);
+                            const float2 wj = __fmul2_rn(pdup(ownA[j * stride[d]]), dfj);
+                            dF = __ffma2_rn(pdup(cD[id[d]][j]), wj, dF);
+                            E = __ffma2_rn(pdup(cdef[j]), wj, E);
+                            trL = __ffma2_rn(pdup(cl[1][j]), wj, trL);
+                            trR = __ffma2_rn(pdup(cl[0][j]), wj, trR);
+                            fmL = __ffma2_rn(pdup(cl[1][j]), dfj, fmL);
+                            fmR = __ffma2_rn(pdup(cl[0][j]), dfj, fmR);
+                        }
+                        float2 X[2];
+#pragma unroll
+                        for (int side = 0; side < 2; ++side) {
+                            const int fpi = d == 0 ? id[1] + Q * id[2] : (d == 1 ? id[0] + Q * id[2] : id[0] + Q * id[1]);
+                            const float A = sAf[buf][(le * 6 + 2 * d + side) * Q * Q + fpi];
+                            const float un = side ? A : -A;               // outward
+                            const int en = en_[d][side];
+                            const int kind = a.mesh.face_kind[2 * d + side];
+                            float2 dev;
+                            if (en < 0 && kind == BGK_FK_CLOSED) {
+                                dev = nfi2;                               // F^I = 0
+                            } else if (un > 0.f) {
+                                dev = side ? fmR : fmL;
+                            } else if (en >= e0 && en < e0 + EB) {
+                                const float *nb0 = sf[buf][0] + (en - e0) * NS + base[d];
+                                const float *nb1 = sf[buf][1] + (en - e0) * NS + base[d];
+                                dev = pdup(0.f);
+#pragma unroll
+                                for (int j = 0; j < Q; ++j)
+                                    dev = __ffma2_rn(pdup(cl[side][j]),
+                                                     __fadd2_rn(make_float2(nb0[j * stride[d]], nb1[j * stride[d]]), nfi2), dev);
+                            } else if (en >= 0) {
+                                const float *nb0 = fs0 + (size_t)en * NS + base[d], *nb1 = fs1 + (size_t)en * NS + base[d];
+                                dev = pdup(0.f);
+#pragma unroll
+                                for (int j = 0; j < Q; ++j)
+                                    dev = __ffma2_rn(pdup(cl[side][j]),
+                                                     __fadd2_rn(make_float2(__ldg(nb0 + j * stride[d]), __ldg(nb1 + j * stride[d])), nfi2),
+                                                     dev);
+                            } else {
+                                double fp0 = __ldg(a.bcval + ((size_t)(2 * d + side) * C + 0) * a.Nu + k);
+                                double fp1 = __ldg(a.bcval + ((size_t)(2 * d + side) * C + 1) * a.Nu + k);
+                                if (kind == BGK_FK_DIFFUSE) {
+                                    const double rw = __ldg(a.rho_w + ((size_t)e * 6 + 2 * d + side) * Q * Q + fpi);
+                                    fp0 *= rw;
+                                    fp1 *= rw;
+                                }
+                                dev = __fadd2_rn(make_float2((float)fp0, (float)fp1), nfi2);
+                            }
+                            X[side] = __ffma2_rn(pdup(A), dev, pneg(side ? trR : trL));
+                        }
+                        div = __fadd2_rn(div, __ffma2_rn(X[1], pdup(cg[1][id[d]]),
+                                                         __ffma2_rn(X[0], pdup(cg[0][id[d]]), psub(dF, E))));
+                    }
+                    const float uH = fmaf(u[0], sG[tid][9], fmaf(u[1], sG[tid][10], u[2] * sG[tid][11]));
+                    div = __fmul2_rn(__ffma2_rn(fi2, pdup(uH), div), pdup(sG[tid][12]));
+                    const float2 eqv = make_float2(g32, __fmul_rn(gfac, g32));
+                    const float2 eqc = make_float2(gc, __fmul_rn(gfac, gc));
+                    const float2 it2 = pdup(itau);
+                    const float2 R = __ffma2_rn(psub(eqv, fi2), it2, __ffma2_rn(eqc, it2, pneg(div)));
+                    float2 out = fab == 1.f ? fi2 : __fmul2_rn(pdup(fab), fi2);
+                    if (fa != 0.f)
+                        out = __ffma2_rn(pdup(fa), psub(make_float2(__ldg(a.f_n + (size_t)k * slab + p),
+                                                                    __ldg(a.f_n + ((size_t)a.Nu + k) * slab + p)), fi2), out);
+                    out = __ffma2_rn(pdup(fc), R, out);
+                    a.f_out[(size_t)k * slab + p] = out.x;
+                    a.f_out[((size_t)a.Nu + k) * slab + p] = out.y;
+                    outv[0] = out.x;
+                    outv[C - 1] = out.y;
+                } else {
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
                     const float *fs = a.f_s + ((size_t)c * a.Nu + k) * slab;
@@ -315,6 +404,7 @@ __global__ void __launch_bounds__(256, BGK_PLAIN_MINB) k_stage_f32(StageArgs<flo
                     out = fmaf(fc, R, out);
                     a.f_out[((size_t)c * a.Nu + k) * slab + p] = out;
                     outv[c] = out;
+                }
                 }
                 acc.add(trap(j1, vn1), jt1, outv[0], C == 2 ? outv[C - 1] : 0.f);
             }
