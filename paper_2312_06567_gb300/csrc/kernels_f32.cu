@@ -293,6 +293,72 @@ __global__ void __launch_bounds__(256, BGK_PLAIN_MINB) k_stage_f32(StageArgs<flo
                     a.f_out[((size_t)a.Nu + k) * slab + p] = out.y;
                     outv[0] = out.x;
                     outv[C - 1] = out.y;
+                } else if constexpr (!CURV && C == 2) {
+                    // box, F and G: each component's operations exactly as in the
+                    // scalar body below, on the pair (F, G)
+                    const float2 fi2 = make_float2(fself[0], fself[1]), nfi2 = pneg(fi2);
+                    const float *fs0 = a.f_s + (size_t)k * slab, *fs1 = a.f_s + ((size_t)a.Nu + k) * slab;
+                    float2 div = pdup(0.f);
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        const int side = u[d] > 0.f ? 0 : 1;
+                        const float *own0 = sf[buf][0] + le * NS + base[d], *own1 = sf[buf][1] + le * NS + base[d];
+                        float2 t = pdup(0.f);
+#pragma unroll
+                        for (int m = 1; m < Q; ++m) {
+                            const int j = (id[d] + m) % Q;
+                            t = __ffma2_rn(pdup(sD[side][id[d]][j]),
+                                           __fadd2_rn(make_float2(own0[j * stride[d]], own1[j * stride[d]]), nfi2), t);
+                        }
+                        const int en = side ? en_[d][1] : en_[d][0];
+                        float2 dn;
+                        if (en >= e0 && en < e0 + EB) {
+                            const float *nb0 = sf[buf][0] + (en - e0) * NS + base[d];
+                            const float *nb1 = sf[buf][1] + (en - e0) * NS + base[d];
+                            dn = __fmul2_rn(pdup(sdlam[side]), fi2);
+#pragma unroll
+                            for (int j = 0; j < Q; ++j)
+                                dn = __ffma2_rn(pdup(slam[side][j]),
+                                                __fadd2_rn(make_float2(nb0[j * stride[d]], nb1[j * stride[d]]), nfi2), dn);
+                        } else if (en >= 0) {
+                            const float *nb0 = fs0 + (size_t)en * NS + base[d], *nb1 = fs1 + (size_t)en * NS + base[d];
+                            dn = __fmul2_rn(pdup(sdlam[side]), fi2);
+#pragma unroll
+                            for (int j = 0; j < Q; ++j)
+                                dn = __ffma2_rn(pdup(slam[side][j]),
+                                                __fadd2_rn(make_float2(__ldg(nb0 + j * stride[d]), __ldg(nb1 + j * stride[d])), nfi2),
+                                                dn);
+                        } else if (a.mesh.specular[2 * d + side]) {
+                            const int km = mirror_velocity(k, d, a.vg.n);
+                            const float *mr0 = a.f_s + (size_t)km * slab + (size_t)e * NS + base[d];
+                            const float *mr1 = a.f_s + ((size_t)a.Nu + km) * slab + (size_t)e * NS + base[d];
+                            dn = __fmul2_rn(pdup(sdlam[1 - side]), fi2);
+#pragma unroll
+                            for (int j = 0; j < Q; ++j)
+                                dn = __ffma2_rn(pdup(slam[1 - side][j]),
+                                                __fadd2_rn(make_float2(__ldg(mr0 + j * stride[d]), __ldg(mr1 + j * stride[d])), nfi2),
+                                                dn);
+                        } else {
+                            dn = __fadd2_rn(make_float2((float)__ldg(a.bcval + ((size_t)(2 * d + side) * C + 0) * a.Nu + k),
+                                                        (float)__ldg(a.bcval + ((size_t)(2 * d + side) * C + 1) * a.Nu + k)),
+                                            nfi2);
+                        }
+                        t = __ffma2_rn(pdup(sdg[side][id[d]]), dn, __ffma2_rn(pdup(seps[side][id[d]]), fi2, t));
+                        div = __ffma2_rn(pdup(toh[d] * u[d]), t, div);
+                    }
+                    const float2 eqv = make_float2(g32, __fmul_rn(gfac, g32));
+                    const float2 eqc = make_float2(gc, __fmul_rn(gfac, gc));
+                    const float2 it2 = pdup(itau);
+                    const float2 R = __ffma2_rn(psub(eqv, fi2), it2, __ffma2_rn(eqc, it2, pneg(div)));
+                    float2 out = fab == 1.f ? fi2 : __fmul2_rn(pdup(fab), fi2);
+                    if (fa != 0.f)
+                        out = __ffma2_rn(pdup(fa), psub(make_float2(__ldg(a.f_n + (size_t)k * slab + p),
+                                                                    __ldg(a.f_n + ((size_t)a.Nu + k) * slab + p)), fi2), out);
+                    out = __ffma2_rn(pdup(fc), R, out);
+                    a.f_out[(size_t)k * slab + p] = out.x;
+                    a.f_out[((size_t)a.Nu + k) * slab + p] = out.y;
+                    outv[0] = out.x;
+                    outv[C - 1] = out.y;
                 } else {
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
