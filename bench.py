@@ -165,7 +165,7 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# Algorithmic work per DOF ("Roofline accounting").
+# Algorithmic work per DOF: the method's arithmetic and bytes, not the kernels' instruction counts.
 def stage_flops_per_dof(p, C):
     """Flops of the fused stage per DOF: FR per component (sum-factorised
     derivative, inflow trace, lift, metric scaling) 6(p+1) + 5 + 12 + 9/(p+1) + 6;
