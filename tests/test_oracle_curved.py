@@ -337,3 +337,28 @@ def test_curved_element_residual_from_its_block_equals_the_whole_mesh():
         Re = curved.element_residual(wl.p, pb.vg, pb.gas, x[idx], f[:, :, idx, :])
         scale = np.abs(R[:, :, e, :]).max()
         assert np.max(np.abs(Re - R[:, :, e, :])) <= 1e-13 * scale
+
+
+@pytest.mark.parametrize("make", [lambda: W.sphere_ogrid(n=(3, 4, 6), p=2),
+                                  lambda: W.wavy_periodic_box(p=3, n=(2, 3, 2), amp=0.06)])
+def test_workload_geometry_is_continuous_across_faces(make):
+    """The generators sample the analytic map at each element's GLL points, so
+    the degree-p interpolants of neighbouring elements agree on their shared
+    face (the continuity that exact free-stream preservation rests on); periodic
+    translations of the box are removed before comparing."""
+    wl = make()
+    x = W.node_positions(wl)
+    q = wl.p + 1
+    fr = FR1D(wl.p)
+    x6 = x.reshape(wl.n_elem, q, q, q, 3)
+    mesh = curved.CurvedMesh(wl.mesh_n, wl.periodic, x, wl.p)
+    for d in range(3):
+        xl = np.moveaxis(x6, 3 - d, -2)                       # [e, a, b, line, 3]
+        hi = np.einsum("j,eabjn->eabn", fr.l_plus, xl)
+        lo = np.einsum("j,eabjn->eabn", fr.l_minus, xl)
+        nb = mesh.nbr[(d, 1)]
+        inner = nb >= 0
+        jump = hi[inner] - lo[nb[inner]]
+        if wl.mapping is not None and wl.name.startswith("wavy"):
+            jump -= np.round(jump)                             # the unit period of the box
+        assert np.max(np.abs(jump)) <= 1e-12 * np.max(np.abs(x)), (d, np.max(np.abs(jump)))
