@@ -132,8 +132,9 @@ BGK_API bgk_status bgk_destroy(bgk_ctx *ctx);
 /* N_e, N_s, N_u and the number of components (1 or 2). */
 BGK_API bgk_status bgk_sizes(const bgk_ctx *ctx, int *n_elem, int *n_sol, int *n_vel, int *n_comp);
 
-/* Solution-node coordinates x[P][3], P = N_e N_s, in the context's own
- * Gauss--Legendre node placement. */
+/* Solution-node coordinates x[P][3], P = N_e N_s: on the uniform box in the
+ * context's own Gauss--Legendre node placement; on a curvilinear mesh the
+ * node_xyz the context was created with. */
 BGK_API bgk_status bgk_node_coords(const bgk_ctx *ctx, double *x, int on_device);
 
 /* Copy the state in / out (f[c][k][e][s], element type by precision). */
@@ -275,7 +276,9 @@ BGK_API bgk_status bgk_moments_noalloc(const bgk_vgrid_desc *vgrid, const double
  * derivative plus correction-function terms carrying the central common
  * interface value; at a Dirichlet face the average with the face state's
  * density).  out is host memory (on_device = 0) or device memory (1).
- * Errors: BGK_EINVAL, BGK_ECUDA. */
+ * Errors: BGK_EINVAL, BGK_ECUDA; BGK_ENOTSUP on the curvilinear path
+ * (node_xyz, diffuse or closed faces), where the gradient would need the
+ * metric terms. */
 BGK_API bgk_status bgk_macro(bgk_ctx *ctx, double *out, int on_device);
 
 /* The Q' solve alone (section "Numerical method", discrete compatibility):
@@ -285,8 +288,11 @@ BGK_API bgk_status bgk_macro(bgk_ctx *ctx, double *out, int on_device);
 BGK_API bgk_status bgk_qprime(bgk_ctx *ctx, const double *m, int n_points, double *qp, int *iters,
                       int on_device);
 
-/* Domain totals (rho, rho U, E) = sum_e sum_s W_s |J_e| sum_k w_k psi_k f of
- * the stored state (W_s tensor Gauss weights, |J_e| the affine Jacobian). */
+/* Domain totals (rho, rho U, E) = sum_e sum_s W_s J_s sum_k w_k psi_k f of
+ * the stored state (W_s tensor Gauss weights, J_s the Jacobian at the node:
+ * the affine |J_e| on the box; on a curvilinear mesh det(dX/dxi) of the
+ * element's interpolant in the FP64 form, and 1 / (1/J_s rounded to FP32) in
+ * the mixed form, the quadrature its stage conserves exactly). */
 BGK_API bgk_status bgk_totals(bgk_ctx *ctx, double totals[5]);
 
 /* Newton statistics accumulated since the last call (then reset):
