@@ -129,6 +129,18 @@ BGK_API bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bg
                       const bgk_gas_desc *gas, int precision, void *stream);
 BGK_API bgk_status bgk_destroy(bgk_ctx *ctx);
 
+/* The metric terms the library builds for a curvilinear mesh (host only, no
+ * context, no CUDA call): for mesh->node_xyz (required) and the FR order,
+ * S[P][9] = (S^1, S^2, S^3) at each solution node (S^d = J grad xi_d, the
+ * conservative curl form on the element's Gauss--Lobatto points evaluated at
+ * the Gauss nodes), J[P] = det(dX/dxi) at the nodes, and the face vectors
+ * fvec[N_e][6][(p+1)^2][3] (face 2d + (side > 0), oriented along +xi_d, the
+ * two sides' traces averaged; face point indexed by the two other node
+ * indices, lower axis fastest).  Buffers are host memory owned by the caller.
+ * Errors: BGK_EINVAL (missing arguments, invalid sizes, a non-positive
+ * Jacobian). */
+BGK_API bgk_status bgk_curved_metrics(const bgk_mesh_desc *mesh, double *S, double *J, double *fvec);
+
 /* N_e, N_s, N_u and the number of components (1 or 2). */
 BGK_API bgk_status bgk_sizes(const bgk_ctx *ctx, int *n_elem, int *n_sol, int *n_vel, int *n_comp);
 

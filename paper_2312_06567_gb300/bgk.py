@@ -45,6 +45,7 @@ SIGNATURES = {
     "bgk_sizes": (c_int, [c_void_p] + [ctypes.POINTER(c_int)] * 4),
     "bgk_node_coords": (c_int, [c_void_p, c_void_p, c_int]),
     "bgk_set_es_tensor": (c_int, [c_void_p, c_int]),
+    "bgk_curved_metrics": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "bgk_set_state": (c_int, [c_void_p, c_void_p, c_int]),
     "bgk_get_state": (c_int, [c_void_p, c_void_p, c_int]),
     "bgk_set_maxwellian": (c_int, [c_void_p, c_void_p, c_int]),
@@ -166,6 +167,23 @@ def descriptors(wl, node_xyz=None):
         v.n[d], v.lo[d], v.hi[d] = wl.vel_n[d], wl.vel_lo[d], wl.vel_hi[d]
     g = GasDesc(wl.delta, wl.Pr, wl.mu_ref, wl.theta_ref, wl.theta_S)
     return m, v, g
+
+
+def curved_metrics(wl, node_xyz):
+    """bgk_curved_metrics: (S[P, 3, 3] with S[p, d] = S^d, J[P], fvec[Ne, 6, q*q, 3])
+    of a curvilinear workload's node coordinates (host only)."""
+    lib = load()
+    x = np.ascontiguousarray(node_xyz, dtype=np.float64)
+    m, _, _ = descriptors(wl, x)
+    P = x.shape[0] * x.shape[1]
+    q = wl.p + 1
+    S = np.empty((P, 3, 3))
+    J = np.empty(P)
+    fv = np.empty((x.shape[0], 6, q * q, 3))
+    st = lib.bgk_curved_metrics(ctypes.byref(m), S.ctypes.data, J.ctypes.data, fv.ctypes.data)
+    if st != BGK_OK:
+        raise BGKError(st, "bgk_curved_metrics failed")
+    return S, J, fv
 
 
 def moments_noalloc(vgrid, f, n_comp, n_points, m, stream=None):

@@ -760,6 +760,27 @@ bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
     return st;
 }
 
+bgk_status bgk_curved_metrics(const bgk_mesh_desc *mesh, double *S, double *J, double *fvec) {
+    if (!mesh || !mesh->node_xyz || !S || !J || !fvec) return BGK_EINVAL;
+    if (mesh->order < 1 || mesh->order > 4) return BGK_EINVAL;
+    for (int d = 0; d < 3; ++d)
+        if (mesh->n[d] < 1) return BGK_EINVAL;
+    FROps fr{};
+    build_fr(mesh->order, fr);
+    int periodic[3];
+    for (int d = 0; d < 3; ++d) periodic[d] = mesh->periodic[d] ? 1 : 0;
+    std::vector<double> geo, fv;
+    std::string err;
+    if (!build_curved_geometry(fr, mesh->n, periodic, mesh->node_xyz, geo, fv, err)) return BGK_EINVAL;
+    const size_t P = geo.size() / BGK_NGEO;
+    for (size_t p = 0; p < P; ++p) {
+        for (int i = 0; i < 9; ++i) S[p * 9 + i] = geo[p * BGK_NGEO + i];
+        J[p] = 1.0 / geo[p * BGK_NGEO + 9];
+    }
+    std::memcpy(fvec, fv.data(), fv.size() * sizeof(double));
+    return BGK_OK;
+}
+
 bgk_status bgk_destroy(bgk_ctx *ctx) {
     if (!ctx) return BGK_EINVAL;
     cudaStreamSynchronize(ctx->stream);

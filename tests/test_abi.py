@@ -119,3 +119,30 @@ def test_curvilinear_descriptors_rejected_on_the_host(libbgk):
     st = lib.bgk_create(ctypes.byref(h), ctypes.byref(m), ctypes.byref(v), ctypes.byref(g), bgk.BGK_FP64, None)
     lib.bgk_destroy(h)
     assert st == bgk.BGK_EINVAL
+
+
+def test_library_metric_terms_equal_the_oracle(libbgk):
+    """Host-side metric terms of the library (bgk_curved_metrics) against the
+    oracle's independently written curl form: node metrics S^d, Jacobians and
+    averaged face vectors of the sphere O-grid (p = 1, 2) and a warped periodic
+    box (p = 3), to 1e-12 of their scale."""
+    import numpy as np
+    from oracle import curved
+    from paper_2312_06567_gb300 import workloads as W
+    cases = [W.sphere_ogrid(n=(2, 4, 6), p=1), W.sphere_ogrid(n=(2, 3, 4), p=2),
+             W.wavy_periodic_box(p=3, n=(2, 2, 3), amp=0.07)]
+    for wl in cases:
+        x = W.node_positions(wl)
+        S, J, fv = bgk.curved_metrics(wl, x)
+        mesh = curved.CurvedMesh(wl.mesh_n, wl.periodic, x, wl.p)
+        q = wl.p + 1
+        So = np.moveaxis(mesh.S.reshape(wl.n_elem, 3, 3, -1), 3, 1).reshape(-1, 3, 3)   # [P, d, n]
+        sc = np.max(np.abs(So))
+        assert np.max(np.abs(S - So)) <= 1e-12 * sc, wl.name
+        assert np.max(np.abs(J - mesh.J.reshape(-1))) <= 1e-12 * np.max(mesh.J), wl.name
+        for d in range(3):
+            for side in (-1, 1):
+                # both ordered (higher axis, lower axis) with the lower one fastest
+                f_o = mesh.face[(d, side)].reshape(wl.n_elem, q * q, 3)
+                f_l = fv[:, 2 * d + (side > 0)]
+                assert np.max(np.abs(f_l - f_o)) <= 1e-12 * sc, (wl.name, d, side)
