@@ -141,6 +141,17 @@ BGK_API bgk_status bgk_destroy(bgk_ctx *ctx);
  * Jacobian). */
 BGK_API bgk_status bgk_curved_metrics(const bgk_mesh_desc *mesh, double *S, double *J, double *fvec);
 
+/* The 1-D FR operators the library builds for order p (host only, section
+ * "Numerical method": Gauss--Legendre nodes, the Lagrange derivative, the
+ * traces l_j(+-1), the DG-recovering correction-function derivatives), q =
+ * p + 1: fr_out = [xi(q), w(q), D(q*q, row-major D_ij = l_j'(xi_i)), l(-1)(q),
+ * l(+1)(q), g_L'(q), g_R'(q)]; and the FP32 tables of the curvilinear mixed
+ * stage: curv32_out = [D(q*q), l(+1)(q), l(-1)(q), g_L'(q), g_R'(q), def(q)]
+ * (l(-1) and g_L' the mirror images of l(+1) and g_R', def the column-sum
+ * defects of the rounded deviation-form operator divided by sum w).  Buffers
+ * are host memory owned by the caller.  Errors: BGK_EINVAL. */
+BGK_API bgk_status bgk_fr_tables(int order, double *fr_out, float *curv32_out);
+
 /* N_e, N_s, N_u and the number of components (1 or 2). */
 BGK_API bgk_status bgk_sizes(const bgk_ctx *ctx, int *n_elem, int *n_sol, int *n_vel, int *n_comp);
 

@@ -46,6 +46,7 @@ SIGNATURES = {
     "bgk_node_coords": (c_int, [c_void_p, c_void_p, c_int]),
     "bgk_set_es_tensor": (c_int, [c_void_p, c_int]),
     "bgk_curved_metrics": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "bgk_fr_tables": (c_int, [c_int, c_void_p, c_void_p]),
     "bgk_set_state": (c_int, [c_void_p, c_void_p, c_int]),
     "bgk_get_state": (c_int, [c_void_p, c_void_p, c_int]),
     "bgk_set_maxwellian": (c_int, [c_void_p, c_void_p, c_int]),
@@ -167,6 +168,30 @@ def descriptors(wl, node_xyz=None):
         v.n[d], v.lo[d], v.hi[d] = wl.vel_n[d], wl.vel_lo[d], wl.vel_hi[d]
     g = GasDesc(wl.delta, wl.Pr, wl.mu_ref, wl.theta_ref, wl.theta_S)
     return m, v, g
+
+
+def fr_tables(order):
+    """bgk_fr_tables: the library's FP64 FR operators and the FP32 tables of the
+    curvilinear mixed stage, as dicts of numpy arrays (host only)."""
+    lib = load()
+    q = order + 1
+    fr = np.empty(6 * q + q * q)
+    c32 = np.empty(q * q + 5 * q, dtype=np.float32)
+    st = lib.bgk_fr_tables(order, fr.ctypes.data, c32.ctypes.data)
+    if st != BGK_OK:
+        raise BGKError(st, "bgk_fr_tables failed")
+    names = [("xi", q), ("w", q), ("D", q * q), ("lm", q), ("lp", q), ("dgL", q), ("dgR", q)]
+    out, o = {}, 0
+    for n, k in names:
+        out[n] = fr[o:o + k].copy()
+        o += k
+    out["D"] = out["D"].reshape(q, q)
+    c, o = {}, 0
+    for n, k in [("D", q * q), ("lp", q), ("lm", q), ("dgL", q), ("dgR", q), ("def", q)]:
+        c[n] = c32[o:o + k].copy()
+        o += k
+    c["D"] = c["D"].reshape(q, q)
+    return out, c
 
 
 def curved_metrics(wl, node_xyz):

@@ -760,6 +760,33 @@ bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
     return st;
 }
 
+bgk_status bgk_fr_tables(int order, double *fr_out, float *curv32_out) {
+    if (order < 1 || order > 4 || !fr_out || !curv32_out) return BGK_EINVAL;
+    FROps fr{};
+    build_fr(order, fr);
+    CurvOps32 c;
+    build_curv_ops32(fr, c);
+    const int q = order + 1;
+    double *o = fr_out;
+    for (int i = 0; i < q; ++i) *o++ = fr.xi[i];
+    for (int i = 0; i < q; ++i) *o++ = fr.wq[i];
+    for (int i = 0; i < q; ++i)
+        for (int j = 0; j < q; ++j) *o++ = fr.D[i][j];
+    for (int i = 0; i < q; ++i) *o++ = fr.lm[i];
+    for (int i = 0; i < q; ++i) *o++ = fr.lp[i];
+    for (int i = 0; i < q; ++i) *o++ = fr.dgL[i];
+    for (int i = 0; i < q; ++i) *o++ = fr.dgR[i];
+    float *f = curv32_out;
+    for (int i = 0; i < q; ++i)
+        for (int j = 0; j < q; ++j) *f++ = c.D[i][j];
+    for (int i = 0; i < q; ++i) *f++ = c.lp[i];
+    for (int i = 0; i < q; ++i) *f++ = c.lm[i];
+    for (int i = 0; i < q; ++i) *f++ = c.dgL[i];
+    for (int i = 0; i < q; ++i) *f++ = c.dgR[i];
+    for (int i = 0; i < q; ++i) *f++ = c.def[i];
+    return BGK_OK;
+}
+
 bgk_status bgk_curved_metrics(const bgk_mesh_desc *mesh, double *S, double *J, double *fvec) {
     if (!mesh || !mesh->node_xyz || !S || !J || !fvec) return BGK_EINVAL;
     if (mesh->order < 1 || mesh->order > 4) return BGK_EINVAL;

@@ -146,3 +146,68 @@ def test_library_metric_terms_equal_the_oracle(libbgk):
                 f_o = mesh.face[(d, side)].reshape(wl.n_elem, q * q, 3)
                 f_l = fv[:, 2 * d + (side > 0)]
                 assert np.max(np.abs(f_l - f_o)) <= 1e-12 * sc, (wl.name, d, side)
+
+
+def test_library_fr_operators_equal_the_oracle(libbgk):
+    """The library's host FR operators (nodes, weights, D, traces, correction
+    derivatives) equal the oracle's pinned FR1D to 1e-14, p = 1..4."""
+    import numpy as np
+    from oracle.fr import FR1D
+    for p in (1, 2, 3, 4):
+        lib_fr, _ = bgk.fr_tables(p)
+        o = FR1D(p)
+        for name, ref in (("xi", o.xi), ("w", o.wq), ("D", o.D), ("lm", o.l_minus), ("lp", o.l_plus),
+                          ("dgL", o.dgL), ("dgR", o.dgR)):
+            assert np.max(np.abs(lib_fr[name] - ref)) <= 1e-14 * max(1.0, np.max(np.abs(ref))), (p, name)
+
+
+def test_curvilinear_fp32_line_operator_conserves_exactly():
+    """One line of the curvilinear mixed stage, applied in exact rational
+    arithmetic to the library's stored FP32 tables: each node's residual is
+    the deviation form (off-diagonal D and the column defects acting on
+    A_j (f_j - f_i), the two lifted face jumps A_face (F* - f_i) - trace) plus
+    f_i times its geometric remainder (the f_i-proportional terms of the same
+    operator written on A_j - A_i).  Whatever the node values, flux
+    coefficients and common fluxes, the W-weighted sum of the residuals equals
+    the face fluxes s_R A_R F*_R + s_L A_L F*_L with s_R = -s_L = sum W g_R'
+    (the same weight on both sides of every face), to the rounding of the
+    stored defects: the FP32 tables conserve the quadrature total exactly."""
+    import random
+    from fractions import Fraction as Fr
+    rng = random.Random(7)
+    for p in (1, 2, 3):
+        fr, c = bgk.fr_tables(p)
+        q = p + 1
+        W = [Fr(float(v)) for v in fr["w"]]
+        D = [[Fr(float(c["D"][i][j])) for j in range(q)] for i in range(q)]
+        lp = [Fr(float(v)) for v in c["lp"]]
+        lm = [Fr(float(v)) for v in c["lm"]]
+        gL = [Fr(float(v)) for v in c["dgL"]]
+        gR = [Fr(float(v)) for v in c["dgR"]]
+        de = [Fr(float(v)) for v in c["def"]]
+        # the left-face tables are the mirror images of the right-face ones
+        assert all(lm[i] == lp[q - 1 - i] and gL[i] == -gR[q - 1 - i] for i in range(q))
+        sR = sum(W[i] * gR[i] for i in range(q))
+        sL = sum(W[i] * gL[i] for i in range(q))
+        assert sR + sL == 0 and abs(float(sR) - 1.0) < 1e-6
+        # constant data see no defect: the defects sum to zero up to their FP32 rounding
+        dscale = max(abs(float(v)) for v in c["def"]) + 1e-30
+        assert abs(float(sum(de))) <= q * 2.0 ** -23 * dscale
+        for trial in range(4):
+            A = [Fr(rng.uniform(-2, 2)) for _ in range(q)]
+            AL, AR = Fr(rng.uniform(-2, 2)), Fr(rng.uniform(-2, 2))
+            f = [Fr(rng.uniform(0, 1)) for _ in range(q)]
+            FL, FR = Fr(rng.uniform(0, 1)), Fr(rng.uniform(0, 1))
+            total = Fr(0)
+            for i in range(q):
+                w = [A[j] * (f[j] - f[i]) for j in range(q)]
+                t = sum((D[i][j] - de[j]) * w[j] for j in range(q) if j != i)
+                t += gL[i] * (AL * (FL - f[i]) - sum(lm[j] * w[j] for j in range(q)))
+                t += gR[i] * (AR * (FR - f[i]) - sum(lp[j] * w[j] for j in range(q)))
+                dA = [A[j] - A[i] for j in range(q)]
+                H = sum(D[i][j] * dA[j] for j in range(q) if j != i) - sum(de[j] * dA[j] for j in range(q))
+                H += gR[i] * (AR - A[i] - sum(lp[j] * dA[j] for j in range(q)))
+                H += gL[i] * (AL - A[i] - sum(lm[j] * dA[j] for j in range(q)))
+                total += W[i] * (t + f[i] * H)
+            err = total - (sR * AR * FR + sL * AL * FL)
+            assert abs(float(err)) <= 1e-13, (p, trial, float(err))
