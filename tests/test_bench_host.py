@@ -1,0 +1,84 @@
+"""Host logic of the benchmark on the CPU: the clock summary of the sampled
+nvidia-smi rows, the per-kernel roofline arithmetic, the choice of the
+dominant kernel and the algorithmic work counts the roofline divides."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _row(sm, mx, hw="Not Active", hwt="Not Active", swt="Not Active", cap="Not Active"):
+    return "0, %s, %s, 812.40, 0x0000000000000000, %s, %s, %s, %s\n" % (sm, mx, hw, hwt, swt, cap)
+
+
+def test_clock_summary_median_max_and_no_reasons():
+    c = bench.summarize_clocks([_row(2070, 2070), _row(2055, 2070), _row(2070, 2070)])
+    assert c["sm_mhz"] == 2070 and c["sm_max_mhz"] == 2070 and c["reasons"] == [] and c["samples"] == 3
+
+
+def test_clock_summary_reports_each_active_reason_once():
+    rows = [_row(1980, 2070, cap="Active"), _row(2070, 2070), _row(1900, 2070, cap="Active", hwt="Active")]
+    c = bench.summarize_clocks(rows)
+    assert c["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+    assert c["sm_mhz"] == 1980
+
+
+def test_clock_summary_skips_short_rows_and_unavailable_clocks():
+    rows = ["garbage\n", "0, [N/A], [N/A], 1.0, 0x0, Not Active, Not Active, Not Active, Not Active\n",
+            _row(2070, 2070)]
+    c = bench.summarize_clocks(rows)
+    assert c["samples"] == 2 and c["sm_mhz"] == 2070 and c["sm_max_mhz"] == 2070
+    assert bench.summarize_clocks([])["reasons"] == ["no samples"]
+
+
+class _WL:
+    def __init__(self, dof, p, n_comp, n1):
+        self.dof, self.p, self.n_comp, self.vel_n = dof, p, n_comp, (n1, n1, n1)
+
+
+def _result(stage_ms, q_ms, launches, iters):
+    return {"prof": {"stage": (stage_ms * launches, launches), "qprime": (q_ms * launches, launches)},
+            "newton": {"mean_iters": iters}}
+
+
+def test_mixed_roofline_is_algorithmic_bytes_over_event_time():
+    wl = _WL(3.62e9, 3, 1, 24)
+    peaks = {"hbm_gbs": 6689.8, "fp32_fma": 78.5e12, "fp64_fma": 1.256e12}
+    rl = bench.kernel_rooflines(wl, _result(21.4, 7.9, 9, 0.0), peaks, "mixed")
+    st = rl["stage"]
+    assert st["bound"] == "hbm" and st["unit"] == "GB/s"
+    # 10.67 B per DOF (F read + write, f^n in two of three stages, FP32) in 21.4 ms
+    assert st["achieved"] == pytest.approx(3.62e9 * 4 * 8 / 3 / 21.4e-3 / 1e9)
+    assert st["achieved"] == pytest.approx(1804, rel=1e-3)
+    assert st["frac"] == pytest.approx(st["achieved"] / 6689.8)
+    assert st["traffic"] is None
+    d = bench.dominant_roofline(rl)
+    assert d["kernel"] == "stage" and "MEASURED_PEAKS" in d["peak_source"]
+
+
+def test_fp64_roofline_counts_flops_and_evaluations():
+    wl = _WL(3.62e9, 3, 1, 24)
+    peaks = {"hbm_gbs": 6689.8, "fp32_fma": 78.5e12, "fp64_fma": 1.256e12}
+    rl = bench.kernel_rooflines(wl, _result(384.0, 246.0, 3, 2.0), peaks, "fp64")
+    assert rl["stage"]["achieved"] == pytest.approx(3.62e9 * 100.25 / 0.384 / 1e12)
+    assert rl["qprime"]["achieved"] == pytest.approx(3.62e9 * 3.0 * (12 + 109 / 24) / 0.246 / 1e12)
+    assert rl["stage"]["frac"] == pytest.approx(rl["stage"]["achieved"] / 1.256)
+    assert bench.dominant_roofline(rl)["kernel"] == "stage"
+    # the longer kernel dominates whichever it is
+    rl = bench.kernel_rooflines(wl, _result(100.0, 246.0, 3, 2.0), peaks, "fp64")
+    assert bench.dominant_roofline(rl)["kernel"] == "qprime"
+
+
+def test_algorithmic_work_counts():
+    # FR 6(p+1) + 5 + 12 + 9/(p+1) + 6 per component, equilibrium/source/RK 26 + 3, epilogue 22
+    assert bench.stage_flops_per_dof(3, 1) == pytest.approx(100.25)
+    assert bench.stage_flops_per_dof(1, 1) == pytest.approx(6 * 2 + 5 + 12 + 4.5 + 6 + 29 + 22)
+    # G adds a second FR, 4 source flops and 2 epilogue flops
+    assert bench.stage_flops_per_dof(2, 2) - bench.stage_flops_per_dof(2, 1) == pytest.approx(6 * 3 + 5 + 12 + 3 + 6 + 6)
+    assert bench.stage_bytes_per_dof(1, 4) == pytest.approx(32 / 3)
+    assert bench.stage_bytes_per_dof(2, 8) == pytest.approx(128 / 3)
+    assert bench.job_throughput(1, 3.62e9, 3, 87.9 * 3) == pytest.approx(3.62e9 * 3 / (87.9e-3))
