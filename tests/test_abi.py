@@ -211,3 +211,46 @@ def test_curvilinear_fp32_line_operator_conserves_exactly():
                 total += W[i] * (t + f[i] * H)
             err = total - (sR * AR * FR + sL * AL * FL)
             assert abs(float(err)) <= 1e-13, (p, trial, float(err))
+
+
+def test_plain_c_program_links_and_calls_the_library(tmp_path, libbgk):
+    """A C program built against include/bgk.h and linked to libbgk.so (no
+    ctypes) gets BGK_EINVAL and a message for an invalid descriptor and for
+    missing arguments, and reads the FR operators, which equal the oracle's."""
+    import subprocess
+    import numpy as np
+    from oracle.fr import FR1D
+    src = tmp_path / "client.c"
+    src.write_text("""#include <stdio.h>
+#include <string.h>
+#include "bgk.h"
+int main(void) {
+  bgk_mesh_desc m; memset(&m, 0, sizeof m);
+  bgk_vgrid_desc v = {{8, 8, 8}, {-6, -6, -6}, {6, 6, 6}};
+  bgk_gas_desc g = {0.0, 1.0, 0.08, 1.0, -1.0};
+  m.n[0] = m.n[1] = m.n[2] = 2; m.hi[0] = m.hi[1] = m.hi[2] = 1.0;
+  m.periodic[0] = m.periodic[1] = m.periodic[2] = 1; m.order = 9;          /* order out of range */
+  bgk_ctx *ctx = NULL;
+  int st = bgk_create(&ctx, &m, &v, &g, BGK_FP64, NULL);
+  const char *msg = bgk_last_error(ctx);
+  printf("%d %d\\n", st, (int)(msg != NULL && strlen(msg) > 0));
+  bgk_destroy(ctx);
+  printf("%d %d\\n", bgk_curved_metrics(&m, NULL, NULL, NULL), bgk_fr_tables(0, NULL, NULL));
+  double fr[6 * 4 + 16]; float c32[16 + 5 * 4];
+  printf("%d\\n", bgk_fr_tables(3, fr, c32));
+  for (int i = 0; i < 6 * 4 + 16; ++i) printf("%.17g\\n", fr[i]);
+  return 0;
+}
+""")
+    exe = tmp_path / "client"
+    libdir = os.path.join(ROOT, "paper_2312_06567_gb300")
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-L", libdir, "-lbgk",
+                    "-Wl,-rpath," + libdir, "-o", str(exe)], check=True)
+    lines = subprocess.check_output([str(exe)]).decode().split("\n")
+    assert lines[0].split() == [str(bgk.BGK_EINVAL), "1"]
+    assert lines[1].split() == [str(bgk.BGK_EINVAL)] * 2
+    assert int(lines[2]) == bgk.BGK_OK
+    v = np.array([float(t) for t in lines[3:3 + 40]])
+    o = FR1D(3)
+    ref = np.concatenate([o.xi, o.wq, o.D.ravel(), o.l_minus, o.l_plus, o.dgL, o.dgR])
+    assert np.max(np.abs(v - ref)) <= 1e-14 * np.max(np.abs(ref))
