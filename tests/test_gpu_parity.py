@@ -176,3 +176,30 @@ def test_newton_nonconvergence_is_reported_not_trapped(lib):
         s.set_newton(1e-13, 50)
         s.set_state(f)
         assert s.step(wl.dt(), 1) == lib.BGK_OK
+
+
+def test_degenerate_and_rejected_calls_leave_the_context_usable(lib):
+    """Zero steps leave the state and totals bit for bit; a non-positive dt, a
+    negative step count and an empty Q' batch are rejected with BGK_EINVAL
+    before any launch; the context then steps and matches the oracle."""
+    wl = CASES["sine_box_p1"]()
+    f = W.random_anisotropic_state(wl, seed=2)
+    dt = wl.dt()
+    with lib.Solver(wl) as s:
+        s.set_state(f)
+        t0 = s.totals()
+        assert s.step(dt, 0) == lib.BGK_OK
+        assert np.array_equal(s.get_state(), f)
+        assert np.array_equal(s.totals(), t0)
+        for bad_dt, n in ((0.0, 1), (-dt, 1), (float("nan"), 1), (dt, -1)):
+            with pytest.raises(lib.BGKError) as ei:
+                s.step(bad_dt, n)
+            assert ei.value.status == lib.BGK_EINVAL
+        with pytest.raises(lib.BGKError) as ei:
+            s.qprime(np.zeros((0, 11)))
+        assert ei.value.status == lib.BGK_EINVAL
+        assert np.array_equal(s.get_state(), f)
+        assert s.step(dt, 1) == lib.BGK_OK
+        f_gpu = s.get_state()
+    f_ora, _ = ostage.problem_from_workload(wl).step(f, dt)
+    assert slab_err(f_gpu, f_ora) <= TOL
