@@ -254,3 +254,34 @@ int main(void) {
     o = FR1D(3)
     ref = np.concatenate([o.xi, o.wq, o.D.ravel(), o.l_minus, o.l_plus, o.dgL, o.dgR])
     assert np.max(np.abs(v - ref)) <= 1e-14 * np.max(np.abs(ref))
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without the built library the binding raises (there is no CPU path)."""
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_2312_06567_gb300 import bgk, workloads as W\n"
+            "bgk.LIB_PATH = %r\n"
+            "try:\n"
+            "    bgk.load(bgk.LIB_PATH)\n"
+            "except RuntimeError as e:\n"
+            "    assert 'no CPU fallback' in str(e); print('load raised')\n"
+            "import functools\n"
+            "bgk.load = functools.partial(bgk.load, %r)\n"
+            "try:\n"
+            "    bgk.Solver(W.periodic_sine_box())\n"
+            "except RuntimeError as e:\n"
+            "    print('solver raised')\n") % (ROOT, str(tmp_path / "absent.so"), str(tmp_path / "absent.so"))
+    out = subprocess.check_output([sys.executable, "-c", code]).decode()
+    assert "load raised" in out and "solver raised" in out
+
+
+def test_product_package_never_imports_the_oracle():
+    """The oracle is test infrastructure: no module of the package imports it."""
+    pkg = os.path.join(ROOT, "paper_2312_06567_gb300")
+    for f in os.listdir(pkg):
+        if f.endswith(".py"):
+            text = open(os.path.join(pkg, f)).read()
+            assert not re.search(r"^\s*(from|import)\s+oracle\b", text, re.M), f
+            assert "oracle" not in re.findall(r"import_module\(['\"](\w+)", text), f
