@@ -35,6 +35,20 @@
 #define BGK_VTAB 8          // velocity table record: u1 u2 u3 w e=|u|^2/2 w*u1 w*u1^2 (2/h1)*u1
 #define BGK_MAXV 128        // nodes per velocity axis at most
 
+// Dynamic shared-memory limits a launcher has raised with cudaFuncSetAttribute,
+// which acts on the calling thread's current device: one entry per device, so
+// each device of a process gets its own call.
+#define BGK_MAX_DEVICES 64
+struct SmemLimit {
+    size_t set[BGK_MAX_DEVICES] = {};
+    // the current device's entry, or nullptr if the device cannot be queried
+    size_t *slot() {
+        int d = 0;
+        if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= BGK_MAX_DEVICES) return nullptr;
+        return &set[d];
+    }
+};
+
 // Device status bits (OR-ed by kernels, read by the host after a stage).
 #define BGK_DEV_NOCONV 1u
 #define BGK_DEV_NONFINITE 2u

@@ -807,11 +807,13 @@ template <int Q, int C>
 static cudaError_t stage32_tma(const StageArgs<float> &a, int n_vblk, int depth, cudaStream_t s) {
     using G = TmaGeom<Q, C>;
     const size_t smem = tma_smem<Q, C>(depth);
-    static size_t attr = 0;               // dynamic shared memory limit set so far
-    if (smem > attr) {
+    static SmemLimit lim;                 // dynamic shared memory limit set so far, per device
+    size_t *attr = lim.slot();
+    if (!attr) return cudaErrorInvalidDevice;
+    if (smem > *attr) {
         cudaError_t e = cudaFuncSetAttribute(k_stage_f32_tma<Q, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        attr = smem;
+        *attr = smem;
     }
     const int cpr = (a.mesh.n[0] + G::EB - 1) / G::EB;
     dim3 grid(cpr * a.mesh.n[1] * a.mesh.n[2], n_vblk);

@@ -644,15 +644,17 @@ size_t line_smem(int depth) {
 template <int Q, int C, int EB, int NPT>
 cudaError_t line_launch(const StageArgs<float> &a, int n_vblk, int depth, cudaStream_t s) {
     const size_t smem = line_smem<Q, C, EB, NPT>(depth);
-    static size_t attr = 0;
-    if (smem > attr) {
+    static SmemLimit lim;
+    size_t *attr = lim.slot();
+    if (!attr) return cudaErrorInvalidDevice;
+    if (smem > *attr) {
         cudaError_t e = cudaFuncSetAttribute(k_stage_f32_line<Q, C, EB, NPT, false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_stage_f32_line<Q, C, EB, NPT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem);
         if (e != cudaSuccess) return e;
-        attr = smem;
+        *attr = smem;
     }
     const int cpr = (a.mesh.n[0] + EB - 1) / EB;
     dim3 grid(cpr * a.mesh.n[1] * a.mesh.n[2], n_vblk);

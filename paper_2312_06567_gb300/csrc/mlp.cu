@@ -178,11 +178,13 @@ size_t mlp_train_smem() { return sizeof(TrainSmem); }
 cudaError_t launch_mlp_train(const MlpParams &p, const float *x, const float *t, const int *idx, int nb,
                              float *grad, double *loss, int bf16, cudaStream_t s) {
     const size_t smem = sizeof(TrainSmem);
-    static bool attr = false;
-    if (!attr) {
+    static SmemLimit lim;
+    size_t *attr = lim.slot();
+    if (!attr) return cudaErrorInvalidDevice;
+    if (smem > *attr) {
         cudaError_t e = cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        attr = true;
+        *attr = smem;
     }
     k_mlp_train<<<(nb + SB - 1) / SB, NT, smem, s>>>(p, x, t, idx, nb, grad, loss, bf16);
     return cudaGetLastError();
