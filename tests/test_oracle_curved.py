@@ -291,6 +291,34 @@ def test_wall_density_balances_the_outgoing_mass_flux():
     assert np.all(np.abs(flux) <= 1e-14 * scale)
 
 
+@pytest.mark.parametrize("theta_g,theta_w", [(1.0, 0.5), (0.6, 1.4)])
+def test_wall_density_tends_to_the_half_space_flux_balance(theta_g, theta_w):
+    """Gas at rest at (rho_g, theta_g) against a wall at theta_w: the mass
+    carried toward the wall by a half-Maxwellian is rho sqrt(theta / 2 pi), so
+    the balance gives rho_w = rho_g sqrt(theta_g / theta_w) (kinetic theory,
+    independent of the discretisation).  On symmetric grids with a node at
+    u_n = 0 the discrete rho_w converges to it at second order in the normal
+    velocity spacing (the one-sided sums have a kink at u_n = 0)."""
+    errs = []
+    for n1 in (17, 33, 65):
+        wl = W.wavy_periodic_box(p=1, n=(2, 1, 1), vel_n=(n1, 21, 21)).replace(
+            periodic=(False, True, True), delta=0.0, vel_lo=(-7.0, -7.0, -7.0), vel_hi=(7.0, 7.0, 7.0),
+            diffuse={(0, s): ((0.0, 0.0, 0.0), theta_w) for s in (-1, 1)}, mapping=None)
+        x = W.node_positions(wl)
+        pb = curved.problem_from_workload(wl, x)
+        f = W.maxwellian_state(wl, x, fields=(np.full(x.shape[:-1], 1.3), np.zeros(x.shape),
+                                              np.full(x.shape[:-1], theta_g)))
+        q = pb.q
+        fl = np.moveaxis(f.reshape(f.shape[:3] + (q, q, q)), 5, -1)
+        fm = np.einsum("j,...j->...", pb.fr.l_minus, fl)
+        rho_w = pb.wall_density(0, -1, fm)[pb.mesh.nbr[(0, -1)] < 0]
+        exact = 1.3 * np.sqrt(theta_g / theta_w)
+        errs.append(float(np.max(np.abs(rho_w - exact))) / exact)
+    assert errs[-1] <= 5e-3, errs
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(rates >= 1.9), (errs, rates)
+
+
 def test_closed_faces_conserve_every_total():
     """No flux crosses a closed face: a box closed at both ends of the first
     axis conserves all five totals through a full step."""
