@@ -277,3 +277,36 @@ def test_es_source_relaxes_stress_and_heat_flux_at_the_prandtl_rates(delta, Pr):
     dq = 0.5 * np.einsum("k,ki->i", w * S * np.sum(c * c, axis=1), c)
     assert np.max(np.abs(dev(dPi) + (P / mu) * dev(Pi))) <= 1e-9 * (P / mu) * np.max(np.abs(dev(Pi)))
     assert np.max(np.abs(dq + (Pr * P / mu) * q)) <= 1e-9 * (Pr * P / mu) * np.max(np.abs(q))
+
+
+@pytest.mark.parametrize("delta,Pr,gfac", [(2.0, 0.72, 1.6), (2.0, 1.0, 0.5), (3.0, 2 / 3, 2.5), (0.0, 0.72, 0.0)])
+def test_modified_temperature_and_internal_energy_relaxation(delta, Pr, gfac):
+    """Continuous limit of the compatibility conditions: a Gaussian with
+    covariance T' = theta'/Pr I + (1 - 1/Pr) Pi/rho and the internal energy
+    delta theta'/2 per unit mass carry the energy of f only if
+    theta' = (tr Pi / Pr + 2 E_int) / ((3/Pr + delta) rho) (theta' = theta at
+    Pr = 1), with rho' = rho; the internal energy then relaxes toward
+    delta rho theta'/2 at rate 1/tau.  On a fine velocity grid the Newton solve
+    and the G source reproduce these closed forms to the grid's spectral
+    accuracy."""
+    vg = VelocityGrid((41, 41, 41), (-8.0,) * 3, (8.0,) * 3)
+    u, w = vg.u, vg.w
+    parts = [(0.7, np.array([0.3, -0.2, 0.1]), np.array([[1.0, 0.2, 0.0], [0.2, 0.7, 0.1], [0.0, 0.1, 0.9]])),
+             (0.5, np.array([-0.5, 0.4, 0.0]), np.array([[0.6, -0.1, 0.05], [-0.1, 1.1, 0.0], [0.05, 0.0, 0.8]]))]
+    F = _gaussian_mixture(u, parts)
+    G = gfac * F if delta > 0 else None
+    mu = 0.05
+    gas = bgk.Gas(delta=delta, Pr=Pr, mu_ref=mu, theta_S=-1.0)
+    _, S_G, info = bgk.bgk_source(F[:, None], None if G is None else G[:, None], gas, vg)
+    assert np.all(info["converged"])
+    rho = np.sum(w * F)
+    c = u - np.sum(w[:, None] * u * F[:, None], axis=0) / rho
+    Pi = np.einsum("k,ki,kj->ij", w * F, c, c)
+    e_int = np.sum(w * G) if G is not None else 0.0
+    theta_p = (np.trace(Pi) / Pr + 2.0 * e_int) / ((3.0 / Pr + delta) * rho)
+    assert abs(info["qp"][0, 4] / theta_p - 1.0) <= 5e-9
+    assert abs(info["qp"][0, 0] / rho - 1.0) <= 5e-9
+    if G is not None:
+        tau = mu / (Pr * (np.trace(Pi) + 2.0 * e_int) / (3.0 + delta))
+        target = (0.5 * delta * rho * theta_p - e_int) / tau
+        assert abs(np.sum(w * S_G[:, 0]) - target) <= 5e-9 * abs(target)
