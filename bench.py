@@ -193,6 +193,20 @@ def qprime_flops_per_dof_eval(n1):
     return 12.0 + (70.0 + 30.0 + 9.0) / n1
 
 
+def drift_is_conservation(wl):
+    """True when every face is periodic or collapsed: only then are mass,
+    momentum and energy closed, so the totals' change per step measures
+    conservation (Dirichlet faces carry flux, diffuse walls exchange momentum
+    and energy, specular faces change the normal momentum)."""
+    for d in range(3):
+        if wl.periodic[d]:
+            continue
+        for side in (-1, 1):
+            if (d, side) not in tuple(wl.closed):
+                return False
+    return True
+
+
 def max_over_ranks(x, world, device=None):
     """The largest x over the ranks (the slowest rank's time; x itself on one
     rank).  Works with any torch.distributed backend (gloo needs device=None)."""
@@ -455,10 +469,11 @@ def main():
         "config": {"workload": wl.name, "dof": wl.dof, "elements": wl.n_elem, "order": wl.p,
                    "velocities": wl.n_vel, "form": main_form, "parallelism": "replicas",
                    "l2": "inputs larger than L2 (state %.1f GB per copy)" %
-                         (wl.dof * (8 if main_form == "fp64" else 4) / 1e9)},
+                         (wl.dof * wl.n_comp * (8 if main_form == "fp64" else 4) / 1e9)},
         "clocks": r["clocks"],
         "e2e": r["e2e"],
         "conservation_drift_per_step": r["drift"],
+        "drift_is_conservation": drift_is_conservation(wl),
         "gpu_launches": launches,
         "kernels_ms_per_step": {k: v[0] for k, v in r["prof"].items()},
         "launch": "cuda graph replay" if not args.no_graphs else "direct launches",

@@ -82,3 +82,15 @@ def test_algorithmic_work_counts():
     assert bench.stage_bytes_per_dof(1, 4) == pytest.approx(32 / 3)
     assert bench.stage_bytes_per_dof(2, 8) == pytest.approx(128 / 3)
     assert bench.job_throughput(1, 3.62e9, 3, 87.9 * 3) == pytest.approx(3.62e9 * 3 / (87.9e-3))
+
+
+def test_drift_is_a_conservation_measure_only_on_closed_meshes():
+    from paper_2312_06567_gb300 import workloads as W
+    assert bench.drift_is_conservation(W.taylor_green_box())            # periodic box
+    assert bench.drift_is_conservation(W.periodic_sine_box())
+    assert not bench.drift_is_conservation(W.normal_shock_tube())       # Dirichlet x-ends
+    assert not bench.drift_is_conservation(W.sphere_ogrid(n=(2, 4, 4), vel_n=(6, 6, 6)))  # wall, farfield
+    box = W.normal_shock_tube().replace(dirichlet={})
+    assert bench.drift_is_conservation(box.replace(closed=((0, -1), (0, 1))))
+    assert not bench.drift_is_conservation(box.replace(specular=((0, -1), (0, 1))))
+    assert not bench.drift_is_conservation(box.replace(closed=((0, -1),), specular=((0, 1),)))
