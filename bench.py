@@ -455,8 +455,18 @@ def main():
     wl, results, peaks = run_ours(args, rank, world, dev)
     if rank != 0:
         return
-    main_form = next((f for f in ("mixed_learned", "mixed", "fp64") if f in results), list(results)[0])
     peaks["hbm_gbs"] = _measured_hbm()
+    line = compose_line(args, wl, results, peaks, world)
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl)
+    print(json.dumps(line))
+
+
+def compose_line(args, wl, results, peaks, world):
+    """The benchmark's JSON line from the per-form results of run_ours: the
+    headline form (mixed + learned guess, else mixed, else FP64) at the top
+    level, the other forms under their names."""
+    main_form = next((f for f in ("mixed_learned", "mixed", "fp64") if f in results), list(results)[0])
     r = results[main_form]
     ms_per_step = r["ms"] / args.steps
     value = job_throughput(world, wl.dof, args.steps, r["ms"])
@@ -499,9 +509,7 @@ def main():
                           "conservation_drift_per_step": rr["drift"],
                           "roofline_kernels": kernel_rooflines(wl, rr, peaks, form),
                           "stage_kernel": rr["stage_kernel"], "clocks": rr["clocks"]}
-    if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl)
-    print(json.dumps(line))
+    return line
 
 
 if __name__ == "__main__":

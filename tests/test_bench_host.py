@@ -94,3 +94,48 @@ def test_drift_is_a_conservation_measure_only_on_closed_meshes():
     assert bench.drift_is_conservation(box.replace(closed=((0, -1), (0, 1))))
     assert not bench.drift_is_conservation(box.replace(specular=((0, -1), (0, 1))))
     assert not bench.drift_is_conservation(box.replace(closed=((0, -1),), specular=((0, 1),)))
+
+
+def _fake_form(stage_ms, q_ms, iters, learned=False, e2e=None):
+    """What run_ours records per form, for one profiled step (3 stages)."""
+    prof = {"moments": (0.0, 0), "qprime": (3 * q_ms, 3), "stage": (3 * stage_ms, 3), "other": (0.0, 0),
+            "wall": (0.0, 0)}
+    newton = dict(mean_iters=iters, max_iters=int(iters), max_residual=1e-7)
+    if learned:
+        newton["guess_fallbacks"] = 0
+        newton["training"] = {"seconds": 0.5, "epochs": 8}
+    return dict(ms=3 * (3 * stage_ms + 3 * q_ms), status="BGK_OK", prof=prof,
+                clocks={"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []},
+                newton=newton, e2e=e2e, drift=3e-11, stage_kernel={"variant": "line", "depth": 2, "ms_per_stage": stage_ms},
+                diagnostics=None)
+
+
+def test_json_line_carries_the_contract_keys():
+    """compose_line on recorded-looking results: the headline form, the
+    contract keys, the dominant kernel's roofline with the measured traffic,
+    the other forms nested, and a line that serialises as JSON."""
+    import argparse
+    import json
+    from paper_2312_06567_gb300 import workloads as W
+    wl = W.taylor_green_box()
+    e2e = {"value": 2.1e10, "unit": bench.UNIT, "h2d_bytes_per_step": 14495514624, "d2h_bytes_per_step": 14495514624}
+    results = {"fp64": _fake_form(383.0, 247.0, 2.0),
+               "mixed": _fake_form(21.5, 11.6, 1.0),
+               "mixed_learned": _fake_form(21.4, 7.9, 0.0, learned=True, e2e=e2e)}
+    peaks = {"fp64_fma": 1.256e12, "fp32_fma": 78.5e12, "hbm_gbs": 6689.8}
+    args = argparse.Namespace(steps=3, warmup=3, no_graphs=False)
+    line = bench.compose_line(args, wl, results, peaks, 1)
+    json.dumps(line)
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "clocks", "e2e", "gpu_launches", "roofline"):
+        assert k in line, k
+    assert line["config"]["form"] == "mixed_learned" and line["config"]["workload"] == wl.name
+    assert line["value"] == pytest.approx(wl.dof * 3 / (3 * (3 * 21.4 + 3 * 7.9) / 3 * 1e-3))
+    assert line["gpu_launches"] == 6 * 3 and line["e2e"] == e2e
+    assert line["drift_is_conservation"] is True
+    rl = line["roofline"]
+    assert rl["kernel"] == "stage" and rl["bound"] == "hbm" and rl["unit"] == "GB/s"
+    assert rl["frac"] == pytest.approx(rl["achieved"] / 6689.8)
+    assert rl["traffic"] == pytest.approx(11.25 * wl.dof)      # ncu traffic of the line kernel, per launch
+    assert set(line) >= {"mixed", "fp64"} and line["fp64"]["value"] < line["mixed"]["value"]
+    assert line["fp64"]["roofline_kernels"]["stage"]["unit"] == "TFLOP/s"
