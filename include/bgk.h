@@ -121,16 +121,24 @@ typedef struct {
     double delta, Pr, mu_ref, theta_ref, theta_S;
 } bgk_gas_desc;
 
-/* Create a solver context on the current CUDA device.  stream: a
- * cudaStream_t (NULL = legacy default stream).  Allocates three state
- * copies (f^n and two stage buffers) plus per-point work arrays.
+/* Create a solver context on the current CUDA device for the problem as the
+ * paper states it (section "Methodology": the mesh and FR order, the discrete
+ * velocity set and its weights, the gas), with the state precision
+ * BGK_FP64 or BGK_MIXED.  stream: a cudaStream_t (NULL = legacy default
+ * stream).  Allocates three state copies (f^n and two stage buffers) plus
+ * per-point work arrays; the descriptors are read during the call only.  On
+ * failure *out may still hold a context whose bgk_last_error explains the
+ * error; pass it to bgk_destroy.
  * Errors: BGK_EINVAL (descriptor), BGK_ENOMEM, BGK_ECUDA. */
 BGK_API bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_desc *vgrid,
                       const bgk_gas_desc *gas, int precision, void *stream);
+/* Synchronise the context's stream, release every device buffer, graph,
+ * stream and event it owns, and free it.  Errors: BGK_EINVAL (NULL). */
 BGK_API bgk_status bgk_destroy(bgk_ctx *ctx);
 
-/* The metric terms the library builds for a curvilinear mesh (host only, no
- * context, no CUDA call): for mesh->node_xyz (required) and the FR order,
+/* The metric terms the library builds for a curvilinear mesh (section
+ * "Numerical method": FR on curved elements through the transformed flux;
+ * host only, no context, no CUDA call): for mesh->node_xyz (required) and the FR order,
  * S[P][9] = (S^1, S^2, S^3) at each solution node (S^d = J grad xi_d, the
  * conservative curl form on the element's Gauss--Lobatto points evaluated at
  * the Gauss nodes), J[P] = det(dX/dxi) at the nodes, and the face vectors
@@ -152,21 +160,30 @@ BGK_API bgk_status bgk_curved_metrics(const bgk_mesh_desc *mesh, double *S, doub
  * are host memory owned by the caller.  Errors: BGK_EINVAL. */
 BGK_API bgk_status bgk_fr_tables(int order, double *fr_out, float *curv32_out);
 
-/* N_e, N_s, N_u and the number of components (1 or 2). */
+/* N_e, N_s, N_u and the number of components (1 or 2); any output may be
+ * NULL.  Errors: BGK_EINVAL (NULL context). */
 BGK_API bgk_status bgk_sizes(const bgk_ctx *ctx, int *n_elem, int *n_sol, int *n_vel, int *n_comp);
 
 /* Solution-node coordinates x[P][3], P = N_e N_s: on the uniform box in the
  * context's own Gauss--Legendre node placement; on a curvilinear mesh the
- * node_xyz the context was created with. */
+ * node_xyz the context was created with.  x is host (on_device = 0) or device
+ * memory (1), written before the call returns.  Errors: BGK_EINVAL, BGK_ECUDA. */
 BGK_API bgk_status bgk_node_coords(const bgk_ctx *ctx, double *x, int on_device);
 
-/* Copy the state in / out (f[c][k][e][s], element type by precision). */
+/* Copy the state in / out: the distribution f of section "Governing
+ * equations" (F, and G when delta > 0) as f[c][k][e][s], double for
+ * BGK_FP64 and float for BGK_MIXED, C N_u P elements.  f is host
+ * (on_device = 0) or device memory (1); host copies complete before the
+ * call returns, device copies are ordered on the context's stream.  Setting
+ * the state invalidates the cached moments.  Errors: BGK_EINVAL (NULL),
+ * BGK_ECUDA. */
 BGK_API bgk_status bgk_set_state(bgk_ctx *ctx, const void *f, int on_device);
 BGK_API bgk_status bgk_get_state(bgk_ctx *ctx, void *f, int on_device);
 
 /* Set f to the isotropic Maxwellian of q[P][5] = (rho, U1, U2, U3, theta) at
  * every node (G = delta theta / 2 F).  Section "Governing equations", g_u
- * with T = theta I. */
+ * with T = theta I.  q is host (on_device = 0) or device memory (1).
+ * Errors: BGK_EINVAL (NULL), BGK_ECUDA. */
 BGK_API bgk_status bgk_set_maxwellian(bgk_ctx *ctx, const double *q, int on_device);
 
 /* Run bgk_step as CUDA-graph replays (enable = 1) or as direct launches
@@ -197,12 +214,16 @@ BGK_API bgk_status bgk_set_graphs(bgk_ctx *ctx, int enable);
  * monatomic gas only). */
 BGK_API bgk_status bgk_set_es_tensor(bgk_ctx *ctx, int enable);
 
-/* Newton controls of the Q' solve: stop when the scaled residual
- * max(|R_rho|/rho, |R_rhoU|_inf/(rho sqrt(theta)), |R_E|/E) <= tol, at most
- * max_iter updates (defaults 1e-13, 50). */
+/* Newton controls of the Q' solve (section "Numerical method": Newton's
+ * method on the discrete compatibility conditions): stop when the scaled
+ * residual max(|R_rho|/rho, |R_rhoU|_inf/(rho sqrt(theta)), |R_E|/E) <= tol,
+ * at most max_iter updates (defaults 1e-13, 50).  Errors: BGK_EINVAL (NULL,
+ * tol not positive, max_iter < 0). */
 BGK_API bgk_status bgk_set_newton(bgk_ctx *ctx, double tol, int max_iter);
 
-/* Engine of the Q' velocity sums.  fp32_sums = 0: FP64 throughout (the FP64
+/* Engine of the Q' velocity sums (the discrete compatibility solve of
+ * section "Numerical method"; the result is the same solution, the engine
+ * only sets the arithmetic of its sums).  fp32_sums = 0: FP64 throughout (the FP64
  * form, and optionally the mixed form).  fp32_sums = 1 (mixed form only, its
  * default): the velocity sums of the Newton iteration run on the FP32 pipe
  * (GB300 issues FP64 at 1/64 of the FP32 rate), the per-point Newton algebra
@@ -234,7 +255,8 @@ BGK_API bgk_status bgk_set_qprime_engine(bgk_ctx *ctx, int fp32_sums);
  * (variants 2-6 on the FP64 form or an unsupported order). */
 BGK_API bgk_status bgk_set_stage_kernel(bgk_ctx *ctx, int variant, int depth);
 
-/* Autotune the mixed-form stage kernel on this context's own problem: time
+/* Autotune the mixed-form stage kernel on this context's own problem (the
+ * launch configuration only; every candidate computes the same values): time
  * the plain kernel and every supported asynchronous variant at every ring
  * depth (2, 3, 4, 6, 8, 12, 16), each over `reps` stages with f^n and the moment
  * epilogue (time step dt), from the current state into a scratch buffer, and
@@ -247,25 +269,37 @@ BGK_API bgk_status bgk_set_stage_kernel(bgk_ctx *ctx, int variant, int depth);
 BGK_API bgk_status bgk_tune_stage(bgk_ctx *ctx, double dt, int reps, int *variant_out, int *depth_out,
                                   double *ms_out);
 
-/* One residual R(f) = -div(u f) + (g(Q') - f)/tau of f_in into r_out (both
- * with the state's layout and element type).  Test and debug entry; it
- * leaves the state unchanged. */
+/* One residual R(f) = -div(u f) + (g(Q') - f)/tau of f_in into r_out (the
+ * semi-discrete right-hand side of section "Methodology": FR advection plus
+ * the conservative BGK source), both with the state's layout and element
+ * type, both host (on_device = 0) or both device memory (1).  Test and debug
+ * entry; it leaves the state unchanged.  Errors: BGK_EINVAL (NULL), BGK_ECUDA,
+ * BGK_ENOCONV (a Q' solve did not converge; r_out uses the last iterate). */
 BGK_API bgk_status bgk_rhs(bgk_ctx *ctx, const void *f_in, void *r_out, int on_device);
 
-/* n_steps steps of SSP-RK3 (Shu--Osher) with step dt on the stored state.
- * Each stage is two kernels: the Q' solve from the moments of the stage
- * input, and the fused FR + source + RK update that also reduces the
- * moments of its output.  Returns BGK_ENOCONV if a Newton solve did not
- * converge (the step is still completed with the last iterate). */
+/* n_steps steps of SSP-RK3 (Shu--Osher) with step dt on the stored state
+ * (the explicit time marching of section "Methodology").  Each stage is two
+ * kernels: the Q' solve from the moments of the stage input, and the fused
+ * FR + source + RK update that also reduces the moments of its output.
+ * n_steps = 0 leaves the state as it is.  Errors: BGK_EINVAL (NULL, dt not
+ * positive, n_steps < 0), BGK_ECUDA, BGK_ETIMEOUT; BGK_ENOCONV if a Newton
+ * solve did not converge (the step is still completed with the last
+ * iterate). */
 BGK_API bgk_status bgk_step(bgk_ctx *ctx, double dt, int n_steps);
 
-/* One stage f_out = a f^n + b f_s + c R(f_s) with f^n the stored state and
- * f_s = f_in (device arrays, state layout); f_out must not alias f_in. */
+/* One Shu--Osher stage f_out = a f^n + b f_s + c R(f_s) with f^n = f_n (may
+ * be NULL when a = 0) and f_s = f_in: device arrays in the state's layout
+ * and element type; f_out must not alias f_in.  The stored state is not
+ * used or changed.  Errors: BGK_EINVAL (NULL f_in or f_out, aliasing, a != 0
+ * without f_n), BGK_ECUDA, BGK_ETIMEOUT, BGK_ENOCONV. */
 BGK_API bgk_status bgk_stage(bgk_ctx *ctx, const void *f_n, const void *f_in, void *f_out,
                      double a, double b, double c);
 
-/* Raw velocity moments of the stored state, m[P][11]: sum w F, sum w u_d F
- * (3), sum w u_d^2 F (3), sum w u1u2 F, sum w u1u3 F, sum w u2u3 F, sum w G. */
+/* Raw velocity moments of the stored state (section "Governing equations":
+ * the moments that give Q = (rho, rho U, E)), m[P][11]: sum w F, sum w u_d F
+ * (3), sum w u_d^2 F (3), sum w u1u2 F, sum w u1u3 F, sum w u2u3 F, sum w G,
+ * summed in FP64.  m is host (on_device = 0) or device memory (1).
+ * Errors: BGK_EINVAL (NULL), BGK_ECUDA. */
 BGK_API bgk_status bgk_moments(bgk_ctx *ctx, double *m, int on_device);
 
 /* Raw moments of a caller-owned state without allocating any device memory.
@@ -315,20 +349,25 @@ BGK_API bgk_status bgk_qprime(bgk_ctx *ctx, const double *m, int n_points, doubl
  * the stored state (W_s tensor Gauss weights, J_s the Jacobian at the node:
  * the affine |J_e| on the box; on a curvilinear mesh det(dX/dxi) of the
  * element's interpolant in the FP64 form, and 1 / (1/J_s rounded to FP32) in
- * the mixed form, the quadrature its stage conserves exactly). */
+ * the mixed form, the quadrature its stage conserves exactly): the conserved
+ * quantities of section "Governing equations".  totals is host memory.
+ * Errors: BGK_EINVAL (NULL), BGK_ECUDA. */
 BGK_API bgk_status bgk_totals(bgk_ctx *ctx, double totals[5]);
 
 /* Newton statistics accumulated since the last call (then reset):
  * mean and max update count per point solve, and the worst final scaled
- * residual. */
+ * residual; any output may be NULL.  Errors: BGK_EINVAL (NULL context),
+ * BGK_ECUDA. */
 BGK_API bgk_status bgk_stats(bgk_ctx *ctx, double *mean_iters, int *max_iters, double *max_residual);
 
-/* Per-kernel timing on the context's stream.  enable = 1 starts recording a
+/* Per-kernel timing on the context's stream (instrumentation; the paper has
+ * no counterpart).  enable = 1 starts recording a
  * CUDA event pair around every kernel the context launches (and clears the
  * accumulators); 0 stops.  bgk_profile_read synchronises and returns, per
  * kernel kind (BGK_K_*), the summed device milliseconds and launch counts
- * since the last enable; either array may be NULL.  Launch counts are kept
- * even when timing is off. */
+ * since the last enable; either array may be NULL (host memory otherwise).
+ * Launch counts are kept even when timing is off.  Errors: BGK_EINVAL (NULL
+ * context), BGK_ECUDA. */
 #define BGK_K_MOMENTS 0    /* raw moment partials of a state            */
 #define BGK_K_QPRIME 1     /* moment reduction + Q' Newton solve        */
 #define BGK_K_STAGE 2      /* fused FR + source + RK + moment epilogue  */
@@ -338,10 +377,12 @@ BGK_API bgk_status bgk_stats(bgk_ctx *ctx, double *mean_iters, int *max_iters, d
 BGK_API bgk_status bgk_profile(bgk_ctx *ctx, int enable);
 BGK_API bgk_status bgk_profile_read(bgk_ctx *ctx, double ms[BGK_NKINDS], long long launches[BGK_NKINDS]);
 
-/* Roofline probes of the current device (no context): kind 0 = FP64 FMA
- * throughput, 1 = FP32 FMA throughput (both in flop/s, an FMA = 2 flops),
- * 2 = FP64 exp() throughput (calls/s), 3 = FP32 exp2f throughput (calls/s).
- * Each runs a register-resident kernel over every SM for ~50 ms. */
+/* Roofline probes of the current device (no context; measurement, not the
+ * method): kind 0 = FP64 FMA throughput, 1 = FP32 FMA throughput (both in
+ * flop/s, an FMA = 2 flops), 2 = FP64 exp() throughput (calls/s), 3 = FP32
+ * exp2f throughput (calls/s), into *value (host).  Each runs a
+ * register-resident kernel over every SM for ~50 ms.  Errors: BGK_EINVAL
+ * (kind out of range, NULL value), BGK_ENOMEM, BGK_ECUDA. */
 BGK_API bgk_status bgk_probe_peak(int kind, double *value);
 
 /* ---- Learned initial guess of the Q' solve -------------------------------
@@ -361,31 +402,43 @@ BGK_API bgk_status bgk_probe_peak(int kind, double *value);
 #define BGK_MLP_LOG_STRIDE 14 /* 9 features then 5 targets per logged pair */
 
 /* mode 0: start Newton from the macroscopic state; 1: from the network
- * (requires weights from bgk_mlp_train or bgk_mlp_weights). */
+ * (requires weights from bgk_mlp_train or bgk_mlp_weights); bf16 = 1 runs
+ * the inference on BF16-rounded weights and layer inputs.  Errors:
+ * BGK_EINVAL (NULL, mode out of range, mode 1 without weights). */
 BGK_API bgk_status bgk_set_guess(bgk_ctx *ctx, int mode, int bf16);
 /* Start (enable = 1, clearing earlier pairs) or stop logging the (features,
- * Delta) pair of every converged point solve, at most max_pairs of them. */
+ * Delta) pair of every converged point solve, at most max_pairs of them
+ * (device memory owned by the context).  Errors: BGK_EINVAL (NULL, enable
+ * with max_pairs <= 0), BGK_ENOMEM, BGK_ECUDA. */
 BGK_API bgk_status bgk_mlp_log(bgk_ctx *ctx, int enable, long long max_pairs);
-/* Copy up to max_pairs logged pairs (host out[n][14]); *n_out = pairs copied. */
+/* Copy up to max_pairs logged pairs (host out[n][14]); *n_out = pairs copied.
+ * Errors: BGK_EINVAL (NULL, max_pairs < 0), BGK_ECUDA. */
 BGK_API bgk_status bgk_mlp_log_read(bgk_ctx *ctx, float *out, long long max_pairs, long long *n_out);
 /* Train from scratch on the logged pairs: normalisation from their mean and
  * standard deviation, He-normal initialisation from seed, Adam with a cosine
  * learning-rate decay from lr to lr/10, MSE loss on normalised targets.
- * *final_loss = mean batch loss of the last epoch. */
+ * *final_loss (host, may be NULL) = mean batch loss of the last epoch.
+ * Errors: BGK_EINVAL (NULL, epochs, batch or lr not positive, fewer logged
+ * pairs than one batch), BGK_ENOMEM, BGK_ECUDA. */
 BGK_API bgk_status bgk_mlp_train(bgk_ctx *ctx, int epochs, int batch, float lr, unsigned long long seed,
                                  int bf16, double *final_loss);
 /* Save (load = 0) or load (load = 1) the weights and normalisation:
- * host buf[BGK_MLP_NPARAM + BGK_MLP_NNORM]. */
+ * host buf[BGK_MLP_NPARAM + BGK_MLP_NNORM], copied.  Errors: BGK_EINVAL
+ * (NULL, saving before any training or load), BGK_ECUDA. */
 BGK_API bgk_status bgk_mlp_weights(bgk_ctx *ctx, float *buf, int load);
 /* Loss and gradient of the current weights on one batch (host arrays:
  * x[n][9] raw features, t[n][5] raw targets, grad[BGK_MLP_NPARAM]); the
- * training kernel's forward and backward pass without the update. */
+ * training kernel's forward and backward pass without the update.  Errors:
+ * BGK_EINVAL (NULL, n <= 0, no trained or loaded network), BGK_ENOMEM,
+ * BGK_ECUDA. */
 BGK_API bgk_status bgk_mlp_grad(bgk_ctx *ctx, const float *x, const float *t, int n, int bf16, double *loss,
                                 float *grad);
-/* Number of learned guesses discarded since the last call (then reset). */
+/* Number of learned guesses discarded since the last call (then reset), into
+ * host *fallbacks.  Errors: BGK_EINVAL (NULL), BGK_ECUDA. */
 BGK_API bgk_status bgk_mlp_stats(bgk_ctx *ctx, unsigned long long *fallbacks);
 
-/* Text of the last error on this context (never NULL). */
+/* Text of the last error on this context (never NULL; "null context" for a
+ * NULL context); valid until the next call on the context. */
 BGK_API const char *bgk_last_error(const bgk_ctx *ctx);
 
 #ifdef __cplusplus

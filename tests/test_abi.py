@@ -285,3 +285,14 @@ def test_product_package_never_imports_the_oracle():
             text = open(os.path.join(pkg, f)).read()
             assert not re.search(r"^\s*(from|import)\s+oracle\b", text, re.M), f
             assert "oracle" not in re.findall(r"import_module\(['\"](\w+)", text), f
+
+
+def test_every_entry_point_documents_its_errors():
+    """Each declaration in include/bgk.h is preceded (directly, or as part of a
+    group sharing one comment) by a comment that states its error behaviour."""
+    text = open(os.path.join(ROOT, "include", "bgk.h")).read()
+    for m in re.finditer(r"BGK_API\s+([\w\s\*]+?)\b(bgk_\w+)\s*\(", text):
+        if "char" in m.group(1):                      # bgk_last_error returns text, not a status
+            continue
+        comment = text[:m.start()].rsplit("/*", 1)[1]
+        assert re.search(r"Errors?:|BGK_E[A-Z]+", comment), m.group(2)
