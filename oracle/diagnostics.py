@@ -53,3 +53,44 @@ def macro_fields(problem, m):
     gnorm = np.sqrt(np.sum(grad * grad, axis=-1)).reshape(-1)
     kn = lam * gnorm / rho
     return np.stack([rho, U[:, 0], U[:, 1], U[:, 2], theta, pres, mach, lam, gnorm, kn], axis=1)
+
+
+def macro_fields_curved(problem, m):
+    """[P, 10] fields of the moments m[P, 11] on a curvilinear mesh (points
+    e-major; problem is an oracle.curved.CurvedProblem).
+
+    The gradient of the mapped density polynomial by the chain rule,
+        grad rho = (1/J) sum_d S^d d rho~/d xi_d,   S^d = J grad xi_d,
+    with d rho~/d xi_d the same FR-corrected line derivative as on the box
+    (central common value at interior faces, the face state's density
+    averaged in at a Dirichlet face).  At a diffuse wall or a collapsed face
+    the common value is the element's own trace: neither prescribes a
+    density.  On an affine box S^d/J = (2/h_d) e_d and this is macro_fields."""
+    gas, mesh, fr, q = problem.gas, problem.mesh, problem.fr, problem.q
+    rho, U, E, theta, pres, Pi = bgk.macroscopic(m, gas)
+    Ne = mesh.n_elem
+    mach = np.sqrt(np.sum(U * U, axis=1) / (gas.gamma * theta))
+    lam = gas.viscosity(theta) / rho * np.sqrt(np.pi / (2.0 * theta))
+    r6 = rho.reshape(Ne, q, q, q)                    # [e, i3, i2, i1]
+    dxi = np.zeros((Ne, 3, q, q, q))
+    for d in range(3):
+        ax = 3 - d                                   # axis of i_{d+1}
+        rl = np.moveaxis(r6, ax, -1)                 # line index last: [e, a, b, i]
+        drl = np.einsum("ij,...j->...i", fr.D, rl)
+        tr_L = np.einsum("j,...j->...", fr.l_minus, rl)
+        tr_R = np.einsum("j,...j->...", fr.l_plus, rl)
+        for side, tr_own, tr_other, dg in ((-1, tr_L, tr_R, fr.dgL), (1, tr_R, tr_L, fr.dgR)):
+            nb = mesh.nbr[(d, side)]
+            outer = np.empty_like(tr_own)
+            inner = nb >= 0
+            outer[inner] = tr_other[nb[inner]]
+            if np.any(~inner):
+                outer[~inner] = (problem.dirichlet[(d, side)][0] if (d, side) in problem.dirichlet
+                                 else tr_own[~inner])
+            common = 0.5 * (tr_own + outer)
+            drl = drl + (common - tr_own)[..., None] * dg
+        dxi[:, d] = np.moveaxis(drl, -1, ax)
+    grad = np.einsum("ednabc,edabc->eabcn", mesh.S, dxi) / mesh.J[..., None]
+    gnorm = np.sqrt(np.sum(grad * grad, axis=-1)).reshape(-1)
+    kn = lam * gnorm / rho
+    return np.stack([rho, U[:, 0], U[:, 1], U[:, 2], theta, pres, mach, lam, gnorm, kn], axis=1)
