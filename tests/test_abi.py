@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import numpy as np
+
 from paper_2312_06567_gb300 import bgk
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -297,3 +299,32 @@ def test_every_entry_point_documents_its_errors():
         before = re.sub(r"^#define.*$", "", text[:m.start()], flags=re.M)   # inline comments of constants
         comment = before.rsplit("/*", 1)[1]
         assert re.search(r"Errors?:|BGK_E[A-Z]+", comment), m.group(2)
+
+
+def test_descriptors_carry_each_workload_face():
+    """The binding's descriptors: face 2d + (side > 0) gets the workload's kind
+    and state (Dirichlet (rho, U, theta); diffuse (1, U_w, theta_w)),
+    periodic axes and sizes as defined, the gas as given."""
+    from paper_2312_06567_gb300 import workloads as W
+    shock = W.normal_shock_tube()
+    m, v, g = bgk.descriptors(shock)
+    assert list(m.periodic) == [0, 1, 1] and list(m.n) == list(shock.mesh_n) and m.order == shock.p
+    assert m.face_type[0] == m.face_type[1] == bgk.BGK_FACE_DIRICHLET
+    for f, key in ((0, (0, -1)), (1, (0, 1))):
+        rho, U, th = shock.dirichlet[key]
+        assert list(m.bc_state[f]) == [rho, U[0], U[1], U[2], th]
+    assert m.bc_state[0][1] > m.bc_state[1][1] > 0                  # supersonic inflow, slower outflow
+    assert (g.delta, g.Pr, g.mu_ref) == (shock.delta, shock.Pr, shock.mu_ref)
+    assert list(v.n) == list(shock.vel_n) and list(v.lo) == list(shock.vel_lo)
+    og = W.sphere_ogrid(n=(2, 4, 4), vel_n=(6, 6, 6))
+    x = np.ascontiguousarray(W.node_positions(og))
+    m, _, _ = bgk.descriptors(og, x)
+    assert list(m.periodic) == [0, 0, 1]
+    assert m.face_type[0] == bgk.BGK_FACE_DIFFUSE and m.face_type[1] == bgk.BGK_FACE_DIRICHLET
+    assert m.face_type[2] == m.face_type[3] == bgk.BGK_FACE_CLOSED
+    U_w, th_w = og.diffuse[(0, -1)]
+    assert list(m.bc_state[0]) == [1.0, U_w[0], U_w[1], U_w[2], th_w]
+    assert m.node_xyz == x.ctypes.data
+    spec = shock.replace(dirichlet={(0, 1): shock.dirichlet[(0, 1)]}, specular=((0, -1),))
+    m, _, _ = bgk.descriptors(spec)
+    assert m.face_type[0] == bgk.BGK_FACE_SPECULAR and m.face_type[1] == bgk.BGK_FACE_DIRICHLET
