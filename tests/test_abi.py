@@ -328,3 +328,21 @@ def test_descriptors_carry_each_workload_face():
     spec = shock.replace(dirichlet={(0, 1): shock.dirichlet[(0, 1)]}, specular=((0, -1),))
     m, _, _ = bgk.descriptors(spec)
     assert m.face_type[0] == bgk.BGK_FACE_SPECULAR and m.face_type[1] == bgk.BGK_FACE_DIRICHLET
+
+
+def test_noalloc_moments_reject_invalid_arguments_before_any_cuda_call(libbgk):
+    """bgk_moments_noalloc validates on the host first: more points than its
+    fixed 2^21-double scratch holds (11 n_points > 2^21), no points, a third
+    component, a one-node velocity axis, missing pointers -> BGK_EINVAL."""
+    v = bgk.VGridDesc()
+    for d in range(3):
+        v.n[d], v.lo[d], v.hi[d] = 8, -6.0, 6.0
+    dummy = ctypes.c_void_p(16)                 # never dereferenced on these paths
+    call = lambda vg, f, nc, npts, m: libbgk.bgk_moments_noalloc(vg, f, nc, npts, m, None)
+    assert call(ctypes.byref(v), dummy, 1, (1 << 21) // 11 + 1, dummy) == bgk.BGK_EINVAL
+    assert call(ctypes.byref(v), dummy, 1, 0, dummy) == bgk.BGK_EINVAL
+    assert call(ctypes.byref(v), dummy, 3, 10, dummy) == bgk.BGK_EINVAL
+    assert call(ctypes.byref(v), None, 1, 10, dummy) == bgk.BGK_EINVAL
+    assert call(None, dummy, 1, 10, dummy) == bgk.BGK_EINVAL
+    v.n[1] = 1
+    assert call(ctypes.byref(v), dummy, 1, 10, dummy) == bgk.BGK_EINVAL
