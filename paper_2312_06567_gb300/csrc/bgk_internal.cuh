@@ -246,7 +246,9 @@ cudaError_t launch_wall_density(const T *f, const T *fvec, const double *bcval, 
                                 const int *wall_ef, int n_wall, int q, int Ne, int Nu, int C, FROps fr,
                                 double *rho_w, cudaStream_t s);
 
-// Launchers (kernels_f64.cu).
+// Launchers: the Q' solve and its tensor refinement (kernels_qprime.cu); the
+// FP64 moments, stage and Maxwellian (kernels_f64.cu); the FP32 moments and
+// stage (kernels_f32.cu, the line kernels in kernels_f32_line.cu).
 cudaError_t launch_moments_f64(const MomentArgs64 &a, int n_vblk, cudaStream_t s);
 cudaError_t launch_qprime(const QPrimeArgs &a, bool fp32_sums, cudaStream_t s);
 // tensor variant of the ES equilibrium: refines the eq record k_qprime wrote

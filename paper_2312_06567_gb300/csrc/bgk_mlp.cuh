@@ -1,5 +1,5 @@
 // The learned Q' guess network shared by the training kernels (mlp.cu) and
-// the Newton kernel's inline inference (kernels_f64.cu).
+// the Newton kernel's inline inference (kernels_qprime.cu).
 //
 // Parameters, one flat FP32 array (row-major [fan_in][fan_out] matrices):
 //   W1[9][64] b1[64] W2[64][64] b2[64] W3[64][5] b3[5]        (MLP_NPARAM)
