@@ -139,3 +139,15 @@ def test_json_line_carries_the_contract_keys():
     assert rl["traffic"] == pytest.approx(11.25 * wl.dof)      # ncu traffic of the line kernel, per launch
     assert set(line) >= {"mixed", "fp64"} and line["fp64"]["value"] < line["mixed"]["value"]
     assert line["fp64"]["roofline_kernels"]["stage"]["unit"] == "TFLOP/s"
+
+
+def test_clock_sampler_without_nvidia_smi_reports_it(monkeypatch):
+    """No nvidia-smi on the host: the sampler records that instead of failing."""
+    def missing(*a, **k):
+        raise OSError("nvidia-smi not found")
+    monkeypatch.setattr(bench.subprocess, "Popen", missing)
+    cs = bench.ClockSampler(0)
+    cs.start()
+    c = cs.stop()
+    assert c["sm_mhz"] is None and c["reasons"] == ["nvidia-smi unavailable"]
+    os.unlink(cs.out.name)
