@@ -143,6 +143,8 @@ class ClockSampler:
 
     def stop(self):
         if self.proc is None:
+            self.out.close()
+            os.unlink(self.out.name)
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
         self.proc.wait()

@@ -150,4 +150,4 @@ def test_clock_sampler_without_nvidia_smi_reports_it(monkeypatch):
     cs.start()
     c = cs.stop()
     assert c["sm_mhz"] is None and c["reasons"] == ["nvidia-smi unavailable"]
-    os.unlink(cs.out.name)
+    assert not os.path.exists(cs.out.name)                  # no temporary file left behind
