@@ -151,6 +151,7 @@ class ClockSampler:
         self.out.flush()
         with open(self.out.name) as fh:
             lines = fh.readlines()
+        self.out.close()
         os.unlink(self.out.name)
         return summarize_clocks(lines)
 
