@@ -151,3 +151,22 @@ def test_clock_sampler_without_nvidia_smi_reports_it(monkeypatch):
     c = cs.stop()
     assert c["sm_mhz"] is None and c["reasons"] == ["nvidia-smi unavailable"]
     assert not os.path.exists(cs.out.name)                  # no temporary file left behind
+
+
+def test_clock_sampler_reads_a_running_nvidia_smi(tmp_path, monkeypatch):
+    """A stand-in nvidia-smi on PATH printing rows every 50 ms: the sampler
+    starts it, stops it and summarises what it printed."""
+    import stat
+    import time
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\nwhile true; do\n"
+                    "  echo '0, 2070, 2070, 900.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active'\n"
+                    "  sleep 0.05\ndone\n")
+    fake.chmod(fake.stat().st_mode | stat.S_IEXEC)
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ.get("PATH", ""))
+    cs = bench.ClockSampler(0)
+    cs.start()
+    time.sleep(0.4)
+    c = cs.stop()
+    assert c["samples"] >= 2 and c["sm_mhz"] == 2070 and c["reasons"] == ["sw_power_cap"]
+    assert not os.path.exists(cs.out.name)
