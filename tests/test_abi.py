@@ -126,13 +126,15 @@ def test_curvilinear_descriptors_rejected_on_the_host(libbgk):
 def test_library_metric_terms_equal_the_oracle(libbgk):
     """Host-side metric terms of the library (bgk_curved_metrics) against the
     oracle's independently written curl form: node metrics S^d, Jacobians and
-    averaged face vectors of the sphere O-grid (p = 1, 2) and a warped periodic
-    box (p = 3), to 1e-12 of their scale."""
+    averaged face vectors of the sphere O-grid (p = 1, 2; small and the
+    benchmark's full 6912 elements) and a warped periodic box (p = 3), to 1e-12
+    of their scale."""
     import numpy as np
     from oracle import curved
     from paper_2312_06567_gb300 import workloads as W
     cases = [W.sphere_ogrid(n=(2, 4, 6), p=1), W.sphere_ogrid(n=(2, 3, 4), p=2),
-             W.wavy_periodic_box(p=3, n=(2, 2, 3), amp=0.07)]
+             W.wavy_periodic_box(p=3, n=(2, 2, 3), amp=0.07),
+             W.sphere_ogrid()]                            # the benchmark's full 12 x 24 x 24 mesh
     for wl in cases:
         x = W.node_positions(wl)
         S, J, fv = bgk.curved_metrics(wl, x)
