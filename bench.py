@@ -114,10 +114,60 @@ def cpu_baseline(wl, target_s=12.0):
         tot_wall += w_
         tot_cpu += c
     return {"value": tot_dof / tot_wall, "unit": UNIT, "cores": round(tot_cpu / tot_wall, 2),
-            "kind": "oracle",
+            "kind": "oracle", "stages": n,
             "sample": "%d oracle stage(s) of the workload reduced to %s elements (%d nodes x %d "
                       "velocities = %d DOF each), %.1f s wall" % (n, "x".join(map(str, _sample_mesh(wl))),
                                                                    dof // wl.n_vel, wl.n_vel, dof, tot_wall)}
+
+
+def _oracle_worker_ready(_):
+    """Warm-up task of the all-cores pool: import the oracle before the clock."""
+    from oracle import curved, stage  # noqa: F401
+    time.sleep(0.05)
+    return os.getpid()
+
+
+def _oracle_worker(job):
+    """One process of the all-cores timing: `reps` oracle stages of the named
+    workload's sample.  Returns (DOF, wall s, cpu s)."""
+    name, reps = job
+    wl = WORKLOADS[name]()
+    tot = [0, 0.0, 0.0]
+    for _ in range(reps):
+        d, w_, c = oracle_stage_sample(wl)
+        tot[0] += d
+        tot[1] += w_
+        tot[2] += c
+    return tuple(tot)
+
+
+def cpu_baseline_all_cores(name, reps, procs=None):
+    """The oracle as it stands on every host core: one spawned process per core
+    (BLAS held to one thread each), each running `reps` stages of its own copy
+    of the sample; DOF-updates/s of all of them over the batch's wall time,
+    with the processes started and the oracle imported before the clock."""
+    import multiprocessing as mp
+    procs = procs or len(os.sched_getaffinity(0))
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(procs) as pool:
+            pool.map(_oracle_worker_ready, range(4 * procs), chunksize=1)
+            t0 = time.perf_counter()
+            res = pool.map(_oracle_worker, [(name, reps)] * procs, chunksize=1)
+            wall = time.perf_counter() - t0
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    dof = sum(r[0] for r in res)
+    cpu = sum(r[2] for r in res)
+    return {"value": dof / wall, "unit": UNIT, "processes": procs, "cores": round(cpu / wall, 2),
+            "sample": "%d processes x %d oracle stage(s) of the same sample, %.1f s wall" % (procs, reps, wall)}
 
 
 # ---------------------------------------------------------------------------
@@ -462,6 +512,7 @@ def main():
     line = compose_line(args, wl, results, peaks, world)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
+        line["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores(args.workload, line["cpu_baseline"]["stages"])
     print(json.dumps(line))
 
 

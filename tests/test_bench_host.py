@@ -170,3 +170,11 @@ def test_clock_sampler_reads_a_running_nvidia_smi(tmp_path, monkeypatch):
     c = cs.stop()
     assert c["samples"] >= 2 and c["sm_mhz"] == 2070 and c["reasons"] == ["sw_power_cap"]
     assert not os.path.exists(cs.out.name)
+
+
+def test_all_cores_oracle_timing_runs_spawned_processes():
+    """The all-cores leg of the CPU baseline: spawned processes (never forked
+    after CUDA work), each running the unchanged oracle on its own sample."""
+    r = bench.cpu_baseline_all_cores("sine_box", 1, procs=2)
+    assert r["processes"] == 2 and r["value"] > 0 and r["cores"] > 0.5
+    assert r["unit"] == bench.UNIT and "2 processes" in r["sample"]
