@@ -512,7 +512,11 @@ def main():
     line = compose_line(args, wl, results, peaks, world)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
-        line["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores(args.workload, line["cpu_baseline"]["stages"])
+        try:
+            line["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores(args.workload,
+                                                                       line["cpu_baseline"]["stages"])
+        except Exception as exc:             # the line is printed whatever the host's process limits
+            line["cpu_baseline"]["all_cores"] = {"unavailable": "%s: %s" % (type(exc).__name__, exc)}
     print(json.dumps(line))
 
 
