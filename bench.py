@@ -145,7 +145,8 @@ def cpu_baseline_all_cores(name, reps, procs=None):
     """The oracle as it stands on every host core: one spawned process per core
     (BLAS held to one thread each), each running `reps` stages of its own copy
     of the sample; DOF-updates/s of all of them over the batch's wall time,
-    with the processes started and the oracle imported before the clock."""
+    with the processes started and the oracle imported before the clock.
+    Waits are bounded (a lost worker raises multiprocessing.TimeoutError)."""
     import multiprocessing as mp
     procs = procs or len(os.sched_getaffinity(0))
     keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
@@ -153,10 +154,10 @@ def cpu_baseline_all_cores(name, reps, procs=None):
     for k in keys:
         os.environ[k] = "1"
     try:
-        with mp.get_context("spawn").Pool(procs) as pool:
-            pool.map(_oracle_worker_ready, range(4 * procs), chunksize=1)
+        with mp.get_context("spawn").Pool(procs) as pool:      # leaving the block terminates the workers
+            pool.map_async(_oracle_worker_ready, range(4 * procs), chunksize=1).get(timeout=60)
             t0 = time.perf_counter()
-            res = pool.map(_oracle_worker, [(name, reps)] * procs, chunksize=1)
+            res = pool.map_async(_oracle_worker, [(name, reps)] * procs, chunksize=1).get(timeout=300)
             wall = time.perf_counter() - t0
     finally:
         for k, v in saved.items():
