@@ -348,3 +348,14 @@ def test_noalloc_moments_reject_invalid_arguments_before_any_cuda_call(libbgk):
     assert call(None, dummy, 1, 10, dummy) == bgk.BGK_EINVAL
     v.n[1] = 1
     assert call(ctypes.byref(v), dummy, 1, 10, dummy) == bgk.BGK_EINVAL
+
+
+def test_header_compiles_cleanly_as_c99_and_cxx11(tmp_path):
+    """include/bgk.h is a plain C header: strict C99 and C++11, every warning an error."""
+    import subprocess
+    src = "#include \"bgk.h\"\nint main(void) { return (int)sizeof(bgk_mesh_desc) > 0 ? 0 : 1; }\n"
+    for ext, cc, std in (("c", "gcc", "-std=c99"), ("cpp", "g++", "-std=c++11")):
+        f = tmp_path / ("h." + ext)
+        f.write_text(src)
+        subprocess.run([cc, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        "-fsyntax-only", str(f)], check=True)
