@@ -359,3 +359,29 @@ def test_header_compiles_cleanly_as_c99_and_cxx11(tmp_path):
         f.write_text(src)
         subprocess.run([cc, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
                         "-fsyntax-only", str(f)], check=True)
+
+
+def test_binding_signatures_match_the_header_prototypes():
+    """Every ctypes signature has the prototype's argument count, and each
+    scalar argument the prototype's C type (a pointer may be c_void_p or a typed
+    pointer); the return types are the status int (or text)."""
+    text = open(os.path.join(ROOT, "include", "bgk.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    scalars = {"int": ctypes.c_int, "double": ctypes.c_double, "float": ctypes.c_float,
+               "long long": ctypes.c_longlong, "unsigned long long": ctypes.c_ulonglong}
+    seen = 0
+    for m in re.finditer(r"BGK_API\s+([\w\s\*]+?)\b(bgk_\w+)\s*\(([^)]*)\)", text):
+        ret, name, params = m.group(1).strip(), m.group(2), m.group(3)
+        res, args = bgk.SIGNATURES[name]
+        assert (res is ctypes.c_char_p) == ("char" in ret), name
+        plist = [p.strip() for p in params.split(",") if p.strip() and p.strip() != "void"]
+        assert len(plist) == len(args), name
+        for p, a in zip(plist, args):
+            if "*" in p or "[" in p:
+                assert a is ctypes.c_void_p or a is ctypes.c_char_p or hasattr(a, "_type_") and \
+                    issubclass(a, ctypes._Pointer), (name, p)
+                continue
+            ctype = re.sub(r"\s+\w+$", "", p.replace("const ", "")).strip()
+            assert a is scalars[ctype], (name, p, a)
+        seen += 1
+    assert seen == len(bgk.SIGNATURES)
