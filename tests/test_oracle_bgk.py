@@ -310,3 +310,22 @@ def test_modified_temperature_and_internal_energy_relaxation(delta, Pr, gfac):
         tau = mu / (Pr * (np.trace(Pi) + 2.0 * e_int) / (3.0 + delta))
         target = (0.5 * delta * rho * theta_p - e_int) / tau
         assert abs(np.sum(w * S_G[:, 0]) - target) <= 5e-9 * abs(target)
+
+
+@pytest.mark.parametrize("Pr", [2 / 3, 0.72, 1.0, 3.0])
+def test_es_source_dissipates_entropy(Pr):
+    """H-theorem of the ES-BGK model (monatomic, Pr >= 2/3): the source never
+    produces entropy, sum_k w S ln F < 0 away from equilibrium.  A necessary
+    property of the source on seeded anisotropic states of the Taylor--Green
+    physics, not a sharp check of T itself (other pins fix T)."""
+    wl = W.reduced(W.taylor_green_box(), mesh_n=(2, 1, 1), vel_n=(20, 20, 20)).replace(p=1)
+    vg = VelocityGrid(wl.vel_n, wl.vel_lo, wl.vel_hi)
+    gas = bgk.Gas(delta=0.0, Pr=Pr, mu_ref=0.05, theta_S=-1.0)
+    for seed in range(2):
+        F = W.random_anisotropic_state(wl, seed=seed)[0].reshape(wl.n_vel, -1)
+        S, _, info = bgk.bgk_source(F, None, gas, vg)
+        assert np.all(info["converged"])
+        lnF = np.log(np.maximum(F, 1e-300))
+        dH = np.sum(vg.w[:, None] * S * lnF, axis=0)
+        scale = np.sum(vg.w[:, None] * np.abs(S * lnF), axis=0)
+        assert np.all(dH < -1e-3 * scale), (Pr, seed, float(np.max(dH / scale)))
