@@ -178,3 +178,22 @@ def test_all_cores_oracle_timing_runs_spawned_processes():
     r = bench.cpu_baseline_all_cores("sine_box", 1, procs=2)
     assert r["processes"] == 2 and r["value"] > 0 and r["cores"] > 0.5
     assert r["unit"] == bench.UNIT and "2 processes" in r["sample"]
+
+
+def test_reference_arm_line_carries_the_contract_keys(monkeypatch, capsys):
+    """bench.py --impl reference (the oracle on the host cores) prints one JSON
+    line with the metric, its cpu_baseline description and a zero-copy e2e."""
+    import json
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--workload", "sine_box",
+                                      "--steps", "1", "--warmup", "0"])
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    monkeypatch.delenv("RANK", raising=False)
+    bench.main()
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["value"] > 0 and line["steps"] == 1 and line["higher_is_better"] is True
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] > 0 and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert line["config"]["workload"] == bench.WORKLOADS["sine_box"]().name
