@@ -8,7 +8,16 @@ step is one SSP-RK3 step = 3 stages; value = DOF x 3 K / (timed seconds),
 summed over ranks (independent replicas, weak scaling).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--forms fp64,mixed] [--no-cpu-baseline]
+                  [--workload NAME] [--forms fp64,mixed,mixed_learned]
+                  [--stage-kernel tune|auto|plain|async|line|...] [--depth S]
+                  [--no-graphs] [--e2e-steps E] [--no-cpu-baseline]
+
+Workloads: taylor_green (default), sine_box, normal_shock, sphere_ogrid and
+smaller copies of the box and the O-grid for profiling.  The line carries the
+headline form (mixed + learned guess) at the top level and the other forms
+under their names, the dominant kernel's roofline, the clocks sampled during
+the timed steps, the end-to-end number through host buffers and the oracle's
+CPU baseline (one process and all cores).
 
 --impl reference times the FP64 CPU oracle (the method written out plainly,
 test infrastructure) on the host cores on a bounded sample of the same
