@@ -179,7 +179,7 @@ def test_curvilinear_fp32_line_operator_conserves_exactly():
     import random
     from fractions import Fraction as Fr
     rng = random.Random(7)
-    for p in (1, 2, 3):
+    for p in (1, 2, 3, 4):
         fr, c = bgk.fr_tables(p)
         q = p + 1
         W = [Fr(float(v)) for v in fr["w"]]
