@@ -385,3 +385,27 @@ def test_binding_signatures_match_the_header_prototypes():
             assert a is scalars[ctype], (name, p, a)
         seen += 1
     assert seen == len(bgk.SIGNATURES)
+
+
+def test_face_vectors_are_single_valued_on_a_discontinuous_mesh():
+    """One element of a warped box perturbed on its own (the geometry no
+    longer matches across its faces): each shared face still carries one face
+    vector, bit for bit the same from both sides (the two traces averaged),
+    and it equals the oracle's."""
+    from oracle import curved
+    from paper_2312_06567_gb300 import workloads as W
+    wl = W.wavy_periodic_box(p=2, n=(3, 3, 2), amp=0.05)
+    x = np.ascontiguousarray(W.node_positions(wl))
+    e = 1 + 3 * (1 + 3 * 0)                                      # an inner element of the first two axes
+    x[e] += 0.01 * np.random.default_rng(4).standard_normal(x[e].shape)
+    S, J, fv = bgk.curved_metrics(wl, x)
+    mesh = curved.CurvedMesh(wl.mesh_n, wl.periodic, x, wl.p)
+    q = wl.p + 1
+    n1, n2 = wl.mesh_n[0], wl.mesh_n[1]
+    stride = (1, n1, n1 * n2)
+    for d in range(3):
+        c = (e % n1, (e // n1) % n2, e // (n1 * n2))[d]
+        nb = e + stride[d] if c < wl.mesh_n[d] - 1 else e - (wl.mesh_n[d] - 1) * stride[d]
+        assert np.array_equal(fv[e, 2 * d + 1], fv[nb, 2 * d]), d              # shared face, both sides
+        f_o = mesh.face[(d, 1)].reshape(wl.n_elem, q * q, 3)[e]
+        assert np.max(np.abs(fv[e, 2 * d + 1] - f_o)) <= 1e-12 * np.max(np.abs(f_o)), d
