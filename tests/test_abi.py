@@ -409,3 +409,19 @@ def test_face_vectors_are_single_valued_on_a_discontinuous_mesh():
         assert np.array_equal(fv[e, 2 * d + 1], fv[nb, 2 * d]), d              # shared face, both sides
         f_o = mesh.face[(d, 1)].reshape(wl.n_elem, q * q, 3)[e]
         assert np.max(np.abs(fv[e, 2 * d + 1] - f_o)) <= 1e-12 * np.max(np.abs(f_o)), d
+
+
+def test_collapsed_pole_faces_have_zero_face_vectors():
+    """The polar faces of the latitude--longitude O-grid collapse onto the
+    axis: the library's face vectors (area-weighted normals) vanish there to
+    rounding, p = 1 and 2, so no flux could cross them even if they were not
+    declared closed."""
+    from paper_2312_06567_gb300 import workloads as W
+    for p in (1, 2):
+        wl = W.sphere_ogrid(n=(3, 6, 8), p=p)
+        assert set(wl.closed) == {(1, -1), (1, 1)}
+        _, _, fv = bgk.curved_metrics(wl, np.ascontiguousarray(W.node_positions(wl)))
+        c2 = (np.arange(wl.n_elem) // wl.mesh_n[0]) % wl.mesh_n[1]
+        scale = np.abs(fv).max()
+        assert np.abs(fv[c2 == 0][:, 2]).max() <= 1e-14 * scale
+        assert np.abs(fv[c2 == wl.mesh_n[1] - 1][:, 3]).max() <= 1e-14 * scale
