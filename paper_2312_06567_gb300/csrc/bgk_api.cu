@@ -1202,7 +1202,7 @@ bgk_status bgk_mlp_weights(bgk_ctx *ctx, float *buf, int load) {
 // Upload x[n][9], t[n][5] (host) and run the training kernel over all n samples.
 static bgk_status mlp_batch_pass(bgk_ctx *ctx, const float *dx, const float *dt, const int *didx, int n,
                                  int bf16) {
-    MlpParams p{ctx->mlp_w, ctx->mlp_norm};
+    MlpParams p{ctx->mlp_w, ctx->mlp_norm, nullptr};   // training rounds the master weights itself
     LaunchScope ls(ctx, BGK_K_OTHER);
     CU(launch_mlp_train(p, dx, dt, didx, n, ctx->mlp_grad, ctx->mlp_loss, bf16, ctx->stream));
     return BGK_OK;
