@@ -455,8 +455,10 @@ def kernel_rooflines(wl, r, peaks, form):
 
 
 # DRAM bytes per DOF of a stage launch, mean over the three stages of a step,
-# from the ncu capture summarised in profiles/ncu_stage_f32_line_*.md (valid
-# for that kernel variant as it stands; traffic per DOF does not depend on N_e).
+# from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# line kernel on the Taylor--Green physics at 8x8x4 elements, p = 3, 24^3
+# velocities (valid for that kernel variant as it stands; traffic per DOF does
+# not depend on N_e).
 MEASURED_STAGE_TRAFFIC_PER_DOF = {"line": 11.25}
 
 

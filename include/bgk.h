@@ -317,8 +317,14 @@ BGK_API bgk_status bgk_moments(bgk_ctx *ctx, double *m, int on_device);
  * n_points * 11 must not exceed 2^21 (n_points <= 190650), else BGK_EINVAL.
  * All calls share that array, so calls that overlap on the GPU race; each
  * call overwrites every partial sum it reads, so nothing needs clearing.
- * The first call on each device looks up the array's device address; make
- * it before starting any stream capture.  Errors: BGK_EINVAL, BGK_ECUDA. */
+ * The array's device address belongs to a CUDA context: a call whose stream
+ * is not being captured looks it up for the context current on the calling
+ * thread (the first such call on a device is the set-up), so calls from
+ * another context on the same device, or after cudaDeviceReset, use their
+ * own context's copy.  A call made while its stream is being captured reuses
+ * the address found by the last uncaptured call on that device (BGK_ECUDA if
+ * there was none): make one call, from the capturing context, before any
+ * stream capture.  Errors: BGK_EINVAL, BGK_ECUDA. */
 BGK_API bgk_status bgk_moments_noalloc(const bgk_vgrid_desc *vgrid, const double *f, int n_comp,
                                        int n_points, double *m, void *stream);
 
@@ -351,8 +357,14 @@ BGK_API bgk_status bgk_qprime(bgk_ctx *ctx, const double *m, int n_points, doubl
  * element's interpolant in the FP64 form, and 1 / (1/J_s rounded to FP32) in
  * the mixed form, the quadrature its stage conserves exactly): the conserved
  * quantities of section "Governing equations".  totals is host memory.
- * Errors: BGK_EINVAL (NULL), BGK_ECUDA. */
-BGK_API bgk_status bgk_totals(bgk_ctx *ctx, double totals[5]);
+ * entropy (host memory, may be NULL): the discrete entropy
+ * H = sum_e sum_s W_s J_s sum_k w_k F ln F of the stored F component with the
+ * same quadrature, summed in FP64 (section "Numerical method": the
+ * discrete-velocity BGK relaxation does not increase it).  It is NaN when
+ * some stored F is not positive.  With delta > 0 it covers F only (the paper
+ * states no entropy functional for the reduced F, G pair).
+ * Errors: BGK_EINVAL (NULL context or totals), BGK_ECUDA. */
+BGK_API bgk_status bgk_totals(bgk_ctx *ctx, double totals[5], double *entropy);
 
 /* Newton statistics accumulated since the last call (then reset):
  * mean and max update count per point solve, and the worst final scaled

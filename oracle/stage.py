@@ -212,6 +212,36 @@ def element_residual(h, p, vg, gas, f27, guess=None, tol=1e-13, max_iter=50, wit
     return (R, S) if with_source else R
 
 
+def slab_residual(h, n_yz, p, vg, gas, dirichlet, f3, target, with_source=False, tol=1e-13, max_iter=50):
+    """R(f) = -div(u f) + S(f) of one first-axis slab of elements (the n2 x n3
+    elements at one first-axis index) of a mesh that is periodic in its second
+    and third directions, from three consecutive slabs.
+
+    f3[C, Nu, 3 n2 n3, Ns] holds the slabs in mesh order (element
+    e = i1 + 3 (i2 + n2 i3), i1 = 0, 1, 2); the sub-box of spacing h has
+    Dirichlet first-axis faces with the given states.  The residual of slab
+    `target` is exact when target = 1 (both first-axis neighbours present)
+    and when the target's outer face is the full mesh's own Dirichlet face
+    (target 0 at the low end, 2 at the high end).  Used to check slabs of
+    states too large for the whole-mesh routines.  Returns R[C, Nu, n2 n3, Ns]
+    (and the source part S with with_source)."""
+    from .mesh import BoxMesh
+    n2, n3 = n_yz
+    hh = np.asarray(h, dtype=np.float64)
+    mesh = BoxMesh((3, n2, n3), (0.0, 0.0, 0.0), (3.0 * hh[0], n2 * hh[1], n3 * hh[2]), (False, True, True))
+    prob = Problem(mesh, p, vg, gas, dirichlet=dirichlet)
+    div = prob.divergence(f3)
+    C, Nu = f3.shape[:2]
+    sel = np.array([target + 3 * (i2 + n2 * i3) for i3 in range(n3) for i2 in range(n2)])
+    div = div[:, :, sel, :]
+    F = f3[0][:, sel, :].reshape(Nu, -1)
+    G = f3[1][:, sel, :].reshape(Nu, -1) if C == 2 else None
+    S_F, S_G, _ = bgk.bgk_source(F, G, gas, vg, tol=tol, max_iter=max_iter)
+    S = np.stack([S_F] + ([S_G] if C == 2 else [])).reshape(div.shape)
+    R = S - div
+    return (R, S) if with_source else R
+
+
 def cfl_dt(mesh, vg, p, cfl):
     """dt = CFL h_min / (u_max (2p + 1)) (the paper gives only the explicit scheme)."""
     umax = float(np.max(np.abs(vg.u)))

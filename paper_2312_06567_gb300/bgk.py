@@ -64,7 +64,7 @@ SIGNATURES = {
     "bgk_moments_noalloc": (c_int, [ctypes.POINTER(VGridDesc), c_void_p, c_int, c_int, c_void_p,
                                     c_void_p]),
     "bgk_qprime": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_int]),
-    "bgk_totals": (c_int, [c_void_p, ctypes.POINTER(c_double)]),
+    "bgk_totals": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
     "bgk_stats": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int),
                           ctypes.POINTER(c_double)]),
     "bgk_set_guess": (c_int, [c_void_p, c_int, c_int]),
@@ -211,11 +211,33 @@ def curved_metrics(wl, node_xyz):
     return S, J, fv
 
 
+def _require_cuda_f64(name, t, n):
+    """A CUDA float64 contiguous tensor of at least n elements, else ValueError
+    (before any library call: the kernels would read or write past it)."""
+    if not (hasattr(t, "is_cuda") and hasattr(t, "dtype")):
+        raise ValueError("%s must be a CUDA torch tensor, got %s" % (name, type(t).__name__))
+    import torch
+    if not t.is_cuda:
+        raise ValueError("%s must be in device memory" % name)
+    if t.dtype != torch.float64:
+        raise ValueError("%s must be float64, got %s" % (name, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if t.numel() < n:
+        raise ValueError("%s holds %d elements, the call needs %d" % (name, t.numel(), n))
+
+
 def moments_noalloc(vgrid, f, n_comp, n_points, m, stream=None):
     """bgk_moments_noalloc: raw moments of a device state into a device output
     without any device allocation by the library (see include/bgk.h).
     vgrid: VGridDesc; f: CUDA tensor [n_comp, N_u, n_points] float64;
-    m: CUDA tensor [n_points, 11] float64."""
+    m: CUDA tensor [n_points, 11] float64.  Wrong device, dtype or size
+    raises ValueError before the library is called."""
+    n_vel = int(vgrid.n[0]) * int(vgrid.n[1]) * int(vgrid.n[2])
+    if n_comp not in (1, 2) or n_points <= 0 or n_vel <= 0:
+        raise ValueError("n_comp must be 1 or 2 and n_points, N_u positive")
+    _require_cuda_f64("f", f, n_comp * n_vel * n_points)
+    _require_cuda_f64("m", m, n_points * 11)
     lib = load()
     st = lib.bgk_moments_noalloc(ctypes.byref(vgrid), _ptr(f)[0], n_comp, n_points, _ptr(m)[0],
                                  _stream_handle(stream))
@@ -388,8 +410,15 @@ class Solver:
 
     def totals(self):
         t = (c_double * 5)()
-        self._check(self.lib.bgk_totals(self._h, t))
+        self._check(self.lib.bgk_totals(self._h, t, None))
         return np.array(list(t))
+
+    def entropy(self):
+        """bgk_totals' entropy output: sum W J sum_k w F ln F of the stored F (NaN if some F <= 0)."""
+        t = (c_double * 5)()
+        h = c_double()
+        self._check(self.lib.bgk_totals(self._h, t, ctypes.byref(h)))
+        return h.value
 
     def stats(self):
         mean, mx, res = c_double(), c_int(), c_double()

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <limits>
 #include <vector>
 
 #include "../../include/bgk.h"
@@ -1115,13 +1116,41 @@ bgk_status bgk_qprime(bgk_ctx *ctx, const double *m, int n_points, double *qp, i
     return check_device_status(ctx);
 }
 
-bgk_status bgk_totals(bgk_ctx *ctx, double totals[5]) {
+bgk_status bgk_totals(bgk_ctx *ctx, double totals[5], double *entropy) {
     if (!ctx || !totals) return BGK_EINVAL;
     std::vector<double> m((size_t)ctx->P * BGK_NMOM);
     bgk_status st = bgk_moments(ctx, m.data(), 0);
     if (st) return st;
+    std::vector<double> hp;
+    unsigned int nonpos = 0;
+    if (entropy) {
+        // per-point sum_k w_k F ln F in FP64 (a velocity-block partial, then
+        // the sum over blocks), weighed below with the totals' quadrature
+        double *dpart = nullptr, *dh = nullptr;
+        unsigned int *dbad = nullptr;
+        CU(cudaMallocAsync((void **)&dpart, (size_t)ctx->n_vblk * ctx->P * sizeof(double), ctx->stream));
+        CU(cudaMallocAsync((void **)&dh, (size_t)ctx->P * sizeof(double), ctx->stream));
+        CU(cudaMallocAsync((void **)&dbad, sizeof(unsigned int), ctx->stream));
+        CU(cudaMemsetAsync(dbad, 0, sizeof(unsigned int), ctx->stream));
+        {
+            LaunchScope ls(ctx, BGK_K_OTHER);
+            if (ctx->precision == BGK_FP64)
+                CU(launch_entropy<double>((const double *)ctx->f[0], ctx->vtab, ctx->Nu, ctx->P, ctx->Kblk,
+                                          ctx->n_vblk, dpart, dh, dbad, ctx->stream));
+            else
+                CU(launch_entropy<float>((const float *)ctx->f[0], ctx->vtab, ctx->Nu, ctx->P, ctx->Kblk,
+                                         ctx->n_vblk, dpart, dh, dbad, ctx->stream));
+        }
+        hp.resize(ctx->P);
+        CU(cudaMemcpyAsync(hp.data(), dh, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaMemcpyAsync(&nonpos, dbad, sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaFreeAsync(dpart, ctx->stream));
+        CU(cudaFreeAsync(dh, ctx->stream));
+        CU(cudaFreeAsync(dbad, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+    }
     const int q = ctx->q;
-    double t[5] = {0, 0, 0, 0, 0};
+    double t[5] = {0, 0, 0, 0, 0}, H = 0.0;
     for (int p = 0; p < ctx->P; ++p) {
         const int s = p % ctx->Ns;
         const double W = ctx->curved ? ctx->geo_h[(size_t)p * BGK_NGEO + 10]
@@ -1129,8 +1158,10 @@ bgk_status bgk_totals(bgk_ctx *ctx, double totals[5]) {
         const double *mm = &m[(size_t)p * BGK_NMOM];
         t[0] += W * mm[0]; t[1] += W * mm[1]; t[2] += W * mm[2]; t[3] += W * mm[3];
         t[4] += W * (0.5 * (mm[4] + mm[5] + mm[6]) + mm[10]);
+        if (entropy) H += W * hp[p];
     }
     for (int j = 0; j < 5; ++j) totals[j] = t[j];
+    if (entropy) *entropy = nonpos ? std::numeric_limits<double>::quiet_NaN() : H;
     return BGK_OK;
 }
 

@@ -272,5 +272,10 @@ cudaError_t launch_maxwellian_f32(float *f, const double *q, const double *vtab,
                                   double delta, cudaStream_t s);
 cudaError_t launch_macro(const double *mom, double *out, int P, const MeshInfo &mesh, const FROps &fr,
                          const GasInfo &gas, const double face_rho[6], cudaStream_t s);
+// per-point entropy sum_k w_k F ln F of the F component (kernels_f64.cu);
+// part holds n_vblk * P doubles, *nonpos counts the non-positive values
+template <typename T>
+cudaError_t launch_entropy(const T *f, const double *vtab, int Nu, int P, int Kblk, int n_vblk, double *part,
+                           double *h_out, unsigned int *nonpos, cudaStream_t s);
 cudaError_t launch_reduce_moments(const double *part, int n_vblk, int P, double *m_out,
                                   cudaStream_t s);

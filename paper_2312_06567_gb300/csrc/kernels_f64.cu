@@ -48,6 +48,36 @@ __global__ void __launch_bounds__(256) k_moments_f64(MomentArgs64 a) {
     for (int j = 0; j < BGK_NMOM; ++j) a.part[((size_t)vb * BGK_NMOM + j) * a.P + p] = m[j];
 }
 
+// Discrete entropy of the F component, partial over velocity blocks
+// (section "Numerical method": the discrete-velocity BGK step obeys a
+// discrete H-theorem): part[vb][p] = sum_{k in block vb} w_k F ln F in FP64;
+// a non-positive F has no entropy and is counted in *nonpos instead.
+template <typename T>
+__global__ void __launch_bounds__(256) k_entropy_partial(const T *f, const double *vtab, int Nu, int P, int Kblk,
+                                                         double *part, unsigned int *nonpos) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const int vb = blockIdx.y;
+    const int k0 = vb * Kblk, k1 = min(Nu, k0 + Kblk);
+    double h = 0.0;
+    unsigned int bad = 0;
+    for (int k = k0; k < k1; ++k) {
+        const double F = (double)f[(size_t)k * P + p];
+        if (F > 0.0) h = fma(__ldg(vtab + (size_t)k * BGK_VTAB + 3) * F, log(F), h);
+        else ++bad;
+    }
+    part[(size_t)vb * P + p] = h;
+    if (bad) atomicAdd(nonpos, bad);
+}
+
+__global__ void k_reduce_entropy(const double *part, int n_vblk, int P, double *h_out) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    double s = 0.0;
+    for (int vb = 0; vb < n_vblk; ++vb) s += part[(size_t)vb * P + p];
+    h_out[p] = s;
+}
+
 __global__ void k_reduce_moments(const double *part, int n_vblk, int P, double *m_out) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P) return;
@@ -363,6 +393,21 @@ cudaError_t launch_moments_f64(const MomentArgs64 &a, int n_vblk, cudaStream_t s
     k_moments_f64<<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_entropy(const T *f, const double *vtab, int Nu, int P, int Kblk, int n_vblk, double *part,
+                           double *h_out, unsigned int *nonpos, cudaStream_t s) {
+    dim3 grid((P + 255) / 256, n_vblk);
+    k_entropy_partial<T><<<grid, 256, 0, s>>>(f, vtab, Nu, P, Kblk, part, nonpos);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_reduce_entropy<<<(P + 255) / 256, 256, 0, s>>>(part, n_vblk, P, h_out);
+    return cudaGetLastError();
+}
+template cudaError_t launch_entropy<double>(const double *, const double *, int, int, int, int, double *, double *,
+                                            unsigned int *, cudaStream_t);
+template cudaError_t launch_entropy<float>(const float *, const double *, int, int, int, int, double *, double *,
+                                           unsigned int *, cudaStream_t);
 
 cudaError_t launch_reduce_moments(const double *part, int n_vblk, int P, double *m_out,
                                   cudaStream_t s) {

@@ -19,9 +19,15 @@
 //    from different host threads without ordering) race on it.
 //  * Host code may not pass the array's name to a kernel: on the host that
 //    name is only a stand-in, not a device address.  The device address is
-//    looked up once per device with cudaGetSymbolAddress, on the first call
-//    made with that device current; make that first call before any stream
-//    capture begins.
+//    looked up with cudaGetSymbolAddress for the context current on the
+//    calling thread.  The set-up happens on the first call made with a
+//    device current; later calls whose stream is not being captured look the
+//    address up again (cheap), so a call from another context on the same
+//    device (a plugin host's own driver-API context, or after
+//    cudaDeviceReset) gets that context's address.  A call whose stream is
+//    being captured uses the address the last uncaptured call on that
+//    device found: make at least one call on the device, from the context
+//    that will capture, before any stream capture begins.
 #include <mutex>
 
 #include "../../include/bgk.h"
@@ -93,18 +99,26 @@ __global__ void k_moments_finish_noalloc(const double *scr, int n_vblk, int P, d
     }
 }
 
-// Device address of the scratch array for the current device (looked up once).
-cudaError_t scratch_for_current_device(double **out) {
+// Device address of the scratch array in the calling thread's current
+// context: looked up whenever the stream is not being captured (and kept per
+// device); during a capture the kept address is used (no lookup may run
+// then).
+cudaError_t scratch_for_current_device(cudaStream_t s, double **out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= BGK_NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void *ptr = nullptr;
         e = cudaGetSymbolAddress(&ptr, g_moment_scratch);
         if (e != cudaSuccess) return e;
         g_scratch_ptr[dev] = (double *)ptr;
+    } else if (!g_scratch_ptr[dev]) {
+        return cudaErrorStreamCaptureUnsupported;    // no uncaptured call on this device yet
     }
     *out = g_scratch_ptr[dev];
     return cudaSuccess;
@@ -138,8 +152,8 @@ extern "C" BGK_API bgk_status bgk_moments_noalloc(const bgk_vgrid_desc *vgrid, c
     n_vblk = (Nu + Kblk - 1) / Kblk;
 
     double *scr = nullptr;
-    if (scratch_for_current_device(&scr) != cudaSuccess) return BGK_ECUDA;
     cudaStream_t s = (cudaStream_t)stream;
+    if (scratch_for_current_device(s, &scr) != cudaSuccess) return BGK_ECUDA;
     dim3 grid(n_pb, (unsigned)n_vblk);
     k_moments_partial_noalloc<<<grid, 256, 0, s>>>(f, n_comp, (int)Nu, n_points, Kblk, g, scr);
     if (cudaGetLastError() != cudaSuccess) return BGK_ECUDA;

@@ -5,6 +5,7 @@ import os
 import re
 
 import numpy as np
+import pytest
 
 from paper_2312_06567_gb300 import bgk
 
@@ -348,6 +349,52 @@ def test_noalloc_moments_reject_invalid_arguments_before_any_cuda_call(libbgk):
     assert call(None, dummy, 1, 10, dummy) == bgk.BGK_EINVAL
     v.n[1] = 1
     assert call(ctypes.byref(v), dummy, 1, 10, dummy) == bgk.BGK_EINVAL
+
+
+def test_noalloc_binding_refuses_wrong_buffers_before_calling_the_library(monkeypatch):
+    """The Python wrapper of bgk_moments_noalloc checks device, dtype,
+    contiguity and size of f and m and raises ValueError before the library
+    is loaded or called (a wrong buffer would be read or written out of
+    bounds on the device)."""
+    torch = pytest.importorskip("torch")
+
+    def never(*a, **k):
+        raise AssertionError("the library must not be reached")
+    monkeypatch.setattr(bgk, "load", never)
+    v = bgk.VGridDesc()
+    for d in range(3):
+        v.n[d], v.lo[d], v.hi[d] = 4, -3.0, 3.0
+    P = 10
+    cpu_f = torch.zeros((1, 64, P), dtype=torch.float64)
+    cpu_m = torch.zeros((P, 11), dtype=torch.float64)
+    with pytest.raises(ValueError, match="device memory"):
+        bgk.moments_noalloc(v, cpu_f, 1, P, cpu_m)
+    with pytest.raises(ValueError, match="CUDA torch tensor"):
+        bgk.moments_noalloc(v, np.zeros((1, 64, P)), 1, P, cpu_m)
+    with pytest.raises(ValueError):
+        bgk.moments_noalloc(v, cpu_f, 3, P, cpu_m)
+    with pytest.raises(ValueError):
+        bgk.moments_noalloc(v, cpu_f, 1, 0, cpu_m)
+
+    class FakeCuda:
+        """Stands for a CUDA tensor on a machine without a GPU."""
+        def __init__(self, n, dtype=torch.float64, contiguous=True):
+            self.is_cuda, self.dtype, self._n, self._c = True, dtype, n, contiguous
+        def numel(self):
+            return self._n
+        def is_contiguous(self):
+            return self._c
+    ok_f, ok_m = FakeCuda(64 * P), FakeCuda(11 * P)
+    with pytest.raises(ValueError, match="float64"):
+        bgk.moments_noalloc(v, FakeCuda(64 * P, torch.float32), 1, P, ok_m)
+    with pytest.raises(ValueError, match="needs"):
+        bgk.moments_noalloc(v, FakeCuda(64 * P - 1), 1, P, ok_m)
+    with pytest.raises(ValueError, match="needs"):
+        bgk.moments_noalloc(v, FakeCuda(64 * P), 2, P, ok_m)
+    with pytest.raises(ValueError, match="needs"):
+        bgk.moments_noalloc(v, ok_f, 1, P, FakeCuda(11 * P - 1))
+    with pytest.raises(ValueError, match="contiguous"):
+        bgk.moments_noalloc(v, ok_f, 1, P, FakeCuda(11 * P, contiguous=False))
 
 
 def test_header_compiles_cleanly_as_c99_and_cxx11(tmp_path):

@@ -1,0 +1,125 @@
+"""Parity at the normal shock's full size (64x4x4 hex over [-20, 40] x [0, 1]^2
+mean free paths, p = 2, 32^3 velocities, diatomic: F and G, 9.06e8 DOF) on
+sampled first-axis slabs, both forms, in the benchmark's launch configuration.
+
+The state (a deterministic non-equilibrium mixture around the M = 8 shock's
+tanh profile) is generated on the device in FP64 per velocity chunk; the three
+consecutive slabs around each sampled slab (the low Dirichlet end, the slab
+holding the shock, the high Dirichlet end) are generated on the host from the
+same per-point parameters.  The GPU computes the residual and a Runge--Kutta
+stage of the whole state; the oracle computes the sampled slab from its three
+slabs (slab_residual, pinned against the whole-mesh residual, Dirichlet ends
+included).  Bars: 1e-12 (FP64 form) and 1e-5 (mixed form), velocity by
+velocity, of max|f| over the three slabs times the advection rate plus max|S|
+(the upwind flux brings in the neighbours' traces, which across the shock and
+in the velocity tails can exceed the slab's own f by orders of magnitude); for
+the mixed form also its contract, the stage output's moments per point within
+1e-5 of rho, rho sqrt(theta) and E."""
+import numpy as np
+import pytest
+
+from oracle import bgk as obgk
+from oracle import stage as ostage
+from oracle.velocity import VelocityGrid
+from paper_2312_06567_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+SLABS = (0, 21, 63)              # low Dirichlet end, the shock (x = 0 lies in slab 21), high Dirichlet end
+
+
+@pytest.fixture(scope="module")
+def lib(libbgk, cuda_device):
+    from paper_2312_06567_gb300 import bgk
+    return bgk
+
+
+@pytest.fixture(scope="module")
+def shock_state(cuda_device):
+    import torch
+    wl = W.normal_shock_tube()
+    free = torch.cuda.mem_get_info()[0]
+    if free < 120e9:
+        pytest.skip("needs ~120 GB of free device memory, %.0f GB free" % (free / 1e9))
+    x = W.node_positions(wl).reshape(-1, 3)
+    P = x.shape[0]
+    elem = np.repeat(np.arange(wl.n_elem), wl.n_sol)
+    par = W.mixture_params(wl, x, elem)
+    u = W.velocity_nodes(wl)
+    n1, n2, n3 = wl.mesh_n
+    host = {}
+    for e1 in SLABS:
+        first = min(max(e1 - 1, 0), n1 - 3)
+        blk = [first + d1 + n1 * (i2 + n2 * i3) for i3 in range(n3) for i2 in range(n2) for d1 in range(3)]
+        pts = (np.asarray(blk)[:, None] * wl.n_sol + np.arange(wl.n_sol)[None, :]).ravel()
+        sub = {k: v[pts] for k, v in par.items()}
+        F = W.mixture_values(sub, u, np.exp)
+        host[e1] = (first, np.stack([F, sub["gfac"][None, :] * F]))
+    dpar = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in par.items()}
+    du = torch.from_numpy(u).cuda()
+    f64 = torch.empty((wl.n_comp, wl.n_vel, P), dtype=torch.float64, device="cuda")
+    step = 1024
+    for k0 in range(0, wl.n_vel, step):
+        k1 = min(wl.n_vel, k0 + step)
+        F = W.mixture_values(dpar, du[k0:k1], torch.exp)
+        f64[0, k0:k1] = F
+        f64[1, k0:k1] = dpar["gfac"][None, :] * F
+    shape = (wl.n_comp, wl.n_vel, wl.n_elem, wl.n_sol)
+    yield wl, f64.view(shape), host
+    del f64
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("form", ["mixed", "fp64"])
+def test_full_size_shock_residual_and_stage_on_sampled_slabs(lib, shock_state, form):
+    import torch
+    wl, f64, host = shock_state
+    prec = lib.BGK_MIXED if form == "mixed" else lib.BGK_FP64
+    f = f64.float() if form == "mixed" else f64
+    dt = wl.dt()
+    with lib.Solver(wl, prec) as s:
+        if form == "mixed":
+            s.set_state(f)
+            s.tune_stage(dt, reps=1)                 # the benchmark's launch configuration
+        r = torch.empty_like(f)
+        s.rhs(f, r)
+        out = torch.empty_like(f)
+        s.stage(f, f, out, 0.75, 0.25, 0.25 * dt)
+    vg = VelocityGrid(wl.vel_n, wl.vel_lo, wl.vel_hi)
+    gas = obgk.Gas(delta=wl.delta, Pr=wl.Pr, mu_ref=wl.mu_ref, theta_ref=wl.theta_ref, theta_S=wl.theta_S)
+    h = np.array([(wl.mesh_hi[d] - wl.mesh_lo[d]) / wl.mesh_n[d] for d in range(3)])
+    adv = np.sum(2 * np.abs(vg.u) / h, axis=1)
+    n1, n2, n3 = wl.mesh_n
+    tol = 1e-5 if form == "mixed" else 1e-12
+    for e1, (first, blk) in host.items():
+        f3 = blk.reshape(wl.n_comp, wl.n_vel, 3 * n2 * n3, wl.n_sol)
+        if form == "mixed":
+            f3 = f3.astype(np.float32).astype(np.float64)
+        R, S = ostage.slab_residual(h, (n2, n3), wl.p, vg, gas, wl.dirichlet, f3, e1 - first, with_source=True)
+        sel = [e1 + n1 * (i2 + n2 * i3) for i3 in range(n3) for i2 in range(n2)]
+        loc = [e1 - first + 3 * (i2 + n2 * i3) for i3 in range(n3) for i2 in range(n2)]
+        fe = f3[:, :, loc, :]
+        fnb = np.abs(f3).reshape(wl.n_comp, wl.n_vel, -1).max(axis=2)
+        Smax = np.abs(S).reshape(wl.n_comp, wl.n_vel, -1).max(axis=2)
+        scale = fnb * adv[None, :] + Smax
+        scale = np.maximum(scale, 1e-25 * scale.max())
+        r_e = r[:, :, sel, :].double().cpu().numpy()
+        err = float(np.max(np.abs(r_e - R).reshape(wl.n_comp, wl.n_vel, -1).max(axis=2) / scale))
+        assert err <= tol, (form, e1, err)
+        o_e = out[:, :, sel, :].double().cpu().numpy()
+        o_ora = fe + (0.25 * dt) * R                                  # 0.75 f + 0.25 (f + dt R(f))
+        sc = (np.abs(fe).reshape(wl.n_comp, wl.n_vel, -1).max(axis=2)
+              + 0.25 * dt * (np.abs(R).reshape(wl.n_comp, wl.n_vel, -1).max(axis=2) + Smax))
+        sc = np.maximum(sc, 1e-25 * sc.max())
+        err_o = float(np.max(np.abs(o_e - o_ora).reshape(wl.n_comp, wl.n_vel, -1).max(axis=2) / sc))
+        assert err_o <= tol, (form, e1, err_o)
+        if form == "mixed":
+            Nu = wl.n_vel
+            m_e = obgk.raw_moments(o_e[0].reshape(Nu, -1), o_e[1].reshape(Nu, -1), vg)
+            m_o = obgk.raw_moments(o_ora[0].reshape(Nu, -1), o_ora[1].reshape(Nu, -1), vg)
+            rho, U, E, th, _, _ = obgk.macroscopic(m_o, gas)
+            rho_e, U_e, E_e, _, _, _ = obgk.macroscopic(m_e, gas)
+            q_err = max(np.max(np.abs(rho_e - rho) / rho),
+                        np.max(np.abs(rho_e[:, None] * U_e - rho[:, None] * U).max(axis=1) / (rho * np.sqrt(th))),
+                        np.max(np.abs(E_e - E) / E))
+            assert q_err <= 1e-5, (e1, q_err)

@@ -207,6 +207,29 @@ def test_element_residual_from_its_block_equals_the_whole_mesh():
         assert np.max(np.abs(Re - R[:, :, e, :])) <= 1e-13 * scale
 
 
+def test_slab_residual_from_three_slabs_equals_the_whole_mesh():
+    """The residual of one first-axis slab evaluated from three consecutive
+    slabs (the normal shock's layout: Dirichlet first-axis ends, periodic in
+    the other two) equals the whole-mesh residual at both Dirichlet ends and
+    in the interior: advection (incl. the Dirichlet exterior state) and the
+    ES source with G."""
+    from oracle import stage as ost
+    from paper_2312_06567_gb300 import workloads as W
+    wl = W.reduced(W.normal_shock_tube(mach=3.0), mesh_n=(6, 2, 3), vel_n=(13, 9, 11)).replace(
+        p=2, vel_lo=(-9.0, -8.0, -8.0), vel_hi=(11.0, 8.0, 8.0))
+    pb = ost.problem_from_workload(wl)
+    f = W.random_anisotropic_state(wl, seed=23)
+    R, _ = pb.rhs(f)
+    n1, n2, n3 = wl.mesh_n
+    for e1 in (0, 3, n1 - 1):
+        first = min(max(e1 - 1, 0), n1 - 3)
+        idx = [first + d1 + n1 * (i2 + n2 * i3) for i3 in range(n3) for i2 in range(n2) for d1 in range(3)]
+        Rs = ost.slab_residual(pb.mesh.h, (n2, n3), wl.p, pb.vg, pb.gas, wl.dirichlet, f[:, :, idx, :], e1 - first)
+        sel = [e1 + n1 * (i2 + n2 * i3) for i3 in range(n3) for i2 in range(n2)]
+        scale = np.abs(R[:, :, sel, :]).max()
+        assert np.max(np.abs(Rs - R[:, :, sel, :])) <= 1e-13 * scale, e1
+
+
 def _mirror_case(p=2, with_g=True):
     """A box [0, L] x [0,1]^2 with specular faces at x = 0 and x = L, and the
     periodic doubled box [-L, L] holding the mirror image of the data."""
