@@ -57,6 +57,7 @@ def parse():
                     help="mixed-form stage kernel; 'tune' times the candidates on the workload (untimed)")
     ap.add_argument("--depth", type=int, default=6, help="copy-ring depth of the async stage kernel")
     ap.add_argument("--no-graphs", action="store_true", help="time direct launches instead of CUDA-graph replays")
+    ap.add_argument("--no-tc-probe", action="store_true", help="skip the tensor-core FR-operator probe")
     return ap.parse_args()
 
 
@@ -298,6 +299,14 @@ def run_ours(args, rank, world, dev):
     if rank == 0:
         for k in ("fp64_fma", "fp64_exp", "fp32_fma", "fp32_exp2"):
             peaks[k] = bgk.probe_peak(k)
+        if wl.p == 3 and not args.no_tc_probe:
+            # the p = 3 FR element operator streamed through tcgen05 MMAs
+            # (2^20 panels = 3.2e9 element-node-velocity DOF, 12.9 GB of
+            # split operands), measured beside the stage it would feed
+            try:
+                peaks["tensor_fr_probe"] = bgk.probe_tc(1 << 20)
+            except Exception as exc:
+                peaks["tensor_fr_probe"] = {"unavailable": "%s: %s" % (type(exc).__name__, exc)}
     forms = [f for f in args.forms.split(",") if f]
     headline = next((f for f in ("mixed_learned", "mixed", "fp64") if f in forms), forms[0])
     for form in forms:
@@ -462,6 +471,33 @@ def kernel_rooflines(wl, r, peaks, form):
 MEASURED_STAGE_TRAFFIC_PER_DOF = {"line": 11.25}
 
 
+def tensor_probe_summary(tc, wl, peaks):
+    """The tensor-core FR-operator probe next to the stage: its rate, the time
+    the own-element operator of all three directions alone would take for the
+    whole state at that rate (split operands resident in HBM, no conversion,
+    no epilogue), and its arithmetic against FP64."""
+    if "unavailable" in tc:
+        return tc
+    bf16 = _measured_bf16()
+    out = {"tflops": tc["flops"] / 1e12, "dof_per_s": tc["dof_per_s"],
+           "operand_gbs": tc["bytes_per_s"] / 1e9, "ms": tc["ms"],
+           "ms_per_stage_equiv": 1e3 * wl.dof / tc["dof_per_s"],
+           "max_rel_err": tc["max_rel_err"], "bias": tc["bias"],
+           "shape": "M=64 N=48 K=16 kind::f16 (BF16 in, FP32 accumulate), 36 MMAs per 48 velocities x 64 nodes",
+           "split": "bf16 hi + lo, three products (hi.hi + lo.hi + hi.lo)"}
+    if bf16:
+        out["frac_of_bf16_peak"] = tc["flops"] / (bf16 * 1e12)
+        out["bf16_peak_tflops"] = bf16
+    return out
+
+
+def _measured_bf16():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def dominant_roofline(rl):
     k = max(rl, key=lambda n: rl[n]["ms"])
     d = dict(rl[k])
@@ -569,6 +605,9 @@ def compose_line(args, wl, results, peaks, world):
         rl["stage"]["traffic"] = MEASURED_STAGE_TRAFFIC_PER_DOF[sk] * wl.dof
     line["roofline"] = dominant_roofline(rl)
     line["roofline_kernels"] = rl
+    tc = peaks.pop("tensor_fr_probe", None)
+    if tc is not None:
+        line["tensor_fr_probe"] = tensor_probe_summary(tc, wl, peaks)
     for form, rr in results.items():
         if form != main_form:
             line[form] = {"value": job_throughput(world, wl.dof, args.steps, rr["ms"]),

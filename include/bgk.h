@@ -397,6 +397,26 @@ BGK_API bgk_status bgk_profile_read(bgk_ctx *ctx, double ms[BGK_NKINDS], long lo
  * (kind out of range, NULL value), BGK_ENOMEM, BGK_ECUDA. */
 BGK_API bgk_status bgk_probe_peak(int kind, double *value);
 
+/* Tensor-core probe of the FR element operator at p = 3 (no context;
+ * measurement, not the method's path).  Per direction the FR derivative of
+ * one element at one velocity, with the own-trace lift folded in, is a dense
+ * 64 x 64 operator on the element's nodes (section "Numerical method"); this
+ * streams n_panels panels of 48 element-velocity columns (BF16 hi and lo
+ * parts of FP32 data, 12 KB each, generated on the device and read by TMA
+ * tiled copies) through tcgen05 MMAs (BF16 x 3 split products, FP32
+ * accumulation in tensor memory) for all three directions and reads the
+ * accumulators back, then checks 8 seeded panels against FP64 on the host.
+ * out (host): [0] useful MMA flop/s, [1] element-node-velocity operator
+ * applications (DOF, three directions each) per second, [2] operand bytes
+ * streamed per second, [3] largest error of an output relative to the sum of
+ * its terms' magnitudes, [4] relative bias of the outputs' magnitudes
+ * (negative: shrunk toward zero), [5] kernel milliseconds.  Allocates
+ * n_panels x 12 KB of device memory for the call.  Errors: BGK_EINVAL
+ * (n_panels outside [16, 2^22], NULL out), BGK_ENOTSUP (not an sm_103
+ * device, or no tensor-map encoder), BGK_ENOMEM, BGK_ECUDA, BGK_ETIMEOUT (a
+ * bounded wait in the kernel gave up). */
+BGK_API bgk_status bgk_probe_tc(long long n_panels, double out[6]);
+
 /* ---- Learned initial guess of the Q' solve -------------------------------
  * Not in the paper (which starts Newton from the macroscopic state): a
  * 9 -> 64 -> 64 -> 5 SiLU network maps the point's state to a correction

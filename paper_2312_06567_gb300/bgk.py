@@ -79,6 +79,7 @@ SIGNATURES = {
     "bgk_profile": (c_int, [c_void_p, c_int]),
     "bgk_profile_read": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(ctypes.c_longlong)]),
     "bgk_probe_peak": (c_int, [c_int, ctypes.POINTER(c_double)]),
+    "bgk_probe_tc": (c_int, [ctypes.c_longlong, ctypes.POINTER(c_double)]),
     "bgk_last_error": (ctypes.c_char_p, [c_void_p]),
 }
 
@@ -96,6 +97,19 @@ def probe_peak(kind):
     if st != BGK_OK:
         raise BGKError(st, "probe %s failed" % kind)
     return v.value
+
+
+def probe_tc(n_panels):
+    """bgk_probe_tc: the p = 3 FR element operator streamed through tcgen05 MMAs.
+    Returns a dict: flops, dof_per_s, bytes_per_s, max_rel_err, bias, ms."""
+    lib = load()
+    out = (c_double * 6)()
+    st = lib.bgk_probe_tc(int(n_panels), out)
+    if st != BGK_OK:
+        raise BGKError(st, "bgk_probe_tc failed")
+    keys = ("flops", "dof_per_s", "bytes_per_s", "max_rel_err", "bias", "ms")
+    return dict(zip(keys, list(out)))
+
 
 _lib = None
 

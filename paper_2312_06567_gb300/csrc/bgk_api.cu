@@ -466,6 +466,8 @@ void box_node_coords(const bgk_ctx *ctx, double *x) {
 
 }  // namespace
 
+void fr_build_host(int p, FROps &fr) { build_fr(p, fr); }
+
 extern "C" {
 
 bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_desc *vg,

@@ -232,6 +232,9 @@ struct MomentArgs64 {
     int Nu, P, Kblk, C;
 };
 
+// The 1-D FR operators of order p on Gauss--Legendre nodes (bgk_api.cu, host).
+void fr_build_host(int p, FROps &fr);
+
 // Curvilinear metric terms (geometry.cu, host): geo[P][BGK_NGEO],
 // fvec[Ne][6][q*q][3]; false with err on a non-positive Jacobian.
 #include <string>
