@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--forms", default="fp64,mixed,mixed_learned")
+    ap.add_argument("--forms", default="fp64,fp64_learned,mixed,mixed_learned")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--workload", default="taylor_green", choices=sorted(WORKLOADS))
@@ -310,7 +310,7 @@ def run_ours(args, rank, world, dev):
     forms = [f for f in args.forms.split(",") if f]
     headline = next((f for f in ("mixed_learned", "mixed", "fp64") if f in forms), forms[0])
     for form in forms:
-        prec = bgk.BGK_FP64 if form == "fp64" else bgk.BGK_MIXED
+        prec = bgk.BGK_FP64 if form.startswith("fp64") else bgk.BGK_MIXED
         learned = form.endswith("_learned")
         s = bgk.Solver(wl, prec, stream=stream)
         x = s.node_coords()
@@ -414,11 +414,77 @@ def run_ours(args, rank, world, dev):
         if learned:
             newton["guess_fallbacks"] = s.mlp_stats()
             newton["training"] = train
+        if learned:
+            newton["held_out"] = held_out_guess(s, wl, dt, torch)
+            if prec == bgk.BGK_MIXED:
+                newton["inference"] = inference_throughput(s, torch, stream)
         results[form] = dict(ms=ms, status=bgk.STATUS_NAMES[st], prof=prof, clocks=ck,
                              newton=newton, e2e=e2e, drift=drift, stage_kernel=tuned, diagnostics=diag)
         s.destroy()
         torch.cuda.empty_cache()
     return wl, results, peaks
+
+
+def held_out_guess(s, wl, dt, torch):
+    """The trained guess on a state it was not trained on (untimed): the
+    current state with an anisotropic, density- and temperature-changing
+    perturbation, f (1 + 0.15 (u1^2 - u2^2)/25 + 0.1 u3/5), one step from q and
+    one from the guess.  Newton updates per solve both ways, the guesses
+    discarded, and the largest difference of the two results."""
+    f = torch.empty(s.shape, dtype=torch.float64 if s.precision == 0 else torch.float32, device="cuda")
+    s.get_state(f)
+    u = torch.from_numpy(W.velocity_nodes(wl)).to(device="cuda", dtype=f.dtype)
+    fac = 1.0 + 0.15 * (u[:, 0] ** 2 - u[:, 1] ** 2) / 25.0 + 0.1 * u[:, 2] / 5.0
+    f.mul_(fac.view(1, -1, 1, 1).clamp_min(0.2))
+    out = {}
+    res = []
+    for mode in (0, 1):
+        s.set_guess(mode, bf16=True)
+        s.set_state(f)
+        s.stats()
+        s.mlp_stats()
+        s.step(dt, 1)
+        mean_it, max_it, r = s.stats()
+        out["from_q" if mode == 0 else "learned"] = {"mean_iters": mean_it, "max_iters": max_it,
+                                                     "max_residual": r}
+        if mode:
+            out["learned"]["guess_fallbacks"] = s.mlp_stats()
+        g = torch.empty_like(f)
+        s.get_state(g)
+        res.append(g)
+    scale = res[0].abs().amax(dim=(0, 2, 3)).clamp_min(1e-300)
+    out["max_rel_diff"] = float(((res[1] - res[0]).abs().amax(dim=(0, 2, 3)) / scale).max())
+    out["state"] = "the benchmark state after the timed steps times (1 + 0.15 (u1^2-u2^2)/25 + 0.1 u3/5)"
+    del f, res
+    return out
+
+
+def inference_throughput(s, torch, stream, sizes=(1000000, 10000000), reps=5):
+    """bgk_mlp_infer (tensor cores) on batches resampled (seed 1) from the
+    logged training features: points per second at each batch size."""
+    pairs = s.mlp_log_read(1 << 22)
+    if len(pairs) == 0:
+        return None
+    rng = np.random.default_rng(1)
+    out = {}
+    for B in sizes:
+        x = torch.from_numpy(np.ascontiguousarray(pairs[rng.integers(0, len(pairs), B), :9])).cuda()
+        d = torch.empty((B, 5), dtype=torch.float32, device="cuda")
+        s.mlp_infer(x, d)                            # warm-up
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            s.mlp_infer(x, d)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        flops = 2.0 * (9 * 64 + 64 * 64 + 64 * 5) * B
+        out[str(B)] = {"ms": ms, "points_per_s": B / (ms * 1e-3), "tflops": flops / (ms * 1e-3) / 1e12}
+        del x, d
+    out["kernel"] = "tcgen05 kind::f16, BF16 in, FP32 accumulate, 128 points per MMA tile"
+    return out
 
 
 def stage_bytes_per_dof(C, elem):
@@ -443,7 +509,7 @@ def kernel_rooflines(wl, r, peaks, form):
     evals = r["newton"]["mean_iters"] + 1.0           # updates + the converged check
     ms_s = prof["stage"][0] / max(prof["stage"][1], 1)
     ms_q = prof["qprime"][0] / max(prof["qprime"][1], 1)
-    if form == "fp64":
+    if form.startswith("fp64"):
         fl = wl.dof * stage_flops_per_dof(wl.p, wl.n_comp)
         out["stage"] = {"bound": "alu", "kernel": "stage", "pipe": "fp64", "achieved": fl / (ms_s * 1e-3) / 1e12,
                         "peak": peaks["fp64_fma"] / 1e12, "unit": "TFLOP/s", "ms": ms_s}

@@ -351,6 +351,50 @@ BGK_API bgk_status bgk_macro(bgk_ctx *ctx, double *out, int on_device);
 BGK_API bgk_status bgk_qprime(bgk_ctx *ctx, const double *m, int n_points, double *qp, int *iters,
                       int on_device);
 
+/* ---- Velocity shards (several GPUs, one per shard) -------------------------
+ * The method couples velocities only through the moments of f (section
+ * "Numerical method": the FR advection of every velocity is independent, the
+ * BGK source needs Q of the whole velocity set).  So the velocity set can be
+ * split: a shard holds the third-axis velocity planes [slab_lo, slab_hi) of
+ * the grid for every element and node, and one SSP-RK3 step is three rounds of
+ *   bgk_shard_partials(shard, m)      partial raw moments of the stage input
+ *   (the caller sums m over all shards, e.g. an NCCL all-reduce, in place)
+ *   bgk_shard_stage(shard, m, stage, dt)   Q' from the summed moments over the
+ *                                     whole grid, then the fused stage on the
+ *                                     shard's own velocities
+ * for stage = 0, 1, 2.  Every shard solves Q' for every point (the same
+ * inputs give the same q' everywhere); the exchange is 11 doubles per point
+ * per stage.  The shards of one grid together equal the unsharded context.
+ *
+ * bgk_create_shard: as bgk_create, vgrid describing the WHOLE grid; the
+ * context holds n[0] n[1] (slab_hi - slab_lo) velocities (bgk_sizes), in the
+ * layout of bgk_set_state with the third axis restricted to the slab.
+ * Trapezoid weights are those of the whole grid (half weight only at its
+ * ends).  Supported: periodic and Dirichlet faces on box or curvilinear
+ * meshes.  Errors: BGK_EINVAL (slab outside [0, n[2]] or fewer than two
+ * planes, and bgk_create's checks), BGK_ENOTSUP (specular, diffuse or closed
+ * faces), BGK_ENOMEM, BGK_ECUDA.  On a shard bgk_moments and bgk_totals
+ * return the shard's part (sums over its velocities; add them over the
+ * shards); bgk_step, bgk_stage, bgk_rhs, bgk_macro and bgk_tune_stage return
+ * BGK_ENOTSUP. */
+BGK_API bgk_status bgk_create_shard(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_desc *vgrid,
+                                    const bgk_gas_desc *gas, int precision, void *cuda_stream, int slab_lo,
+                                    int slab_hi);
+/* Partial raw moments of the current stage input over this context's
+ * velocities, m[11][n_points] FP64 in DEVICE memory (caller-owned; slot order
+ * of bgk_moments, transposed: slot-major), written asynchronously on the
+ * context's stream.  Also valid on an unsharded context (then the full
+ * moments).  Errors: BGK_EINVAL (NULL), BGK_ECUDA. */
+BGK_API bgk_status bgk_shard_partials(bgk_ctx *ctx, double *m);
+/* Stage `stage` (0, 1, 2) of an SSP-RK3 step of size dt from the moments m
+ * (device [11][n_points], summed over all shards of the grid): the Q' solve
+ * over the whole grid, the fused stage on this context's velocities, and the
+ * partial moments of the next stage's input; after stage 2 the stored state
+ * is the step's result.  Asynchronous apart from the device status read.
+ * Errors: BGK_EINVAL (NULL, stage or dt out of range, no partials taken
+ * since the state was set), BGK_ENOCONV, BGK_ETIMEOUT, BGK_ECUDA. */
+BGK_API bgk_status bgk_shard_stage(bgk_ctx *ctx, const double *m, int stage, double dt);
+
 /* Domain totals (rho, rho U, E) = sum_e sum_s W_s J_s sum_k w_k psi_k f of
  * the stored state (W_s tensor Gauss weights, J_s the Jacobian at the node:
  * the affine |J_e| on the box; on a curvilinear mesh det(dX/dxi) of the
@@ -465,6 +509,15 @@ BGK_API bgk_status bgk_mlp_weights(bgk_ctx *ctx, float *buf, int load);
  * BGK_ECUDA. */
 BGK_API bgk_status bgk_mlp_grad(bgk_ctx *ctx, const float *x, const float *t, int n, int bf16, double *loss,
                                 float *grad);
+/* Batched inference of the current network on tensor cores: the guess
+ * correction delta[n][5] for raw features x[n][9] (layouts of the training
+ * pairs), BF16 weights and layer inputs, FP32 accumulation in tensor memory
+ * (tcgen05), FP32 biases and SiLU; the same network the Newton kernel
+ * evaluates inline for every point.  x and delta are device (on_device = 1)
+ * or host memory.  Errors: BGK_EINVAL (NULL, n outside [1, 2^31], no trained
+ * or loaded network), BGK_ENOMEM, BGK_ECUDA, BGK_ETIMEOUT (a bounded wait in
+ * the kernel gave up). */
+BGK_API bgk_status bgk_mlp_infer(bgk_ctx *ctx, const float *x, long long n, float *delta, int on_device);
 /* Number of learned guesses discarded since the last call (then reset), into
  * host *fallbacks.  Errors: BGK_EINVAL (NULL), BGK_ECUDA. */
 BGK_API bgk_status bgk_mlp_stats(bgk_ctx *ctx, unsigned long long *fallbacks);

@@ -106,3 +106,24 @@ def predict(params, norm, x):
     x_mean, x_std, t_mean, t_std = norm
     y, _ = forward(params, (x - x_mean) / x_std)
     return y * t_std + t_mean
+
+
+def bf16_round(x):
+    """Nearest BF16 value (8 significant bits, ties to even) of each entry,
+    taken from its FP32 rounding, as FP64.  The tensor cores and the BF16
+    inference see layer inputs and weights in this format."""
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    u = a.view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward_bf16(params, xn, rnd=bf16_round):
+    """The network with BF16 weights and layer inputs (normalised features and
+    both hidden activations rounded with rnd), FP64 sums, exact biases:
+    the arithmetic of the library's BF16 inference, with its FP32 sums
+    replaced by exact ones."""
+    W1, b1, W2, b2, W3, b3 = params
+    h1 = rnd(silu(rnd(xn) @ rnd(W1) + b1))
+    h2 = rnd(silu(h1 @ rnd(W2) + b2))
+    return h2 @ rnd(W3) + b3

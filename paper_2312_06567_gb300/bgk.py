@@ -80,11 +80,17 @@ SIGNATURES = {
     "bgk_profile_read": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(ctypes.c_longlong)]),
     "bgk_probe_peak": (c_int, [c_int, ctypes.POINTER(c_double)]),
     "bgk_probe_tc": (c_int, [ctypes.c_longlong, ctypes.POINTER(c_double)]),
+    "bgk_create_shard": (c_int, [ctypes.POINTER(c_void_p), c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int,
+                                 c_int]),
+    "bgk_shard_partials": (c_int, [c_void_p, c_void_p]),
+    "bgk_shard_stage": (c_int, [c_void_p, c_void_p, c_int, c_double]),
+    "bgk_mlp_infer": (c_int, [c_void_p, c_void_p, ctypes.c_longlong, c_void_p, c_int]),
     "bgk_last_error": (ctypes.c_char_p, [c_void_p]),
 }
 
 KERNEL_KINDS = ("moments", "qprime", "stage", "other", "wall")
 MLP_NPARAM, MLP_NNORM, MLP_LOG_STRIDE = 5125, 28, 14
+MLP_OUT = 5
 MLP_SHAPES = ((9, 64), (64,), (64, 64), (64,), (64, 5), (5,))
 PROBE_KINDS = {"fp64_fma": 0, "fp32_fma": 1, "fp64_exp": 2, "fp32_exp2": 3}
 
@@ -262,18 +268,27 @@ def moments_noalloc(vgrid, f, n_comp, n_points, m, stream=None):
 class Solver:
     """One libbgk context.  Methods carry the C entry points' names."""
 
-    def __init__(self, wl, precision=BGK_FP64, stream=None):
+    def __init__(self, wl, precision=BGK_FP64, stream=None, shard=None):
+        """shard=(slab_lo, slab_hi): a velocity shard holding the third-axis
+        velocity planes [slab_lo, slab_hi) of the workload's grid
+        (bgk_create_shard); None: every velocity (bgk_create)."""
         self.lib = load()
         self.wl = wl
         self.precision = precision
+        self.shard = tuple(shard) if shard is not None else None
         self._h = c_void_p()
         self._xyz = None
         if getattr(wl, "mapping", None) is not None:
             from . import workloads
             self._xyz = np.ascontiguousarray(workloads.node_positions(wl), dtype=np.float64)
         m, v, g = descriptors(wl, self._xyz)
-        st = self.lib.bgk_create(ctypes.byref(self._h), ctypes.byref(m), ctypes.byref(v),
-                                 ctypes.byref(g), precision, _stream_handle(stream))
+        if self.shard is None:
+            st = self.lib.bgk_create(ctypes.byref(self._h), ctypes.byref(m), ctypes.byref(v),
+                                     ctypes.byref(g), precision, _stream_handle(stream))
+        else:
+            st = self.lib.bgk_create_shard(ctypes.byref(self._h), ctypes.byref(m), ctypes.byref(v),
+                                           ctypes.byref(g), precision, _stream_handle(stream),
+                                           int(self.shard[0]), int(self.shard[1]))
         if st != BGK_OK:
             msg = self.lib.bgk_last_error(self._h).decode() if self._h else ""
             if self._h:
@@ -488,6 +503,37 @@ class Solver:
             grads.append(g[off:off + n].reshape(shp).astype(np.float64))
             off += n
         return loss.value, grads
+
+    # -- velocity shards -------------------------------------------------------
+    def shard_partials(self, m):
+        """bgk_shard_partials into the device tensor m[11, n_points] (float64)."""
+        if not (getattr(m, "is_cuda", False) and m.dtype.is_floating_point and m.element_size() == 8
+                and m.is_contiguous() and m.numel() >= 11 * self.n_points):
+            raise ValueError("m must be a contiguous CUDA float64 tensor of 11 x n_points")
+        self._check(self.lib.bgk_shard_partials(self._h, _ptr(m)[0]))
+
+    def shard_stage(self, m, stage, dt):
+        """bgk_shard_stage from the summed moments m[11, n_points] (device)."""
+        if not (getattr(m, "is_cuda", False) and m.element_size() == 8 and m.is_contiguous()
+                and m.numel() >= 11 * self.n_points):
+            raise ValueError("m must be a contiguous CUDA float64 tensor of 11 x n_points")
+        st = self.lib.bgk_shard_stage(self._h, _ptr(m)[0], int(stage), float(dt))
+        if st not in (BGK_OK, BGK_ENOCONV):
+            self._check(st)
+        return st
+
+    def mlp_infer(self, x, out=None):
+        """bgk_mlp_infer: delta[n, 5] of raw features x[n, 9] (numpy or CUDA tensors)."""
+        if isinstance(x, np.ndarray):
+            x = np.ascontiguousarray(x, dtype=np.float32)
+            out = np.empty((x.shape[0], MLP_OUT), dtype=np.float32) if out is None else out
+        n = x.shape[0]
+        px, dev = _ptr(x)
+        po, dev_o = _ptr(out)
+        if dev != dev_o:
+            raise ValueError("x and out must both be host or both be device memory")
+        self._check(self.lib.bgk_mlp_infer(self._h, px, n, po, dev))
+        return out
 
     def mlp_stats(self):
         n = ctypes.c_ulonglong()

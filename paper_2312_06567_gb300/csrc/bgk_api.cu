@@ -21,7 +21,13 @@ struct bgk_ctx {
     MeshInfo mesh;
     FROps fr;
     GasInfo gas;
-    VelGrid vg;
+    VelGrid vg;                       // the velocities this context holds (a slab of the third axis if sharded)
+    VelGrid vg_q;                     // the whole velocity grid: the Q' solve's sums run over it
+    int Nu_q;                         // its size
+    double *vtab_q;                   // its tables (the same arrays as vtab / vtab32 unless sharded)
+    float4 *vtab32_q;
+    bool shard;                       // holds third-axis velocity planes [slab_lo, slab_hi) of the grid
+    int slab_lo, slab_hi;
     double jac;                       // |J_e|
     double lo[3];                     // mesh box corner
     double bc[6][5];
@@ -253,10 +259,10 @@ bgk_status run_moments(bgk_ctx *ctx, const void *f, bool resum = false) {
 bgk_status run_qprime(bgk_ctx *ctx, const double *part, int n_vblk, int P, double *eq, double *qp,
                       int *iters, const double *guess) {
     QPrimeArgs a{};
-    a.part = part; a.n_vblk = n_vblk; a.vtab = ctx->vtab; a.vtab32 = ctx->vtab32; a.guess = guess; a.eq = eq; a.qp = qp;
+    a.part = part; a.n_vblk = n_vblk; a.vtab = ctx->vtab_q; a.vtab32 = ctx->vtab32_q; a.guess = guess; a.eq = eq; a.qp = qp;
     a.eq32 = (eq && eq == ctx->eq) ? ctx->eq32 : nullptr;
-    a.iters = iters; a.status = ctx->status; a.stats = ctx->stats; a.P = P; a.Nu = ctx->Nu;
-    a.tol = ctx->tol; a.tol32 = 1e-6; a.max_iter = ctx->max_iter; a.gas = ctx->gas; a.vg = ctx->vg;
+    a.iters = iters; a.status = ctx->status; a.stats = ctx->stats; a.P = P; a.Nu = ctx->Nu_q;
+    a.tol = ctx->tol; a.tol32 = 1e-6; a.max_iter = ctx->max_iter; a.gas = ctx->gas; a.vg = ctx->vg_q;
     a.mixed = ctx->precision == BGK_MIXED ? 1 : 0;
     a.mlp.w = ctx->mlp_w; a.mlp.norm = ctx->mlp_norm; a.mlp.w16 = ctx->mlp_w16;
     a.guess_mode = (ctx->guess_mode == 1 && ctx->mlp_ready) ? 1 : 0;
@@ -470,9 +476,47 @@ void fr_build_host(int p, FROps &fr) { build_fr(p, fr); }
 
 extern "C" {
 
+}  // extern "C"
+namespace {
+// A context over the velocity planes [s_lo, s_hi) of the grid's third axis
+// (the whole grid: 0, n[2]).
+bgk_status create_ctx(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_desc *vg,
+                      const bgk_gas_desc *gas, int precision, void *stream, int s_lo, int s_hi);
+}  // namespace
+extern "C" {
+
 bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_desc *vg,
                       const bgk_gas_desc *gas, int precision, void *stream) {
     if (!out || !mesh || !vg || !gas) return BGK_EINVAL;
+    return create_ctx(out, mesh, vg, gas, precision, stream, 0, vg->n[2]);
+}
+
+bgk_status bgk_create_shard(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_desc *vg,
+                            const bgk_gas_desc *gas, int precision, void *stream, int slab_lo, int slab_hi) {
+    if (!out || !mesh || !vg || !gas) return BGK_EINVAL;
+    *out = nullptr;
+    if (slab_lo < 0 || slab_hi > vg->n[2] || slab_hi - slab_lo < 2) {
+        bgk_ctx *ctx = new bgk_ctx();
+        ctx->err = "a shard holds third-axis velocity planes [slab_lo, slab_hi) with 0 <= slab_lo, "
+                   "slab_hi <= n[2] and at least two planes";
+        *out = ctx;
+        return BGK_EINVAL;
+    }
+    for (int f = 0; f < 6; ++f)
+        if (!mesh->periodic[f / 2] && mesh->face_type[f] != BGK_FACE_DIRICHLET) {
+            bgk_ctx *ctx = new bgk_ctx();
+            ctx->err = "a velocity shard supports periodic and Dirichlet faces only (specular faces mirror "
+                       "velocities across shards, diffuse walls and closed faces sum over all velocities)";
+            *out = ctx;
+            return BGK_ENOTSUP;
+        }
+    return create_ctx(out, mesh, vg, gas, precision, stream, slab_lo, slab_hi);
+}
+
+}  // extern "C"
+namespace {
+bgk_status create_ctx(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_desc *vg,
+                      const bgk_gas_desc *gas, int precision, void *stream, int s_lo, int s_hi) {
     *out = nullptr;
     bgk_ctx *ctx = new bgk_ctx();
     auto bad = [&](const char *msg) {
@@ -501,9 +545,10 @@ bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
                 if (ft == BGK_FACE_DIFFUSE && !(b[4] > 0.0)) return bad("a diffuse wall needs theta_w > 0");
             }
     const long long Ne = (long long)mesh->n[0] * mesh->n[1] * mesh->n[2];
-    const long long Nu = (long long)vg->n[0] * vg->n[1] * vg->n[2];
+    const long long Nu_full = (long long)vg->n[0] * vg->n[1] * vg->n[2];
+    const long long Nu = (long long)vg->n[0] * vg->n[1] * (s_hi - s_lo);     // the planes this context holds
     const long long Ns = (long long)(mesh->order + 1) * (mesh->order + 1) * (mesh->order + 1);
-    if (Ne * Ns > (1ll << 30) || Nu > (1ll << 30)) return bad("problem too large");
+    if (Ne * Ns > (1ll << 30) || Nu_full > (1ll << 30)) return bad("problem too large");
     bool curved = mesh->node_xyz != nullptr, any_specular = false;
     for (int f = 0; f < 6; ++f) {
         const int d = f / 2;
@@ -537,15 +582,26 @@ bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
     ctx->stage_depth = 6;
     ctx->graphs_on = false;
     ctx->cap_stream = nullptr;
+    ctx->shard = s_lo != 0 || s_hi != vg->n[2];
+    ctx->slab_lo = s_lo;
+    ctx->slab_hi = s_hi;
     for (int d = 0; d < 3; ++d) {
-        ctx->vn[d] = vg->n[d];
-        ctx->vg.n[d] = vg->n[d];
-        ctx->vg.lo[d] = vg->lo[d];
-        ctx->vg.h[d] = (vg->hi[d] - vg->lo[d]) / (vg->n[d] - 1);
+        const double h = (vg->hi[d] - vg->lo[d]) / (vg->n[d] - 1);
+        ctx->vg_q.n[d] = vg->n[d];
+        ctx->vg_q.lo[d] = vg->lo[d];
+        ctx->vg_q.h[d] = h;
+        ctx->vn[d] = d == 2 ? s_hi - s_lo : vg->n[d];
+        ctx->vg.n[d] = ctx->vn[d];
+        ctx->vg.lo[d] = d == 2 ? std::fma((double)s_lo, h, vg->lo[d]) : vg->lo[d];
+        ctx->vg.h[d] = h;
         ctx->mesh.n[d] = mesh->n[d];
         ctx->mesh.periodic[d] = mesh->periodic[d] ? 1 : 0;
         ctx->mesh.two_over_h[d] = 2.0 * mesh->n[d] / (mesh->hi[d] - mesh->lo[d]);
     }
+    ctx->vg_q.w3lo = ctx->vg_q.w3hi = 1;
+    ctx->vg.w3lo = s_lo == 0 ? 1 : 0;            // interior slab ends carry full trapezoid weight
+    ctx->vg.w3hi = s_hi == vg->n[2] ? 1 : 0;
+    ctx->Nu_q = (int)Nu_full;
     ctx->mesh.Ne = ctx->Ne; ctx->mesh.Ns = ctx->Ns;
     for (int f = 0; f < 6; ++f) {
         ctx->mesh.specular[f] = !mesh->periodic[f / 2] && mesh->face_type[f] == BGK_FACE_SPECULAR;
@@ -611,17 +667,24 @@ bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
             wt[d].push_back((j == 0 || j == vg->n[d] - 1) ? 0.5 * h : h);
         }
     }
-    ctx->vtab_h.assign((size_t)Nu * BGK_VTAB, 0.0);
-    for (int k = 0; k < Nu; ++k) {
-        const int k1 = k % vg->n[0], k2 = (k / vg->n[0]) % vg->n[1], k3 = k / (vg->n[0] * vg->n[1]);
-        double *v = &ctx->vtab_h[(size_t)k * BGK_VTAB];
-        v[0] = ax[0][k1]; v[1] = ax[1][k2]; v[2] = ax[2][k3];
-        v[3] = wt[0][k1] * wt[1][k2] * wt[2][k3];
-        v[4] = 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-        v[5] = v[3] * v[0];
-        v[6] = v[3] * v[0] * v[0];
-        v[7] = 2.0 * mesh->n[0] / (mesh->hi[0] - mesh->lo[0]) * v[0];   // (2/h_1) u_1
-    }
+    // the table of velocities k3 in [k3_from, k3_from + n_k / (n0 n1)), weights of the whole grid
+    auto fill_vtab = [&](std::vector<double> &tab, long long n_k, int k3_from) {
+        tab.assign((size_t)n_k * BGK_VTAB, 0.0);
+        for (long long k = 0; k < n_k; ++k) {
+            const int k1 = (int)(k % vg->n[0]), k2 = (int)((k / vg->n[0]) % vg->n[1]);
+            const int k3 = k3_from + (int)(k / ((long long)vg->n[0] * vg->n[1]));
+            double *v = &tab[(size_t)k * BGK_VTAB];
+            v[0] = ax[0][k1]; v[1] = ax[1][k2]; v[2] = ax[2][k3];
+            v[3] = wt[0][k1] * wt[1][k2] * wt[2][k3];
+            v[4] = 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+            v[5] = v[3] * v[0];
+            v[6] = v[3] * v[0] * v[0];
+            v[7] = 2.0 * mesh->n[0] / (mesh->hi[0] - mesh->lo[0]) * v[0];   // (2/h_1) u_1
+        }
+    };
+    fill_vtab(ctx->vtab_h, Nu, s_lo);
+    std::vector<double> vtab_q_h;
+    if (ctx->shard) fill_vtab(vtab_q_h, Nu_full, 0);
     // Dirichlet exterior states per face and velocity
     std::vector<double> bcv((size_t)6 * ctx->C * Nu, 0.0);
     for (int face = 0; face < 6; ++face) {
@@ -681,6 +744,27 @@ bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
     }
     if (st == BGK_OK) cu(cudaMalloc(&ctx->vtab32, v32.size() * sizeof(float4)), "cudaMalloc(vtab32)");
     if (st == BGK_OK) cu(cudaMemcpyAsync(ctx->vtab32, v32.data(), v32.size() * sizeof(float4), cudaMemcpyHostToDevice, ctx->stream), "upload vtab32");
+    // the whole grid's tables for the Q' solve of a shard
+    ctx->vtab_q = ctx->vtab;
+    ctx->vtab32_q = ctx->vtab32;
+    std::vector<float4> v32q;
+    if (st == BGK_OK && ctx->shard) {
+        ctx->vtab_q = nullptr;
+        ctx->vtab32_q = nullptr;
+        v32q.resize((size_t)Nu_full);
+        for (long long k = 0; k < Nu_full; ++k) {
+            const double *v = &vtab_q_h[(size_t)k * BGK_VTAB];
+            v32q[k] = make_float4((float)v[0], (float)v[1], (float)v[2], 0.f);
+        }
+        cu(cudaMalloc(&ctx->vtab_q, vtab_q_h.size() * sizeof(double)), "cudaMalloc(vtab_q)");
+        if (st == BGK_OK) cu(cudaMalloc(&ctx->vtab32_q, v32q.size() * sizeof(float4)), "cudaMalloc(vtab32_q)");
+        if (st == BGK_OK)
+            cu(cudaMemcpyAsync(ctx->vtab_q, vtab_q_h.data(), vtab_q_h.size() * sizeof(double), cudaMemcpyHostToDevice,
+                               ctx->stream), "upload vtab_q");
+        if (st == BGK_OK)
+            cu(cudaMemcpyAsync(ctx->vtab32_q, v32q.data(), v32q.size() * sizeof(float4), cudaMemcpyHostToDevice,
+                               ctx->stream), "upload vtab32_q");
+    }
     if (st == BGK_OK && curved) {
         const size_t ng = ctx->geo_h.size(), nf = fvec_h.size();
         const int q = ctx->q, Ns = ctx->Ns;
@@ -762,6 +846,8 @@ bgk_status bgk_create(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
     *out = ctx;
     return st;
 }
+}  // namespace
+extern "C" {
 
 bgk_status bgk_fr_tables(int order, double *fr_out, float *curv32_out) {
     if (order < 1 || order > 4 || !fr_out || !curv32_out) return BGK_EINVAL;
@@ -821,6 +907,7 @@ bgk_status bgk_destroy(bgk_ctx *ctx) {
     for (int i = 0; i < 3; ++i) cudaFree(ctx->f[i]);
     cudaFree(ctx->part); cudaFree(ctx->mom); cudaFree(ctx->eq); cudaFree(ctx->qp);
     cudaFree(ctx->iters); cudaFree(ctx->eq32); cudaFree(ctx->vtab); cudaFree(ctx->vtab32); cudaFree(ctx->bcval); cudaFree(ctx->status);
+    if (ctx->shard) { cudaFree(ctx->vtab_q); cudaFree(ctx->vtab32_q); }
     cudaFree(ctx->stats);
     cudaFree(ctx->geo); cudaFree(ctx->fvec); cudaFree(ctx->geo32); cudaFree(ctx->fvec32);
     cudaFree(ctx->rho_w); cudaFree(ctx->wall_ef);
@@ -930,6 +1017,7 @@ bgk_status bgk_set_stage_kernel(bgk_ctx *ctx, int variant, int depth) {
 
 bgk_status bgk_tune_stage(bgk_ctx *ctx, double dt, int reps, int *variant_out, int *depth_out, double *ms_out) {
     if (!ctx || !(dt > 0.0) || reps < 1) return BGK_EINVAL;
+    if (ctx->shard) return fail(ctx, BGK_ENOTSUP, "tune on an unsharded context of the same problem (a shard's own moments are partial)");
     if (ctx->precision != BGK_MIXED) {
         if (variant_out) *variant_out = BGK_STAGE_PLAIN;
         if (depth_out) *depth_out = ctx->stage_depth;
@@ -999,6 +1087,7 @@ bgk_status bgk_set_newton(bgk_ctx *ctx, double tol, int max_iter) {
 
 bgk_status bgk_step(bgk_ctx *ctx, double dt, int n_steps) {
     if (!ctx || !(dt > 0.0) || n_steps < 0) return BGK_EINVAL;
+    if (ctx->shard) return fail(ctx, BGK_ENOTSUP, "a velocity shard steps through bgk_shard_partials and bgk_shard_stage");
     bgk_status st;
     if (!ctx->part_valid) {
         if ((st = run_moments(ctx, ctx->f[0]))) return st;
@@ -1021,6 +1110,7 @@ bgk_status bgk_step(bgk_ctx *ctx, double dt, int n_steps) {
 bgk_status bgk_stage(bgk_ctx *ctx, const void *f_n, const void *f_in, void *f_out, double a,
                      double b, double c) {
     if (!ctx || !f_in || !f_out || f_in == f_out) return BGK_EINVAL;
+    if (ctx->shard) return fail(ctx, BGK_ENOTSUP, "a velocity shard needs the summed moments: use bgk_shard_stage");
     if (a != 0.0 && !f_n) return BGK_EINVAL;
     bgk_status st;
     if ((st = run_moments(ctx, f_in))) return st;
@@ -1031,6 +1121,7 @@ bgk_status bgk_stage(bgk_ctx *ctx, const void *f_n, const void *f_in, void *f_ou
 
 bgk_status bgk_rhs(bgk_ctx *ctx, const void *f_in, void *r_out, int on_device) {
     if (!ctx || !f_in || !r_out) return BGK_EINVAL;
+    if (ctx->shard) return fail(ctx, BGK_ENOTSUP, "a velocity shard needs the summed moments: use bgk_shard_stage");
     const size_t bytes = (size_t)ctx->C * ctx->Nu * ctx->P * ctx->elem;
     CU(cudaMemcpyAsync(ctx->f[1], f_in, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                        ctx->stream));
@@ -1041,6 +1132,36 @@ bgk_status bgk_rhs(bgk_ctx *ctx, const void *f_in, void *r_out, int on_device) {
     CU(cudaMemcpyAsync(r_out, ctx->f[2], bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                        ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
+    return check_device_status(ctx);
+}
+
+bgk_status bgk_shard_partials(bgk_ctx *ctx, double *m) {
+    if (!ctx || !m) return BGK_EINVAL;
+    bgk_status st;
+    if (!ctx->part_valid) {
+        if ((st = run_moments(ctx, ctx->f[0]))) return st;
+        ctx->part_valid = true;
+    }
+    LaunchScope ls(ctx, BGK_K_OTHER);
+    CU(launch_sum_partials(ctx->part, ctx->n_vblk, ctx->P, m, ctx->stream));
+    return BGK_OK;
+}
+
+bgk_status bgk_shard_stage(bgk_ctx *ctx, const double *m, int stage, double dt) {
+    if (!ctx || !m || stage < 0 || stage > 2 || !(dt > 0.0)) return BGK_EINVAL;
+    if (!ctx->part_valid) return fail(ctx, BGK_EINVAL, "no partial moments of the stage input: call bgk_shard_partials first");
+    void *f0 = ctx->f[0], *f1 = ctx->f[1], *f2 = ctx->f[2];
+    bgk_status st = run_qprime(ctx, m, 1, ctx->P, ctx->eq, ctx->qp, nullptr, nullptr);
+    if (st) return st;
+    if (stage == 0) st = run_stage(ctx, nullptr, f0, f1, 0.0, 1.0, dt, true);
+    else if (stage == 1) st = run_stage(ctx, f0, f1, f2, 0.75, 0.25, 0.25 * dt, true);
+    else st = run_stage(ctx, f0, f2, f1, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0 * dt, true);
+    if (st) return st;
+    if (stage == 2) {
+        ctx->f[0] = f1;
+        ctx->f[1] = f0;
+    }
+    ctx->part_valid = true;           // the epilogue wrote the partials of the next stage's input
     return check_device_status(ctx);
 }
 
@@ -1064,6 +1185,7 @@ bgk_status bgk_moments(bgk_ctx *ctx, double *m, int on_device) {
 bgk_status bgk_macro(bgk_ctx *ctx, double *out, int on_device) {
     if (!ctx || !out) return BGK_EINVAL;
     if (ctx->curved) return fail(ctx, BGK_ENOTSUP, "macroscopic diagnostics are implemented for the uniform box mesh");
+    if (ctx->shard) return fail(ctx, BGK_ENOTSUP, "macroscopic diagnostics need every velocity (not a shard)");
     bgk_status st;
     if (!ctx->part_valid) {
         if ((st = run_moments(ctx, ctx->f[0], true))) return st;
@@ -1266,6 +1388,34 @@ bgk_status bgk_mlp_grad(bgk_ctx *ctx, const float *x, const float *t, int n, int
     CU(cudaMemsetAsync(ctx->mlp_grad, 0, MLP_NPARAM * sizeof(float), ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     return BGK_OK;
+}
+
+bgk_status bgk_mlp_infer(bgk_ctx *ctx, const float *x, long long n, float *delta, int on_device) {
+    if (!ctx || !x || !delta || n <= 0 || n > (1ll << 31)) return BGK_EINVAL;
+    if (!ctx->mlp_ready) return fail(ctx, BGK_EINVAL, "no trained or loaded network");
+    const float *dx = x;
+    float *dd = delta;
+    if (!on_device) {
+        float *bx = nullptr, *bd = nullptr;
+        CU(cudaMallocAsync((void **)&bx, (size_t)n * MLP_IN * sizeof(float), ctx->stream));
+        CU(cudaMallocAsync((void **)&bd, (size_t)n * MLP_OUT * sizeof(float), ctx->stream));
+        CU(cudaMemcpyAsync(bx, x, (size_t)n * MLP_IN * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+        dx = bx;
+        dd = bd;
+    }
+    MlpParams mp;
+    mp.w = ctx->mlp_w; mp.norm = ctx->mlp_norm; mp.w16 = ctx->mlp_w16;
+    {
+        LaunchScope ls(ctx, BGK_K_OTHER);
+        CU(launch_mlp_infer_tc(mp, dx, n, dd, ctx->status, ctx->stream));
+    }
+    if (!on_device) {
+        CU(cudaMemcpyAsync(delta, dd, (size_t)n * MLP_OUT * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaFreeAsync((void *)dx, ctx->stream));
+        CU(cudaFreeAsync(dd, ctx->stream));
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+    return check_device_status(ctx);
 }
 
 bgk_status bgk_mlp_train(bgk_ctx *ctx, int epochs, int batch, float lr, unsigned long long seed, int bf16,

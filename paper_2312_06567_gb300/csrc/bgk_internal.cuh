@@ -83,11 +83,20 @@ struct MeshInfo {
     int Ne, Ns;
 };
 
-// Uniform velocity grid: node j on axis d is lo[d] + j h[d].
+// Uniform velocity grid: node j on axis d is lo[d] + j h[d].  A context that
+// holds a slab of the third axis (a velocity shard) sees the slab as its grid;
+// w3lo / w3hi say whether the slab's first / last third-axis plane is an end of
+// the whole grid (trapezoid half weight) or an interior plane (full weight).
 struct VelGrid {
     int n[3];
     double lo[3], h[3];
+    int w3lo, w3hi;
 };
+
+// Trapezoid factor of third-axis plane j3 of a (possibly sharded) grid.
+__host__ __device__ __forceinline__ float trap3(int j3, const VelGrid &vg) {
+    return ((j3 == 0 && vg.w3lo) || (j3 == vg.n[2] - 1 && vg.w3hi)) ? 0.5f : 1.0f;
+}
 
 struct GasInfo {
     double delta, Pr, mu_ref, theta_ref, theta_S, gamma;
@@ -280,5 +289,8 @@ cudaError_t launch_macro(const double *mom, double *out, int P, const MeshInfo &
 template <typename T>
 cudaError_t launch_entropy(const T *f, const double *vtab, int Nu, int P, int Kblk, int n_vblk, double *part,
                            double *h_out, unsigned int *nonpos, cudaStream_t s);
+// out[j][p] = sum over velocity blocks of part[vb][j][p] (kernels_f64.cu):
+// a shard's partial raw moments in the layout the Q' solve reads (one block)
+cudaError_t launch_sum_partials(const double *part, int n_vblk, int P, double *out, cudaStream_t s);
 cudaError_t launch_reduce_moments(const double *part, int n_vblk, int P, double *m_out,
                                   cudaStream_t s);

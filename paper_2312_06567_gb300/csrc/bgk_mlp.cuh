@@ -70,6 +70,9 @@ __device__ __forceinline__ void mlp_infer_warp(const MlpParams &p, const float x
     }
 }
 
+// batched inference on tensor cores (mlp_tc.cu): delta[n][5] from raw features x[n][9]
+cudaError_t launch_mlp_infer_tc(const MlpParams &p, const float *x, long long n, float *delta, unsigned int *status,
+                                cudaStream_t s);
 size_t mlp_train_smem();
 cudaError_t launch_mlp_train(const MlpParams &p, const float *x, const float *t, const int *idx, int nb,
                              float *grad, double *loss, int bf16, cudaStream_t s);

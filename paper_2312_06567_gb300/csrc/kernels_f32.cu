@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(256, BGK_PLAIN_MINB) k_stage_f32(StageArgs<flo
         const int line = kl / vn1;
         const int j2 = line % vn2, j3 = line / vn2;
         if (j3 != acc.j3cur) {
-            if (acc.j3cur >= 0) acc.flush_plane(trap(acc.j3cur, vn3), (float)(acc.j3cur - jc[2]));
+            if (acc.j3cur >= 0) acc.flush_plane(trap3(acc.j3cur, vg), (float)(acc.j3cur - jc[2]));
             acc.j3cur = j3;
         }
         const float4 vl = __ldg(a.vtab32 + kl);
@@ -478,7 +478,7 @@ __global__ void __launch_bounds__(256, BGK_PLAIN_MINB) k_stage_f32(StageArgs<flo
         }
         acc.end_line(trap(j2, vn2), (float)(j2 - jc[1]));
     }
-    if (acc.j3cur >= 0) acc.flush_plane(trap(acc.j3cur, vn3), (float)(acc.j3cur - jc[2]));
+    if (acc.j3cur >= 0) acc.flush_plane(trap3(acc.j3cur, vg), (float)(acc.j3cur - jc[2]));
     if (a.part && active) {
         double m[BGK_NMOM];
         index_to_raw(acc.J, vg, uc, m);
@@ -594,7 +594,7 @@ __global__ void __launch_bounds__(TmaGeom<Q, C>::NTHR, 2) k_stage_f32_tma(StageA
         const int line = kl / vn1;
         const int j2 = line % vn2, j3 = line / vn2;
         if (j3 != acc.j3cur) {
-            if (acc.j3cur >= 0) acc.flush_plane(trap(acc.j3cur, vn3), (float)(acc.j3cur - jc[2]));
+            if (acc.j3cur >= 0) acc.flush_plane(trap3(acc.j3cur, vg), (float)(acc.j3cur - jc[2]));
             acc.j3cur = j3;
         }
         const float4 vl = __ldg(a.vtab32 + kl);
@@ -671,7 +671,7 @@ __global__ void __launch_bounds__(TmaGeom<Q, C>::NTHR, 2) k_stage_f32_tma(StageA
         if (lane == 0) atomicOr(a.status, BGK_DEV_TIMEOUT);
         return;
     }
-    if (acc.j3cur >= 0) acc.flush_plane(trap(acc.j3cur, vn3), (float)(acc.j3cur - jc[2]));
+    if (acc.j3cur >= 0) acc.flush_plane(trap3(acc.j3cur, vg), (float)(acc.j3cur - jc[2]));
     if (a.part && active) {
         double J[11], m[BGK_NMOM];
         acc.get(J);
@@ -699,7 +699,7 @@ __global__ void __launch_bounds__(256) k_moments_f32_exact(const float *f, doubl
         const int line = kl / vn1;
         const int j2 = line % vn2, j3 = line / vn2;
         if (j3 != acc.j3cur) {
-            if (acc.j3cur >= 0) acc.flush_plane(trap(acc.j3cur, vn3), (float)(acc.j3cur - jc[2]));
+            if (acc.j3cur >= 0) acc.flush_plane(trap3(acc.j3cur, vg), (float)(acc.j3cur - jc[2]));
             acc.j3cur = j3;
         }
         float jt1 = (float)(-jc[0]);
@@ -712,7 +712,7 @@ __global__ void __launch_bounds__(256) k_moments_f32_exact(const float *f, doubl
         }
         acc.end_line(trap(j2, vn2), (float)(j2 - jc[1]));
     }
-    if (acc.j3cur >= 0) acc.flush_plane(trap(acc.j3cur, vn3), (float)(acc.j3cur - jc[2]));
+    if (acc.j3cur >= 0) acc.flush_plane(trap3(acc.j3cur, vg), (float)(acc.j3cur - jc[2]));
     const double uc[3] = {vg.lo[0] + jc[0] * vg.h[0], vg.lo[1] + jc[1] * vg.h[1], vg.lo[2] + jc[2] * vg.h[2]};
     double m[BGK_NMOM];
     index_to_raw(acc.J, vg, uc, m);

@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
     int j3cur = -1;
     bool first_plane = true;
     auto flush_plane = [&](int j3) {
-        const double c = trap(j3, vn3), t = (float)(j3 - jc[2]);
+        const double c = trap3(j3, vg), t = (float)(j3 - jc[2]);
 #pragma unroll
         for (int i = 0; i < NPT; ++i) {
             float *P = Pme + i * 2 * NQ * NCT;

@@ -78,6 +78,16 @@ __global__ void k_reduce_entropy(const double *part, int n_vblk, int P, double *
     h_out[p] = s;
 }
 
+__global__ void k_sum_partials(const double *part, int n_vblk, int P, double *out) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    for (int j = 0; j < BGK_NMOM; ++j) {
+        double s = 0.0;
+        for (int vb = 0; vb < n_vblk; ++vb) s += part[((size_t)vb * BGK_NMOM + j) * P + p];
+        out[(size_t)j * P + p] = s;
+    }
+}
+
 __global__ void k_reduce_moments(const double *part, int n_vblk, int P, double *m_out) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P) return;
@@ -408,6 +418,11 @@ template cudaError_t launch_entropy<double>(const double *, const double *, int,
                                             unsigned int *, cudaStream_t);
 template cudaError_t launch_entropy<float>(const float *, const double *, int, int, int, int, double *, double *,
                                            unsigned int *, cudaStream_t);
+
+cudaError_t launch_sum_partials(const double *part, int n_vblk, int P, double *out, cudaStream_t s) {
+    k_sum_partials<<<(P + 255) / 256, 256, 0, s>>>(part, n_vblk, P, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_reduce_moments(const double *part, int n_vblk, int P, double *m_out,
                                   cudaStream_t s) {

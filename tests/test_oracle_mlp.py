@@ -89,3 +89,37 @@ def test_invariants_of_a_rotated_anisotropic_state():
     assert np.isclose(x[0, 5], ev.sum(), rtol=1e-9)
     assert np.isclose(x[0, 6], ev[0] * ev[1] + ev[0] * ev[2] + ev[1] * ev[2], rtol=1e-9)
     assert np.isclose(x[0, 7], ev.prod(), rtol=1e-9)
+
+
+def test_bf16_rounding_closed_forms():
+    """BF16 keeps 8 significant bits with ties to even: 1 + 2^-8 is a tie and
+    rounds to 1, 1 + 3 2^-9 rounds up to 1 + 2^-7, -(1 + 3 2^-8) is a tie
+    between 1 + 2^-7 (odd) and 1 + 2^-6 (even); BF16 values are fixed points;
+    the relative error of any rounding is at most 2^-8."""
+    r = mlp.bf16_round
+    assert r(1 + 2.0 ** -8) == 1.0
+    assert r(1 + 3 * 2.0 ** -9) == 1 + 2.0 ** -7
+    assert r(-(1 + 3 * 2.0 ** -8)) == -(1 + 2.0 ** -6)
+    assert r(0.0) == 0.0 and r(2.0 ** -100) == 2.0 ** -100
+    rng = np.random.default_rng(4)
+    v = rng.standard_normal(10000) * np.exp(rng.uniform(-20, 20, 10000))
+    b = r(v)
+    assert np.all(r(b) == b)
+    assert np.max(np.abs(b - v) / np.abs(v)) <= 2.0 ** -8 * (1 + 1e-6)
+
+
+def test_bf16_forward_structure():
+    """With the identity for the rounding the BF16 forward pass is the FP64
+    network; with BF16 rounding its outputs stay within the first-order bound
+    of the roundings (2^-8 of the magnitudes that enter each layer)."""
+    rng = np.random.default_rng(5)
+    params = mlp.init_params(6)
+    xn = rng.standard_normal((50, 9))
+    y, _ = mlp.forward(params, xn)
+    assert np.allclose(mlp.forward_bf16(params, xn, rnd=lambda a: a), y, rtol=0, atol=1e-14)
+    yb = mlp.forward_bf16(params, xn)
+    W1, b1, W2, b2, W3, b3 = params
+    h1 = np.abs(mlp.silu(xn @ W1 + b1))
+    bound = 8 * 2.0 ** -8 * (np.abs(mlp.silu(h1 @ W2 + b2)) @ np.abs(W3)
+                             + (h1 @ np.abs(W2)) @ np.abs(W3) + ((np.abs(xn) @ np.abs(W1)) @ np.abs(W2)) @ np.abs(W3))
+    assert np.all(np.abs(yb - y) <= bound)
