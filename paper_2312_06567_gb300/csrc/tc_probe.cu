@@ -207,8 +207,11 @@ __global__ void __launch_bounds__(PTHREADS, 1)
             *abort_flag = 1;
             atomicOr(status, BGK_DEV_TIMEOUT);
         }
-    } else {
-        // ---- TMEM readback: warp w reads lanes 32 (w % 4) .. + 15 (the M = 64 layout) ----
+    } else if (warp >= 1) {
+        // ---- TMEM readback (whole warps 1-4; lanes 1-31 of warp 0 stay out:
+        // tcgen05.ld and __all_sync are collective over the full warp, and its
+        // lane 0 is the issuing thread): warp w reads lanes 32 (w % 4) .. + 15,
+        // the M = 64 layout ----
         const int q = warp % 4;
         const int r0 = 16 * q + lane / 4, r1 = r0 + 8;      // this thread's two output rows
         double sum = 0.0;
