@@ -375,11 +375,10 @@ def run_ours(args, rank, world, dev):
         tot1 = s.totals()
         scale = np.array([tot0[0]] * 4 + [tot0[4]])
         drift = float(np.max(np.abs(tot1 - tot0) / scale)) / args.steps
-        diag = None
-        if wl.mapping is None and not wl.diffuse and not wl.closed:
-            mac = s.macro()                             # Kn_GLL etc. of the final state (untimed)
-            diag = {"kn_gll_max": float(mac[:, 9].max()), "mach_max": float(mac[:, 6].max()),
-                    "breakdown_fraction": float(np.mean(mac[:, 9] > 0.05))}
+        mac = s.macro()                                 # Kn_GLL etc. of the final state (untimed)
+        diag = {"kn_gll_max": float(mac[:, 9].max()), "mach_max": float(mac[:, 6].max()),
+                "breakdown_fraction": float(np.mean(mac[:, 9] > 0.05))}
+        diag.update(shock_diagnostics(wl, mac))
         # per-kernel times: one more step with direct launches and an event
         # pair around each kernel (outside the timed region)
         s.profile(True)
@@ -423,6 +422,29 @@ def run_ours(args, rank, world, dev):
         s.destroy()
         torch.cuda.empty_cache()
     return wl, results, peaks
+
+
+def shock_diagnostics(wl, mac):
+    """Shock and sonic-surface quantities of the final state (postprocess):
+    the number of Mach = 1 crossings along the first-axis node lines, the
+    max-slope shock thickness where a shock is set up (the normal shock), and
+    the shock standoff on the stagnation line of the sphere O-grid."""
+    from paper_2312_06567_gb300 import postprocess as pp
+    x = W.node_positions(wl).reshape(-1, 3)
+    lines = pp.first_axis_lines(wl)
+    out = {"sonic_crossings": len(pp.mach_crossings(x, mac[:, 6], lines))}
+    if wl.dirichlet and (0, -1) in wl.dirichlet and (0, 1) in wl.dirichlet and wl.mapping is None:
+        r1, r2 = wl.dirichlet[(0, -1)][0], wl.dirichlet[(0, 1)][0]
+        out["shock_thickness_max_slope"] = pp.max_slope_thickness(r1, r2, float(mac[:, 8].max()))
+    if wl.mapping is not None and wl.diffuse:
+        # the line whose nodes point most nearly against the freestream (+x)
+        xn = x[lines[:, 0]]
+        j = int(np.argmax(-xn[:, 0] / np.linalg.norm(xn, axis=1)))
+        sv, pt = pp.max_gradient_position(x, mac[:, 8], lines[j])
+        r_body = float(np.linalg.norm(wl.mapping(np.array([[0.0, 0.5, 0.5]]))[0]))    # the wall's radius
+        out["stagnation_line_shock_radius"] = float(np.linalg.norm(pt))
+        out["shock_standoff"] = float(np.linalg.norm(pt)) - r_body
+    return out
 
 
 def held_out_guess(s, wl, dt, torch):

@@ -338,10 +338,11 @@ BGK_API bgk_status bgk_moments_noalloc(const bgk_vgrid_desc *vgrid, const double
  * grad rho is the gradient of the FR-corrected density polynomial (nodal
  * derivative plus correction-function terms carrying the central common
  * interface value; at a Dirichlet face the average with the face state's
- * density).  out is host memory (on_device = 0) or device memory (1).
- * Errors: BGK_EINVAL, BGK_ECUDA; BGK_ENOTSUP on the curvilinear path
- * (node_xyz, diffuse or closed faces), where the gradient would need the
- * metric terms. */
+ * density; at a specular, diffuse or collapsed face the element's own trace);
+ * on a curvilinear mesh by the chain rule through the metric terms,
+ * grad rho = (1/J) sum_d S^d d rho/d xi_d.  out is host memory
+ * (on_device = 0) or device memory (1).  Errors: BGK_EINVAL, BGK_ECUDA;
+ * BGK_ENOTSUP on a velocity shard (the moments would be partial). */
 BGK_API bgk_status bgk_macro(bgk_ctx *ctx, double *out, int on_device);
 
 /* The Q' solve alone (section "Numerical method", discrete compatibility):

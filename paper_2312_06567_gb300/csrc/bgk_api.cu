@@ -1184,7 +1184,6 @@ bgk_status bgk_moments(bgk_ctx *ctx, double *m, int on_device) {
 
 bgk_status bgk_macro(bgk_ctx *ctx, double *out, int on_device) {
     if (!ctx || !out) return BGK_EINVAL;
-    if (ctx->curved) return fail(ctx, BGK_ENOTSUP, "macroscopic diagnostics are implemented for the uniform box mesh");
     if (ctx->shard) return fail(ctx, BGK_ENOTSUP, "macroscopic diagnostics need every velocity (not a shard)");
     bgk_status st;
     if (!ctx->part_valid) {
@@ -1199,7 +1198,8 @@ bgk_status bgk_macro(bgk_ctx *ctx, double *out, int on_device) {
     {
         LaunchScope ls(ctx, BGK_K_OTHER);
         CU(launch_reduce_moments(ctx->part, ctx->n_vblk, ctx->P, ctx->mom, ctx->stream));
-        CU(launch_macro(ctx->mom, dst, ctx->P, ctx->mesh, ctx->fr, ctx->gas, face_rho, ctx->stream));
+        CU(launch_macro(ctx->mom, dst, ctx->P, ctx->mesh, ctx->fr, ctx->gas, face_rho, ctx->curved ? ctx->geo : nullptr,
+                        ctx->stream));
     }
     if (!on_device) {
         CU(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, ctx->stream));

@@ -283,7 +283,7 @@ bool stage_f32_variant_supported(const StageArgs<float> &a, int C, int variant, 
 cudaError_t launch_maxwellian_f32(float *f, const double *q, const double *vtab, int Nu, int P, int C,
                                   double delta, cudaStream_t s);
 cudaError_t launch_macro(const double *mom, double *out, int P, const MeshInfo &mesh, const FROps &fr,
-                         const GasInfo &gas, const double face_rho[6], cudaStream_t s);
+                         const GasInfo &gas, const double face_rho[6], const double *geo, cudaStream_t s);
 // per-point entropy sum_k w_k F ln F of the F component (kernels_f64.cu);
 // part holds n_vblk * P doubles, *nonpos counts the non-positive values
 template <typename T>

@@ -6,15 +6,19 @@
 // of the FR-corrected density polynomial along each reference direction:
 // the nodal derivative plus the correction-function derivatives times the
 // differences between the central common interface value (at a Dirichlet
-// face, the average with the face state's density; at a specular face the
-// element's own trace) and the element's trace.
+// face, the average with the face state's density; at a specular, diffuse
+// or collapsed face the element's own trace: none of them prescribes a
+// density) and the element's trace.  On the box d/dx_d = (2/h_d) d/dxi_d; on
+// a curvilinear mesh the chain rule grad rho = (1/J) sum_d S^d d rho/d xi_d
+// with the node's metric terms S^d = J grad xi_d.
 // FP64; one thread per point.
 #include "bgk_internal.cuh"
 
 namespace {
 
+// geo: the curvilinear node records [P][BGK_NGEO] (S^1, S^2, S^3, 1/J, ...) or null on the box
 __global__ void k_macro(const double *mom, double *out, int P, MeshInfo mesh, FROps fr, GasInfo gas,
-                        double3 bc_lo, double3 bc_hi) {
+                        double3 bc_lo, double3 bc_hi, const double *geo) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P) return;
     const int q = fr.q, NS = q * q * q;
@@ -41,7 +45,7 @@ __global__ void k_macro(const double *mom, double *out, int P, MeshInfo mesh, FR
     const int estr[3] = {1, n1, n1 * n2};
     const int nn[3] = {n1, n2, n3};
     const double face_lo[3] = {bc_lo.x, bc_lo.y, bc_lo.z}, face_hi[3] = {bc_hi.x, bc_hi.y, bc_hi.z};
-    double g2 = 0.0;
+    double dxi[3];
     for (int d = 0; d < 3; ++d) {
         const int base = s - id[d] * stride[d];
         const int i = id[d];
@@ -60,18 +64,31 @@ __global__ void k_macro(const double *mom, double *out, int P, MeshInfo mesh, FR
             outL = 0.0;
             for (int j = 0; j < q; ++j) outL = fma(fr.lp[j], mom[((size_t)eL * NS + base + j * stride[d]) * BGK_NMOM], outL);
         } else {
-            outL = mesh.specular[2 * d] ? trL : face_lo[d];        // a specular face mirrors the element
+            // a Dirichlet face prescribes the density; the other faces give the element's own trace
+            outL = (mesh.face_kind[2 * d] == BGK_FK_DIRICHLET && !mesh.specular[2 * d]) ? face_lo[d] : trL;
         }
         if (eR >= 0) {
             outR = 0.0;
             for (int j = 0; j < q; ++j) outR = fma(fr.lm[j], mom[((size_t)eR * NS + base + j * stride[d]) * BGK_NMOM], outR);
         } else {
-            outR = mesh.specular[2 * d + 1] ? trR : face_hi[d];
+            outR = (mesh.face_kind[2 * d + 1] == BGK_FK_DIRICHLET && !mesh.specular[2 * d + 1]) ? face_hi[d] : trR;
         }
         const double cL = 0.5 * (trL + outL), cR = 0.5 * (trR + outR);
         der += (cL - trL) * fr.dgL[i] + (cR - trR) * fr.dgR[i];
-        const double gd = mesh.two_over_h[d] * der;
-        g2 = fma(gd, gd, g2);
+        dxi[d] = der;
+    }
+    double g2 = 0.0;
+    if (geo) {
+        const double *g = geo + (size_t)p * BGK_NGEO;
+        for (int c = 0; c < 3; ++c) {
+            const double gc = g[9] * (g[c] * dxi[0] + g[3 + c] * dxi[1] + g[6 + c] * dxi[2]);
+            g2 = fma(gc, gc, g2);
+        }
+    } else {
+        for (int d = 0; d < 3; ++d) {
+            const double gd = mesh.two_over_h[d] * dxi[d];
+            g2 = fma(gd, gd, g2);
+        }
     }
     const double gn = sqrt(g2);
     double *o = out + (size_t)p * BGK_NMACRO;
@@ -82,9 +99,9 @@ __global__ void k_macro(const double *mom, double *out, int P, MeshInfo mesh, FR
 }  // namespace
 
 cudaError_t launch_macro(const double *mom, double *out, int P, const MeshInfo &mesh, const FROps &fr,
-                         const GasInfo &gas, const double face_rho[6], cudaStream_t s) {
+                         const GasInfo &gas, const double face_rho[6], const double *geo, cudaStream_t s) {
     const double3 lo = make_double3(face_rho[0], face_rho[2], face_rho[4]);
     const double3 hi = make_double3(face_rho[1], face_rho[3], face_rho[5]);
-    k_macro<<<(P + 255) / 256, 256, 0, s>>>(mom, out, P, mesh, fr, gas, lo, hi);
+    k_macro<<<(P + 255) / 256, 256, 0, s>>>(mom, out, P, mesh, fr, gas, lo, hi, geo);
     return cudaGetLastError();
 }
