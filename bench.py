@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--depth", type=int, default=6, help="copy-ring depth of the async stage kernel")
     ap.add_argument("--no-graphs", action="store_true", help="time direct launches instead of CUDA-graph replays")
     ap.add_argument("--no-tc-probe", action="store_true", help="skip the tensor-core FR-operator probe")
+    ap.add_argument("--tc-probe-panels", type=int, default=1 << 20,
+                    help="panels (48 velocities x 64 nodes, 12 KB each) the tensor-core probe streams")
     return ap.parse_args()
 
 
@@ -301,10 +303,10 @@ def run_ours(args, rank, world, dev):
             peaks[k] = bgk.probe_peak(k)
         if wl.p == 3 and not args.no_tc_probe:
             # the p = 3 FR element operator streamed through tcgen05 MMAs
-            # (2^20 panels = 3.2e9 element-node-velocity DOF, 12.9 GB of
-            # split operands), measured beside the stage it would feed
+            # (by default 2^20 panels = 3.2e9 element-node-velocity DOF,
+            # 12.9 GB of split operands), measured beside the stage it would feed
             try:
-                peaks["tensor_fr_probe"] = bgk.probe_tc(1 << 20)
+                peaks["tensor_fr_probe"] = bgk.probe_tc(args.tc_probe_panels)
             except Exception as exc:
                 peaks["tensor_fr_probe"] = {"unavailable": "%s: %s" % (type(exc).__name__, exc)}
     forms = [f for f in args.forms.split(",") if f]

@@ -92,12 +92,12 @@ def test_sharded_stepper_drives_library_shards(lib):
     'all-reduce' (the identity): the whole grid in one shard context equals
     the plain context bit for bit."""
     import torch
-    wl = W.reduced(W.taylor_green_box(), mesh_n=(2, 2, 1), vel_n=(8, 7, 6)).replace(p=1)
+    wl = W.reduced(W.taylor_green_box(), mesh_n=(2, 2, 1), vel_n=(10, 9, 8)).replace(p=1)
     f0 = W.random_anisotropic_state(wl, seed=42)
     dt = wl.dt()
     with lib.Solver(wl) as s:
         s.set_state(f0)
-        s.step(dt, 2)
+        assert s.step(dt, 2) == lib.BGK_OK
         ref = s.get_state()
     with lib.Solver(wl, shard=(0, wl.vel_n[2])) as s:
         s.set_state(f0)
