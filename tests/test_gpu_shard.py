@@ -92,8 +92,8 @@ def test_sharded_stepper_drives_library_shards(lib):
     'all-reduce' (the identity): the whole grid in one shard context equals
     the plain context bit for bit."""
     import torch
-    wl = W.reduced(W.taylor_green_box(), mesh_n=(2, 2, 1), vel_n=(10, 9, 8)).replace(p=1)
-    f0 = W.random_anisotropic_state(wl, seed=42)
+    wl = W.reduced(W.taylor_green_box(), mesh_n=(3, 2, 2), vel_n=(9, 8, 12)).replace(p=2)
+    f0 = W.random_anisotropic_state(wl, seed=41)
     dt = wl.dt()
     with lib.Solver(wl) as s:
         s.set_state(f0)
