@@ -8,16 +8,20 @@ step is one SSP-RK3 step = 3 stages; value = DOF x 3 K / (timed seconds),
 summed over ranks (independent replicas, weak scaling).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload NAME] [--forms fp64,mixed,mixed_learned]
+                  [--workload NAME] [--forms fp64,fp64_learned,mixed,mixed_learned]
                   [--stage-kernel tune|auto|plain|async|line|...] [--depth S]
                   [--no-graphs] [--e2e-steps E] [--no-cpu-baseline]
+                  [--no-tc-probe] [--tc-probe-panels N] [--no-other-workloads]
 
 Workloads: taylor_green (default), sine_box, normal_shock, sphere_ogrid and
 smaller copies of the box and the O-grid for profiling.  The line carries the
 headline form (mixed + learned guess) at the top level and the other forms
 under their names, the dominant kernel's roofline, the clocks sampled during
-the timed steps, the end-to-end number through host buffers and the oracle's
-CPU baseline (one process and all cores).
+the timed steps, the end-to-end number through host buffers (with the copies'
+bandwidth), the oracle's CPU baseline (one process and all cores), the
+tensor-core FR-operator probe, the learned guess's held-out check and batched
+inference, and -- for the default Taylor--Green run -- the normal shock and the
+sphere O-grid (mixed + learned guess) nested under other_workloads.
 
 --impl reference times the FP64 CPU oracle (the method written out plainly,
 test infrastructure) on the host cores on a bounded sample of the same
@@ -58,6 +62,8 @@ def parse():
     ap.add_argument("--depth", type=int, default=6, help="copy-ring depth of the async stage kernel")
     ap.add_argument("--no-graphs", action="store_true", help="time direct launches instead of CUDA-graph replays")
     ap.add_argument("--no-tc-probe", action="store_true", help="skip the tensor-core FR-operator probe")
+    ap.add_argument("--no-other-workloads", action="store_true",
+                    help="skip the normal shock and sphere O-grid lines nested in the default run")
     ap.add_argument("--tc-probe-panels", type=int, default=1 << 20,
                     help="panels (48 velocities x 64 nodes, 12 KB each) the tensor-core probe streams")
     return ap.parse_args()
@@ -400,16 +406,29 @@ def run_ours(args, rank, world, dev):
             s.step(dt, 1)
             s.get_state(host)
             torch.cuda.synchronize()
+            t_in = t_step = t_out = 0.0
             t0 = time.perf_counter()
             for _ in range(args.e2e_steps):
-                s.set_state(host)
+                ta = time.perf_counter()
+                s.set_state(host)                    # returns after the copy (host memory)
+                tb = time.perf_counter()
                 s.step(dt, 1)
-                s.get_state(host)
+                torch.cuda.synchronize()
+                tc = time.perf_counter()
+                s.get_state(host)                    # returns after the copy
+                td = time.perf_counter()
+                t_in += tb - ta
+                t_step += tc - tb
+                t_out += td - tc
             torch.cuda.synchronize()
             e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
             nbytes = host.numel() * host.element_size()
             e2e = {"value": job_throughput(world, wl.dof, args.e2e_steps, 1e3 * e2e_s), "unit": UNIT,
-                   "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+                   "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                   "h2d_gbs": nbytes * args.e2e_steps / t_in / 1e9,
+                   "d2h_gbs": nbytes * args.e2e_steps / t_out / 1e9,
+                   "step_ms": 1e3 * t_step / args.e2e_steps,
+                   "copies": "one cudaMemcpyAsync each way per step from pinned host memory"}
             del host
         newton = dict(mean_iters=mean_it, max_iters=max_it, max_residual=res)
         if learned:
@@ -647,6 +666,23 @@ def main():
         return
     peaks["hbm_gbs"] = _measured_hbm()
     line = compose_line(args, wl, results, peaks, world)
+    if world == 1 and args.workload == "taylor_green" and not args.no_other_workloads:
+        # the normal shock and the sphere O-grid at full size, mixed form + learned
+        # guess, beside the headline (their own clocks and kernel times)
+        line["other_workloads"] = {}
+        for name in ("normal_shock", "sphere_ogrid"):
+            sub = argparse.Namespace(**vars(args))
+            sub.workload, sub.forms, sub.e2e_steps, sub.steps, sub.no_tc_probe = name, "mixed_learned", 0, 2, True
+            try:
+                wl2, res2, pk2 = run_ours(sub, rank, world, dev)
+                pk2["hbm_gbs"] = peaks["hbm_gbs"]
+                l2 = compose_line(sub, wl2, res2, pk2, world)
+                line["other_workloads"][name] = {
+                    k: l2[k] for k in ("value", "ms_per_step", "config", "kernels_ms_per_step", "roofline", "clocks",
+                                       "conservation_drift_per_step", "drift_is_conservation", "newton",
+                                       "stage_kernel", "diagnostics", "status")}
+            except Exception as exc:
+                line["other_workloads"][name] = {"unavailable": "%s: %s" % (type(exc).__name__, exc)}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
         try:
