@@ -290,5 +290,5 @@ def test_curvilinear_declines_what_it_does_not_support(lib):
         s.set_stage_kernel("plain", 4)
         v, d, ms = s.tune_stage(wl.dt(), reps=1)
         assert v in ("auto", "plain")
-        with pytest.raises(RuntimeError):
-            s.macro()
+        # the macroscopic diagnostics take the metric terms (not declined)
+        assert np.all(np.isfinite(s.macro()))
