@@ -277,6 +277,25 @@ BGK_API bgk_status bgk_tune_stage(bgk_ctx *ctx, double dt, int reps, int *varian
  * BGK_ENOCONV (a Q' solve did not converge; r_out uses the last iterate). */
 BGK_API bgk_status bgk_rhs(bgk_ctx *ctx, const void *f_in, void *r_out, int on_device);
 
+/* Pipelined stepping from host memory to host memory: copy the state f_in
+ * (host, layout of bgk_set_state) to the device, advance it n_steps SSP-RK3
+ * steps of size dt, copy the result to f_out (host).  Asynchronous: the call
+ * returns after enqueueing; the host-to-device copy of this call and the
+ * device-to-host copy of the previous call's result run on their own streams
+ * and overlap the compute, so a loop of calls keeps both copy directions and
+ * the GPU busy at once.  f_in and f_out must stay valid and unmodified until
+ * bgk_step_host_sync returns (pinned memory gives the full copy rate).  Uses
+ * one more state-sized device buffer (allocated on the first call) and direct
+ * launches instead of CUDA graphs.  Any other call that reads or writes the
+ * state waits for the pipeline first.  Errors: BGK_EINVAL (NULL, dt <= 0,
+ * n_steps < 1), BGK_ENOTSUP (a velocity shard), BGK_ENOMEM, BGK_ECUDA. */
+BGK_API bgk_status bgk_step_host(bgk_ctx *ctx, const void *f_in, void *f_out, double dt, int n_steps);
+/* Wait for every bgk_step_host call: all results are in their f_out, the
+ * context's state is the last result.  Device failures (Newton
+ * non-convergence, a bounded wait that gave up) are reported here.  Errors:
+ * BGK_EINVAL (NULL), BGK_ENOCONV, BGK_ETIMEOUT, BGK_ECUDA. */
+BGK_API bgk_status bgk_step_host_sync(bgk_ctx *ctx);
+
 /* n_steps steps of SSP-RK3 (Shu--Osher) with step dt on the stored state
  * (the explicit time marching of section "Methodology").  Each stage is two
  * kernels: the Q' solve from the moments of the stage input, and the fused

@@ -80,6 +80,8 @@ SIGNATURES = {
     "bgk_profile_read": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(ctypes.c_longlong)]),
     "bgk_probe_peak": (c_int, [c_int, ctypes.POINTER(c_double)]),
     "bgk_probe_tc": (c_int, [ctypes.c_longlong, ctypes.POINTER(c_double)]),
+    "bgk_step_host": (c_int, [c_void_p, c_void_p, c_void_p, c_double, c_int]),
+    "bgk_step_host_sync": (c_int, [c_void_p]),
     "bgk_create_shard": (c_int, [ctypes.POINTER(c_void_p), c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int,
                                  c_int]),
     "bgk_shard_partials": (c_int, [c_void_p, c_void_p]),
@@ -503,6 +505,27 @@ class Solver:
             grads.append(g[off:off + n].reshape(shp).astype(np.float64))
             off += n
         return loss.value, grads
+
+    def step_host(self, f_in, f_out, dt, n_steps=1):
+        """bgk_step_host: enqueue f_in (host) -> n_steps -> f_out (host); returns
+        at once.  Keep both buffers alive until step_host_sync()."""
+        pi, din = _ptr(f_in)
+        po, dout = _ptr(f_out)
+        if din or dout:
+            raise ValueError("step_host takes host buffers (pinned for the full copy rate)")
+        for t in (f_in, f_out):
+            if tuple(t.shape) != self.shape:
+                raise ValueError("state shape %s, expected %s" % (tuple(t.shape), self.shape))
+            if np.dtype(str(t.dtype).replace("torch.", "")) != np.dtype(self.dtype):
+                raise ValueError("state dtype %s, expected %s" % (t.dtype, np.dtype(self.dtype)))
+        self._check(self.lib.bgk_step_host(self._h, pi, po, float(dt), int(n_steps)))
+
+    def step_host_sync(self):
+        """bgk_step_host_sync: wait for every step_host call; returns the status."""
+        st = self.lib.bgk_step_host_sync(self._h)
+        if st not in (BGK_OK, BGK_ENOCONV):
+            self._check(st)
+        return st
 
     # -- velocity shards -------------------------------------------------------
     def shard_partials(self, m):

@@ -69,6 +69,19 @@ struct bgk_ctx {
     // between two buffers); recaptured when a launch parameter changes
     bool graphs_on;
     cudaStream_t cap_stream;          // private stream the graphs are captured on
+    // pipelined host-to-host stepping (bgk_step_host): a fourth state buffer,
+    // copy streams in each direction, and per buffer the event of its last
+    // device-to-host copy
+    struct HostPipe {
+        void *extra = nullptr;        // the fourth state buffer
+        cudaStream_t s_in = nullptr, s_out = nullptr;
+        cudaEvent_t ev_in = nullptr, ev_comp = nullptr;
+        void *buf[4] = {nullptr, nullptr, nullptr, nullptr};
+        cudaEvent_t ev_out[4] = {nullptr, nullptr, nullptr, nullptr};
+        bool out_pending[4] = {false, false, false, false};
+        void *prev_res = nullptr;     // the result before the last one (the next input's buffer)
+        bool active = false;
+    } pipe;
     struct StepGraph {
         cudaGraphExec_t exec = nullptr;
         void *f[3] = {nullptr, nullptr, nullptr};
@@ -902,6 +915,16 @@ bgk_status bgk_destroy(bgk_ctx *ctx) {
     cudaStreamSynchronize(ctx->stream);
     drop_graphs(ctx);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    {
+        bgk_ctx::HostPipe &hp = ctx->pipe;
+        if (hp.s_in) { cudaStreamSynchronize(hp.s_in); cudaStreamDestroy(hp.s_in); }
+        if (hp.s_out) { cudaStreamSynchronize(hp.s_out); cudaStreamDestroy(hp.s_out); }
+        if (hp.ev_in) cudaEventDestroy(hp.ev_in);
+        if (hp.ev_comp) cudaEventDestroy(hp.ev_comp);
+        for (int i = 0; i < 4; ++i)
+            if (hp.ev_out[i]) cudaEventDestroy(hp.ev_out[i]);
+        cudaFree(hp.extra);
+    }
     for (auto &r : ctx->prof_pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : ctx->ev_pool) cudaEventDestroy(e);
     for (int i = 0; i < 3; ++i) cudaFree(ctx->f[i]);
@@ -942,6 +965,10 @@ bgk_status bgk_node_coords(const bgk_ctx *ctx_c, double *x, int on_device) {
 
 bgk_status bgk_set_state(bgk_ctx *ctx, const void *f, int on_device) {
     if (!ctx || !f) return BGK_EINVAL;
+    if (ctx->pipe.active) {                 // host copies of bgk_step_host may still read the state
+        bgk_status ps = bgk_step_host_sync(ctx);
+        if (ps) return ps;
+    }
     const size_t bytes = (size_t)ctx->C * ctx->Nu * ctx->P * ctx->elem;
     CU(cudaMemcpyAsync(ctx->f[0], f, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                        ctx->stream));
@@ -952,6 +979,10 @@ bgk_status bgk_set_state(bgk_ctx *ctx, const void *f, int on_device) {
 
 bgk_status bgk_get_state(bgk_ctx *ctx, void *f, int on_device) {
     if (!ctx || !f) return BGK_EINVAL;
+    if (ctx->pipe.active) {
+        bgk_status ps = bgk_step_host_sync(ctx);
+        if (ps) return ps;
+    }
     const size_t bytes = (size_t)ctx->C * ctx->Nu * ctx->P * ctx->elem;
     CU(cudaMemcpyAsync(f, ctx->f[0], bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                        ctx->stream));
@@ -961,6 +992,10 @@ bgk_status bgk_get_state(bgk_ctx *ctx, void *f, int on_device) {
 
 bgk_status bgk_set_maxwellian(bgk_ctx *ctx, const double *q, int on_device) {
     if (!ctx || !q) return BGK_EINVAL;
+    if (ctx->pipe.active) {
+        bgk_status ps = bgk_step_host_sync(ctx);
+        if (ps) return ps;
+    }
     const double *dq = q;
     double *tmp = nullptr;
     if (!on_device) {
@@ -1089,6 +1124,7 @@ bgk_status bgk_step(bgk_ctx *ctx, double dt, int n_steps) {
     if (!ctx || !(dt > 0.0) || n_steps < 0) return BGK_EINVAL;
     if (ctx->shard) return fail(ctx, BGK_ENOTSUP, "a velocity shard steps through bgk_shard_partials and bgk_shard_stage");
     bgk_status st;
+    if (ctx->pipe.active && (st = bgk_step_host_sync(ctx))) return st;
     if (!ctx->part_valid) {
         if ((st = run_moments(ctx, ctx->f[0]))) return st;
         ctx->part_valid = true;
@@ -1104,6 +1140,82 @@ bgk_status bgk_step(bgk_ctx *ctx, double dt, int n_steps) {
         ctx->f[0] = f1;
         ctx->f[1] = f0;
     }
+    return check_device_status(ctx);
+}
+
+namespace {
+// index of a state buffer among the pipeline's four
+int pipe_index(const bgk_ctx::HostPipe &hp, const void *b) {
+    for (int i = 0; i < 4; ++i)
+        if (hp.buf[i] == b) return i;
+    return -1;
+}
+}  // namespace
+
+bgk_status bgk_step_host(bgk_ctx *ctx, const void *f_in, void *f_out, double dt, int n_steps) {
+    if (!ctx || !f_in || !f_out || !(dt > 0.0) || n_steps < 1) return BGK_EINVAL;
+    if (ctx->shard) return fail(ctx, BGK_ENOTSUP, "a velocity shard steps through bgk_shard_partials and bgk_shard_stage");
+    bgk_ctx::HostPipe &hp = ctx->pipe;
+    const size_t bytes = (size_t)ctx->C * ctx->Nu * ctx->P * ctx->elem;
+    if (!hp.active) {
+        // set up: the fourth buffer, the copy streams and events; the current
+        // state buffer becomes the "result before the last one" (no copy pending)
+        if (!hp.extra) CU(cudaMalloc(&hp.extra, bytes));
+        if (!hp.s_in) CU(cudaStreamCreateWithFlags(&hp.s_in, cudaStreamNonBlocking));
+        if (!hp.s_out) CU(cudaStreamCreateWithFlags(&hp.s_out, cudaStreamNonBlocking));
+        if (!hp.ev_in) CU(cudaEventCreateWithFlags(&hp.ev_in, cudaEventDisableTiming));
+        if (!hp.ev_comp) CU(cudaEventCreateWithFlags(&hp.ev_comp, cudaEventDisableTiming));
+        for (int i = 0; i < 4; ++i)
+            if (!hp.ev_out[i]) CU(cudaEventCreateWithFlags(&hp.ev_out[i], cudaEventDisableTiming));
+        hp.buf[0] = ctx->f[0]; hp.buf[1] = ctx->f[1]; hp.buf[2] = ctx->f[2]; hp.buf[3] = hp.extra;
+        for (int i = 0; i < 4; ++i) hp.out_pending[i] = false;
+        // the first input goes to the fourth buffer; the state buffer is free after it
+        hp.prev_res = hp.extra;
+        hp.active = true;
+    }
+    // this call's input buffer: the result before the last one, once its
+    // device-to-host copy (if any) has finished
+    void *in = hp.prev_res;
+    const int ii = pipe_index(hp, in);
+    if (ii < 0) return fail(ctx, BGK_ECUDA, "host pipeline lost track of its buffers");
+    if (hp.out_pending[ii]) CU(cudaStreamWaitEvent(hp.s_in, hp.ev_out[ii], 0));
+    CU(cudaMemcpyAsync(in, f_in, bytes, cudaMemcpyHostToDevice, hp.s_in));
+    CU(cudaEventRecord(hp.ev_in, hp.s_in));
+    // compute on the context's stream: the new input, the last call's free
+    // buffer as the first stage buffer, the second stage buffer unchanged
+    void *last_res = ctx->f[0], *free_buf = ctx->f[1];
+    CU(cudaStreamWaitEvent(ctx->stream, hp.ev_in, 0));
+    ctx->f[0] = in;
+    ctx->f[1] = free_buf;
+    ctx->part_valid = false;
+    bgk_status st;
+    if ((st = run_moments(ctx, ctx->f[0]))) return st;
+    ctx->part_valid = true;
+    for (int n = 0; n < n_steps; ++n) {
+        void *f0 = ctx->f[0], *f1 = ctx->f[1];
+        if ((st = enqueue_step(ctx, dt))) return st;
+        ctx->f[0] = f1;
+        ctx->f[1] = f0;
+    }
+    CU(cudaEventRecord(hp.ev_comp, ctx->stream));
+    // the result's device-to-host copy after the compute, on its own stream
+    const int ri = pipe_index(hp, ctx->f[0]);
+    if (ri < 0) return fail(ctx, BGK_ECUDA, "host pipeline lost track of its buffers");
+    CU(cudaStreamWaitEvent(hp.s_out, hp.ev_comp, 0));
+    CU(cudaMemcpyAsync(f_out, ctx->f[0], bytes, cudaMemcpyDeviceToHost, hp.s_out));
+    CU(cudaEventRecord(hp.ev_out[ri], hp.s_out));
+    hp.out_pending[ri] = true;
+    hp.prev_res = last_res;
+    return BGK_OK;
+}
+
+bgk_status bgk_step_host_sync(bgk_ctx *ctx) {
+    if (!ctx) return BGK_EINVAL;
+    bgk_ctx::HostPipe &hp = ctx->pipe;
+    if (hp.s_in) CU(cudaStreamSynchronize(hp.s_in));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (hp.s_out) CU(cudaStreamSynchronize(hp.s_out));
+    for (int i = 0; i < 4; ++i) hp.out_pending[i] = false;
     return check_device_status(ctx);
 }
 
