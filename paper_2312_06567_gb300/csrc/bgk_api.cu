@@ -923,11 +923,24 @@ bgk_status bgk_destroy(bgk_ctx *ctx) {
         if (hp.ev_comp) cudaEventDestroy(hp.ev_comp);
         for (int i = 0; i < 4; ++i)
             if (hp.ev_out[i]) cudaEventDestroy(hp.ev_out[i]);
-        cudaFree(hp.extra);
     }
     for (auto &r : ctx->prof_pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : ctx->ev_pool) cudaEventDestroy(e);
-    for (int i = 0; i < 3; ++i) cudaFree(ctx->f[i]);
+    // the state buffers: f[0..2], plus the host pipeline's fourth buffer,
+    // which may have rotated into f[] (free each pointer once)
+    {
+        void *bufs[4] = {ctx->f[0], ctx->f[1], ctx->f[2], ctx->pipe.extra};
+        for (int i = 0; i < 4; ++i) {
+            bool seen = false;
+            for (int j = 0; j < i; ++j) seen = seen || bufs[j] == bufs[i];
+            if (bufs[i] && !seen) cudaFree(bufs[i]);
+        }
+        if (ctx->pipe.prev_res && ctx->pipe.prev_res != ctx->pipe.extra) {
+            bool seen = false;
+            for (int j = 0; j < 4; ++j) seen = seen || bufs[j] == ctx->pipe.prev_res;
+            if (!seen) cudaFree(ctx->pipe.prev_res);
+        }
+    }
     cudaFree(ctx->part); cudaFree(ctx->mom); cudaFree(ctx->eq); cudaFree(ctx->qp);
     cudaFree(ctx->iters); cudaFree(ctx->eq32); cudaFree(ctx->vtab); cudaFree(ctx->vtab32); cudaFree(ctx->bcval); cudaFree(ctx->status);
     if (ctx->shard) { cudaFree(ctx->vtab_q); cudaFree(ctx->vtab32_q); }
