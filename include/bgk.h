@@ -285,8 +285,10 @@ BGK_API bgk_status bgk_rhs(bgk_ctx *ctx, const void *f_in, void *r_out, int on_d
  * and overlap the compute, so a loop of calls keeps both copy directions and
  * the GPU busy at once.  f_in and f_out must stay valid and unmodified until
  * bgk_step_host_sync returns (pinned memory gives the full copy rate).  Uses
- * one more state-sized device buffer (allocated on the first call) and direct
- * launches instead of CUDA graphs.  Any other call that reads or writes the
+ * one or two more state-sized device buffers (allocated on the first call;
+ * two when the device has 8 GiB to spare beyond them, so that an input copy
+ * waits only for the output copy of three calls back) and direct launches
+ * instead of CUDA graphs.  Any other call that reads or writes the
  * state waits for the pipeline first.  Errors: BGK_EINVAL (NULL, dt <= 0,
  * n_steps < 1), BGK_ENOTSUP (a velocity shard), BGK_ENOMEM, BGK_ECUDA. */
 BGK_API bgk_status bgk_step_host(bgk_ctx *ctx, const void *f_in, void *f_out, double dt, int n_steps);

@@ -73,13 +73,14 @@ struct bgk_ctx {
     // copy streams in each direction, and per buffer the event of its last
     // device-to-host copy
     struct HostPipe {
-        void *extra = nullptr;        // the fourth state buffer
+        void *extra[2] = {nullptr, nullptr};   // one or two more state buffers
+        int n_extra = 0;
         cudaStream_t s_in = nullptr, s_out = nullptr;
         cudaEvent_t ev_in = nullptr, ev_comp = nullptr;
-        void *buf[4] = {nullptr, nullptr, nullptr, nullptr};
-        cudaEvent_t ev_out[4] = {nullptr, nullptr, nullptr, nullptr};
-        bool out_pending[4] = {false, false, false, false};
-        void *prev_res = nullptr;     // the result before the last one (the next input's buffer)
+        void *buf[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+        cudaEvent_t ev_out[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+        bool out_pending[5] = {false, false, false, false, false};
+        void *older[2] = {nullptr, nullptr};   // earlier results, oldest first: the next inputs' buffers
         bool active = false;
     } pipe;
     struct StepGraph {
@@ -921,7 +922,7 @@ bgk_status bgk_destroy(bgk_ctx *ctx) {
         if (hp.s_out) { cudaStreamSynchronize(hp.s_out); cudaStreamDestroy(hp.s_out); }
         if (hp.ev_in) cudaEventDestroy(hp.ev_in);
         if (hp.ev_comp) cudaEventDestroy(hp.ev_comp);
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 5; ++i)
             if (hp.ev_out[i]) cudaEventDestroy(hp.ev_out[i]);
     }
     for (auto &r : ctx->prof_pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -929,16 +930,11 @@ bgk_status bgk_destroy(bgk_ctx *ctx) {
     // the state buffers: f[0..2], plus the host pipeline's fourth buffer,
     // which may have rotated into f[] (free each pointer once)
     {
-        void *bufs[4] = {ctx->f[0], ctx->f[1], ctx->f[2], ctx->pipe.extra};
-        for (int i = 0; i < 4; ++i) {
+        void *bufs[5] = {ctx->f[0], ctx->f[1], ctx->f[2], ctx->pipe.extra[0], ctx->pipe.extra[1]};
+        for (int i = 0; i < 5; ++i) {
             bool seen = false;
             for (int j = 0; j < i; ++j) seen = seen || bufs[j] == bufs[i];
             if (bufs[i] && !seen) cudaFree(bufs[i]);
-        }
-        if (ctx->pipe.prev_res && ctx->pipe.prev_res != ctx->pipe.extra) {
-            bool seen = false;
-            for (int j = 0; j < 4; ++j) seen = seen || bufs[j] == ctx->pipe.prev_res;
-            if (!seen) cudaFree(ctx->pipe.prev_res);
         }
     }
     cudaFree(ctx->part); cudaFree(ctx->mom); cudaFree(ctx->eq); cudaFree(ctx->qp);
@@ -1157,10 +1153,10 @@ bgk_status bgk_step(bgk_ctx *ctx, double dt, int n_steps) {
 }
 
 namespace {
-// index of a state buffer among the pipeline's four
+// index of a state buffer among the pipeline's
 int pipe_index(const bgk_ctx::HostPipe &hp, const void *b) {
-    for (int i = 0; i < 4; ++i)
-        if (hp.buf[i] == b) return i;
+    for (int i = 0; i < 5; ++i)
+        if (hp.buf[i] && hp.buf[i] == b) return i;
     return -1;
 }
 }  // namespace
@@ -1171,24 +1167,40 @@ bgk_status bgk_step_host(bgk_ctx *ctx, const void *f_in, void *f_out, double dt,
     bgk_ctx::HostPipe &hp = ctx->pipe;
     const size_t bytes = (size_t)ctx->C * ctx->Nu * ctx->P * ctx->elem;
     if (!hp.active) {
-        // set up: the fourth buffer, the copy streams and events; the current
-        // state buffer becomes the "result before the last one" (no copy pending)
-        if (!hp.extra) CU(cudaMalloc(&hp.extra, bytes));
+        // set up: one or two more state buffers (two when the device has room:
+        // then an input copy never waits for the output copy of the call before
+        // last), the copy streams and events; the current state buffer counts
+        // as the last result (no copy pending)
+        if (hp.n_extra == 0) {
+            size_t free_b = 0, total_b = 0;
+            CU(cudaMemGetInfo(&free_b, &total_b));
+            CU(cudaMalloc(&hp.extra[0], bytes));
+            hp.n_extra = 1;
+            if (free_b > 2 * bytes + ((size_t)8 << 30)) {
+                if (cudaMalloc(&hp.extra[1], bytes) == cudaSuccess) hp.n_extra = 2;
+                else { hp.extra[1] = nullptr; cudaGetLastError(); }
+            }
+        }
         if (!hp.s_in) CU(cudaStreamCreateWithFlags(&hp.s_in, cudaStreamNonBlocking));
         if (!hp.s_out) CU(cudaStreamCreateWithFlags(&hp.s_out, cudaStreamNonBlocking));
         if (!hp.ev_in) CU(cudaEventCreateWithFlags(&hp.ev_in, cudaEventDisableTiming));
         if (!hp.ev_comp) CU(cudaEventCreateWithFlags(&hp.ev_comp, cudaEventDisableTiming));
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 5; ++i)
             if (!hp.ev_out[i]) CU(cudaEventCreateWithFlags(&hp.ev_out[i], cudaEventDisableTiming));
-        hp.buf[0] = ctx->f[0]; hp.buf[1] = ctx->f[1]; hp.buf[2] = ctx->f[2]; hp.buf[3] = hp.extra;
-        for (int i = 0; i < 4; ++i) hp.out_pending[i] = false;
-        // the first input goes to the fourth buffer; the state buffer is free after it
-        hp.prev_res = hp.extra;
+        hp.buf[0] = ctx->f[0]; hp.buf[1] = ctx->f[1]; hp.buf[2] = ctx->f[2];
+        hp.buf[3] = hp.extra[0]; hp.buf[4] = hp.extra[1];
+        for (int i = 0; i < 5; ++i) hp.out_pending[i] = false;
+        hp.older[0] = hp.extra[0];
+        hp.older[1] = hp.extra[1];
+        // the state buffer joins the queue of results: its next input copy
+        // waits for whatever the context's stream still has in flight
+        CU(cudaEventRecord(hp.ev_comp, ctx->stream));
+        CU(cudaStreamWaitEvent(hp.s_in, hp.ev_comp, 0));
         hp.active = true;
     }
-    // this call's input buffer: the result before the last one, once its
+    // this call's input buffer: the oldest earlier result, once its
     // device-to-host copy (if any) has finished
-    void *in = hp.prev_res;
+    void *in = hp.older[0];
     const int ii = pipe_index(hp, in);
     if (ii < 0) return fail(ctx, BGK_ECUDA, "host pipeline lost track of its buffers");
     if (hp.out_pending[ii]) CU(cudaStreamWaitEvent(hp.s_in, hp.ev_out[ii], 0));
@@ -1196,10 +1208,9 @@ bgk_status bgk_step_host(bgk_ctx *ctx, const void *f_in, void *f_out, double dt,
     CU(cudaEventRecord(hp.ev_in, hp.s_in));
     // compute on the context's stream: the new input, the last call's free
     // buffer as the first stage buffer, the second stage buffer unchanged
-    void *last_res = ctx->f[0], *free_buf = ctx->f[1];
+    void *last_res = ctx->f[0];
     CU(cudaStreamWaitEvent(ctx->stream, hp.ev_in, 0));
     ctx->f[0] = in;
-    ctx->f[1] = free_buf;
     ctx->part_valid = false;
     bgk_status st;
     if ((st = run_moments(ctx, ctx->f[0]))) return st;
@@ -1218,7 +1229,13 @@ bgk_status bgk_step_host(bgk_ctx *ctx, const void *f_in, void *f_out, double dt,
     CU(cudaMemcpyAsync(f_out, ctx->f[0], bytes, cudaMemcpyDeviceToHost, hp.s_out));
     CU(cudaEventRecord(hp.ev_out[ri], hp.s_out));
     hp.out_pending[ri] = true;
-    hp.prev_res = last_res;
+    // the queue of earlier results: drop the one just used as input, append the last
+    if (hp.n_extra == 2) {
+        hp.older[0] = hp.older[1];
+        hp.older[1] = last_res;
+    } else {
+        hp.older[0] = last_res;
+    }
     return BGK_OK;
 }
 
@@ -1228,7 +1245,7 @@ bgk_status bgk_step_host_sync(bgk_ctx *ctx) {
     if (hp.s_in) CU(cudaStreamSynchronize(hp.s_in));
     CU(cudaStreamSynchronize(ctx->stream));
     if (hp.s_out) CU(cudaStreamSynchronize(hp.s_out));
-    for (int i = 0; i < 4; ++i) hp.out_pending[i] = false;
+    for (int i = 0; i < 5; ++i) hp.out_pending[i] = false;
     return check_device_status(ctx);
 }
 

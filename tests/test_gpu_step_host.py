@@ -1,11 +1,13 @@
 """Pipelined host-to-host stepping (bgk_step_host) against the plain
 set_state / step / get_state sequence (GPU, through the C-ABI).
 
-Three independent inputs go through the pipeline back to back (each call's
-input copy and the previous result's output copy overlap the compute); every
-result must equal the sequential one bit for bit (the same kernels in the same
-order), in both forms, with one and with two steps per call, and the context's
-state after the sync is the last result."""
+Five independent inputs go through the pipeline back to back (each call's
+input copy and the earlier results' output copies overlap the compute; five
+calls rotate every state buffer through every role); every result must equal
+the sequential one bit for bit (the same kernels in the same order), in both
+forms, with one and with two steps per call, and the context's state after the
+sync is the last result.  Ordinary stepping keeps working on the rotated
+buffers, and the pipeline keeps working after it."""
 import numpy as np
 import pytest
 
@@ -26,7 +28,7 @@ def test_pipelined_host_steps_equal_sequential_ones(lib, form, n_steps, pinned):
     wl = W.reduced(W.taylor_green_box(), mesh_n=(3, 2, 2), vel_n=(9, 8, 12)).replace(p=2)
     prec = lib.BGK_FP64 if form == "fp64" else lib.BGK_MIXED
     dt_np = np.float64 if form == "fp64" else np.float32
-    ins = [W.random_anisotropic_state(wl, seed=60 + i).astype(dt_np) for i in range(3)]
+    ins = [W.random_anisotropic_state(wl, seed=60 + i).astype(dt_np) for i in range(5)]
     dt = wl.dt()
     with lib.Solver(wl, prec) as s:
         ref = []
@@ -47,12 +49,20 @@ def test_pipelined_host_steps_equal_sequential_ones(lib, form, n_steps, pinned):
         assert s.step_host_sync() == lib.BGK_OK
         outs = [np.asarray(b) for b in hout]
         last = s.get_state()
+        outs = [o.copy() for o in outs]
+        # ordinary stepping on the rotated buffers (CUDA graphs keyed on them)
+        s.set_state(ins[1])
+        assert s.step(dt, n_steps) == lib.BGK_OK
+        plain = s.get_state()
         # the pipeline keeps going after an ordinary call
         s.set_state(ins[0])
-        s.step_host(hin[0], hout[0], dt, n_steps)
+        for a, b in zip(hin[:3], hout[:3]):
+            s.step_host(a, b, dt, n_steps)
         assert s.step_host_sync() == lib.BGK_OK
-        again = np.asarray(hout[0])
+        again = [np.asarray(b).copy() for b in hout[:3]]
     for o, r in zip(outs, ref):
         assert np.array_equal(o, r)
     assert np.array_equal(last, ref[-1])
-    assert np.array_equal(again, ref[0])
+    assert np.array_equal(plain, ref[1])
+    for o, r in zip(again, ref[:3]):
+        assert np.array_equal(o, r)
