@@ -284,11 +284,10 @@ __global__ void __launch_bounds__(256, BGK_PLAIN_MINB) k_stage_f32(StageArgs<flo
                     const float2 eqc = make_float2(gc, __fmul_rn(gfac, gc));
                     const float2 it2 = pdup(itau);
                     const float2 R = __ffma2_rn(psub(eqv, fi2), it2, __ffma2_rn(eqc, it2, pneg(div)));
-                    float2 out = fab == 1.f ? fi2 : __fmul2_rn(pdup(fab), fi2);
-                    if (fa != 0.f)
-                        out = __ffma2_rn(pdup(fa), psub(make_float2(__ldg(a.f_n + (size_t)k * slab + p),
-                                                                    __ldg(a.f_n + ((size_t)a.Nu + k) * slab + p)), fi2), out);
-                    out = __ffma2_rn(pdup(fc), R, out);
+                    const float2 fn2 = fa != 0.f ? make_float2(__ldg(a.f_n + (size_t)k * slab + p),
+                                                               __ldg(a.f_n + ((size_t)a.Nu + k) * slab + p))
+                                                 : pdup(0.f);
+                    const float2 out = rk_update2(fi2, fn2, R, fa, fab, fc, fa != 0.f);
                     a.f_out[(size_t)k * slab + p] = out.x;
                     a.f_out[((size_t)a.Nu + k) * slab + p] = out.y;
                     outv[0] = out.x;
@@ -350,11 +349,10 @@ __global__ void __launch_bounds__(256, BGK_PLAIN_MINB) k_stage_f32(StageArgs<flo
                     const float2 eqc = make_float2(gc, __fmul_rn(gfac, gc));
                     const float2 it2 = pdup(itau);
                     const float2 R = __ffma2_rn(psub(eqv, fi2), it2, __ffma2_rn(eqc, it2, pneg(div)));
-                    float2 out = fab == 1.f ? fi2 : __fmul2_rn(pdup(fab), fi2);
-                    if (fa != 0.f)
-                        out = __ffma2_rn(pdup(fa), psub(make_float2(__ldg(a.f_n + (size_t)k * slab + p),
-                                                                    __ldg(a.f_n + ((size_t)a.Nu + k) * slab + p)), fi2), out);
-                    out = __ffma2_rn(pdup(fc), R, out);
+                    const float2 fn2 = fa != 0.f ? make_float2(__ldg(a.f_n + (size_t)k * slab + p),
+                                                               __ldg(a.f_n + ((size_t)a.Nu + k) * slab + p))
+                                                 : pdup(0.f);
+                    const float2 out = rk_update2(fi2, fn2, R, fa, fab, fc, fa != 0.f);
                     a.f_out[(size_t)k * slab + p] = out.x;
                     a.f_out[((size_t)a.Nu + k) * slab + p] = out.y;
                     outv[0] = out.x;
@@ -464,10 +462,8 @@ __global__ void __launch_bounds__(256, BGK_PLAIN_MINB) k_stage_f32(StageArgs<flo
                     const float eqv = (c == 0) ? g32 : __fmul_rn(gfac, g32);
                     const float eqc = (c == 0) ? gc : __fmul_rn(gfac, gc);
                     const float R = fmaf(eqv - fself[c], itau, fmaf(eqc, itau, -div));
-                    float out = fab == 1.f ? fself[c] : fab * fself[c];
-                    if (fa != 0.f)
-                        out = fmaf(fa, __ldg(a.f_n + ((size_t)c * a.Nu + k) * slab + p) - fself[c], out);
-                    out = fmaf(fc, R, out);
+                    const float fn = fa != 0.f ? __ldg(a.f_n + ((size_t)c * a.Nu + k) * slab + p) : 0.f;
+                    const float out = rk_update(fself[c], fn, R, fa, fab, fc, fa != 0.f);
                     a.f_out[((size_t)c * a.Nu + k) * slab + p] = out;
                     outv[c] = out;
                 }
@@ -651,9 +647,7 @@ __global__ void __launch_bounds__(TmaGeom<Q, C>::NTHR, 2) k_stage_f32_tma(StageA
                     const float eqv = (c == 0) ? g32 : __fmul_rn(gfac, g32);
                     const float eqc = (c == 0) ? gc : __fmul_rn(gfac, gc);
                     const float R = fmaf(eqv - fi, itau, fmaf(eqc, itau, -div));
-                    float out = fab == 1.f ? fi : fab * fi;
-                    if (fa != 0.f) out = fmaf(fa, sc[fn_off] - fi, out);
-                    out = fmaf(fc, R, out);
+                    const float out = rk_update(fi, fa != 0.f ? sc[fn_off] : 0.f, R, fa, fab, fc, fa != 0.f);
                     a.f_out[((size_t)c * a.Nu + k) * slab + p] = out;
                     outv[c] = out;
                 }

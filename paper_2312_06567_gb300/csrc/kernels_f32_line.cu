@@ -527,9 +527,8 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                             const float2 F2 = make_float2(Fi[i], Fi[i + 1]), it2 = make_float2(itau[i], itau[i + 1]);
                             const float2 R = __ffma2_rn(sub2(eqv, F2), it2,
                                                         __ffma2_rn(eqc, it2, make_float2(-div[i], -div[i + 1])));
-                            float2 out = fab == 1.f ? F2 : __fmul2_rn(dup2(fab), F2);
-                            if (fa != 0.f) out = __ffma2_rn(dup2(fa), sub2(make_float2(FN[i], FN[i + 1]), F2), out);
-                            const float2 o = __ffma2_rn(dup2(fc), R, out);
+                            const float2 o = rk_update2(F2, fa != 0.f ? make_float2(FN[i], FN[i + 1]) : dup2(0.f), R, fa,
+                                                        fab, fc, fa != 0.f);
                             outv[c][i] = o.x; outv[c][i + 1] = o.y;
                         }
                     } else {
@@ -543,9 +542,7 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                         const float eqv = (c == 0) ? g32 : __fmul_rn(gfac[i], g32);
                         const float eqc = (c == 0) ? gc : __fmul_rn(gfac[i], gc);
                         const float R = fmaf(eqv - Fi[i], itau[i], fmaf(eqc, itau[i], -div[i]));
-                        float out = fab == 1.f ? Fi[i] : fab * Fi[i];
-                        if (fa != 0.f) out = fmaf(fa, FN[i] - Fi[i], out);
-                        outv[c][i] = fmaf(fc, R, out);
+                        outv[c][i] = rk_update(Fi[i], fa != 0.f ? FN[i] : 0.f, R, fa, fab, fc, fa != 0.f);
                     }
                     }
                     st_vec<NPT>(a.f_out + ((size_t)c * a.Nu + k) * slab + pb, outv[c]);
