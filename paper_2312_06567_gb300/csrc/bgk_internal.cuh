@@ -125,6 +125,15 @@ struct Eq32 {
         A12 = __fmul_rn((float)q[7], 2.f * s2); A13 = __fmul_rn((float)q[8], 2.f * s2);
         A23 = __fmul_rn((float)q[9], 2.f * s2);
     }
+    // the ten parameters in the order load() sets them (E0, V1..V3, A11..A23)
+    __device__ __forceinline__ void set(const float *v) {
+        E0 = v[0]; V1 = v[1]; V2 = v[2]; V3 = v[3];
+        A11 = v[4]; A22 = v[5]; A33 = v[6]; A12 = v[7]; A13 = v[8]; A23 = v[9];
+    }
+    __device__ __forceinline__ void get(float *v) const {
+        v[0] = E0; v[1] = V1; v[2] = V2; v[3] = V3;
+        v[4] = A11; v[5] = A22; v[6] = A33; v[7] = A12; v[8] = A13; v[9] = A23;
+    }
     // per first-axis line: the coefficient of c1 and the constant part
     __device__ __forceinline__ void line(float u2, float u3, float &lin, float &cst) const {
         const float c2 = __fsub_rn(u2, V2), c3 = __fsub_rn(u3, V3);

@@ -32,6 +32,8 @@
 // sums, and fits gamma so that g32 (1 + gamma . phi(ut)), phi = (1, ut,
 // |ut|^2/2), has exactly the moments of f: the discrete compatibility
 // condition then holds for the equilibrium actually used.
+#include <type_traits>
+
 #include "bgk_internal.cuh"
 
 namespace {
@@ -234,10 +236,11 @@ __device__ __forceinline__ void equilibrium_params(const PointState &ps, double 
 // low (optional): exact centred moments (sum w g, sum w g ut_d, sum w g |ut|^2/2)
 // of the equilibrium actually used, replacing the first three orders of M in
 // the residual and the Jacobian's leading terms.
-__device__ __forceinline__ double assemble(const double M[35], const PointState &ps, const GasInfo &gs,
+template <typename MT>
+__device__ __forceinline__ double assemble(const MT *M, const PointState &ps, const GasInfo &gs,
                                            const double x[5], const Sym3 &A, double R[5], double (*J)[5],
                                            const double *low = nullptr) {
-#define MM(p1, p2, p3) M[midx(p1, p2, p3)]
+#define MM(p1, p2, p3) ((double)M[midx(p1, p2, p3)])
     const double *U0 = ps.U0;
     const double hd = 0.5 * gs.delta;
     const double dl[3] = {x[1] - U0[0], x[2] - U0[1], x[3] - U0[2]};
@@ -418,48 +421,88 @@ __device__ __forceinline__ void plane_add(float &P, float &Pc, float c, float su
     Pc = fmaf(c, err, Pc);
 }
 
-// Exact index moments J_abc = sum c g32 jt1^a jt2^b jt3^c of the stage's FP32
-// equilibrium (jt = j - jc centred indices, c the trapezoid factors):
-// J000 J100 J200 J010 J020 J001 J002, reduced over the warp (every lane
-// returns them).  Lane l takes a contiguous run of lines; the line sums are
-// error-free (Sum2) sums of exact products, the lines of one plane
-// (j3 = const) accumulate as (sum, error) pairs with exact coefficients, and
-// the planes in FP64, so the result is accurate to O(2^-48) of the sums.
-__device__ __forceinline__ void correction_sums(const QPrimeArgs &a, int lane, double c0, const double x[5],
-                                                const Sym3 &A, const float *su1, double Jm[7]) {
-    const VelGrid &vg = a.vg;
-    const int n1 = vg.n[0], n2 = vg.n[1], n3 = vg.n[2];
-    const int jc[3] = {(n1 - 1) / 2, (n2 - 1) / 2, (n3 - 1) / 2};
+// The per-point FP32 parameters of the velocity passes, formed once per point
+// (by the lane that does the point's algebra) so the passes on the whole
+// warp run on the FP32 pipe only: the stage's equilibrium Eq32 (its ten
+// parameters, the same conversions as the stage's own record) and the
+// offsets U0_1, lo_2 - U0_2, lo_3 - U0_3 of the centred coordinates.
+constexpr int QEF = 13;
+__device__ __forceinline__ void point_eqf(const PointState &ps, double c0, const double x[5], const Sym3 &A,
+                                          const VelGrid &vg, float ef[QEF]) {
     const double qd[10] = {c0, x[1], x[2], x[3], A.t11, A.t22, A.t33, A.t12, A.t13, A.t23};
     Eq32 e32;
     e32.load(qd);
+    e32.get(ef);
+    ef[10] = (float)ps.U0[0];
+    ef[11] = (float)(vg.lo[1] - ps.U0[1]);
+    ef[12] = (float)(vg.lo[2] - ps.U0[2]);
+}
+
+// Error-free FP32 pairs (s + c) for the index moments of a whole velocity
+// grid: a plane's (sum, error) pairs times exact or exactly split weights
+// join the pair (TwoSum, TwoProd), so the moments stay accurate to O(2^-48)
+// without the FP64 pipe.
+__device__ __forceinline__ void pair_add(float &s, float &c, float v, float ve) {
+    const float t = __fadd_rn(s, v);
+    const float bp = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(e, ve));
+}
+// J pair k += w * (P + Pc), w exact in FP32 (a small integer or half of one)
+__device__ __forceinline__ void pair_axpy(float &s, float &c, float w, float P, float Pc) {
+    const float p = __fmul_rn(w, P);
+    pair_add(s, c, p, fmaf(w, Pc, fmaf(w, P, -p)));
+}
+// the plane j3's five plane pairs into the seven index-moment pairs
+// J000 J100 J200 J010 J020 J001 J002 (Js[k], Jc[k])
+__device__ __forceinline__ void plane_to_pairs(float (&Js)[7], float (&Jc)[7], float (&P)[5], float (&Pc)[5], int j3,
+                                               int n3, int jc3) {
+    const float c3 = (j3 == 0 || j3 == n3 - 1) ? 0.5f : 1.f, t3 = (float)(j3 - jc3);
+    const float w5 = __fmul_rn(c3, t3), w6 = __fmul_rn(w5, t3);       // exact
 #pragma unroll
-    for (int i = 0; i < 7; ++i) Jm[i] = 0.0;
+    for (int i = 0; i < 5; ++i) pair_axpy(Js[i], Jc[i], c3, P[i], Pc[i]);
+    pair_axpy(Js[5], Jc[5], w5, P[0], Pc[0]);
+    pair_axpy(Js[6], Jc[6], w6, P[0], Pc[0]);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) P[i] = Pc[i] = 0.f;
+}
+// sum of the seven pairs over the warp (every lane returns them)
+__device__ __forceinline__ void pair_warp_sum(float (&Js)[7], float (&Jc)[7]) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int i = 0; i < 7; ++i) {
+            const float s2 = __shfl_xor_sync(0xffffffffu, Js[i], o), c2 = __shfl_xor_sync(0xffffffffu, Jc[i], o);
+            pair_add(Js[i], Jc[i], s2, c2);
+        }
+    }
+}
+
+// Exact index moments J_abc = sum c g32 jt1^a jt2^b jt3^c of the stage's FP32
+// equilibrium (jt = j - jc centred indices, c the trapezoid factors):
+// J000 J100 J200 J010 J020 J001 J002 as (sum, error) pairs, reduced over the
+// warp (every lane returns them).  Lane l takes a contiguous run of lines;
+// the line sums are error-free (Sum2) sums of exact products, the lines of
+// one plane (j3 = const) accumulate as (sum, error) pairs with exact
+// coefficients, and the planes as error-free pairs, so s + c is accurate to
+// O(2^-48) of the sums.  ef: the point's parameters (point_eqf).
+__device__ __forceinline__ void correction_sums(const QPrimeArgs &a, int lane, const float *ef, const float *su1,
+                                                float (&Js)[7], float (&Jc)[7]) {
+    const VelGrid &vg = a.vg;
+    const int n1 = vg.n[0], n2 = vg.n[1], n3 = vg.n[2];
+    const int jc[3] = {(n1 - 1) / 2, (n2 - 1) / 2, (n3 - 1) / 2};
+    Eq32 e32;
+    e32.set(ef);
+#pragma unroll
+    for (int i = 0; i < 7; ++i) Js[i] = Jc[i] = 0.f;
     float P[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, Pc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     const int nl = n2 * n3, chunk = (nl + 31) / 32;
     const int l0 = min(nl, lane * chunk), l1 = min(nl, l0 + chunk);
     int j3cur = l0 < l1 ? l0 / n2 : -1;
-    // plane (j3) sums into the FP64 index moments (written out twice below,
-    // not as a lambda, so the pairs stay in registers)
-#define BGK_FLUSH_PLANE(J3)                                                                     \
-    do {                                                                                        \
-        const double c3 = ((J3) == 0 || (J3) == n3 - 1) ? 0.5 : 1.0, t3 = (double)((J3) - jc[2]); \
-        double Pd[5];                                                                           \
-        _Pragma("unroll") for (int i = 0; i < 5; ++i) {                                         \
-            Pd[i] = (double)P[i] + (double)Pc[i];                                               \
-            P[i] = Pc[i] = 0.f;                                                                 \
-        }                                                                                       \
-        Jm[0] = fma(c3, Pd[0], Jm[0]);                                                          \
-        Jm[1] = fma(c3, Pd[1], Jm[1]);                                                          \
-        Jm[2] = fma(c3, Pd[2], Jm[2]);                                                          \
-        Jm[3] = fma(c3, Pd[3], Jm[3]);                                                          \
-        Jm[4] = fma(c3, Pd[4], Jm[4]);                                                          \
-        Jm[5] = fma(c3 * t3, Pd[0], Jm[5]);                                                     \
-        Jm[6] = fma(c3 * t3 * t3, Pd[0], Jm[6]);                                                \
-    } while (0)
     for (int line = l0; line < l1; ++line) {
         const int j2 = line % n2, j3 = line / n2;
-        if (j3 != j3cur) { BGK_FLUSH_PLANE(j3cur); j3cur = j3; }
+        if (j3 != j3cur) { plane_to_pairs(Js, Jc, P, Pc, j3cur, n3, jc[2]); j3cur = j3; }
         const float4 *vl32 = a.vtab32 + (size_t)line * n1;
         float lin, cst;
         e32.line(vl32[0].y, vl32[0].z, lin, cst);
@@ -485,10 +528,14 @@ __device__ __forceinline__ void correction_sums(const QPrimeArgs &a, int lane, d
         plane_add(P[3], Pc[3], b, L0, C0);
         plane_add(P[4], Pc[4], bb, L0, C0);
     }
-    if (j3cur >= 0) BGK_FLUSH_PLANE(j3cur);
-#undef BGK_FLUSH_PLANE
+    if (j3cur >= 0) plane_to_pairs(Js, Jc, P, Pc, j3cur, n3, jc[2]);
+    pair_warp_sum(Js, Jc);
+}
+
+// the index moments in FP64 from their pairs
+__device__ __forceinline__ void pairs_to_jm(const float *Jp, double Jm[7]) {
 #pragma unroll
-    for (int i = 0; i < 7; ++i) Jm[i] = warp_sum(Jm[i]);
+    for (int k = 0; k < 7; ++k) Jm[k] = (double)Jp[2 * k] + (double)Jp[2 * k + 1];
 }
 
 // gamma from G gamma = T - S (one thread), with S the moments of g32 from the
@@ -513,8 +560,9 @@ __device__ __forceinline__ void exact_low_moments(const VelGrid &vg, const Point
     S[4] = 0.5 * W * s4;
 }
 
+template <typename MT>
 __device__ __forceinline__ void correction_fit(const QPrimeArgs &a, const PointState &ps, const double x[5],
-                                               const double Jm[7], const double Gsrc[35], double gam[5]) {
+                                               const double Jm[7], const MT *Gsrc, double gam[5]) {
     double S[5];
     exact_low_moments(a.vg, ps, Jm, S);
     // targets: the centred moments of f, with the G equilibrium's share of
@@ -528,7 +576,7 @@ __device__ __forceinline__ void correction_fit(const QPrimeArgs &a, const PointS
     T[3] = m[3] - ps.U0[2] * m[0];
     T[4] = ps.Eth - gfac * m[0];
     // G_ij = sum w phi_i phi_j g from the solve's moments (accuracy not critical)
-#define MM(p1, p2, p3) Gsrc[midx(p1, p2, p3)]
+#define MM(p1, p2, p3) ((double)Gsrc[midx(p1, p2, p3)])
     double Gm[5][5];
     Gm[0][0] = MM(0, 0, 0);
     Gm[0][1] = MM(1, 0, 0); Gm[0][2] = MM(0, 1, 0); Gm[0][3] = MM(0, 0, 1);
@@ -724,10 +772,10 @@ struct Engine64 {
 
 // FP32: same walk in FP32, monomials formed on the fly (no table), anchors
 // from the FP32 exp2 unit; the 35 moments accumulate in FP32 per lane and
-// are reduced across the warp in FP64.
+// are reduced across the warp in FP32 (every lane returns them).
 struct Engine32 {
     __device__ void moments(const VelGrid &vg, const PointState &ps, const double x[5], const Sym3 &Ad, double c0d,
-                            int lane, double Md[35]) const {
+                            int lane, float (&Mo)[35]) const {
         const int n1 = vg.n[0], n2 = vg.n[1], n3 = vg.n[2];
         const float h1 = (float)vg.h[0];
         const float s1 = (float)(vg.lo[0] - ps.U0[0]);
@@ -789,7 +837,7 @@ struct Engine32 {
         // the lane partials carry FP32 rounding already; the tree sum in FP32
         // keeps the reduction off the FP64 pipe
 #pragma unroll
-        for (int i = 0; i < 35; ++i) Md[i] = (double)warp_sumf(M[i]);
+        for (int i = 0; i < 35; ++i) Mo[i] = warp_sumf(M[i]);
     }
 };
 
@@ -799,49 +847,31 @@ struct Engine32 {
 // correction_sums), which give the exact discrete moments of g32 and so the
 // residual of the equilibrium actually used, and (b) into plain FP32 line
 // sums T_m = sum_j1 w1 g32 ut1^m, m <= 4, folded per line into the 35 centred
-// moments (as in Engine32) for the Jacobian and the correction's G.
-__device__ __forceinline__ void fused_pass(const QPrimeArgs &a, int lane, const PointState &ps, double c0,
-                                           const double x[5], const Sym3 &A, const float *su1, double Md[35],
-                                           double Jm[7]) {
+// moments (as in Engine32) for the Jacobian and the correction's G.  All on
+// the FP32 pipe; every lane returns the moments M (FP32 sums) and the index
+// moment pairs.
+__device__ __forceinline__ void fused_pass(const QPrimeArgs &a, int lane, const float *ef, const float *su1,
+                                           float (&M)[35], float (&Js)[7], float (&Jc)[7]) {
     const VelGrid &vg = a.vg;
     const int n1 = vg.n[0], n2 = vg.n[1], n3 = vg.n[2];
     const int jc[3] = {(n1 - 1) / 2, (n2 - 1) / 2, (n3 - 1) / 2};
-    const double qd[10] = {c0, x[1], x[2], x[3], A.t11, A.t22, A.t33, A.t12, A.t13, A.t23};
     Eq32 e32;
-    e32.load(qd);
-    const float U0x = (float)ps.U0[0];
+    e32.set(ef);
+    const float U0x = ef[10], o2 = ef[11], o3 = ef[12];
     const float h1 = (float)vg.h[0], h2 = (float)vg.h[1], h3 = (float)vg.h[2];
-    const float o2 = (float)(vg.lo[1] - ps.U0[1]), o3 = (float)(vg.lo[2] - ps.U0[2]);
-    float M[35];
 #pragma unroll
     for (int i = 0; i < 35; ++i) M[i] = 0.f;
 #pragma unroll
-    for (int i = 0; i < 7; ++i) Jm[i] = 0.0;
+    for (int i = 0; i < 7; ++i) Js[i] = Jc[i] = 0.f;
     float P[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, Pc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     const int nl = n2 * n3, chunk = (nl + 31) / 32;
     const int l0 = min(nl, lane * chunk), l1 = min(nl, l0 + chunk);
     int j3cur = l0 < l1 ? l0 / n2 : -1;
-#define BGK_FLUSH_PLANE(J3)                                                                     \
-    do {                                                                                        \
-        const double c3 = ((J3) == 0 || (J3) == n3 - 1) ? 0.5 : 1.0, t3 = (double)((J3) - jc[2]); \
-        double Pd[5];                                                                           \
-        _Pragma("unroll") for (int i = 0; i < 5; ++i) {                                         \
-            Pd[i] = (double)P[i] + (double)Pc[i];                                               \
-            P[i] = Pc[i] = 0.f;                                                                 \
-        }                                                                                       \
-        Jm[0] = fma(c3, Pd[0], Jm[0]);                                                          \
-        Jm[1] = fma(c3, Pd[1], Jm[1]);                                                          \
-        Jm[2] = fma(c3, Pd[2], Jm[2]);                                                          \
-        Jm[3] = fma(c3, Pd[3], Jm[3]);                                                          \
-        Jm[4] = fma(c3, Pd[4], Jm[4]);                                                          \
-        Jm[5] = fma(c3 * t3, Pd[0], Jm[5]);                                                     \
-        Jm[6] = fma(c3 * t3 * t3, Pd[0], Jm[6]);                                                \
-    } while (0)
     // the end of a line: its error-free sums into the plane pairs (in line
     // order, flushing finished planes) and its Jacobian sums into the moments
     auto end_line = [&](int line, float L0, float C0, float L1, float C1, float L2, float C2, const float (&Tm)[5]) {
         const int j2 = line % n2, j3 = line / n2;
-        if (j3 != j3cur) { BGK_FLUSH_PLANE(j3cur); j3cur = j3; }
+        if (j3 != j3cur) { plane_to_pairs(Js, Jc, P, Pc, j3cur, n3, jc[2]); j3cur = j3; }
         const float c2 = trapf(j2, n2), jt2 = (float)(j2 - jc[1]);
         const float b = __fmul_rn(c2, jt2), bb = __fmul_rn(b, jt2);                  // exact
         plane_add(P[0], Pc[0], c2, L0, C0);
@@ -911,12 +941,10 @@ __device__ __forceinline__ void fused_pass(const QPrimeArgs &a, int lane, const 
             end_line(line + 1, L0.y, C0.y, L1.y, C1.y, L2.y, C2.y, Tm);
         }
     }
-    if (j3cur >= 0) BGK_FLUSH_PLANE(j3cur);
-#undef BGK_FLUSH_PLANE
+    if (j3cur >= 0) plane_to_pairs(Js, Jc, P, Pc, j3cur, n3, jc[2]);
+    pair_warp_sum(Js, Jc);
 #pragma unroll
-    for (int i = 0; i < 7; ++i) Jm[i] = warp_sum(Jm[i]);
-#pragma unroll
-    for (int i = 0; i < 35; ++i) Md[i] = (double)warp_sumf(M[i]);
+    for (int i = 0; i < 35; ++i) M[i] = warp_sumf(M[i]);
 }
 
 // One block solves a batch of QB points.  The velocity sums run one warp per
@@ -926,14 +954,17 @@ __device__ __forceinline__ void fused_pass(const QPrimeArgs &a, int lane, const 
 constexpr int QB = 32;
 constexpr int QW = 8;
 
+template <bool F32>
 struct QPShared {
+    using MT = typename std::conditional<F32, float, double>::type;
     PointState ps[QB];
     double x[QB][5];
     double A[QB][6];
     double c0[QB];
     double res[QB];
-    double M[QB][35];
-    double Jm[QB][7];
+    MT M[QB][35];            // the velocity pass's moments (FP32 sums with the FP32 engine)
+    float Jp[QB][14];        // exact index moments of g32 as (sum, error) pairs
+    float ef[QB][QEF];       // the FP32 pass parameters (point_eqf)
     int it[QB], tot[QB];
     int conv[QB], from_guess[QB], active[QB];
     int fused[QB];           // next evaluation by the fused pass (FP32-sum engine)
@@ -945,7 +976,7 @@ __device__ __forceinline__ Sym3 load_sym3(const double *t) { return Sym3{t[0], t
 
 template <bool F32>
 __global__ void __launch_bounds__(QB * QW, 2) k_qprime(QPrimeArgs a) {
-    __shared__ QPShared S;
+    __shared__ QPShared<F32> S;
     __shared__ float su1[BGK_MAXV];          // u1 of the first-axis velocity nodes (the same on every line)
     extern __shared__ double dyn_tab[];      // FP64 engine: [QW][n1][5] tables w1 ut1^m
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -985,34 +1016,44 @@ __global__ void __launch_bounds__(QB * QW, 2) k_qprime(QPrimeArgs a) {
             S.A[lane][0] = A.t11; S.A[lane][1] = A.t22; S.A[lane][2] = A.t33;
             S.A[lane][3] = A.t12; S.A[lane][4] = A.t13; S.A[lane][5] = A.t23;
             S.c0[lane] = c0;
+            if (F32 && S.fused[lane]) point_eqf(S.ps[lane], c0, S.x[lane], A, a.vg, S.ef[lane]);
         }
         __syncthreads();
         for (int i = wib; i < nb; i += QW) {
             if (!S.active[i]) continue;
-            const Sym3 A = load_sym3(S.A[i]);
-            double x[5];
+            if constexpr (F32) {
+                float M[35];
+                if (S.fused[i]) {
+                    float Js[7], Jc[7];
+                    fused_pass(a, lane, S.ef[i], su1, M, Js, Jc);
+                    if (lane == 0) {
 #pragma unroll
-            for (int j = 0; j < 5; ++j) x[j] = S.x[i][j];
-            double M[35];
-            if (F32 && S.fused[i]) {
-                double Jm[7];
-                fused_pass(a, lane, S.ps[i], S.c0[i], x, A, su1, M, Jm);
+                        for (int j = 0; j < 7; ++j) { S.Jp[i][2 * j] = Js[j]; S.Jp[i][2 * j + 1] = Jc[j]; }
+                    }
+                } else {
+                    double x[5];
+#pragma unroll
+                    for (int j = 0; j < 5; ++j) x[j] = S.x[i][j];
+                    Engine32 e32;
+                    e32.moments(a.vg, S.ps[i], x, load_sym3(S.A[i]), S.c0[i], lane, M);
+                }
                 if (lane == 0) {
 #pragma unroll
-                    for (int j = 0; j < 7; ++j) S.Jm[i][j] = Jm[j];
+                    for (int j = 0; j < 35; ++j) S.M[i][j] = M[j];
+                    S.exact[i] = S.fused[i];
                 }
-            } else if (F32) {
-                Engine32 e32;
-                e32.moments(a.vg, S.ps[i], x, A, S.c0[i], lane, M);
             } else {
+                double x[5], M[35];
+#pragma unroll
+                for (int j = 0; j < 5; ++j) x[j] = S.x[i][j];
                 Engine64 e64;
                 e64.init(reinterpret_cast<double (*)[5]>(dyn_tab + (size_t)wib * a.vg.n[0] * 5), a.vg, S.ps[i], lane);
-                e64.moments(a.vg, S.ps[i], x, A, S.c0[i], lane, M);
-            }
-            if (lane == 0) {
+                e64.moments(a.vg, S.ps[i], x, load_sym3(S.A[i]), S.c0[i], lane, M);
+                if (lane == 0) {
 #pragma unroll
-                for (int j = 0; j < 35; ++j) S.M[i][j] = M[j];
-                S.exact[i] = F32 && S.fused[i];
+                    for (int j = 0; j < 35; ++j) S.M[i][j] = M[j];
+                    S.exact[i] = 0;
+                }
             }
             __syncwarp();
         }
@@ -1027,7 +1068,11 @@ __global__ void __launch_bounds__(QB * QW, 2) k_qprime(QPrimeArgs a) {
                 const Sym3 A = load_sym3(S.A[lane]);
                 double R[5], J[5][5], low[5];
                 const bool ex = S.exact[lane];
-                if (ex) exact_low_moments(a.vg, ps, S.Jm[lane], low);
+                if (ex) {
+                    double Jm[7];
+                    pairs_to_jm(S.Jp[lane], Jm);
+                    exact_low_moments(a.vg, ps, Jm, low);
+                }
                 // the residual first; the Jacobian only if an update may follow
                 const double res = assemble(S.M[lane], ps, a.gas, x, A, R, nullptr, ex ? low : nullptr);
                 // The exact residual of the mixed form measures the stage's FP32
@@ -1083,15 +1128,17 @@ __global__ void __launch_bounds__(QB * QW, 2) k_qprime(QPrimeArgs a) {
     // -- mixed form: exact moments of the stage's FP32 equilibrium, one warp per point
     const bool fit = a.mixed && a.eq;
     if (fit) {
+        // the parameters of the equilibrium the stage will use (the final x)
+        if (wib == 0 && lane < nb && !S.exact[lane])
+            point_eqf(S.ps[lane], S.c0[lane], S.x[lane], load_sym3(S.A[lane]), a.vg, S.ef[lane]);
+        __syncthreads();
         for (int i = wib; i < nb; i += QW) {
             if (S.exact[i]) continue;            // the fused pass measured them already
-            double x[5], Jm[7];
-#pragma unroll
-            for (int j = 0; j < 5; ++j) x[j] = S.x[i][j];
-            correction_sums(a, lane, S.c0[i], x, load_sym3(S.A[i]), su1, Jm);
+            float Js[7], Jc[7];
+            correction_sums(a, lane, S.ef[i], su1, Js, Jc);
             if (lane == 0) {
 #pragma unroll
-                for (int j = 0; j < 7; ++j) S.Jm[i][j] = Jm[j];
+                for (int j = 0; j < 7; ++j) { S.Jp[i][2 * j] = Js[j]; S.Jp[i][2 * j + 1] = Jc[j]; }
             }
         }
         __syncthreads();
@@ -1103,7 +1150,11 @@ __global__ void __launch_bounds__(QB * QW, 2) k_qprime(QPrimeArgs a) {
         double x[5], gam[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll
         for (int j = 0; j < 5; ++j) x[j] = S.x[i][j];
-        if (fit && valid) correction_fit(a, S.ps[i], x, S.Jm[i], S.M[i], gam);
+        if (fit && valid) {
+            double Jm[7];
+            pairs_to_jm(S.Jp[i], Jm);
+            correction_fit(a, S.ps[i], x, Jm, S.M[i], gam);
+        }
         point_epilogue(a, p0 + i, valid, S.ps[i], x, load_sym3(S.A[i]), S.c0[i], gam, S.tot[i], S.conv[i] != 0,
                        S.res[i]);
     }
@@ -1249,7 +1300,10 @@ __global__ void __launch_bounds__(QW * 32) k_qprime_tensor(QPrimeArgs a) {
         double M[35];
         if (F32) {
             Engine32 e32;
-            e32.moments(a.vg, ps, x, A, pr[0], lane, M);
+            float Mf[35];
+            e32.moments(a.vg, ps, x, A, pr[0], lane, Mf);
+#pragma unroll
+            for (int j = 0; j < 35; ++j) M[j] = Mf[j];
         } else {
             e64.moments(a.vg, ps, x, A, pr[0], lane, M);
         }
@@ -1328,8 +1382,13 @@ __global__ void __launch_bounds__(QW * 32) k_qprime_tensor(QPrimeArgs a) {
     x[4] = (T.t11 + T.t22 + T.t33) / 3.0;
     double gam[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     if (a.mixed && a.eq) {
+        float ef[QEF], Js[7], Jc[7], Jp[14];
+        point_eqf(ps, pr[0], x, A, a.vg, ef);
+        correction_sums(a, lane, ef, su1, Js, Jc);
+#pragma unroll
+        for (int j = 0; j < 7; ++j) { Jp[2 * j] = Js[j]; Jp[2 * j + 1] = Jc[j]; }
         double Jm[7];
-        correction_sums(a, lane, pr[0], x, A, su1, Jm);
+        pairs_to_jm(Jp, Jm);
         if (lane == 0) correction_fit(a, ps, x, Jm, S.M[wib], gam);
     }
     const int tot = __shfl_sync(0xffffffffu, it, 0);
