@@ -231,8 +231,16 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
     unsigned long long *bars = reinterpret_cast<unsigned long long *>(Psm + NPT * 2 * NQ * NCT);
     unsigned int *rel = reinterpret_cast<unsigned int *>(bars + 2 * S);
     unsigned int *fills = rel + S;
-    __shared__ float sD[2][Q][Q];
-    __shared__ float sdg[2][Q], seps[2][Q], slam[2][Q], sdlam[2];
+    __shared__ __align__(16) float sD[2][Q][Q];
+    __shared__ __align__(16) float sdg[2][Q];
+    __shared__ __align__(16) float seps[2][Q];
+    __shared__ __align__(16) float slam[2][Q];
+    __shared__ float sdlam[2];
+    // the same entries arranged for whole-row vector loads: sDr[side][n][m] =
+    // sD[side][n][(n + m) mod Q] (row n in the canonical order from n), and
+    // sCf[side][n] = (dlam, dg_n, eps_n, 0)
+    __shared__ __align__(16) float sDr[2][Q][Q];
+    __shared__ float4 sCf[2][Q];
     __shared__ float su1[BGK_MAXV];                      // u1 of the first-axis nodes (the same on every line)
     __shared__ unsigned int s_exited;
     constexpr int NW = LG::NW;
@@ -260,6 +268,15 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
     }
     for (int j = tid; j < vn1; j += blockDim.x) su1[j] = __ldg(a.vtab32 + j).x;
     load_ops_f32<Q>(a.fr, tid, sD, sdg, seps, slam, sdlam);
+    __syncthreads();
+    if (tid < 2 * Q * Q) {
+        const int side = tid / (Q * Q), n = (tid / Q) % Q, m = tid % Q;
+        sDr[side][n][m] = sD[side][n][(n + m) % Q];
+    }
+    if (tid < 2 * Q) {
+        const int side = tid / Q, n = tid % Q;
+        sCf[side][n] = make_float4(sdlam[side], sdg[side][n], seps[side][n], 0.f);
+    }
     __syncthreads();
 
     // ---- consumers: thread = (element l of the run, node line r = jy + Q kz, part h of the line) ----
@@ -400,11 +417,13 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                                 for (int j = i + 1; j < Q; ++j) dv[i][j] = F[j] - F[i];
 #pragma unroll
                             for (int i = 0; i < NPT; ++i) {
+                                float Dr[Q];
+                                ld_vec<Q>(&sD[sx][i][0], Dr);
                                 t[i] = 0.f;
 #pragma unroll
                                 for (int m = 1; m < Q; ++m) {
                                     const int j = (i + m) % Q;      // the canonical order
-                                    t[i] = fmaf(sD[sx][i][j], j > i ? dv[i][j] : -dv[j][i], t[i]);
+                                    t[i] = fmaf(Dr[j], j > i ? dv[i][j] : -dv[j][i], t[i]);
                                 }
                             }
                         } else {
@@ -427,40 +446,50 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                         if (!BC || !((bcm >> sx) & 1)) {
                             float NB[Q];
                             ld_vec<Q>(sc + own_off + (sx ? NS : -NS) + ln, NB);
+                            float Lr[Q];
+                            ld_vec<Q>(&slam[sx][0], Lr);
                             scale_vec<NPT>(dn, sdlam[sx], Fi);
 #pragma unroll
                             for (int j = 0; j < Q; ++j) {
                                 float NBj[NPT];
 #pragma unroll
                                 for (int i = 0; i < NPT; ++i) NBj[i] = NB[j];
-                                acc_dev<NPT>(dn, slam[sx][j], NBj, nFi);
+                                acc_dev<NPT>(dn, Lr[j], NBj, nFi);
                             }
                         } else {
                             const float bv = (float)__ldg(a.bcval + ((size_t)(0 + sx) * C + c) * a.Nu + k);
 #pragma unroll
                             for (int i = 0; i < NPT; ++i) dn[i] = bv - Fi[i];
                         }
-                        lift_vec<NPT>(t, &sdg[sx][i0], &seps[sx][i0], dn, Fi, toh0 * u1, div, true);
+                        float Gr[NPT], Er[NPT];
+                        ld_vec<NPT>(&sdg[sx][i0], Gr);
+                        ld_vec<NPT>(&seps[sx][i0], Er);
+                        lift_vec<NPT>(t, Gr, Er, dn, Fi, toh0 * u1, div, true);
                     }
                     // ---- second direction: lines (j', kz) of the element and of the upwind y element
                     {
                         float t[NPT], dn[NPT];
 #pragma unroll
                         for (int i = 0; i < NPT; ++i) t[i] = 0.f;
+                        float Dr[Q];
+                        ld_vec<Q>(&sDr[sy][jy][0], Dr);
+                        const float4 cf = sCf[sy][jy];
 #pragma unroll
                         for (int m = 1; m < Q; ++m) {
                             const int jp = (jy + m) & (Q - 1);       // the canonical order
                             float Gv[NPT];
                             ld_vec<NPT>(sc + own_off + Q * (jp + Q * kz) + i0, Gv);
-                            acc_dev<NPT>(t, sD[sy][jy][jp], Gv, nFi);
+                            acc_dev<NPT>(t, Dr[m], Gv, nFi);
                         }
                         if (!BC || !((bcm >> (2 + sy)) & 1)) {
-                            scale_vec<NPT>(dn, sdlam[sy], Fi);
+                            float Lr[Q];
+                            ld_vec<Q>(&slam[sy][0], Lr);
+                            scale_vec<NPT>(dn, cf.x, Fi);
 #pragma unroll
                             for (int jp = 0; jp < Q; ++jp) {
                                 float H[NPT];
                                 ld_vec<NPT>(sc + (SLOTS + l) * NS + Q * (jp + Q * kz) + i0, H);
-                                acc_dev<NPT>(dn, slam[sy][jp], H, nFi);
+                                acc_dev<NPT>(dn, Lr[jp], H, nFi);
                             }
                         } else {
                             const float bv = (float)__ldg(a.bcval + ((size_t)(2 + sy) * C + c) * a.Nu + k);
@@ -469,7 +498,7 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                         }
                         float dgv[NPT], epv[NPT];
 #pragma unroll
-                        for (int i = 0; i < NPT; ++i) { dgv[i] = sdg[sy][jy]; epv[i] = seps[sy][jy]; }
+                        for (int i = 0; i < NPT; ++i) { dgv[i] = cf.y; epv[i] = cf.z; }
                         lift_vec<NPT>(t, dgv, epv, dn, Fi, toh1 * u2, div, false);
                     }
                     // ---- third direction: lines (jy, k') of the element and of the upwind z element
@@ -477,20 +506,25 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                         float t[NPT], dn[NPT];
 #pragma unroll
                         for (int i = 0; i < NPT; ++i) t[i] = 0.f;
+                        float Dr[Q];
+                        ld_vec<Q>(&sDr[sz][kz][0], Dr);
+                        const float4 cf = sCf[sz][kz];
 #pragma unroll
                         for (int m = 1; m < Q; ++m) {
                             const int kp = (kz + m) & (Q - 1);       // the canonical order
                             float Gv[NPT];
                             ld_vec<NPT>(sc + own_off + Q * (jy + Q * kp) + i0, Gv);
-                            acc_dev<NPT>(t, sD[sz][kz][kp], Gv, nFi);
+                            acc_dev<NPT>(t, Dr[m], Gv, nFi);
                         }
                         if (!BC || !((bcm >> (4 + sz)) & 1)) {
-                            scale_vec<NPT>(dn, sdlam[sz], Fi);
+                            float Lr[Q];
+                            ld_vec<Q>(&slam[sz][0], Lr);
+                            scale_vec<NPT>(dn, cf.x, Fi);
 #pragma unroll
                             for (int kp = 0; kp < Q; ++kp) {
                                 float H[NPT];
                                 ld_vec<NPT>(sc + (SLOTS + EB + l) * NS + Q * (jy + Q * kp) + i0, H);
-                                acc_dev<NPT>(dn, slam[sz][kp], H, nFi);
+                                acc_dev<NPT>(dn, Lr[kp], H, nFi);
                             }
                         } else {
                             const float bv = (float)__ldg(a.bcval + ((size_t)(4 + sz) * C + c) * a.Nu + k);
@@ -499,7 +533,7 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                         }
                         float dgv[NPT], epv[NPT];
 #pragma unroll
-                        for (int i = 0; i < NPT; ++i) { dgv[i] = sdg[sz][kz]; epv[i] = seps[sz][kz]; }
+                        for (int i = 0; i < NPT; ++i) { dgv[i] = cf.y; epv[i] = cf.z; }
                         lift_vec<NPT>(t, dgv, epv, dn, Fi, toh2 * u3, div, false);
                     }
                     // ---- equilibrium, source and Runge--Kutta update
