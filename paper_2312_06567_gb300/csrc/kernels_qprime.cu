@@ -426,7 +426,7 @@ __device__ __forceinline__ void plane_add(float &P, float &Pc, float c, float su
 // warp run on the FP32 pipe only: the stage's equilibrium Eq32 (its ten
 // parameters, the same conversions as the stage's own record) and the
 // offsets U0_1, lo_2 - U0_2, lo_3 - U0_3 of the centred coordinates.
-constexpr int QEF = 13;
+constexpr int QEF = 14;
 __device__ __forceinline__ void point_eqf(const PointState &ps, double c0, const double x[5], const Sym3 &A,
                                           const VelGrid &vg, float ef[QEF]) {
     const double qd[10] = {c0, x[1], x[2], x[3], A.t11, A.t22, A.t33, A.t12, A.t13, A.t23};
@@ -436,6 +436,7 @@ __device__ __forceinline__ void point_eqf(const PointState &ps, double c0, const
     ef[10] = (float)ps.U0[0];
     ef[11] = (float)(vg.lo[1] - ps.U0[1]);
     ef[12] = (float)(vg.lo[2] - ps.U0[2]);
+    ef[13] = (float)(vg.lo[0] + ((vg.n[0] - 1) / 2) * vg.h[0] - ps.U0[0]);   // centre of the first axis - U0_1
 }
 
 // Error-free FP32 pairs (s + c) for the index moments of a whole velocity
@@ -479,6 +480,32 @@ __device__ __forceinline__ void pair_warp_sum(float (&Js)[7], float (&Jc)[7]) {
     }
 }
 
+// The error-free line sums of a velocity line without products in the
+// walk: with A_k = sum_{j<=k} c g_j, B_k = sum_{m<=k} A_m, C_k = sum_{m<=k} B_m
+// (error-free pair sums, taken in index order), at the line's end
+//   sum_j c g_j            = A
+//   sum_j (n - j) c g_j    = B
+//   sum_j (n - j)^2 c g_j  = 2 C - B,
+// so with jt = j - jc = K - (n - j), K = n - jc:
+//   L1 = sum jt c g   = K A - B
+//   L2 = sum jt^2 c g = K^2 A - (2K + 1) B + 2 C.
+// The integer weights are exact in FP32 and each product joins its pair with
+// its exact error, so L1 and L2 are accurate to O(2^-48) of the largest term.
+__device__ __forceinline__ void pair_wadd(float &s, float &c, float w, float vs, float vc) {
+    const float p = __fmul_rn(w, vs);
+    pair_add(s, c, p, fmaf(w, vc, fmaf(w, vs, -p)));
+}
+__device__ __forceinline__ void line_sums_from_prefix(float K, float As, float Ac, float Bs, float Bc, float Cs,
+                                                      float Cc, float &L1, float &C1, float &L2, float &C2) {
+    L1 = 0.f; C1 = 0.f;
+    pair_wadd(L1, C1, K, As, Ac);
+    pair_wadd(L1, C1, -1.f, Bs, Bc);
+    L2 = 0.f; C2 = 0.f;
+    pair_wadd(L2, C2, __fmul_rn(K, K), As, Ac);
+    pair_wadd(L2, C2, -fmaf(2.f, K, 1.f), Bs, Bc);
+    pair_wadd(L2, C2, 2.f, Cs, Cc);
+}
+
 // Exact index moments J_abc = sum c g32 jt1^a jt2^b jt3^c of the stage's FP32
 // equilibrium (jt = j - jc centred indices, c the trapezoid factors):
 // J000 J100 J200 J010 J020 J001 J002 as (sum, error) pairs, reduced over the
@@ -506,20 +533,18 @@ __device__ __forceinline__ void correction_sums(const QPrimeArgs &a, int lane, c
         const float4 *vl32 = a.vtab32 + (size_t)line * n1;
         float lin, cst;
         e32.line(vl32[0].y, vl32[0].z, lin, cst);
-        float L0 = 0.f, C0 = 0.f, L1 = 0.f, C1 = 0.f, L2 = 0.f, C2 = 0.f;
-        float jt = (float)(-jc[0]);
-        for (int j1 = 0; j1 < n1; ++j1, jt += 1.f) {
+        float L0 = 0.f, C0 = 0.f, Bs = 0.f, Bc = 0.f, Cs = 0.f, Cc = 0.f;
+        for (int j1 = 0; j1 < n1; ++j1) {
             const float g = e32.g(su1[j1], lin, cst);
             const float cg = (j1 == 0 || j1 == n1 - 1) ? __fmul_rn(0.5f, g) : g;     // exact
             sum2(L0, C0, cg);
-            const float p1 = __fmul_rn(cg, jt);
-            sum2(L1, C1, p1);
-            C1 = __fadd_rn(C1, fmaf(cg, jt, -p1));                          // exact product error
-            const float jj = __fmul_rn(jt, jt);                             // exact
-            const float p2 = __fmul_rn(cg, jj);
-            sum2(L2, C2, p2);
-            C2 = __fadd_rn(C2, fmaf(cg, jj, -p2));
+            sum2(Bs, Bc, L0);
+            Bc = __fadd_rn(Bc, C0);
+            sum2(Cs, Cc, Bs);
+            Cc = __fadd_rn(Cc, Bc);
         }
+        float L1, C1, L2, C2;
+        line_sums_from_prefix((float)(n1 - jc[0]), L0, C0, Bs, Bc, Cs, Cc, L1, C1, L2, C2);
         const float c2 = trapf(j2, n2), t2 = (float)(j2 - jc[1]);
         const float b = __fmul_rn(c2, t2), bb = __fmul_rn(b, t2);                  // exact
         plane_add(P[0], Pc[0], c2, L0, C0);
@@ -857,8 +882,9 @@ __device__ __forceinline__ void fused_pass(const QPrimeArgs &a, int lane, const 
     const int jc[3] = {(n1 - 1) / 2, (n2 - 1) / 2, (n3 - 1) / 2};
     Eq32 e32;
     e32.set(ef);
-    const float U0x = ef[10], o2 = ef[11], o3 = ef[12];
+    const float U0x = ef[10], o2 = ef[11], o3 = ef[12], dlt = ef[13];
     const float h1 = (float)vg.h[0], h2 = (float)vg.h[1], h3 = (float)vg.h[2];
+    const float K = (float)(n1 - jc[0]);
 #pragma unroll
     for (int i = 0; i < 35; ++i) M[i] = 0.f;
 #pragma unroll
@@ -869,7 +895,12 @@ __device__ __forceinline__ void fused_pass(const QPrimeArgs &a, int lane, const 
     int j3cur = l0 < l1 ? l0 / n2 : -1;
     // the end of a line: its error-free sums into the plane pairs (in line
     // order, flushing finished planes) and its Jacobian sums into the moments
-    auto end_line = [&](int line, float L0, float C0, float L1, float C1, float L2, float C2, const float (&Tm)[5]) {
+    auto end_line = [&](int line, float L0, float C0, float L1, float C1, float L2, float C2, float T3, float T4) {
+        // the Jacobian line sums of order <= 2 from the exact index sums:
+        // ut = u1 - U0_1 = dlt + h1 jt on the grid
+        const float S0 = __fadd_rn(L0, C0), S1 = __fadd_rn(L1, C1), S2 = __fadd_rn(L2, C2);
+        const float Tm[5] = {S0, fmaf(h1, S1, dlt * S0), fmaf(h1 * h1, S2, fmaf(2.f * dlt * h1, S1, dlt * dlt * S0)),
+                             T3, T4};
         const int j2 = line % n2, j3 = line / n2;
         if (j3 != j3cur) { plane_to_pairs(Js, Jc, P, Pc, j3cur, n3, jc[2]); j3cur = j3; }
         const float c2 = trapf(j2, n2), jt2 = (float)(j2 - jc[1]);
@@ -908,37 +939,35 @@ __device__ __forceinline__ void fused_pass(const QPrimeArgs &a, int lane, const 
         if (two) e32.line(vl32[n1].y, vl32[n1].z, linB, cstB);
         const float2 lin2 = make_float2(linA, linB), cst2 = make_float2(cstA, cstB);
         const float2 A11 = qdup2(e32.A11), E0 = qdup2(e32.E0);
-        float2 L0 = qdup2(0.f), C0 = L0, L1 = L0, C1 = L0, L2 = L0, C2 = L0;
-        float2 T0 = L0, T1 = L0, T2 = L0, T3 = L0, T4 = L0;
-        float jt = (float)(-jc[0]);
-        for (int j1 = 0; j1 < n1; ++j1, jt += 1.f) {
+        // error-free prefix sums A (= L0), B, C of the line (line_sums_from_prefix)
+        float2 L0 = qdup2(0.f), C0 = L0, Bs = L0, Bc = L0, Cs = L0, Cc = L0;
+        float2 T3 = L0, T4 = L0;
+        for (int j1 = 0; j1 < n1; ++j1) {
             const float u1 = su1[j1];
             const float2 c1 = qdup2(__fsub_rn(u1, e32.V1));
             const float2 ex = __ffma2_rn(c1, __ffma2_rn(A11, c1, lin2), cst2);
             const float2 g = __fmul2_rn(E0, make_float2(Eq32::ex2(ex.x), Eq32::ex2(ex.y)));
             const float2 cg = (j1 == 0 || j1 == n1 - 1) ? __fmul2_rn(qdup2(0.5f), g) : g;     // exact
             qsum2x2(L0, C0, cg);
-            const float2 jtv = qdup2(jt);
-            const float2 p1 = __fmul2_rn(cg, jtv);
-            qsum2x2(L1, C1, p1);
-            C1 = __fadd2_rn(C1, __ffma2_rn(cg, jtv, qneg2(p1)));
-            const float2 jj = qdup2(__fmul_rn(jt, jt));
-            const float2 p2 = __fmul2_rn(cg, jj);
-            qsum2x2(L2, C2, p2);
-            C2 = __fadd2_rn(C2, __ffma2_rn(cg, jj, qneg2(p2)));
-            // Jacobian line sums (plain FP32)
-            const float2 ut = qdup2(u1 - U0x);
-            const float2 t1 = __fmul2_rn(cg, ut), t2 = __fmul2_rn(t1, ut), t3 = __fmul2_rn(t2, ut);
-            T0 = __fadd2_rn(T0, cg); T1 = __fadd2_rn(T1, t1); T2 = __fadd2_rn(T2, t2); T3 = __fadd2_rn(T3, t3);
-            T4 = __ffma2_rn(t3, ut, T4);
+            qsum2x2(Bs, Bc, L0);
+            Bc = __fadd2_rn(Bc, C0);
+            qsum2x2(Cs, Cc, Bs);
+            Cc = __fadd2_rn(Cc, Bc);
+            // Jacobian line sums of order 3 and 4 (plain FP32)
+            const float ut = __fsub_rn(u1, U0x), ut3 = ut * ut * ut;
+            const float2 t3 = __fmul2_rn(cg, qdup2(ut3));
+            T3 = __fadd2_rn(T3, t3);
+            T4 = __ffma2_rn(t3, qdup2(ut), T4);
         }
         {
-            const float Tm[5] = {T0.x, T1.x, T2.x, T3.x, T4.x};
-            end_line(line, L0.x, C0.x, L1.x, C1.x, L2.x, C2.x, Tm);
+            float L1, C1, L2, C2;
+            line_sums_from_prefix(K, L0.x, C0.x, Bs.x, Bc.x, Cs.x, Cc.x, L1, C1, L2, C2);
+            end_line(line, L0.x, C0.x, L1, C1, L2, C2, T3.x, T4.x);
         }
         if (two) {
-            const float Tm[5] = {T0.y, T1.y, T2.y, T3.y, T4.y};
-            end_line(line + 1, L0.y, C0.y, L1.y, C1.y, L2.y, C2.y, Tm);
+            float L1, C1, L2, C2;
+            line_sums_from_prefix(K, L0.y, C0.y, Bs.y, Bc.y, Cs.y, Cc.y, L1, C1, L2, C2);
+            end_line(line + 1, L0.y, C0.y, L1, C1, L2, C2, T3.y, T4.y);
         }
     }
     if (j3cur >= 0) plane_to_pairs(Js, Jc, P, Pc, j3cur, n3, jc[2]);
