@@ -255,6 +255,17 @@ BGK_API bgk_status bgk_set_qprime_engine(bgk_ctx *ctx, int fp32_sums);
  * (variants 2-6 on the FP64 form or an unsupported order). */
 BGK_API bgk_status bgk_set_stage_kernel(bgk_ctx *ctx, int variant, int depth);
 
+/* Test entry for the bounded waits of the copy-ring kernels (variants 2-6):
+ * with after > 0 every block's ring delivers only its first `after`
+ * velocities and stops, so the consumers' next wait runs out, after
+ * wait_seconds (0: about 2 s) instead of about 2 s; the kernel then lets its
+ * issued copies land, sets its timeout status and returns, and the next
+ * status check reports BGK_ETIMEOUT.  The state written by such a stage is
+ * incomplete.  after = 0 restores normal operation (and the 2 s limit).
+ * Waits for the context's stream first.  Errors: BGK_EINVAL (NULL, after < 0,
+ * wait_seconds outside [0, 10]). */
+BGK_API bgk_status bgk_test_ring_stall(bgk_ctx *ctx, int after, double wait_seconds);
+
 /* Autotune the mixed-form stage kernel on this context's own problem (the
  * launch configuration only; every candidate computes the same values): time
  * the plain kernel and every supported asynchronous variant at every ring

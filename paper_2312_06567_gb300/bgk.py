@@ -53,6 +53,7 @@ SIGNATURES = {
     "bgk_set_newton": (c_int, [c_void_p, c_double, c_int]),
     "bgk_set_qprime_engine": (c_int, [c_void_p, c_int]),
     "bgk_set_stage_kernel": (c_int, [c_void_p, c_int, c_int]),
+    "bgk_test_ring_stall": (c_int, [c_void_p, c_int, c_double]),
     "bgk_set_graphs": (c_int, [c_void_p, c_int]),
     "bgk_tune_stage": (c_int, [c_void_p, c_double, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
                                ctypes.POINTER(c_double)]),
@@ -370,6 +371,11 @@ class Solver:
 
     def set_qprime_engine(self, fp32_sums):
         self._check(self.lib.bgk_set_qprime_engine(self._h, 1 if fp32_sums else 0))
+
+    def test_ring_stall(self, after, wait_seconds=0.0):
+        """Test entry: the copy rings deliver only `after` velocities per block
+        (0 restores), the bounded waits give up after wait_seconds."""
+        self._check(self.lib.bgk_test_ring_stall(self._h, int(after), float(wait_seconds)))
 
     STAGE_KERNELS = {"auto": 0, "plain": 1, "async": 2, "line": 3, "line_wide": 4, "half": 5, "half_wide": 6}
 

@@ -65,6 +65,8 @@ struct bgk_ctx {
     int qp_fp32;                      // Q' velocity sums on the FP32 pipe (mixed form default)
     int es_tensor;                    // tensor variant of the discrete ES equilibrium (delta = 0)
     int stage_variant, stage_depth;   // FP32 stage kernel choice and copy-ring depth
+    int ring_limit;                   // test hook (bgk_test_ring_stall): velocities a ring delivers, 0 = all
+    unsigned long long wait_ns;       // bounded-wait limit of the ring kernels, 0 = about 2 s
     // CUDA graphs of one SSP-RK3 step, one per buffer parity (f[0] alternates
     // between two buffers); recaptured when a launch parameter changes
     bool graphs_on;
@@ -362,6 +364,8 @@ StageArgs<T> stage_args(bgk_ctx *ctx, const void *fn, const void *fs, void *fo, 
     s.a = a; s.b = b; s.c = c; s.Nu = ctx->Nu; s.P = ctx->P; s.Kblk = ctx->Kblk;
     s.vg = ctx->vg; s.fr = ctx->fr; s.mesh = ctx->mesh;
     s.a32 = (float)a; s.ab32 = (float)(a + b); s.c32 = (float)c;
+    s.wait_ns = ctx->wait_ns;
+    s.ring_limit = ctx->ring_limit;
     for (int d = 0; d < 3; ++d) s.toh32[d] = (float)ctx->mesh.two_over_h[d];
     if (ctx->curved) set_geometry<T>(ctx, s);
     return s;
@@ -423,6 +427,8 @@ std::vector<double> step_signature(const bgk_ctx *ctx, double dt) {
             (double)(uintptr_t)ctx->log,
             (double)ctx->log_max,
             (double)ctx->stage_variant,
+            (double)ctx->ring_limit,
+            (double)ctx->wait_ns,
             (double)ctx->stage_depth,
             (double)ctx->qp_fp32,
             (double)ctx->es_tensor};
@@ -1056,6 +1062,14 @@ bgk_status bgk_set_stage_kernel(bgk_ctx *ctx, int variant, int depth) {
     }
     ctx->stage_variant = variant;
     ctx->stage_depth = depth;
+    return BGK_OK;
+}
+
+bgk_status bgk_test_ring_stall(bgk_ctx *ctx, int after, double wait_seconds) {
+    if (!ctx || after < 0 || !(wait_seconds >= 0.0) || wait_seconds > 10.0) return BGK_EINVAL;
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->ring_limit = after;
+    ctx->wait_ns = after > 0 ? (unsigned long long)(wait_seconds * 1e9) : 0ull;
     return BGK_OK;
 }
 

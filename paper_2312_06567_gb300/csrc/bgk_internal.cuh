@@ -209,6 +209,11 @@ struct StageArgs {
     // the compiler rematerialises them inside the velocity loop)
     float a32, ab32, c32, toh32[3];
     int Nu, P, Kblk;
+    // bounded waits of the copy-ring kernels: limit (0: about 2 s), and the
+    // number of velocities a block's ring delivers before it stops (0: all;
+    // set only by the test entry bgk_test_ring_stall)
+    unsigned long long wait_ns;
+    int ring_limit;
     VelGrid vg;
     FROps fr;
     MeshInfo mesh;

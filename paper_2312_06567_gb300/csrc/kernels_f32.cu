@@ -602,7 +602,7 @@ __global__ void __launch_bounds__(TmaGeom<Q, C>::NTHR, 2) k_stage_f32_tma(StageA
         float jt1 = (float)(-jc[0]);
         for (int j1 = 0; j1 < vn1; ++j1, jt1 += 1.f) {
             const int k = kl + j1;
-            ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(bars + slot), par));
+            ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(bars + slot), par, a.wait_ns));
             if (!ok) break;
             if (active) {
                 const float *st = sbuf + (size_t)slot * STAGE;

@@ -261,7 +261,8 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
             fills[i] = 0;
         }
         // the first S velocities
-        for (int i = 0; i < S && i < nk; ++i) {
+        const int nring = a.ring_limit > 0 ? min(nk, a.ring_limit) : nk;
+        for (int i = 0; i < S && i < nring; ++i) {
             ring_issue<Q, C, EB>(a, g, sbuf, bars, i, k0 + i);
             fills[i] = 1;
         }
@@ -389,7 +390,7 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
         float jt1 = (float)(-jc[0]);
         for (int j1 = 0; j1 < vn1; ++j1, jt1 += 1.f) {
             const int k = kl + j1;
-            ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(bars + slot), par));
+            ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(bars + slot), par, a.wait_ns));
             if (!ok) break;
             if (active) {
                 const float *st = sbuf + (size_t)slot * STAGE;
@@ -603,7 +604,7 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                     rel[slot] = 0;
                     __threadfence_block();
                     const int inext = (k - k0) + S;
-                    if (inext < nk) {
+                    if (inext < nk && (a.ring_limit <= 0 || inext < a.ring_limit)) {
                         ring_issue<Q, C, EB>(a, g, sbuf, bars, slot, k0 + inext);
                         fills[slot] += 1;
                     }
@@ -638,7 +639,7 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
             if (atomicAdd(&s_exited, 1u) == NW - 1) {
                 __threadfence_block();
                 for (int i = 0; i < S; ++i)
-                    if (fills[i] > 0) mbar_wait(smem_u32(bars + i), (fills[i] - 1) & 1);
+                    if (fills[i] > 0) mbar_wait(smem_u32(bars + i), (fills[i] - 1) & 1, a.wait_ns);
             }
         }
         return;

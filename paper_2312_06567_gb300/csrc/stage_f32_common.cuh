@@ -292,15 +292,16 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 // Wait for the completion of the barrier phase of the given parity; false
-// after about 2 s without it.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// after limit_ns (0: about 2 s) without it.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long limit_ns = 0) {
     if (mbar_try(bar, parity)) return true;
+    const unsigned long long lim = limit_ns ? limit_ns : 2000000000ull;
     const unsigned long long t0 = global_ns();
     for (;;) {
         // the timer is read once per 32 polls (each poll may suspend briefly)
         for (int i = 0; i < 32; ++i)
             if (mbar_try(bar, parity)) return true;
-        if (global_ns() - t0 > 2000000000ull) return false;
+        if (global_ns() - t0 > lim) return false;
     }
 }
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const float *src, uint32_t bytes, uint32_t bar) {
@@ -393,15 +394,16 @@ __device__ void ring_producer(const StageArgs<float> &a, const RunGeom &g, float
                               int S, int k0, int k1, volatile int *abort) {
     int i = 0;
     bool ok = true;
-    for (; i < k1 - k0; ++i) {
+    const int n = a.ring_limit > 0 ? min(k1 - k0, a.ring_limit) : k1 - k0;
+    for (; i < n; ++i) {
         const int slot = i % S;
-        if (i >= S && !mbar_wait(smem_u32(bars + S + slot), ((i / S) & 1) ^ 1)) { ok = false; break; }
+        if (i >= S && !mbar_wait(smem_u32(bars + S + slot), ((i / S) & 1) ^ 1, a.wait_ns)) { ok = false; break; }
         if (*abort) { ok = false; break; }
         ring_issue<Q, C, EB>(a, g, sbuf, bars, slot, k0 + i);
     }
     if (!ok) {
         // no copy may still be in flight when the block exits
-        for (int j = max(0, i - S); j < i; ++j) mbar_wait(smem_u32(bars + j % S), (j / S) & 1);
+        for (int j = max(0, i - S); j < i; ++j) mbar_wait(smem_u32(bars + j % S), (j / S) & 1, a.wait_ns);
         atomicOr(a.status, BGK_DEV_TIMEOUT);
     }
 }
