@@ -41,7 +41,10 @@ struct LineGeom {
     static constexpr int NQ = C == 2 ? 7 : 6;           // plane quantities per point
     // resident blocks asked of the register allocator: a budget of about 96
     // registers per thread (128 with a whole line per thread)
-    static constexpr int MINB = 65536 / (NTHR * (NPT == Q ? 128 : 96)) > 0 ? 65536 / (NTHR * (NPT == Q ? 128 : 96)) : 1;
+    // (Q = 3: 288 threads, two blocks of at most 112 registers)
+    static constexpr int MINB = Q == 3 ? 2
+                                       : (65536 / (NTHR * (NPT == Q ? 128 : 96)) > 0 ? 65536 / (NTHR * (NPT == Q ? 128 : 96))
+                                                                                      : 1);
     static_assert(NCT % 32 == 0, "consumer threads must fill whole warps");
     static_assert(Q % NPT == 0, "a thread takes a whole fraction of a line");
 };
@@ -59,6 +62,10 @@ __device__ __forceinline__ void ld_vec<2>(const float *p, float (&v)[2]) {
     v[0] = t.x; v[1] = t.y;
 }
 template <>
+__device__ __forceinline__ void ld_vec<3>(const float *p, float (&v)[3]) {
+    v[0] = p[0]; v[1] = p[1]; v[2] = p[2];               // 4-byte aligned only
+}
+template <>
 __device__ __forceinline__ void ld_vec<1>(const float *p, float (&v)[1]) {
     v[0] = *p;
 }
@@ -71,6 +78,10 @@ __device__ __forceinline__ void st_vec<4>(float *p, const float (&v)[4]) {
 template <>
 __device__ __forceinline__ void st_vec<2>(float *p, const float (&v)[2]) {
     *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+}
+template <>
+__device__ __forceinline__ void st_vec<3>(float *p, const float (&v)[3]) {
+    p[0] = v[0]; p[1] = v[1]; p[2] = v[2];
 }
 template <>
 __device__ __forceinline__ void st_vec<1>(float *p, const float (&v)[1]) {
@@ -291,7 +302,7 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
     const int bcm = !BC ? 0
                         : (l == 0 && g.xn0 < 0 ? 1 : 0) | (l == g.nel - 1 && g.xn1 < 0 ? 2 : 0) | (g.yn0 < 0 ? 4 : 0) |
                               (g.yn1 < 0 ? 8 : 0) | (g.zn0 < 0 ? 16 : 0) | (g.zn1 < 0 ? 32 : 0);
-    const int own_off = (l + 1) * NS;                    // own element within a component's stage region
+    const int own_off = (l + SG::PAD) * NS;              // own element within a component's stage region
     const int ln = Q * r;                                // own line within an element
     const bool mom = a.part != nullptr;
     // per-point FP32 parameters used every velocity
@@ -435,7 +446,7 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                                 for (int m = 1; m < Q; ++m) {
                                     // node j = (i0 + i + m) mod Q of the line, picked from F
                                     // without indexing a register array at run time
-                                    const int j = (i0 + i + m) & (Q - 1);
+                                    const int j = (i0 + i + m) % Q;
                                     float Fj = F[0];
 #pragma unroll
                                     for (int jj = 1; jj < Q; ++jj) Fj = j == jj ? F[jj] : Fj;
@@ -477,7 +488,7 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                         const float4 cf = sCf[sy][jy];
 #pragma unroll
                         for (int m = 1; m < Q; ++m) {
-                            const int jp = (jy + m) & (Q - 1);       // the canonical order
+                            const int jp = (jy + m) % Q;             // the canonical order
                             float Gv[NPT];
                             ld_vec<NPT>(sc + own_off + Q * (jp + Q * kz) + i0, Gv);
                             acc_dev<NPT>(t, Dr[m], Gv, nFi);
@@ -512,7 +523,7 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                         const float4 cf = sCf[sz][kz];
 #pragma unroll
                         for (int m = 1; m < Q; ++m) {
-                            const int kp = (kz + m) & (Q - 1);       // the canonical order
+                            const int kp = (kz + m) % Q;             // the canonical order
                             float Gv[NPT];
                             ld_vec<NPT>(sc + own_off + Q * (jy + Q * kp) + i0, Gv);
                             acc_dev<NPT>(t, Dr[m], Gv, nFi);
@@ -712,10 +723,22 @@ cudaError_t line_dispatch(int kind, bool launch, const StageArgs<float> &a, int 
     }
 }
 
+// p = 2: runs of 32 elements (288 threads, one line of 3 points each), the
+// line mapping only
+template <int C>
+cudaError_t line_dispatch3(int kind, bool launch, const StageArgs<float> &a, int n_vblk, int depth, cudaStream_t s,
+                           size_t *smem) {
+    if (kind != 0) return cudaErrorInvalidValue;
+    *smem = line_smem<3, C, 32, 3>(depth);
+    return launch ? line_launch<3, C, 32, 3>(a, n_vblk, depth, s) : cudaSuccess;
+}
+
 cudaError_t line_any(int kind, bool launch, const StageArgs<float> &a, int C, int n_vblk, int depth, cudaStream_t s,
                      size_t *smem) {
     if (a.fr.q == 4) return C == 1 ? line_dispatch<4, 1>(kind, launch, a, n_vblk, depth, s, smem)
                                    : line_dispatch<4, 2>(kind, launch, a, n_vblk, depth, s, smem);
+    if (a.fr.q == 3) return C == 1 ? line_dispatch3<1>(kind, launch, a, n_vblk, depth, s, smem)
+                                   : line_dispatch3<2>(kind, launch, a, n_vblk, depth, s, smem);
     return C == 1 ? line_dispatch<2, 1>(kind, launch, a, n_vblk, depth, s, smem)
                   : line_dispatch<2, 2>(kind, launch, a, n_vblk, depth, s, smem);
 }
@@ -726,8 +749,10 @@ bool aligned_to(const void *p, uintptr_t n) { return ((uintptr_t)p & (n - 1)) ==
 
 bool stage_f32_line_supported(const StageArgs<float> &a, int C, int kind, int depth) {
     const int Q = a.fr.q;
-    if (Q != 2 && Q != 4) return false;
+    if (Q != 2 && Q != 3 && Q != 4) return false;
     if (kind < 0 || kind > 3 || depth < 2 || depth > BGK_MAX_DEPTH || !a.eq32) return false;
+    // p = 2: the line mapping, on rows of whole 4-element (16-byte) groups
+    if (Q == 3 && (kind != 0 || a.mesh.n[0] % 4 != 0)) return false;
     for (int f = 0; f < 6; ++f)
         if (a.mesh.specular[f]) return false;               // reflected traces are not staged
     if (a.geo) return false;                                // curvilinear: the plain kernel only

@@ -317,7 +317,13 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const float *src, uint32_
 template <int Q, int C, int EB, bool FN = true>
 struct StageGeom {
     static constexpr int NS = Q * Q * Q;
-    static constexpr int SLOTS = EB + 2;
+    // x-halo slots on each side of the run: one element where an element is
+    // a whole number of 16-byte units (Q = 2, 4); at Q = 3 (108 bytes) the
+    // halo is copied as 4 elements (432 bytes) so that every bulk copy starts
+    // and ends on a 16-byte boundary, the neighbour being the one next to
+    // the run
+    static constexpr int PAD = Q == 3 ? 4 : 1;
+    static constexpr int SLOTS = EB + 2 * PAD;
     static constexpr int PER_C = (SLOTS + (FN ? 3 : 2) * EB) * NS;   // f^n run only with FN
     static constexpr int STAGE = C * PER_C;               // floats per stage buffer
 };
@@ -360,9 +366,9 @@ template <int Q, int C, int EB, bool FN = true>
 __device__ __forceinline__ void ring_issue(const StageArgs<float> &a, const RunGeom &g, float *sbuf,
                                            unsigned long long *bars, int slot, int k) {
     using SG = StageGeom<Q, C, EB, FN>;
-    constexpr int NS = SG::NS, SLOTS = SG::SLOTS, PER_C = SG::PER_C, STAGE = SG::STAGE;
+    constexpr int NS = SG::NS, SLOTS = SG::SLOTS, PER_C = SG::PER_C, STAGE = SG::STAGE, PAD = SG::PAD;
     const size_t slab = (size_t)a.P;
-    const uint32_t runb = (uint32_t)(g.nel * NS * 4), elb = NS * 4;
+    const uint32_t runb = (uint32_t)(g.nel * NS * 4), elb = PAD * NS * 4;
     const bool with_fn = FN && a.a32 != 0.f;
     const float4 u = __ldg(a.vtab32 + k);
     const int xe = u.x > 0.f ? g.xn0 : g.xn1, ye = u.y > 0.f ? g.yn0 : g.yn1, ze = u.z > 0.f ? g.zn0 : g.zn1;
@@ -375,8 +381,13 @@ __device__ __forceinline__ void ring_issue(const StageArgs<float> &a, const RunG
     for (int c = 0; c < C; ++c) {
         const float *src = a.f_s + ((size_t)c * a.Nu + k) * slab;
         float *own = st + c * PER_C;
-        bulk_g2s(smem_u32(own + NS), src + (size_t)g.e0 * NS, runb, full);
-        if (xe >= 0) bulk_g2s(smem_u32(own + (u.x > 0.f ? 0 : (g.nel + 1) * NS)), src + (size_t)xe * NS, elb, full);
+        bulk_g2s(smem_u32(own + PAD * NS), src + (size_t)g.e0 * NS, runb, full);
+        // the upwind x neighbour: left of the run into slot PAD - 1 (with the
+        // PAD - 1 elements before it), right of it into slot PAD + nel (with
+        // the PAD - 1 after it)
+        if (xe >= 0)
+            bulk_g2s(smem_u32(own + (u.x > 0.f ? 0 : (g.nel + PAD) * NS)),
+                     src + (size_t)(u.x > 0.f ? xe - (PAD - 1) : xe) * NS, elb, full);
         if (ye >= 0) bulk_g2s(smem_u32(own + SLOTS * NS), src + (size_t)ye * NS, runb, full);
         if (ze >= 0) bulk_g2s(smem_u32(own + (SLOTS + EB) * NS), src + (size_t)ze * NS, runb, full);
         if (with_fn)

@@ -38,13 +38,25 @@ ASYNC_CASES = {
     "tgv_es_p3_two_runs": lambda: _mild_es_box(mesh_n=(6, 3, 2), vel_n=(9, 8, 7)),
     "shock_fg_p3_dirichlet": lambda: _mild_shock(mesh_n=(6, 1, 1), vel_n=(16, 10, 9)).replace(p=3),
     "shock_fg_p3_dirichlet_3d": lambda: _mild_shock(mesh_n=(5, 2, 3), vel_n=(12, 9, 8)).replace(p=3),
+    # Q = 3 (the line mapping on rows of whole 4-element groups): 32-element runs
+    # with 4-element halo copies; one short run, a full and a short run, F/G with
+    # Dirichlet x-ends, and a periodic single-component box
+    "shock_fg_p2_rows8": lambda: _mild_shock(mesh_n=(8, 1, 2), vel_n=(13, 9, 8)),
+    "shock_fg_p2_two_runs": lambda: _mild_shock(mesh_n=(36, 1, 1), vel_n=(12, 9, 8)),
+    "es_box_p2_periodic": lambda: _mild_es_box(mesh_n=(4, 2, 2), p=2, vel_n=(9, 8, 7)),
 }
 
 
 def _smem_bytes(variant, q, C, depth):
     """Shared memory of an asynchronous stage kernel (the launcher's formula);
-    a configuration above 200 KB is refused by design."""
+    a configuration above 200 KB is refused by design (and every variant but
+    the line mapping at q = 3)."""
     ns = q ** 3
+    if q == 3:
+        if variant != "line":
+            return 1 << 30
+        eb, nq = 32, (7 if C == 2 else 6)
+        return depth * C * (4 * eb + 8) * ns * 4 + 3 * 2 * nq * (eb * 9) * 4 + 16 * depth
     if variant == "async":
         eb = 256 // ns
         nct = eb * ns
@@ -105,7 +117,8 @@ def test_async_stage_entry_point_with_fn(lib):
 
 
 def test_async_stage_unsupported_configurations(lib):
-    # p = 2: element slabs of 27 floats are not whole 16-byte units
+    # p = 2 on rows of 6 elements: element slabs of 27 floats, rows not whole
+    # 4-element (16-byte) groups
     wl = _mild_shock()
     with lib.Solver(wl, lib.BGK_MIXED) as s:
         for variant in VARIANTS:
