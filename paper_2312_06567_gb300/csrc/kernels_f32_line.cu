@@ -41,8 +41,10 @@ struct LineGeom {
     static constexpr int NQ = C == 2 ? 7 : 6;           // plane quantities per point
     // resident blocks asked of the register allocator: a budget of about 96
     // registers per thread (128 with a whole line per thread)
-    // (Q = 3: 288 threads, two blocks of at most 112 registers)
-    static constexpr int MINB = Q == 3 ? 2
+    // (Q = 3: 288 threads; one block per SM without spills measured faster
+    // than two capped at 96 registers: 41.4 vs 53.7 ms per step on the
+    // normal shock)
+    static constexpr int MINB = Q == 3 ? 1
                                        : (65536 / (NTHR * (NPT == Q ? 128 : 96)) > 0 ? 65536 / (NTHR * (NPT == Q ? 128 : 96))
                                                                                       : 1);
     static_assert(NCT % 32 == 0, "consumer threads must fill whole warps");
