@@ -79,6 +79,12 @@ def _shock():
     return W.normal_shock_tube()
 
 
+def _shock_small():
+    """The normal shock physics on 16x4x4 elements (2.3e8 DOF, F and G): the size
+    used for ncu captures of its stage kernel."""
+    return W.reduced(W.normal_shock_tube(), mesh_n=(16, 4, 4))
+
+
 def _ogrid_small():
     """The sphere O-grid physics on 6x12x12 elements (4.4e8 DOF): the size used
     for ncu captures of the curvilinear kernels."""
@@ -91,7 +97,7 @@ def _ogrid_tiny():
 
 
 WORKLOADS = {"taylor_green": W.taylor_green_box, "taylor_green_8x8x4": _tg_small,
-             "normal_shock": _shock, "sine_box": W.periodic_sine_box,
+             "normal_shock": _shock, "normal_shock_16x4x4": _shock_small, "sine_box": W.periodic_sine_box,
              "sphere_ogrid": W.sphere_ogrid, "sphere_ogrid_6x12x12": _ogrid_small,
              "sphere_ogrid_4x8x8": _ogrid_tiny}
 

@@ -35,19 +35,20 @@ namespace {
 template <int Q, int C, int EB, int NPT>
 struct LineGeom {
     static constexpr int NH = Q / NPT;                  // threads per node line
-    static constexpr int NCT = EB * Q * Q * NH;         // consumer threads
+    // consumer threads: the run's lines, rounded up to whole warps (at Q = 3
+    // the last warp's extra threads map past the run and stay idle)
+    static constexpr int NCT = (EB * Q * Q * NH + 31) / 32 * 32;
     static constexpr int NTHR = NCT;                    // no producer warp: the ring feeds itself
     static constexpr int NW = NCT / 32;
     static constexpr int NQ = C == 2 ? 7 : 6;           // plane quantities per point
     // resident blocks asked of the register allocator: a budget of about 96
     // registers per thread (128 with a whole line per thread)
-    // (Q = 3: 288 threads; one block per SM without spills measured faster
-    // than two capped at 96 registers: 41.4 vs 53.7 ms per step on the
-    // normal shock)
-    static constexpr int MINB = Q == 3 ? 1
+    // (Q = 3: 16-element runs, 144 threads in 160: two blocks per SM of up to
+    // 204 registers, no spills; capping at 96 registers with spills was slower,
+    // 53.7 vs 40.7 ms per step on the normal shock)
+    static constexpr int MINB = Q == 3 ? 2
                                        : (65536 / (NTHR * (NPT == Q ? 128 : 96)) > 0 ? 65536 / (NTHR * (NPT == Q ? 128 : 96))
                                                                                       : 1);
-    static_assert(NCT % 32 == 0, "consumer threads must fill whole warps");
     static_assert(Q % NPT == 0, "a thread takes a whole fraction of a line");
 };
 
@@ -256,6 +257,8 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
     __shared__ float4 sCf[2][Q];
     __shared__ float su1[BGK_MAXV];                      // u1 of the first-axis nodes (the same on every line)
     __shared__ unsigned int s_exited;
+    __shared__ unsigned long long s_wait_ns;
+    __shared__ int s_nfill;                              // velocities the ring delivers
     constexpr int NW = LG::NW;
     const int tid = threadIdx.x;
     RunGeom g;
@@ -269,12 +272,14 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
     if (tid == 0) {
         ring_init(bars, S, NW);
         s_exited = 0;
+        s_wait_ns = a.wait_ns;
         for (int i = 0; i < S; ++i) {
             rel[i] = 0;
             fills[i] = 0;
         }
         // the first S velocities
         const int nring = a.ring_limit > 0 ? min(nk, a.ring_limit) : nk;
+        s_nfill = nring;
         for (int i = 0; i < S && i < nring; ++i) {
             ring_issue<Q, C, EB>(a, g, sbuf, bars, i, k0 + i);
             fills[i] = 1;
@@ -403,7 +408,7 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
         float jt1 = (float)(-jc[0]);
         for (int j1 = 0; j1 < vn1; ++j1, jt1 += 1.f) {
             const int k = kl + j1;
-            ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(bars + slot), par, a.wait_ns));
+            ok = __all_sync(0xffffffffu, mbar_wait_s(smem_u32(bars + slot), par, &s_wait_ns));
             if (!ok) break;
             if (active) {
                 const float *st = sbuf + (size_t)slot * STAGE;
@@ -617,7 +622,7 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                     rel[slot] = 0;
                     __threadfence_block();
                     const int inext = (k - k0) + S;
-                    if (inext < nk && (a.ring_limit <= 0 || inext < a.ring_limit)) {
+                    if (inext < *(volatile int *)&s_nfill) {
                         ring_issue<Q, C, EB>(a, g, sbuf, bars, slot, k0 + inext);
                         fills[slot] += 1;
                     }
@@ -725,14 +730,14 @@ cudaError_t line_dispatch(int kind, bool launch, const StageArgs<float> &a, int 
     }
 }
 
-// p = 2: runs of 32 elements (288 threads, one line of 3 points each), the
+// p = 2: runs of 16 elements (144 lines of 3 points, in five warps), the
 // line mapping only
 template <int C>
 cudaError_t line_dispatch3(int kind, bool launch, const StageArgs<float> &a, int n_vblk, int depth, cudaStream_t s,
                            size_t *smem) {
     if (kind != 0) return cudaErrorInvalidValue;
-    *smem = line_smem<3, C, 32, 3>(depth);
-    return launch ? line_launch<3, C, 32, 3>(a, n_vblk, depth, s) : cudaSuccess;
+    *smem = line_smem<3, C, 16, 3>(depth);
+    return launch ? line_launch<3, C, 16, 3>(a, n_vblk, depth, s) : cudaSuccess;
 }
 
 cudaError_t line_any(int kind, bool launch, const StageArgs<float> &a, int C, int n_vblk, int depth, cudaStream_t s,

@@ -304,6 +304,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigne
         if (global_ns() - t0 > lim) return false;
     }
 }
+// The same wait with its limit read from shared memory only once the first
+// poll fails (keeps the limit out of the registers of a hot loop).
+__device__ __forceinline__ bool mbar_wait_s(uint32_t bar, uint32_t parity, const volatile unsigned long long *limit_ns) {
+    if (mbar_try(bar, parity)) return true;
+    return mbar_wait(bar, parity, *limit_ns);
+}
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const float *src, uint32_t bytes, uint32_t bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                  "l"(src), "r"(bytes), "r"(bar)

@@ -38,11 +38,11 @@ ASYNC_CASES = {
     "tgv_es_p3_two_runs": lambda: _mild_es_box(mesh_n=(6, 3, 2), vel_n=(9, 8, 7)),
     "shock_fg_p3_dirichlet": lambda: _mild_shock(mesh_n=(6, 1, 1), vel_n=(16, 10, 9)).replace(p=3),
     "shock_fg_p3_dirichlet_3d": lambda: _mild_shock(mesh_n=(5, 2, 3), vel_n=(12, 9, 8)).replace(p=3),
-    # Q = 3 (the line mapping on rows of whole 4-element groups): 32-element runs
+    # Q = 3 (the line mapping on rows of whole 4-element groups): 16-element runs
     # with 4-element halo copies; one short run, a full and a short run, F/G with
     # Dirichlet x-ends, and a periodic single-component box
     "shock_fg_p2_rows8": lambda: _mild_shock(mesh_n=(8, 1, 2), vel_n=(13, 9, 8)),
-    "shock_fg_p2_two_runs": lambda: _mild_shock(mesh_n=(36, 1, 1), vel_n=(12, 9, 8)),
+    "shock_fg_p2_two_runs": lambda: _mild_shock(mesh_n=(20, 1, 1), vel_n=(12, 9, 8)),
     "es_box_p2_periodic": lambda: _mild_es_box(mesh_n=(4, 2, 2), p=2, vel_n=(9, 8, 7)),
 }
 
@@ -55,8 +55,9 @@ def _smem_bytes(variant, q, C, depth):
     if q == 3:
         if variant != "line":
             return 1 << 30
-        eb, nq = 32, (7 if C == 2 else 6)
-        return depth * C * (4 * eb + 8) * ns * 4 + 3 * 2 * nq * (eb * 9) * 4 + 16 * depth
+        eb, nq = 16, (7 if C == 2 else 6)
+        nct = (eb * 9 + 31) // 32 * 32
+        return depth * C * (4 * eb + 8) * ns * 4 + 3 * 2 * nq * nct * 4 + 16 * depth
     if variant == "async":
         eb = 256 // ns
         nct = eb * ns
