@@ -10,7 +10,7 @@ summed over ranks (independent replicas, weak scaling).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload NAME] [--forms fp64,fp64_learned,mixed,mixed_learned]
                   [--stage-kernel tune|auto|plain|async|line|...] [--depth S]
-                  [--no-graphs] [--e2e-steps E] [--no-cpu-baseline]
+                  [--no-graphs] [--velocity-blocks N] [--e2e-steps E] [--no-cpu-baseline]
                   [--no-tc-probe] [--tc-probe-panels N] [--no-other-workloads]
 
 Workloads: taylor_green (default), sine_box, normal_shock, sphere_ogrid and
@@ -61,6 +61,8 @@ def parse():
                     help="mixed-form stage kernel; 'tune' times the candidates on the workload (untimed)")
     ap.add_argument("--depth", type=int, default=6, help="copy-ring depth of the async stage kernel")
     ap.add_argument("--no-graphs", action="store_true", help="time direct launches instead of CUDA-graph replays")
+    ap.add_argument("--velocity-blocks", type=int, default=0,
+                    help="velocity blocks of the stage grid (0: the context's choice, tuned with --stage-kernel tune)")
     ap.add_argument("--no-tc-probe", action="store_true", help="skip the tensor-core FR-operator probe")
     ap.add_argument("--no-other-workloads", action="store_true",
                     help="skip the normal shock and sphere O-grid lines nested in the default run")
@@ -341,6 +343,11 @@ def run_ours(args, rank, world, dev):
             else:
                 s.set_stage_kernel(args.stage_kernel, args.depth)
                 tuned = {"variant": args.stage_kernel, "depth": args.depth}
+            if args.velocity_blocks > 0:
+                s.set_velocity_blocks(args.velocity_blocks)
+            nvb, per_blk, _ = s.velocity_blocks()
+            tuned["velocity_blocks"] = nvb
+            tuned["velocities_per_block"] = per_blk
         train = None
         if learned:
             # warm-up steps log the solver's own (features, Delta) pairs; the

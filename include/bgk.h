@@ -255,6 +255,22 @@ BGK_API bgk_status bgk_set_qprime_engine(bgk_ctx *ctx, int fp32_sums);
  * (variants 2-6 on the FP64 form or an unsupported order). */
 BGK_API bgk_status bgk_set_stage_kernel(bgk_ctx *ctx, int variant, int depth);
 
+/* Velocity blocking of the stage and moment kernels: the velocities are
+ * split into n blocks of whole first-axis lines (the last may be shorter),
+ * each a separate CTA column of the stage grid with its own moment partials
+ * (bgk_create picks about enough blocks to fill the GPU; more blocks fill its
+ * last wave of CTAs better and cost the Q' solve more partial sums;
+ * bgk_tune_stage also chooses n).  The values computed change in the last
+ * bits with n (the partial sums are taken in another grouping), not beyond.
+ * Waits for the context's stream; the next step recomputes the moments.
+ * Errors: BGK_EINVAL (NULL, n < 1, n above the context's maximum, given by
+ * bgk_get_velocity_blocks). */
+BGK_API bgk_status bgk_set_velocity_blocks(bgk_ctx *ctx, int n);
+/* The current velocity blocking: number of blocks, velocities per block and
+ * the most blocks bgk_set_velocity_blocks accepts (outputs may be NULL).
+ * Errors: BGK_EINVAL (NULL context). */
+BGK_API bgk_status bgk_get_velocity_blocks(const bgk_ctx *ctx, int *n_blocks, int *per_block, int *max_blocks);
+
 /* Test entry for the bounded waits of the copy-ring kernels (variants 2-6):
  * with after > 0 every block's ring delivers only its first `after`
  * velocities and stops, so the consumers' next wait runs out, after
@@ -267,11 +283,14 @@ BGK_API bgk_status bgk_set_stage_kernel(bgk_ctx *ctx, int variant, int depth);
 BGK_API bgk_status bgk_test_ring_stall(bgk_ctx *ctx, int after, double wait_seconds);
 
 /* Autotune the mixed-form stage kernel on this context's own problem (the
- * launch configuration only; every candidate computes the same values): time
- * the plain kernel and every supported asynchronous variant at every ring
+ * launch configuration only; every kernel candidate computes the same values):
+ * time the plain kernel and every supported asynchronous variant at every ring
  * depth (2, 3, 4, 6, 8, 12, 16), each over `reps` stages with f^n and the moment
  * epilogue (time step dt), from the current state into a scratch buffer, and
- * keep the fastest (as bgk_set_stage_kernel would).  The state is not
+ * keep the fastest (as bgk_set_stage_kernel would); then, for that kernel, time
+ * Q' solve + stage at the velocity blockings from the current count to four
+ * times it that split the lines evenly and keep the fastest (as
+ * bgk_set_velocity_blocks would).  The state is not
  * changed; the cached moments are recomputed by the next step.  Outputs (each
  * may be NULL): the chosen variant and depth and its mean time per stage in
  * ms.  The FP64 form has one kernel: returns variant 1 and 0 ms.  Errors:

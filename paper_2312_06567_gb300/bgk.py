@@ -54,6 +54,8 @@ SIGNATURES = {
     "bgk_set_qprime_engine": (c_int, [c_void_p, c_int]),
     "bgk_set_stage_kernel": (c_int, [c_void_p, c_int, c_int]),
     "bgk_test_ring_stall": (c_int, [c_void_p, c_int, c_double]),
+    "bgk_set_velocity_blocks": (c_int, [c_void_p, c_int]),
+    "bgk_get_velocity_blocks": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "bgk_set_graphs": (c_int, [c_void_p, c_int]),
     "bgk_tune_stage": (c_int, [c_void_p, c_double, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
                                ctypes.POINTER(c_double)]),
@@ -371,6 +373,15 @@ class Solver:
 
     def set_qprime_engine(self, fp32_sums):
         self._check(self.lib.bgk_set_qprime_engine(self._h, 1 if fp32_sums else 0))
+
+    def set_velocity_blocks(self, n):
+        self._check(self.lib.bgk_set_velocity_blocks(self._h, int(n)))
+
+    def velocity_blocks(self):
+        """(number of velocity blocks, velocities per block, most blocks accepted)."""
+        n, per, mx = c_int(), c_int(), c_int()
+        self._check(self.lib.bgk_get_velocity_blocks(self._h, ctypes.byref(n), ctypes.byref(per), ctypes.byref(mx)))
+        return n.value, per.value, mx.value
 
     def test_ring_stall(self, after, wait_seconds=0.0):
         """Test entry: the copy rings deliver only `after` velocities per block

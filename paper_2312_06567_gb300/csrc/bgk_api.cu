@@ -59,6 +59,7 @@ struct bgk_ctx {
     NewtonStats *stats;
     int *iters;
     int Kblk, n_vblk;
+    int lines, n_vblk_cap;            // first-axis velocity lines; most velocity blocks the partials hold
     bool part_valid;
     double tol;
     int max_iter;
@@ -427,6 +428,7 @@ std::vector<double> step_signature(const bgk_ctx *ctx, double dt) {
             (double)(uintptr_t)ctx->log,
             (double)ctx->log_max,
             (double)ctx->stage_variant,
+            (double)ctx->Kblk,
             (double)ctx->ring_limit,
             (double)ctx->wait_ns,
             (double)ctx->stage_depth,
@@ -730,6 +732,8 @@ bgk_status create_ctx(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
         const int lines_per_blk = (lines + want - 1) / want;
         ctx->Kblk = lines_per_blk * vg->n[0];
         ctx->n_vblk = (int)((Nu + ctx->Kblk - 1) / ctx->Kblk);
+        ctx->lines = lines;
+        ctx->n_vblk_cap = std::max(ctx->n_vblk, std::min(64, lines));   // room for bgk_set_velocity_blocks
     }
 
     bgk_status st = BGK_OK;
@@ -747,7 +751,7 @@ bgk_status create_ctx(bgk_ctx **out, const bgk_mesh_desc *mesh, const bgk_vgrid_
         if (st == BGK_OK) cu(cudaMalloc(&ctx->f[i], fbytes), "cudaMalloc(state)");
     }
     const size_t P = ctx->P;
-    if (st == BGK_OK) cu(cudaMalloc(&ctx->part, (size_t)ctx->n_vblk * BGK_NMOM * P * sizeof(double)), "cudaMalloc(part)");
+    if (st == BGK_OK) cu(cudaMalloc(&ctx->part, (size_t)ctx->n_vblk_cap * BGK_NMOM * P * sizeof(double)), "cudaMalloc(part)");
     if (st == BGK_OK) cu(cudaMalloc(&ctx->mom, P * BGK_NMOM * sizeof(double)), "cudaMalloc(mom)");
     if (st == BGK_OK) cu(cudaMalloc(&ctx->eq, P * BGK_NEQ * sizeof(double)), "cudaMalloc(eq)");
     ctx->eq32 = nullptr;
@@ -1065,6 +1069,39 @@ bgk_status bgk_set_stage_kernel(bgk_ctx *ctx, int variant, int depth) {
     return BGK_OK;
 }
 
+}  // extern "C"
+namespace {
+// Velocity blocking: n blocks of whole first-axis lines (the last may be
+// shorter); the cached partials and captured graphs no longer apply.
+void set_blocking(bgk_ctx *ctx, int n) {
+    const int lpb = (ctx->lines + n - 1) / n;
+    ctx->Kblk = lpb * ctx->vg.n[0];
+    ctx->n_vblk = (int)((ctx->Nu + ctx->Kblk - 1) / ctx->Kblk);
+    ctx->part_valid = false;
+    drop_graphs(ctx);
+}
+}  // namespace
+extern "C" {
+
+bgk_status bgk_set_velocity_blocks(bgk_ctx *ctx, int n) {
+    if (!ctx || n < 1) return BGK_EINVAL;
+    if (n > ctx->n_vblk_cap)
+        return fail(ctx, BGK_EINVAL, "at most %d velocity blocks on this context", ctx->n_vblk_cap);
+    bgk_status st;
+    if (ctx->pipe.active && (st = bgk_step_host_sync(ctx))) return st;
+    CU(cudaStreamSynchronize(ctx->stream));
+    set_blocking(ctx, n);
+    return BGK_OK;
+}
+
+bgk_status bgk_get_velocity_blocks(const bgk_ctx *ctx, int *n_blocks, int *per_block, int *max_blocks) {
+    if (!ctx) return BGK_EINVAL;
+    if (n_blocks) *n_blocks = ctx->n_vblk;
+    if (per_block) *per_block = ctx->Kblk;
+    if (max_blocks) *max_blocks = ctx->n_vblk_cap;
+    return BGK_OK;
+}
+
 bgk_status bgk_test_ring_stall(bgk_ctx *ctx, int after, double wait_seconds) {
     if (!ctx || after < 0 || !(wait_seconds >= 0.0) || wait_seconds > 10.0) return BGK_EINVAL;
     CU(cudaStreamSynchronize(ctx->stream));
@@ -1115,10 +1152,45 @@ bgk_status bgk_tune_stage(bgk_ctx *ctx, double dt, int reps, int *variant_out, i
         if (err != cudaSuccess) break;
         if (ms / reps < best) { best = ms / reps; pick = c; }
     }
+    ctx->part_valid = false;              // the partials now describe the scratch output
+    if (err == cudaSuccess) {
+        // then the velocity blocking for the chosen kernel: blocks of whole
+        // lines, from the default count to four times it, splitting the lines
+        // evenly; each candidate timed as Q' solve + stage (more blocks fill
+        // the GPU's last wave of CTAs better and cost the Q' solve more
+        // partial sums)
+        const int n0 = ctx->n_vblk;
+        std::vector<int> nb{n0};
+        for (int n = n0 + 1; n <= std::min(ctx->n_vblk_cap, 4 * n0); ++n)
+            if (ctx->lines % n == 0) nb.push_back(n);
+        double best_nb = 1e300;
+        int pick_nb = n0;
+        const StageArgs<float> sp = stage_args<float>(ctx, ctx->f[0], ctx->f[0], ctx->f[2], 0.75, 0.25, 0.25 * dt, true);
+        for (int n : nb) {
+            set_blocking(ctx, n);
+            if ((st = run_moments(ctx, ctx->f[0]))) break;
+            StageArgs<float> sn = sp;
+            sn.Kblk = ctx->Kblk;
+            if ((st = run_qprime(ctx, ctx->part, ctx->n_vblk, ctx->P, ctx->eq, ctx->qp, nullptr, nullptr))) break;
+            err = launch_stage_f32(sn, ctx->C, ctx->n_vblk, pick.v, pick.d, ctx->stream);       // warm-up
+            if (err == cudaSuccess) err = cudaEventRecord(ea, ctx->stream);
+            for (int r = 0; r < reps && err == cudaSuccess && !st; ++r) {
+                st = run_qprime(ctx, ctx->part, ctx->n_vblk, ctx->P, ctx->eq, ctx->qp, nullptr, nullptr);
+                if (!st) err = launch_stage_f32(sn, ctx->C, ctx->n_vblk, pick.v, pick.d, ctx->stream);
+            }
+            if (err == cudaSuccess && !st) err = cudaEventRecord(eb, ctx->stream);
+            if (err == cudaSuccess && !st) err = cudaEventSynchronize(eb);
+            float ms = 0.f;
+            if (err == cudaSuccess && !st) err = cudaEventElapsedTime(&ms, ea, eb);
+            if (err != cudaSuccess || st) break;
+            if (ms / reps < best_nb) { best_nb = ms / reps; pick_nb = n; }
+        }
+        set_blocking(ctx, pick_nb);
+    }
     cudaEventDestroy(ea);
     cudaEventDestroy(eb);
+    if (st) return st;
     CU(err);
-    ctx->part_valid = false;              // the partials now describe the scratch output
     if ((st = check_device_status(ctx))) return st;
     ctx->stage_variant = pick.v;
     ctx->stage_depth = pick.d;

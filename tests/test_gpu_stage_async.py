@@ -171,3 +171,33 @@ def test_tuner_keeps_state_and_picks_a_supported_kernel(lib):
         f1 = s.get_state()
     _, f_p, _ = _run(lib, wl, f0, "plain", 6, 1)
     assert np.array_equal(f1, f_p)
+
+
+def test_velocity_blocking_changes_only_the_last_bits(lib):
+    """bgk_set_velocity_blocks regroups the moment partials (and the stage
+    grid); two steps agree with the default blocking within the mixed form's
+    1e-5, and the blocking is reported back; counts above the maximum are
+    refused."""
+    wl = ASYNC_CASES["tgv_es_p3_two_runs"]()
+    f0 = W.random_anisotropic_state(wl, seed=9).astype(np.float32)
+    outs = {}
+    for n in (0, 1, 3, 5):
+        with lib.Solver(wl, lib.BGK_MIXED) as s:
+            s.set_stage_kernel("line", 2)
+            nb, per, mx = s.velocity_blocks()
+            assert 1 <= nb <= mx and per % wl.vel_n[0] == 0 and nb * per >= wl.n_vel
+            if n:
+                s.set_velocity_blocks(n)
+                nb, per, _ = s.velocity_blocks()
+                lines = wl.n_vel // wl.vel_n[0]
+                assert per == -(-lines // n) * wl.vel_n[0] and nb == -(-wl.n_vel // per)
+            with pytest.raises(RuntimeError):
+                s.set_velocity_blocks(mx + 1)
+            s.set_state(f0)
+            assert s.step(wl.dt(), 2) == lib.BGK_OK
+            outs[n] = (s.get_state().astype(np.float64), s.moments())
+    f_ref, m_ref = outs[0]
+    scale = np.abs(f_ref).reshape(f_ref.shape[0], f_ref.shape[1], -1).max(axis=2)[:, :, None, None]
+    for n, (f, m) in outs.items():
+        assert np.max(np.abs(f - f_ref) / np.maximum(scale, 1e-300)) <= 1e-5, n
+        assert np.max(np.abs(m - m_ref) / np.maximum(np.abs(m_ref).max(axis=0), 1e-300)) <= 1e-5, n
