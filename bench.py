@@ -598,11 +598,14 @@ def kernel_rooflines(wl, r, peaks, form):
 
 
 # DRAM bytes per DOF of a stage launch, mean over the three stages of a step,
-# from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# line kernel on the Taylor--Green physics at 8x8x4 elements, p = 3, 24^3
-# velocities (valid for that kernel variant as it stands; traffic per DOF does
-# not depend on N_e).
-MEASURED_STAGE_TRAFFIC_PER_DOF = {"line": 11.25}
+# from ncu captures (dram__bytes_read.sum + dram__bytes_write.sum) of a stage
+# that reads f^n (the second), with the first stage's f^n read (4 B/DOF per
+# component) taken off for the mean: the line kernel on the Taylor--Green
+# physics at 8x8x4 elements, p = 3, 24^3 velocities (12.71 B/DOF captured), and
+# on the normal shock physics at 16x4x4 elements, p = 2, F and G (24.10 B/DOF).
+# Valid for those kernels as they stand; traffic per DOF does not depend on N_e.
+# Keys: (variant, p, components).
+MEASURED_STAGE_TRAFFIC_PER_DOF = {("line", 3, 1): 11.38, ("line", 2, 2): 21.43}
 
 
 def tensor_probe_summary(tc, wl, peaks):
@@ -751,8 +754,8 @@ def compose_line(args, wl, results, peaks, world):
         "peaks_measured": peaks,
     }
     rl = kernel_rooflines(wl, r, peaks, main_form)
-    sk = (r.get("stage_kernel") or {}).get("variant")
-    if sk in MEASURED_STAGE_TRAFFIC_PER_DOF and wl.p == 3 and wl.n_comp == 1:
+    sk = ((r.get("stage_kernel") or {}).get("variant"), wl.p, wl.n_comp)
+    if sk in MEASURED_STAGE_TRAFFIC_PER_DOF and "stage" in rl:
         rl["stage"]["traffic"] = MEASURED_STAGE_TRAFFIC_PER_DOF[sk] * wl.dof
     line["roofline"] = dominant_roofline(rl)
     line["roofline_kernels"] = rl
