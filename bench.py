@@ -336,9 +336,10 @@ def run_ours(args, rank, world, dev):
         q = np.concatenate([rho.reshape(-1, 1), U.reshape(-1, 3), theta.reshape(-1, 1)], axis=1)
         s.set_maxwellian(q)
         tuned = None
-        if prec == bgk.BGK_MIXED:
+        if args.stage_kernel == "tune" or prec == bgk.BGK_MIXED:
             if args.stage_kernel == "tune":
-                v, d, tms = s.tune_stage(dt)
+                # (the FP64 form has one stage kernel: only its velocity blocking is tuned)
+                v, d, tms = s.tune_stage(dt, reps=3 if prec == bgk.BGK_MIXED else 1)
                 tuned = {"variant": v, "depth": d, "ms_per_stage": tms}
             else:
                 s.set_stage_kernel(args.stage_kernel, args.depth)

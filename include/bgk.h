@@ -293,7 +293,8 @@ BGK_API bgk_status bgk_test_ring_stall(bgk_ctx *ctx, int after, double wait_seco
  * bgk_set_velocity_blocks would).  The state is not
  * changed; the cached moments are recomputed by the next step.  Outputs (each
  * may be NULL): the chosen variant and depth and its mean time per stage in
- * ms.  The FP64 form has one kernel: returns variant 1 and 0 ms.  Errors:
+ * ms.  The FP64 form has one kernel: only its velocity blocking is chosen (by
+ * the stage's time); returns variant 1 and that kernel's time.  Errors:
  * BGK_EINVAL, BGK_ECUDA, BGK_ETIMEOUT, BGK_ENOCONV (the Q' solve of the
  * current state). */
 BGK_API bgk_status bgk_tune_stage(bgk_ctx *ctx, double dt, int reps, int *variant_out, int *depth_out,

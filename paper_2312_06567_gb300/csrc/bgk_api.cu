@@ -1113,13 +1113,48 @@ bgk_status bgk_test_ring_stall(bgk_ctx *ctx, int after, double wait_seconds) {
 bgk_status bgk_tune_stage(bgk_ctx *ctx, double dt, int reps, int *variant_out, int *depth_out, double *ms_out) {
     if (!ctx || !(dt > 0.0) || reps < 1) return BGK_EINVAL;
     if (ctx->shard) return fail(ctx, BGK_ENOTSUP, "tune on an unsharded context of the same problem (a shard's own moments are partial)");
+    bgk_status st;
     if (ctx->precision != BGK_MIXED) {
+        // one stage kernel: only the velocity blocking is chosen, by the
+        // stage's time (the FP64 Q' solve does not depend on it)
+        const int n0 = ctx->n_vblk;
+        std::vector<int> nb{n0};
+        for (int n = n0 + 1; n <= std::min(ctx->n_vblk_cap, 4 * n0); ++n)
+            if (ctx->lines % n == 0) nb.push_back(n);
+        if (!ctx->part_valid) {
+            if ((st = run_moments(ctx, ctx->f[0]))) return st;
+            ctx->part_valid = true;
+        }
+        if ((st = run_qprime(ctx, ctx->part, ctx->n_vblk, ctx->P, ctx->eq, ctx->qp, nullptr, nullptr))) return st;
+        cudaEvent_t ea = nullptr, eb = nullptr;
+        CU(cudaEventCreate(&ea));
+        CU(cudaEventCreate(&eb));
+        cudaError_t err = cudaSuccess;
+        double best = 1e300;
+        int pick_nb = n0;
+        for (int n : nb) {
+            set_blocking(ctx, n);
+            StageArgs<double> sd = stage_args<double>(ctx, ctx->f[0], ctx->f[0], ctx->f[2], 0.75, 0.25, 0.25 * dt, true);
+            err = launch_stage_f64(sd, ctx->C, ctx->n_vblk, ctx->stream);                   // warm-up
+            if (err == cudaSuccess) err = cudaEventRecord(ea, ctx->stream);
+            for (int r = 0; r < reps && err == cudaSuccess; ++r) err = launch_stage_f64(sd, ctx->C, ctx->n_vblk, ctx->stream);
+            if (err == cudaSuccess) err = cudaEventRecord(eb, ctx->stream);
+            if (err == cudaSuccess) err = cudaEventSynchronize(eb);
+            float ms = 0.f;
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, ea, eb);
+            if (err != cudaSuccess) break;
+            if (ms / reps < best) { best = ms / reps; pick_nb = n; }
+        }
+        cudaEventDestroy(ea);
+        cudaEventDestroy(eb);
+        set_blocking(ctx, pick_nb);
+        CU(err);
+        if ((st = check_device_status(ctx))) return st;
         if (variant_out) *variant_out = BGK_STAGE_PLAIN;
         if (depth_out) *depth_out = ctx->stage_depth;
-        if (ms_out) *ms_out = 0.0;
+        if (ms_out) *ms_out = best;
         return BGK_OK;
     }
-    bgk_status st;
     if (!ctx->part_valid) {
         if ((st = run_moments(ctx, ctx->f[0]))) return st;
         ctx->part_valid = true;
