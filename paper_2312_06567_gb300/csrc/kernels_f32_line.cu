@@ -415,6 +415,134 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                 const float u1 = su1[j1];
                 const int sx = u1 > 0.f ? 0 : 1;
                 float outv[C][NPT];
+                if constexpr (C == 2 && NPT == Q && NPT % 2 == 1) {
+                    // F and G of each point as one packed FP32 pair: every
+                    // component's operations exactly those of the per-component
+                    // body below (x - y as x + (-y), negation exact), so the
+                    // results are the same bit for bit; the equilibrium is
+                    // evaluated once for both
+                    const float *s0 = st, *s1 = st + PER_C;
+                    auto ld2 = [&](int off, int n, float2 *v) {
+                        for (int i = 0; i < n; ++i) v[i] = make_float2(s0[off + i], s1[off + i]);
+                    };
+                    float2 F2[NPT], nF2[NPT], div2[NPT];
+                    ld2(own_off + ln + i0, NPT, F2);
+#pragma unroll
+                    for (int i = 0; i < NPT; ++i) nF2[i] = make_float2(-F2[i].x, -F2[i].y);
+                    // ---- first direction
+                    {
+                        float2 F[Q], t[NPT];
+                        ld2(own_off + ln, Q, F);
+                        float2 dv[Q][Q];
+#pragma unroll
+                        for (int i = 0; i < Q; ++i)
+#pragma unroll
+                            for (int j = i + 1; j < Q; ++j) dv[i][j] = sub2(F[j], F[i]);
+#pragma unroll
+                        for (int i = 0; i < NPT; ++i) {
+                            float Dr[Q];
+                            ld_vec<Q>(&sD[sx][i][0], Dr);
+                            t[i] = dup2(0.f);
+#pragma unroll
+                            for (int m = 1; m < Q; ++m) {
+                                const int j = (i + m) % Q;
+                                t[i] = __ffma2_rn(dup2(Dr[j]), j > i ? dv[i][j] : neg2(dv[j][i]), t[i]);
+                            }
+                        }
+                        float2 dn[NPT];
+                        if (!BC || !((bcm >> sx) & 1)) {
+                            float2 NB[Q];
+                            ld2(own_off + (sx ? NS : -NS) + ln, Q, NB);
+                            float Lr[Q];
+                            ld_vec<Q>(&slam[sx][0], Lr);
+#pragma unroll
+                            for (int i = 0; i < NPT; ++i) dn[i] = __fmul2_rn(dup2(sdlam[sx]), F2[i]);
+#pragma unroll
+                            for (int j = 0; j < Q; ++j)
+#pragma unroll
+                                for (int i = 0; i < NPT; ++i)
+                                    dn[i] = __ffma2_rn(dup2(Lr[j]), __fadd2_rn(NB[j], nF2[i]), dn[i]);
+                        } else {
+                            const float2 bv = make_float2((float)__ldg(a.bcval + ((size_t)(0 + sx) * C + 0) * a.Nu + k),
+                                                          (float)__ldg(a.bcval + ((size_t)(0 + sx) * C + 1) * a.Nu + k));
+#pragma unroll
+                            for (int i = 0; i < NPT; ++i) dn[i] = __fadd2_rn(bv, nF2[i]);
+                        }
+                        float Gr[NPT], Er[NPT];
+                        ld_vec<NPT>(&sdg[sx][i0], Gr);
+                        ld_vec<NPT>(&seps[sx][i0], Er);
+                        const float2 cu = dup2(toh0 * u1);
+#pragma unroll
+                        for (int i = 0; i < NPT; ++i) {
+                            t[i] = __ffma2_rn(dup2(Gr[i]), dn[i], __ffma2_rn(dup2(Er[i]), F2[i], t[i]));
+                            div2[i] = __ffma2_rn(cu, t[i], dup2(0.f));
+                        }
+                    }
+                    // ---- second and third directions
+#pragma unroll
+                    for (int dd = 1; dd < 3; ++dd) {
+                        const int sd = dd == 1 ? sy : sz, nd = dd == 1 ? jy : kz;
+                        float2 t[NPT], dn[NPT];
+#pragma unroll
+                        for (int i = 0; i < NPT; ++i) t[i] = dup2(0.f);
+                        float Dr[Q];
+                        ld_vec<Q>(&sDr[sd][nd][0], Dr);
+                        const float4 cf = sCf[sd][nd];
+#pragma unroll
+                        for (int m = 1; m < Q; ++m) {
+                            const int jq = (nd + m) % Q;
+                            float2 Gv[NPT];
+                            ld2(own_off + (dd == 1 ? Q * (jq + Q * kz) : Q * (jy + Q * jq)) + i0, NPT, Gv);
+#pragma unroll
+                            for (int i = 0; i < NPT; ++i) t[i] = __ffma2_rn(dup2(Dr[m]), __fadd2_rn(Gv[i], nF2[i]), t[i]);
+                        }
+                        if (!BC || !((bcm >> (2 * dd + sd)) & 1)) {
+                            float Lr[Q];
+                            ld_vec<Q>(&slam[sd][0], Lr);
+#pragma unroll
+                            for (int i = 0; i < NPT; ++i) dn[i] = __fmul2_rn(dup2(cf.x), F2[i]);
+#pragma unroll
+                            for (int jq = 0; jq < Q; ++jq) {
+                                float2 H[NPT];
+                                ld2((dd == 1 ? (SLOTS + l) * NS + Q * (jq + Q * kz) : (SLOTS + EB + l) * NS + Q * (jy + Q * jq)) + i0,
+                                    NPT, H);
+#pragma unroll
+                                for (int i = 0; i < NPT; ++i) dn[i] = __ffma2_rn(dup2(Lr[jq]), __fadd2_rn(H[i], nF2[i]), dn[i]);
+                            }
+                        } else {
+                            const float2 bv = make_float2((float)__ldg(a.bcval + ((size_t)(2 * dd + sd) * C + 0) * a.Nu + k),
+                                                          (float)__ldg(a.bcval + ((size_t)(2 * dd + sd) * C + 1) * a.Nu + k));
+#pragma unroll
+                            for (int i = 0; i < NPT; ++i) dn[i] = __fadd2_rn(bv, nF2[i]);
+                        }
+                        const float2 cu = dup2(dd == 1 ? toh1 * u2 : toh2 * u3);
+#pragma unroll
+                        for (int i = 0; i < NPT; ++i) {
+                            t[i] = __ffma2_rn(dup2(cf.y), dn[i], __ffma2_rn(dup2(cf.z), F2[i], t[i]));
+                            div2[i] = __ffma2_rn(cu, t[i], div2[i]);
+                        }
+                    }
+                    // ---- equilibrium (once for both), source and Runge--Kutta update
+                    float2 FN[NPT];
+                    if (fa != 0.f) ld2((SLOTS + 2 * EB + l) * NS + ln + i0, NPT, FN);
+#pragma unroll
+                    for (int i = 0; i < NPT; ++i) {
+                        const float c1 = __fsub_rn(u1, V1[i]);
+                        const float g32 = __fmul_rn(E0[i], Eq32::ex2(fmaf(c1, fmaf(A11[i], c1, lin[i]), cst[i])));
+                        const float t1 = u1 - U0x[i];
+                        const float corr = fmaf(t1, fmaf(gm4h[i], t1, gm1[i]), cl[i]);
+                        const float gc = __fmul_rn(g32, corr);
+                        const float2 eqv = make_float2(g32, __fmul_rn(gfac[i], g32));
+                        const float2 eqc = make_float2(gc, __fmul_rn(gfac[i], gc));
+                        const float2 it2 = dup2(itau[i]);
+                        const float2 R = __ffma2_rn(__fadd2_rn(eqv, nF2[i]), it2, __ffma2_rn(eqc, it2, neg2(div2[i])));
+                        const float2 o = rk_update2(F2[i], fa != 0.f ? FN[i] : dup2(0.f), R, fa, fab, fc, fa != 0.f);
+                        outv[0][i] = o.x;
+                        outv[C - 1][i] = o.y;
+                    }
+                    st_vec<NPT>(a.f_out + (size_t)k * slab + pb, outv[0]);
+                    st_vec<NPT>(a.f_out + ((size_t)a.Nu + k) * slab + pb, outv[C - 1]);
+                } else {
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
                     const float *sc = st + c * PER_C;
@@ -599,6 +727,7 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                     }
                     }
                     st_vec<NPT>(a.f_out + ((size_t)c * a.Nu + k) * slab + pb, outv[c]);
+                }
                 }
                 if (mom) {
                     const float cj = trap(j1, vn1);
