@@ -43,10 +43,11 @@ struct LineGeom {
     static constexpr int NQ = C == 2 ? 7 : 6;           // plane quantities per point
     // resident blocks asked of the register allocator: a budget of about 96
     // registers per thread (128 with a whole line per thread)
-    // (Q = 3: 16-element runs, 144 threads in 160: two blocks per SM of up to
-    // 204 registers, no spills; capping at 96 registers with spills was slower,
-    // 53.7 vs 40.7 ms per step on the normal shock)
-    static constexpr int MINB = Q == 3 ? 2
+    // (Q = 3: 16-element runs, 144 threads in 160: three blocks per SM of up
+    // to 136 registers, which the packed F/G body fits without spills -- 28.3
+    // ms of stage per step on the normal shock against 35.7 with two blocks;
+    // the per-component body needed 167 registers)
+    static constexpr int MINB = Q == 3 ? 3
                                        : (65536 / (NTHR * (NPT == Q ? 128 : 96)) > 0 ? 65536 / (NTHR * (NPT == Q ? 128 : 96))
                                                                                       : 1);
     static_assert(Q % NPT == 0, "a thread takes a whole fraction of a line");
