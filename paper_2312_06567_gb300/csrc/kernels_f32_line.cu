@@ -95,27 +95,25 @@ __device__ __forceinline__ void st_vec<1>(float *p, const float (&v)[1]) {
 // Element-wise FR updates over a thread's NPT points.  With NPT even they run
 // on pairs of points with the packed FP32 instructions (two IEEE operations
 // per issue, each rounded exactly as its scalar form), so the results are
-// bit-identical to the scalar sequence of the other FP32 stage kernels;
-// x - y is evaluated as x + (-y), the same IEEE operation.
-template <int N>
-__device__ __forceinline__ void negate(const float (&a)[N], float (&n)[N]) {
-#pragma unroll
-    for (int i = 0; i < N; ++i) n[i] = -a[i];
-}
+// bit-identical to the scalar sequence of the other FP32 stage kernels.
+// x - y, one rounding of the exact difference, is the same IEEE operation as
+// x + (-y) and, paired, fma(y, -1, x) (y * -1 is exact).
+__device__ __forceinline__ float2 sub2(float2 x, float2 y) { return __ffma2_rn(y, make_float2(-1.f, -1.f), x); }
+
 // t[i] = fmaf(D, G[i] - F[i], t[i]), D common to the points
 template <int N>
-__device__ __forceinline__ void acc_dev(float (&t)[N], float D, const float (&G)[N], const float (&nF)[N]) {
+__device__ __forceinline__ void acc_dev(float (&t)[N], float D, const float (&G)[N], const float (&F)[N]) {
     if constexpr (N % 2 == 0) {
         const float2 d2 = make_float2(D, D);
 #pragma unroll
         for (int i = 0; i < N; i += 2) {
-            const float2 dv = __fadd2_rn(make_float2(G[i], G[i + 1]), make_float2(nF[i], nF[i + 1]));
+            const float2 dv = sub2(make_float2(G[i], G[i + 1]), make_float2(F[i], F[i + 1]));
             const float2 r = __ffma2_rn(d2, dv, make_float2(t[i], t[i + 1]));
             t[i] = r.x; t[i + 1] = r.y;
         }
     } else {
 #pragma unroll
-        for (int i = 0; i < N; ++i) t[i] = fmaf(D, __fadd_rn(G[i], nF[i]), t[i]);
+        for (int i = 0; i < N; ++i) t[i] = fmaf(D, __fsub_rn(G[i], F[i]), t[i]);
     }
 }
 // y[i] = c * F[i]
@@ -157,8 +155,14 @@ __device__ __forceinline__ void lift_vec(float (&t)[N], const float *a, const fl
     }
 }
 
-// x - y as one rounding of the exact difference (y * -1 is exact), paired
-__device__ __forceinline__ float2 sub2(float2 x, float2 y) { return __ffma2_rn(y, make_float2(-1.f, -1.f), x); }
+// shared-memory fetch-and-add by one thread, as one PTX atomic (no
+// warp-aggregation sequence around it)
+__device__ __forceinline__ unsigned int atom_add_shared(unsigned int *p, unsigned int v) {
+    unsigned int old;
+    asm volatile("atom.shared.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(smem_u32(p)), "r"(v) : "memory");
+    return old;
+}
+
 __device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
 __device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
 // sum2 on two independent (sum, error) pairs at once
@@ -193,24 +197,26 @@ struct LineAcc {
     }
 };
 
-// LineAcc::add of two points at once, operation for operation
+// LineAcc::add of two points at once, operation for operation; the product
+// errors are taken negated, -(x y - p) = fma(x, -y, p) exactly, and
+// subtracted, so no value is negated per point
 template <int C>
 __device__ __forceinline__ void add_pair(LineAcc<C> &A, LineAcc<C> &B, float cj1, float jt1, float2 F, float2 G) {
     const float2 cF = __fmul2_rn(dup2(cj1), F);
     float2 s = make_float2(A.L[0], B.L[0]), e = make_float2(A.Lc[0], B.Lc[0]);
     sum2x2(s, e, cF);
     A.L[0] = s.x; B.L[0] = s.y; A.Lc[0] = e.x; B.Lc[0] = e.y;
-    const float2 jt = dup2(jt1);
-    const float2 p1 = __fmul2_rn(cF, jt);
+    const float njt1 = -jt1;
+    const float2 p1 = __fmul2_rn(cF, dup2(jt1));
     s = make_float2(A.L[1], B.L[1]); e = make_float2(A.Lc[1], B.Lc[1]);
     sum2x2(s, e, p1);
-    e = __fadd2_rn(e, __ffma2_rn(cF, jt, neg2(p1)));
+    e = sub2(e, __ffma2_rn(cF, dup2(njt1), p1));
     A.L[1] = s.x; B.L[1] = s.y; A.Lc[1] = e.x; B.Lc[1] = e.y;
-    const float2 jj = dup2(__fmul_rn(jt1, jt1));
-    const float2 p2 = __fmul2_rn(cF, jj);
+    const float jj = __fmul_rn(jt1, jt1), njj = __fmul_rn(njt1, jt1);       // exact
+    const float2 p2 = __fmul2_rn(cF, dup2(jj));
     s = make_float2(A.L[2], B.L[2]); e = make_float2(A.Lc[2], B.Lc[2]);
     sum2x2(s, e, p2);
-    e = __fadd2_rn(e, __ffma2_rn(cF, jj, neg2(p2)));
+    e = sub2(e, __ffma2_rn(cF, dup2(njj), p2));
     A.L[2] = s.x; B.L[2] = s.y; A.Lc[2] = e.x; B.Lc[2] = e.y;
     if constexpr (C == 2) {
         s = make_float2(A.L[3], B.L[3]); e = make_float2(A.Lc[3], B.Lc[3]);
@@ -256,7 +262,12 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
     // sCf[side][n] = (dlam, dg_n, eps_n, 0)
     __shared__ __align__(16) float sDr[2][Q][Q];
     __shared__ float4 sCf[2][Q];
-    __shared__ float su1[BGK_MAXV];                      // u1 of the first-axis nodes (the same on every line)
+    // the velocity grid's axis values (a tensor grid: u_d of a velocity
+    // depends on its index on axis d only) with the first axis's trapezoid
+    // factors, so neither the consumers nor the ring refill read the velocity
+    // table from global memory
+    __shared__ float2 su1c[BGK_MAXV];                    // (u1, trapezoid factor) of the first-axis nodes
+    __shared__ float su2[BGK_MAXV], su3[BGK_MAXV];
     __shared__ unsigned int s_exited;
     __shared__ unsigned long long s_wait_ns;
     __shared__ int s_nfill;                              // velocities the ring delivers
@@ -286,7 +297,9 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
             fills[i] = 1;
         }
     }
-    for (int j = tid; j < vn1; j += blockDim.x) su1[j] = __ldg(a.vtab32 + j).x;
+    for (int j = tid; j < vn1; j += blockDim.x) su1c[j] = make_float2(__ldg(a.vtab32 + j).x, trap(j, vn1));
+    for (int j = tid; j < vn2; j += blockDim.x) su2[j] = __ldg(a.vtab32 + (size_t)j * vn1).y;
+    for (int j = tid; j < vn3; j += blockDim.x) su3[j] = __ldg(a.vtab32 + (size_t)j * vn1 * vn2).z;
     load_ops_f32<Q>(a.fr, tid, sD, sdg, seps, slam, sdlam);
     __syncthreads();
     if (tid < 2 * Q * Q) {
@@ -384,8 +397,7 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
             if (j3cur >= 0) flush_plane(j3cur);
             j3cur = j3;
         }
-        const float4 vl = __ldg(a.vtab32 + kl);
-        const float u2 = vl.y, u3 = vl.z;
+        const float u2 = su2[j2], u3 = su3[j3];
         const int sy = u2 > 0.f ? 0 : 1, sz = u3 > 0.f ? 0 : 1;
         // per-point line constants of the equilibrium exponent and the correction
         float lin[NPT], cst[NPT], cl[NPT];
@@ -413,7 +425,7 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
             if (!ok) break;
             if (active) {
                 const float *st = sbuf + (size_t)slot * STAGE;
-                const float u1 = su1[j1];
+                const float u1 = su1c[j1].x;
                 const int sx = u1 > 0.f ? 0 : 1;
                 float outv[C][NPT];
                 if constexpr (C == 2 && NPT == Q && NPT % 2 == 1) {
@@ -547,9 +559,8 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
                     const float *sc = st + c * PER_C;
-                    float Fi[NPT], nFi[NPT];             // this thread's nodes (and their negatives)
+                    float Fi[NPT];                       // this thread's nodes
                     ld_vec<NPT>(sc + own_off + ln + i0, Fi);
-                    negate<NPT>(Fi, nFi);
                     float div[NPT];
                     // ---- first direction: the line itself and the upwind neighbour's line
                     {
@@ -602,7 +613,7 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                                 float NBj[NPT];
 #pragma unroll
                                 for (int i = 0; i < NPT; ++i) NBj[i] = NB[j];
-                                acc_dev<NPT>(dn, Lr[j], NBj, nFi);
+                                acc_dev<NPT>(dn, Lr[j], NBj, Fi);
                             }
                         } else {
                             const float bv = (float)__ldg(a.bcval + ((size_t)(0 + sx) * C + c) * a.Nu + k);
@@ -627,7 +638,7 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                             const int jp = (jy + m) % Q;             // the canonical order
                             float Gv[NPT];
                             ld_vec<NPT>(sc + own_off + Q * (jp + Q * kz) + i0, Gv);
-                            acc_dev<NPT>(t, Dr[m], Gv, nFi);
+                            acc_dev<NPT>(t, Dr[m], Gv, Fi);
                         }
                         if (!BC || !((bcm >> (2 + sy)) & 1)) {
                             float Lr[Q];
@@ -637,7 +648,7 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                             for (int jp = 0; jp < Q; ++jp) {
                                 float H[NPT];
                                 ld_vec<NPT>(sc + (SLOTS + l) * NS + Q * (jp + Q * kz) + i0, H);
-                                acc_dev<NPT>(dn, Lr[jp], H, nFi);
+                                acc_dev<NPT>(dn, Lr[jp], H, Fi);
                             }
                         } else {
                             const float bv = (float)__ldg(a.bcval + ((size_t)(2 + sy) * C + c) * a.Nu + k);
@@ -662,7 +673,7 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                             const int kp = (kz + m) % Q;             // the canonical order
                             float Gv[NPT];
                             ld_vec<NPT>(sc + own_off + Q * (jy + Q * kp) + i0, Gv);
-                            acc_dev<NPT>(t, Dr[m], Gv, nFi);
+                            acc_dev<NPT>(t, Dr[m], Gv, Fi);
                         }
                         if (!BC || !((bcm >> (4 + sz)) & 1)) {
                             float Lr[Q];
@@ -672,7 +683,7 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                             for (int kp = 0; kp < Q; ++kp) {
                                 float H[NPT];
                                 ld_vec<NPT>(sc + (SLOTS + EB + l) * NS + Q * (jy + Q * kp) + i0, H);
-                                acc_dev<NPT>(dn, Lr[kp], H, nFi);
+                                acc_dev<NPT>(dn, Lr[kp], H, Fi);
                             }
                         } else {
                             const float bv = (float)__ldg(a.bcval + ((size_t)(4 + sz) * C + c) * a.Nu + k);
@@ -731,7 +742,7 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                 }
                 }
                 if (mom) {
-                    const float cj = trap(j1, vn1);
+                    const float cj = su1c[j1].y;
                     if constexpr (NPT % 2 == 0) {
 #pragma unroll
                         for (int i = 0; i < NPT; i += 2)
@@ -748,12 +759,18 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
             __syncwarp();
             if (lane == 0) {
                 __threadfence_block();
-                if (atomicAdd(&rel[slot], 1u) == NW - 1) {
+                if (atom_add_shared(&rel[slot], 1u) == NW - 1) {
                     rel[slot] = 0;
                     __threadfence_block();
                     const int inext = (k - k0) + S;
                     if (inext < *(volatile int *)&s_nfill) {
-                        ring_issue<Q, C, EB>(a, g, sbuf, bars, slot, k0 + inext);
+                        // velocity k + S by its axis indices (velocity blocks are whole lines)
+                        int i1 = j1 + S, i2 = j2, i3 = j3;
+                        while (i1 >= vn1) {
+                            i1 -= vn1;
+                            if (++i2 == vn2) { i2 = 0; ++i3; }
+                        }
+                        ring_issue_u<Q, C, EB>(a, g, sbuf, bars, slot, k + S, make_float3(su1c[i1].x, su2[i2], su3[i3]));
                         fills[slot] += 1;
                     }
                 }

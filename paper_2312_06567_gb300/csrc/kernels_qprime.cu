@@ -874,9 +874,12 @@ struct Engine32 {
 // sums T_m = sum_j1 w1 g32 ut1^m, m <= 4, folded per line into the 35 centred
 // moments (as in Engine32) for the Jacobian and the correction's G.  All on
 // the FP32 pipe; every lane returns the moments M (FP32 sums) and the index
-// moment pairs.
+// moment pairs.  tab: the warp's [2 n1] first-axis table, filled here for
+// the point: node j1's (c1, c1, ut, ut) and (ut^3, ut^3, w1, w1), c1 = u1 -
+// V1, ut = u1 - U0_1, w1 the trapezoid factor -- what the walk would
+// otherwise form per velocity, as pairs for its packed instructions.
 __device__ __forceinline__ void fused_pass(const QPrimeArgs &a, int lane, const float *ef, const float *su1,
-                                           float (&M)[35], float (&Js)[7], float (&Jc)[7]) {
+                                           float4 *tab, float (&M)[35], float (&Js)[7], float (&Jc)[7]) {
     const VelGrid &vg = a.vg;
     const int n1 = vg.n[0], n2 = vg.n[1], n3 = vg.n[2];
     const int jc[3] = {(n1 - 1) / 2, (n2 - 1) / 2, (n3 - 1) / 2};
@@ -885,6 +888,16 @@ __device__ __forceinline__ void fused_pass(const QPrimeArgs &a, int lane, const 
     const float U0x = ef[10], o2 = ef[11], o3 = ef[12], dlt = ef[13];
     const float h1 = (float)vg.h[0], h2 = (float)vg.h[1], h3 = (float)vg.h[2];
     const float K = (float)(n1 - jc[0]);
+    __syncwarp();
+    for (int j = lane; j < n1; j += 32) {
+        const float u1 = su1[j];
+        const float c1 = __fsub_rn(u1, e32.V1);
+        const float ut = __fsub_rn(u1, U0x), ut3 = ut * ut * ut;
+        const float w1 = (j == 0 || j == n1 - 1) ? 0.5f : 1.f;
+        tab[2 * j] = make_float4(c1, c1, ut, ut);
+        tab[2 * j + 1] = make_float4(ut3, ut3, w1, w1);
+    }
+    __syncwarp();
 #pragma unroll
     for (int i = 0; i < 35; ++i) M[i] = 0.f;
 #pragma unroll
@@ -943,21 +956,20 @@ __device__ __forceinline__ void fused_pass(const QPrimeArgs &a, int lane, const 
         float2 L0 = qdup2(0.f), C0 = L0, Bs = L0, Bc = L0, Cs = L0, Cc = L0;
         float2 T3 = L0, T4 = L0;
         for (int j1 = 0; j1 < n1; ++j1) {
-            const float u1 = su1[j1];
-            const float2 c1 = qdup2(__fsub_rn(u1, e32.V1));
+            const float4 ta = tab[2 * j1], tb = tab[2 * j1 + 1];
+            const float2 c1 = make_float2(ta.x, ta.y);
             const float2 ex = __ffma2_rn(c1, __ffma2_rn(A11, c1, lin2), cst2);
             const float2 g = __fmul2_rn(E0, make_float2(Eq32::ex2(ex.x), Eq32::ex2(ex.y)));
-            const float2 cg = (j1 == 0 || j1 == n1 - 1) ? __fmul2_rn(qdup2(0.5f), g) : g;     // exact
+            const float2 cg = __fmul2_rn(make_float2(tb.z, tb.w), g);                     // exact
             qsum2x2(L0, C0, cg);
             qsum2x2(Bs, Bc, L0);
             Bc = __fadd2_rn(Bc, C0);
             qsum2x2(Cs, Cc, Bs);
             Cc = __fadd2_rn(Cc, Bc);
             // Jacobian line sums of order 3 and 4 (plain FP32)
-            const float ut = __fsub_rn(u1, U0x), ut3 = ut * ut * ut;
-            const float2 t3 = __fmul2_rn(cg, qdup2(ut3));
+            const float2 t3 = __fmul2_rn(cg, make_float2(tb.x, tb.y));
             T3 = __fadd2_rn(T3, t3);
-            T4 = __ffma2_rn(t3, qdup2(ut), T4);
+            T4 = __ffma2_rn(t3, make_float2(ta.z, ta.w), T4);
         }
         {
             float L1, C1, L2, C2;
@@ -1007,7 +1019,7 @@ template <bool F32>
 __global__ void __launch_bounds__(QB * QW, 2) k_qprime(QPrimeArgs a) {
     __shared__ QPShared<F32> S;
     __shared__ float su1[BGK_MAXV];          // u1 of the first-axis velocity nodes (the same on every line)
-    extern __shared__ double dyn_tab[];      // FP64 engine: [QW][n1][5] tables w1 ut1^m
+    extern __shared__ double dyn_tab[];      // FP64 engine: [QW][n1][5] tables w1 ut1^m; FP32: [QW][2 n1] float4
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int p0 = blockIdx.x * QB;
     const int nb = min(QB, a.P - p0);
@@ -1054,7 +1066,8 @@ __global__ void __launch_bounds__(QB * QW, 2) k_qprime(QPrimeArgs a) {
                 float M[35];
                 if (S.fused[i]) {
                     float Js[7], Jc[7];
-                    fused_pass(a, lane, S.ef[i], su1, M, Js, Jc);
+                    fused_pass(a, lane, S.ef[i], su1, reinterpret_cast<float4 *>(dyn_tab) + (size_t)wib * 2 * a.vg.n[0], M,
+                               Js, Jc);
                     if (lane == 0) {
 #pragma unroll
                         for (int j = 0; j < 7; ++j) { S.Jp[i][2 * j] = Js[j]; S.Jp[i][2 * j + 1] = Jc[j]; }
@@ -1437,12 +1450,32 @@ cudaError_t launch_qprime_tensor(const QPrimeArgs &a, bool fp32_sums, cudaStream
     return cudaGetLastError();
 }
 
+// raise a kernel's dynamic shared-memory limit to `bytes` once per device
+template <typename K>
+cudaError_t allow_dyn_smem(K kernel, SmemLimit &lim, size_t bytes) {
+    size_t *attr = lim.slot();
+    if (!attr) return cudaErrorInvalidDevice;
+    if (bytes > *attr) {
+        const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+        *attr = bytes;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_qprime(const QPrimeArgs &a, bool fp32_sums, cudaStream_t s) {
     const unsigned grid = (unsigned)((a.P + QB - 1) / QB);
     if (fp32_sums) {
-        k_qprime<true><<<grid, QB * QW, 0, s>>>(a);
+        static SmemLimit lim32;
+        const size_t dyn = (size_t)QW * 2 * a.vg.n[0] * sizeof(float4);      // the fused pass's tables
+        const cudaError_t e = allow_dyn_smem(k_qprime<true>, lim32, dyn);
+        if (e != cudaSuccess) return e;
+        k_qprime<true><<<grid, QB * QW, dyn, s>>>(a);
     } else {
+        static SmemLimit lim64;
         const size_t dyn = (size_t)QW * a.vg.n[0] * 5 * sizeof(double);
+        const cudaError_t e = allow_dyn_smem(k_qprime<false>, lim64, dyn);
+        if (e != cudaSuccess) return e;
         k_qprime<false><<<grid, QB * QW, dyn, s>>>(a);
     }
     return cudaGetLastError();

@@ -365,18 +365,18 @@ __device__ __forceinline__ void ring_init(unsigned long long *bars, int S, int c
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// Copy everything velocity k needs into ring slot `slot`: the run, the upwind
-// x element (if outside the run), the upwind y and z runs and (with FN) f^n,
-// with bulk copies that complete on the slot's full barrier (one thread).
+// Copy everything velocity k (components u) needs into ring slot `slot`: the
+// run, the upwind x element (if outside the run), the upwind y and z runs and
+// (with FN) f^n, with bulk copies that complete on the slot's full barrier
+// (one thread).
 template <int Q, int C, int EB, bool FN = true>
-__device__ __forceinline__ void ring_issue(const StageArgs<float> &a, const RunGeom &g, float *sbuf,
-                                           unsigned long long *bars, int slot, int k) {
+__device__ __forceinline__ void ring_issue_u(const StageArgs<float> &a, const RunGeom &g, float *sbuf,
+                                             unsigned long long *bars, int slot, int k, float3 u) {
     using SG = StageGeom<Q, C, EB, FN>;
     constexpr int NS = SG::NS, SLOTS = SG::SLOTS, PER_C = SG::PER_C, STAGE = SG::STAGE, PAD = SG::PAD;
     const size_t slab = (size_t)a.P;
     const uint32_t runb = (uint32_t)(g.nel * NS * 4), elb = PAD * NS * 4;
     const bool with_fn = FN && a.a32 != 0.f;
-    const float4 u = __ldg(a.vtab32 + k);
     const int xe = u.x > 0.f ? g.xn0 : g.xn1, ye = u.y > 0.f ? g.yn0 : g.yn1, ze = u.z > 0.f ? g.zn0 : g.zn1;
     const uint32_t bytes =
         C * (runb + (xe >= 0 ? elb : 0u) + (ye >= 0 ? runb : 0u) + (ze >= 0 ? runb : 0u) + (with_fn ? runb : 0u));
@@ -400,6 +400,13 @@ __device__ __forceinline__ void ring_issue(const StageArgs<float> &a, const RunG
             bulk_g2s(smem_u32(own + (SLOTS + 2 * EB) * NS), a.f_n + ((size_t)c * a.Nu + k) * slab + (size_t)g.e0 * NS,
                      runb, full);
     }
+}
+// the same with u read from the velocity table
+template <int Q, int C, int EB, bool FN = true>
+__device__ __forceinline__ void ring_issue(const StageArgs<float> &a, const RunGeom &g, float *sbuf,
+                                           unsigned long long *bars, int slot, int k) {
+    const float4 u = __ldg(a.vtab32 + k);
+    ring_issue_u<Q, C, EB, FN>(a, g, sbuf, bars, slot, k, make_float3(u.x, u.y, u.z));
 }
 
 // The producer (one thread): for every velocity of [k0, k1) wait until the
