@@ -757,23 +757,26 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
             // release the slot; the warp that releases it last refills it with
             // the velocity S ahead
             __syncwarp();
+            int go = 0;
             if (lane == 0) {
                 __threadfence_block();
                 if (atom_add_shared(&rel[slot], 1u) == NW - 1) {
                     rel[slot] = 0;
                     __threadfence_block();
-                    const int inext = (k - k0) + S;
-                    if (inext < *(volatile int *)&s_nfill) {
-                        // velocity k + S by its axis indices (velocity blocks are whole lines)
-                        int i1 = j1 + S, i2 = j2, i3 = j3;
-                        while (i1 >= vn1) {
-                            i1 -= vn1;
-                            if (++i2 == vn2) { i2 = 0; ++i3; }
-                        }
-                        ring_issue_u<Q, C, EB>(a, g, sbuf, bars, slot, k + S, make_float3(su1c[i1].x, su2[i2], su3[i3]));
-                        fills[slot] += 1;
-                    }
+                    go = (k - k0) + S < *(volatile int *)&s_nfill ? 2 : 1;
                 }
+            }
+            // the whole warp refills the slot (warp-uniform operands; one
+            // elected lane issues the copies)
+            if (__shfl_sync(0xffffffffu, go, 0) == 2) {
+                // velocity k + S by its axis indices (velocity blocks are whole lines)
+                int i1 = j1 + S, i2 = j2, i3 = j3;
+                while (i1 >= vn1) {
+                    i1 -= vn1;
+                    if (++i2 == vn2) { i2 = 0; ++i3; }
+                }
+                ring_issue_u<Q, C, EB, true, true>(a, g, sbuf, bars, slot, k + S, make_float3(su1c[i1].x, su2[i2], su3[i3]));
+                if (lane == 0) fills[slot] += 1;
             }
             if (++slot == S) { slot = 0; par ^= 1u; }
         }

@@ -955,6 +955,9 @@ __device__ __forceinline__ void fused_pass(const QPrimeArgs &a, int lane, const 
         // error-free prefix sums A (= L0), B, C of the line (line_sums_from_prefix)
         float2 L0 = qdup2(0.f), C0 = L0, Bs = L0, Bc = L0, Cs = L0, Cc = L0;
         float2 T3 = L0, T4 = L0;
+        // unrolled by two: one velocity's table loads, exponent and
+        // equilibrium overlap the previous one's dependent sum chains
+#pragma unroll 2
         for (int j1 = 0; j1 < n1; ++j1) {
             const float4 ta = tab[2 * j1], tb = tab[2 * j1 + 1];
             const float2 c1 = make_float2(ta.x, ta.y);

@@ -315,6 +315,22 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const float *src, uint32_
                  "l"(src), "r"(bytes), "r"(bar)
                  : "memory");
 }
+// The same two operations executed by a whole warp with warp-uniform
+// operands: one lane, chosen by elect.sync, performs them.
+__device__ __forceinline__ void mbar_expect_tx_warp(uint32_t bar, uint32_t bytes) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\telect.sync _|p, 0xffffffff;\n\t"
+        "@p mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n\t}" ::"r"(bar),
+        "r"(bytes)
+        : "memory");
+}
+__device__ __forceinline__ void bulk_g2s_warp(uint32_t dst, const float *src, uint32_t bytes, uint32_t bar) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\telect.sync _|p, 0xffffffff;\n\t"
+        "@p cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n\t}" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
 
 // A block of a pipelined stage kernel owns a run of up to EB consecutive
 // elements of one mesh row (first axis); its stage buffer holds, per
@@ -369,7 +385,9 @@ __device__ __forceinline__ void ring_init(unsigned long long *bars, int S, int c
 // run, the upwind x element (if outside the run), the upwind y and z runs and
 // (with FN) f^n, with bulk copies that complete on the slot's full barrier
 // (one thread).
-template <int Q, int C, int EB, bool FN = true>
+// WARP: called by a whole warp with warp-uniform arguments (one elected lane
+// issues), else by one thread.
+template <int Q, int C, int EB, bool FN = true, bool WARP = false>
 __device__ __forceinline__ void ring_issue_u(const StageArgs<float> &a, const RunGeom &g, float *sbuf,
                                              unsigned long long *bars, int slot, int k, float3 u) {
     using SG = StageGeom<Q, C, EB, FN>;
@@ -381,24 +399,28 @@ __device__ __forceinline__ void ring_issue_u(const StageArgs<float> &a, const Ru
     const uint32_t bytes =
         C * (runb + (xe >= 0 ? elb : 0u) + (ye >= 0 ? runb : 0u) + (ze >= 0 ? runb : 0u) + (with_fn ? runb : 0u));
     const uint32_t full = smem_u32(bars + slot);
-    mbar_expect_tx(full, bytes);
+    if constexpr (WARP) mbar_expect_tx_warp(full, bytes);
+    else mbar_expect_tx(full, bytes);
+    auto copy = [&](uint32_t dst, const float *src, uint32_t nb) {
+        if constexpr (WARP) bulk_g2s_warp(dst, src, nb, full);
+        else bulk_g2s(dst, src, nb, full);
+    };
     float *st = sbuf + (size_t)slot * STAGE;
 #pragma unroll
     for (int c = 0; c < C; ++c) {
         const float *src = a.f_s + ((size_t)c * a.Nu + k) * slab;
         float *own = st + c * PER_C;
-        bulk_g2s(smem_u32(own + PAD * NS), src + (size_t)g.e0 * NS, runb, full);
+        copy(smem_u32(own + PAD * NS), src + (size_t)g.e0 * NS, runb);
         // the upwind x neighbour: left of the run into slot PAD - 1 (with the
         // PAD - 1 elements before it), right of it into slot PAD + nel (with
         // the PAD - 1 after it)
         if (xe >= 0)
-            bulk_g2s(smem_u32(own + (u.x > 0.f ? 0 : (g.nel + PAD) * NS)),
-                     src + (size_t)(u.x > 0.f ? xe - (PAD - 1) : xe) * NS, elb, full);
-        if (ye >= 0) bulk_g2s(smem_u32(own + SLOTS * NS), src + (size_t)ye * NS, runb, full);
-        if (ze >= 0) bulk_g2s(smem_u32(own + (SLOTS + EB) * NS), src + (size_t)ze * NS, runb, full);
+            copy(smem_u32(own + (u.x > 0.f ? 0 : (g.nel + PAD) * NS)), src + (size_t)(u.x > 0.f ? xe - (PAD - 1) : xe) * NS,
+                 elb);
+        if (ye >= 0) copy(smem_u32(own + SLOTS * NS), src + (size_t)ye * NS, runb);
+        if (ze >= 0) copy(smem_u32(own + (SLOTS + EB) * NS), src + (size_t)ze * NS, runb);
         if (with_fn)
-            bulk_g2s(smem_u32(own + (SLOTS + 2 * EB) * NS), a.f_n + ((size_t)c * a.Nu + k) * slab + (size_t)g.e0 * NS,
-                     runb, full);
+            copy(smem_u32(own + (SLOTS + 2 * EB) * NS), a.f_n + ((size_t)c * a.Nu + k) * slab + (size_t)g.e0 * NS, runb);
     }
 }
 // the same with u read from the velocity table
