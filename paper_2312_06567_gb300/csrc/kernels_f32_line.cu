@@ -423,7 +423,11 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
             const int k = kl + j1;
             ok = __all_sync(0xffffffffu, mbar_wait_s(smem_u32(bars + slot), par, &s_wait_ns));
             if (!ok) break;
-            if (active) {
+            // every thread computes (an idle one, past the end of a short run,
+            // on stage slots that hold no element of its own: finite or not,
+            // its values are never stored), so the loop body does not diverge;
+            // only the stores depend on `active`
+            {
                 const float *st = sbuf + (size_t)slot * STAGE;
                 const float u1 = su1c[j1].x;
                 const int sx = u1 > 0.f ? 0 : 1;
@@ -553,8 +557,10 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                         outv[0][i] = o.x;
                         outv[C - 1][i] = o.y;
                     }
-                    st_vec<NPT>(a.f_out + (size_t)k * slab + pb, outv[0]);
-                    st_vec<NPT>(a.f_out + ((size_t)a.Nu + k) * slab + pb, outv[C - 1]);
+                    if (active) {
+                        st_vec<NPT>(a.f_out + (size_t)k * slab + pb, outv[0]);
+                        st_vec<NPT>(a.f_out + ((size_t)a.Nu + k) * slab + pb, outv[C - 1]);
+                    }
                 } else {
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
@@ -738,7 +744,7 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                         outv[c][i] = rk_update(Fi[i], fa != 0.f ? FN[i] : 0.f, R, fa, fab, fc, fa != 0.f);
                     }
                     }
-                    st_vec<NPT>(a.f_out + ((size_t)c * a.Nu + k) * slab + pb, outv[c]);
+                    if (active) st_vec<NPT>(a.f_out + ((size_t)c * a.Nu + k) * slab + pb, outv[c]);
                 }
                 }
                 if (mom) {
