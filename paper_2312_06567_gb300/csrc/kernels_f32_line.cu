@@ -28,6 +28,8 @@
 // FP64 index moments accumulate in the moment-partials buffer, which this
 // block owns for its points and velocity block, converted to raw moments at
 // the end.  Dzanic & Martinelli, arXiv 2312.06567, section "Methodology".
+#include <type_traits>
+
 #include "stage_f32_common.cuh"
 
 namespace {
@@ -195,6 +197,28 @@ struct LineAcc {
         Lc[2] = __fadd_rn(Lc[2], fmaf(cF, jj, -p2));
         if (C == 2) sum2(L[C == 2 ? 3 : 0], Lc[C == 2 ? 3 : 0], __fmul_rn(cj1, G));
     }
+    __device__ __forceinline__ float Ls(int q) const { return L[q]; }
+    __device__ __forceinline__ float Lcs(int q) const { return Lc[q]; }
+};
+
+// LineAcc<2>::add of one point on packed FP32, lane for lane the same
+// operations: the (sum, error) pairs (L0, L3) of c F and c G side by side,
+// and (L1, L2) of c F jt and c F jt^2 (their product errors taken negated,
+// fma(x, -y, p) = -(x y - p) exactly, and subtracted)
+struct LineAccFG {
+    float2 A, Ae, B, Be;
+    __device__ __forceinline__ void zero() { A = Ae = B = Be = make_float2(0.f, 0.f); }
+    __device__ __forceinline__ void add(float cj1, float jt1, float F, float G) {
+        const float2 cFG = __fmul2_rn(dup2(cj1), make_float2(F, G));
+        sum2x2(A, Ae, cFG);
+        const float jj = __fmul_rn(jt1, jt1), njt1 = -jt1, njj = __fmul_rn(njt1, jt1);      // exact
+        const float2 cF = dup2(cFG.x);
+        const float2 p = __fmul2_rn(cF, make_float2(jt1, jj));
+        sum2x2(B, Be, p);
+        Be = sub2(Be, __ffma2_rn(cF, make_float2(njt1, njj), p));
+    }
+    __device__ __forceinline__ float Ls(int q) const { return q == 0 ? A.x : q == 1 ? B.x : q == 2 ? B.y : A.y; }
+    __device__ __forceinline__ float Lcs(int q) const { return q == 0 ? Ae.x : q == 1 ? Be.x : q == 2 ? Be.y : Ae.y; }
 };
 
 // LineAcc::add of two points at once, operation for operation; the product
@@ -415,7 +439,9 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                 cl[i] = fmaf(r4.x, t2, fmaf(r4.y, t3, fmaf(0.5f * r5.x, fmaf(t2, t2, t3 * t3), r3.w)));
             }
         }
-        LineAcc<C> acc[NPT];
+        // F and G with an odd number of points: each point's sums as pairs
+        using Acc = typename std::conditional<C == 2 && NPT % 2 == 1, LineAccFG, LineAcc<C>>::type;
+        Acc acc[NPT];
 #pragma unroll
         for (int i = 0; i < NPT; ++i) acc[i].zero();
         float jt1 = (float)(-jc[0]);
@@ -435,17 +461,15 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                 if constexpr (C == 2 && NPT == Q && NPT % 2 == 1) {
                     // F and G of each point as one packed FP32 pair: every
                     // component's operations exactly those of the per-component
-                    // body below (x - y as x + (-y), negation exact), so the
-                    // results are the same bit for bit; the equilibrium is
+                    // body below (x - y as fma(y, -1, x), the same rounding), so
+                    // the results are the same bit for bit; the equilibrium is
                     // evaluated once for both
                     const float *s0 = st, *s1 = st + PER_C;
                     auto ld2 = [&](int off, int n, float2 *v) {
                         for (int i = 0; i < n; ++i) v[i] = make_float2(s0[off + i], s1[off + i]);
                     };
-                    float2 F2[NPT], nF2[NPT], div2[NPT];
+                    float2 F2[NPT], div2[NPT];
                     ld2(own_off + ln + i0, NPT, F2);
-#pragma unroll
-                    for (int i = 0; i < NPT; ++i) nF2[i] = make_float2(-F2[i].x, -F2[i].y);
                     // ---- first direction
                     {
                         float2 F[Q], t[NPT];
@@ -478,12 +502,12 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                             for (int j = 0; j < Q; ++j)
 #pragma unroll
                                 for (int i = 0; i < NPT; ++i)
-                                    dn[i] = __ffma2_rn(dup2(Lr[j]), __fadd2_rn(NB[j], nF2[i]), dn[i]);
+                                    dn[i] = __ffma2_rn(dup2(Lr[j]), sub2(NB[j], F2[i]), dn[i]);
                         } else {
                             const float2 bv = make_float2((float)__ldg(a.bcval + ((size_t)(0 + sx) * C + 0) * a.Nu + k),
                                                           (float)__ldg(a.bcval + ((size_t)(0 + sx) * C + 1) * a.Nu + k));
 #pragma unroll
-                            for (int i = 0; i < NPT; ++i) dn[i] = __fadd2_rn(bv, nF2[i]);
+                            for (int i = 0; i < NPT; ++i) dn[i] = sub2(bv, F2[i]);
                         }
                         float Gr[NPT], Er[NPT];
                         ld_vec<NPT>(&sdg[sx][i0], Gr);
@@ -511,7 +535,7 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                             float2 Gv[NPT];
                             ld2(own_off + (dd == 1 ? Q * (jq + Q * kz) : Q * (jy + Q * jq)) + i0, NPT, Gv);
 #pragma unroll
-                            for (int i = 0; i < NPT; ++i) t[i] = __ffma2_rn(dup2(Dr[m]), __fadd2_rn(Gv[i], nF2[i]), t[i]);
+                            for (int i = 0; i < NPT; ++i) t[i] = __ffma2_rn(dup2(Dr[m]), sub2(Gv[i], F2[i]), t[i]);
                         }
                         if (!BC || !((bcm >> (2 * dd + sd)) & 1)) {
                             float Lr[Q];
@@ -524,13 +548,13 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                                 ld2((dd == 1 ? (SLOTS + l) * NS + Q * (jq + Q * kz) : (SLOTS + EB + l) * NS + Q * (jy + Q * jq)) + i0,
                                     NPT, H);
 #pragma unroll
-                                for (int i = 0; i < NPT; ++i) dn[i] = __ffma2_rn(dup2(Lr[jq]), __fadd2_rn(H[i], nF2[i]), dn[i]);
+                                for (int i = 0; i < NPT; ++i) dn[i] = __ffma2_rn(dup2(Lr[jq]), sub2(H[i], F2[i]), dn[i]);
                             }
                         } else {
                             const float2 bv = make_float2((float)__ldg(a.bcval + ((size_t)(2 * dd + sd) * C + 0) * a.Nu + k),
                                                           (float)__ldg(a.bcval + ((size_t)(2 * dd + sd) * C + 1) * a.Nu + k));
 #pragma unroll
-                            for (int i = 0; i < NPT; ++i) dn[i] = __fadd2_rn(bv, nF2[i]);
+                            for (int i = 0; i < NPT; ++i) dn[i] = sub2(bv, F2[i]);
                         }
                         const float2 cu = dup2(dd == 1 ? toh1 * u2 : toh2 * u3);
 #pragma unroll
@@ -552,7 +576,7 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
                         const float2 eqv = make_float2(g32, __fmul_rn(gfac[i], g32));
                         const float2 eqc = make_float2(gc, __fmul_rn(gfac[i], gc));
                         const float2 it2 = dup2(itau[i]);
-                        const float2 R = __ffma2_rn(__fadd2_rn(eqv, nF2[i]), it2, __ffma2_rn(eqc, it2, neg2(div2[i])));
+                        const float2 R = __ffma2_rn(sub2(eqv, F2[i]), it2, __ffma2_rn(eqc, it2, neg2(div2[i])));
                         const float2 o = rk_update2(F2[i], fa != 0.f ? FN[i] : dup2(0.f), R, fa, fab, fc, fa != 0.f);
                         outv[0][i] = o.x;
                         outv[C - 1][i] = o.y;
@@ -794,13 +818,13 @@ __global__ void __launch_bounds__(LineGeom<Q, C, EB, NPT>::NTHR, LineGeom<Q, C, 
 #pragma unroll
             for (int i = 0; i < NPT; ++i) {
                 float *P = Pme + i * 2 * NQ * NCT;
-                plane_add_s<NQ>(P, NCT, 0, c2, acc[i].L[0], acc[i].Lc[0]);
-                plane_add_s<NQ>(P, NCT, 1, c2, acc[i].L[1], acc[i].Lc[1]);
-                plane_add_s<NQ>(P, NCT, 2, c2, acc[i].L[2], acc[i].Lc[2]);
-                plane_add_s<NQ>(P, NCT, 3, bq, acc[i].L[0], acc[i].Lc[0]);
-                plane_add_s<NQ>(P, NCT, 4, bq, acc[i].L[1], acc[i].Lc[1]);
-                plane_add_s<NQ>(P, NCT, 5, bbq, acc[i].L[0], acc[i].Lc[0]);
-                if (C == 2) plane_add_s<NQ>(P, NCT, NQ - 1, c2, acc[i].L[C == 2 ? 3 : 0], acc[i].Lc[C == 2 ? 3 : 0]);
+                plane_add_s<NQ>(P, NCT, 0, c2, acc[i].Ls(0), acc[i].Lcs(0));
+                plane_add_s<NQ>(P, NCT, 1, c2, acc[i].Ls(1), acc[i].Lcs(1));
+                plane_add_s<NQ>(P, NCT, 2, c2, acc[i].Ls(2), acc[i].Lcs(2));
+                plane_add_s<NQ>(P, NCT, 3, bq, acc[i].Ls(0), acc[i].Lcs(0));
+                plane_add_s<NQ>(P, NCT, 4, bq, acc[i].Ls(1), acc[i].Lcs(1));
+                plane_add_s<NQ>(P, NCT, 5, bbq, acc[i].Ls(0), acc[i].Lcs(0));
+                if (C == 2) plane_add_s<NQ>(P, NCT, NQ - 1, c2, acc[i].Ls(3), acc[i].Lcs(3));
             }
         }
     }
