@@ -601,12 +601,13 @@ def kernel_rooflines(wl, r, peaks, form):
 # DRAM bytes per DOF of a stage launch, mean over the three stages of a step,
 # from ncu captures (dram__bytes_read.sum + dram__bytes_write.sum) of a stage
 # that reads f^n (the second), with the first stage's f^n read (4 B/DOF per
-# component) taken off for the mean: the line kernel on the Taylor--Green
-# physics at 8x8x4 elements, p = 3, 24^3 velocities (12.71 B/DOF captured), and
-# on the normal shock physics at 16x4x4 elements, p = 2, F and G (24.83 B/DOF).
+# component) taken off for the mean: the line kernels on the Taylor--Green
+# physics at 8x8x4 elements, p = 3, 24^3 velocities (4-element runs 12.75 B/DOF
+# captured, 8-element runs 12.77), and on the normal shock physics at 16x4x4
+# elements, p = 2, F and G (25.21 B/DOF).
 # Valid for those kernels as they stand; traffic per DOF does not depend on N_e.
 # Keys: (variant, p, components).
-MEASURED_STAGE_TRAFFIC_PER_DOF = {("line", 3, 1): 11.38, ("line", 2, 2): 22.16}
+MEASURED_STAGE_TRAFFIC_PER_DOF = {("line", 3, 1): 11.42, ("line_wide", 3, 1): 11.44, ("line", 2, 2): 22.54}
 
 
 def tensor_probe_summary(tc, wl, peaks):
