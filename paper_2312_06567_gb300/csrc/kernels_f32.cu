@@ -13,6 +13,8 @@
 // with exact coefficients c2 jt2^b in Kahan-compensated FP32, and the planes
 // in FP64; the index moments J_abc = sum c F jt1^a jt2^b jt3^c are turned
 // into the raw moments sum w u^alpha F in FP64 at the end.
+#include <type_traits>
+
 #include "stage_f32_common.cuh"
 
 namespace {
@@ -72,6 +74,10 @@ __global__ void __launch_bounds__(256, BGK_PLAIN_MINB) k_stage_f32(StageArgs<flo
     __shared__ float seps[2][Q];          // eps_i = sum_j Dt_ij + dg_i  (exact defect, tiny)
     __shared__ float slam[2][Q];          // neighbour-trace weights lambda_j
     __shared__ float sdlam[2];            // sum_j lambda_j - 1 (exact defect, tiny)
+    // CURV: the moment accumulators (the FP64 index moments [11][NT], then the
+    // plane pairs [14][NT]) live in dynamic shared memory, leaving the
+    // registers to the curvilinear operator
+    extern __shared__ __align__(16) double dyn_acc[];
     const int tid = threadIdx.x;
     // Operators and the deviation form.  With f_i the thread's own value,
     //   t_i = sum_j Dt_ij (f_j - f_i) + dg_i dn + eps_i f_i,
@@ -151,8 +157,9 @@ __global__ void __launch_bounds__(256, BGK_PLAIN_MINB) k_stage_f32(StageArgs<flo
     // SSP-RK3 a + b = 1 exactly, which FP32 roundings of a and b would not keep
     // (1/3 and 2/3 both round up in FP32, a 3e-8 mass gain per step).
     const float fa = a.a32, fab = a.ab32, fc = a.c32;
-    IndexMoments acc;
-    acc.init();
+    typename std::conditional<CURV, IndexMomentsS, IndexMoments>::type acc;
+    if constexpr (CURV) acc.init(reinterpret_cast<float *>(dyn_acc + 11 * NT), dyn_acc, NT, tid);
+    else acc.init();
     const size_t slab = (size_t)a.P;
     __syncthreads();
 
@@ -476,8 +483,12 @@ __global__ void __launch_bounds__(256, BGK_PLAIN_MINB) k_stage_f32(StageArgs<flo
     }
     if (acc.j3cur >= 0) acc.flush_plane(trap3(acc.j3cur, vg), (float)(acc.j3cur - jc[2]));
     if (a.part && active) {
-        double m[BGK_NMOM];
-        index_to_raw(acc.J, vg, uc, m);
+        double m[BGK_NMOM], Jv[11];
+        if constexpr (CURV) acc.get(Jv);
+        else
+#pragma unroll
+            for (int q = 0; q < 11; ++q) Jv[q] = acc.J[q];
+        index_to_raw(Jv, vg, uc, m);
 #pragma unroll
         for (int j = 0; j < BGK_NMOM; ++j) a.part[((size_t)vb * BGK_NMOM + j) * a.P + p] = m[j];
     }
@@ -781,8 +792,20 @@ static cudaError_t stage32_q(const StageArgs<float> &a, int C, int n_vblk, cudaS
     constexpr int NS = Q * Q * Q, EB = 256 / NS;
     dim3 grid((a.mesh.Ne + EB - 1) / EB, n_vblk);
     if (a.geo) {
-        if (C == 1) k_stage_f32<Q, 1, true><<<grid, EB * NS, 0, s>>>(a);
-        else k_stage_f32<Q, 2, true><<<grid, EB * NS, 0, s>>>(a);
+        // the curvilinear instantiations' moment accumulators (dynamic shared memory)
+        const size_t dyn = (size_t)EB * NS * (11 * sizeof(double) + 14 * sizeof(float));
+        static SmemLimit lim;
+        size_t *attr = lim.slot();
+        if (!attr) return cudaErrorInvalidDevice;
+        if (dyn > *attr) {
+            cudaError_t e = cudaFuncSetAttribute(k_stage_f32<Q, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_stage_f32<Q, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+            if (e != cudaSuccess) return e;
+            *attr = dyn;
+        }
+        if (C == 1) k_stage_f32<Q, 1, true><<<grid, EB * NS, dyn, s>>>(a);
+        else k_stage_f32<Q, 2, true><<<grid, EB * NS, dyn, s>>>(a);
     } else {
         if (C == 1) k_stage_f32<Q, 1, false><<<grid, EB * NS, 0, s>>>(a);
         else k_stage_f32<Q, 2, false><<<grid, EB * NS, 0, s>>>(a);

@@ -97,10 +97,8 @@ __device__ __forceinline__ void st_vec<1>(float *p, const float (&v)[1]) {
 // Element-wise FR updates over a thread's NPT points.  With NPT even they run
 // on pairs of points with the packed FP32 instructions (two IEEE operations
 // per issue, each rounded exactly as its scalar form), so the results are
-// bit-identical to the scalar sequence of the other FP32 stage kernels.
-// x - y, one rounding of the exact difference, is the same IEEE operation as
-// x + (-y) and, paired, fma(y, -1, x) (y * -1 is exact).
-__device__ __forceinline__ float2 sub2(float2 x, float2 y) { return __ffma2_rn(y, make_float2(-1.f, -1.f), x); }
+// bit-identical to the scalar sequence of the other FP32 stage kernels
+// (x - y as sub2, the pair helpers of stage_f32_common.cuh).
 
 // t[i] = fmaf(D, G[i] - F[i], t[i]), D common to the points
 template <int N>
@@ -165,16 +163,6 @@ __device__ __forceinline__ unsigned int atom_add_shared(unsigned int *p, unsigne
     return old;
 }
 
-__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
-__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
-// sum2 on two independent (sum, error) pairs at once
-__device__ __forceinline__ void sum2x2(float2 &s, float2 &c, float2 v) {
-    const float2 t = __fadd2_rn(s, v);
-    const float2 bp = sub2(t, s);
-    const float2 e = __fadd2_rn(sub2(s, sub2(t, bp)), sub2(v, bp));
-    s = t;
-    c = __fadd2_rn(c, e);
-}
 
 // Line sums of one point (the first level of IndexMoments): F, F jt, F jt^2
 // and, with two components, G; error-free pairs.

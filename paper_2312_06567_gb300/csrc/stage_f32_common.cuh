@@ -20,6 +20,22 @@ __device__ __forceinline__ void sum2(float &s, float &comp, float v) {
     comp = __fadd_rn(comp, e);
 }
 
+// Packed FP32 pairs (two IEEE operations per issue, each rounded exactly as
+// its scalar form).  x - y, one rounding of the exact difference, is the
+// same IEEE operation as x + (-y) and, paired, fma(y, -1, x) (y * -1 is
+// exact).
+__device__ __forceinline__ float2 sub2(float2 x, float2 y) { return __ffma2_rn(y, make_float2(-1.f, -1.f), x); }
+__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
+// sum2 on two independent (sum, error) pairs at once
+__device__ __forceinline__ void sum2x2(float2 &s, float2 &c, float2 v) {
+    const float2 t = __fadd2_rn(s, v);
+    const float2 bp = sub2(t, s);
+    const float2 e = __fadd2_rn(sub2(s, sub2(t, bp)), sub2(v, bp));
+    s = t;
+    c = __fadd2_rn(c, e);
+}
+
 // Index moments (J000, J100, J200, J010, J110, J020, J001, J101, J011, J002, JG)
 // of one thread -> the 11 raw moment slots, W = h1 h2 h3.
 __device__ __forceinline__ void index_to_raw(const double J[11], const VelGrid &vg, const double uc[3],
@@ -68,7 +84,9 @@ __device__ __forceinline__ float2 rk_update2(float2 F, float2 FN, float2 R, floa
 // them in registers would cost the pipelined stage kernel a third of its
 // occupancy.
 struct IndexMomentsS {
-    float L[4], Lc[4];
+    // the current line's (sum, error) pairs as packed pairs: A = (L0, LG) of
+    // c F and c G, B = (L1, L2) of c F jt and c F jt^2
+    float2 A, Ae, B, Be;
     float *P;                 // [14][n]: P[0..6] then Pc[0..6]
     double *J;                // [11][n]
     int n;
@@ -77,25 +95,24 @@ struct IndexMomentsS {
         P = Ps + t;
         J = Js + t;
         n = ncol;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) L[i] = Lc[i] = 0.f;
+        A = Ae = B = Be = make_float2(0.f, 0.f);
 #pragma unroll
         for (int i = 0; i < 14; ++i) P[i * n] = 0.f;
 #pragma unroll
         for (int i = 0; i < 11; ++i) J[i * n] = 0.0;
         j3cur = -1;
     }
+    // IndexMoments::add, lane for lane the same operations on the pairs (the
+    // product errors taken negated, fma(x, -y, p) = -(x y - p) exactly, and
+    // subtracted)
     __device__ __forceinline__ void add(float cj1, float jt1, float F, float G) {
-        const float cF = __fmul_rn(cj1, F);
-        sum2(L[0], Lc[0], cF);
-        const float p1 = __fmul_rn(cF, jt1);
-        sum2(L[1], Lc[1], p1);
-        Lc[1] = __fadd_rn(Lc[1], fmaf(cF, jt1, -p1));
-        const float jj = __fmul_rn(jt1, jt1);
-        const float p2 = __fmul_rn(cF, jj);
-        sum2(L[2], Lc[2], p2);
-        Lc[2] = __fadd_rn(Lc[2], fmaf(cF, jj, -p2));
-        sum2(L[3], Lc[3], __fmul_rn(cj1, G));
+        const float2 cFG = __fmul2_rn(dup2(cj1), make_float2(F, G));
+        sum2x2(A, Ae, cFG);
+        const float jj = __fmul_rn(jt1, jt1), njt1 = -jt1, njj = __fmul_rn(njt1, jt1);      // exact
+        const float2 cF = dup2(cFG.x);
+        const float2 p = __fmul2_rn(cF, make_float2(jt1, jj));
+        sum2x2(B, Be, p);
+        Be = sub2(Be, __ffma2_rn(cF, make_float2(njt1, njj), p));
     }
     __device__ __forceinline__ void plane_add(int i, float c, float sum, float err) {
         float ps = P[i * n], pc = P[(7 + i) * n];
@@ -108,15 +125,14 @@ struct IndexMomentsS {
     }
     __device__ __forceinline__ void end_line(float c2, float jt2) {
         const float a = c2, b = __fmul_rn(c2, jt2), bb = __fmul_rn(__fmul_rn(c2, jt2), jt2);
-        plane_add(0, a, L[0], Lc[0]);
-        plane_add(1, a, L[1], Lc[1]);
-        plane_add(2, a, L[2], Lc[2]);
-        plane_add(3, b, L[0], Lc[0]);
-        plane_add(4, b, L[1], Lc[1]);
-        plane_add(5, bb, L[0], Lc[0]);
-        plane_add(6, a, L[3], Lc[3]);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) L[i] = Lc[i] = 0.f;
+        plane_add(0, a, A.x, Ae.x);
+        plane_add(1, a, B.x, Be.x);
+        plane_add(2, a, B.y, Be.y);
+        plane_add(3, b, A.x, Ae.x);
+        plane_add(4, b, B.x, Be.x);
+        plane_add(5, bb, A.x, Ae.x);
+        plane_add(6, a, A.y, Ae.y);
+        A = Ae = B = Be = make_float2(0.f, 0.f);
     }
     __device__ __forceinline__ void flush_plane(float c3, float jt3) {
         const double c = c3, t = jt3;
