@@ -21,8 +21,13 @@
 // The operands arrive through the copy ring of the node-per-thread pipelined
 // kernel, fed here without a producer warp: the consumer warp that releases
 // a slot last (a shared-memory count, ordered by block-scope fences before
-// and after it) refills the slot for the velocity S ahead (ring_issue), so
-// every register of the block works on the stage.  The FP32 equilibrium
+// and after it) refills the slot for the velocity S ahead (ring_issue_u), as
+// a whole warp with one elected lane issuing the copies, so every register
+// of the block works on the stage.  The velocity grid's axis values sit in
+// shared memory (a tensor grid), so neither the consumers nor the refill
+// wait on a load of the velocity table.  Every thread runs the velocity body
+// (an idle one past the end of a short run only skips its stores), so the
+// body does not diverge.  The FP32 equilibrium
 // parameters come from the record the Q' solve writes beside its FP64 one
 // (BGK_NEQ32), the plane-level moment pairs live in shared memory and the
 // FP64 index moments accumulate in the moment-partials buffer, which this
