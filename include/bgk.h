@@ -290,10 +290,11 @@ BGK_API bgk_status bgk_test_ring_stall(bgk_ctx *ctx, int after, double wait_seco
  * keep the fastest (as bgk_set_stage_kernel would); then, for that kernel, time
  * Q' solve + stage at the velocity blockings from the current count to four
  * times it that split the lines evenly and keep the fastest (as
- * bgk_set_velocity_blocks would).  The state is not
+ * bgk_set_velocity_blocks would); then, at that blocking, time the kernel's
+ * ring depths again and keep the fastest.  The state is not
  * changed; the cached moments are recomputed by the next step.  Outputs (each
  * may be NULL): the chosen variant and depth and its mean time per stage in
- * ms.  The FP64 form has one kernel: only its velocity blocking is chosen (by
+ * ms (at the chosen blocking; for the plain kernel at the default one).  The FP64 form has one kernel: only its velocity blocking is chosen (by
  * the stage's time); returns variant 1 and that kernel's time.  Errors:
  * BGK_EINVAL, BGK_ECUDA, BGK_ETIMEOUT, BGK_ENOCONV (the Q' solve of the
  * current state). */

@@ -1221,6 +1221,31 @@ bgk_status bgk_tune_stage(bgk_ctx *ctx, double dt, int reps, int *variant_out, i
             if (ms / reps < best_nb) { best_nb = ms / reps; pick_nb = n; }
         }
         set_blocking(ctx, pick_nb);
+        // then the ring depths of that kernel again, at the chosen blocking
+        // (the first search timed them at the default one); stage time only
+        if (!st && err == cudaSuccess && pick.v != BGK_STAGE_PLAIN) {
+            StageArgs<float> sn = sp;
+            sn.Kblk = ctx->Kblk;
+            double best_d = 1e300;
+            int pick_d = pick.d;
+            for (int d : {2, 3, 4, 6, 8, 12, 16}) {
+                if (!stage_f32_variant_supported(sn, ctx->C, pick.v, d)) continue;
+                err = launch_stage_f32(sn, ctx->C, ctx->n_vblk, pick.v, d, ctx->stream);      // warm-up
+                if (err == cudaSuccess) err = cudaEventRecord(ea, ctx->stream);
+                for (int r = 0; r < reps && err == cudaSuccess; ++r)
+                    err = launch_stage_f32(sn, ctx->C, ctx->n_vblk, pick.v, d, ctx->stream);
+                if (err == cudaSuccess) err = cudaEventRecord(eb, ctx->stream);
+                if (err == cudaSuccess) err = cudaEventSynchronize(eb);
+                float ms = 0.f;
+                if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, ea, eb);
+                if (err != cudaSuccess) break;
+                if (ms / reps < best_d) { best_d = ms / reps; pick_d = d; }
+            }
+            if (err == cudaSuccess) {
+                pick.d = pick_d;
+                best = best_d;
+            }
+        }
     }
     cudaEventDestroy(ea);
     cudaEventDestroy(eb);
